@@ -1,0 +1,482 @@
+"""Pins of the FP64 oracle against what the paper and the mathematics fix.
+
+The oracle restates the method; these tests check it against things other
+than itself: the Riemann invariants and jump relations of the relaxation
+system (Eqs. relaxh--relaxqs), the Suliciu solver it reduces to at A_g = 0
+(Sec. 3, first property of the relaxation model; Sec. 2 after Eq. bedload
+Grass), conservation of water and sediment (Eq. bedload system), positivity
+(Sec. 3), an independent 50-digit step, the migration direction of dunes and
+antidunes (Sec. 2, eigenvalue discussion; Secs. 5.1, 5.2), and the lack of
+well-balancing (Sec. 4).  ``test_planted_mistakes.py`` checks that plausible
+mistakes planted in a copy of the oracle fail these pins.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1307_0491_gb300 import workloads as W
+from tests import indep
+
+G = 9.81
+
+
+def wl_params(**kw):
+    p = W.base_params(**kw)
+    return p
+
+
+def rand_pairs(seed, n, jump=0.1, bedload="grass", **kw):
+    """Random left/right state pairs around h ~ 1, u ~ 0.4, z ~ 0.1."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for _ in range(n):
+        H = rng.uniform(0.5, 2.0)
+        u = rng.uniform(-1.0, 1.0)
+        v = rng.uniform(-0.5, 0.5)
+        Z = rng.uniform(0.0, 0.5)
+        d = rng.uniform(-jump, jump, size=4)
+        L = (H, H * u, H * v, Z)
+        H2 = H * (1 + d[0])
+        R = (H2, H2 * (u + d[1]), H2 * (v + d[2]), Z + 0.5 * d[3])
+        out.append((L, R))
+    return out
+
+
+# ---------------------------------------------------------------------------
+# closures
+
+@pytest.mark.parametrize("m", [1.0, 2.0, 3.0, 4.0, 2.5])
+def test_grass_closure_closed_form(orc, m):
+    """Q = A_g u |U|^(m_g-1) (Eq. bedload Grass, 2D form) and its derivative."""
+    pw = wl_params(A_g=0.37, m_g=m)
+    P = oracle.Params.from_workload(pw)
+    for (H, un, ut) in [(1.3, 0.7, 0.2), (0.8, -1.1, 0.5), (2.0, 0.3, 0.0), (1.0, -0.4, 0.0)]:
+        c = orc.cell_project(P, (H, H * un, H * ut, 0.0))
+        sp = math.hypot(un, ut)
+        assert c["Om"] == pytest.approx(0.37 * un * sp ** (m - 1), rel=1e-14)
+        # derivative against a central difference in un at fixed H
+        e = 1e-6
+        qp = orc.cell_project(P, (H, H * (un + e), H * ut, 0.0))["Om"]
+        qm = orc.cell_project(P, (H, H * (un - e), H * ut, 0.0))["Om"]
+        assert c["dOm"] == pytest.approx((qp - qm) / (2 * e), rel=1e-7)
+        assert c["Pi"] == pytest.approx(G * H * H / 2, rel=1e-15)
+        assert c["ca"] == pytest.approx(H * math.sqrt(G * H), rel=1e-15)
+    # zero threshold: motion starts with the flow (Sec. 2 after Eq. bedload Grass)
+    c = orc.cell_project(P, (1.0, 1e-9, 0.0, 0.0))
+    assert c["Om"] > 0
+
+
+@pytest.mark.parametrize("fric", ["darcy", "strickler"])
+def test_mpm_closure_closed_form(orc, fric):
+    """q_b = sqrt((s-1) g d_s^3) 8 (tau* - tau*_cr)_+^(3/2) (Eq. MPM), tau* from
+    tau_b = rho g h S_f with the Darcy-Weisbach or Manning S_f (Sec. 2)."""
+    pw = wl_params(bedload="mpm", friction=fric, f_dw=0.02, K_st=30.0)
+    P = oracle.Params.from_workload(pw)
+    for (H, un, ut) in [(0.5, 3.0, 0.4), (0.7, -2.5, 1.0), (0.4, 2.0, 0.0), (1.0, 0.05, 0.0)]:
+        c = orc.cell_project(P, (H, H * un, H * ut, 0.0))
+        sp = math.hypot(un, ut)
+        # tau_b / ((rho_s - rho) g d_s) with tau_b = rho g h S_f, |S_f| from Sec. 2
+        if fric == "darcy":
+            Sf = 0.02 * sp * sp / (8 * G * H)
+        else:
+            Sf = (1 / 30.0) ** 2 * sp * sp / H ** (4 / 3)
+        tstar = G * H * Sf / (1.65 * G * 1e-3)
+        qstar = 8 * max(tstar - 0.05, 0.0) ** 1.5
+        q = qstar * math.sqrt(1.65 * G * 1e-9) * un / sp
+        assert c["Om"] == pytest.approx(q, rel=1e-13, abs=1e-300)
+        e = 1e-6
+        qp = orc.cell_project(P, (H, H * (un + e), H * ut, 0.0))["Om"]
+        qm = orc.cell_project(P, (H, H * (un - e), H * ut, 0.0))["Om"]
+        assert c["dOm"] == pytest.approx((qp - qm) / (2 * e), rel=1e-6, abs=1e-12)
+
+
+# ---------------------------------------------------------------------------
+# one interface
+
+def _invariant_residuals(res, pw, Lc, Rc):
+    """Max relative residual of the 20 invariant relations of the five waves
+    plus the wave-speed relations, recomputed from the primary outputs
+    (tau_k, u_k, v_k, Z_k) of the solver."""
+    g = pw["g"]
+    a, b = res["a"], res["b"]
+    ai, bi = indep.celerities(pw, Lc, Rc)
+    worst = max(abs(a - ai) / ai, abs(b - bi) / bi)
+    K = (a * a - b * b) / (2 * g)
+    tau, u, v, Z, lam = res["tau"], res["u"], res["v"], res["Z"], res["lam"]
+    HL, HR = Lc[0], Rc[0]
+    tL, tR = 1 / HL, 1 / HR
+    uL, uR = Lc[1] / HL, Rc[1] / HR
+    vL, vR = Lc[2] / HL, Rc[2] / HR
+    ZL, ZR = Lc[3], Rc[3]
+    PL, PR = g * HL * HL / 2, g * HR * HR / 2
+    OL, _ = indep.closure(pw, HL, uL, vL)
+    OR, _ = indep.closure(pw, HR, uR, vR)
+    t1, t2, t3, t4 = tau[1:5]
+    u1, u2, u3, u4 = u[1:5]
+    Z1, Z2, Z3, Z4 = Z[1:5]
+    l1, l2, l3, l4, l5 = lam
+    su = abs(uL) + abs(uR) + a * (tL + tR)
+    sp = PL + PR + a * a * (tL + tR)
+    sz = abs(ZL) + abs(ZR) + K * (tL * tL + tR * tR)
+    # Pi of the intermediate states from the a-wave invariants on each side
+    P1 = PL + a * a * (tL - t1)
+    P2 = P1 + a * a * (t1 - t2)
+    P4 = PR + a * a * (tR - t4)
+    P3 = P4 + a * a * (t4 - t3)
+    # Omega of the intermediate states from the b-wave invariants on each side
+    O2 = OL + l2 * (Z2 - Z1)
+    O3 = OR - l4 * (Z4 - Z3)
+    # Z* carries the rounding of K tau^2 (cancellation in Z - K tau^2), so the
+    # Omega relations are measured against (|lambda2| + |lambda4|) * sz
+    so = abs(OL) + abs(OR) + (abs(l2) + abs(l4)) * sz
+    rel = [
+        # lambda1 wave: u - a tau, Z, Omega (Pi + a^2 tau used to define P1)
+        ((u1 - a * t1) - (uL - a * tL)) / su, (Z1 - ZL) / sz,
+        # lambda2 wave: u - b tau, Z - K tau^2
+        ((u2 - b * t2) - (u1 - b * t1)) / su, ((Z2 - K * t2 * t2) - (Z1 - K * t1 * t1)) / sz,
+        # contact: u, Pi, Z, Omega continuous
+        (u3 - u2) / su, (P3 - P2) / sp, (Z3 - Z2) / sz, (O3 - O2) / so,
+        # lambda4 wave
+        ((u4 + b * t4) - (u3 + b * t3)) / su, ((Z4 - K * t4 * t4) - (Z3 - K * t3 * t3)) / sz,
+        # lambda5 wave
+        ((u4 + a * t4) - (uR + a * tR)) / su, (Z4 - ZR) / sz,
+        # tangential velocity passive, jumps only at the contact
+        (v[1] - vL) / (abs(vL) + 1), (v[2] - vL) / (abs(vL) + 1), (v[3] - vR) / (abs(vR) + 1),
+        (v[4] - vR) / (abs(vR) + 1),
+        # wave speeds (linear degeneracy: equal on both sides of each wave)
+        (l1 - (uL - a * tL)) / su, (l1 - (u1 - a * t1)) / su,
+        (l2 - (u1 - b * t1)) / su, (l2 - (u2 - b * t2)) / su,
+        (l3 - u2) / su,
+        (l4 - (u3 + b * t3)) / su, (l4 - (u4 + b * t4)) / su,
+        (l5 - (uR + a * tR)) / su, (l5 - (u4 + a * t4)) / su,
+    ]
+    return max(worst, max(abs(x) for x in rel))
+
+
+@pytest.mark.parametrize("bedload", ["grass", "mpm"])
+def test_riemann_invariants_and_order(orc, bedload):
+    """All Riemann invariants of the five linearly degenerate waves (derived
+    from Eqs. relaxh--relaxqs) hold across the computed fan; the specific
+    volumes are positive and the speeds ordered (Sec. 3: positivity)."""
+    extra = dict(friction="darcy", f_dw=0.02) if bedload == "mpm" else dict(A_g=0.05, m_g=3.0)
+    pw = wl_params(bedload=bedload, **extra)
+    P = oracle.Params.from_workload(pw)
+    pairs = rand_pairs(1, 300, jump=0.2)
+    if bedload == "mpm":  # supercritical flows so that the threshold is exceeded
+        pairs = [((L[0], L[1] + 2.5 * L[0], L[2], L[3]), (R[0], R[1] + 2.5 * R[0], R[2], R[3])) for L, R in pairs]
+    worst = 0.0
+    for L, R in pairs:
+        r = orc.riemann(P, L, R)
+        assert r["status"] == 0
+        assert np.all(r["tau"] > 0)
+        assert np.all(np.diff(r["lam"]) >= 0)
+        worst = max(worst, _invariant_residuals(r, pw, L, R))
+    assert worst < 1e-13, worst
+
+
+def test_riemann_rankine_hugoniot(orc):
+    """Conservative rows: sum_k lambda_k [H]_k = [Hu] (Eq. relaxh) and
+    sum_k lambda_k [Z]_k = [Omega] (Eq. relaxz); per wave lambda_k [H]_k =
+    [Hu]_k; momentum (Eq. relaxq): sum_k lambda_k [Hu]_k = [Hu^2 + Pi] +
+    g sum_{b-waves} Hbar_k [Z]_k with Hbar_k the harmonic mean of H across the
+    wave (what the invariants of the b-waves give for the non-conservative
+    product g H dZ); tangential momentum [Huv]."""
+    pw = wl_params(A_g=0.05, m_g=3.0)
+    P = oracle.Params.from_workload(pw)
+    worst = 0.0
+    for L, R in rand_pairs(2, 300, jump=0.2):
+        r = orc.riemann(P, L, R)
+        assert r["status"] == 0
+        A = r["Am"] + r["Ap"]
+        HL, HR = L[0], R[0]
+        uL, uR = L[1] / HL, R[1] / HR
+        vL, vR = L[2] / HL, R[2] / HR
+        OL, _ = indep.closure(pw, HL, uL, vL)
+        OR, _ = indep.closure(pw, HR, uR, vR)
+        tau, Z = r["tau"], r["Z"]
+        Hb2 = 2 / (tau[1] + tau[2])
+        Hb4 = 2 / (tau[3] + tau[4])
+        mom = (R[1] * uR + G * HR * HR / 2) - (L[1] * uL + G * HL * HL / 2) + G * (
+            Hb2 * (Z[2] - Z[1]) + Hb4 * (Z[4] - Z[3]))
+        scale_q = abs(L[1] * uL) + abs(R[1] * uR) + G * HL * HL
+        worst = max(worst,
+                    abs(A[0] - (R[1] - L[1])) / (abs(L[1]) + abs(R[1]) + 1),
+                    abs(A[3] - (OR - OL)) / (abs(OL) + abs(OR) + (abs(r["lam"][1]) + abs(r["lam"][3])) * (
+                        abs(L[3]) + abs(R[3]) + r["K"] * (tau[1] ** 2 + tau[4] ** 2))),
+                    abs(A[1] - mom) / scale_q,
+                    abs(A[2] - (R[2] * uR - L[2] * uL)) / (abs(L[2] * uL) + abs(R[2] * uR) + 1))
+        # per wave lambda [H] = [Hu]
+        H = 1 / tau
+        H[0], H[5] = HL, HR
+        q = H * r["u"]
+        q[0], q[5] = L[1], R[1]
+        for k in range(5):
+            worst = max(worst, abs(r["lam"][k] * (H[k + 1] - H[k]) - (q[k + 1] - q[k])) / (abs(q[k]) + 1))
+    assert worst < 1e-13, worst
+
+
+def test_riemann_identical_states_zero(orc):
+    """Equal states: p0 = tauL + tauR is the root, all fluctuations vanish
+    exactly (reading R3)."""
+    P = oracle.Params.from_workload(wl_params(A_g=0.1))
+    s = (1.3, 0.4, -0.2, 0.25)
+    r = orc.riemann(P, s, s)
+    assert np.all(r["Am"] == 0) and np.all(r["Ap"] == 0)
+
+
+def test_riemann_reduces_to_suliciu(orc):
+    """A_g = 0 on a flat bed: no sediment, the b-waves carry no jump and the
+    scheme is the Suliciu relaxation solver for shallow water (Sec. 3, first
+    property; Sec. 2: A_g = 0 gives a rigid bed), coded independently."""
+    pw = wl_params(A_g=0.0)
+    P = oracle.Params.from_workload(pw)
+    worst = 0.0
+    for L, R in rand_pairs(3, 300, jump=0.3):
+        R = (R[0], R[1], R[2], L[3])  # flat bed
+        r = orc.riemann(P, L, R)
+        assert r["status"] == 0
+        Am, Ap, a = indep.suliciu_fluct(pw, L, R)
+        assert r["a"] == pytest.approx(a, rel=1e-15)
+        scale = abs(L[1]) + abs(R[1]) + G * max(L[0], R[0]) ** 2
+        for c in range(3):
+            cc = c
+            worst = max(worst, abs(r["Am"][cc] - Am[c]) / scale, abs(r["Ap"][cc] - Ap[c]) / scale)
+        # no sediment: the bed jump vanishes up to the rounding of K tau^2
+        zscale = (abs(r["lam"][1]) + abs(r["lam"][3])) * r["K"] * (r["tau"][1] ** 2 + r["tau"][4] ** 2)
+        assert abs(r["Am"][3]) <= 1e-14 * zscale and abs(r["Ap"][3]) <= 1e-14 * zscale
+    assert worst < 1e-14, worst
+
+
+def test_riemann_against_50_digit_system(orc):
+    """The scalar Newton in p = tau1 + tau4 lands on the same intermediate
+    states as a 50-digit solve of the four contact conditions."""
+    pytest.importorskip("mpmath")
+    pw = wl_params(A_g=0.2, m_g=3.0)
+    P = oracle.Params.from_workload(pw)
+    worst = 0.0
+    for L, R in rand_pairs(4, 25, jump=0.2):
+        r = orc.riemann(P, L, R)
+        Am, Ap, m = indep.mp_fluct(pw, L, R)
+        for k in range(4):
+            worst = max(worst, abs(r["tau"][k + 1] - float(m["tau"][k])) / r["tau"][k + 1])
+        scale = abs(L[1]) + abs(R[1]) + G * max(L[0], R[0]) ** 2
+        for c in range(4):
+            worst = max(worst, abs(r["Am"][c] - float(Am[c])) / scale, abs(r["Ap"][c] - float(Ap[c])) / scale)
+    assert worst < 1e-13, worst
+
+
+# ---------------------------------------------------------------------------
+# whole steps
+
+def _run(orc, w, nsteps, dts=None):
+    P = oracle.Params.from_workload(w["params"])
+    return orc.run(P, nsteps, w["h"], w["hu"], w["hv"], w["z"], dts=dts)
+
+
+@pytest.mark.parametrize("dim", [1, 2])
+def test_single_step_50_digit(orc, dim):
+    """Two steps on a 6-cell (1D) or 4 x 3 (2D) grid, every boundary type,
+    against an independent 50-digit stepper (ghosts, CFL step, fluxes,
+    update, friction)."""
+    pytest.importorskip("mpmath")
+    cases = []
+    if dim == 1:
+        w = W.random_smooth(6, 1, seed=5, dim=1, bc=("periodic", "periodic", "free", "free"), A_g=0.1)
+        cases.append(w)
+        w = W.random_smooth(6, 1, seed=6, dim=1, bc=("inflow_q", "free", "free", "free"), A_g=0.1, q_in=0.35)
+        cases.append(w)
+        w = W.random_smooth(6, 1, seed=7, dim=1, bc=("inflow_qh", "wall", "free", "free"), A_g=0.05, m_g=2.0,
+                            q_in=0.3, h_in=1.05, friction="strickler", K_st=30.0)
+        cases.append(w)
+    else:
+        w = W.random_smooth(4, 3, seed=8, bc=("periodic", "periodic", "periodic", "periodic"), A_g=0.1)
+        cases.append(w)
+        w = W.random_smooth(4, 3, seed=9, bc=("inflow_q", "free", "wall", "free"), A_g=0.1, q_in=0.3,
+                            friction="darcy", f_dw=0.05)
+        cases.append(w)
+        w = W.random_smooth(4, 3, seed=10, bc=("inflow_qh", "free", "free", "wall"), q_in=2.0, h_in=1.0,
+                            bedload="mpm", friction="strickler", K_st=20.0, d_s=5e-4)
+        w["hu"] = w["hu"] * 6.0
+        cases.append(w)
+    for w in cases:
+        p = w["params"]
+        ny = p["ny"] if dim == 2 else 1
+        st = [np.asarray(w[k]).reshape(ny, p["nx"]).tolist() if w[k] is not None else None
+              for k in ("h", "hu", "hv", "z")]
+        if st[2] is None:
+            st[2] = [[0.0] * p["nx"]]
+        r = _run(orc, w, 2)
+        out1, dt1 = indep.mp_step(p, *st)
+        st2 = [[[c[k] for c in row] for row in out1] for k in range(4)]
+        out2, dt2 = indep.mp_step(p, *st2)
+        assert r["dts"][0] == pytest.approx(float(dt1), rel=1e-14)
+        assert r["dts"][1] == pytest.approx(float(dt2), rel=1e-14)
+        names = ("h", "hu", "hv", "z")
+        for k, name in enumerate(names):
+            if dim == 1 and name == "hv":
+                continue
+            mine = np.asarray(r[name]).reshape(ny, p["nx"])
+            ref = np.array([[float(c[k]) for c in row] for row in out2])
+            scale = np.max(np.abs(ref)) + 1e-3
+            assert np.max(np.abs(mine - ref)) / scale < 1e-13, (name, np.max(np.abs(mine - ref)) / scale)
+
+
+@pytest.mark.parametrize("case", ["periodic1d", "periodic2d", "walls1d", "walls2d"])
+def test_mass_conservation(orc, case):
+    """Water and sediment masses are conserved on periodic and walled domains
+    (conservative rows of Eq. bedload system)."""
+    if case == "periodic1d":
+        w = W.random_smooth(64, 1, seed=11, dim=1, bc=("periodic",) * 4, A_g=0.05)
+    elif case == "periodic2d":
+        w = W.random_smooth(24, 16, seed=12, bc=("periodic",) * 4, A_g=0.05)
+    elif case == "walls1d":
+        w = W.random_smooth(64, 1, seed=13, dim=1, bc=("wall",) * 4, A_g=0.05)
+    else:
+        w = W.random_smooth(24, 16, seed=14, bc=("wall",) * 4, A_g=0.05, friction="strickler", K_st=30.0)
+    r = _run(orc, w, 200)
+    p = w["params"]
+    cell = (p["lx"] / p["nx"]) * ((p["ly"] / p["ny"]) if p["dim"] == 2 else 1.0)
+    m0h = np.sum(np.asarray(w["h"])) * cell
+    m0z = np.sum(np.asarray(w["z"])) * cell
+    assert np.max(np.abs(r["diag"][:, 0] - m0h)) / m0h < 1e-13
+    assert np.max(np.abs(r["diag"][:, 1] - m0z)) / m0z < 1e-13
+    assert np.all(r["h"] > 0)
+
+
+def test_momentum_conserved_flat_periodic(orc):
+    """Flat bed, no friction, periodic: sum(hu) is conserved too (Eq. bedload
+    system with z_b,x = 0)."""
+    w = W.random_smooth(64, 1, seed=15, dim=1, bc=("periodic",) * 4, A_g=0.0)
+    w["z"] = np.full_like(w["z"], 0.1)
+    r = _run(orc, w, 200)
+    q0 = np.sum(w["hu"])
+    assert abs(np.sum(r["hu"]) - q0) / np.sum(np.abs(w["hu"])) < 1e-13
+
+
+def test_flat_bed_rigid_bed_stays(orc):
+    """A_g = 0: z stays constant on a flat bed (Sec. 2: rigid bed), up to
+    rounding."""
+    w = W.random_smooth(32, 8, seed=16, bc=("periodic",) * 4, A_g=0.0)
+    w["z"] = np.full_like(w["z"], 0.3)
+    r = _run(orc, w, 50)
+    assert np.max(np.abs(r["z"] - 0.3)) < 1e-14
+
+
+def test_positivity_thin_dam_break(orc):
+    """Dam break onto a 1 mm layer at CFL 0.5: the depth stays positive
+    (Sec. 3: positivity of the relaxation solver)."""
+    w = W.thin_dam_break(200, 1e-3)
+    r = _run(orc, w, 400)
+    assert np.all(r["h"] > 0)
+    assert np.min(r["h"]) < 2e-3
+
+
+def test_2d_y_invariant_equals_1d(orc):
+    """2D on y-invariant data (v = 0, periodic in y) with the time steps of the
+    1D run reproduces the 1D run in every row."""
+    w1 = W.dune1d(nx=200, nsteps=300)
+    w1["params"]["lx"] = 200.0
+    r1 = _run(orc, w1, 300)
+    ny = 5
+    p2 = dict(w1["params"])
+    p2.update(dim=2, ny=ny, ly=5.0, bc=("periodic", "periodic", "periodic", "periodic"))
+    w2 = dict(params=p2, h=np.tile(w1["h"], (ny, 1)), hu=np.tile(w1["hu"], (ny, 1)),
+              hv=np.zeros((ny, 200)), z=np.tile(w1["z"], (ny, 1)))
+    r2 = _run(orc, w2, 300, dts=r1["dts"])
+    for name in ("h", "hu", "z"):
+        ref = r1[name]
+        err = np.max(np.abs(r2[name] - ref[None, :])) / np.max(np.abs(ref))
+        assert err < 1e-14, (name, err)
+    assert np.all(r2["hv"] == 0)
+
+
+def _centroid(z, base, dx):
+    w = np.clip(z - base, 0, None)
+    x = (np.arange(z.size) + 0.5) * dx
+    return np.sum(w * x) / np.sum(w)
+
+
+def _sediment_celerity(h, q, A_g, m_g=3.0):
+    """Sediment wave speed of the quasi-linear SVE system: the root of the
+    characteristic polynomial p_A(lambda) = -lambda[(u - lambda)^2 - g h] +
+    g h (beta lambda + alpha) of Sec. 2 that is smallest in magnitude, with
+    alpha = dq_b/dh, beta = dq_b/d(hu) for Grass q_b = A_g u^m_g."""
+    u = q / h
+    beta = A_g * m_g * u ** (m_g - 1) / h
+    alpha = -u * beta
+    gh = G * h
+    # -l^3 + 2u l^2 - (u^2 - gh - gh beta) l + gh alpha
+    roots = np.roots([-1.0, 2 * u, -(u * u - gh - gh * beta), gh * alpha])
+    roots = roots[np.abs(roots.imag) < 1e-12].real
+    return roots[np.argmin(np.abs(roots))]
+
+
+def test_dune_moves_downstream_at_sediment_celerity(orc):
+    """Fr < 1 (1D dune test of Sec. 5.1, A_g = 1, m_g = 3): the bump migrates
+    downstream (Sec. 2, eigenvalue discussion), and once the start-up
+    transient has left (t in [200 s, 700 s], T = 700 s as in Sec. 5.1) its
+    centroid moves within 10 % of the sediment eigenvalue of A(W) at the
+    undisturbed state."""
+    nx = 400
+    w = W.paper_dune1d(nx=nx)
+    P = oracle.Params.from_workload(w["params"])
+    dx = 1000.0 / nx
+    # advance to t ~ 200 s, then to t ~ 700 s (CFL steps)
+    st = (w["h"], w["hu"], w["z"])
+    t = 0.0
+    marks = []
+    for target in (200.0, 700.0):
+        while t < target:
+            r = orc.run(P, 50, *st[:2], None, st[2], t0=t)
+            st = (r["h"], r["hu"], r["z"])
+            t = r["t"]
+        marks.append((t, _centroid(st[2], 0.1, dx)))
+    speed = (marks[1][1] - marks[0][1]) / (marks[1][0] - marks[0][0])
+    lam_s = _sediment_celerity(10.0 - 0.1, 10.0, 1.0)
+    assert lam_s > 0 and speed > 0
+    assert abs(speed - lam_s) / lam_s < 0.10, (speed, lam_s)
+
+
+def test_antidune_moves_upstream_at_sediment_celerity(orc):
+    """Fr > 1 (1D antidune test of Sec. 5.2, A_g = 1e-3, m_g = 3, with a 5 cm
+    bump so that the supercritical Bernoulli profile exists over the crest):
+    the bump migrates upstream (Sec. 2, eigenvalue discussion; Sec. 5.2), at
+    the sediment eigenvalue of A(W) at the inflow state within 10 %."""
+    nx = 480
+    w = W.paper_antidune1d(nx=nx, bump=0.05, A_g=1e-3)
+    P = oracle.Params.from_workload(w["params"])
+    dx = 24.0 / nx
+    c0 = _centroid(w["z"], 0.0, dx)
+    r = orc.run(P, 1500, w["h"], w["hu"], None, w["z"])
+    c1 = _centroid(r["z"], 0.0, dx)
+    speed = (c1 - c0) / r["t"]
+    lam_s = _sediment_celerity(0.5, 1.7, 1e-3)
+    assert lam_s < 0 and speed < 0
+    assert abs(speed - lam_s) / abs(lam_s) < 0.10, (speed, lam_s)
+
+
+def test_not_well_balanced(orc):
+    """Lake at rest over a bump is not preserved (Sec. 4: the scheme is not
+    well balanced); the spurious velocity shrinks when the grid is refined."""
+    umax = []
+    for nx in (50, 100, 200):
+        w = W.lake_at_rest(nx)
+        r = _run(orc, w, 4 * nx // 50 * 10)
+        umax.append(np.max(np.abs(r["hu"] / r["h"])))
+    assert umax[0] > 1e-6
+    assert umax[2] < umax[1] < umax[0]
+
+
+def test_cfl_rule(orc):
+    """CFL step (reading R5) from an independent computation of the extreme
+    wave speeds."""
+    w = W.random_smooth(8, 5, seed=17, bc=("inflow_q", "free", "wall", "free"), q_in=0.3, A_g=0.1)
+    p = w["params"]
+    P = oracle.Params.from_workload(p)
+    dt = orc.cfl(P, w["h"], w["hu"], w["hv"], w["z"])
+    out, dtm = indep.mp_step(p, w["h"].tolist(), w["hu"].tolist(), w["hv"].tolist(), w["z"].tolist())
+    assert dt == pytest.approx(float(dtm), rel=1e-14)
