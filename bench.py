@@ -1,0 +1,309 @@
+#!/usr/bin/env python
+"""Benchmark of the Saint-Venant--Exner relaxation step on GB300.
+
+Workload: the 2D dune channel, FP64 (1024 x 512 cells over 1000 x 500 m,
+Gaussian dune, Grass m_g = 3, A_g = 1e-3, Strickler K = 40, inflow / free
+boundaries).  One "step" = one time step of the whole hot path: interface
+Riemann solves + CFL reduction (interface kernel) and cell update +
+friction + projection + ghosts + mass sums (cell kernel).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line (rank 0).  N > 1 (torchrun): every rank runs its own
+replica of the workload (independent runs, no data-path collective: weak
+scaling); the time is the max over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "2D cell-updates/s"
+UNIT = "cell-updates/s"
+BYTES_PER_CELL_FP64 = 64           # read h, hu, hv, zb once + write once (FP64)
+# algorithmic FP64 operations of one interface solve (+, -, *, /, sqrt
+# counted as one each; comparisons not counted), from the operation list of
+# the solver: celerities and constants, one F/F' evaluation, one Newton
+# update, intermediate states and fluctuations
+FLOP_SETUP, FLOP_EVAL, FLOP_UPDATE, FLOP_FINAL = 30, 76, 4, 75
+FP64_PEAK_FLOPS = 152 * 2 * 2 * 2070e6   # 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz
+L2_FLUSH_BYTES = 256 << 20
+
+
+def workload_desc(nx, ny):
+    return (f"2D dune FP64 {nx}x{ny} (1000x500 m, Gaussian dune, Grass m_g=3 A_g=1e-3, Strickler K=40, "
+            f"inflow q=0.5 / free outflow)")
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except Exception:
+        return {}
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.dev = device_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "200",
+                 "-i", str(self.dev)], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.remove(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        smax = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower().startswith("active")})
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def cpu_oracle_rate(w, budget_s: float = 10.0, max_steps: int = 20):
+    """The FP64 oracle on the host, as it stands, on the full grid of the
+    workload for as many steps as fit in about budget_s (at least 1)."""
+    import oracle
+
+    o = oracle.get()
+    P = oracle.Params.from_workload(w["params"])
+    cells = w["params"]["nx"] * w["params"]["ny"]
+    t0 = time.perf_counter()
+    r = o.run(P, 1, w["h"], w["hu"], w["hv"], w["z"])
+    t1 = time.perf_counter()
+    first = t1 - t0
+    more = int(max(0, min(max_steps - 1, math.floor(budget_s / max(first, 1e-9)) - 1)))
+    if more > 0:
+        t2 = time.perf_counter()
+        o.run(P, more, r["h"], r["hu"], r["hv"], r["z"])
+        t3 = time.perf_counter()
+        steps, secs = more, t3 - t2
+    else:
+        steps, secs = 1, first
+    return cells * steps / secs, steps, secs
+
+
+def run_reference(args, world, rank):
+    """Reference arm: the FP64 CPU oracle timed on the host cores, one full
+    grid step per step."""
+    if rank != 0:
+        return 0
+    import oracle
+    from paper_1307_0491_gb300 import workloads as W
+
+    w = W.dune2d()
+    nx, ny = w["params"]["nx"], w["params"]["ny"]
+    o = oracle.get()
+    P = oracle.Params.from_workload(w["params"])
+    st = (w["h"], w["hu"], w["hv"], w["z"])
+    for _ in range(args.warmup):
+        r = o.run(P, 1, *st)
+        st = (r["h"], r["hu"], r["hv"], r["z"])
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        r = o.run(P, 1, *st)
+        st = (r["h"], r["hu"], r["hv"], r["z"])
+    secs = time.perf_counter() - t0
+    value = nx * ny * args.steps / secs
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": secs / args.steps * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": workload_desc(nx, ny), "nx": nx, "ny": ny, "precision": "fp64"},
+        "cpu_baseline": {"kind": "oracle", "cores": 1, "value": value, "unit": UNIT,
+                         "sample": f"full {nx}x{ny} grid, {args.steps} steps after {args.warmup} warm-up steps, "
+                                   f"single-threaded C oracle (-O2, no FMA contraction)"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args, world, rank, local):
+    import torch
+
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    from paper_1307_0491_gb300 import build as B
+    from paper_1307_0491_gb300 import sve
+    from paper_1307_0491_gb300 import workloads as W
+
+    B.build()
+    w = W.dune2d(seed=rank)
+    nx, ny = w["params"]["nx"], w["params"]["ny"]
+    cells = nx * ny
+    stream = torch.cuda.current_stream()
+    solver = sve.Solver(w["params"], "fp64", stream=stream.cuda_stream)
+    solver.set_state(w["h"], w["hu"], w["hv"], w["z"])
+    for _ in range(args.warmup):
+        solver.step(1)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    n_iface = (nx + 1) * ny + nx * (ny + 1)
+    c0 = solver.counters()
+    solver.profile(True)
+    clocks = ClockSampler(local)
+    clocks.start()
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.barrier()
+    torch.cuda.synchronize()
+    for k in range(args.steps):
+        flush.zero_()                      # L2 flush between timed steps (outside the events)
+        ev[k][0].record(stream)
+        solver.step_async(1)
+        ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clk = clocks.stop()
+    solver.sync()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    total_ms = float(np.sum(step_ms))
+    prof = solver.profile_read()
+    solver.profile(False)
+    c1 = solver.counters()
+    if world > 1:
+        t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms_per_step = total_ms / args.steps
+    value = world * cells * args.steps / (total_ms * 1e-3)
+
+    # dominant kernel: the interface kernel (Riemann solves), FP64-ALU bound
+    updates = (c1["newton_iters"] - c0["newton_iters"]) / (n_iface * args.steps)
+    flop_iface = FLOP_SETUP + (1 + updates) * FLOP_EVAL + updates * FLOP_UPDATE + FLOP_FINAL
+    iface_ms = prof["iface_ms"] / max(prof["iface_launches"], 1)
+    cell_ms = prof["cell_ms"] / max(prof["cell_launches"], 1)
+    achieved = n_iface * flop_iface / (iface_ms * 1e-3)
+    pk = peaks()
+    hbm = pk.get("hbm_gbs", 6800.3)
+    roofline = {"bound": "alu", "achieved": achieved / 1e12, "peak": FP64_PEAK_FLOPS / 1e12, "unit": "TFLOP/s",
+                "frac": achieved / FP64_PEAK_FLOPS, "traffic": None,
+                "kernel": "interface_kernel<double>", "peak_source": "152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz "
+                "(GB300 FP64 nominal 1.25 TFLOP/s); a measured DFMA loop gave 1.19 TFLOP/s",
+                "flop_per_interface": flop_iface, "newton_updates_per_solve": updates,
+                "iface_ms": iface_ms, "cell_ms": cell_ms,
+                "hbm_frac_of_step": (BYTES_PER_CELL_FP64 * cells / (ms_per_step * 1e-3)) / (hbm * 1e9),
+                "hbm_peak_gbs": hbm}
+
+    # end to end through the C ABI from pinned host memory
+    e2e_steps = min(args.steps, 10)
+    host_in = {k: torch.from_numpy(np.ascontiguousarray(w[k])).pin_memory() for k in ("h", "hu", "hv", "z")}
+    host_out = {k: torch.empty_like(host_in[k]).pin_memory() for k in host_in}
+    ptr = {k: host_in[k].data_ptr() for k in host_in}
+    optr = {k: host_out[k].data_ptr() for k in host_out}
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        rc = sve.sve_set_state(solver.h, ptr["h"], ptr["hu"], ptr["hv"], ptr["z"], sve.SVE_HOST)
+        rc = rc or sve.sve_step(solver.h, 1)[0]
+        rc = rc or sve.sve_get_state(solver.h, optr["h"], optr["hu"], optr["hv"], optr["z"], sve.SVE_HOST)
+        if rc:
+            raise sve.SveError(rc, "e2e step")
+    e2e_s = time.perf_counter() - t0
+    if world > 1:
+        t = torch.tensor([e2e_s], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    io_bytes = 4 * 8 * cells
+    e2e = {"value": world * cells * e2e_steps / e2e_s, "unit": UNIT, "h2d_bytes_per_step": io_bytes,
+           "d2h_bytes_per_step": io_bytes, "steps": e2e_steps}
+    solver.close()
+
+    line = None
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": workload_desc(nx, ny), "nx": nx, "ny": ny, "precision": "fp64",
+                       "per_rank": "independent replica (seed = rank)",
+                       "l2": f"flushed between timed steps ({L2_FLUSH_BYTES >> 20} MiB write outside the events)"},
+            "roofline": roofline,
+            "e2e": e2e,
+            "gpu_launches": int(prof["iface_launches"] + prof["cell_launches"]),
+            "clocks": clk,
+        }
+        if world == 1 and not args.no_cpu_baseline:
+            rate, nsteps, secs = cpu_oracle_rate(w)
+            line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
+                                    "sample": f"full {nx}x{ny} grid, {nsteps} step(s) in {secs:.1f} s, "
+                                              f"single-threaded C oracle"}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    world, rank, local = dist_setup()
+    if args.impl == "reference":
+        return run_reference(args, world, rank)
+    return run_ours(args, world, rank, local)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,187 @@
+/*
+ * sve.h -- C ABI of libsve, the GB300 (sm_103a) time stepper for the
+ * Saint-Venant--Exner system with the relaxation-solver interface fluxes of
+ * Audusse, Delestre, Le, Masson-Fauchier, Navaro, Serra, "Parallelization of
+ * a relaxation scheme modelling the bedload transport of sediments in shallow
+ * water flow" (arXiv:1307.0491).
+ *
+ * One step (Sec. 3, the procedure stated after the list of properties of the
+ * relaxation model): project the auxiliary variables to equilibrium
+ * (Pi = g h^2/2, Omega = q_b; lambda -> 0 in Eqs. relaxpi, relaxqs), solve
+ * the homogeneous relaxation Riemann problem (Eqs. relaxh--relaxqs) at every
+ * interface, and average the juxtaposed Riemann solutions over each cell
+ * (Godunov); then apply semi-implicit friction (S_f laws of Sec. 2).  The 2D
+ * step is the unsplit method of lines on a structured grid (Sec. 4).  The time
+ * step is the global CFL step of the current state.
+ *
+ * Conventions
+ *   - State: four fields h, hu, hv, zb (water depth, x and y discharge, bed
+ *     elevation), each nx*ny values, row-major [ny][nx] with x fastest.  In
+ *     1D (dim = 1) ny = 1 and hv is ignored (pass NULL).
+ *   - Precision: SVE_FP64 state arrays are double; SVE_FP32 state arrays are
+ *     float (the time, time step and mass sums stay double).
+ *   - where = SVE_HOST: pointers are host memory; SVE_DEVICE: pointers are
+ *     device memory of the current device, contiguous, of the state type.
+ *   - Ownership: the caller owns every buffer it passes; the library copies on
+ *     set and writes into the caller's buffers on get.  The library owns its
+ *     device state, scratch, status word and CUDA graph.
+ *   - Streams: all device work is enqueued on the handle's stream (default:
+ *     the legacy default stream; see sve_set_stream).
+ *   - Errors: every int-returning call returns SVE_OK (0) or a negative
+ *     SVE_ERR_* code; sve_strerror names it.  Device-detected errors (a
+ *     Riemann solve that does not converge, a non-positive depth, a NaN, a bad
+ *     time step) are latched in a device status word; the step calls return
+ *     the latched code.  A handle is not thread-safe.
+ */
+#ifndef SVE_H
+#define SVE_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- codes -------------------------------------------------------------- */
+enum {
+  SVE_OK = 0,
+  SVE_ERR_ARG = -1,       /* invalid argument or configuration */
+  SVE_ERR_CUDA = -2,      /* a CUDA runtime call failed */
+  SVE_ERR_OOM = -3,       /* device allocation failed */
+  SVE_ERR_NEG_DEPTH = -4, /* a depth became <= 0 */
+  SVE_ERR_RIEMANN = -5,   /* an interface Riemann problem had no solution with positive specific volumes */
+  SVE_ERR_NAN = -6,       /* a non-finite value appeared in the state */
+  SVE_ERR_DT = -7,        /* a time step was <= 0 or non-finite */
+  SVE_ERR_STATE = -8      /* no state has been set on the handle */
+};
+
+enum { SVE_FP64 = 0, SVE_FP32 = 1 };                       /* state precision */
+enum { SVE_GRASS = 0, SVE_MPM = 1 };                       /* bedload law */
+enum { SVE_FRIC_NONE = 0, SVE_FRIC_DARCY = 1, SVE_FRIC_STRICKLER = 2 };
+enum { SVE_BC_PERIODIC = 0, SVE_BC_FREE = 1, SVE_BC_INFLOW_Q = 2, SVE_BC_INFLOW_QH = 3, SVE_BC_WALL = 4 };
+enum { SVE_HOST = 0, SVE_DEVICE = 1 };
+enum { SVE_W = 0, SVE_E = 1, SVE_S = 2, SVE_N = 3 };
+
+/* ---- configuration -------------------------------------------------------
+ * dim           1 or 2.
+ * nx, ny        cells (ny = 1 in 1D).
+ * lx, ly        domain lengths [m]; dx = lx/nx, dy = ly/ny.
+ * g             gravity [m/s^2].
+ * cfl           CFL number of the time step: dt = cfl dx / Sx (1D),
+ *               dt = cfl / (Sx/dx + Sy/dy) (2D), S = max over interfaces of
+ *               the extreme relaxation wave speeds |u - a/h|, |u + a/h|.
+ * precision     SVE_FP64 or SVE_FP32 (state storage and arithmetic).
+ * bedload       SVE_GRASS: q_b = A_g u |u|^(m_g - 1) (Eq. bedload Grass, 2D:
+ *               vector u); SVE_MPM: Meyer-Peter & Mueller (Eq. MPM) with
+ *               tau* from the friction law (non-dimensional form of Sec. 2).
+ * A_g, m_g      Grass constants (1 <= m_g <= 4).
+ * s, d_s, tau_cr  MPM: relative density, grain diameter [m], critical Shields.
+ * friction      SVE_FRIC_NONE / _DARCY (f_dw) / _STRICKLER (K_st = 1/n).
+ * bc[4]         W, E, S, N ghost rules: PERIODIC (both sides of an axis),
+ *               FREE (copy), INFLOW_Q (inward normal discharge q_in, h and
+ *               zb copied), INFLOW_QH (h = h_in as well), WALL (mirror).
+ * q_in, h_in    inflow data.
+ * kappa_a, beta_min, gamma_z  relaxation celerities of one interface:
+ *               a = max(kappa_a max(a0, b0), sqrt(b^2 + 2 g gamma_z |dzb| hmax^2)),
+ *               b = max(b0, beta_min a0), with a0 = max h sqrt(g h) and
+ *               b0 = max sqrt((h u)^2 + g h^2 dq_b/du) the bounds of Eq. (ab).
+ * newton_tol, newton_maxit   stopping rule of the scalar Newton iteration of
+ *               each Riemann solve (|dp| <= tol p).
+ */
+typedef struct sve_config {
+  int dim;
+  int nx, ny;
+  double lx, ly, g;
+  double cfl;
+  int precision;
+  int bedload;
+  double A_g, m_g;
+  double s, d_s, tau_cr;
+  int friction;
+  double f_dw, K_st;
+  int bc[4];
+  double q_in, h_in;
+  double kappa_a, beta_min, gamma_z;
+  double newton_tol;
+  int newton_maxit;
+} sve_config;
+
+typedef struct sve_handle sve_handle;
+
+/* Fill *cfg with the defaults (2D, FP64, g = 9.81, cfl = 0.9, Grass A_g = 1e-3,
+ * m_g = 3, MPM s = 2.65, d_s = 1e-3, tau_cr = 0.05, no friction, periodic in
+ * x, free in y, kappa_a = 1.1, beta_min = 0.01, gamma_z = 2, newton_tol =
+ * 1e-12, newton_maxit = 30).  Sizes must still be set. */
+int sve_config_default(sve_config* cfg);
+
+/* Validate cfg, allocate the device state and scratch on the current device
+ * and return a handle in *out.  SVE_ERR_ARG on an invalid configuration,
+ * SVE_ERR_OOM if device memory runs out. */
+int sve_create(const sve_config* cfg, sve_handle** out);
+
+/* Use the CUDA stream `stream` (a cudaStream_t, NULL = legacy default) for
+ * all later work of the handle. */
+int sve_set_stream(sve_handle* h, void* stream);
+
+/* Copy a state in (t is reset to 0).  hv may be NULL in 1D.  The state is
+ * checked on the device (depth > 0, finite): the first failing check is
+ * returned. */
+int sve_set_state(sve_handle* h, const void* depth, const void* hu, const void* hv, const void* zb, int where);
+
+/* Advance nsteps CFL steps.  *t_out (nullable) receives the simulated time.
+ * Blocks until the steps are done and returns the first latched device
+ * error, if any. */
+int sve_step(sve_handle* h, int nsteps, double* t_out);
+
+/* Advance nsteps steps of the given sizes dts[0..nsteps-1] (host memory). */
+int sve_step_dt(sve_handle* h, int nsteps, const double* dts);
+
+/* Copy the state out (interior cells only).  hv may be NULL in 1D.  Blocks
+ * until the copy is done. */
+int sve_get_state(sve_handle* h, void* depth, void* hu, void* hv, void* zb, int where);
+
+/* Diagnostics after the last step: mass_h = sum h dx dy, mass_z = sum zb dx dy
+ * (FP64, summed in a fixed order), the simulated time and the last time step.
+ * Any pointer may be NULL.  Blocks. */
+int sve_get_diag(sve_handle* h, double* mass_h, double* mass_z, double* t, double* last_dt);
+
+/* Time steps of the last sve_step / sve_step_dt call: copies min(n, steps of
+ * that call) values into dts (host).  Returns the number copied (>= 0) or an
+ * error code. */
+int sve_get_dts(sve_handle* h, double* dts, int n);
+
+/* Release everything the handle owns.  NULL is accepted. */
+void sve_destroy(sve_handle* h);
+
+/* Static text for a code. */
+const char* sve_strerror(int code);
+
+/* Number of kernel launches the last sve_step / sve_step_dt /
+ * sve_step_async call enqueued (inside graphs or not). */
+long long sve_last_launch_count(sve_handle* h);
+
+/* Enqueue nsteps CFL steps on the handle's stream and return without waiting
+ * (the step of Sec. 3, as in sve_step).  Device errors are latched and
+ * returned by sve_sync or by any later blocking call. */
+int sve_step_async(sve_handle* h, int nsteps);
+
+/* Wait for the handle's enqueued work; return the latched device status. */
+int sve_sync(sve_handle* h);
+
+/* Kernel timing.  on != 0: later steps are launched one by one (no graph)
+ * and bracketed by CUDA events on the handle's stream; the totals restart
+ * at 0.  on == 0 switches it off. */
+int sve_profile(sve_handle* h, int on);
+
+/* Device time [ms] and launch count accumulated since sve_profile(h, 1):
+ * index 0 = interface kernel (Riemann solves), 1 = cell kernel (update).
+ * ms and launches point to two elements each.  Blocks. */
+int sve_profile_read(sve_handle* h, double* ms, long long* launches);
+
+/* Counters since the last sve_set_state: steps taken and Newton updates
+ * summed over all interface Riemann solves.  Either pointer may be NULL.
+ * Blocks; returns the latched device status. */
+int sve_get_counters(sve_handle* h, long long* steps, unsigned long long* newton_iters);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SVE_H */

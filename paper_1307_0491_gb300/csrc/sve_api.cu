@@ -1,0 +1,507 @@
+// sve_api.cu -- host side of libsve: handle, device memory, state transfer,
+// the step loop (CUDA graphs of step pairs) and error reporting.  The C ABI is
+// declared in include/sve.h.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <vector>
+
+#include "../../include/sve.h"
+#include "sve_device.cuh"
+
+using sve::DevParams;
+using sve::DevScalars;
+using sve::DevState;
+
+namespace {
+
+constexpr int kGraphSteps = 16;  // steps per captured graph
+
+struct Graph {
+  cudaGraphExec_t exec = nullptr;
+};
+
+}  // namespace
+
+struct sve_handle {
+  sve_config cfg;
+  DevParams P;
+  int device = 0;
+  cudaStream_t stream = nullptr;   // user stream (nullptr = legacy default)
+  cudaStream_t capture = nullptr;  // private stream used only to capture graphs
+  bool has_state = false;
+  size_t elem = 8;                 // bytes per state element
+  long long next = 0;              // padded cells
+  void* fields[13] = {};           // h hu hv z tau u v pi omx omy ca cbx cby
+  void* fx = nullptr;
+  void* fy = nullptr;
+  double* spart = nullptr;
+  double* mpart = nullptr;
+  DevScalars* sc = nullptr;
+  double* dtlog = nullptr;
+  int dtlog_cap = 0;
+  double* fixed = nullptr;
+  int fixed_cap = 0;
+  int nb_iface = 0, nb_cell = 0;
+  Graph graph[2];                  // [fixed]
+  long long last_launches = 0;
+  int last_steps = 0;
+  // kernel timing (sve_profile): 3 events per step, read back lazily
+  bool profiling = false;
+  std::vector<cudaEvent_t> events;
+  size_t events_used = 0;
+  double prof_ms[2] = {0.0, 0.0};
+  long long prof_launches[2] = {0, 0};
+};
+
+namespace {
+
+#define SVE_TRY(expr)                         \
+  do {                                        \
+    cudaError_t _e = (expr);                  \
+    if (_e != cudaSuccess) return SVE_ERR_CUDA; \
+  } while (0)
+
+int status_to_code(int st) {
+  if (st & sve::ST_NAN) return SVE_ERR_NAN;
+  if (st & sve::ST_NEG_DEPTH) return SVE_ERR_NEG_DEPTH;
+  if (st & sve::ST_RIEMANN) return SVE_ERR_RIEMANN;
+  if (st & sve::ST_DT) return SVE_ERR_DT;
+  return SVE_OK;
+}
+
+int validate(const sve_config* c) {
+  if (!c) return SVE_ERR_ARG;
+  if (c->dim != 1 && c->dim != 2) return SVE_ERR_ARG;
+  if (c->nx < 1 || c->ny < 1 || (c->dim == 1 && c->ny != 1)) return SVE_ERR_ARG;
+  if ((long long)c->nx * c->ny > (1LL << 31) - 1) return SVE_ERR_ARG;
+  if (!(c->lx > 0) || (c->dim == 2 && !(c->ly > 0)) || !(c->g > 0) || !(c->cfl > 0)) return SVE_ERR_ARG;
+  if (c->precision != SVE_FP64 && c->precision != SVE_FP32) return SVE_ERR_ARG;
+  if (c->bedload != SVE_GRASS && c->bedload != SVE_MPM) return SVE_ERR_ARG;
+  if (c->bedload == SVE_GRASS && (!(c->m_g >= 1.0) || !(c->m_g <= 4.0) || !(c->A_g >= 0.0))) return SVE_ERR_ARG;
+  if (c->friction < SVE_FRIC_NONE || c->friction > SVE_FRIC_STRICKLER) return SVE_ERR_ARG;
+  if (c->bedload == SVE_MPM && (c->friction == SVE_FRIC_NONE || !(c->s > 1.0) || !(c->d_s > 0.0))) return SVE_ERR_ARG;
+  if (c->friction == SVE_FRIC_STRICKLER && !(c->K_st > 0)) return SVE_ERR_ARG;
+  if (c->friction == SVE_FRIC_DARCY && !(c->f_dw >= 0)) return SVE_ERR_ARG;
+  const int nsides = c->dim == 2 ? 4 : 2;
+  for (int s = 0; s < nsides; ++s)
+    if (c->bc[s] < SVE_BC_PERIODIC || c->bc[s] > SVE_BC_WALL) return SVE_ERR_ARG;
+  if ((c->bc[0] == SVE_BC_PERIODIC) != (c->bc[1] == SVE_BC_PERIODIC)) return SVE_ERR_ARG;
+  if (c->dim == 2 && (c->bc[2] == SVE_BC_PERIODIC) != (c->bc[3] == SVE_BC_PERIODIC)) return SVE_ERR_ARG;
+  if (!(c->kappa_a > 1.0) || !(c->beta_min > 0.0) || !(c->gamma_z >= 0.0)) return SVE_ERR_ARG;
+  if (!(c->newton_tol > 0.0) || c->newton_maxit < 1 || c->newton_maxit > 1000) return SVE_ERR_ARG;
+  return SVE_OK;
+}
+
+void make_params(const sve_config* c, DevParams* P) {
+  memset(P, 0, sizeof(*P));
+  P->dim = c->dim;
+  P->nx = c->nx;
+  P->ny = c->dim == 2 ? c->ny : 1;
+  P->ex = c->nx + 2;
+  P->dx = c->lx / c->nx;
+  P->dy = c->dim == 2 ? c->ly / c->ny : 1.0;
+  P->inv_dx = 1.0 / P->dx;
+  P->inv_dy = 1.0 / P->dy;
+  P->g = c->g;
+  P->cfl = c->cfl;
+  P->bedload = c->bedload;
+  P->A_g = c->A_g;
+  P->m_g = c->m_g;
+  P->m_int = (c->m_g == 1.0 || c->m_g == 2.0 || c->m_g == 3.0 || c->m_g == 4.0) ? (int)c->m_g : 0;
+  const double sm1 = c->s - 1.0;
+  P->mpm_C = 8.0 * sqrt(sm1 * c->g * c->d_s * c->d_s * c->d_s);
+  if (c->friction == SVE_FRIC_DARCY) {
+    P->mpm_alpha = c->f_dw / (8.0 * c->g * sm1 * c->d_s);
+  } else if (c->friction == SVE_FRIC_STRICKLER) {
+    const double n = 1.0 / c->K_st;
+    P->mpm_alpha = (n * n) / (sm1 * c->d_s);
+  }
+  P->tau_cr = c->tau_cr;
+  P->friction = c->friction;
+  if (c->friction == SVE_FRIC_DARCY) P->fric_c = c->f_dw / 8.0;
+  else if (c->friction == SVE_FRIC_STRICKLER) P->fric_c = c->g / (c->K_st * c->K_st);
+  for (int s = 0; s < 4; ++s) P->bc[s] = c->bc[s];
+  P->q_in = c->q_in;
+  P->h_in = c->h_in;
+  P->kappa_a = c->kappa_a;
+  P->beta_min = c->beta_min;
+  P->gamma_z = c->gamma_z;
+  P->newton_tol = c->newton_tol;
+  P->newton_maxit = c->newton_maxit;
+  P->nfx = (long long)(P->nx + 1) * P->ny;
+  P->nfy = P->dim == 2 ? (long long)P->nx * (P->ny + 1) : 0;
+  P->nbx = (int)((P->nfx + sve::kThreads - 1) / sve::kThreads);
+  P->nby = (int)((P->nfy + sve::kThreads - 1) / sve::kThreads);
+}
+
+template <typename T>
+DevState<T> state_of(const sve_handle* h) {
+  DevState<T> S;
+  T** f[13] = {&S.h, &S.hu, &S.hv, &S.z, &S.tau, &S.u, &S.v, &S.pi, &S.omx, &S.omy, &S.ca, &S.cbx, &S.cby};
+  for (int k = 0; k < 13; ++k) *f[k] = (T*)h->fields[k];
+  S.fx = (T*)h->fx;
+  S.fy = (T*)h->fy;
+  return S;
+}
+
+template <typename T>
+void launch_step(sve_handle* h, cudaStream_t st, int fixed, cudaEvent_t* ev) {
+  DevState<T> S = state_of<T>(h);
+  if (ev) cudaEventRecord(ev[0], st);
+  sve::interface_kernel<T><<<h->nb_iface, sve::kThreads, 0, st>>>(h->P, S, h->sc, h->spart, h->fixed, h->dtlog, fixed);
+  if (ev) cudaEventRecord(ev[1], st);
+  sve::cell_kernel<T><<<h->nb_cell, sve::kThreads, 0, st>>>(h->P, S, h->sc, h->mpart);
+  if (ev) cudaEventRecord(ev[2], st);
+}
+
+void launch_step_any(sve_handle* h, cudaStream_t st, int fixed, cudaEvent_t* ev = nullptr) {
+  if (h->cfg.precision == SVE_FP64) launch_step<double>(h, st, fixed, ev);
+  else launch_step<float>(h, st, fixed, ev);
+}
+
+// Three events for one profiled step (grown on demand).
+cudaEvent_t* next_events(sve_handle* h) {
+  while (h->events.size() < h->events_used + 3) {
+    cudaEvent_t e;
+    if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+    h->events.push_back(e);
+  }
+  cudaEvent_t* ev = &h->events[h->events_used];
+  h->events_used += 3;
+  return ev;
+}
+
+// Fold the recorded events into the per-kernel totals (waits for them).
+int drain_events(sve_handle* h) {
+  for (size_t k = 0; k + 3 <= h->events_used; k += 3) {
+    float a = 0.f, b = 0.f;
+    if (cudaEventSynchronize(h->events[k + 2]) != cudaSuccess) return SVE_ERR_CUDA;
+    if (cudaEventElapsedTime(&a, h->events[k], h->events[k + 1]) != cudaSuccess) return SVE_ERR_CUDA;
+    if (cudaEventElapsedTime(&b, h->events[k + 1], h->events[k + 2]) != cudaSuccess) return SVE_ERR_CUDA;
+    h->prof_ms[0] += a;
+    h->prof_ms[1] += b;
+    h->prof_launches[0] += 1;
+    h->prof_launches[1] += 1;
+  }
+  h->events_used = 0;
+  return SVE_OK;
+}
+
+int ensure_capacity(double** buf, int* cap, int n) {
+  if (n <= *cap) return SVE_OK;
+  int ncap = n > 2 * *cap ? n : 2 * *cap;
+  double* nb = nullptr;
+  if (cudaMalloc(&nb, sizeof(double) * (size_t)ncap) != cudaSuccess) return SVE_ERR_OOM;
+  if (*buf) cudaFree(*buf);
+  *buf = nb;
+  *cap = ncap;
+  return SVE_OK;
+}
+
+int get_graph(sve_handle* h, int fixed, cudaGraphExec_t* out) {
+  Graph& G = h->graph[fixed ? 1 : 0];
+  if (!G.exec) {
+    cudaGraph_t g = nullptr;
+    SVE_TRY(cudaStreamBeginCapture(h->capture, cudaStreamCaptureModeThreadLocal));
+    for (int s = 0; s < kGraphSteps; ++s) launch_step_any(h, h->capture, fixed);
+    cudaError_t e = cudaStreamEndCapture(h->capture, &g);
+    if (e != cudaSuccess) return SVE_ERR_CUDA;
+    e = cudaGraphInstantiate(&G.exec, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) { G.exec = nullptr; return SVE_ERR_CUDA; }
+  }
+  *out = G.exec;
+  return SVE_OK;
+}
+
+void drop_graphs(sve_handle* h) {
+  for (auto& G : h->graph) {
+    if (G.exec) cudaGraphExecDestroy(G.exec);
+    G.exec = nullptr;
+  }
+}
+
+// Enqueue nsteps steps on the handle's stream (graphs of kGraphSteps steps
+// where possible; single launches with events when profiling).
+int enqueue_steps(sve_handle* h, int nsteps, int fixed) {
+  if (!h->has_state) return SVE_ERR_STATE;
+  double* old = h->dtlog;
+  int rc = ensure_capacity(&h->dtlog, &h->dtlog_cap, nsteps > 0 ? nsteps : 1);
+  if (rc) return rc;
+  if (h->dtlog != old) drop_graphs(h);  // graphs hold the dtlog pointer
+  SVE_TRY(cudaMemsetAsync(&h->sc->call_step, 0, sizeof(int), h->stream));
+  int done = 0;
+  if (nsteps >= kGraphSteps && !h->profiling) {
+    cudaGraphExec_t ex;
+    rc = get_graph(h, fixed, &ex);
+    if (rc) return rc;
+    for (; done + kGraphSteps <= nsteps; done += kGraphSteps) SVE_TRY(cudaGraphLaunch(ex, h->stream));
+  }
+  for (; done < nsteps; ++done) {
+    cudaEvent_t* ev = h->profiling ? next_events(h) : nullptr;
+    if (h->profiling && !ev) return SVE_ERR_CUDA;
+    launch_step_any(h, h->stream, fixed, ev);
+  }
+  SVE_TRY(cudaGetLastError());
+  h->last_launches = 2LL * nsteps;
+  h->last_steps = nsteps;
+  return SVE_OK;
+}
+
+int wait_status(sve_handle* h) {
+  DevScalars s;
+  SVE_TRY(cudaMemcpyAsync(&s, h->sc, sizeof(s), cudaMemcpyDeviceToHost, h->stream));
+  SVE_TRY(cudaStreamSynchronize(h->stream));
+  return status_to_code(s.status);
+}
+
+int run_steps(sve_handle* h, int nsteps, int fixed) {
+  int rc = enqueue_steps(h, nsteps, fixed);
+  if (rc) return rc;
+  return wait_status(h);
+}
+
+}  // namespace
+
+extern "C" {
+
+int sve_config_default(sve_config* c) {
+  if (!c) return SVE_ERR_ARG;
+  memset(c, 0, sizeof(*c));
+  c->dim = 2;
+  c->nx = 0;
+  c->ny = 0;
+  c->lx = 1.0;
+  c->ly = 1.0;
+  c->g = 9.81;
+  c->cfl = 0.9;
+  c->precision = SVE_FP64;
+  c->bedload = SVE_GRASS;
+  c->A_g = 1e-3;
+  c->m_g = 3.0;
+  c->s = 2.65;
+  c->d_s = 1e-3;
+  c->tau_cr = 0.05;
+  c->friction = SVE_FRIC_NONE;
+  c->bc[0] = SVE_BC_PERIODIC;
+  c->bc[1] = SVE_BC_PERIODIC;
+  c->bc[2] = SVE_BC_FREE;
+  c->bc[3] = SVE_BC_FREE;
+  c->kappa_a = 1.1;
+  c->beta_min = 0.01;
+  c->gamma_z = 2.0;
+  c->newton_tol = 1e-12;
+  c->newton_maxit = 30;
+  return SVE_OK;
+}
+
+int sve_create(const sve_config* cfg, sve_handle** out) {
+  if (!out) return SVE_ERR_ARG;
+  *out = nullptr;
+  int rc = validate(cfg);
+  if (rc) return rc;
+  sve_handle* h = new sve_handle();
+  h->cfg = *cfg;
+  make_params(cfg, &h->P);
+  if (cudaGetDevice(&h->device) != cudaSuccess) { delete h; return SVE_ERR_CUDA; }
+  h->elem = cfg->precision == SVE_FP64 ? 8 : 4;
+  h->next = (long long)(h->P.nx + 2) * (h->P.ny + 2);
+  h->nb_iface = h->P.nbx + h->P.nby;
+  h->nb_cell = (int)(((long long)h->P.nx * h->P.ny + sve::kThreads - 1) / sve::kThreads);
+  bool ok = true;
+  for (int k = 0; k < 13 && ok; ++k) ok = cudaMalloc(&h->fields[k], h->elem * (size_t)h->next) == cudaSuccess;
+  ok = ok && cudaMalloc(&h->fx, 8 * h->elem * (size_t)h->P.nfx) == cudaSuccess;
+  ok = ok && cudaMalloc(&h->fy, 8 * h->elem * (size_t)(h->P.nfy > 0 ? h->P.nfy : 1)) == cudaSuccess;
+  ok = ok && cudaMalloc(&h->spart, sizeof(double) * (size_t)h->nb_iface) == cudaSuccess;
+  ok = ok && cudaMalloc(&h->mpart, 2 * sizeof(double) * (size_t)h->nb_cell) == cudaSuccess;
+  ok = ok && cudaMalloc(&h->sc, sizeof(DevScalars)) == cudaSuccess;
+  if (!ok) { sve_destroy(h); return SVE_ERR_OOM; }
+  if (ensure_capacity(&h->dtlog, &h->dtlog_cap, 1024)) { sve_destroy(h); return SVE_ERR_OOM; }
+  if (ensure_capacity(&h->fixed, &h->fixed_cap, 1024)) { sve_destroy(h); return SVE_ERR_OOM; }
+  if (cudaStreamCreateWithFlags(&h->capture, cudaStreamNonBlocking) != cudaSuccess) { sve_destroy(h); return SVE_ERR_CUDA; }
+  for (int k = 0; k < 13; ++k) cudaMemset(h->fields[k], 0, h->elem * (size_t)h->next);
+  cudaMemset(h->sc, 0, sizeof(DevScalars));
+  if (cudaDeviceSynchronize() != cudaSuccess) { sve_destroy(h); return SVE_ERR_CUDA; }
+  *out = h;
+  return SVE_OK;
+}
+
+int sve_set_stream(sve_handle* h, void* stream) {
+  if (!h) return SVE_ERR_ARG;
+  h->stream = (cudaStream_t)stream;
+  return SVE_OK;
+}
+
+int sve_set_state(sve_handle* h, const void* depth, const void* hu, const void* hv, const void* zb, int where) {
+  if (!h || !depth || !hu || !zb || (h->cfg.dim == 2 && !hv)) return SVE_ERR_ARG;
+  if (where != SVE_HOST && where != SVE_DEVICE) return SVE_ERR_ARG;
+  const DevParams& P = h->P;
+  const size_t row = h->elem * (size_t)P.nx;
+  const size_t pitch = h->elem * (size_t)P.ex;
+  const cudaMemcpyKind kind = where == SVE_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+  const void* src[4] = {depth, hu, h->cfg.dim == 2 ? hv : nullptr, zb};
+  for (int f = 0; f < 4; ++f) {
+    char* dst = (char*)h->fields[f] + h->elem * (size_t)(P.ex + 1);
+    if (src[f]) SVE_TRY(cudaMemcpy2DAsync(dst, pitch, src[f], row, row, P.ny, kind, h->stream));
+    else SVE_TRY(cudaMemsetAsync(h->fields[f], 0, h->elem * (size_t)h->next, h->stream));
+  }
+  SVE_TRY(cudaMemsetAsync(h->sc, 0, sizeof(DevScalars), h->stream));
+  if (h->cfg.precision == SVE_FP64)
+    sve::init_kernel<double><<<h->nb_cell, sve::kThreads, 0, h->stream>>>(P, state_of<double>(h), h->sc, h->mpart);
+  else
+    sve::init_kernel<float><<<h->nb_cell, sve::kThreads, 0, h->stream>>>(P, state_of<float>(h), h->sc, h->mpart);
+  SVE_TRY(cudaGetLastError());
+  DevScalars s;
+  SVE_TRY(cudaMemcpyAsync(&s, h->sc, sizeof(s), cudaMemcpyDeviceToHost, h->stream));
+  SVE_TRY(cudaStreamSynchronize(h->stream));
+  h->has_state = true;
+  h->last_steps = 0;
+  return status_to_code(s.status);
+}
+
+int sve_step(sve_handle* h, int nsteps, double* t_out) {
+  if (!h || nsteps < 0) return SVE_ERR_ARG;
+  int rc = run_steps(h, nsteps, 0);
+  if (t_out && rc != SVE_ERR_CUDA) {
+    double t = 0;
+    if (cudaMemcpy(&t, &h->sc->t, sizeof(double), cudaMemcpyDeviceToHost) == cudaSuccess) *t_out = t;
+  }
+  return rc;
+}
+
+int sve_step_dt(sve_handle* h, int nsteps, const double* dts) {
+  if (!h || nsteps < 0 || (nsteps > 0 && !dts)) return SVE_ERR_ARG;
+  for (int k = 0; k < nsteps; ++k)
+    if (!(dts[k] > 0.0) || !isfinite(dts[k])) return SVE_ERR_ARG;
+  double* old = h->fixed;
+  int rc = ensure_capacity(&h->fixed, &h->fixed_cap, nsteps > 0 ? nsteps : 1);
+  if (rc) return rc;
+  if (h->fixed != old) drop_graphs(h);
+  if (nsteps > 0)
+    SVE_TRY(cudaMemcpyAsync(h->fixed, dts, sizeof(double) * (size_t)nsteps, cudaMemcpyHostToDevice, h->stream));
+  return run_steps(h, nsteps, 1);
+}
+
+int sve_get_state(sve_handle* h, void* depth, void* hu, void* hv, void* zb, int where) {
+  if (!h) return SVE_ERR_ARG;
+  if (!h->has_state) return SVE_ERR_STATE;
+  if (where != SVE_HOST && where != SVE_DEVICE) return SVE_ERR_ARG;
+  const DevParams& P = h->P;
+  const size_t row = h->elem * (size_t)P.nx;
+  const size_t pitch = h->elem * (size_t)P.ex;
+  const cudaMemcpyKind kind = where == SVE_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
+  void* dst[4] = {depth, hu, hv, zb};
+  for (int f = 0; f < 4; ++f) {
+    if (!dst[f] || (f == 2 && h->cfg.dim == 1)) continue;
+    const char* src = (const char*)h->fields[f] + h->elem * (size_t)(P.ex + 1);
+    SVE_TRY(cudaMemcpy2DAsync(dst[f], row, src, pitch, row, P.ny, kind, h->stream));
+  }
+  SVE_TRY(cudaStreamSynchronize(h->stream));
+  return SVE_OK;
+}
+
+int sve_get_diag(sve_handle* h, double* mass_h, double* mass_z, double* t, double* last_dt) {
+  if (!h) return SVE_ERR_ARG;
+  if (!h->has_state) return SVE_ERR_STATE;
+  DevScalars s;
+  SVE_TRY(cudaMemcpyAsync(&s, h->sc, sizeof(s), cudaMemcpyDeviceToHost, h->stream));
+  SVE_TRY(cudaStreamSynchronize(h->stream));
+  if (mass_h) *mass_h = s.mass_h;
+  if (mass_z) *mass_z = s.mass_z;
+  if (t) *t = s.t;
+  if (last_dt) *last_dt = s.dt;
+  return status_to_code(s.status);
+}
+
+int sve_get_dts(sve_handle* h, double* dts, int n) {
+  if (!h || n < 0 || (n > 0 && !dts)) return SVE_ERR_ARG;
+  int m = n < h->last_steps ? n : h->last_steps;
+  if (m > 0) {
+    SVE_TRY(cudaMemcpyAsync(dts, h->dtlog, sizeof(double) * (size_t)m, cudaMemcpyDeviceToHost, h->stream));
+    SVE_TRY(cudaStreamSynchronize(h->stream));
+  }
+  return m;
+}
+
+void sve_destroy(sve_handle* h) {
+  if (!h) return;
+  drop_graphs(h);
+  cudaStreamSynchronize(h->stream);
+  for (auto e : h->events) cudaEventDestroy(e);
+  for (auto& f : h->fields)
+    if (f) cudaFree(f);
+  if (h->fx) cudaFree(h->fx);
+  if (h->fy) cudaFree(h->fy);
+  if (h->spart) cudaFree(h->spart);
+  if (h->mpart) cudaFree(h->mpart);
+  if (h->sc) cudaFree(h->sc);
+  if (h->dtlog) cudaFree(h->dtlog);
+  if (h->fixed) cudaFree(h->fixed);
+  if (h->capture) cudaStreamDestroy(h->capture);
+  delete h;
+}
+
+const char* sve_strerror(int code) {
+  switch (code) {
+    case SVE_OK: return "ok";
+    case SVE_ERR_ARG: return "invalid argument";
+    case SVE_ERR_CUDA: return "CUDA runtime error";
+    case SVE_ERR_OOM: return "out of device memory";
+    case SVE_ERR_NEG_DEPTH: return "non-positive water depth";
+    case SVE_ERR_RIEMANN: return "Riemann problem without a solution with positive specific volumes";
+    case SVE_ERR_NAN: return "non-finite value in the state";
+    case SVE_ERR_DT: return "invalid time step";
+    case SVE_ERR_STATE: return "no state set";
+    default: return "unknown error";
+  }
+}
+
+long long sve_last_launch_count(sve_handle* h) { return h ? h->last_launches : -1; }
+
+int sve_step_async(sve_handle* h, int nsteps) {
+  if (!h || nsteps < 0) return SVE_ERR_ARG;
+  return enqueue_steps(h, nsteps, 0);
+}
+
+int sve_sync(sve_handle* h) {
+  if (!h) return SVE_ERR_ARG;
+  if (!h->has_state) return SVE_ERR_STATE;
+  return wait_status(h);
+}
+
+int sve_profile(sve_handle* h, int on) {
+  if (!h) return SVE_ERR_ARG;
+  int rc = drain_events(h);
+  h->profiling = on != 0;
+  h->prof_ms[0] = h->prof_ms[1] = 0.0;
+  h->prof_launches[0] = h->prof_launches[1] = 0;
+  return rc;
+}
+
+int sve_profile_read(sve_handle* h, double* ms, long long* launches) {
+  if (!h || !ms || !launches) return SVE_ERR_ARG;
+  int rc = drain_events(h);
+  if (rc) return rc;
+  ms[0] = h->prof_ms[0];
+  ms[1] = h->prof_ms[1];
+  launches[0] = h->prof_launches[0];
+  launches[1] = h->prof_launches[1];
+  return SVE_OK;
+}
+
+int sve_get_counters(sve_handle* h, long long* steps, unsigned long long* newton_iters) {
+  if (!h) return SVE_ERR_ARG;
+  if (!h->has_state) return SVE_ERR_STATE;
+  DevScalars s;
+  SVE_TRY(cudaMemcpyAsync(&s, h->sc, sizeof(s), cudaMemcpyDeviceToHost, h->stream));
+  SVE_TRY(cudaStreamSynchronize(h->stream));
+  if (steps) *steps = s.steps;
+  if (newton_iters) *newton_iters = s.newton_iters;
+  return status_to_code(s.status);
+}
+
+}  // extern "C"

@@ -1,0 +1,604 @@
+// sve_device.cuh -- device code of libsve: equilibrium projection, closures,
+// the relaxation Riemann solver and the two step kernels.
+//
+// Step n (Sec. 3 of arXiv:1307.0491, the procedure after the list of
+// properties of the relaxation model), split in two launches so that every
+// floating-point operation of the method is done exactly once per step
+// (GB300's FP64 pipe is ~1/58 of its FP32 pipe, so recomputation, not memory
+// traffic, is what costs):
+//   interface_kernel: one thread per interface (x then y) reads the projected
+//     states of its two cells, solves the homogeneous relaxation Riemann
+//     problem (Eqs. relaxh--relaxqs, lambda -> 0 projection already done),
+//     stores the fluctuations A-dU, A+dU and reduces the extreme wave speed;
+//     the last block to finish turns the speeds into the CFL time step.
+//   cell_kernel: one thread per cell averages the Riemann fans (Godunov, in
+//     fluctuation form), applies semi-implicit friction, checks the state,
+//     projects the new state to equilibrium (Pi = g h^2 / 2, Omega = q_b)
+//     for the next step, fills the ghost ring and reduces the mass sums.
+// The state and its projection live in ghost-padded arrays of
+// (ny + 2) x (nx + 2) cells and are updated in place.
+#pragma once
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+namespace sve {
+
+enum : int { ST_RIEMANN = 1, ST_NEG_DEPTH = 2, ST_NAN = 4, ST_DT = 8 };
+enum : int { GHOST_PERIODIC = 0, GHOST_FREE = 1, GHOST_INFLOW_Q = 2, GHOST_INFLOW_QH = 3, GHOST_WALL = 4 };
+
+// Physical and numerical constants, precomputed on the host.
+struct DevParams {
+  int dim, nx, ny, ex;  // ex = nx + 2 (padded row length)
+  double dx, dy, inv_dx, inv_dy, g, cfl;
+  int bedload;          // 0 Grass, 1 MPM
+  double A_g, m_g;
+  int m_int;            // m_g if it is 1, 2, 3 or 4, else 0 (pow path)
+  double mpm_C;         // 8 sqrt((s-1) g d_s^3)
+  double mpm_alpha;     // Darcy: f / (8 g (s-1) d_s);  Manning: n^2 / ((s-1) d_s)  (divided by h^(1/3))
+  double tau_cr;
+  int friction;         // 0 none, 1 Darcy, 2 Strickler
+  double fric_c;        // Darcy: f / 8;  Strickler: g / K^2
+  int bc[4];
+  double q_in, h_in;
+  double kappa_a, beta_min, gamma_z, newton_tol;
+  int newton_maxit;
+  long long nfx, nfy;   // number of x- and y-interfaces
+  int nbx, nby;         // blocks of the interface kernel over x and y interfaces
+};
+
+// Device scalars of one handle.
+struct DevScalars {
+  double dt, t;
+  double mass_h, mass_z;
+  double Sx, Sy;
+  int status;
+  int call_step;        // step index inside the current step call
+  unsigned int done_iface, done_cell;
+  long long steps;      // total steps since the state was set
+  unsigned long long newton_iters;  // Newton updates summed over all solves since the state was set
+};
+
+// Ghost-padded state and projection (SoA) of precision T.
+template <typename T>
+struct DevState {
+  T *h, *hu, *hv, *z;                        // conserved
+  T *tau, *u, *v, *pi, *omx, *omy, *ca, *cbx, *cby;  // projection
+  T *fx, *fy;                                // fluctuations: 8 planes (A- H,qn,qt,Z, A+ H,qn,qt,Z)
+};
+
+template <typename T> __device__ __forceinline__ T tmax(T a, T b) { return a > b ? a : b; }
+template <typename T> __device__ __forceinline__ T tabs(T a) { return a < T(0) ? -a : a; }
+__device__ __forceinline__ double tsqrt(double x) { return sqrt(x); }
+__device__ __forceinline__ float tsqrt(float x) { return sqrtf(x); }
+__device__ __forceinline__ double tcbrt(double x) { return cbrt(x); }
+__device__ __forceinline__ float tcbrt(float x) { return cbrtf(x); }
+__device__ __forceinline__ double tpow(double x, double y) { return pow(x, y); }
+__device__ __forceinline__ float tpow(float x, float y) { return powf(x, y); }
+__device__ __forceinline__ bool tfinite(double x) { return isfinite(x); }
+__device__ __forceinline__ bool tfinite(float x) { return isfinite(x); }
+
+// ---- closures (Sec. 2) -----------------------------------------------------
+// Normal bedload flux Q = q_b . n and dQ/du_n at fixed h.
+// Grass (Eq. bedload Grass, 2D form): Q = A_g un |U|^(m-1),
+//   dQ/dun = A_g (|U|^(m-1) + (m-1) un^2 |U|^(m-3)).
+// MPM (Eq. MPM): Q = C (tau* - tau*_cr)_+^(3/2) un/|U|, tau* = alpha |U|^2.
+template <typename T>
+__device__ __forceinline__ void closure(const DevParams& P, T H, T un, T ut, T& Q, T& dQ) {
+  const T speed2 = un * un + ut * ut;
+  if (P.bedload == 0) {
+    const T A = T(P.A_g);
+    if (speed2 == T(0)) {
+      Q = T(0);
+      dQ = (P.m_int == 1) ? A : T(0);
+      return;
+    }
+    T pm1, second;
+    switch (P.m_int) {
+      case 1: pm1 = T(1); second = T(0); break;
+      case 2: { T sp = tsqrt(speed2); pm1 = sp; second = (un * un) / sp; } break;
+      case 3: pm1 = speed2; second = T(2) * (un * un); break;
+      case 4: { T sp = tsqrt(speed2); pm1 = speed2 * sp; second = T(3) * (un * un) * sp; } break;
+      default: {
+        T sp = tsqrt(speed2);
+        T m = T(P.m_g);
+        pm1 = tpow(sp, m - T(1));
+        second = (m - T(1)) * (un * un) * tpow(sp, m - T(3));
+      }
+    }
+    Q = A * un * pm1;
+    dQ = A * (pm1 + second);
+    return;
+  }
+  T alpha = T(P.mpm_alpha);
+  if (P.friction != 1) alpha = alpha / tcbrt(H);
+  const T theta = alpha * speed2 - T(P.tau_cr);
+  if (speed2 == T(0) || !(theta > T(0))) {
+    Q = T(0);
+    dQ = T(0);
+    return;
+  }
+  const T sp = tsqrt(speed2);
+  const T isp = T(1) / sp;
+  const T sth = tsqrt(theta);
+  const T th32 = theta * sth;
+  const T C = T(P.mpm_C);
+  Q = C * th32 * (un * isp);
+  dQ = C * (T(3) * sth * alpha * (un * un) * isp + th32 * (ut * ut) * (isp * isp * isp));
+}
+
+// Projected cell in the frame of one interface: n = normal, t = tangential.
+template <typename T>
+struct Cell {
+  T H, Hn, Ht, Z;        // conserved
+  T tau, un, ut, Pi, Om, ca, cb;
+};
+
+// ---- relaxation Riemann solver --------------------------------------------
+// Five linearly degenerate waves u - a tau, u - b tau, u, u + b tau, u + a tau
+// (tau = 1/H).  Riemann invariants (derived from Eqs. relaxh--relaxqs):
+//   a-waves: u -+ a tau, Pi + a^2 tau, Z, Omega
+//   b-waves: u -+ b tau, Pi + a^2 tau, Z - K tau^2, Omega - lambda Z,
+//            K = (a^2 - b^2)/(2g)
+//   contact: u, Pi, Z, Omega.
+// Writing W1..W4 through them leaves p = tau1 + tau4, fixed by continuity of
+// Omega across the contact, F(p) = 0, solved by a safeguarded Newton
+// iteration started from the root of the fluid part alone (the Suliciu
+// solution).  Returns false if no solution with positive tau_k was found.
+template <typename T>
+struct NewtonEval {
+  T tau1, tau2, tau3, tau4, u1, u4, lam2, lam4, Zs, F, dF;
+};
+
+template <typename T>
+__device__ __forceinline__ void newton_eval(T p, T a, T b, T K, T inv_b, T inv_K, T D, T C0, T dZ, T dsig,
+                                            T dN, const Cell<T>& L, const Cell<T>& R, NewtonEval<T>& e) {
+  const T amb = a - b;
+  const T sigma = (C0 - amb * p) * inv_b;          // from u* continuity
+  e.tau2 = T(0.5) * (sigma - D);                    // from Pi continuity
+  e.tau3 = T(0.5) * (sigma + D);
+  const T N = dZ + K * D * sigma;
+  const T ip = T(1) / p;
+  const T m = -N * ip * inv_K;                      // from Z* continuity
+  e.tau1 = T(0.5) * (p + m);
+  e.tau4 = T(0.5) * (p - m);
+  e.u1 = L.un + a * (e.tau1 - L.tau);
+  e.u4 = R.un - a * (e.tau4 - R.tau);
+  e.lam2 = e.u1 - b * e.tau1;
+  e.lam4 = e.u4 + b * e.tau4;
+  e.Zs = L.Z + K * (e.tau2 * e.tau2 - e.tau1 * e.tau1);
+  const T zl = e.Zs - L.Z, zr = e.Zs - R.Z;
+  e.F = (L.Om - R.Om) + e.lam2 * zl - e.lam4 * zr;
+  const T dm = -dN * ip * inv_K - m * ip;
+  const T dtau1 = T(0.5) * (T(1) + dm);
+  const T dtau4 = T(0.5) * (T(1) - dm);
+  const T dtau2 = T(0.5) * dsig;
+  const T dZs = T(2) * K * (e.tau2 * dtau2 - e.tau1 * dtau1);
+  e.dF = amb * dtau1 * zl + e.lam2 * dZs + amb * dtau4 * zr - e.lam4 * dZs;
+}
+
+template <typename T>
+__device__ __forceinline__ bool newton_positive(const NewtonEval<T>& e) {
+  return e.tau1 > T(0) && e.tau2 > T(0) && e.tau3 > T(0) && e.tau4 > T(0);
+}
+
+template <typename T> __device__ __forceinline__ T eps_of();
+template <> __device__ __forceinline__ double eps_of<double>() { return 2.220446049250313e-16; }
+template <> __device__ __forceinline__ float eps_of<float>() { return 1.1920929e-7f; }
+
+// iters receives the number of Newton updates (0 for identical states).
+template <typename T>
+__device__ bool riemann_solve(const DevParams& P, const Cell<T>& L, const Cell<T>& R, T Am[4], T Ap[4], T& smax,
+                              int& iters) {
+  iters = 0;
+  const T g = T(P.g);
+  // celerities: bounds of Eq. (ab), kappa_a, beta_min floor, bed-step bound
+  const T a0 = tmax(L.ca, R.ca);
+  const T b0 = tmax(L.cb, R.cb);
+  T a = T(P.kappa_a) * tmax(a0, b0);
+  const T b = tmax(b0, T(P.beta_min) * a0);
+  const T Hmax = tmax(L.H, R.H);
+  const T dZ = R.Z - L.Z;
+  const T need = b * b + T(2) * g * T(P.gamma_z) * tabs(dZ) * (Hmax * Hmax);
+  if (a * a < need) a = tsqrt(need);
+  const T lam1 = L.un - a * L.tau;
+  const T lam5 = R.un + a * R.tau;
+  smax = tmax(tabs(lam1), tabs(lam5));
+#pragma unroll
+  for (int c = 0; c < 4; ++c) { Am[c] = T(0); Ap[c] = T(0); }
+  if (L.H == R.H && L.Hn == R.Hn && L.Ht == R.Ht && L.Z == R.Z) return true;
+
+  const T inv_a = T(1) / a;
+  const T inv_b = T(1) / b;
+  const T K = (a * a - b * b) / (T(2) * g);
+  const T inv_K = T(1) / K;
+  const T D = (R.tau - L.tau) + (R.Pi - L.Pi) * (inv_a * inv_a);
+  const T du = R.un - L.un;
+  const T C0 = du + a * (L.tau + R.tau);
+  const T dsig = -(a - b) * inv_b;
+  const T dN = K * D * dsig;
+  T p = L.tau + R.tau + du * inv_a;
+  NewtonEval<T> e;
+  newton_eval(p, a, b, K, inv_b, inv_K, D, C0, dZ, dsig, dN, L, R, e);
+  bool ok = false;
+  // a relative step below a few units of roundoff of T is never reached:
+  // floor the tolerance at 16 eps (3.6e-15 in FP64, 1.9e-6 in FP32)
+  const T tol = tmax(T(P.newton_tol), T(16) * eps_of<T>());
+  int it = 0;
+  for (; it < P.newton_maxit; ++it) {
+    T step = -e.F / e.dF;
+    if (!tfinite(step)) break;
+    NewtonEval<T> tr;
+    bool pos = false;
+    for (int h = 0; h <= 60; ++h) {
+      newton_eval(p + step, a, b, K, inv_b, inv_K, D, C0, dZ, dsig, dN, L, R, tr);
+      if (newton_positive(tr)) { pos = true; break; }
+      step = T(0.5) * step;
+    }
+    if (!pos) break;
+    p = p + step;
+    e = tr;
+    if (tabs(step) <= tol * p) { ok = true; ++it; break; }
+  }
+  iters = it;
+  if (!ok || !newton_positive(e)) return false;
+
+  // intermediate states W1..W4 and the fluctuations sum_{lam<0} lam [U],
+  // sum_{lam>0} lam [U] of U = (H, H un, H ut, Z)
+  const T us = e.u1 + b * (e.tau2 - e.tau1);
+  T U[6][4];
+  U[0][0] = L.H; U[0][1] = L.Hn; U[0][2] = L.Ht; U[0][3] = L.Z;
+  U[5][0] = R.H; U[5][1] = R.Hn; U[5][2] = R.Ht; U[5][3] = R.Z;
+  const T tk[4] = {e.tau1, e.tau2, e.tau3, e.tau4};
+  const T uk[4] = {e.u1, us, us, e.u4};
+  const T vk[4] = {L.ut, L.ut, R.ut, R.ut};
+  const T zk[4] = {L.Z, e.Zs, e.Zs, R.Z};
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const T Hk = T(1) / tk[k];
+    U[k + 1][0] = Hk;
+    U[k + 1][1] = Hk * uk[k];
+    U[k + 1][2] = Hk * vk[k];
+    U[k + 1][3] = zk[k];
+  }
+  const T lam[5] = {lam1, e.lam2, us, e.lam4, lam5};
+#pragma unroll
+  for (int k = 0; k < 5; ++k) {
+    const T lk = lam[k];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      const T jump = U[k + 1][c] - U[k][c];
+      if (lk < T(0)) Am[c] += lk * jump;
+      else if (lk > T(0)) Ap[c] += lk * jump;
+    }
+  }
+  return true;
+}
+
+// ---- ghost cells ----------------------------------------------------------
+// Ghost state of side s (0 W, 1 E, 2 S, 3 N) from the adjacent (or periodic
+// partner) state in = (H, Hu, Hv, Z).
+template <typename T>
+__device__ __forceinline__ void ghost_state(const DevParams& P, int s, const T in[4], T out[4]) {
+  const int normal = (s < 2) ? 1 : 2;
+  const int tangent = (s < 2) ? 2 : 1;
+  const T inward = (s == 0 || s == 2) ? T(1) : T(-1);
+#pragma unroll
+  for (int c = 0; c < 4; ++c) out[c] = in[c];
+  switch (P.bc[s]) {
+    case GHOST_INFLOW_Q: out[normal] = inward * T(P.q_in); out[tangent] = T(0); break;
+    case GHOST_INFLOW_QH: out[0] = T(P.h_in); out[normal] = inward * T(P.q_in); out[tangent] = T(0); break;
+    case GHOST_WALL: out[normal] = -in[normal]; break;
+    default: break;
+  }
+}
+
+// Project conserved (H, Hu, Hv, Z) and store state + projection at ext index e.
+template <typename T>
+__device__ __forceinline__ void store_cell(const DevParams& P, const DevState<T>& S, long long e, const T s[4]) {
+  const T H = s[0];
+  const T tau = T(1) / H;
+  const T u = s[1] * tau;
+  const T v = s[2] * tau;
+  T Qx, dQx, Qy = T(0), dQy = T(0);
+  closure(P, H, u, v, Qx, dQx);
+  if (P.dim == 2) closure(P, H, v, u, Qy, dQy);
+  const T g = T(P.g);
+  S.h[e] = H; S.hu[e] = s[1]; S.hv[e] = s[2]; S.z[e] = s[3];
+  S.tau[e] = tau; S.u[e] = u; S.v[e] = v;
+  S.pi[e] = T(0.5) * g * H * H;
+  S.omx[e] = Qx; S.omy[e] = Qy;
+  S.ca[e] = H * tsqrt(g * H);
+  S.cbx[e] = tsqrt(s[1] * s[1] + g * H * H * dQx);
+  S.cby[e] = tsqrt(s[2] * s[2] + g * H * H * dQy);
+}
+
+__device__ __forceinline__ long long ext_index(const DevParams& P, int i, int j) {
+  return (long long)(j + 1) * P.ex + (i + 1);
+}
+
+// Write the ghosts that the interior cell (i, j) with new state s feeds.
+template <typename T>
+__device__ __forceinline__ void write_ghosts(const DevParams& P, const DevState<T>& S, int i, int j, const T s[4]) {
+  T gs[4];
+  const bool perx = P.bc[0] == GHOST_PERIODIC;
+  if ((!perx && i == 0) || (perx && i == P.nx - 1)) { ghost_state(P, 0, s, gs); store_cell(P, S, ext_index(P, -1, j), gs); }
+  if ((!perx && i == P.nx - 1) || (perx && i == 0)) { ghost_state(P, 1, s, gs); store_cell(P, S, ext_index(P, P.nx, j), gs); }
+  if (P.dim == 2) {
+    const bool pery = P.bc[2] == GHOST_PERIODIC;
+    if ((!pery && j == 0) || (pery && j == P.ny - 1)) { ghost_state(P, 2, s, gs); store_cell(P, S, ext_index(P, i, -1), gs); }
+    if ((!pery && j == P.ny - 1) || (pery && j == 0)) { ghost_state(P, 3, s, gs); store_cell(P, S, ext_index(P, i, P.ny), gs); }
+  }
+}
+
+__device__ __forceinline__ double warp_max(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+template <int NT>
+__device__ __forceinline__ double block_max(double v, double* sh) {
+  v = warp_max(v);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  if (l == 0) sh[w] = v;
+  __syncthreads();
+  double r = 0.0;
+  if (threadIdx.x == 0) {
+    r = sh[0];
+    for (int k = 1; k < NT / 32; ++k) r = fmax(r, sh[k]);
+  }
+  __syncthreads();
+  return r;
+}
+
+template <int NT>
+__device__ __forceinline__ void block_sum2(double& a, double& b, double* sh) {
+  a = warp_sum(a);
+  b = warp_sum(b);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  if (l == 0) { sh[2 * w] = a; sh[2 * w + 1] = b; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double ra = 0.0, rb = 0.0;
+    for (int k = 0; k < NT / 32; ++k) { ra += sh[2 * k]; rb += sh[2 * k + 1]; }
+    a = ra;
+    b = rb;
+  }
+  __syncthreads();
+}
+
+// Sum of the per-block (h, z) partials by the last block: thread t adds
+// blocks t, t + NT, ... in order, then a fixed shuffle tree -- the same
+// order on every run (deterministic), with no serial loop over all blocks.
+template <int NT>
+__device__ __forceinline__ void reduce_partials(const double* mpart, unsigned nblocks, double& a, double& b,
+                                                double* sh) {
+  const volatile double* vp = mpart;
+  a = 0.0;
+  b = 0.0;
+  for (unsigned k = threadIdx.x; k < nblocks; k += NT) { a += vp[2 * k]; b += vp[2 * k + 1]; }
+  block_sum2<NT>(a, b, sh);
+}
+
+// ---- kernels -------------------------------------------------------------
+
+constexpr int kThreads = 256;
+
+// Load the projected cell at ext index e in the x (ydir = false) or y frame.
+template <typename T>
+__device__ __forceinline__ Cell<T> load_cell(const DevState<T>& S, long long e, bool ydir) {
+  Cell<T> c;
+  c.H = S.h[e];
+  c.Z = S.z[e];
+  c.tau = S.tau[e];
+  c.Pi = S.pi[e];
+  c.ca = S.ca[e];
+  if (!ydir) {
+    c.Hn = S.hu[e]; c.Ht = S.hv[e]; c.un = S.u[e]; c.ut = S.v[e]; c.Om = S.omx[e]; c.cb = S.cbx[e];
+  } else {
+    c.Hn = S.hv[e]; c.Ht = S.hu[e]; c.un = S.v[e]; c.ut = S.u[e]; c.Om = S.omy[e]; c.cb = S.cby[e];
+  }
+  return c;
+}
+
+// One thread per interface.  Blocks [0, nbx) cover the x-interfaces
+// (i - 1/2, j), i in [0, nx], j in [0, ny); blocks [nbx, nbx + nby) cover the
+// y-interfaces (i, j - 1/2), i in [0, nx), j in [0, ny].  The last block to
+// finish reduces the per-block speeds into the time step of this step.
+template <typename T>
+__global__ void __launch_bounds__(kThreads) interface_kernel(DevParams P, DevState<T> S, DevScalars* sc,
+                                                             double* spart, const double* fixed_dts,
+                                                             double* dtlog, int fixed) {
+  __shared__ double sh[2 * (kThreads / 32)];
+  __shared__ bool last;
+  const bool ydir = blockIdx.x >= (unsigned)P.nbx;
+  const long long k = (long long)(ydir ? blockIdx.x - P.nbx : blockIdx.x) * kThreads + threadIdx.x;
+  double smax = 0.0;
+  int iters = 0;
+  if (!ydir && k < P.nfx) {
+    const int row = (int)(k / (P.nx + 1));
+    const int i = (int)(k - (long long)row * (P.nx + 1));
+    const long long eR = ext_index(P, i, row);
+    const Cell<T> L = load_cell(S, eR - 1, false);
+    const Cell<T> R = load_cell(S, eR, false);
+    T Am[4], Ap[4], s;
+    if (!riemann_solve(P, L, R, Am, Ap, s, iters)) atomicOr(&sc->status, ST_RIEMANN);
+    smax = (double)s;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) { S.fx[c * P.nfx + k] = Am[c]; S.fx[(4 + c) * P.nfx + k] = Ap[c]; }
+  } else if (ydir && k < P.nfy) {
+    const int row = (int)(k / P.nx);  // j in [0, ny]
+    const int i = (int)(k - (long long)row * P.nx);
+    const long long eR = ext_index(P, i, row);
+    const Cell<T> L = load_cell(S, eR - P.ex, true);
+    const Cell<T> R = load_cell(S, eR, true);
+    T Am[4], Ap[4], s;
+    if (!riemann_solve(P, L, R, Am, Ap, s, iters)) atomicOr(&sc->status, ST_RIEMANN);
+    smax = (double)s;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) { S.fy[c * P.nfy + k] = Am[c]; S.fy[(4 + c) * P.nfy + k] = Ap[c]; }
+  }
+  const double bm = block_max<kThreads>(smax, sh);
+  // Newton updates of the block (for the operation count of the step)
+  double it_sum = (double)iters, dummy = 0.0;
+  block_sum2<kThreads>(it_sum, dummy, sh);
+  if (threadIdx.x == 0) {
+    atomicAdd(&sc->newton_iters, (unsigned long long)it_sum);
+    spart[blockIdx.x] = bm;
+    __threadfence();
+    const unsigned int ticket = atomicAdd(&sc->done_iface, 1u);
+    last = (ticket == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (!last) return;
+  // last block: reduce the partials (volatile reads after the fence)
+  __threadfence();
+  const volatile double* vp = spart;
+  double sx = 0.0, sy = 0.0;
+  for (int b = threadIdx.x; b < P.nbx; b += kThreads) sx = fmax(sx, vp[b]);
+  for (int b = P.nbx + threadIdx.x; b < P.nbx + P.nby; b += kThreads) sy = fmax(sy, vp[b]);
+  sx = block_max<kThreads>(sx, sh);
+  sy = block_max<kThreads>(sy, sh);
+  if (threadIdx.x == 0) {
+    double dt;
+    const int cs = sc->call_step;
+    if (fixed) dt = fixed_dts[cs];
+    else if (P.dim == 1) dt = P.cfl * P.dx / sx;
+    else dt = P.cfl / (sx / P.dx + sy / P.dy);
+    if (!(dt > 0.0) || !isfinite(dt)) { atomicOr(&sc->status, ST_DT); dt = 0.0; }
+    sc->dt = dt;
+    sc->Sx = sx;
+    sc->Sy = sy;
+    dtlog[cs] = dt;
+    sc->done_iface = 0u;
+  }
+}
+
+// One thread per interior cell (i, j): Godunov average in fluctuation form,
+// friction, checks, projection of the new state, ghosts, mass partials.
+template <typename T>
+__global__ void __launch_bounds__(kThreads) cell_kernel(DevParams P, DevState<T> S, DevScalars* sc, double* mpart) {
+  __shared__ double sh[2 * (kThreads / 32)];
+  __shared__ bool last;
+  const long long k = (long long)blockIdx.x * kThreads + threadIdx.x;
+  const long long ncell = (long long)P.nx * P.ny;
+  double mh = 0.0, mz = 0.0;
+  if (k < ncell) {
+    const int j = (int)(k / P.nx);
+    const int i = (int)(k - (long long)j * P.nx);
+    const long long e = ext_index(P, i, j);
+    const double dt = sc->dt;
+    const T dtx = T(dt * P.inv_dx);
+    const long long kx = (long long)j * (P.nx + 1) + i;
+    T s[4] = {S.h[e], S.hu[e], S.hv[e], S.z[e]};
+    T ax[4];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) ax[c] = S.fx[(4 + c) * P.nfx + kx] + S.fx[c * P.nfx + kx + 1];
+    if (P.dim == 2) {
+      const T dty = T(dt * P.inv_dy);
+      const long long ky = (long long)j * P.nx + i;
+      T ay[4];
+#pragma unroll
+      for (int c = 0; c < 4; ++c) ay[c] = S.fy[(4 + c) * P.nfy + ky] + S.fy[c * P.nfy + ky + P.nx];
+      // y frame (H, Hv, Hu, Z) back to (H, Hu, Hv, Z)
+      s[0] = s[0] - (dtx * ax[0] + dty * ay[0]);
+      s[1] = s[1] - (dtx * ax[1] + dty * ay[2]);
+      s[2] = s[2] - (dtx * ax[2] + dty * ay[1]);
+      s[3] = s[3] - (dtx * ax[3] + dty * ay[3]);
+    } else {
+      s[0] = s[0] - dtx * ax[0];
+      s[1] = s[1] - dtx * ax[1];
+      s[3] = s[3] - dtx * ax[3];
+    }
+    // semi-implicit friction: q <- q / (1 + dt C(h) |q|)
+    if (P.friction != 0) {
+      const T H = s[0];
+      const T qn = tsqrt(s[1] * s[1] + s[2] * s[2]);
+      T C;
+      if (P.friction == 1) C = T(P.fric_c) / (H * H);
+      else C = T(P.fric_c) / (H * H * tcbrt(H));
+      const T inv_den = T(1) / (T(1) + T(dt) * C * qn);
+      s[1] = s[1] * inv_den;
+      s[2] = s[2] * inv_den;
+    }
+    if (!(tfinite(s[0]) && tfinite(s[1]) && tfinite(s[2]) && tfinite(s[3]))) atomicOr(&sc->status, ST_NAN);
+    else if (!(s[0] > T(0))) atomicOr(&sc->status, ST_NEG_DEPTH);
+    store_cell(P, S, e, s);
+    write_ghosts(P, S, i, j, s);
+    mh = (double)s[0];
+    mz = (double)s[3];
+  }
+  block_sum2<kThreads>(mh, mz, sh);
+  if (threadIdx.x == 0) {
+    mpart[2 * blockIdx.x] = mh;
+    mpart[2 * blockIdx.x + 1] = mz;
+    __threadfence();
+    const unsigned int ticket = atomicAdd(&sc->done_cell, 1u);
+    last = (ticket == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  double sh_h, sh_z;
+  reduce_partials<kThreads>(mpart, gridDim.x, sh_h, sh_z, sh);
+  if (threadIdx.x == 0) {
+    const double cell = P.dx * (P.dim == 2 ? P.dy : 1.0);
+    sc->mass_h = sh_h * cell;
+    sc->mass_z = sh_z * cell;
+    sc->t += sc->dt;
+    sc->call_step += 1;
+    sc->steps += 1;
+    sc->done_cell = 0u;
+  }
+}
+
+// Initialisation: every padded cell; interior cells are projected from the
+// state as stored, ghost cells get their rule from the adjacent / periodic
+// partner interior cell.  Also checks the state and reduces the masses.
+template <typename T>
+__global__ void __launch_bounds__(kThreads) init_kernel(DevParams P, DevState<T> S, DevScalars* sc, double* mpart) {
+  __shared__ double sh[2 * (kThreads / 32)];
+  __shared__ bool last;
+  const long long k = (long long)blockIdx.x * kThreads + threadIdx.x;
+  const long long ncell = (long long)P.nx * P.ny;
+  double mh = 0.0, mz = 0.0;
+  if (k < ncell) {
+    const int j = (int)(k / P.nx);
+    const int i = (int)(k - (long long)j * P.nx);
+    const long long e = ext_index(P, i, j);
+    T s[4] = {S.h[e], S.hu[e], P.dim == 2 ? S.hv[e] : T(0), S.z[e]};
+    if (!(tfinite(s[0]) && tfinite(s[1]) && tfinite(s[2]) && tfinite(s[3]))) atomicOr(&sc->status, ST_NAN);
+    else if (!(s[0] > T(0))) atomicOr(&sc->status, ST_NEG_DEPTH);
+    store_cell(P, S, e, s);
+    write_ghosts(P, S, i, j, s);
+    mh = (double)s[0];
+    mz = (double)s[3];
+  }
+  block_sum2<kThreads>(mh, mz, sh);
+  if (threadIdx.x == 0) {
+    mpart[2 * blockIdx.x] = mh;
+    mpart[2 * blockIdx.x + 1] = mz;
+    __threadfence();
+    const unsigned int ticket = atomicAdd(&sc->done_cell, 1u);
+    last = (ticket == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  double sh_h, sh_z;
+  reduce_partials<kThreads>(mpart, gridDim.x, sh_h, sh_z, sh);
+  if (threadIdx.x == 0) {
+    const double cell = P.dx * (P.dim == 2 ? P.dy : 1.0);
+    sc->mass_h = sh_h * cell;
+    sc->mass_z = sh_z * cell;
+    sc->done_cell = 0u;
+  }
+}
+
+}  // namespace sve

@@ -1,0 +1,315 @@
+"""Python binding of libsve (include/sve.h): argument marshalling only.
+
+The functions ``sve_*`` below have the names and arguments of the C ABI; all
+work of a step runs in the library's CUDA kernels.  ``Solver`` is a thin
+convenience wrapper that maps a workload parameter dict (string-valued
+enums) to ``sve_config`` and moves numpy arrays or torch tensors in and out.
+
+The library must have been built (``paper_1307_0491_gb300.build.build()``);
+there is no fallback: loading fails loudly when ``libsve.so`` is missing.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+SVE_OK = 0
+SVE_ERR_ARG, SVE_ERR_CUDA, SVE_ERR_OOM = -1, -2, -3
+SVE_ERR_NEG_DEPTH, SVE_ERR_RIEMANN, SVE_ERR_NAN, SVE_ERR_DT, SVE_ERR_STATE = -4, -5, -6, -7, -8
+SVE_FP64, SVE_FP32 = 0, 1
+SVE_GRASS, SVE_MPM = 0, 1
+SVE_FRIC_NONE, SVE_FRIC_DARCY, SVE_FRIC_STRICKLER = 0, 1, 2
+SVE_BC_PERIODIC, SVE_BC_FREE, SVE_BC_INFLOW_Q, SVE_BC_INFLOW_QH, SVE_BC_WALL = 0, 1, 2, 3, 4
+SVE_HOST, SVE_DEVICE = 0, 1
+
+#: every symbol include/sve.h declares
+EXPORTS = ("sve_config_default", "sve_create", "sve_set_stream", "sve_set_state", "sve_step", "sve_step_dt",
+           "sve_get_state", "sve_get_diag", "sve_get_dts", "sve_destroy", "sve_strerror", "sve_last_launch_count",
+           "sve_step_async", "sve_sync", "sve_profile", "sve_profile_read", "sve_get_counters")
+
+
+class sve_config(ctypes.Structure):
+    _fields_ = [
+        ("dim", ctypes.c_int), ("nx", ctypes.c_int), ("ny", ctypes.c_int),
+        ("lx", ctypes.c_double), ("ly", ctypes.c_double), ("g", ctypes.c_double), ("cfl", ctypes.c_double),
+        ("precision", ctypes.c_int), ("bedload", ctypes.c_int),
+        ("A_g", ctypes.c_double), ("m_g", ctypes.c_double),
+        ("s", ctypes.c_double), ("d_s", ctypes.c_double), ("tau_cr", ctypes.c_double),
+        ("friction", ctypes.c_int),
+        ("f_dw", ctypes.c_double), ("K_st", ctypes.c_double),
+        ("bc", ctypes.c_int * 4),
+        ("q_in", ctypes.c_double), ("h_in", ctypes.c_double),
+        ("kappa_a", ctypes.c_double), ("beta_min", ctypes.c_double), ("gamma_z", ctypes.c_double),
+        ("newton_tol", ctypes.c_double),
+        ("newton_maxit", ctypes.c_int),
+    ]
+
+
+_LIB = None
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def load() -> ctypes.CDLL:
+    """Load libsve.so (built in-tree).  Raises if it is missing."""
+    global _LIB
+    if _LIB is not None:
+        return _LIB
+    path = lib_path()
+    if not os.path.exists(path):
+        raise RuntimeError(f"libsve.so not found at {path}: build it with paper_1307_0491_gb300.build.build()")
+    L = ctypes.CDLL(path)
+    vp, dp, ip = ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.c_int
+    cfgp = ctypes.POINTER(sve_config)
+    sig = {
+        "sve_config_default": ([cfgp], ip),
+        "sve_create": ([cfgp, ctypes.POINTER(vp)], ip),
+        "sve_set_stream": ([vp, vp], ip),
+        "sve_set_state": ([vp, vp, vp, vp, vp, ip], ip),
+        "sve_step": ([vp, ip, dp], ip),
+        "sve_step_dt": ([vp, ip, dp], ip),
+        "sve_get_state": ([vp, vp, vp, vp, vp, ip], ip),
+        "sve_get_diag": ([vp, dp, dp, dp, dp], ip),
+        "sve_get_dts": ([vp, dp, ip], ip),
+        "sve_destroy": ([vp], None),
+        "sve_strerror": ([ip], ctypes.c_char_p),
+        "sve_last_launch_count": ([vp], ctypes.c_longlong),
+        "sve_step_async": ([vp, ip], ip),
+        "sve_sync": ([vp], ip),
+        "sve_profile": ([vp, ip], ip),
+        "sve_profile_read": ([vp, dp, ctypes.POINTER(ctypes.c_longlong)], ip),
+        "sve_get_counters": ([vp, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_ulonglong)], ip),
+    }
+    for name, (args, res) in sig.items():
+        fn = getattr(L, name)
+        fn.argtypes = args
+        fn.restype = res
+    _LIB = L
+    return L
+
+
+# ---- the C ABI, same names ---------------------------------------------------
+
+def sve_config_default(cfg: sve_config) -> int:
+    return load().sve_config_default(ctypes.byref(cfg))
+
+
+def sve_create(cfg: sve_config) -> tuple[int, ctypes.c_void_p]:
+    h = ctypes.c_void_p()
+    rc = load().sve_create(ctypes.byref(cfg), ctypes.byref(h))
+    return rc, h
+
+
+def sve_set_stream(h, stream: int | None) -> int:
+    return load().sve_set_stream(h, ctypes.c_void_p(stream or 0))
+
+
+def sve_set_state(h, depth: int, hu: int, hv: int | None, zb: int, where: int) -> int:
+    return load().sve_set_state(h, depth, hu, hv, zb, where)
+
+
+def sve_step(h, nsteps: int) -> tuple[int, float]:
+    t = ctypes.c_double(0.0)
+    rc = load().sve_step(h, int(nsteps), ctypes.byref(t))
+    return rc, t.value
+
+
+def sve_step_dt(h, dts) -> int:
+    a = np.ascontiguousarray(np.asarray(dts, dtype=np.float64))
+    return load().sve_step_dt(h, int(a.size), a.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+
+
+def sve_get_state(h, depth: int, hu: int, hv: int | None, zb: int, where: int) -> int:
+    return load().sve_get_state(h, depth, hu, hv, zb, where)
+
+
+def sve_get_diag(h) -> tuple[int, dict]:
+    vals = [ctypes.c_double() for _ in range(4)]
+    rc = load().sve_get_diag(h, *[ctypes.byref(v) for v in vals])
+    return rc, dict(mass_h=vals[0].value, mass_z=vals[1].value, t=vals[2].value, dt=vals[3].value)
+
+
+def sve_get_dts(h, n: int) -> tuple[int, np.ndarray]:
+    out = np.zeros(max(n, 1))
+    rc = load().sve_get_dts(h, out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), int(n))
+    return rc, out[: max(rc, 0)]
+
+
+def sve_destroy(h) -> None:
+    load().sve_destroy(h)
+
+
+def sve_strerror(code: int) -> str:
+    return load().sve_strerror(int(code)).decode()
+
+
+def sve_last_launch_count(h) -> int:
+    return int(load().sve_last_launch_count(h))
+
+
+def sve_step_async(h, nsteps: int) -> int:
+    return load().sve_step_async(h, int(nsteps))
+
+
+def sve_sync(h) -> int:
+    return load().sve_sync(h)
+
+
+def sve_profile(h, on: bool) -> int:
+    return load().sve_profile(h, 1 if on else 0)
+
+
+def sve_profile_read(h) -> tuple[int, list, list]:
+    ms = (ctypes.c_double * 2)()
+    n = (ctypes.c_longlong * 2)()
+    rc = load().sve_profile_read(h, ms, n)
+    return rc, list(ms), list(n)
+
+
+def sve_get_counters(h) -> tuple[int, int, int]:
+    steps = ctypes.c_longlong(0)
+    its = ctypes.c_ulonglong(0)
+    rc = load().sve_get_counters(h, ctypes.byref(steps), ctypes.byref(its))
+    return rc, steps.value, its.value
+
+
+# ---- convenience wrapper ---------------------------------------------------
+
+class SveError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        super().__init__(f"{where}: {sve_strerror(code)} ({code})")
+        self.code = code
+
+
+def _check(rc: int, where: str) -> int:
+    if rc < 0:
+        raise SveError(rc, where)
+    return rc
+
+
+_BEDLOAD = {"grass": SVE_GRASS, "mpm": SVE_MPM}
+_FRICTION = {"none": SVE_FRIC_NONE, "darcy": SVE_FRIC_DARCY, "strickler": SVE_FRIC_STRICKLER}
+_BC = {"periodic": SVE_BC_PERIODIC, "free": SVE_BC_FREE, "inflow_q": SVE_BC_INFLOW_Q,
+       "inflow_qh": SVE_BC_INFLOW_QH, "wall": SVE_BC_WALL}
+
+
+def config_from_params(p: dict, precision: str = "fp64") -> sve_config:
+    """sve_config from a workload parameter dict (string-valued enums)."""
+    c = sve_config()
+    _check(sve_config_default(c), "sve_config_default")
+    for name, _ in sve_config._fields_:
+        if name in ("bc", "precision", "bedload", "friction"):
+            continue
+        if name in p:
+            setattr(c, name, p[name])
+    c.precision = SVE_FP64 if precision == "fp64" else SVE_FP32
+    c.bedload = _BEDLOAD[p["bedload"]] if isinstance(p.get("bedload"), str) else int(p.get("bedload", 0))
+    c.friction = _FRICTION[p["friction"]] if isinstance(p.get("friction"), str) else int(p.get("friction", 0))
+    bc = p.get("bc", ("periodic", "periodic", "free", "free"))
+    c.bc = (ctypes.c_int * 4)(*[_BC[b] if isinstance(b, str) else int(b) for b in bc])
+    return c
+
+
+class Solver:
+    """One SVE simulation on the current CUDA device (owns a libsve handle)."""
+
+    def __init__(self, params: dict, precision: str = "fp64", stream: int | None = None):
+        self.params = dict(params)
+        self.precision = precision
+        self.dtype = np.float64 if precision == "fp64" else np.float32
+        self.dim = int(params["dim"])
+        self.nx, self.ny = int(params["nx"]), int(params["ny"]) if int(params["dim"]) == 2 else 1
+        self.cfg = config_from_params(params, precision)
+        rc, self.h = sve_create(self.cfg)
+        _check(rc, "sve_create")
+        if stream is not None:
+            _check(sve_set_stream(self.h, stream), "sve_set_stream")
+
+    def close(self):
+        if getattr(self, "h", None):
+            sve_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _shape(self):
+        return (self.ny, self.nx) if self.dim == 2 else (self.nx,)
+
+    def set_state(self, h, hu, hv, z):
+        """Host arrays (numpy) or CUDA tensors (torch); copied in."""
+        if hasattr(h, "is_cuda") and h.is_cuda:
+            ts = [x.contiguous() for x in (h, hu, z)]
+            hvp = hv.contiguous().data_ptr() if (self.dim == 2 and hv is not None) else None
+            self._keep = ts
+            return _check(sve_set_state(self.h, ts[0].data_ptr(), ts[1].data_ptr(), hvp, ts[2].data_ptr(),
+                                        SVE_DEVICE), "sve_set_state")
+        arrs = [np.ascontiguousarray(np.asarray(x, dtype=self.dtype).reshape(self._shape())) for x in (h, hu, z)]
+        hva = (np.ascontiguousarray(np.asarray(hv, dtype=self.dtype).reshape(self._shape()))
+               if self.dim == 2 else None)
+        return _check(sve_set_state(self.h, arrs[0].ctypes.data, arrs[1].ctypes.data,
+                                    hva.ctypes.data if hva is not None else None, arrs[2].ctypes.data, SVE_HOST),
+                      "sve_set_state")
+
+    def step(self, nsteps: int) -> float:
+        rc, t = sve_step(self.h, nsteps)
+        _check(rc, "sve_step")
+        return t
+
+    def step_dt(self, dts) -> None:
+        _check(sve_step_dt(self.h, dts), "sve_step_dt")
+
+    def get_state(self) -> dict:
+        shp = self._shape()
+        out = {k: np.empty(shp, dtype=self.dtype) for k in ("h", "hu", "z")}
+        out["hv"] = np.empty(shp, dtype=self.dtype) if self.dim == 2 else None
+        _check(sve_get_state(self.h, out["h"].ctypes.data, out["hu"].ctypes.data,
+                             out["hv"].ctypes.data if out["hv"] is not None else None, out["z"].ctypes.data,
+                             SVE_HOST), "sve_get_state")
+        return out
+
+    def get_state_device(self, h, hu, hv, z) -> None:
+        """Copy the state into CUDA tensors (contiguous, state dtype)."""
+        _check(sve_get_state(self.h, h.data_ptr(), hu.data_ptr(), hv.data_ptr() if hv is not None else None,
+                             z.data_ptr(), SVE_DEVICE), "sve_get_state")
+
+    def diag(self) -> dict:
+        rc, d = sve_get_diag(self.h)
+        _check(rc, "sve_get_diag")
+        return d
+
+    def dts(self, n: int) -> np.ndarray:
+        rc, d = sve_get_dts(self.h, n)
+        _check(rc, "sve_get_dts")
+        return d
+
+    def launches(self) -> int:
+        return sve_last_launch_count(self.h)
+
+    def step_async(self, nsteps: int) -> None:
+        _check(sve_step_async(self.h, nsteps), "sve_step_async")
+
+    def sync(self) -> None:
+        _check(sve_sync(self.h), "sve_sync")
+
+    def profile(self, on: bool) -> None:
+        _check(sve_profile(self.h, on), "sve_profile")
+
+    def profile_read(self) -> dict:
+        rc, ms, n = sve_profile_read(self.h)
+        _check(rc, "sve_profile_read")
+        return dict(iface_ms=ms[0], cell_ms=ms[1], iface_launches=n[0], cell_launches=n[1])
+
+    def counters(self) -> dict:
+        rc, steps, its = sve_get_counters(self.h)
+        _check(rc, "sve_get_counters")
+        return dict(steps=steps, newton_iters=its)
