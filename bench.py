@@ -39,11 +39,24 @@ BYTES_PER_CELL_FP64 = 64           # read h, hu, hv, zb once + write once (FP64)
 FLOP_SETUP, FLOP_EVAL, FLOP_UPDATE, FLOP_FINAL = 30, 76, 4, 75
 FP64_PEAK_FLOPS = 152 * 2 * 2 * 2070e6   # 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz
 L2_FLUSH_BYTES = 256 << 20
+# DRAM bytes (read + write) of one interface-kernel launch on this workload,
+# from the ncu capture summarised in profiles/interface_kernel_dune2d_fp64_1024x512.md,
+# valid only for the kernel source it was taken with (sha256 prefix)
+IFACE_TRAFFIC = {"sha256": "ed773ffc1d487e72", "bytes": 92_883_712}
 
 
 def workload_desc(nx, ny):
     return (f"2D dune FP64 {nx}x{ny} (1000x500 m, Gaussian dune, Grass m_g=3 A_g=1e-3, Strickler K=40, "
             f"inflow q=0.5 / free outflow)")
+
+
+def iface_traffic():
+    """Measured traffic per launch, or None if the kernel changed since."""
+    import hashlib
+
+    src = os.path.join(ROOT, "paper_1307_0491_gb300", "csrc", "sve_device.cuh")
+    sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    return IFACE_TRAFFIC["bytes"] if sha == IFACE_TRAFFIC["sha256"] else None
 
 
 def peaks():
@@ -231,7 +244,7 @@ def run_ours(args, world, rank, local):
     pk = peaks()
     hbm = pk.get("hbm_gbs", 6800.3)
     roofline = {"bound": "alu", "achieved": achieved / 1e12, "peak": FP64_PEAK_FLOPS / 1e12, "unit": "TFLOP/s",
-                "frac": achieved / FP64_PEAK_FLOPS, "traffic": None,
+                "frac": achieved / FP64_PEAK_FLOPS, "traffic": iface_traffic(),
                 "kernel": "interface_kernel<double>", "peak_source": "152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz "
                 "(GB300 FP64 nominal 1.25 TFLOP/s); a measured DFMA loop gave 1.19 TFLOP/s",
                 "flop_per_interface": flop_iface, "newton_updates_per_solve": updates,
