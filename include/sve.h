@@ -50,7 +50,8 @@ enum {
   SVE_ERR_RIEMANN = -5,   /* an interface Riemann problem had no solution with positive specific volumes */
   SVE_ERR_NAN = -6,       /* a non-finite value appeared in the state */
   SVE_ERR_DT = -7,        /* a time step was <= 0 or non-finite */
-  SVE_ERR_STATE = -8      /* no state has been set on the handle */
+  SVE_ERR_STATE = -8,     /* no state has been set on the handle */
+  SVE_ERR_NOALLOC_SIZE = -9 /* the grid does not fit the static scratch of sve_step_noalloc */
 };
 
 enum { SVE_FP64 = 0, SVE_FP32 = 1 };                       /* state precision */
@@ -180,6 +181,41 @@ int sve_profile_read(sve_handle* h, double* ms, long long* launches);
  * summed over all interface Riemann solves.  Either pointer may be NULL.
  * Blocks; returns the latched device status. */
 int sve_get_counters(sve_handle* h, long long* steps, unsigned long long* newton_iters);
+
+/* ---- stepping without device allocation ----------------------------------
+ * The paper has no counterpart of this entry point: it serves callers that
+ * cannot call cudaMalloc -- code living under a framework's caching allocator
+ * that owns (or has reserved all of) the device memory, real-time loops that
+ * must not pay allocation latency or fail for lack of memory mid-run, and
+ * plug-ins that are handed device buffers but no allocator.
+ *
+ * sve_step_noalloc advances the caller's state by nsteps CFL steps (the same
+ * kernels and arithmetic as sve_create + sve_set_state + sve_step).  The
+ * caller passes its state as device arrays (depth, hu, hv, zb: nx*ny values
+ * of the configured precision, row-major [ny][nx], hv NULL in 1D), updated
+ * in place, and the simulated time in *t_inout (host; read, then
+ * overwritten with the time after the steps).  stream: a cudaStream_t or
+ * NULL (legacy default stream).  Blocks until the steps are done.
+ *
+ * No memory is allocated: every other buffer (padded state, projection,
+ * fluctuations, block partials, scalars) lives in one file-scope device
+ * array of SVE_NOALLOC_SCRATCH_BYTES that every GPU loading the library
+ * holds until the process exits.  A configuration whose buffers do not fit
+ * returns SVE_ERR_NOALLOC_SIZE without touching the state; in FP64 a step
+ * needs about 232 bytes per cell (13 padded fields + 8 fluctuation planes
+ * per interface), so grids up to about 36 000 cells fit (e.g. 180 x 180).
+ *
+ * The first call on a device looks up the device address of the array
+ * (cudaGetSymbolAddress, with that device current); make that first call
+ * before any stream capture.  All calls share the array and it keeps the
+ * previous call's contents (each call clears what must start at zero): two
+ * calls that overlap on the GPU -- on different streams or devices' threads
+ * sharing one device -- race on it and must be serialised by the caller.
+ * Errors: SVE_ERR_ARG (bad config or pointers), SVE_ERR_NOALLOC_SIZE, the
+ * latched device errors of the steps, SVE_ERR_CUDA. */
+#define SVE_NOALLOC_SCRATCH_BYTES (8u << 20)
+int sve_step_noalloc(const sve_config* cfg, void* depth, void* hu, void* hv, void* zb, int nsteps, double* t_inout,
+                     void* stream);
 
 #ifdef __cplusplus
 }

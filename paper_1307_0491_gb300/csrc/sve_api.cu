@@ -267,6 +267,12 @@ int run_steps(sve_handle* h, int nsteps, int fixed) {
 
 }  // namespace
 
+// Shared with sve_noalloc.cu (not part of the C ABI).
+__attribute__((visibility("hidden"))) int sve_internal_validate(const sve_config* c) { return validate(c); }
+__attribute__((visibility("hidden"))) void sve_internal_make_params(const sve_config* c, DevParams* P) {
+  make_params(c, P);
+}
+
 extern "C" {
 
 int sve_config_default(sve_config* c) {
@@ -456,6 +462,7 @@ const char* sve_strerror(int code) {
     case SVE_ERR_NAN: return "non-finite value in the state";
     case SVE_ERR_DT: return "invalid time step";
     case SVE_ERR_STATE: return "no state set";
+    case SVE_ERR_NOALLOC_SIZE: return "grid too large for the static scratch of sve_step_noalloc";
     default: return "unknown error";
   }
 }

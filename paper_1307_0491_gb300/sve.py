@@ -20,6 +20,8 @@ from . import build as _build
 SVE_OK = 0
 SVE_ERR_ARG, SVE_ERR_CUDA, SVE_ERR_OOM = -1, -2, -3
 SVE_ERR_NEG_DEPTH, SVE_ERR_RIEMANN, SVE_ERR_NAN, SVE_ERR_DT, SVE_ERR_STATE = -4, -5, -6, -7, -8
+SVE_ERR_NOALLOC_SIZE = -9
+SVE_NOALLOC_SCRATCH_BYTES = 8 << 20
 SVE_FP64, SVE_FP32 = 0, 1
 SVE_GRASS, SVE_MPM = 0, 1
 SVE_FRIC_NONE, SVE_FRIC_DARCY, SVE_FRIC_STRICKLER = 0, 1, 2
@@ -29,7 +31,7 @@ SVE_HOST, SVE_DEVICE = 0, 1
 #: every symbol include/sve.h declares
 EXPORTS = ("sve_config_default", "sve_create", "sve_set_stream", "sve_set_state", "sve_step", "sve_step_dt",
            "sve_get_state", "sve_get_diag", "sve_get_dts", "sve_destroy", "sve_strerror", "sve_last_launch_count",
-           "sve_step_async", "sve_sync", "sve_profile", "sve_profile_read", "sve_get_counters")
+           "sve_step_async", "sve_sync", "sve_profile", "sve_profile_read", "sve_get_counters", "sve_step_noalloc")
 
 
 class sve_config(ctypes.Structure):
@@ -85,6 +87,7 @@ def load() -> ctypes.CDLL:
         "sve_profile": ([vp, ip], ip),
         "sve_profile_read": ([vp, dp, ctypes.POINTER(ctypes.c_longlong)], ip),
         "sve_get_counters": ([vp, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_ulonglong)], ip),
+        "sve_step_noalloc": ([cfgp, vp, vp, vp, vp, ip, dp, vp], ip),
     }
     for name, (args, res) in sig.items():
         fn = getattr(L, name)
@@ -177,6 +180,16 @@ def sve_get_counters(h) -> tuple[int, int, int]:
     its = ctypes.c_ulonglong(0)
     rc = load().sve_get_counters(h, ctypes.byref(steps), ctypes.byref(its))
     return rc, steps.value, its.value
+
+
+def sve_step_noalloc(cfg: sve_config, depth: int, hu: int, hv: int | None, zb: int, nsteps: int, t: float,
+                     stream: int | None = None) -> tuple[int, float]:
+    """Steps on caller-owned device arrays without any device allocation
+    (scratch in the library's static device array); returns (code, time)."""
+    tt = ctypes.c_double(t)
+    rc = load().sve_step_noalloc(ctypes.byref(cfg), depth, hu, hv, zb, int(nsteps), ctypes.byref(tt),
+                                 ctypes.c_void_p(stream or 0))
+    return rc, tt.value
 
 
 # ---- convenience wrapper ---------------------------------------------------
