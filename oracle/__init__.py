@@ -112,7 +112,7 @@ class Params:
     kappa_a: float = 1.1
     beta_min: float = 0.01
     gamma_z: float = 2.0
-    newton_tol: float = 1e-12
+    newton_tol: float = 1e-9
     newton_maxit: int = 30
 
     def to_c(self) -> _Params:

@@ -55,9 +55,12 @@
  *   R2  Newton from p0 = tauL + tauR + (uR - uL)/a (the Suliciu root; it
  *       equals the exact root for equal states and for A_g = 0 on a flat
  *       bed, and it is the root continuously connected to the solution
- *       without sediment); stops when |dp| <= newton_tol * p; at most
- *       newton_maxit iterations; a step that would make any tau_k <= 0
- *       (equivalently, break the wave order) is halved, at most 60 times.
+ *       without sediment); stops after the update with |dp| <= newton_tol * p
+ *       (default 1e-9: quadratic convergence, with |F''/2F'| p about 25 on
+ *       smooth data, leaves an error near 2.5e-17 p, below FP64 rounding);
+ *       at most newton_maxit iterations; a step that would make any
+ *       tau_k <= 0 (equivalently, break the wave order) is halved, at most
+ *       60 times.
  *   R3  Bitwise-identical left and right states give zero fluctuations
  *       without a solve.
  *   R4  2D: unsplit method of lines (Sec. 4) -- x and y fluctuations of the

@@ -32,7 +32,7 @@ import numpy as np
 G = 9.81
 
 #: defaults of the numerical parameters every run carries
-NUMERICS = dict(g=G, cfl=0.9, kappa_a=1.1, beta_min=0.01, gamma_z=2.0, newton_tol=1e-12, newton_maxit=30)
+NUMERICS = dict(g=G, cfl=0.9, kappa_a=1.1, beta_min=0.01, gamma_z=2.0, newton_tol=1e-9, newton_maxit=30)
 
 
 def base_params(**kw) -> dict:
