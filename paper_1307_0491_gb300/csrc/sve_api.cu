@@ -107,6 +107,7 @@ void make_params(const sve_config* c, DevParams* P) {
   P->inv_dx = 1.0 / P->dx;
   P->inv_dy = 1.0 / P->dy;
   P->g = c->g;
+  P->inv_2g = 1.0 / (2.0 * c->g);
   P->cfl = c->cfl;
   P->bedload = c->bedload;
   P->A_g = c->A_g;
@@ -300,7 +301,7 @@ int sve_config_default(sve_config* c) {
   c->kappa_a = 1.1;
   c->beta_min = 0.01;
   c->gamma_z = 2.0;
-  c->newton_tol = 1e-12;
+  c->newton_tol = 1e-9;
   c->newton_maxit = 30;
   return SVE_OK;
 }

@@ -30,7 +30,7 @@ enum : int { GHOST_PERIODIC = 0, GHOST_FREE = 1, GHOST_INFLOW_Q = 2, GHOST_INFLO
 // Physical and numerical constants, precomputed on the host.
 struct DevParams {
   int dim, nx, ny, ex;  // ex = nx + 2 (padded row length)
-  double dx, dy, inv_dx, inv_dy, g, cfl;
+  double dx, dy, inv_dx, inv_dy, g, cfl, inv_2g;
   int bedload;          // 0 Grass, 1 MPM
   double A_g, m_g;
   int m_int;            // m_g if it is 1, 2, 3 or 4, else 0 (pow path)
@@ -78,6 +78,53 @@ __device__ __forceinline__ float tpow(float x, float y) { return powf(x, y); }
 __device__ __forceinline__ bool tfinite(double x) { return isfinite(x); }
 __device__ __forceinline__ bool tfinite(float x) { return isfinite(x); }
 
+// ---- FP64 arithmetic on GB300 -------------------------------------------
+// GB300 issues about two FP64 instructions per SM clock.  Measured costs in
+// DFMA issue slots: IEEE divide ~4.6, square root ~7.5, cube root ~12;
+// FP64 compare, select and min/max one slot each.  Divides and square roots
+// stay IEEE (Newton-Raphson refinement of FP32 seeds measured slower); the
+// inverse cube root of the Strickler law is refined from an FP32 seed (it
+// replaces a cube root and a divide); comparisons, |.| and max of
+// non-negative values use integer operations on the bit patterns.
+
+// x^(-1/3) for x > 0: rcbrtf seed, two Newton-Raphson steps of
+// y <- y + (y/3)(1 - x y^3) (the classical iteration for the inverse cube
+// root; the error e becomes ~2e^2 per step), IEEE fallback outside the FP32
+// exponent range.  tests/test_gpu_arith.py compares it with 1/cbrt.
+__device__ __forceinline__ bool f32_safe(double x) {
+  const int e = (int)((__double_as_longlong(x) >> 52) & 0x7ff);
+  return e > 1023 - 120 && e < 1023 + 120;
+}
+__device__ __forceinline__ double rcbrt64(double x) {
+  if (!f32_safe(x)) return 1.0 / cbrt(x);
+  double y = (double)rcbrtf((float)x);
+  const double third = 1.0 / 3.0;
+  double y3 = y * y * y;
+  y = fma(third * y, fma(-x, y3, 1.0), y);
+  y3 = y * y * y;
+  return fma(third * y, fma(-x, y3, 1.0), y);
+}
+__device__ __forceinline__ float rcbrt64(float x) { return rcbrtf(x); }
+
+// max / |.| of non-negative doubles by integer compares of the bit patterns
+// (IEEE order of non-negative values is their integer order), keeping them
+// off the FP64 pipe.  Not for negative or NaN arguments.
+__device__ __forceinline__ double nnmax(double a, double b) {
+  const long long ia = __double_as_longlong(a), ib = __double_as_longlong(b);
+  return __longlong_as_double(ia > ib ? ia : ib);
+}
+__device__ __forceinline__ float nnmax(float a, float b) { return fmaxf(a, b); }
+__device__ __forceinline__ double absbits(double a) {
+  return __longlong_as_double(__double_as_longlong(a) & 0x7fffffffffffffffLL);
+}
+__device__ __forceinline__ float absbits(float a) { return fabsf(a); }
+__device__ __forceinline__ bool positive(double a) { return __double_as_longlong(a) > 0LL; }
+__device__ __forceinline__ bool positive(float a) { return a > 0.0f; }
+__device__ __forceinline__ bool same_bits(double a, double b) {
+  return __double_as_longlong(a) == __double_as_longlong(b);
+}
+__device__ __forceinline__ bool same_bits(float a, float b) { return __float_as_int(a) == __float_as_int(b); }
+
 // ---- closures (Sec. 2) -----------------------------------------------------
 // Normal bedload flux Q = q_b . n and dQ/du_n at fixed h.
 // Grass (Eq. bedload Grass, 2D form): Q = A_g un |U|^(m-1),
@@ -111,7 +158,7 @@ __device__ __forceinline__ void closure(const DevParams& P, T H, T un, T ut, T& 
     return;
   }
   T alpha = T(P.mpm_alpha);
-  if (P.friction != 1) alpha = alpha / tcbrt(H);
+  if (P.friction != 1) alpha = alpha * rcbrt64(H);
   const T theta = alpha * speed2 - T(P.tau_cr);
   if (speed2 == T(0) || !(theta > T(0))) {
     Q = T(0);
@@ -145,46 +192,99 @@ struct Cell {
 // Omega across the contact, F(p) = 0, solved by a safeguarded Newton
 // iteration started from the root of the fluid part alone (the Suliciu
 // solution).  Returns false if no solution with positive tau_k was found.
+// Per-interface constants of the Newton iteration.
+template <typename T>
+struct NewtonConst {
+  T a, b, K, inv_b, inv_K, D, C0, dZ, dsig, dN;
+};
+
+// The intermediate states as functions of p (every invariant relation of the
+// a- and b-waves and the contact holds for any p) and the residual F(p) of
+// the one remaining condition, continuity of Omega across the contact.
 template <typename T>
 struct NewtonEval {
-  T tau1, tau2, tau3, tau4, u1, u4, lam2, lam4, Zs, F, dF;
+  T tau1, tau2, tau3, tau4, u1, u4, lam2, lam4, Zs, F;
+  T m, ip, zl, zr;  // kept for F'(p)
 };
 
 template <typename T>
-__device__ __forceinline__ void newton_eval(T p, T a, T b, T K, T inv_b, T inv_K, T D, T C0, T dZ, T dsig,
-                                            T dN, const Cell<T>& L, const Cell<T>& R, NewtonEval<T>& e) {
-  const T amb = a - b;
-  const T sigma = (C0 - amb * p) * inv_b;          // from u* continuity
-  e.tau2 = T(0.5) * (sigma - D);                    // from Pi continuity
-  e.tau3 = T(0.5) * (sigma + D);
-  const T N = dZ + K * D * sigma;
-  const T ip = T(1) / p;
-  const T m = -N * ip * inv_K;                      // from Z* continuity
-  e.tau1 = T(0.5) * (p + m);
-  e.tau4 = T(0.5) * (p - m);
-  e.u1 = L.un + a * (e.tau1 - L.tau);
-  e.u4 = R.un - a * (e.tau4 - R.tau);
-  e.lam2 = e.u1 - b * e.tau1;
-  e.lam4 = e.u4 + b * e.tau4;
-  e.Zs = L.Z + K * (e.tau2 * e.tau2 - e.tau1 * e.tau1);
-  const T zl = e.Zs - L.Z, zr = e.Zs - R.Z;
-  e.F = (L.Om - R.Om) + e.lam2 * zl - e.lam4 * zr;
-  const T dm = -dN * ip * inv_K - m * ip;
+__device__ __forceinline__ void newton_eval(T p, const NewtonConst<T>& c, const Cell<T>& L, const Cell<T>& R,
+                                            NewtonEval<T>& e) {
+  const T amb = c.a - c.b;
+  const T sigma = (c.C0 - amb * p) * c.inv_b;       // from u* continuity
+  e.tau2 = T(0.5) * (sigma - c.D);                  // from Pi continuity
+  e.tau3 = T(0.5) * (sigma + c.D);
+  const T N = c.dZ + c.K * c.D * sigma;
+  e.ip = T(1) / p;
+  e.m = -N * e.ip * c.inv_K;                        // from Z* continuity
+  e.tau1 = T(0.5) * (p + e.m);
+  e.tau4 = T(0.5) * (p - e.m);
+  e.u1 = L.un + c.a * (e.tau1 - L.tau);
+  e.u4 = R.un - c.a * (e.tau4 - R.tau);
+  e.lam2 = e.u1 - c.b * e.tau1;
+  e.lam4 = e.u4 + c.b * e.tau4;
+  e.Zs = L.Z + c.K * (e.tau2 * e.tau2 - e.tau1 * e.tau1);
+  e.zl = e.Zs - L.Z;
+  e.zr = e.Zs - R.Z;
+  e.F = (L.Om - R.Om) + e.lam2 * e.zl - e.lam4 * e.zr;
+}
+
+// Analytic F'(p) at an evaluated point.
+template <typename T>
+__device__ __forceinline__ T newton_deriv(const NewtonConst<T>& c, const NewtonEval<T>& e) {
+  const T amb = c.a - c.b;
+  const T dm = -c.dN * e.ip * c.inv_K - e.m * e.ip;
   const T dtau1 = T(0.5) * (T(1) + dm);
   const T dtau4 = T(0.5) * (T(1) - dm);
-  const T dtau2 = T(0.5) * dsig;
-  const T dZs = T(2) * K * (e.tau2 * dtau2 - e.tau1 * dtau1);
-  e.dF = amb * dtau1 * zl + e.lam2 * dZs + amb * dtau4 * zr - e.lam4 * dZs;
+  const T dtau2 = T(0.5) * c.dsig;
+  const T dZs = T(2) * c.K * (e.tau2 * dtau2 - e.tau1 * dtau1);
+  return amb * dtau1 * e.zl + e.lam2 * dZs + amb * dtau4 * e.zr - e.lam4 * dZs;
 }
 
 template <typename T>
 __device__ __forceinline__ bool newton_positive(const NewtonEval<T>& e) {
-  return e.tau1 > T(0) && e.tau2 > T(0) && e.tau3 > T(0) && e.tau4 > T(0);
+  return positive(e.tau1) && positive(e.tau2) && positive(e.tau3) && positive(e.tau4);
+}
+
+// Safeguarded Newton from the evaluated point (p, e): steps that would make
+// a tau_k non-positive are halved (at most 60 times); stops when
+// |step| <= tol p.  iters is incremented per accepted update.
+template <typename T>
+__device__ __forceinline__ bool newton_loop(const NewtonConst<T>& c, const Cell<T>& L, const Cell<T>& R, T& p,
+                                            NewtonEval<T>& e, int maxit, T tol, int& iters) {
+  for (int it = 0; it < maxit; ++it) {
+    T step = -e.F / newton_deriv(c, e);
+    if (!tfinite(step)) return false;
+    NewtonEval<T> tr;
+    bool pos = false;
+    for (int h = 0; h <= 60; ++h) {
+      newton_eval(p + step, c, L, R, tr);
+      if (newton_positive(tr)) { pos = true; break; }
+      step = T(0.5) * step;
+    }
+    if (!pos) return false;
+    p = p + step;
+    e = tr;
+    ++iters;
+    if (absbits(step) <= tol * p) return true;
+  }
+  return false;
 }
 
 template <typename T> __device__ __forceinline__ T eps_of();
 template <> __device__ __forceinline__ double eps_of<double>() { return 2.220446049250313e-16; }
 template <> __device__ __forceinline__ float eps_of<float>() { return 1.1920929e-7f; }
+
+// Root of F for one interface, from p0 (the root of the fluid part alone).
+// Returns false if no root with positive tau_k was reached.
+template <typename T>
+__device__ __forceinline__ bool newton_root(const DevParams& P, const NewtonConst<T>& c, const Cell<T>& L,
+                                            const Cell<T>& R, T p0, NewtonEval<T>& e, int& iters) {
+  const T tol = tmax(T(P.newton_tol), T(16) * eps_of<T>());
+  T p = p0;
+  newton_eval(p, c, L, R, e);
+  return newton_loop(c, L, R, p, e, P.newton_maxit, tol, iters);
+}
 
 // iters receives the number of Newton updates (0 for identical states).
 template <typename T>
@@ -193,54 +293,40 @@ __device__ bool riemann_solve(const DevParams& P, const Cell<T>& L, const Cell<T
   iters = 0;
   const T g = T(P.g);
   // celerities: bounds of Eq. (ab), kappa_a, beta_min floor, bed-step bound
-  const T a0 = tmax(L.ca, R.ca);
-  const T b0 = tmax(L.cb, R.cb);
-  T a = T(P.kappa_a) * tmax(a0, b0);
-  const T b = tmax(b0, T(P.beta_min) * a0);
-  const T Hmax = tmax(L.H, R.H);
+  const T a0 = nnmax(L.ca, R.ca);
+  const T b0 = nnmax(L.cb, R.cb);
+  T a = T(P.kappa_a) * nnmax(a0, b0);
+  const T b = nnmax(b0, T(P.beta_min) * a0);
+  const T Hmax = nnmax(L.H, R.H);
   const T dZ = R.Z - L.Z;
-  const T need = b * b + T(2) * g * T(P.gamma_z) * tabs(dZ) * (Hmax * Hmax);
+  const T need = b * b + T(2) * g * T(P.gamma_z) * absbits(dZ) * (Hmax * Hmax);
   if (a * a < need) a = tsqrt(need);
   const T lam1 = L.un - a * L.tau;
   const T lam5 = R.un + a * R.tau;
-  smax = tmax(tabs(lam1), tabs(lam5));
+  smax = nnmax(absbits(lam1), absbits(lam5));
 #pragma unroll
   for (int c = 0; c < 4; ++c) { Am[c] = T(0); Ap[c] = T(0); }
-  if (L.H == R.H && L.Hn == R.Hn && L.Ht == R.Ht && L.Z == R.Z) return true;
+  if (same_bits(L.H, R.H) && same_bits(L.Hn, R.Hn) && same_bits(L.Ht, R.Ht) && same_bits(L.Z, R.Z)) return true;
 
-  const T inv_a = T(1) / a;
-  const T inv_b = T(1) / b;
-  const T K = (a * a - b * b) / (T(2) * g);
-  const T inv_K = T(1) / K;
-  const T D = (R.tau - L.tau) + (R.Pi - L.Pi) * (inv_a * inv_a);
+  NewtonConst<T> c;
+  const T rab = T(1) / (a * b);       // one divide for 1/a and 1/b
+  const T inv_a = b * rab;
+  c.a = a;
+  c.b = b;
+  c.inv_b = a * rab;
+  const T a2mb2 = a * a - b * b;
+  c.K = a2mb2 * T(P.inv_2g);
+  c.inv_K = T(2) * g / a2mb2;
+  c.D = (R.tau - L.tau) + (R.Pi - L.Pi) * (inv_a * inv_a);
   const T du = R.un - L.un;
-  const T C0 = du + a * (L.tau + R.tau);
-  const T dsig = -(a - b) * inv_b;
-  const T dN = K * D * dsig;
-  T p = L.tau + R.tau + du * inv_a;
+  c.C0 = du + a * (L.tau + R.tau);
+  c.dZ = dZ;
+  c.dsig = -(a - b) * c.inv_b;
+  c.dN = c.K * c.D * c.dsig;
+  // start: the root of the fluid part alone (Suliciu), p = sigma
+  const T p0 = L.tau + R.tau + du * inv_a;
   NewtonEval<T> e;
-  newton_eval(p, a, b, K, inv_b, inv_K, D, C0, dZ, dsig, dN, L, R, e);
-  bool ok = false;
-  // a relative step below a few units of roundoff of T is never reached:
-  // floor the tolerance at 16 eps (3.6e-15 in FP64, 1.9e-6 in FP32)
-  const T tol = tmax(T(P.newton_tol), T(16) * eps_of<T>());
-  int it = 0;
-  for (; it < P.newton_maxit; ++it) {
-    T step = -e.F / e.dF;
-    if (!tfinite(step)) break;
-    NewtonEval<T> tr;
-    bool pos = false;
-    for (int h = 0; h <= 60; ++h) {
-      newton_eval(p + step, a, b, K, inv_b, inv_K, D, C0, dZ, dsig, dN, L, R, tr);
-      if (newton_positive(tr)) { pos = true; break; }
-      step = T(0.5) * step;
-    }
-    if (!pos) break;
-    p = p + step;
-    e = tr;
-    if (tabs(step) <= tol * p) { ok = true; ++it; break; }
-  }
-  iters = it;
+  const bool ok = newton_root(P, c, L, R, p0, e, iters);
   if (!ok || !newton_positive(e)) return false;
 
   // intermediate states W1..W4 and the fluctuations sum_{lam<0} lam [U],
@@ -266,10 +352,10 @@ __device__ bool riemann_solve(const DevParams& P, const Cell<T>& L, const Cell<T
   for (int k = 0; k < 5; ++k) {
     const T lk = lam[k];
 #pragma unroll
-    for (int c = 0; c < 4; ++c) {
-      const T jump = U[k + 1][c] - U[k][c];
-      if (lk < T(0)) Am[c] += lk * jump;
-      else if (lk > T(0)) Ap[c] += lk * jump;
+    for (int cc = 0; cc < 4; ++cc) {
+      const T jump = U[k + 1][cc] - U[k][cc];
+      if (lk < T(0)) Am[cc] += lk * jump;
+      else if (lk > T(0)) Ap[cc] += lk * jump;
     }
   }
   return true;
@@ -295,9 +381,9 @@ __device__ __forceinline__ void ghost_state(const DevParams& P, int s, const T i
 
 // Project conserved (H, Hu, Hv, Z) and store state + projection at ext index e.
 template <typename T>
-__device__ __forceinline__ void store_cell(const DevParams& P, const DevState<T>& S, long long e, const T s[4]) {
+__device__ __forceinline__ void store_cell(const DevParams& P, const DevState<T>& S, long long e, const T s[4],
+                                           T tau) {
   const T H = s[0];
-  const T tau = T(1) / H;
   const T u = s[1] * tau;
   const T v = s[2] * tau;
   T Qx, dQx, Qy = T(0), dQy = T(0);
@@ -310,7 +396,7 @@ __device__ __forceinline__ void store_cell(const DevParams& P, const DevState<T>
   S.omx[e] = Qx; S.omy[e] = Qy;
   S.ca[e] = H * tsqrt(g * H);
   S.cbx[e] = tsqrt(s[1] * s[1] + g * H * H * dQx);
-  S.cby[e] = tsqrt(s[2] * s[2] + g * H * H * dQy);
+  S.cby[e] = P.dim == 2 ? tsqrt(s[2] * s[2] + g * H * H * dQy) : T(0);
 }
 
 __device__ __forceinline__ long long ext_index(const DevParams& P, int i, int j) {
@@ -322,12 +408,24 @@ template <typename T>
 __device__ __forceinline__ void write_ghosts(const DevParams& P, const DevState<T>& S, int i, int j, const T s[4]) {
   T gs[4];
   const bool perx = P.bc[0] == GHOST_PERIODIC;
-  if ((!perx && i == 0) || (perx && i == P.nx - 1)) { ghost_state(P, 0, s, gs); store_cell(P, S, ext_index(P, -1, j), gs); }
-  if ((!perx && i == P.nx - 1) || (perx && i == 0)) { ghost_state(P, 1, s, gs); store_cell(P, S, ext_index(P, P.nx, j), gs); }
+  if ((!perx && i == 0) || (perx && i == P.nx - 1)) {
+    ghost_state(P, 0, s, gs);
+    store_cell(P, S, ext_index(P, -1, j), gs, T(1) / gs[0]);
+  }
+  if ((!perx && i == P.nx - 1) || (perx && i == 0)) {
+    ghost_state(P, 1, s, gs);
+    store_cell(P, S, ext_index(P, P.nx, j), gs, T(1) / gs[0]);
+  }
   if (P.dim == 2) {
     const bool pery = P.bc[2] == GHOST_PERIODIC;
-    if ((!pery && j == 0) || (pery && j == P.ny - 1)) { ghost_state(P, 2, s, gs); store_cell(P, S, ext_index(P, i, -1), gs); }
-    if ((!pery && j == P.ny - 1) || (pery && j == 0)) { ghost_state(P, 3, s, gs); store_cell(P, S, ext_index(P, i, P.ny), gs); }
+    if ((!pery && j == 0) || (pery && j == P.ny - 1)) {
+      ghost_state(P, 2, s, gs);
+      store_cell(P, S, ext_index(P, i, -1), gs, T(1) / gs[0]);
+    }
+    if ((!pery && j == P.ny - 1) || (pery && j == 0)) {
+      ghost_state(P, 3, s, gs);
+      store_cell(P, S, ext_index(P, i, P.ny), gs, T(1) / gs[0]);
+    }
   }
 }
 
@@ -516,20 +614,20 @@ __global__ void __launch_bounds__(kThreads) cell_kernel(DevParams P, DevState<T>
       s[1] = s[1] - dtx * ax[1];
       s[3] = s[3] - dtx * ax[3];
     }
-    // semi-implicit friction: q <- q / (1 + dt C(h) |q|)
+    const T tau = T(1) / s[0];
+    // semi-implicit friction: q <- q / (1 + dt C(h) |q|),
+    // C = f / (8 h^2) (Darcy) or g / (K^2 h^(7/3)) (Strickler)
     if (P.friction != 0) {
-      const T H = s[0];
       const T qn = tsqrt(s[1] * s[1] + s[2] * s[2]);
-      T C;
-      if (P.friction == 1) C = T(P.fric_c) / (H * H);
-      else C = T(P.fric_c) / (H * H * tcbrt(H));
-      const T inv_den = T(1) / (T(1) + T(dt) * C * qn);
-      s[1] = s[1] * inv_den;
-      s[2] = s[2] * inv_den;
+      T C = T(P.fric_c) * (tau * tau);
+      if (P.friction == 2) C = C * rcbrt64(s[0]);
+      const T den = T(1) + T(dt) * C * qn;
+      s[1] = s[1] / den;
+      s[2] = s[2] / den;
     }
     if (!(tfinite(s[0]) && tfinite(s[1]) && tfinite(s[2]) && tfinite(s[3]))) atomicOr(&sc->status, ST_NAN);
-    else if (!(s[0] > T(0))) atomicOr(&sc->status, ST_NEG_DEPTH);
-    store_cell(P, S, e, s);
+    else if (!positive(s[0])) atomicOr(&sc->status, ST_NEG_DEPTH);
+    store_cell(P, S, e, s, tau);
     write_ghosts(P, S, i, j, s);
     mh = (double)s[0];
     mz = (double)s[3];
@@ -574,8 +672,8 @@ __global__ void __launch_bounds__(kThreads) init_kernel(DevParams P, DevState<T>
     const long long e = ext_index(P, i, j);
     T s[4] = {S.h[e], S.hu[e], P.dim == 2 ? S.hv[e] : T(0), S.z[e]};
     if (!(tfinite(s[0]) && tfinite(s[1]) && tfinite(s[2]) && tfinite(s[3]))) atomicOr(&sc->status, ST_NAN);
-    else if (!(s[0] > T(0))) atomicOr(&sc->status, ST_NEG_DEPTH);
-    store_cell(P, S, e, s);
+    else if (!positive(s[0])) atomicOr(&sc->status, ST_NEG_DEPTH);
+    store_cell(P, S, e, s, T(1) / s[0]);
     write_ghosts(P, S, i, j, s);
     mh = (double)s[0];
     mz = (double)s[3];
