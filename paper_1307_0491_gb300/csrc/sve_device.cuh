@@ -120,6 +120,14 @@ __device__ __forceinline__ double absbits(double a) {
 __device__ __forceinline__ float absbits(float a) { return fabsf(a); }
 __device__ __forceinline__ bool positive(double a) { return __double_as_longlong(a) > 0LL; }
 __device__ __forceinline__ bool positive(float a) { return a > 0.0f; }
+__device__ __forceinline__ bool negative(double a) {  // a < 0 (-0.0 counts as 0)
+  return __double_as_longlong(a) < 0LL && __double_as_longlong(a) != (long long)0x8000000000000000ULL;
+}
+__device__ __forceinline__ bool negative(float a) { return a < 0.0f; }
+__device__ __forceinline__ bool finite_bits(double a) {
+  return (__double_as_longlong(a) & 0x7ff0000000000000LL) != 0x7ff0000000000000LL;
+}
+__device__ __forceinline__ bool finite_bits(float a) { return isfinite(a); }
 __device__ __forceinline__ bool same_bits(double a, double b) {
   return __double_as_longlong(a) == __double_as_longlong(b);
 }
@@ -329,35 +337,53 @@ __device__ bool riemann_solve(const DevParams& P, const Cell<T>& L, const Cell<T
   const bool ok = newton_root(P, c, L, R, p0, e, iters);
   if (!ok || !newton_positive(e)) return false;
 
-  // intermediate states W1..W4 and the fluctuations sum_{lam<0} lam [U],
-  // sum_{lam>0} lam [U] of U = (H, H un, H ut, Z)
+  // Fluctuations A- = sum_{lam_k < 0} lam_k [U]_k and A+ = sum_{lam_k >= 0}
+  // lam_k [U]_k over the five waves, U = (H, H un, H ut, Z), written with the
+  // jump relations every wave of the fan satisfies (for any p): lam [H] =
+  // [H un], lam [H ut] = [H un ut], lam [H un] = [H un^2 + Pi] + g Hbar [Z]
+  // (Hbar = 2/(tau- + tau+), nonzero [Z] only at the b-waves), lam [Z] at the
+  // b-waves.  With m = the number of waves of negative speed, the minus sums
+  // telescope to (flux of state m) - (flux of L): one divide for H_m and one
+  // per b-wave instead of one per intermediate state.
   const T us = e.u1 + b * (e.tau2 - e.tau1);
-  T U[6][4];
-  U[0][0] = L.H; U[0][1] = L.Hn; U[0][2] = L.Ht; U[0][3] = L.Z;
-  U[5][0] = R.H; U[5][1] = R.Hn; U[5][2] = R.Ht; U[5][3] = R.Z;
-  const T tk[4] = {e.tau1, e.tau2, e.tau3, e.tau4};
-  const T uk[4] = {e.u1, us, us, e.u4};
-  const T vk[4] = {L.ut, L.ut, R.ut, R.ut};
-  const T zk[4] = {L.Z, e.Zs, e.Zs, R.Z};
-#pragma unroll
-  for (int k = 0; k < 4; ++k) {
-    const T Hk = T(1) / tk[k];
-    U[k + 1][0] = Hk;
-    U[k + 1][1] = Hk * uk[k];
-    U[k + 1][2] = Hk * vk[k];
-    U[k + 1][3] = zk[k];
+  const T lam2 = e.lam2, lam4 = e.lam4;
+  const int m = (int)negative(lam1) + (int)negative(lam2) + (int)negative(us) + (int)negative(lam4) +
+                (int)negative(lam5);
+  const T a2 = a * a;
+  // flux (H un, H un^2 + Pi, H un ut) of L, R and of the state m
+  const T FhL = L.Hn, FqL = L.Hn * L.un + L.Pi, FvL = L.Hn * L.ut;
+  const T FhR = R.Hn, FqR = R.Hn * R.un + R.Pi, FvR = R.Hn * R.ut;
+  T Fh, Fq, Fv;
+  if (m == 0) {
+    Fh = FhL; Fq = FqL; Fv = FvL;
+  } else if (m == 5) {
+    Fh = FhR; Fq = FqR; Fv = FvR;
+  } else {
+    // W1, W2 carry the left tangential velocity and Pi_L + a^2 (tau_L - tau);
+    // W3, W4 the right ones
+    const bool left = m <= 2;
+    const T tk = m == 1 ? e.tau1 : (m == 2 ? e.tau2 : (m == 3 ? e.tau3 : e.tau4));
+    const T uk = m == 1 ? e.u1 : (m == 4 ? e.u4 : us);
+    const T vk = left ? L.ut : R.ut;
+    const T Pk = left ? L.Pi + a2 * (L.tau - tk) : R.Pi + a2 * (R.tau - tk);
+    const T Hk = T(1) / tk;
+    Fh = Hk * uk;
+    Fq = Fh * uk + Pk;
+    Fv = Fh * vk;
   }
-  const T lam[5] = {lam1, e.lam2, us, e.lam4, lam5};
-#pragma unroll
-  for (int k = 0; k < 5; ++k) {
-    const T lk = lam[k];
-#pragma unroll
-    for (int cc = 0; cc < 4; ++cc) {
-      const T jump = U[k + 1][cc] - U[k][cc];
-      if (lk < T(0)) Am[cc] += lk * jump;
-      else if (lk > T(0)) Ap[cc] += lk * jump;
-    }
-  }
+  // b-waves: bed jumps and the non-conservative source g Hbar [Z]
+  const T zj2 = e.Zs - L.Z, zj4 = R.Z - e.Zs;
+  const T S2 = T(2) * g * zj2 / (e.tau1 + e.tau2);
+  const T S4 = T(2) * g * zj4 / (e.tau3 + e.tau4);
+  const bool n2 = negative(lam2), n4 = negative(lam4);
+  Am[0] = Fh - FhL;
+  Ap[0] = FhR - Fh;
+  Am[1] = (Fq - FqL) + ((n2 ? S2 : T(0)) + (n4 ? S4 : T(0)));
+  Ap[1] = (FqR - Fq) + ((n2 ? T(0) : S2) + (n4 ? T(0) : S4));
+  Am[2] = Fv - FvL;
+  Ap[2] = FvR - Fv;
+  Am[3] = (n2 ? lam2 * zj2 : T(0)) + (n4 ? lam4 * zj4 : T(0));
+  Ap[3] = (n2 ? T(0) : lam2 * zj2) + (n4 ? T(0) : lam4 * zj4);
   return true;
 }
 
@@ -542,12 +568,26 @@ __global__ void __launch_bounds__(kThreads) interface_kernel(DevParams P, DevSta
 #pragma unroll
     for (int c = 0; c < 4; ++c) { S.fy[c * P.nfy + k] = Am[c]; S.fy[(4 + c) * P.nfy + k] = Ap[c]; }
   }
-  const double bm = block_max<kThreads>(smax, sh);
-  // Newton updates of the block (for the operation count of the step)
-  double it_sum = (double)iters, dummy = 0.0;
-  block_sum2<kThreads>(it_sum, dummy, sh);
+  // block max of the (non-negative) speeds and sum of the Newton updates,
+  // both on integers (off the FP64 pipe)
+  long long bits = __double_as_longlong(smax);
+  int its = iters;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const long long ob = __shfl_xor_sync(0xffffffffu, bits, o);
+    bits = ob > bits ? ob : bits;
+    its += __shfl_xor_sync(0xffffffffu, its, o);
+  }
+  __shared__ long long shb[kThreads / 32];
+  __shared__ int shi[kThreads / 32];
+  if ((threadIdx.x & 31) == 0) { shb[threadIdx.x >> 5] = bits; shi[threadIdx.x >> 5] = its; }
+  __syncthreads();
   if (threadIdx.x == 0) {
-    atomicAdd(&sc->newton_iters, (unsigned long long)it_sum);
+    long long bb = shb[0];
+    int ii = shi[0];
+    for (int w = 1; w < kThreads / 32; ++w) { bb = shb[w] > bb ? shb[w] : bb; ii += shi[w]; }
+    const double bm = __longlong_as_double(bb);
+    atomicAdd(&sc->newton_iters, (unsigned long long)ii);
     spart[blockIdx.x] = bm;
     __threadfence();
     const unsigned int ticket = atomicAdd(&sc->done_iface, 1u);
@@ -625,7 +665,8 @@ __global__ void __launch_bounds__(kThreads) cell_kernel(DevParams P, DevState<T>
       s[1] = s[1] / den;
       s[2] = s[2] / den;
     }
-    if (!(tfinite(s[0]) && tfinite(s[1]) && tfinite(s[2]) && tfinite(s[3]))) atomicOr(&sc->status, ST_NAN);
+    if (!(finite_bits(s[0]) && finite_bits(s[1]) && finite_bits(s[2]) && finite_bits(s[3])))
+      atomicOr(&sc->status, ST_NAN);
     else if (!positive(s[0])) atomicOr(&sc->status, ST_NEG_DEPTH);
     store_cell(P, S, e, s, tau);
     write_ghosts(P, S, i, j, s);
