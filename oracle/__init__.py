@@ -167,6 +167,13 @@ class Oracle:
         L.orc_run.argtypes = [ctypes.POINTER(_Params), ctypes.c_int, dp, dp, dp, dp, dp, dp, dp, dp,
                               ctypes.POINTER(ctypes.c_int)]
         L.orc_run.restype = ctypes.c_int
+        for name in ("orc_block_ghost", "orc_block_speeds", "orc_block_advance"):
+            getattr(L, name).argtypes = [ctypes.POINTER(_Params), ctypes.c_int, ctypes.c_int, dp, dp, dp, dp] + (
+                [ctypes.c_int] if name == "orc_block_ghost" else [dp] if name == "orc_block_speeds" else
+                [ctypes.c_double])
+            getattr(L, name).restype = ctypes.c_int
+        L.orc_block_dt.argtypes = [ctypes.POINTER(_Params), ctypes.c_double, ctypes.c_double, dp]
+        L.orc_block_dt.restype = ctypes.c_int
         assert L.orc_sizeof_params() == ctypes.sizeof(_Params), "oracle params struct mismatch"
         assert L.orc_sizeof_riemann_out() == ctypes.sizeof(_RiemannOut), "oracle riemann struct mismatch"
 
@@ -250,6 +257,50 @@ class Oracle:
             "z": z.reshape(shape), "t": t.value, "dts": dts_out[:nsteps], "diag": diag[: 2 * nsteps].reshape(-1, 2),
             "status": st, "done": done.value,
         }
+
+
+class Block:
+    """One padded block (nxl + 2) x (nyl + 2) of a domain decomposition of
+    the grid of ``params`` (whose nx, ny are the whole grid's sizes)."""
+
+    def __init__(self, orc: "Oracle", p: Params, nxl: int, nyl: int):
+        self.orc, self.p, self.cp = orc, p, p.to_c()
+        self.nxl, self.nyl = nxl, nyl
+        self.f = {k: np.zeros((nyl + 2, nxl + 2)) for k in ("h", "hu", "hv", "z")}
+
+    def set_interior(self, h, hu, hv, z):
+        for k, a in zip(("h", "hu", "hv", "z"), (h, hu, hv, z)):
+            self.f[k][1:-1, 1:-1] = np.asarray(a).reshape(self.nyl, self.nxl)
+
+    def interior(self, k):
+        return self.f[k][1:-1, 1:-1]
+
+    def _ptrs(self):
+        return [self.f[k].ctypes.data_as(ctypes.POINTER(ctypes.c_double)) for k in ("h", "hu", "hv", "z")]
+
+    def ghost(self, side: int):
+        st = self.orc.lib.orc_block_ghost(ctypes.byref(self.cp), self.nxl, self.nyl, *self._ptrs(), int(side))
+        if st:
+            raise OracleError(st, "block_ghost")
+
+    def speeds(self):
+        S = (ctypes.c_double * 2)()
+        st = self.orc.lib.orc_block_speeds(ctypes.byref(self.cp), self.nxl, self.nyl, *self._ptrs(), S)
+        if st:
+            raise OracleError(st, "block_speeds")
+        return S[0], S[1]
+
+    def dt(self, Sx: float, Sy: float) -> float:
+        d = ctypes.c_double(0.0)
+        st = self.orc.lib.orc_block_dt(ctypes.byref(self.cp), Sx, Sy, ctypes.byref(d))
+        if st:
+            raise OracleError(st, "block_dt")
+        return d.value
+
+    def advance(self, dt: float):
+        st = self.orc.lib.orc_block_advance(ctypes.byref(self.cp), self.nxl, self.nyl, *self._ptrs(), float(dt))
+        if st:
+            raise OracleError(st, "block_advance")
 
 
 _DEFAULT: Oracle | None = None

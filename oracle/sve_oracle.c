@@ -447,7 +447,6 @@ static void orc_friction(const orc_params* P, double dt, double h, double* q1, d
 typedef struct {
   int nx, ny, ex;
   double *H, *Hu, *Hv, *Z;
-  orc_cell* cell;
 } orc_ext;
 
 static int orc_ext_alloc(orc_ext* X, int nx, int ny) {
@@ -457,11 +456,10 @@ static int orc_ext_alloc(orc_ext* X, int nx, int ny) {
   X->Hu = calloc(n, sizeof(double));
   X->Hv = calloc(n, sizeof(double));
   X->Z = calloc(n, sizeof(double));
-  X->cell = calloc(n, sizeof(orc_cell));
-  return (X->H && X->Hu && X->Hv && X->Z && X->cell) ? ORC_OK : ORC_ERR_ARG;
+  return (X->H && X->Hu && X->Hv && X->Z) ? ORC_OK : ORC_ERR_ARG;
 }
 static void orc_ext_free(orc_ext* X) {
-  free(X->H); free(X->Hu); free(X->Hv); free(X->Z); free(X->cell);
+  free(X->H); free(X->Hu); free(X->Hv); free(X->Z);
 }
 static size_t orc_xi(const orc_ext* X, int i, int j) { return (size_t)(j + 1) * X->ex + (size_t)(i + 1); }
 
@@ -522,10 +520,14 @@ static void orc_conserved(const orc_ext* X, int i, int j, int ydir, double c[4])
   c[3] = X->Z[k];
 }
 
-/* CFL time step of the padded state (reading R5). */
-static double orc_cfl_dt(const orc_params* P, const orc_ext* X) {
+/* Cell sizes of the whole grid (a padded block of a domain decomposition
+ * uses the same ones). */
+static double orc_dx(const orc_params* P) { return P->lx / P->nx; }
+static double orc_dy(const orc_params* P) { return (P->dim == 2) ? P->ly / P->ny : 1.0; }
+
+/* Extreme wave speeds over the interfaces of a padded block (reading R5). */
+static void orc_ext_speeds(const orc_params* P, const orc_ext* X, double* Sx_out, double* Sy_out) {
   int nx = X->nx, ny = X->ny;
-  double dx = P->lx / nx;
   double Sx = 0.0, Sy = 0.0;
   for (int j = 0; j < ny; ++j)
     for (int i = 0; i <= nx; ++i) {
@@ -534,27 +536,33 @@ static double orc_cfl_dt(const orc_params* P, const orc_ext* X) {
       double s = orc_interface_speed(P, &L, &R);
       if (s > Sx) Sx = s;
     }
-  if (P->dim == 1) return P->cfl * dx / Sx;
-  double dy = P->ly / ny;
-  for (int j = 0; j <= ny; ++j)
-    for (int i = 0; i < nx; ++i) {
-      orc_cell L = orc_project_dir(P, X, i, j - 1, 1);
-      orc_cell R = orc_project_dir(P, X, i, j, 1);
-      double s = orc_interface_speed(P, &L, &R);
-      if (s > Sy) Sy = s;
-    }
-  return P->cfl / (Sx / dx + Sy / dy);
+  if (P->dim == 2)
+    for (int j = 0; j <= ny; ++j)
+      for (int i = 0; i < nx; ++i) {
+        orc_cell L = orc_project_dir(P, X, i, j - 1, 1);
+        orc_cell R = orc_project_dir(P, X, i, j, 1);
+        double s = orc_interface_speed(P, &L, &R);
+        if (s > Sy) Sy = s;
+      }
+  *Sx_out = Sx;
+  *Sy_out = Sy;
 }
 
-/* One step of the scheme on (h, hu, hv, z) in place.  dt > 0 fixed, or
- * dt <= 0 for the CFL step; the step used is returned in *dt_used. */
-static int orc_step(const orc_params* P, orc_ext* X, double dt_fixed, double* h, double* hu, double* hv, double* z,
-                    double* dt_used, double* work /* 4 * nx * ny accumulators */) {
+/* CFL time step from the extreme speeds (reading R5). */
+static double orc_dt_of_speeds(const orc_params* P, double Sx, double Sy) {
+  if (P->dim == 1) return P->cfl * orc_dx(P) / Sx;
+  return P->cfl / (Sx / orc_dx(P) + Sy / orc_dy(P));
+}
+
+static double orc_cfl_dt(const orc_params* P, const orc_ext* X) {
+  double Sx, Sy;
+  orc_ext_speeds(P, X, &Sx, &Sy);
+  return orc_dt_of_speeds(P, Sx, Sy);
+}
+
+/* Validity of a padded state (interior and ghosts, corners excepted). */
+static int orc_ext_check(const orc_params* P, const orc_ext* X) {
   int nx = X->nx, ny = X->ny;
-  double dx = P->lx / nx;
-  double dy = (P->dim == 2) ? P->ly / ny : 1.0;
-  orc_fill(P, X, h, hu, hv, z);
-  /* validity of the state at time n (incl. ghosts) */
   for (int j = (P->dim == 2 ? -1 : 0); j <= (P->dim == 2 ? ny : ny - 1); ++j)
     for (int i = -1; i <= nx; ++i) {
       int corner = (P->dim == 2) && (i < 0 || i >= nx) && (j < 0 || j >= ny);
@@ -563,9 +571,16 @@ static int orc_step(const orc_params* P, orc_ext* X, double dt_fixed, double* h,
       int st = orc_check_cell(X->H[k], X->Hu[k], X->Hv[k], X->Z[k]);
       if (st) return st;
     }
-  double dt = dt_fixed > 0.0 ? dt_fixed : orc_cfl_dt(P, X);
-  if (!(dt > 0.0) || !isfinite(dt)) return ORC_ERR_DT;
-  *dt_used = dt;
+  return ORC_OK;
+}
+
+/* The update of Sec. 3 on a padded block whose ghosts are filled: one
+ * Riemann solve per interface, Godunov average of the interior cells in
+ * fluctuation form, then friction; the interior of X is overwritten. */
+static int orc_ext_advance(const orc_params* P, orc_ext* X, double dt, double* work /* 4 nx ny */) {
+  int nx = X->nx, ny = X->ny;
+  double dx = orc_dx(P);
+  double dy = orc_dy(P);
   double* acc = work; /* acc[4*c + comp], comp = H, Hu, Hv, Z */
   memset(acc, 0, sizeof(double) * 4 * (size_t)nx * ny);
   orc_riemann_out o;
@@ -615,18 +630,44 @@ static int orc_step(const orc_params* P, orc_ext* X, double dt_fixed, double* h,
   for (int j = 0; j < ny; ++j)
     for (int i = 0; i < nx; ++i) {
       size_t c = (size_t)j * nx + i;
+      size_t k = orc_xi(X, i, j);
       const double* a = acc + 4 * c;
-      double Hn = h[c] - dt * a[0];
-      double q1 = hu[c] - dt * a[1];
-      double q2 = (P->dim == 2) ? hv[c] - dt * a[2] : 0.0;
-      double Zn = z[c] - dt * a[3];
+      double Hn = X->H[k] - dt * a[0];
+      double q1 = X->Hu[k] - dt * a[1];
+      double q2 = (P->dim == 2) ? X->Hv[k] - dt * a[2] : 0.0;
+      double Zn = X->Z[k] - dt * a[3];
       orc_friction(P, dt, Hn, &q1, &q2);
       int st = orc_check_cell(Hn, q1, q2, Zn);
       if (st) return st;
-      h[c] = Hn;
-      hu[c] = q1;
-      if (P->dim == 2) hv[c] = q2;
-      z[c] = Zn;
+      X->H[k] = Hn;
+      X->Hu[k] = q1;
+      X->Hv[k] = q2;
+      X->Z[k] = Zn;
+    }
+  return ORC_OK;
+}
+
+/* One step of the scheme on (h, hu, hv, z) in place.  dt > 0 fixed, or
+ * dt <= 0 for the CFL step; the step used is returned in *dt_used. */
+static int orc_step(const orc_params* P, orc_ext* X, double dt_fixed, double* h, double* hu, double* hv, double* z,
+                    double* dt_used, double* work /* 4 * nx * ny accumulators */) {
+  int nx = X->nx, ny = X->ny;
+  orc_fill(P, X, h, hu, hv, z);
+  int st = orc_ext_check(P, X);
+  if (st) return st;
+  double dt = dt_fixed > 0.0 ? dt_fixed : orc_cfl_dt(P, X);
+  if (!(dt > 0.0) || !isfinite(dt)) return ORC_ERR_DT;
+  *dt_used = dt;
+  st = orc_ext_advance(P, X, dt, work);
+  if (st) return st;
+  for (int j = 0; j < ny; ++j)
+    for (int i = 0; i < nx; ++i) {
+      size_t c = (size_t)j * nx + i;
+      size_t k = orc_xi(X, i, j);
+      h[c] = X->H[k];
+      hu[c] = X->Hu[k];
+      if (P->dim == 2) hv[c] = X->Hv[k];
+      z[c] = X->Z[k];
     }
   return ORC_OK;
 }
@@ -729,3 +770,71 @@ int orc_run(const orc_params* P, int nsteps, const double* dts, double* h, doubl
 /* Byte sizes of the exported structs, so a caller can check its mirror. */
 int orc_sizeof_params(void) { return (int)sizeof(orc_params); }
 int orc_sizeof_riemann_out(void) { return (int)sizeof(orc_riemann_out); }
+
+/* ---- blocks of a domain decomposition (Sec. 4) ----------------------------
+ * A block is a padded array (nxl + 2) x (nyl + 2) of each field (index
+ * (j + 1)(nxl + 2) + (i + 1)), cut from the grid of P (P->nx, P->ny are the
+ * whole grid's sizes and fix dx, dy).  The caller fills the ghost ring:
+ * halo cells from the neighbouring blocks, or the boundary rule on the
+ * block's physical sides (orc_block_ghost).  The arithmetic is the one the
+ * whole-grid stepper uses, so a decomposed run equals it bit for bit. */
+
+static orc_ext orc_block_view(int nxl, int nyl, double* H, double* Hu, double* Hv, double* Z) {
+  orc_ext X;
+  X.nx = nxl; X.ny = nyl; X.ex = nxl + 2;
+  X.H = H; X.Hu = Hu; X.Hv = Hv; X.Z = Z;
+  return X;
+}
+
+/* Boundary rule of side (0 W, 1 E, 2 S, 3 N) into the block's ghosts from
+ * the block's adjacent interior cells (non-periodic sides only). */
+int orc_block_ghost(const orc_params* P, int nxl, int nyl, double* H, double* Hu, double* Hv, double* Z, int side) {
+  if (!P || nxl < 1 || nyl < 1 || side < 0 || side > 3 || P->bc[side] == ORC_BC_PERIODIC) return ORC_ERR_ARG;
+  orc_ext X = orc_block_view(nxl, nyl, H, Hu, Hv, Z);
+  double in[4], out[4];
+  if (side < 2) {
+    for (int j = 0; j < nyl; ++j) {
+      orc_ext_get(&X, side == 0 ? 0 : nxl - 1, j, in);
+      orc_ghost(P, side, in, out);
+      orc_ext_put(&X, side == 0 ? -1 : nxl, j, out);
+    }
+  } else {
+    for (int i = 0; i < nxl; ++i) {
+      orc_ext_get(&X, i, side == 2 ? 0 : nyl - 1, in);
+      orc_ghost(P, side, in, out);
+      orc_ext_put(&X, i, side == 2 ? -1 : nyl, out);
+    }
+  }
+  return ORC_OK;
+}
+
+/* Extreme wave speeds (S[0] x, S[1] y) over the block's interfaces. */
+int orc_block_speeds(const orc_params* P, int nxl, int nyl, double* H, double* Hu, double* Hv, double* Z,
+                     double* S) {
+  if (!P || !S || nxl < 1 || nyl < 1) return ORC_ERR_ARG;
+  orc_ext X = orc_block_view(nxl, nyl, H, Hu, Hv, Z);
+  int st = orc_ext_check(P, &X);
+  if (st) return st;
+  orc_ext_speeds(P, &X, &S[0], &S[1]);
+  return ORC_OK;
+}
+
+/* CFL step of the whole grid from its extreme speeds. */
+int orc_block_dt(const orc_params* P, double Sx, double Sy, double* dt) {
+  if (!P || !dt) return ORC_ERR_ARG;
+  *dt = orc_dt_of_speeds(P, Sx, Sy);
+  return (*dt > 0.0 && isfinite(*dt)) ? ORC_OK : ORC_ERR_DT;
+}
+
+/* One step of size dt on the block's interior (ghosts filled by the caller). */
+int orc_block_advance(const orc_params* P, int nxl, int nyl, double* H, double* Hu, double* Hv, double* Z,
+                      double dt) {
+  if (!P || nxl < 1 || nyl < 1 || !(dt > 0.0)) return ORC_ERR_ARG;
+  orc_ext X = orc_block_view(nxl, nyl, H, Hu, Hv, Z);
+  double* work = malloc(sizeof(double) * 4 * (size_t)nxl * nyl);
+  if (!work) return ORC_ERR_ARG;
+  int st = orc_ext_check(P, &X);
+  if (!st) st = orc_ext_advance(P, &X, dt, work);
+  free(work);
+  return st;
+}

@@ -31,7 +31,7 @@ MUTANTS = [
      "a[0] += o.Ap[0] / dy; a[1] += o.Ap[1] / dy; a[2] += o.Ap[2] / dy;"),
     ("darcy_friction_power", "C = P->f_dw / (8.0 * h * h);", "C = P->f_dw / (8.0 * h);"),
     ("pressure_factor", "c.Pi = 0.5 * P->g * H * H;", "c.Pi = P->g * H * H;"),
-    ("cfl_drops_y", "return P->cfl / (Sx / dx + Sy / dy);", "return P->cfl / (Sx / dx);"),
+    ("cfl_drops_y", "return P->cfl / (Sx / orc_dx(P) + Sy / orc_dy(P));", "return P->cfl / (Sx / orc_dx(P));"),
     ("inflow_direction", "double inward = (side == 0 || side == 2) ? 1.0 : -1.0;",
      "double inward = (side == 0 || side == 2) ? -1.0 : 1.0;"),
     ("zstar_wrong_index", "double Zs = L->Z + K * (tau2 * tau2 - tau1 * tau1);",
@@ -42,7 +42,7 @@ MUTANTS = [
     ("mpm_derivative_factor", "double d1 = 3.0 * sth * alpha * (un * un) / speed;",
      "double d1 = 1.5 * sth * alpha * (un * un) / speed;"),
     ("tangential_velocity_side", "o->v[3] = R->ut;", "o->v[3] = L->ut;"),
-    ("bed_update_sign", "double Zn = z[c] - dt * a[3];", "double Zn = z[c] + dt * a[3];"),
+    ("bed_update_sign", "double Zn = X->Z[k] - dt * a[3];", "double Zn = X->Z[k] + dt * a[3];"),
     ("wall_not_mirrored", "out[normal] = -in[normal];", "out[normal] = in[normal];"),
     ("bed_step_bound_dropped", "if (a * a < need) a = sqrt(need);", "(void)need;"),
 ]
