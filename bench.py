@@ -180,6 +180,41 @@ def run_reference(args, world, rank):
     return 0
 
 
+def run_batched(args, sve, W, torch, precision: str, plain_value: float):
+    """The batched ensemble: 256 independent 2D dune runs of uneven sizes and
+    parameters stepped together; cell-updates/s over all runs, compared with
+    the plain single-run step of the same precision."""
+    runs = W.ensemble(nruns=args.batch_runs, seed=0)
+    cells = sum(r["params"]["nx"] * r["params"]["ny"] for r in runs)
+    b = sve.Batch([r["params"] for r in runs], precision, stream=torch.cuda.current_stream().cuda_stream)
+    for i, r in enumerate(runs):
+        b.set_state(i, r["h"], r["hu"], r["hv"], r["z"])
+    tile, sched = b.autotune(2)
+    b.step(args.batch_spinup)
+    b.step(2)
+    c0 = b.counters()
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    b.step_async(args.batch_steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    c1 = b.counters()
+    b.close()
+    value = cells * args.batch_steps / (ms * 1e-3)
+    return {"workload": f"{args.batch_runs} independent 2D dune runs, Nx~U{{128..1024}}, Ny~U{{64..512}}, "
+                        f"A_g log-U[1e-4,1e-2], m_g in {{1,2,3,4}}, amplitude U[0.2,1] (seed 0)",
+            "precision": precision, "runs": args.batch_runs, "cells_per_step": cells, "value": value, "unit": UNIT,
+            "ms_per_step": ms / args.batch_steps, "steps": args.batch_steps,
+            "timed_steps_of_run": f"{args.batch_spinup + 2}..{args.batch_spinup + 1 + args.batch_steps}",
+            "launches_per_step": 2, "tile": tile, "schedule": ["run-major", "round-robin"][sched],
+            "newton_updates": c1["newton_iters"] - c0["newton_iters"],
+            "vs_plain": value / plain_value if plain_value else None,
+            "l2": "working set larger than L2 (no flush)"}
+
+
 def run_ours(args, world, rank, local):
     import torch
 
@@ -296,6 +331,10 @@ def run_ours(args, world, rank, local):
             "gpu_launches": int(prof["iface_launches"] + prof["cell_launches"]),
             "clocks": clk,
         }
+        if not args.no_batch:
+            line["batched"] = [run_batched(args, sve, W, torch, "fp64", value)]
+            if args.batch_fp32:
+                line["batched"].append(run_batched(args, sve, W, torch, "fp32", None))
         if world == 1 and not args.no_cpu_baseline:
             rate, nsteps, secs = cpu_oracle_rate(w)
             line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
@@ -316,6 +355,11 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--spinup", type=int, default=400, help="untimed steps before warm-up (run regime)")
+    ap.add_argument("--no-batch", action="store_true", help="skip the batched-ensemble measurement")
+    ap.add_argument("--batch-runs", type=int, default=256)
+    ap.add_argument("--batch-steps", type=int, default=10)
+    ap.add_argument("--batch-spinup", type=int, default=100)
+    ap.add_argument("--batch-fp32", action="store_true", help="also time the FP32-state ensemble")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

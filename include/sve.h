@@ -184,6 +184,44 @@ int sve_profile_read(sve_handle* h, double* ms, long long* launches);
  * Blocks; returns the latched device status. */
 int sve_get_counters(sve_handle* h, long long* steps, unsigned long long* newton_iters);
 
+/* ---- batches of independent runs ------------------------------------------
+ * An ensemble of runs, each with its own configuration (grid size, bedload
+ * and friction parameters, boundaries; all of one precision), its own CFL
+ * time step, time and mass sums, stepped together: every step is one launch
+ * over all runs' interfaces and one over all their cells, cut into tiles of
+ * one run each (a tile table in a schedule order), captured in CUDA graphs.
+ * Each run advances as a single handle with the same configuration would:
+ * the same per-interface and per-cell code, compiled into other kernels, so
+ * results agree to round-off (FMA contraction may differ).  Run r's state
+ * arrays follow the single-run conventions with its own nx, ny. */
+typedef struct sve_batch sve_batch;
+
+/* cfgs[0..nruns-1]: one validated configuration per run (same precision).
+ * Allocates every run's device state; SVE_ERR_ARG / SVE_ERR_OOM. */
+int sve_batch_create(const sve_config* cfgs, int nruns, sve_batch** out);
+int sve_batch_set_stream(sve_batch* b, void* stream);
+/* Copy run `run`'s state in (t of that run reset to 0); checked as in
+ * sve_set_state.  Every run needs a state before the first step. */
+int sve_batch_set_state(sve_batch* b, int run, const void* depth, const void* hu, const void* hv, const void* zb,
+                        int where);
+/* Every run advances nsteps of its own CFL steps.  Blocks; returns the first
+ * latched device error of any run.  _async: enqueue only. */
+int sve_batch_step(sve_batch* b, int nsteps);
+int sve_batch_step_async(sve_batch* b, int nsteps);
+int sve_batch_get_state(sve_batch* b, int run, void* depth, void* hu, void* hv, void* zb, int where);
+int sve_batch_get_diag(sve_batch* b, int run, double* mass_h, double* mass_z, double* t, double* last_dt);
+/* Steps and Newton updates summed over all runs since their states were set. */
+int sve_batch_get_counters(sve_batch* b, long long* steps, unsigned long long* newton_iters);
+/* Time trial_steps steps of every candidate tile size (128, 256 work items)
+ * and schedule (0: run after run, largest first; 1: round robin over the
+ * runs), keep the fastest; the runs' states are restored afterwards.
+ * Reports the choice in *tile, *schedule (nullable). */
+int sve_batch_autotune(sve_batch* b, int trial_steps, int* tile, int* schedule);
+/* Select a tile size and schedule directly. */
+int sve_batch_set_schedule(sve_batch* b, int tile, int schedule);
+long long sve_batch_last_launch_count(sve_batch* b);
+void sve_batch_destroy(sve_batch* b);
+
 /* ---- stepping without device allocation ----------------------------------
  * The paper has no counterpart of this entry point: it serves callers that
  * cannot call cudaMalloc -- code living under a framework's caching allocator

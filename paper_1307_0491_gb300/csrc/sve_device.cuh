@@ -531,6 +531,63 @@ __device__ __forceinline__ Cell<T> load_cell(const DevState<T>& S, long long e, 
   return c;
 }
 
+// One interface of one grid: the x-interface (i - 1/2, j) for k = j (nx + 1)
+// + i, or (ydir) the y-interface (i, j - 1/2) for k = j nx + i.  Solves the
+// Riemann problem, stores the fluctuations, returns the extreme speed and the
+// Newton updates; false if the solve failed (fluctuations zero then).
+template <typename T>
+__device__ __forceinline__ bool interface_item(const DevParams& P, const DevState<T>& S, bool ydir, long long k,
+                                               double& smax, int& iters) {
+  T Am[4], Ap[4], s;
+  bool ok;
+  if (!ydir) {
+    const int row = (int)(k / (P.nx + 1));
+    const int i = (int)(k - (long long)row * (P.nx + 1));
+    const long long eR = ext_index(P, i, row);
+    const Cell<T> L = load_cell(S, eR - 1, false);
+    const Cell<T> R = load_cell(S, eR, false);
+    ok = riemann_solve(P, L, R, Am, Ap, s, iters);
+#pragma unroll
+    for (int c = 0; c < 4; ++c) { S.fx[c * P.nfx + k] = Am[c]; S.fx[(4 + c) * P.nfx + k] = Ap[c]; }
+  } else {
+    const int row = (int)(k / P.nx);  // j in [0, ny]
+    const int i = (int)(k - (long long)row * P.nx);
+    const long long eR = ext_index(P, i, row);
+    const Cell<T> L = load_cell(S, eR - P.ex, true);
+    const Cell<T> R = load_cell(S, eR, true);
+    ok = riemann_solve(P, L, R, Am, Ap, s, iters);
+#pragma unroll
+    for (int c = 0; c < 4; ++c) { S.fy[c * P.nfy + k] = Am[c]; S.fy[(4 + c) * P.nfy + k] = Ap[c]; }
+  }
+  smax = (double)s;
+  return ok;
+}
+
+// Block-wide integer max of non-negative doubles and sum of ints; the
+// result is valid in thread 0.
+template <int NT>
+__device__ __forceinline__ void block_maxbits_sum(double& v, int& n) {
+  long long bits = __double_as_longlong(v);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const long long ob = __shfl_xor_sync(0xffffffffu, bits, o);
+    bits = ob > bits ? ob : bits;
+    n += __shfl_xor_sync(0xffffffffu, n, o);
+  }
+  __shared__ long long shb[NT / 32];
+  __shared__ int shi[NT / 32];
+  if ((threadIdx.x & 31) == 0) { shb[threadIdx.x >> 5] = bits; shi[threadIdx.x >> 5] = n; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    long long bb = shb[0];
+    int ii = shi[0];
+    for (int w = 1; w < NT / 32; ++w) { bb = shb[w] > bb ? shb[w] : bb; ii += shi[w]; }
+    v = __longlong_as_double(bb);
+    n = ii;
+  }
+  __syncthreads();
+}
+
 // One thread per interface.  Blocks [0, nbx) cover the x-interfaces
 // (i - 1/2, j), i in [0, nx], j in [0, ny); blocks [nbx, nbx + nby) cover the
 // y-interfaces (i, j - 1/2), i in [0, nx), j in [0, ny].  The last block to
@@ -545,50 +602,15 @@ __global__ void __launch_bounds__(kThreads) interface_kernel(DevParams P, DevSta
   const long long k = (long long)(ydir ? blockIdx.x - P.nbx : blockIdx.x) * kThreads + threadIdx.x;
   double smax = 0.0;
   int iters = 0;
-  if (!ydir && k < P.nfx) {
-    const int row = (int)(k / (P.nx + 1));
-    const int i = (int)(k - (long long)row * (P.nx + 1));
-    const long long eR = ext_index(P, i, row);
-    const Cell<T> L = load_cell(S, eR - 1, false);
-    const Cell<T> R = load_cell(S, eR, false);
-    T Am[4], Ap[4], s;
-    if (!riemann_solve(P, L, R, Am, Ap, s, iters)) atomicOr(&sc->status, ST_RIEMANN);
-    smax = (double)s;
-#pragma unroll
-    for (int c = 0; c < 4; ++c) { S.fx[c * P.nfx + k] = Am[c]; S.fx[(4 + c) * P.nfx + k] = Ap[c]; }
-  } else if (ydir && k < P.nfy) {
-    const int row = (int)(k / P.nx);  // j in [0, ny]
-    const int i = (int)(k - (long long)row * P.nx);
-    const long long eR = ext_index(P, i, row);
-    const Cell<T> L = load_cell(S, eR - P.ex, true);
-    const Cell<T> R = load_cell(S, eR, true);
-    T Am[4], Ap[4], s;
-    if (!riemann_solve(P, L, R, Am, Ap, s, iters)) atomicOr(&sc->status, ST_RIEMANN);
-    smax = (double)s;
-#pragma unroll
-    for (int c = 0; c < 4; ++c) { S.fy[c * P.nfy + k] = Am[c]; S.fy[(4 + c) * P.nfy + k] = Ap[c]; }
+  if (k < (ydir ? P.nfy : P.nfx)) {
+    if (!interface_item(P, S, ydir, k, smax, iters)) atomicOr(&sc->status, ST_RIEMANN);
   }
   // block max of the (non-negative) speeds and sum of the Newton updates,
   // both on integers (off the FP64 pipe)
-  long long bits = __double_as_longlong(smax);
-  int its = iters;
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    const long long ob = __shfl_xor_sync(0xffffffffu, bits, o);
-    bits = ob > bits ? ob : bits;
-    its += __shfl_xor_sync(0xffffffffu, its, o);
-  }
-  __shared__ long long shb[kThreads / 32];
-  __shared__ int shi[kThreads / 32];
-  if ((threadIdx.x & 31) == 0) { shb[threadIdx.x >> 5] = bits; shi[threadIdx.x >> 5] = its; }
-  __syncthreads();
+  block_maxbits_sum<kThreads>(smax, iters);
   if (threadIdx.x == 0) {
-    long long bb = shb[0];
-    int ii = shi[0];
-    for (int w = 1; w < kThreads / 32; ++w) { bb = shb[w] > bb ? shb[w] : bb; ii += shi[w]; }
-    const double bm = __longlong_as_double(bb);
-    atomicAdd(&sc->newton_iters, (unsigned long long)ii);
-    spart[blockIdx.x] = bm;
+    atomicAdd(&sc->newton_iters, (unsigned long long)iters);
+    spart[blockIdx.x] = smax;
     __threadfence();
     const unsigned int ticket = atomicAdd(&sc->done_iface, 1u);
     last = (ticket == gridDim.x - 1);
@@ -618,6 +640,58 @@ __global__ void __launch_bounds__(kThreads) interface_kernel(DevParams P, DevSta
   }
 }
 
+// One interior cell k = j nx + i of one grid: Godunov average in
+// fluctuation form with step dt, friction, checks, projection of the new
+// state and its ghosts.  Returns status bits; (mh, mz) = new (h, z).
+template <typename T>
+__device__ __forceinline__ int cell_item(const DevParams& P, const DevState<T>& S, long long k, double dt,
+                                         double& mh, double& mz) {
+  const int j = (int)(k / P.nx);
+  const int i = (int)(k - (long long)j * P.nx);
+  const long long e = ext_index(P, i, j);
+  const T dtx = T(dt * P.inv_dx);
+  const long long kx = (long long)j * (P.nx + 1) + i;
+  T s[4] = {S.h[e], S.hu[e], S.hv[e], S.z[e]};
+  T ax[4];
+#pragma unroll
+  for (int c = 0; c < 4; ++c) ax[c] = S.fx[(4 + c) * P.nfx + kx] + S.fx[c * P.nfx + kx + 1];
+  if (P.dim == 2) {
+    const T dty = T(dt * P.inv_dy);
+    const long long ky = (long long)j * P.nx + i;
+    T ay[4];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) ay[c] = S.fy[(4 + c) * P.nfy + ky] + S.fy[c * P.nfy + ky + P.nx];
+    // y frame (H, Hv, Hu, Z) back to (H, Hu, Hv, Z)
+    s[0] = s[0] - (dtx * ax[0] + dty * ay[0]);
+    s[1] = s[1] - (dtx * ax[1] + dty * ay[2]);
+    s[2] = s[2] - (dtx * ax[2] + dty * ay[1]);
+    s[3] = s[3] - (dtx * ax[3] + dty * ay[3]);
+  } else {
+    s[0] = s[0] - dtx * ax[0];
+    s[1] = s[1] - dtx * ax[1];
+    s[3] = s[3] - dtx * ax[3];
+  }
+  const T tau = T(1) / s[0];
+  // semi-implicit friction: q <- q / (1 + dt C(h) |q|),
+  // C = f / (8 h^2) (Darcy) or g / (K^2 h^(7/3)) (Strickler)
+  if (P.friction != 0) {
+    const T qn = tsqrt(s[1] * s[1] + s[2] * s[2]);
+    T C = T(P.fric_c) * (tau * tau);
+    if (P.friction == 2) C = C * rcbrt64(s[0]);
+    const T den = T(1) + T(dt) * C * qn;
+    s[1] = s[1] / den;
+    s[2] = s[2] / den;
+  }
+  int st = 0;
+  if (!(finite_bits(s[0]) && finite_bits(s[1]) && finite_bits(s[2]) && finite_bits(s[3]))) st = ST_NAN;
+  else if (!positive(s[0])) st = ST_NEG_DEPTH;
+  store_cell(P, S, e, s, tau);
+  write_ghosts(P, S, i, j, s);
+  mh = (double)s[0];
+  mz = (double)s[3];
+  return st;
+}
+
 // One thread per interior cell (i, j): Godunov average in fluctuation form,
 // friction, checks, projection of the new state, ghosts, mass partials.
 template <typename T>
@@ -628,50 +702,8 @@ __global__ void __launch_bounds__(kThreads) cell_kernel(DevParams P, DevState<T>
   const long long ncell = (long long)P.nx * P.ny;
   double mh = 0.0, mz = 0.0;
   if (k < ncell) {
-    const int j = (int)(k / P.nx);
-    const int i = (int)(k - (long long)j * P.nx);
-    const long long e = ext_index(P, i, j);
-    const double dt = sc->dt;
-    const T dtx = T(dt * P.inv_dx);
-    const long long kx = (long long)j * (P.nx + 1) + i;
-    T s[4] = {S.h[e], S.hu[e], S.hv[e], S.z[e]};
-    T ax[4];
-#pragma unroll
-    for (int c = 0; c < 4; ++c) ax[c] = S.fx[(4 + c) * P.nfx + kx] + S.fx[c * P.nfx + kx + 1];
-    if (P.dim == 2) {
-      const T dty = T(dt * P.inv_dy);
-      const long long ky = (long long)j * P.nx + i;
-      T ay[4];
-#pragma unroll
-      for (int c = 0; c < 4; ++c) ay[c] = S.fy[(4 + c) * P.nfy + ky] + S.fy[c * P.nfy + ky + P.nx];
-      // y frame (H, Hv, Hu, Z) back to (H, Hu, Hv, Z)
-      s[0] = s[0] - (dtx * ax[0] + dty * ay[0]);
-      s[1] = s[1] - (dtx * ax[1] + dty * ay[2]);
-      s[2] = s[2] - (dtx * ax[2] + dty * ay[1]);
-      s[3] = s[3] - (dtx * ax[3] + dty * ay[3]);
-    } else {
-      s[0] = s[0] - dtx * ax[0];
-      s[1] = s[1] - dtx * ax[1];
-      s[3] = s[3] - dtx * ax[3];
-    }
-    const T tau = T(1) / s[0];
-    // semi-implicit friction: q <- q / (1 + dt C(h) |q|),
-    // C = f / (8 h^2) (Darcy) or g / (K^2 h^(7/3)) (Strickler)
-    if (P.friction != 0) {
-      const T qn = tsqrt(s[1] * s[1] + s[2] * s[2]);
-      T C = T(P.fric_c) * (tau * tau);
-      if (P.friction == 2) C = C * rcbrt64(s[0]);
-      const T den = T(1) + T(dt) * C * qn;
-      s[1] = s[1] / den;
-      s[2] = s[2] / den;
-    }
-    if (!(finite_bits(s[0]) && finite_bits(s[1]) && finite_bits(s[2]) && finite_bits(s[3])))
-      atomicOr(&sc->status, ST_NAN);
-    else if (!positive(s[0])) atomicOr(&sc->status, ST_NEG_DEPTH);
-    store_cell(P, S, e, s, tau);
-    write_ghosts(P, S, i, j, s);
-    mh = (double)s[0];
-    mz = (double)s[3];
+    const int st = cell_item(P, S, k, sc->dt, mh, mz);
+    if (st) atomicOr(&sc->status, st);
   }
   block_sum2<kThreads>(mh, mz, sh);
   if (threadIdx.x == 0) {

@@ -31,7 +31,10 @@ SVE_HOST, SVE_DEVICE = 0, 1
 #: every symbol include/sve.h declares
 EXPORTS = ("sve_config_default", "sve_create", "sve_set_stream", "sve_set_state", "sve_step", "sve_step_dt",
            "sve_get_state", "sve_get_diag", "sve_get_dts", "sve_destroy", "sve_strerror", "sve_last_launch_count",
-           "sve_step_async", "sve_sync", "sve_profile", "sve_profile_read", "sve_get_counters", "sve_step_noalloc")
+           "sve_step_async", "sve_sync", "sve_profile", "sve_profile_read", "sve_get_counters", "sve_step_noalloc",
+           "sve_batch_create", "sve_batch_set_stream", "sve_batch_set_state", "sve_batch_step",
+           "sve_batch_step_async", "sve_batch_get_state", "sve_batch_get_diag", "sve_batch_get_counters",
+           "sve_batch_autotune", "sve_batch_set_schedule", "sve_batch_last_launch_count", "sve_batch_destroy")
 
 
 class sve_config(ctypes.Structure):
@@ -88,6 +91,18 @@ def load() -> ctypes.CDLL:
         "sve_profile_read": ([vp, dp, ctypes.POINTER(ctypes.c_longlong)], ip),
         "sve_get_counters": ([vp, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_ulonglong)], ip),
         "sve_step_noalloc": ([cfgp, vp, vp, vp, vp, ip, dp, vp], ip),
+        "sve_batch_create": ([cfgp, ip, ctypes.POINTER(vp)], ip),
+        "sve_batch_set_stream": ([vp, vp], ip),
+        "sve_batch_set_state": ([vp, ip, vp, vp, vp, vp, ip], ip),
+        "sve_batch_step": ([vp, ip], ip),
+        "sve_batch_step_async": ([vp, ip], ip),
+        "sve_batch_get_state": ([vp, ip, vp, vp, vp, vp, ip], ip),
+        "sve_batch_get_diag": ([vp, ip, dp, dp, dp, dp], ip),
+        "sve_batch_get_counters": ([vp, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_ulonglong)], ip),
+        "sve_batch_autotune": ([vp, ip, ctypes.POINTER(ip), ctypes.POINTER(ip)], ip),
+        "sve_batch_set_schedule": ([vp, ip, ip], ip),
+        "sve_batch_last_launch_count": ([vp], ctypes.c_longlong),
+        "sve_batch_destroy": ([vp], None),
     }
     for name, (args, res) in sig.items():
         fn = getattr(L, name)
@@ -190,6 +205,64 @@ def sve_step_noalloc(cfg: sve_config, depth: int, hu: int, hv: int | None, zb: i
     rc = load().sve_step_noalloc(ctypes.byref(cfg), depth, hu, hv, zb, int(nsteps), ctypes.byref(tt),
                                  ctypes.c_void_p(stream or 0))
     return rc, tt.value
+
+
+def sve_batch_create(cfgs) -> tuple[int, ctypes.c_void_p]:
+    arr = (sve_config * len(cfgs))(*cfgs)
+    b = ctypes.c_void_p()
+    rc = load().sve_batch_create(arr, len(cfgs), ctypes.byref(b))
+    return rc, b
+
+
+def sve_batch_set_state(b, run: int, depth: int, hu: int, hv: int | None, zb: int, where: int) -> int:
+    return load().sve_batch_set_state(b, int(run), depth, hu, hv, zb, where)
+
+
+def sve_batch_step(b, nsteps: int) -> int:
+    return load().sve_batch_step(b, int(nsteps))
+
+
+def sve_batch_step_async(b, nsteps: int) -> int:
+    return load().sve_batch_step_async(b, int(nsteps))
+
+
+def sve_batch_get_state(b, run: int, depth: int, hu: int, hv: int | None, zb: int, where: int) -> int:
+    return load().sve_batch_get_state(b, int(run), depth, hu, hv, zb, where)
+
+
+def sve_batch_get_diag(b, run: int) -> tuple[int, dict]:
+    vals = [ctypes.c_double() for _ in range(4)]
+    rc = load().sve_batch_get_diag(b, int(run), *[ctypes.byref(v) for v in vals])
+    return rc, dict(mass_h=vals[0].value, mass_z=vals[1].value, t=vals[2].value, dt=vals[3].value)
+
+
+def sve_batch_get_counters(b) -> tuple[int, int, int]:
+    steps = ctypes.c_longlong(0)
+    its = ctypes.c_ulonglong(0)
+    rc = load().sve_batch_get_counters(b, ctypes.byref(steps), ctypes.byref(its))
+    return rc, steps.value, its.value
+
+
+def sve_batch_autotune(b, trial_steps: int) -> tuple[int, int, int]:
+    tile, sched = ctypes.c_int(0), ctypes.c_int(0)
+    rc = load().sve_batch_autotune(b, int(trial_steps), ctypes.byref(tile), ctypes.byref(sched))
+    return rc, tile.value, sched.value
+
+
+def sve_batch_set_schedule(b, tile: int, schedule: int) -> int:
+    return load().sve_batch_set_schedule(b, int(tile), int(schedule))
+
+
+def sve_batch_set_stream(b, stream: int | None) -> int:
+    return load().sve_batch_set_stream(b, ctypes.c_void_p(stream or 0))
+
+
+def sve_batch_last_launch_count(b) -> int:
+    return int(load().sve_batch_last_launch_count(b))
+
+
+def sve_batch_destroy(b) -> None:
+    load().sve_batch_destroy(b)
 
 
 # ---- convenience wrapper ---------------------------------------------------
@@ -326,3 +399,73 @@ class Solver:
         rc, steps, its = sve_get_counters(self.h)
         _check(rc, "sve_get_counters")
         return dict(steps=steps, newton_iters=its)
+
+
+class Batch:
+    """An ensemble of independent runs stepped together (sve_batch_*)."""
+
+    def __init__(self, params_list, precision: str = "fp64", stream: int | None = None):
+        self.params = [dict(p) for p in params_list]
+        self.precision = precision
+        self.dtype = np.float64 if precision == "fp64" else np.float32
+        cfgs = [config_from_params(p, precision) for p in self.params]
+        rc, self.h = sve_batch_create(cfgs)
+        _check(rc, "sve_batch_create")
+        if stream is not None:
+            _check(sve_batch_set_stream(self.h, stream), "sve_batch_set_stream")
+
+    def close(self):
+        if getattr(self, "h", None):
+            sve_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _shape(self, r):
+        p = self.params[r]
+        return (p["ny"], p["nx"]) if p["dim"] == 2 else (p["nx"],)
+
+    def set_state(self, r: int, h, hu, hv, z):
+        arrs = [np.ascontiguousarray(np.asarray(x, dtype=self.dtype).reshape(self._shape(r))) for x in (h, hu, z)]
+        hva = (np.ascontiguousarray(np.asarray(hv, dtype=self.dtype).reshape(self._shape(r)))
+               if self.params[r]["dim"] == 2 else None)
+        _check(sve_batch_set_state(self.h, r, arrs[0].ctypes.data, arrs[1].ctypes.data,
+                                   hva.ctypes.data if hva is not None else None, arrs[2].ctypes.data, SVE_HOST),
+               "sve_batch_set_state")
+
+    def step(self, nsteps: int) -> None:
+        _check(sve_batch_step(self.h, nsteps), "sve_batch_step")
+
+    def step_async(self, nsteps: int) -> None:
+        _check(sve_batch_step_async(self.h, nsteps), "sve_batch_step_async")
+
+    def get_state(self, r: int) -> dict:
+        shp = self._shape(r)
+        out = {k: np.empty(shp, dtype=self.dtype) for k in ("h", "hu", "z")}
+        out["hv"] = np.empty(shp, dtype=self.dtype) if self.params[r]["dim"] == 2 else None
+        _check(sve_batch_get_state(self.h, r, out["h"].ctypes.data, out["hu"].ctypes.data,
+                                   out["hv"].ctypes.data if out["hv"] is not None else None, out["z"].ctypes.data,
+                                   SVE_HOST), "sve_batch_get_state")
+        return out
+
+    def diag(self, r: int) -> dict:
+        rc, d = sve_batch_get_diag(self.h, r)
+        _check(rc, "sve_batch_get_diag")
+        return d
+
+    def counters(self) -> dict:
+        rc, steps, its = sve_batch_get_counters(self.h)
+        _check(rc, "sve_batch_get_counters")
+        return dict(steps=steps, newton_iters=its)
+
+    def autotune(self, trial_steps: int = 3) -> tuple[int, int]:
+        rc, tile, sched = sve_batch_autotune(self.h, trial_steps)
+        _check(rc, "sve_batch_autotune")
+        return tile, sched
+
+    def set_schedule(self, tile: int, schedule: int) -> None:
+        _check(sve_batch_set_schedule(self.h, tile, schedule), "sve_batch_set_schedule")
