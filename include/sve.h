@@ -222,6 +222,30 @@ int sve_batch_set_schedule(sve_batch* b, int tile, int schedule);
 long long sve_batch_last_launch_count(sve_batch* b);
 void sve_batch_destroy(sve_batch* b);
 
+/* ---- discrete adjoint ------------------------------------------------------
+ * Gradients through nsteps steps of the scheme, with the time steps of the
+ * forward run recorded and held fixed: the adjoint of the discrete map
+ * U^n -> U^{n+1} (the paper gives the scheme, Sec. 3; its adjoint is this
+ * library's addition).  FP64 state and the Grass law only.
+ *
+ * sve_record_forward advances the handle's current state by nsteps CFL
+ * steps (as sve_step) and records the time steps and a checkpoint of the
+ * conserved state every checkpoint_every steps (<= 0: ceil(sqrt(nsteps))).
+ * The handle then holds U^N.
+ *
+ * sve_adjoint propagates a cotangent of the final state back to the
+ * recorded run's initial state: lam_h, lam_hu, lam_hv, lam_z = dL/dU^N
+ * (nx*ny doubles each, NULL = zero; hv ignored in 1D) in memory `where`;
+ * g_h0 .. g_z0 (nullable, same layout and memory) receive dL/dU^0 and
+ * g_params[3] (host, nullable) = dL/dA_g, dL/dm_g, dL/d(friction
+ * coefficient: K for Strickler, f for Darcy-Weisbach; 0 without friction).
+ * The forward states are recomputed per checkpoint segment.  Afterwards the
+ * handle holds the recorded run's initial state.  SVE_ERR_STATE if nothing
+ * was recorded; SVE_ERR_ARG for FP32 or MPM handles. */
+int sve_record_forward(sve_handle* h, int nsteps, int checkpoint_every);
+int sve_adjoint(sve_handle* h, const void* lam_h, const void* lam_hu, const void* lam_hv, const void* lam_z,
+                int where, void* g_h0, void* g_hu0, void* g_hv0, void* g_z0, double* g_params);
+
 /* ---- stepping without device allocation ----------------------------------
  * The paper has no counterpart of this entry point: it serves callers that
  * cannot call cudaMalloc -- code living under a framework's caching allocator

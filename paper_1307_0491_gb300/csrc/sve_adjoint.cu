@@ -1,0 +1,552 @@
+// sve_adjoint.cu -- hand-written discrete adjoint of the step (include/sve.h,
+// sve_record_forward / sve_adjoint).
+//
+// Step n maps U^n to U^{n+1} = Fric(U^n - dt_n/dx (A+ + A-) - dt_n/dy (...))
+// with the time steps dt_n recorded by the forward run and held fixed.  The
+// reverse sweep propagates lambda^n = (dU^{n+1}/dU^n)^T lambda^{n+1}:
+//   adj_friction_kernel  mu = (dFric/dU~)^T lambda^{n+1} per cell (closed form),
+//                        and the friction coefficient's gradient;
+//   adj_interface_kernel per interface, the Jacobian of (A-, A+) with respect
+//                        to both cells' conserved states, A_g and m_g, by
+//                        forward-mode dual numbers through the very templates
+//                        the step uses (projection, celerities, Newton
+//                        constants, fan); the Newton root enters through the
+//                        implicit function theorem, dp = -F_theta / F_p, at
+//                        the converged p; contracted with mu of both cells;
+//   adj_gather_kernel    lambda^n = mu + the contributions of the cell's four
+//                        interfaces, ghost cells routed back to the cells they
+//                        copy (the transposed ghost rule).
+// Forward states are recomputed per segment from checkpoints taken every C
+// steps (C ~ sqrt(N)): memory of ~2 sqrt(N) states, one extra forward pass.
+// Supported: FP64 state, Grass bedload (A_g, m_g), any friction law (its
+// coefficient: K for Strickler, f for Darcy-Weisbach), every boundary rule.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <string.h>
+
+#include <vector>
+
+#include "../../include/sve.h"
+#include "sve_device.cuh"
+#include "sve_dual.cuh"
+#include "sve_handle.h"
+
+using sve::Cell;
+using sve::DevParams;
+using sve::DevScalars;
+using sve::DevState;
+using sve::Dual;
+using sve::NewtonConst;
+using sve::NewtonEval;
+
+struct sve_adjoint_rec {
+  int nsteps = 0;
+  int every = 0;
+  std::vector<double> dts;          // dt of each recorded step
+  std::vector<double*> checkpoints;  // padded (h, hu, hv, z) at steps 0, C, 2C, ...
+  double* seg = nullptr;            // padded states of one segment (C of them)
+  size_t seg_cap = 0;
+  double* lam = nullptr;            // 2 x 4 interior planes (current, next)
+  double* mu = nullptr;             // 4 interior planes
+  double* gpart = nullptr;          // per-block parameter partials
+  size_t gpart_cap = 0;
+  double* gacc = nullptr;           // [3] accumulated parameter gradients + counters
+  unsigned int* done = nullptr;
+  double t0 = 0.0;
+};
+
+namespace {
+
+constexpr int kAdjThreads = 128;
+
+// Projection of a conserved state (H, Hn, Ht, Z) in an interface frame with the
+// Grass law written through pow, so that A_g and m_g can carry derivatives.
+template <typename T>
+__device__ __forceinline__ Cell<T> project_grass(const DevParams& P, T H, T Hn, T Ht, T Z, T A, T m) {
+  Cell<T> c;
+  c.H = H; c.Hn = Hn; c.Ht = Ht; c.Z = Z;
+  c.tau = T(1) / H;
+  c.un = Hn * c.tau;
+  c.ut = Ht * c.tau;
+  const T g = T(P.g);
+  c.Pi = T(0.5) * g * H * H;
+  const T speed2 = c.un * c.un + c.ut * c.ut;
+  T Q, dQ;
+  if (speed2 == T(0)) {
+    Q = T(0);
+    dQ = (m == T(1)) ? A : T(0);
+  } else {
+    const T sp = sve::tsqrt(speed2);
+    const T pm1 = sve::tpow(sp, m - T(1));
+    const T second = (m - T(1)) * (c.un * c.un) * sve::tpow(sp, m - T(3));
+    Q = A * c.un * pm1;
+    dQ = A * (pm1 + second);
+  }
+  c.Om = Q;
+  c.ca = H * sve::tsqrt(g * H);
+  c.cb = sve::tsqrt(Hn * Hn + g * H * H * dQ);
+  return c;
+}
+
+// One Jacobian pass with 5 dual directions: PASS 0 = the left state's four
+// components and A_g; PASS 1 = the right state's four and m_g.  out[k]
+// (k = 0..7 state components in frame order, 8 = A_g, 9 = m_g) receives
+// w * sum_c (muL_c dA-_c/dx_k + muR_c dA+_c/dx_k).
+template <int PASS>
+__device__ __forceinline__ void jac_pass(const DevParams& P, const double u[8], double A, double m, double pstar,
+                                         double Fp, const double muL[4], const double muR[4], double w,
+                                         double out[10]) {
+  using D = Dual<5>;
+  D x[10];
+#pragma unroll
+  for (int k = 0; k < 8; ++k) x[k] = D(u[k]);
+  x[8] = D(A);
+  x[9] = D(m);
+#pragma unroll
+  for (int j = 0; j < 4; ++j) x[PASS * 4 + j].d[j] = 1.0;
+  x[8 + PASS].d[4] = 1.0;
+  const Cell<D> L = project_grass(P, x[0], x[1], x[2], x[3], x[8], x[9]);
+  const Cell<D> R = project_grass(P, x[4], x[5], x[6], x[7], x[8], x[9]);
+  D a, b;
+  sve::celerities(P, L, R, a, b);
+  NewtonConst<D> c;
+  sve::newton_setup(P, L, R, a, b, c);
+  NewtonEval<D> e;
+  D p(pstar);
+  sve::newton_eval(p, c, L, R, e);  // F and its derivatives at the fixed root
+#pragma unroll
+  for (int j = 0; j < 5; ++j) p.d[j] = -e.F.d[j] / Fp;  // implicit function theorem
+  sve::newton_eval(p, c, L, R, e);
+  D Am[4], Ap[4];
+  sve::fan_fluctuations(P, L, R, c, e, Am, Ap);
+#pragma unroll
+  for (int j = 0; j < 5; ++j) {
+    double s = 0.0;
+#pragma unroll
+    for (int cc = 0; cc < 4; ++cc) s += muL[cc] * Am[cc].d[j] + muR[cc] * Ap[cc].d[j];
+    out[j < 4 ? PASS * 4 + j : 8 + PASS] = w * s;
+  }
+}
+
+// Deterministic sum of per-block partials (n per block) into acc[0..n-1] by
+// the last block of the launch.
+template <int NT>
+__device__ __forceinline__ void finish_partials(const double* part, int nper, double* acc, unsigned int* done) {
+  __shared__ bool last;
+  if (threadIdx.x == 0) {
+    __threadfence();
+    last = atomicAdd(done, 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  if (threadIdx.x == 0) {
+    const volatile double* vp = part;
+    for (int q = 0; q < nper; ++q) {
+      double s = 0.0;
+      for (unsigned b = 0; b < gridDim.x; ++b) s += vp[nper * b + q];
+      acc[q] += s;
+    }
+    *done = 0u;
+  }
+}
+
+__device__ __forceinline__ double block_sum(double v, double* sh) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
+  __syncthreads();
+  double r = 0.0;
+  if (threadIdx.x == 0)
+    for (int w = 0; w < kAdjThreads / 32; ++w) r += sh[w];
+  __syncthreads();
+  return r;
+}
+
+// mu = (dFric/dU~)^T lambda^{n+1} per interior cell; gradient of the friction
+// coefficient.  Fric: q <- q / den, den = 1 + dt C(h) |q|.
+__global__ void __launch_bounds__(kAdjThreads) adj_friction_kernel(DevParams P, DevState<double> S,
+                                                                   const double* lam, double* mu, double dt,
+                                                                   double* gpart, double* gacc,
+                                                                   unsigned int* done) {
+  __shared__ double sh[kAdjThreads / 32];
+  const long long ncell = (long long)P.nx * P.ny;
+  const long long k = (long long)blockIdx.x * kAdjThreads + threadIdx.x;
+  double gk = 0.0;
+  if (k < ncell) {
+    const int j = (int)(k / P.nx), i = (int)(k - (long long)j * P.nx);
+    double s[4];
+    sve::convect_cell(P, S, i, j, sve::ext_index(P, i, j), dt, s);
+    const double lh = lam[k], l1 = lam[ncell + k], l2 = lam[2 * ncell + k], lz = lam[3 * ncell + k];
+    double mh = lh, m1 = l1, m2 = l2;
+    if (P.friction != 0) {
+      const double h = s[0], q1 = s[1], q2 = s[2];
+      const double qn = sqrt(q1 * q1 + q2 * q2);
+      const double tau = 1.0 / h;
+      double C = P.fric_c * tau * tau;
+      if (P.friction == 2) C = C / cbrt(h);
+      const double den = 1.0 + dt * C * qn;
+      const double id = 1.0 / den, id2 = id * id;
+      // dC/dh = -2 C / h (Darcy), -7/3 C / h (Strickler)
+      const double dCdh = (P.friction == 1 ? -2.0 : -7.0 / 3.0) * C * tau;
+      const double lq = l1 * q1 + l2 * q2;  // lambda . q
+      mh = lh - lq * dt * qn * dCdh * id2;
+      if (qn > 0.0) {
+        const double f = dt * C / qn * id2;
+        m1 = l1 * id - lq * f * q1;
+        m2 = l2 * id - lq * f * q2;
+      } else {
+        m1 = l1 * id;
+        m2 = l2 * id;
+      }
+      // coefficient: Strickler K (C = g / (K^2 h^(7/3)): dC/dK = -2 C / K);
+      // Darcy f (C = f / (8 h^2): dC/df = C / f)
+      const double dCdk = P.friction == 2 ? -2.0 * C / P.fric_coef : C / P.fric_coef;
+      gk = -lq * dt * qn * dCdk * id2;
+    }
+    mu[k] = mh;
+    mu[ncell + k] = m1;
+    mu[2 * ncell + k] = m2;
+    mu[3 * ncell + k] = lz;
+  }
+  const double b = block_sum(gk, sh);
+  if (threadIdx.x == 0) gpart[blockIdx.x] = b;
+  finish_partials<kAdjThreads>(gpart, 1, gacc + 2, done);
+}
+
+// Per interface: the Jacobian-transpose product of its fluctuations with mu of
+// its two cells (a ghost side has mu = 0), stored in the fluctuation planes
+// (8 values: left state then right state, interface frame); A_g and m_g
+// gradients accumulated.
+__global__ void __launch_bounds__(kAdjThreads) adj_interface_kernel(DevParams P, DevState<double> S,
+                                                                    const double* mu, double dt, double A,
+                                                                    double m, double* gpart, double* gacc,
+                                                                    unsigned int* done) {
+  __shared__ double sh[kAdjThreads / 32];
+  const long long ncell = (long long)P.nx * P.ny;
+  const long long nall = P.nfx + P.nfy;
+  const long long idx = (long long)blockIdx.x * kAdjThreads + threadIdx.x;
+  double gA = 0.0, gm = 0.0;
+  if (idx < nall) {
+    const bool ydir = idx >= P.nfx;
+    const long long k = ydir ? idx - P.nfx : idx;
+    int iL, jL, iR, jR;
+    if (!ydir) {
+      jR = (int)(k / (P.nx + 1));
+      iR = (int)(k - (long long)jR * (P.nx + 1));
+      iL = iR - 1;
+      jL = jR;
+    } else {
+      jR = (int)(k / P.nx);
+      iR = (int)(k - (long long)jR * P.nx);
+      iL = iR;
+      jL = jR - 1;
+    }
+    const long long eL = sve::ext_index(P, iL, jL), eR = sve::ext_index(P, iR, jR);
+    const bool inL = iL >= 0 && iL < P.nx && jL >= 0 && jL < P.ny;
+    const bool inR = iR >= 0 && iR < P.nx && jR >= 0 && jR < P.ny;
+    const int cn = ydir ? 2 : 1, ct = ydir ? 1 : 2;  // normal / tangential component in (h, hu, hv, z)
+    double muL[4] = {0, 0, 0, 0}, muR[4] = {0, 0, 0, 0};
+    if (inL) {
+      const long long c = (long long)jL * P.nx + iL;
+      muL[0] = mu[c]; muL[1] = mu[cn * ncell + c]; muL[2] = mu[ct * ncell + c]; muL[3] = mu[3 * ncell + c];
+    }
+    if (inR) {
+      const long long c = (long long)jR * P.nx + iR;
+      muR[0] = mu[c]; muR[1] = mu[cn * ncell + c]; muR[2] = mu[ct * ncell + c]; muR[3] = mu[3 * ncell + c];
+    }
+    double out[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+    bool any = false;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) any = any || muL[c] != 0.0 || muR[c] != 0.0;
+    if (any) {
+      const double* hn = ydir ? S.hv : S.hu;
+      const double* ht = ydir ? S.hu : S.hv;
+      const double u[8] = {S.h[eL], hn[eL], ht[eL], S.z[eL], S.h[eR], hn[eR], ht[eR], S.z[eR]};
+      // value pass: the root p* of this interface
+      const Cell<double> Lv = project_grass<double>(P, u[0], u[1], u[2], u[3], A, m);
+      const Cell<double> Rv = project_grass<double>(P, u[4], u[5], u[6], u[7], A, m);
+      double av, bv;
+      sve::celerities(P, Lv, Rv, av, bv);
+      NewtonConst<double> cv;
+      double p = sve::newton_setup(P, Lv, Rv, av, bv, cv);
+      NewtonEval<double> ev;
+      sve::newton_eval(p, cv, Lv, Rv, ev);
+      int its = 0;
+      sve::newton_loop(cv, Lv, Rv, p, ev, P.newton_maxit, fmax(P.newton_tol, 16.0 * 2.220446049250313e-16), its);
+      const double Fp = sve::newton_deriv(cv, ev);
+      const double w = -dt * (ydir ? P.inv_dy : P.inv_dx);
+      jac_pass<0>(P, u, A, m, p, Fp, muL, muR, w, out);
+      jac_pass<1>(P, u, A, m, p, Fp, muL, muR, w, out);
+    }
+    double* v = ydir ? S.fy : S.fx;
+    const long long nf = ydir ? P.nfy : P.nfx;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) v[q * nf + k] = out[q];
+    gA = out[8];
+    gm = out[9];
+  }
+  const double bA = block_sum(gA, sh);
+  const double bm = block_sum(gm, sh);
+  if (threadIdx.x == 0) {
+    gpart[2 * blockIdx.x] = bA;
+    gpart[2 * blockIdx.x + 1] = bm;
+  }
+  finish_partials<kAdjThreads>(gpart, 2, gacc, done);
+}
+
+// Transposed ghost rule of side s in the side's frame (h, normal, tangential,
+// z): periodic / free copy, inflow_q keeps h and z, inflow_qh keeps z, wall
+// mirrors the normal discharge.
+__device__ __forceinline__ void ghost_transpose(int type, double g[4]) {
+  switch (type) {
+    case sve::GHOST_INFLOW_Q: g[1] = 0.0; g[2] = 0.0; break;
+    case sve::GHOST_INFLOW_QH: g[0] = 0.0; g[1] = 0.0; g[2] = 0.0; break;
+    case sve::GHOST_WALL: g[1] = -g[1]; break;
+    default: break;
+  }
+}
+
+__global__ void __launch_bounds__(kAdjThreads) adj_gather_kernel(DevParams P, DevState<double> S, const double* mu,
+                                                                 double* lam) {
+  const long long ncell = (long long)P.nx * P.ny;
+  const long long k = (long long)blockIdx.x * kAdjThreads + threadIdx.x;
+  if (k >= ncell) return;
+  const int j = (int)(k / P.nx), i = (int)(k - (long long)j * P.nx);
+  const long long nfx = P.nfx, nfy = P.nfy;
+  double r[4] = {mu[k], mu[ncell + k], mu[2 * ncell + k], mu[3 * ncell + k]};
+  // x: as the right cell of interface (i - 1/2, j), as the left cell of (i + 1/2, j)
+  const long long kx = (long long)j * (P.nx + 1) + i;
+#pragma unroll
+  for (int c = 0; c < 4; ++c) r[c] += S.fx[(4 + c) * nfx + kx] + S.fx[c * nfx + kx + 1];
+  if (P.dim == 2) {
+    // y frame (h, hv, hu, z)
+    const long long ky = (long long)j * P.nx + i;
+    const double* y = S.fy;
+    r[0] += y[4 * nfy + ky] + y[0 * nfy + ky + P.nx];
+    r[2] += y[5 * nfy + ky] + y[1 * nfy + ky + P.nx];
+    r[1] += y[6 * nfy + ky] + y[2 * nfy + ky + P.nx];
+    r[3] += y[7 * nfy + ky] + y[3 * nfy + ky + P.nx];
+  }
+  // ghosts this cell feeds: their adjoint flows back through the ghost rule
+  double g[4];
+  const bool perx = P.bc[0] == sve::GHOST_PERIODIC;
+  if ((!perx && i == 0) || (perx && i == P.nx - 1)) {  // W ghost: left state of (0 - 1/2, j)
+    const long long kk = (long long)j * (P.nx + 1);
+    for (int c = 0; c < 4; ++c) g[c] = S.fx[c * nfx + kk];
+    ghost_transpose(P.bc[0], g);
+    for (int c = 0; c < 4; ++c) r[c] += g[c];
+  }
+  if ((!perx && i == P.nx - 1) || (perx && i == 0)) {  // E ghost: right state of (nx - 1/2, j)
+    const long long kk = (long long)j * (P.nx + 1) + P.nx;
+    for (int c = 0; c < 4; ++c) g[c] = S.fx[(4 + c) * nfx + kk];
+    ghost_transpose(P.bc[1], g);
+    for (int c = 0; c < 4; ++c) r[c] += g[c];
+  }
+  if (P.dim == 2) {
+    const bool pery = P.bc[2] == sve::GHOST_PERIODIC;
+    if ((!pery && j == 0) || (pery && j == P.ny - 1)) {  // S ghost: left state of (i, 0 - 1/2)
+      const long long kk = i;
+      for (int c = 0; c < 4; ++c) g[c] = S.fy[c * nfy + kk];
+      ghost_transpose(P.bc[2], g);
+      r[0] += g[0]; r[2] += g[1]; r[1] += g[2]; r[3] += g[3];
+    }
+    if ((!pery && j == P.ny - 1) || (pery && j == 0)) {  // N ghost: right state of (i, ny - 1/2)
+      const long long kk = (long long)P.ny * P.nx + i;
+      for (int c = 0; c < 4; ++c) g[c] = S.fy[(4 + c) * nfy + kk];
+      ghost_transpose(P.bc[3], g);
+      r[0] += g[0]; r[2] += g[1]; r[1] += g[2]; r[3] += g[3];
+    }
+  }
+  lam[k] = r[0];
+  lam[ncell + k] = r[1];
+  lam[2 * ncell + k] = r[2];
+  lam[3 * ncell + k] = r[3];
+}
+
+#define ADJ_TRY(expr)                               \
+  do {                                              \
+    if ((expr) != cudaSuccess) return SVE_ERR_CUDA; \
+  } while (0)
+
+int status_of(const sve_handle* h) {
+  DevScalars s;
+  if (cudaMemcpyAsync(&s, h->sc, sizeof(s), cudaMemcpyDeviceToHost, h->stream) != cudaSuccess) return SVE_ERR_CUDA;
+  if (cudaStreamSynchronize(h->stream) != cudaSuccess) return SVE_ERR_CUDA;
+  if (s.status & sve::ST_NAN) return SVE_ERR_NAN;
+  if (s.status & sve::ST_NEG_DEPTH) return SVE_ERR_NEG_DEPTH;
+  if (s.status & sve::ST_RIEMANN) return SVE_ERR_RIEMANN;
+  if (s.status & sve::ST_DT) return SVE_ERR_DT;
+  return SVE_OK;
+}
+
+// copy the 4 padded conserved fields of the handle to / from a buffer
+int save_state(sve_handle* h, double* dst) {
+  const size_t n = (size_t)h->next;
+  for (int f = 0; f < 4; ++f)
+    ADJ_TRY(cudaMemcpyAsync(dst + f * n, h->fields[f], sizeof(double) * n, cudaMemcpyDeviceToDevice, h->stream));
+  return SVE_OK;
+}
+int load_state(sve_handle* h, const double* src) {
+  const size_t n = (size_t)h->next;
+  for (int f = 0; f < 4; ++f)
+    ADJ_TRY(cudaMemcpyAsync(h->fields[f], src + f * n, sizeof(double) * n, cudaMemcpyDeviceToDevice, h->stream));
+  return SVE_OK;
+}
+
+int grow(double** p, size_t* cap, size_t n) {
+  if (*cap >= n) return SVE_OK;
+  if (*p) cudaFree(*p);
+  *p = nullptr;
+  if (cudaMalloc(p, sizeof(double) * n) != cudaSuccess) return SVE_ERR_OOM;
+  *cap = n;
+  return SVE_OK;
+}
+
+void free_rec(sve_adjoint_rec* r) {
+  if (!r) return;
+  for (double* c : r->checkpoints) cudaFree(c);
+  if (r->seg) cudaFree(r->seg);
+  if (r->lam) cudaFree(r->lam);
+  if (r->mu) cudaFree(r->mu);
+  if (r->gpart) cudaFree(r->gpart);
+  if (r->gacc) cudaFree(r->gacc);
+  if (r->done) cudaFree(r->done);
+  delete r;
+}
+
+// one forward step of size dt with the handle's kernels (fixed-dt mode)
+int forward_step(sve_handle* h, double dt) {
+  ADJ_TRY(cudaMemcpyAsync(h->fixed, &dt, sizeof(double), cudaMemcpyHostToDevice, h->stream));
+  ADJ_TRY(cudaMemsetAsync(&h->sc->call_step, 0, sizeof(int), h->stream));
+  DevState<double> S = state_of<double>(h);
+  sve::interface_kernel<double><<<h->nb_iface, sve::kThreads, 0, h->stream>>>(h->P, S, h->sc, h->spart, h->fixed,
+                                                                             h->dtlog, 1);
+  sve::cell_kernel<double><<<h->nb_cell, sve::kThreads, 0, h->stream>>>(h->P, S, h->sc, h->mpart);
+  return cudaGetLastError() == cudaSuccess ? SVE_OK : SVE_ERR_CUDA;
+}
+
+}  // namespace
+
+__attribute__((visibility("hidden"))) void sve_internal_adjoint_free(sve_handle* h) {
+  if (h && h->adj) {
+    cudaStreamSynchronize(h->stream);
+    free_rec(h->adj);
+    h->adj = nullptr;
+  }
+}
+
+extern "C" {
+
+int sve_record_forward(sve_handle* h, int nsteps, int checkpoint_every) {
+  if (!h || nsteps < 1) return SVE_ERR_ARG;
+  if (!h->has_state) return SVE_ERR_STATE;
+  if (h->cfg.precision != SVE_FP64 || h->cfg.bedload != SVE_GRASS) return SVE_ERR_ARG;
+  sve_internal_adjoint_free(h);
+  sve_adjoint_rec* r = new sve_adjoint_rec();
+  h->adj = r;
+  r->nsteps = nsteps;
+  r->every = checkpoint_every > 0 ? checkpoint_every : (int)ceil(sqrt((double)nsteps));
+  if (r->every > nsteps) r->every = nsteps;
+  const int ncp = (nsteps + r->every - 1) / r->every;
+  const size_t n = 4 * (size_t)h->next;
+  double t0 = 0.0;
+  ADJ_TRY(cudaMemcpy(&t0, &h->sc->t, sizeof(double), cudaMemcpyDeviceToHost));
+  r->t0 = t0;
+  r->dts.resize(nsteps);
+  for (int k = 0; k < ncp; ++k) {
+    double* c = nullptr;
+    if (cudaMalloc(&c, sizeof(double) * n) != cudaSuccess) { sve_internal_adjoint_free(h); return SVE_ERR_OOM; }
+    r->checkpoints.push_back(c);
+    int rc = save_state(h, c);
+    const int len = (k + 1) * r->every <= nsteps ? r->every : nsteps - k * r->every;
+    rc = rc ? rc : sve_step(h, len, nullptr);
+    if (rc) { sve_internal_adjoint_free(h); return rc; }
+    if (sve_get_dts(h, r->dts.data() + (size_t)k * r->every, len) != len) { sve_internal_adjoint_free(h); return SVE_ERR_CUDA; }
+  }
+  return SVE_OK;
+}
+
+int sve_adjoint(sve_handle* h, const void* lam_h, const void* lam_hu, const void* lam_hv, const void* lam_z,
+                int where, void* g_h0, void* g_hu0, void* g_hv0, void* g_z0, double* g_params) {
+  if (!h || (where != SVE_HOST && where != SVE_DEVICE)) return SVE_ERR_ARG;
+  sve_adjoint_rec* r = h->adj;
+  if (!r) return SVE_ERR_STATE;
+  const DevParams& P = h->P;
+  const long long ncell = (long long)P.nx * P.ny;
+  const size_t nst = 4 * (size_t)h->next;
+  int rc = SVE_OK;
+  if (!r->lam && cudaMalloc(&r->lam, sizeof(double) * 8 * ncell) != cudaSuccess) return SVE_ERR_OOM;
+  if (!r->mu && cudaMalloc(&r->mu, sizeof(double) * 4 * ncell) != cudaSuccess) return SVE_ERR_OOM;
+  if (!r->gacc && cudaMalloc(&r->gacc, sizeof(double) * 4) != cudaSuccess) return SVE_ERR_OOM;
+  if (!r->done && cudaMalloc(&r->done, sizeof(unsigned int)) != cudaSuccess) return SVE_ERR_OOM;
+  const int nb_if = (int)((P.nfx + P.nfy + kAdjThreads - 1) / kAdjThreads);
+  const int nb_c = (int)((ncell + kAdjThreads - 1) / kAdjThreads);
+  rc = grow(&r->gpart, &r->gpart_cap, 2 * (size_t)(nb_if > nb_c ? nb_if : nb_c));
+  if (rc) return rc;
+  rc = grow(&r->seg, &r->seg_cap, nst * (size_t)r->every);
+  if (rc) return rc;
+  double* lam = r->lam;             // lambda^{n+1}
+  double* lam_next = r->lam + 4 * ncell;
+  ADJ_TRY(cudaMemsetAsync(r->gacc, 0, sizeof(double) * 4, h->stream));
+  ADJ_TRY(cudaMemsetAsync(r->done, 0, sizeof(unsigned int), h->stream));
+  const cudaMemcpyKind kin = where == SVE_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+  const void* lin[4] = {lam_h, lam_hu, lam_hv, lam_z};
+  for (int f = 0; f < 4; ++f) {
+    if (lin[f] && !(f == 2 && P.dim == 1))
+      ADJ_TRY(cudaMemcpyAsync(lam + f * ncell, lin[f], sizeof(double) * ncell, kin, h->stream));
+    else
+      ADJ_TRY(cudaMemsetAsync(lam + f * ncell, 0, sizeof(double) * ncell, h->stream));
+  }
+  DevState<double> S = state_of<double>(h);
+  const int ncp = (int)r->checkpoints.size();
+  for (int k = ncp - 1; k >= 0; --k) {
+    const int n0 = k * r->every;
+    const int len = (k + 1) * r->every <= r->nsteps ? r->every : r->nsteps - n0;
+    // recompute the segment's states U^{n0} .. U^{n0 + len - 1}
+    rc = load_state(h, r->checkpoints[k]);
+    if (rc) return rc;
+    sve::init_kernel<double><<<h->nb_cell, sve::kThreads, 0, h->stream>>>(P, S, h->sc, h->mpart);
+    for (int s = 0; s < len; ++s) {
+      rc = save_state(h, r->seg + (size_t)s * nst);
+      if (!rc) rc = forward_step(h, r->dts[n0 + s]);
+      if (rc) return rc;
+    }
+    // reverse through the segment
+    for (int s = len - 1; s >= 0; --s) {
+      const double dt = r->dts[n0 + s];
+      rc = load_state(h, r->seg + (size_t)s * nst);
+      if (rc) return rc;
+      sve::init_kernel<double><<<h->nb_cell, sve::kThreads, 0, h->stream>>>(P, S, h->sc, h->mpart);
+      // forward fluctuations of step n (needed for the pre-friction state)
+      ADJ_TRY(cudaMemcpyAsync(h->fixed, &dt, sizeof(double), cudaMemcpyHostToDevice, h->stream));
+      ADJ_TRY(cudaMemsetAsync(&h->sc->call_step, 0, sizeof(int), h->stream));
+      sve::interface_kernel<double><<<h->nb_iface, sve::kThreads, 0, h->stream>>>(P, S, h->sc, h->spart,
+                                                                                 h->fixed, h->dtlog, 1);
+      adj_friction_kernel<<<nb_c, kAdjThreads, 0, h->stream>>>(P, S, lam, r->mu, dt, r->gpart, r->gacc, r->done);
+      adj_interface_kernel<<<nb_if, kAdjThreads, 0, h->stream>>>(P, S, r->mu, dt, h->cfg.A_g, h->cfg.m_g,
+                                                                 r->gpart, r->gacc, r->done);
+      adj_gather_kernel<<<nb_c, kAdjThreads, 0, h->stream>>>(P, S, r->mu, lam_next);
+      if (cudaGetLastError() != cudaSuccess) return SVE_ERR_CUDA;
+      double* t = lam;
+      lam = lam_next;
+      lam_next = t;
+    }
+  }
+  rc = status_of(h);
+  if (rc) return rc;
+  const cudaMemcpyKind kout = where == SVE_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
+  void* outs[4] = {g_h0, g_hu0, g_hv0, g_z0};
+  for (int f = 0; f < 4; ++f)
+    if (outs[f] && !(f == 2 && P.dim == 1))
+      ADJ_TRY(cudaMemcpyAsync(outs[f], lam + f * ncell, sizeof(double) * ncell, kout, h->stream));
+  double g[4] = {0, 0, 0, 0};
+  ADJ_TRY(cudaMemcpyAsync(g, r->gacc, sizeof(double) * 4, cudaMemcpyDeviceToHost, h->stream));
+  // the handle now holds the recorded run's initial state at its time
+  ADJ_TRY(cudaMemcpyAsync(&h->sc->t, &r->t0, sizeof(double), cudaMemcpyHostToDevice, h->stream));
+  ADJ_TRY(cudaStreamSynchronize(h->stream));
+  if (g_params) { g_params[0] = g[0]; g_params[1] = g[1]; g_params[2] = g[2]; }
+  return SVE_OK;
+}
+
+}  // extern "C"

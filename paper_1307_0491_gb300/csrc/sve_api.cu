@@ -11,51 +11,15 @@
 
 #include "../../include/sve.h"
 #include "sve_device.cuh"
+#include "sve_handle.h"
 
 using sve::DevParams;
 using sve::DevScalars;
 using sve::DevState;
 
 namespace {
-
 constexpr int kGraphSteps = 16;  // steps per captured graph
-
-struct Graph {
-  cudaGraphExec_t exec = nullptr;
-};
-
 }  // namespace
-
-struct sve_handle {
-  sve_config cfg;
-  DevParams P;
-  int device = 0;
-  cudaStream_t stream = nullptr;   // user stream (nullptr = legacy default)
-  cudaStream_t capture = nullptr;  // private stream used only to capture graphs
-  bool has_state = false;
-  size_t elem = 8;                 // bytes per state element
-  long long next = 0;              // padded cells
-  void* fields[13] = {};           // h hu hv z tau u v pi omx omy ca cbx cby
-  void* fx = nullptr;
-  void* fy = nullptr;
-  double* spart = nullptr;
-  double* mpart = nullptr;
-  DevScalars* sc = nullptr;
-  double* dtlog = nullptr;
-  int dtlog_cap = 0;
-  double* fixed = nullptr;
-  int fixed_cap = 0;
-  int nb_iface = 0, nb_cell = 0;
-  Graph graph[2];                  // [fixed]
-  long long last_launches = 0;
-  int last_steps = 0;
-  // kernel timing (sve_profile): 3 events per step, read back lazily
-  bool profiling = false;
-  std::vector<cudaEvent_t> events;
-  size_t events_used = 0;
-  double prof_ms[2] = {0.0, 0.0};
-  long long prof_launches[2] = {0, 0};
-};
 
 namespace {
 
@@ -123,8 +87,8 @@ void make_params(const sve_config* c, DevParams* P) {
   }
   P->tau_cr = c->tau_cr;
   P->friction = c->friction;
-  if (c->friction == SVE_FRIC_DARCY) P->fric_c = c->f_dw / 8.0;
-  else if (c->friction == SVE_FRIC_STRICKLER) P->fric_c = c->g / (c->K_st * c->K_st);
+  if (c->friction == SVE_FRIC_DARCY) { P->fric_c = c->f_dw / 8.0; P->fric_coef = c->f_dw; }
+  else if (c->friction == SVE_FRIC_STRICKLER) { P->fric_c = c->g / (c->K_st * c->K_st); P->fric_coef = c->K_st; }
   for (int s = 0; s < 4; ++s) P->bc[s] = c->bc[s];
   P->q_in = c->q_in;
   P->h_in = c->h_in;
@@ -137,16 +101,6 @@ void make_params(const sve_config* c, DevParams* P) {
   P->nfy = P->dim == 2 ? (long long)P->nx * (P->ny + 1) : 0;
   P->nbx = (int)((P->nfx + sve::kThreads - 1) / sve::kThreads);
   P->nby = (int)((P->nfy + sve::kThreads - 1) / sve::kThreads);
-}
-
-template <typename T>
-DevState<T> state_of(const sve_handle* h) {
-  DevState<T> S;
-  T** f[13] = {&S.h, &S.hu, &S.hv, &S.z, &S.tau, &S.u, &S.v, &S.pi, &S.omx, &S.omy, &S.ca, &S.cbx, &S.cby};
-  for (int k = 0; k < 13; ++k) *f[k] = (T*)h->fields[k];
-  S.fx = (T*)h->fx;
-  S.fy = (T*)h->fy;
-  return S;
 }
 
 template <typename T>
@@ -204,25 +158,25 @@ int ensure_capacity(double** buf, int* cap, int n) {
 }
 
 int get_graph(sve_handle* h, int fixed, cudaGraphExec_t* out) {
-  Graph& G = h->graph[fixed ? 1 : 0];
-  if (!G.exec) {
+  cudaGraphExec_t& G = h->graph[fixed ? 1 : 0];
+  if (!G) {
     cudaGraph_t g = nullptr;
     SVE_TRY(cudaStreamBeginCapture(h->capture, cudaStreamCaptureModeThreadLocal));
     for (int s = 0; s < kGraphSteps; ++s) launch_step_any(h, h->capture, fixed);
     cudaError_t e = cudaStreamEndCapture(h->capture, &g);
     if (e != cudaSuccess) return SVE_ERR_CUDA;
-    e = cudaGraphInstantiate(&G.exec, g, 0);
+    e = cudaGraphInstantiate(&G, g, 0);
     cudaGraphDestroy(g);
-    if (e != cudaSuccess) { G.exec = nullptr; return SVE_ERR_CUDA; }
+    if (e != cudaSuccess) { G = nullptr; return SVE_ERR_CUDA; }
   }
-  *out = G.exec;
+  *out = G;
   return SVE_OK;
 }
 
 void drop_graphs(sve_handle* h) {
   for (auto& G : h->graph) {
-    if (G.exec) cudaGraphExecDestroy(G.exec);
-    G.exec = nullptr;
+    if (G) cudaGraphExecDestroy(G);
+    G = nullptr;
   }
 }
 
@@ -436,6 +390,7 @@ int sve_get_dts(sve_handle* h, double* dts, int n) {
 
 void sve_destroy(sve_handle* h) {
   if (!h) return;
+  sve_internal_adjoint_free(h);
   drop_graphs(h);
   cudaStreamSynchronize(h->stream);
   for (auto e : h->events) cudaEventDestroy(e);

@@ -39,6 +39,7 @@ struct DevParams {
   double tau_cr;
   int friction;         // 0 none, 1 Darcy, 2 Strickler
   double fric_c;        // Darcy: f / 8;  Strickler: g / K^2
+  double fric_coef;     // the friction law's coefficient: f (Darcy) or K (Strickler)
   int bc[4];
   double q_in, h_in;
   double kappa_a, beta_min, gamma_z, newton_tol;
@@ -294,29 +295,27 @@ __device__ __forceinline__ bool newton_root(const DevParams& P, const NewtonCons
   return newton_loop(c, L, R, p, e, P.newton_maxit, tol, iters);
 }
 
-// iters receives the number of Newton updates (0 for identical states).
+// Celerities of one interface: the bounds of Eq. (ab) over both states,
+// a scaled by kappa_a, b floored at beta_min a0, and a raised so that
+// K tau_min^2 >= gamma_z |dZ| (the sediment waves can carry the bed jump).
 template <typename T>
-__device__ bool riemann_solve(const DevParams& P, const Cell<T>& L, const Cell<T>& R, T Am[4], T Ap[4], T& smax,
-                              int& iters) {
-  iters = 0;
+__device__ __forceinline__ void celerities(const DevParams& P, const Cell<T>& L, const Cell<T>& R, T& a, T& b) {
   const T g = T(P.g);
-  // celerities: bounds of Eq. (ab), kappa_a, beta_min floor, bed-step bound
   const T a0 = nnmax(L.ca, R.ca);
   const T b0 = nnmax(L.cb, R.cb);
-  T a = T(P.kappa_a) * nnmax(a0, b0);
-  const T b = nnmax(b0, T(P.beta_min) * a0);
+  a = T(P.kappa_a) * nnmax(a0, b0);
+  b = nnmax(b0, T(P.beta_min) * a0);
   const T Hmax = nnmax(L.H, R.H);
-  const T dZ = R.Z - L.Z;
-  const T need = b * b + T(2) * g * T(P.gamma_z) * absbits(dZ) * (Hmax * Hmax);
+  const T need = b * b + T(2) * g * T(P.gamma_z) * absbits(R.Z - L.Z) * (Hmax * Hmax);
   if (a * a < need) a = tsqrt(need);
-  const T lam1 = L.un - a * L.tau;
-  const T lam5 = R.un + a * R.tau;
-  smax = nnmax(absbits(lam1), absbits(lam5));
-#pragma unroll
-  for (int c = 0; c < 4; ++c) { Am[c] = T(0); Ap[c] = T(0); }
-  if (same_bits(L.H, R.H) && same_bits(L.Hn, R.Hn) && same_bits(L.Ht, R.Ht) && same_bits(L.Z, R.Z)) return true;
+}
 
-  NewtonConst<T> c;
+// Constants of the Newton iteration; returns its start p0, the root of the
+// fluid part alone (Suliciu), p = sigma.
+template <typename T>
+__device__ __forceinline__ T newton_setup(const DevParams& P, const Cell<T>& L, const Cell<T>& R, T a, T b,
+                                          NewtonConst<T>& c) {
+  const T g = T(P.g);
   const T rab = T(1) / (a * b);       // one divide for 1/a and 1/b
   const T inv_a = b * rab;
   c.a = a;
@@ -328,23 +327,27 @@ __device__ bool riemann_solve(const DevParams& P, const Cell<T>& L, const Cell<T
   c.D = (R.tau - L.tau) + (R.Pi - L.Pi) * (inv_a * inv_a);
   const T du = R.un - L.un;
   c.C0 = du + a * (L.tau + R.tau);
-  c.dZ = dZ;
+  c.dZ = R.Z - L.Z;
   c.dsig = -(a - b) * c.inv_b;
   c.dN = c.K * c.D * c.dsig;
-  // start: the root of the fluid part alone (Suliciu), p = sigma
-  const T p0 = L.tau + R.tau + du * inv_a;
-  NewtonEval<T> e;
-  const bool ok = newton_root(P, c, L, R, p0, e, iters);
-  if (!ok || !newton_positive(e)) return false;
+  return L.tau + R.tau + du * inv_a;
+}
 
-  // Fluctuations A- = sum_{lam_k < 0} lam_k [U]_k and A+ = sum_{lam_k >= 0}
-  // lam_k [U]_k over the five waves, U = (H, H un, H ut, Z), written with the
-  // jump relations every wave of the fan satisfies (for any p): lam [H] =
-  // [H un], lam [H ut] = [H un ut], lam [H un] = [H un^2 + Pi] + g Hbar [Z]
-  // (Hbar = 2/(tau- + tau+), nonzero [Z] only at the b-waves), lam [Z] at the
-  // b-waves.  With m = the number of waves of negative speed, the minus sums
-  // telescope to (flux of state m) - (flux of L): one divide for H_m and one
-  // per b-wave instead of one per intermediate state.
+// Fluctuations A- = sum_{lam_k < 0} lam_k [U]_k and A+ = sum_{lam_k >= 0}
+// lam_k [U]_k over the five waves of the fan evaluated at e, U = (H, H un,
+// H ut, Z), written with the jump relations every wave of the fan satisfies
+// (for any p): lam [H] = [H un], lam [H ut] = [H un ut], lam [H un] =
+// [H un^2 + Pi] + g Hbar [Z] (Hbar = 2/(tau- + tau+), nonzero [Z] only at the
+// b-waves), lam [Z] at the b-waves.  With m = the number of waves of negative
+// speed, the minus sums telescope to (flux of state m) - (flux of L): one
+// divide for H_m and one per b-wave instead of one per intermediate state.
+template <typename T>
+__device__ __forceinline__ void fan_fluctuations(const DevParams& P, const Cell<T>& L, const Cell<T>& R,
+                                                 const NewtonConst<T>& c, const NewtonEval<T>& e, T Am[4], T Ap[4]) {
+  const T g = T(P.g);
+  const T a = c.a, b = c.b;
+  const T lam1 = L.un - a * L.tau;
+  const T lam5 = R.un + a * R.tau;
   const T us = e.u1 + b * (e.tau2 - e.tau1);
   const T lam2 = e.lam2, lam4 = e.lam4;
   const int m = (int)negative(lam1) + (int)negative(lam2) + (int)negative(us) + (int)negative(lam4) +
@@ -384,6 +387,25 @@ __device__ bool riemann_solve(const DevParams& P, const Cell<T>& L, const Cell<T
   Ap[2] = FvR - Fv;
   Am[3] = (n2 ? lam2 * zj2 : T(0)) + (n4 ? lam4 * zj4 : T(0));
   Ap[3] = (n2 ? T(0) : lam2 * zj2) + (n4 ? T(0) : lam4 * zj4);
+}
+
+// iters receives the number of Newton updates (0 for identical states).
+template <typename T>
+__device__ bool riemann_solve(const DevParams& P, const Cell<T>& L, const Cell<T>& R, T Am[4], T Ap[4], T& smax,
+                              int& iters) {
+  iters = 0;
+  T a, b;
+  celerities(P, L, R, a, b);
+  smax = nnmax(absbits(L.un - a * L.tau), absbits(R.un + a * R.tau));
+#pragma unroll
+  for (int c = 0; c < 4; ++c) { Am[c] = T(0); Ap[c] = T(0); }
+  if (same_bits(L.H, R.H) && same_bits(L.Hn, R.Hn) && same_bits(L.Ht, R.Ht) && same_bits(L.Z, R.Z)) return true;
+  NewtonConst<T> c;
+  const T p0 = newton_setup(P, L, R, a, b, c);
+  NewtonEval<T> e;
+  const bool ok = newton_root(P, c, L, R, p0, e, iters);
+  if (!ok || !newton_positive(e)) return false;
+  fan_fluctuations(P, L, R, c, e, Am, Ap);
   return true;
 }
 
@@ -643,15 +665,14 @@ __global__ void __launch_bounds__(kThreads) interface_kernel(DevParams P, DevSta
 // One interior cell k = j nx + i of one grid: Godunov average in
 // fluctuation form with step dt, friction, checks, projection of the new
 // state and its ghosts.  Returns status bits; (mh, mz) = new (h, z).
+// Convective part of the cell update (before friction): s = U - dt/dx (A+
+// of the left + A- of the right interface) - dt/dy (same in y).
 template <typename T>
-__device__ __forceinline__ int cell_item(const DevParams& P, const DevState<T>& S, long long k, double dt,
-                                         double& mh, double& mz) {
-  const int j = (int)(k / P.nx);
-  const int i = (int)(k - (long long)j * P.nx);
-  const long long e = ext_index(P, i, j);
+__device__ __forceinline__ void convect_cell(const DevParams& P, const DevState<T>& S, int i, int j, long long e,
+                                             double dt, T s[4]) {
   const T dtx = T(dt * P.inv_dx);
   const long long kx = (long long)j * (P.nx + 1) + i;
-  T s[4] = {S.h[e], S.hu[e], S.hv[e], S.z[e]};
+  s[0] = S.h[e]; s[1] = S.hu[e]; s[2] = S.hv[e]; s[3] = S.z[e];
   T ax[4];
 #pragma unroll
   for (int c = 0; c < 4; ++c) ax[c] = S.fx[(4 + c) * P.nfx + kx] + S.fx[c * P.nfx + kx + 1];
@@ -671,6 +692,16 @@ __device__ __forceinline__ int cell_item(const DevParams& P, const DevState<T>& 
     s[1] = s[1] - dtx * ax[1];
     s[3] = s[3] - dtx * ax[3];
   }
+}
+
+template <typename T>
+__device__ __forceinline__ int cell_item(const DevParams& P, const DevState<T>& S, long long k, double dt,
+                                         double& mh, double& mz) {
+  const int j = (int)(k / P.nx);
+  const int i = (int)(k - (long long)j * P.nx);
+  const long long e = ext_index(P, i, j);
+  T s[4];
+  convect_cell(P, S, i, j, e, dt, s);
   const T tau = T(1) / s[0];
   // semi-implicit friction: q <- q / (1 + dt C(h) |q|),
   // C = f / (8 h^2) (Darcy) or g / (K^2 h^(7/3)) (Strickler)

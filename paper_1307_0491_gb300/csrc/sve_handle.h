@@ -1,0 +1,56 @@
+// sve_handle.h -- the handle of libsve (private to the library's sources).
+#pragma once
+#include <cuda_runtime.h>
+
+#include <vector>
+
+#include "../../include/sve.h"
+#include "sve_device.cuh"
+
+struct sve_adjoint_rec;  // recorded forward run (sve_adjoint.cu)
+
+struct sve_handle {
+  sve_config cfg;
+  sve::DevParams P;
+  int device = 0;
+  cudaStream_t stream = nullptr;   // user stream (nullptr = legacy default)
+  cudaStream_t capture = nullptr;  // private stream used only to capture graphs
+  bool has_state = false;
+  size_t elem = 8;                 // bytes per state element
+  long long next = 0;              // padded cells
+  void* fields[13] = {};           // h hu hv z tau u v pi omx omy ca cbx cby
+  void* fx = nullptr;
+  void* fy = nullptr;
+  double* spart = nullptr;
+  double* mpart = nullptr;
+  sve::DevScalars* sc = nullptr;
+  double* dtlog = nullptr;
+  int dtlog_cap = 0;
+  double* fixed = nullptr;
+  int fixed_cap = 0;
+  int nb_iface = 0, nb_cell = 0;
+  cudaGraphExec_t graph[2] = {nullptr, nullptr};  // [fixed]
+  long long last_launches = 0;
+  int last_steps = 0;
+  // kernel timing (sve_profile): 3 events per step, read back lazily
+  bool profiling = false;
+  std::vector<cudaEvent_t> events;
+  size_t events_used = 0;
+  double prof_ms[2] = {0.0, 0.0};
+  long long prof_launches[2] = {0, 0};
+  sve_adjoint_rec* adj = nullptr;
+};
+
+// The handle's device arrays as a DevState of precision T.
+template <typename T>
+inline sve::DevState<T> state_of(const sve_handle* h) {
+  sve::DevState<T> S;
+  T** f[13] = {&S.h, &S.hu, &S.hv, &S.z, &S.tau, &S.u, &S.v, &S.pi, &S.omx, &S.omy, &S.ca, &S.cbx, &S.cby};
+  for (int k = 0; k < 13; ++k) *f[k] = (T*)h->fields[k];
+  S.fx = (T*)h->fx;
+  S.fy = (T*)h->fy;
+  return S;
+}
+
+// Implemented in sve_adjoint.cu: releases the recorded forward run.
+__attribute__((visibility("hidden"))) void sve_internal_adjoint_free(sve_handle* h);

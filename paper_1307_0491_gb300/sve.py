@@ -34,7 +34,8 @@ EXPORTS = ("sve_config_default", "sve_create", "sve_set_stream", "sve_set_state"
            "sve_step_async", "sve_sync", "sve_profile", "sve_profile_read", "sve_get_counters", "sve_step_noalloc",
            "sve_batch_create", "sve_batch_set_stream", "sve_batch_set_state", "sve_batch_step",
            "sve_batch_step_async", "sve_batch_get_state", "sve_batch_get_diag", "sve_batch_get_counters",
-           "sve_batch_autotune", "sve_batch_set_schedule", "sve_batch_last_launch_count", "sve_batch_destroy")
+           "sve_batch_autotune", "sve_batch_set_schedule", "sve_batch_last_launch_count", "sve_batch_destroy",
+           "sve_record_forward", "sve_adjoint")
 
 
 class sve_config(ctypes.Structure):
@@ -103,6 +104,8 @@ def load() -> ctypes.CDLL:
         "sve_batch_set_schedule": ([vp, ip, ip], ip),
         "sve_batch_last_launch_count": ([vp], ctypes.c_longlong),
         "sve_batch_destroy": ([vp], None),
+        "sve_record_forward": ([vp, ip, ip], ip),
+        "sve_adjoint": ([vp, vp, vp, vp, vp, ip, vp, vp, vp, vp, dp], ip),
     }
     for name, (args, res) in sig.items():
         fn = getattr(L, name)
@@ -265,6 +268,18 @@ def sve_batch_destroy(b) -> None:
     load().sve_batch_destroy(b)
 
 
+def sve_record_forward(h, nsteps: int, checkpoint_every: int = 0) -> int:
+    return load().sve_record_forward(h, int(nsteps), int(checkpoint_every))
+
+
+def sve_adjoint(h, lam: tuple, where: int, grads: tuple) -> tuple[int, list]:
+    """lam = (lam_h, lam_hu, lam_hv, lam_z) pointers (or None); grads = four
+    output pointers (or None).  Returns (code, [dL/dA_g, dL/dm_g, dL/dK])."""
+    g = (ctypes.c_double * 3)()
+    rc = load().sve_adjoint(h, *lam, where, *grads, g)
+    return rc, list(g)
+
+
 # ---- convenience wrapper ---------------------------------------------------
 
 class SveError(RuntimeError):
@@ -399,6 +414,30 @@ class Solver:
         rc, steps, its = sve_get_counters(self.h)
         _check(rc, "sve_get_counters")
         return dict(steps=steps, newton_iters=its)
+
+    def record_forward(self, nsteps: int, checkpoint_every: int = 0) -> None:
+        _check(sve_record_forward(self.h, nsteps, checkpoint_every), "sve_record_forward")
+
+    def adjoint(self, lam_h=None, lam_hu=None, lam_hv=None, lam_z=None) -> tuple[dict, list]:
+        """Host cotangents of the final state -> (dL/dU^0 as numpy arrays,
+        [dL/dA_g, dL/dm_g, dL/dK])."""
+        shp = self._shape()
+        lam = []
+        keep = []
+        for x in (lam_h, lam_hu, lam_hv, lam_z):
+            if x is None:
+                lam.append(None)
+            else:
+                a = np.ascontiguousarray(np.asarray(x, dtype=np.float64).reshape(shp))
+                keep.append(a)
+                lam.append(a.ctypes.data)
+        out = {k: np.zeros(shp) for k in ("h", "hu", "hv", "z")}
+        ptrs = tuple(out[k].ctypes.data if (k != "hv" or self.dim == 2) else None for k in ("h", "hu", "hv", "z"))
+        rc, gp = sve_adjoint(self.h, tuple(lam), SVE_HOST, ptrs)
+        _check(rc, "sve_adjoint")
+        if self.dim == 1:
+            out["hv"] = None
+        return out, gp
 
 
 class Batch:
