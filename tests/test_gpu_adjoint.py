@@ -117,3 +117,37 @@ def test_autograd_function_matches_adjoint():
     s.close()
     assert np.allclose(z0.grad.cpu().numpy(), grads["z"], rtol=1e-12, atol=1e-15)
     assert np.allclose([A.grad.item(), m.grad.item(), K.grad.item()], gp, rtol=1e-12)
+
+
+@pytest.mark.parametrize("bc,friction", [
+    (("inflow_q", "free", "wall", "free"), "strickler"),
+    (("periodic", "periodic", "periodic", "periodic"), "darcy"),
+])
+def test_gpu_adjoint_equals_oracle_adjoint(bc, friction):
+    """GPU adjoint against the oracle-side adjoint (autograd through the
+    PyTorch-CPU restatement of the step), each from its own forward run and
+    its own CFL time steps: 1e-10 relative."""
+    pytest.importorskip("torch")
+    import oracle
+    from oracle import adjoint as OA
+
+    w, target = case(bc, friction)
+    p = w["params"]
+    n = 20
+    s = sve.Solver(p, "fp64")
+    s.set_state(w["h"], w["hu"], w["hv"], w["z"])
+    s.record_forward(n, 6)
+    fin = s.get_state()
+    grads, gp = s.adjoint(lam_z=2.0 * (fin["z"] - target))
+    s.close()
+    ref = oracle.get().run(oracle.Params.from_workload(p), n, w["h"], w["hu"], w["hv"], w["z"])
+    og = OA.gradients(p, w, ref["dts"], 2.0 * (np.asarray(ref["z"]) - target))
+    # relative L-infinity over the gradient with respect to the initial state,
+    # and over the parameter gradient (A_g, m_g, friction coefficient)
+    scale = max(np.max(np.abs(og["z"])), np.max(np.abs(og["h"])))
+    errs = {f: float(np.max(np.abs(grads[f] - og[f])) / scale) for f in ("z", "h")}
+    pscale = max(abs(b) for b in og["params"])
+    perr = [abs(a - b) / pscale for a, b in zip(gp, og["params"])]
+    print("adjoint vs oracle adjoint:", errs, perr)
+    assert max(errs.values()) <= 1e-10, errs
+    assert max(perr) <= 1e-10, (gp, og["params"])
