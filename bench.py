@@ -215,6 +215,52 @@ def run_batched(args, sve, W, torch, precision: str, plain_value: float):
             "l2": "working set larger than L2 (no flush)"}
 
 
+def run_adjoint(args, sve, W, torch):
+    """Gradient of ||z_b(T) - z_target||^2 with respect to A_g, m_g, K and the
+    initial bed on the adjoint config (2048 x 1024, periodic), over a bounded
+    number of steps: forward record + reverse sweep, against the plain
+    forward step on the same grid."""
+    w = W.adjoint_dune()
+    tgt = W.adjoint_dune(A_g=1.1e-3, m_g=3.1, K_st=36.0, shift=5.0)
+    p = w["params"]
+    cells = p["nx"] * p["ny"]
+    n = args.adjoint_steps
+    # target bed: a forward run of the perturbed setup
+    st = sve.Solver(tgt["params"], "fp64")
+    st.set_state(tgt["h"], tgt["hu"], tgt["hv"], tgt["z"])
+    st.step(n)
+    z_target = st.get_state()["z"]
+    st.close()
+    s = sve.Solver(p, "fp64")
+    s.set_state(w["h"], w["hu"], w["hv"], w["z"])
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    s.step(n)                                   # plain forward on the same grid
+    torch.cuda.synchronize()
+    t_plain = time.perf_counter() - t0
+    s.set_state(w["h"], w["hu"], w["hv"], w["z"])
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    s.record_forward(n, 0)
+    fin = s.get_state()
+    t1 = time.perf_counter()
+    grads, gp = s.adjoint(lam_z=2.0 * (fin["z"] - z_target))
+    torch.cuda.synchronize()
+    t2 = time.perf_counter()
+    s.close()
+    plain = cells * n / t_plain
+    grad_rate = cells * n / (t2 - t0)
+    return {"workload": f"adjoint config {p['nx']}x{p['ny']} periodic, dune physics in 2D, Grass A_g=1e-3 m_g=3, "
+                        f"Strickler K=40; misfit to a (1.1 A_g, m_g=3.1, K=36, +5 m) run",
+            "steps": n, "checkpoint_every": int(math.ceil(math.sqrt(n))),
+            "value": grad_rate, "unit": "cell-updates/s (forward record + reverse sweep)",
+            "plain_forward_value": plain, "vs_plain": grad_rate / plain,
+            "forward_record_s": t1 - t0, "reverse_s": t2 - t1,
+            "grad_params": {"A_g": gp[0], "m_g": gp[1], "K": gp[2]},
+            "grad_z0_max_abs": float(np.max(np.abs(grads["z"]))), "dtype": "f64",
+            "time": "wall clock around the C-ABI calls (host-synchronous)"}
+
+
 def run_ours(args, world, rank, local):
     import torch
 
@@ -333,8 +379,10 @@ def run_ours(args, world, rank, local):
         }
         if not args.no_batch:
             line["batched"] = [run_batched(args, sve, W, torch, "fp64", value)]
-            if args.batch_fp32:
+            if not args.no_batch_fp32:
                 line["batched"].append(run_batched(args, sve, W, torch, "fp32", None))
+        if not args.no_adjoint:
+            line["adjoint"] = run_adjoint(args, sve, W, torch)
         if world == 1 and not args.no_cpu_baseline:
             rate, nsteps, secs = cpu_oracle_rate(w)
             line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
@@ -359,7 +407,9 @@ def main():
     ap.add_argument("--batch-runs", type=int, default=256)
     ap.add_argument("--batch-steps", type=int, default=10)
     ap.add_argument("--batch-spinup", type=int, default=100)
-    ap.add_argument("--batch-fp32", action="store_true", help="also time the FP32-state ensemble")
+    ap.add_argument("--no-batch-fp32", action="store_true", help="skip the FP32-state ensemble")
+    ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint measurement")
+    ap.add_argument("--adjoint-steps", type=int, default=100)
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -19,6 +19,8 @@ Recipes:
     + Darcy-Weisbach.
   * ``ensemble``    -- many independent ``dune2d``-type runs of uneven sizes
     and parameters.
+  * ``adjoint_dune`` -- the dune physics in 2D on a periodic channel, the
+    setting of the gradient (adjoint) runs.
   * ``paper_dune1d``, ``paper_antidune1d``, ``paper_bump2d`` -- the paper's
     own setups (Secs. 5.1--5.3) at a chosen resolution.
   * ``lake_at_rest``, ``thin_dam_break`` -- stress and property cases.
@@ -123,6 +125,28 @@ def ensemble(nruns: int = 256, seed: int = 0, nsteps: int = 1000, nx_range=(128,
                      amp=(amp, amp))
         runs.append(run)
     return runs
+
+
+def adjoint_dune(nx: int = 2048, ny: int = 1024, nsteps: int = 4000, A_g: float = 1e-3, m_g: float = 3.0,
+                 K_st: float = 40.0, shift: float = 0.0) -> dict:
+    """Adjoint config: the 1D dune physics of ``dune1d`` in 2D on a periodic
+    1000 x 500 m channel, z = 0.1 + sin^2(pi (x - 300 - shift)/200)
+    sin^2(pi (y - 150)/200) on [300, 500] x [150, 350] (shifted in x by
+    ``shift``), h = 2 - z, hu = 0.5, hv = 0, Grass A_g, m_g, Strickler K_st.
+    The target bed of the misfit comes from a run with (1.1 A_g, m_g = 3.1,
+    K_st = 36) and shift = 5 m."""
+    lx, ly = 1000.0, 500.0
+    x = _centers(nx, lx)[None, :] - shift
+    y = _centers(ny, ly)[:, None]
+    inside = (x >= 300.0) & (x <= 500.0) & (y >= 150.0) & (y <= 350.0)
+    z = np.where(inside, 0.1 + np.sin(np.pi * (x - 300.0) / 200.0) ** 2 * np.sin(np.pi * (y - 150.0) / 200.0) ** 2,
+                 0.1)
+    h = 2.0 - z
+    hu = np.full((ny, nx), 0.5)
+    hv = np.zeros((ny, nx))
+    params = base_params(dim=2, nx=nx, ny=ny, lx=lx, ly=ly, A_g=A_g, m_g=m_g, friction="strickler", K_st=K_st,
+                         bc=("periodic",) * 4)
+    return dict(params=params, h=h, hu=hu, hv=hv, z=z, nsteps=nsteps)
 
 
 def paper_dune1d(nx: int = 2000, A_g: float = 1.0, m_g: float = 3.0) -> dict:
