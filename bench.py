@@ -45,9 +45,26 @@ L2_FLUSH_BYTES = 256 << 20
 IFACE_TRAFFIC = {"sha256": "ed773ffc1d487e72", "bytes": 92_883_712}
 
 
-def workload_desc(nx, ny):
-    return (f"2D dune FP64 {nx}x{ny} (1000x500 m, Gaussian dune, Grass m_g=3 A_g=1e-3, Strickler K=40, "
-            f"inflow q=0.5 / free outflow)")
+def workload_desc(nx, ny, workload="dune2d", precision="fp64"):
+    if workload == "antidune2d":
+        return (f"2D antidune {precision.upper()} {nx}x{ny} (24x12 m, bed N(0, 1 cm), h=0.5 m, Fr~U[1.2,1.5], "
+                f"MPM + Darcy f=0.02, supercritical inflow / free)")
+    return (f"2D dune {precision.upper()} {nx}x{ny} (1000x500 m, Gaussian dune, Grass m_g=3 A_g=1e-3, "
+            f"Strickler K=40, inflow q=0.5 / free outflow)")
+
+
+def make_workload(args, W, seed=0):
+    """The timed workload: the 2D dune (default, FP64) or the antidune (its
+    FP32 and FP64 forms); --nx/--ny shrink it (profiling captures)."""
+    if args.workload == "antidune2d":
+        kw = {}
+        if args.nx:
+            kw.update(nx=args.nx, ny=args.ny or args.nx // 2)
+        return W.antidune2d(seed=seed, **kw)
+    kw = {}
+    if args.nx:
+        kw.update(nx=args.nx, ny=args.ny or args.nx // 2)
+    return W.dune2d(seed=seed, **kw)
 
 
 def iface_traffic():
@@ -152,7 +169,7 @@ def run_reference(args, world, rank):
     import oracle
     from paper_1307_0491_gb300 import workloads as W
 
-    w = W.dune2d()
+    w = make_workload(args, W)
     nx, ny = w["params"]["nx"], w["params"]["ny"]
     o = oracle.get()
     P = oracle.Params.from_workload(w["params"])
@@ -170,7 +187,8 @@ def run_reference(args, world, rank):
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": secs / args.steps * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": workload_desc(nx, ny), "nx": nx, "ny": ny, "precision": "fp64"},
+        "config": {"workload": workload_desc(nx, ny, args.workload, args.precision), "nx": nx, "ny": ny,
+                   "precision": args.precision},
         "cpu_baseline": {"kind": "oracle", "cores": 1, "value": value, "unit": UNIT,
                          "sample": f"full {nx}x{ny} grid, {args.steps} steps after {args.warmup} warm-up steps, "
                                    f"single-threaded C oracle (-O2, no FMA contraction)"},
@@ -274,11 +292,12 @@ def run_ours(args, world, rank, local):
     from paper_1307_0491_gb300 import workloads as W
 
     B.build()
-    w = W.dune2d(seed=rank)
+    w = make_workload(args, W, seed=rank)
     nx, ny = w["params"]["nx"], w["params"]["ny"]
     cells = nx * ny
     stream = torch.cuda.current_stream()
-    solver = sve.Solver(w["params"], "fp64", stream=stream.cuda_stream)
+    prec = args.precision
+    solver = sve.Solver(w["params"], prec, stream=stream.cuda_stream)
     solver.set_state(w["h"], w["hu"], w["hv"], w["z"])
     # spin-up: the first ~200 steps of the run are cheaper (far from the dune
     # the neighbours are still identical and skip their solves); advance into
@@ -329,18 +348,30 @@ def run_ours(args, world, rank, local):
     achieved = n_iface * flop_iface / (iface_ms * 1e-3)
     pk = peaks()
     hbm = pk.get("hbm_gbs", 6800.3)
+    bytes_per_cell = BYTES_PER_CELL_FP64 if prec == "fp64" else BYTES_PER_CELL_FP64 // 2
+    if prec == "fp32":
+        # FP32 state: the step against the HBM roofline (algorithmic 32 B per cell-update)
+        step_gbs = bytes_per_cell * cells / (ms_per_step * 1e-3) / 1e9
+        roofline_fp32 = {"bound": "hbm", "achieved": step_gbs, "peak": hbm, "unit": "GB/s", "frac": step_gbs / hbm,
+                         "traffic": None, "kernel": "whole step (FP32 state)", "iface_ms": iface_ms,
+                         "cell_ms": cell_ms, "newton_updates_per_solve": updates,
+                         "peak_source": "MEASURED_PEAKS.json hbm_gbs (copy)"}
     roofline = {"bound": "alu", "achieved": achieved / 1e12, "peak": FP64_PEAK_FLOPS / 1e12, "unit": "TFLOP/s",
-                "frac": achieved / FP64_PEAK_FLOPS, "traffic": iface_traffic(),
+                "frac": achieved / FP64_PEAK_FLOPS,
+                "traffic": iface_traffic() if (prec == "fp64" and args.workload == "dune2d" and not args.nx) else None,
                 "kernel": "interface_kernel<double>", "peak_source": "152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz "
                 "(GB300 FP64 nominal 1.25 TFLOP/s); a measured DFMA loop gave 1.19 TFLOP/s",
                 "flop_per_interface": flop_iface, "newton_updates_per_solve": updates,
                 "iface_ms": iface_ms, "cell_ms": cell_ms,
-                "hbm_frac_of_step": (BYTES_PER_CELL_FP64 * cells / (ms_per_step * 1e-3)) / (hbm * 1e9),
+                "hbm_frac_of_step": (bytes_per_cell * cells / (ms_per_step * 1e-3)) / (hbm * 1e9),
                 "hbm_peak_gbs": hbm}
+    if prec == "fp32":
+        roofline = roofline_fp32
 
     # end to end through the C ABI from pinned host memory
     e2e_steps = min(args.steps, 10)
-    host_in = {k: torch.from_numpy(np.ascontiguousarray(w[k])).pin_memory() for k in ("h", "hu", "hv", "z")}
+    npdt = np.float64 if prec == "fp64" else np.float32
+    host_in = {k: torch.from_numpy(np.ascontiguousarray(w[k], dtype=npdt)).pin_memory() for k in ("h", "hu", "hv", "z")}
     host_out = {k: torch.empty_like(host_in[k]).pin_memory() for k in host_in}
     ptr = {k: host_in[k].data_ptr() for k in host_in}
     optr = {k: host_out[k].data_ptr() for k in host_out}
@@ -357,7 +388,7 @@ def run_ours(args, world, rank, local):
         t = torch.tensor([e2e_s], device="cuda", dtype=torch.float64)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         e2e_s = float(t.item())
-    io_bytes = 4 * 8 * cells
+    io_bytes = 4 * (8 if prec == "fp64" else 4) * cells
     e2e = {"value": world * cells * e2e_steps / e2e_s, "unit": UNIT, "h2d_bytes_per_step": io_bytes,
            "d2h_bytes_per_step": io_bytes, "steps": e2e_steps}
     solver.close()
@@ -367,8 +398,9 @@ def run_ours(args, world, rank, local):
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": workload_desc(nx, ny), "nx": nx, "ny": ny, "precision": "fp64",
+            "vs_baseline": None, "dtype": "f64" if prec == "fp64" else "f32 (FP64 dt, t, mass sums)",
+            "data": "synthetic",
+            "config": {"workload": workload_desc(nx, ny, args.workload, prec), "nx": nx, "ny": ny, "precision": prec,
                        "timed_steps_of_run": f"{args.spinup + args.warmup}..{args.spinup + args.warmup + args.steps - 1}",
                        "per_rank": "independent replica (seed = rank)",
                        "l2": f"flushed between timed steps ({L2_FLUSH_BYTES >> 20} MiB write outside the events)"},
@@ -409,6 +441,10 @@ def main():
     ap.add_argument("--batch-spinup", type=int, default=100)
     ap.add_argument("--no-batch-fp32", action="store_true", help="skip the FP32-state ensemble")
     ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint measurement")
+    ap.add_argument("--workload", choices=["dune2d", "antidune2d"], default="dune2d")
+    ap.add_argument("--precision", choices=["fp64", "fp32"], default="fp64")
+    ap.add_argument("--nx", type=int, default=0, help="grid override (profiling captures)")
+    ap.add_argument("--ny", type=int, default=0)
     ap.add_argument("--adjoint-steps", type=int, default=100)
     args = ap.parse_args()
     if args.warmup < 3:
