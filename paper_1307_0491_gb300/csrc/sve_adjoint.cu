@@ -128,11 +128,13 @@ __device__ __forceinline__ void jac_pass(const DevParams& P, const double u[8], 
   }
 }
 
-// Deterministic sum of per-block partials (n per block) into acc[0..n-1] by
-// the last block of the launch.
+// Deterministic sum of per-block partials (nper <= 2 per block) into
+// acc[0..nper-1] by the last block of the launch: thread t adds blocks t,
+// t + NT, ... in order (L2 loads, several in flight), then a fixed tree.
 template <int NT>
 __device__ __forceinline__ void finish_partials(const double* part, int nper, double* acc, unsigned int* done) {
   __shared__ bool last;
+  __shared__ double sh[2 * (NT / 32)];
   if (threadIdx.x == 0) {
     __threadfence();
     last = atomicAdd(done, 1u) == gridDim.x - 1;
@@ -140,13 +142,16 @@ __device__ __forceinline__ void finish_partials(const double* part, int nper, do
   __syncthreads();
   if (!last) return;
   __threadfence();
+  double s0 = 0.0, s1 = 0.0;
+#pragma unroll 4
+  for (unsigned b = threadIdx.x; b < gridDim.x; b += NT) {
+    s0 += __ldcg(part + (size_t)nper * b);
+    if (nper > 1) s1 += __ldcg(part + (size_t)nper * b + 1);
+  }
+  sve::block_sum2<NT>(s0, s1, sh);
   if (threadIdx.x == 0) {
-    const volatile double* vp = part;
-    for (int q = 0; q < nper; ++q) {
-      double s = 0.0;
-      for (unsigned b = 0; b < gridDim.x; ++b) s += vp[nper * b + q];
-      acc[q] += s;
-    }
+    acc[0] += s0;
+    if (nper > 1) acc[1] += s1;
     *done = 0u;
   }
 }

@@ -81,12 +81,16 @@ __global__ void __launch_bounds__(NT) batch_interface_kernel(const BatchRun<T>* 
   __syncthreads();
   if (!last) return;
   __threadfence();
-  const volatile double* vp = spart;
-  double mx = 0.0, my = 0.0;
+  // L2 loads after the fence; integer max of the bit patterns of the
+  // non-negative speeds
+  const long long* bp = reinterpret_cast<const long long*>(spart) + 2 * (size_t)R.part_if;
+  long long bx = 0, by = 0;
+#pragma unroll 4
   for (int b = threadIdx.x; b < R.ntile_if; b += NT) {
-    mx = fmax(mx, vp[2 * (R.part_if + b)]);
-    my = fmax(my, vp[2 * (R.part_if + b) + 1]);
+    bx = max(bx, __ldcg(bp + 2 * b));
+    by = max(by, __ldcg(bp + 2 * b + 1));
   }
+  double mx = __longlong_as_double(bx), my = __longlong_as_double(by);
   mx = sve::block_max<NT>(mx, sh);
   my = sve::block_max<NT>(my, sh);
   if (threadIdx.x == 0) {

@@ -70,8 +70,18 @@ struct DevState {
 
 template <typename T> __device__ __forceinline__ T tmax(T a, T b) { return a > b ? a : b; }
 template <typename T> __device__ __forceinline__ T tabs(T a) { return a < T(0) ? -a : a; }
+// Quotients and square roots: IEEE in FP64; in the FP32-state path the
+// hardware approximations (div.approx, sqrt.approx: ~2 ulp), whose error is
+// far below what FP32 state storage already costs (the FP32 path is checked
+// against the FP64 oracle with stated bounds).
 __device__ __forceinline__ double tsqrt(double x) { return sqrt(x); }
-__device__ __forceinline__ float tsqrt(float x) { return sqrtf(x); }
+__device__ __forceinline__ float tsqrt(float x) {
+  float y;
+  asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ __forceinline__ double tdiv(double a, double b) { return a / b; }
+__device__ __forceinline__ float tdiv(float a, float b) { return __fdividef(a, b); }
 __device__ __forceinline__ double tcbrt(double x) { return cbrt(x); }
 __device__ __forceinline__ float tcbrt(float x) { return cbrtf(x); }
 __device__ __forceinline__ double tpow(double x, double y) { return pow(x, y); }
@@ -152,7 +162,7 @@ __device__ __forceinline__ void closure(const DevParams& P, T H, T un, T ut, T& 
     T pm1, second;
     switch (P.m_int) {
       case 1: pm1 = T(1); second = T(0); break;
-      case 2: { T sp = tsqrt(speed2); pm1 = sp; second = (un * un) / sp; } break;
+      case 2: { T sp = tsqrt(speed2); pm1 = sp; second = tdiv(un * un, sp); } break;
       case 3: pm1 = speed2; second = T(2) * (un * un); break;
       case 4: { T sp = tsqrt(speed2); pm1 = speed2 * sp; second = T(3) * (un * un) * sp; } break;
       default: {
@@ -175,7 +185,7 @@ __device__ __forceinline__ void closure(const DevParams& P, T H, T un, T ut, T& 
     return;
   }
   const T sp = tsqrt(speed2);
-  const T isp = T(1) / sp;
+  const T isp = tdiv(T(1), sp);
   const T sth = tsqrt(theta);
   const T th32 = theta * sth;
   const T C = T(P.mpm_C);
@@ -224,7 +234,7 @@ __device__ __forceinline__ void newton_eval(T p, const NewtonConst<T>& c, const 
   e.tau2 = T(0.5) * (sigma - c.D);                  // from Pi continuity
   e.tau3 = T(0.5) * (sigma + c.D);
   const T N = c.dZ + c.K * c.D * sigma;
-  e.ip = T(1) / p;
+  e.ip = tdiv(T(1), p);
   e.m = -N * e.ip * c.inv_K;                        // from Z* continuity
   e.tau1 = T(0.5) * (p + e.m);
   e.tau4 = T(0.5) * (p - e.m);
@@ -262,7 +272,7 @@ template <typename T>
 __device__ __forceinline__ bool newton_loop(const NewtonConst<T>& c, const Cell<T>& L, const Cell<T>& R, T& p,
                                             NewtonEval<T>& e, int maxit, T tol, int& iters) {
   for (int it = 0; it < maxit; ++it) {
-    T step = -e.F / newton_deriv(c, e);
+    T step = tdiv(-e.F, newton_deriv(c, e));
     if (!tfinite(step)) return false;
     NewtonEval<T> tr;
     bool pos = false;
@@ -283,13 +293,19 @@ __device__ __forceinline__ bool newton_loop(const NewtonConst<T>& c, const Cell<
 template <typename T> __device__ __forceinline__ T eps_of();
 template <> __device__ __forceinline__ double eps_of<double>() { return 2.220446049250313e-16; }
 template <> __device__ __forceinline__ float eps_of<float>() { return 1.1920929e-7f; }
+// Smallest usable relative Newton step: 16 eps in FP64; 64 eps (7.6e-6) in
+// FP32, where the iterates' rounding noise reaches a few eps (quadratic
+// convergence leaves ~25 (7.6e-6)^2 ~ 1e-9 behind, far below FP32 rounding).
+template <typename T> __device__ __forceinline__ T newton_floor();
+template <> __device__ __forceinline__ double newton_floor<double>() { return 16.0 * 2.220446049250313e-16; }
+template <> __device__ __forceinline__ float newton_floor<float>() { return 64.0f * 1.1920929e-7f; }
 
 // Root of F for one interface, from p0 (the root of the fluid part alone).
 // Returns false if no root with positive tau_k was reached.
 template <typename T>
 __device__ __forceinline__ bool newton_root(const DevParams& P, const NewtonConst<T>& c, const Cell<T>& L,
                                             const Cell<T>& R, T p0, NewtonEval<T>& e, int& iters) {
-  const T tol = tmax(T(P.newton_tol), T(16) * eps_of<T>());
+  const T tol = tmax(T(P.newton_tol), newton_floor<T>());
   T p = p0;
   newton_eval(p, c, L, R, e);
   return newton_loop(c, L, R, p, e, P.newton_maxit, tol, iters);
@@ -316,14 +332,14 @@ template <typename T>
 __device__ __forceinline__ T newton_setup(const DevParams& P, const Cell<T>& L, const Cell<T>& R, T a, T b,
                                           NewtonConst<T>& c) {
   const T g = T(P.g);
-  const T rab = T(1) / (a * b);       // one divide for 1/a and 1/b
+  const T rab = tdiv(T(1), a * b);       // one divide for 1/a and 1/b
   const T inv_a = b * rab;
   c.a = a;
   c.b = b;
   c.inv_b = a * rab;
   const T a2mb2 = a * a - b * b;
   c.K = a2mb2 * T(P.inv_2g);
-  c.inv_K = T(2) * g / a2mb2;
+  c.inv_K = tdiv(T(2) * g, a2mb2);
   c.D = (R.tau - L.tau) + (R.Pi - L.Pi) * (inv_a * inv_a);
   const T du = R.un - L.un;
   c.C0 = du + a * (L.tau + R.tau);
@@ -369,15 +385,15 @@ __device__ __forceinline__ void fan_fluctuations(const DevParams& P, const Cell<
     const T uk = m == 1 ? e.u1 : (m == 4 ? e.u4 : us);
     const T vk = left ? L.ut : R.ut;
     const T Pk = left ? L.Pi + a2 * (L.tau - tk) : R.Pi + a2 * (R.tau - tk);
-    const T Hk = T(1) / tk;
+    const T Hk = tdiv(T(1), tk);
     Fh = Hk * uk;
     Fq = Fh * uk + Pk;
     Fv = Fh * vk;
   }
   // b-waves: bed jumps and the non-conservative source g Hbar [Z]
   const T zj2 = e.Zs - L.Z, zj4 = R.Z - e.Zs;
-  const T S2 = T(2) * g * zj2 / (e.tau1 + e.tau2);
-  const T S4 = T(2) * g * zj4 / (e.tau3 + e.tau4);
+  const T S2 = tdiv(T(2) * g * zj2, e.tau1 + e.tau2);
+  const T S4 = tdiv(T(2) * g * zj4, e.tau3 + e.tau4);
   const bool n2 = negative(lam2), n4 = negative(lam4);
   Am[0] = Fh - FhL;
   Ap[0] = FhR - Fh;
@@ -458,21 +474,21 @@ __device__ __forceinline__ void write_ghosts(const DevParams& P, const DevState<
   const bool perx = P.bc[0] == GHOST_PERIODIC;
   if ((!perx && i == 0) || (perx && i == P.nx - 1)) {
     ghost_state(P, 0, s, gs);
-    store_cell(P, S, ext_index(P, -1, j), gs, T(1) / gs[0]);
+    store_cell(P, S, ext_index(P, -1, j), gs, tdiv(T(1), gs[0]));
   }
   if ((!perx && i == P.nx - 1) || (perx && i == 0)) {
     ghost_state(P, 1, s, gs);
-    store_cell(P, S, ext_index(P, P.nx, j), gs, T(1) / gs[0]);
+    store_cell(P, S, ext_index(P, P.nx, j), gs, tdiv(T(1), gs[0]));
   }
   if (P.dim == 2) {
     const bool pery = P.bc[2] == GHOST_PERIODIC;
     if ((!pery && j == 0) || (pery && j == P.ny - 1)) {
       ghost_state(P, 2, s, gs);
-      store_cell(P, S, ext_index(P, i, -1), gs, T(1) / gs[0]);
+      store_cell(P, S, ext_index(P, i, -1), gs, tdiv(T(1), gs[0]));
     }
     if ((!pery && j == P.ny - 1) || (pery && j == 0)) {
       ghost_state(P, 3, s, gs);
-      store_cell(P, S, ext_index(P, i, P.ny), gs, T(1) / gs[0]);
+      store_cell(P, S, ext_index(P, i, P.ny), gs, tdiv(T(1), gs[0]));
     }
   }
 }
@@ -525,10 +541,11 @@ __device__ __forceinline__ void block_sum2(double& a, double& b, double* sh) {
 template <int NT>
 __device__ __forceinline__ void reduce_partials(const double* mpart, unsigned nblocks, double& a, double& b,
                                                 double* sh) {
-  const volatile double* vp = mpart;
   a = 0.0;
   b = 0.0;
-  for (unsigned k = threadIdx.x; k < nblocks; k += NT) { a += vp[2 * k]; b += vp[2 * k + 1]; }
+  // L2 loads (not L1, which is not coherent across SMs), several in flight
+#pragma unroll 4
+  for (unsigned k = threadIdx.x; k < nblocks; k += NT) { a += __ldcg(mpart + 2 * k); b += __ldcg(mpart + 2 * k + 1); }
   block_sum2<NT>(a, b, sh);
 }
 
@@ -639,12 +656,16 @@ __global__ void __launch_bounds__(kThreads) interface_kernel(DevParams P, DevSta
   }
   __syncthreads();
   if (!last) return;
-  // last block: reduce the partials (volatile reads after the fence)
+  // last block: reduce the partials (L2 loads after the fence; integer max
+  // of the bit patterns of the non-negative speeds)
   __threadfence();
-  const volatile double* vp = spart;
-  double sx = 0.0, sy = 0.0;
-  for (int b = threadIdx.x; b < P.nbx; b += kThreads) sx = fmax(sx, vp[b]);
-  for (int b = P.nbx + threadIdx.x; b < P.nbx + P.nby; b += kThreads) sy = fmax(sy, vp[b]);
+  const long long* bp = reinterpret_cast<const long long*>(spart);
+  long long bx = 0, by = 0;
+#pragma unroll 4
+  for (int b = threadIdx.x; b < P.nbx; b += kThreads) bx = max(bx, __ldcg(bp + b));
+#pragma unroll 4
+  for (int b = P.nbx + threadIdx.x; b < P.nbx + P.nby; b += kThreads) by = max(by, __ldcg(bp + b));
+  double sx = __longlong_as_double(bx), sy = __longlong_as_double(by);
   sx = block_max<kThreads>(sx, sh);
   sy = block_max<kThreads>(sy, sh);
   if (threadIdx.x == 0) {
@@ -702,7 +723,7 @@ __device__ __forceinline__ int cell_item(const DevParams& P, const DevState<T>& 
   const long long e = ext_index(P, i, j);
   T s[4];
   convect_cell(P, S, i, j, e, dt, s);
-  const T tau = T(1) / s[0];
+  const T tau = tdiv(T(1), s[0]);
   // semi-implicit friction: q <- q / (1 + dt C(h) |q|),
   // C = f / (8 h^2) (Darcy) or g / (K^2 h^(7/3)) (Strickler)
   if (P.friction != 0) {
@@ -710,8 +731,8 @@ __device__ __forceinline__ int cell_item(const DevParams& P, const DevState<T>& 
     T C = T(P.fric_c) * (tau * tau);
     if (P.friction == 2) C = C * rcbrt64(s[0]);
     const T den = T(1) + T(dt) * C * qn;
-    s[1] = s[1] / den;
-    s[2] = s[2] / den;
+    s[1] = tdiv(s[1], den);
+    s[2] = tdiv(s[2], den);
   }
   int st = 0;
   if (!(finite_bits(s[0]) && finite_bits(s[1]) && finite_bits(s[2]) && finite_bits(s[3]))) st = ST_NAN;
@@ -777,7 +798,7 @@ __global__ void __launch_bounds__(kThreads) init_kernel(DevParams P, DevState<T>
     T s[4] = {S.h[e], S.hu[e], P.dim == 2 ? S.hv[e] : T(0), S.z[e]};
     if (!(tfinite(s[0]) && tfinite(s[1]) && tfinite(s[2]) && tfinite(s[3]))) atomicOr(&sc->status, ST_NAN);
     else if (!positive(s[0])) atomicOr(&sc->status, ST_NEG_DEPTH);
-    store_cell(P, S, e, s, T(1) / s[0]);
+    store_cell(P, S, e, s, tdiv(T(1), s[0]));
     write_ghosts(P, S, i, j, s);
     mh = (double)s[0];
     mz = (double)s[3];

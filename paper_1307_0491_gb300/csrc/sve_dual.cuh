@@ -54,6 +54,7 @@ template <int N> __device__ __forceinline__ Dual<N> operator/(const Dual<N>& a, 
   for (int i = 0; i < N; ++i) r.d[i] = (a.d[i] - r.v * b.d[i]) * ib;
   return r;
 }
+template <int N> __device__ __forceinline__ Dual<N> tdiv(const Dual<N>& a, const Dual<N>& b) { return a / b; }
 template <int N> __device__ __forceinline__ bool operator<(const Dual<N>& a, const Dual<N>& b) { return a.v < b.v; }
 template <int N> __device__ __forceinline__ bool operator>(const Dual<N>& a, const Dual<N>& b) { return a.v > b.v; }
 template <int N> __device__ __forceinline__ bool operator<=(const Dual<N>& a, const Dual<N>& b) { return a.v <= b.v; }

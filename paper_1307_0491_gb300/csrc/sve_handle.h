@@ -29,7 +29,14 @@ struct sve_handle {
   double* fixed = nullptr;
   int fixed_cap = 0;
   int nb_iface = 0, nb_cell = 0;
-  cudaGraphExec_t graph[2] = {nullptr, nullptr};  // [fixed]
+  cudaGraphExec_t graph[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};  // [fixed][parity]
+  // FP32 state: the fused stencil with a double-buffered state; fields[0..3]
+  // always point at the current buffer, other[0..3] at the next one
+  bool fused = false;
+  void* other[4] = {};
+  int parity = 0;  // flips with every step (0: fields hold the buffer allocated first)
+  int fgx = 0, fgy = 0;  // tiles of the fused step in x and y
+  int fgrid_speed = 0, fgrid_fused = 0;  // resident blocks of its two kernels (grid-stride over the tiles)
   long long last_launches = 0;
   int last_steps = 0;
   // kernel timing (sve_profile): 3 events per step, read back lazily
