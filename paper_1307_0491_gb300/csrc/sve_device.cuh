@@ -226,16 +226,10 @@ struct NewtonEval {
   T m, ip, zl, zr;  // kept for F'(p)
 };
 
+// The states at p given m = tau1 - tau4 and 1/p (e.tau2, e.tau3 set).
 template <typename T>
-__device__ __forceinline__ void newton_eval(T p, const NewtonConst<T>& c, const Cell<T>& L, const Cell<T>& R,
-                                            NewtonEval<T>& e) {
-  const T amb = c.a - c.b;
-  const T sigma = (c.C0 - amb * p) * c.inv_b;       // from u* continuity
-  e.tau2 = T(0.5) * (sigma - c.D);                  // from Pi continuity
-  e.tau3 = T(0.5) * (sigma + c.D);
-  const T N = c.dZ + c.K * c.D * sigma;
-  e.ip = tdiv(T(1), p);
-  e.m = -N * e.ip * c.inv_K;                        // from Z* continuity
+__device__ __forceinline__ void newton_states(T p, const NewtonConst<T>& c, const Cell<T>& L, const Cell<T>& R,
+                                              NewtonEval<T>& e) {
   e.tau1 = T(0.5) * (p + e.m);
   e.tau4 = T(0.5) * (p - e.m);
   e.u1 = L.un + c.a * (e.tau1 - L.tau);
@@ -248,11 +242,29 @@ __device__ __forceinline__ void newton_eval(T p, const NewtonConst<T>& c, const 
   e.F = (L.Om - R.Om) + e.lam2 * e.zl - e.lam4 * e.zr;
 }
 
+template <typename T>
+__device__ __forceinline__ void newton_sigma(T p, const NewtonConst<T>& c, NewtonEval<T>& e, T& sigma) {
+  sigma = (c.C0 - (c.a - c.b) * p) * c.inv_b;       // from u* continuity
+  e.tau2 = T(0.5) * (sigma - c.D);                  // from Pi continuity
+  e.tau3 = T(0.5) * (sigma + c.D);
+}
+
+template <typename T>
+__device__ __forceinline__ void newton_eval(T p, const NewtonConst<T>& c, const Cell<T>& L, const Cell<T>& R,
+                                            NewtonEval<T>& e) {
+  T sigma;
+  newton_sigma(p, c, e, sigma);
+  const T N = c.dZ + c.K * c.D * sigma;
+  e.ip = tdiv(T(1), p);
+  e.m = -N * e.ip * c.inv_K;                        // from Z* continuity
+  newton_states(p, c, L, R, e);
+}
+
 // Analytic F'(p) at an evaluated point.
 template <typename T>
-__device__ __forceinline__ T newton_deriv(const NewtonConst<T>& c, const NewtonEval<T>& e) {
+__device__ __forceinline__ T newton_deriv(const NewtonConst<T>& c, const NewtonEval<T>& e, T& dm) {
   const T amb = c.a - c.b;
-  const T dm = -c.dN * e.ip * c.inv_K - e.m * e.ip;
+  dm = -c.dN * e.ip * c.inv_K - e.m * e.ip;
   const T dtau1 = T(0.5) * (T(1) + dm);
   const T dtau4 = T(0.5) * (T(1) - dm);
   const T dtau2 = T(0.5) * c.dsig;
@@ -261,9 +273,21 @@ __device__ __forceinline__ T newton_deriv(const NewtonConst<T>& c, const NewtonE
 }
 
 template <typename T>
+__device__ __forceinline__ T newton_deriv(const NewtonConst<T>& c, const NewtonEval<T>& e) {
+  T dm;
+  return newton_deriv(c, e, dm);
+}
+
+template <typename T>
 __device__ __forceinline__ bool newton_positive(const NewtonEval<T>& e) {
   return positive(e.tau1) && positive(e.tau2) && positive(e.tau3) && positive(e.tau4);
 }
+
+// |x| <= y for y >= 0 on the bit patterns (integer compare, off the FP64 pipe).
+__device__ __forceinline__ bool abs_le(double x, double y) {
+  return (__double_as_longlong(x) & 0x7fffffffffffffffLL) <= __double_as_longlong(y);
+}
+__device__ __forceinline__ bool abs_le(float x, float y) { return fabsf(x) <= y; }
 
 // Safeguarded Newton from the evaluated point (p, e): steps that would make
 // a tau_k non-positive are halved (at most 60 times); stops when
@@ -272,9 +296,28 @@ template <typename T>
 __device__ __forceinline__ bool newton_loop(const NewtonConst<T>& c, const Cell<T>& L, const Cell<T>& R, T& p,
                                             NewtonEval<T>& e, int maxit, T tol, int& iters) {
   for (int it = 0; it < maxit; ++it) {
-    T step = tdiv(-e.F, newton_deriv(c, e));
-    if (!tfinite(step)) return false;
+    T dm;
+    T step = tdiv(-e.F, newton_deriv(c, e, dm));
+    if (!finite_bits(step)) return false;
     NewtonEval<T> tr;
+    const T pn = p + step;
+    if (abs_le(step, tol * pn)) {
+      // The update that meets the stopping rule: |step| <= tol p leaves the
+      // states at p + step first-order updates of those at p (m by dm/dp,
+      // 1/p by -1/p^2; tau2, tau3 exact), an O(tol^2) difference from a full
+      // evaluation -- no divide.
+      T sigma;
+      newton_sigma(pn, c, tr, sigma);
+      tr.m = e.m + dm * step;
+      tr.ip = e.ip - (e.ip * e.ip) * step;
+      newton_states(pn, c, L, R, tr);
+      if (newton_positive(tr)) {
+        p = pn;
+        e = tr;
+        ++iters;
+        return true;
+      }
+    }
     bool pos = false;
     for (int h = 0; h <= 60; ++h) {
       newton_eval(p + step, c, L, R, tr);
@@ -285,7 +328,7 @@ __device__ __forceinline__ bool newton_loop(const NewtonConst<T>& c, const Cell<
     p = p + step;
     e = tr;
     ++iters;
-    if (absbits(step) <= tol * p) return true;
+    if (abs_le(step, tol * p)) return true;
   }
   return false;
 }
@@ -332,14 +375,17 @@ template <typename T>
 __device__ __forceinline__ T newton_setup(const DevParams& P, const Cell<T>& L, const Cell<T>& R, T a, T b,
                                           NewtonConst<T>& c) {
   const T g = T(P.g);
-  const T rab = tdiv(T(1), a * b);       // one divide for 1/a and 1/b
+  // one divide for 1/a, 1/b and 1/K (a^2 - b^2 >= (1 - 1/kappa_a^2) a^2 > 0)
+  const T ab = a * b;
+  const T a2mb2 = a * a - b * b;
+  const T r = tdiv(T(1), ab * a2mb2);
+  const T rab = r * a2mb2;
   const T inv_a = b * rab;
   c.a = a;
   c.b = b;
   c.inv_b = a * rab;
-  const T a2mb2 = a * a - b * b;
   c.K = a2mb2 * T(P.inv_2g);
-  c.inv_K = tdiv(T(2) * g, a2mb2);
+  c.inv_K = (T(2) * g) * (ab * r);
   c.D = (R.tau - L.tau) + (R.Pi - L.Pi) * (inv_a * inv_a);
   const T du = R.un - L.un;
   c.C0 = du + a * (L.tau + R.tau);
@@ -373,6 +419,7 @@ __device__ __forceinline__ void fan_fluctuations(const DevParams& P, const Cell<
   const T FhL = L.Hn, FqL = L.Hn * L.un + L.Pi, FvL = L.Hn * L.ut;
   const T FhR = R.Hn, FqR = R.Hn * R.un + R.Pi, FvR = R.Hn * R.ut;
   T Fh, Fq, Fv;
+  T tkv = T(1), ukv = T(0), vkv = T(0), Pkv = T(0);  // state m (m = 1..4)
   if (m == 0) {
     Fh = FhL; Fq = FqL; Fv = FvL;
   } else if (m == 5) {
@@ -385,15 +432,26 @@ __device__ __forceinline__ void fan_fluctuations(const DevParams& P, const Cell<
     const T uk = m == 1 ? e.u1 : (m == 4 ? e.u4 : us);
     const T vk = left ? L.ut : R.ut;
     const T Pk = left ? L.Pi + a2 * (L.tau - tk) : R.Pi + a2 * (R.tau - tk);
-    const T Hk = tdiv(T(1), tk);
-    Fh = Hk * uk;
-    Fq = Fh * uk + Pk;
-    Fv = Fh * vk;
+    tkv = tk;
+    ukv = uk;
+    vkv = vk;
+    Pkv = Pk;
   }
-  // b-waves: bed jumps and the non-conservative source g Hbar [Z]
+  // b-waves: bed jumps and the non-conservative source g Hbar [Z]; one
+  // divide for 1/tau_k, 1/(tau1 + tau2) and 1/(tau3 + tau4)
   const T zj2 = e.Zs - L.Z, zj4 = R.Z - e.Zs;
-  const T S2 = tdiv(T(2) * g * zj2, e.tau1 + e.tau2);
-  const T S4 = tdiv(T(2) * g * zj4, e.tau3 + e.tau4);
+  const T d12 = e.tau1 + e.tau2, d34 = e.tau3 + e.tau4;
+  const T d1234 = d12 * d34;
+  const T r = tdiv(T(1), tkv * d1234);
+  const T rt = r * tkv;
+  const T S2 = (T(2) * g * zj2) * (rt * d34);
+  const T S4 = (T(2) * g * zj4) * (rt * d12);
+  if (m != 0 && m != 5) {
+    const T Hk = r * d1234;
+    Fh = Hk * ukv;
+    Fq = Fh * ukv + Pkv;
+    Fv = Fh * vkv;
+  }
   const bool n2 = negative(lam2), n4 = negative(lam4);
   Am[0] = Fh - FhL;
   Ap[0] = FhR - Fh;
@@ -519,20 +577,26 @@ __device__ __forceinline__ double block_max(double v, double* sh) {
   return r;
 }
 
+// Block sums of (a, b), valid in thread 0, in a fixed order.  The values go
+// through shared memory and one warp adds them (NT/32 serial adds per lane,
+// then a shuffle tree): a shuffle tree in every warp would cost each thread
+// five FP64 adds per value on GB300's narrow FP64 pipe.
 template <int NT>
 __device__ __forceinline__ void block_sum2(double& a, double& b, double* sh) {
-  a = warp_sum(a);
-  b = warp_sum(b);
-  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
-  if (l == 0) { sh[2 * w] = a; sh[2 * w + 1] = b; }
+  static_assert(NT % 32 == 0, "whole warps");
+  __shared__ double buf[2][NT];
+  buf[0][threadIdx.x] = a;
+  buf[1][threadIdx.x] = b;
   __syncthreads();
-  if (threadIdx.x == 0) {
+  if (threadIdx.x < 32) {
     double ra = 0.0, rb = 0.0;
-    for (int k = 0; k < NT / 32; ++k) { ra += sh[2 * k]; rb += sh[2 * k + 1]; }
-    a = ra;
-    b = rb;
+#pragma unroll
+    for (int k = 0; k < NT / 32; ++k) { ra += buf[0][threadIdx.x + 32 * k]; rb += buf[1][threadIdx.x + 32 * k]; }
+    a = warp_sum(ra);
+    b = warp_sum(rb);
   }
   __syncthreads();
+  (void)sh;
 }
 
 // Sum of the per-block (h, z) partials by the last block: thread t adds
@@ -730,9 +794,9 @@ __device__ __forceinline__ int cell_item(const DevParams& P, const DevState<T>& 
     const T qn = tsqrt(s[1] * s[1] + s[2] * s[2]);
     T C = T(P.fric_c) * (tau * tau);
     if (P.friction == 2) C = C * rcbrt64(s[0]);
-    const T den = T(1) + T(dt) * C * qn;
-    s[1] = tdiv(s[1], den);
-    s[2] = tdiv(s[2], den);
+    const T rden = tdiv(T(1), T(1) + T(dt) * C * qn);
+    s[1] = s[1] * rden;
+    s[2] = s[2] * rden;
   }
   int st = 0;
   if (!(finite_bits(s[0]) && finite_bits(s[1]) && finite_bits(s[2]) && finite_bits(s[3]))) st = ST_NAN;
