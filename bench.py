@@ -279,6 +279,35 @@ def run_adjoint(args, sve, W, torch):
             "time": "wall clock around the C-ABI calls (host-synchronous)"}
 
 
+def run_small1d(args, sve, W, torch):
+    """Small 1D grids, where a step is a few microseconds of work and its FP64
+    work has to be spread over many SMs: the 1D dune (1000 cells, periodic,
+    5000 CFL steps) and the 1D antidune of Sec. 5.2 at J = 2400 (5 cm bump),
+    with one-warp blocks (the automatic choice here) and 256-thread blocks."""
+    out = []
+    for name, w, n in (("1D dune 1000 cells periodic, Grass A_g=1e-3 m_g=3, 5000 CFL steps", W.dune1d(), 5000),
+                       ("1D antidune (Sec. 5.2) 2400 cells, 5 cm bump, supercritical inflow, 5000 CFL steps",
+                        W.paper_antidune1d(nx=2400, bump=0.05), 5000)):
+        row = {"workload": name, "steps": n}
+        for bs in (32, 256):
+            s = sve.Solver(w["params"], "fp64")
+            s.set_block_size(bs)
+            s.set_state(w["h"], w["hu"], w["hv"], w["z"])
+            s.step(200)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            s.step(n)
+            t1 = time.perf_counter()
+            launches = s.launches()
+            s.close()
+            row[f"block{bs}"] = {"steps_per_s": n / (t1 - t0), "cell_updates_per_s": n * w["params"]["nx"] / (t1 - t0),
+                                 "launches": launches}
+        row["narrow_vs_wide"] = row["block32"]["steps_per_s"] / row["block256"]["steps_per_s"]
+        row["time"] = "wall clock around one host-synchronous sve_step call of all steps (CUDA graphs of 16 steps)"
+        out.append(row)
+    return out
+
+
 def run_ours(args, world, rank, local):
     import torch
 
@@ -415,6 +444,8 @@ def run_ours(args, world, rank, local):
                 line["batched"].append(run_batched(args, sve, W, torch, "fp32", None))
         if not args.no_adjoint:
             line["adjoint"] = run_adjoint(args, sve, W, torch)
+        if not args.no_small1d:
+            line["small1d"] = run_small1d(args, sve, W, torch)
         if world == 1 and not args.no_cpu_baseline:
             rate, nsteps, secs = cpu_oracle_rate(w)
             line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
@@ -441,6 +472,7 @@ def main():
     ap.add_argument("--batch-spinup", type=int, default=100)
     ap.add_argument("--no-batch-fp32", action="store_true", help="skip the FP32-state ensemble")
     ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint measurement")
+    ap.add_argument("--no-small1d", action="store_true", help="skip the small-1D measurement")
     ap.add_argument("--workload", choices=["dune2d", "antidune2d"], default="dune2d")
     ap.add_argument("--precision", choices=["fp64", "fp32"], default="fp64")
     ap.add_argument("--nx", type=int, default=0, help="grid override (profiling captures)")

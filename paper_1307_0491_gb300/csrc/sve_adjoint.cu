@@ -68,7 +68,7 @@ __device__ __forceinline__ Cell<T> project_grass(const DevParams& P, T H, T Hn, 
   c.tau = T(1) / H;
   c.un = Hn * c.tau;
   c.ut = Ht * c.tau;
-  const T g = T(P.g);
+  const T g = sve::par<T>(P.g, P.f.g);
   c.Pi = T(0.5) * g * H * H;
   const T speed2 = c.un * c.un + c.ut * c.ut;
   T Q, dQ;
@@ -425,9 +425,10 @@ int forward_step(sve_handle* h, double dt) {
   ADJ_TRY(cudaMemcpyAsync(h->fixed, &dt, sizeof(double), cudaMemcpyHostToDevice, h->stream));
   ADJ_TRY(cudaMemsetAsync(&h->sc->call_step, 0, sizeof(int), h->stream));
   DevState<double> S = state_of<double>(h);
-  sve::interface_kernel<double><<<h->nb_iface, sve::kThreads, 0, h->stream>>>(h->P, S, h->sc, h->spart, h->fixed,
-                                                                             h->dtlog, 1);
-  sve::cell_kernel<double><<<h->nb_cell, sve::kThreads, 0, h->stream>>>(h->P, S, h->sc, h->mpart);
+  const unsigned nbi = (unsigned)sve::iface_blocks(h->P, sve::kThreads);
+  const unsigned nbc = (unsigned)sve::cell_blocks(h->P, sve::kThreads);
+  sve::interface_kernel<double><<<nbi, sve::kThreads, 0, h->stream>>>(h->P, S, h->sc, h->fixed, h->dtlog, 1);
+  sve::cell_kernel<double><<<nbc, sve::kThreads, 0, h->stream>>>(h->P, S, h->sc, h->mpart);
   return cudaGetLastError() == cudaSuccess ? SVE_OK : SVE_ERR_CUDA;
 }
 
@@ -504,6 +505,8 @@ int sve_adjoint(sve_handle* h, const void* lam_h, const void* lam_hu, const void
       ADJ_TRY(cudaMemsetAsync(lam + f * ncell, 0, sizeof(double) * ncell, h->stream));
   }
   DevState<double> S = state_of<double>(h);
+  const unsigned nbi = (unsigned)sve::iface_blocks(P, sve::kThreads);
+  const unsigned nbc = (unsigned)sve::cell_blocks(P, sve::kThreads);
   const int ncp = (int)r->checkpoints.size();
   for (int k = ncp - 1; k >= 0; --k) {
     const int n0 = k * r->every;
@@ -511,7 +514,7 @@ int sve_adjoint(sve_handle* h, const void* lam_h, const void* lam_hu, const void
     // recompute the segment's states U^{n0} .. U^{n0 + len - 1}
     rc = load_state(h, r->checkpoints[k]);
     if (rc) return rc;
-    sve::init_kernel<double><<<h->nb_cell, sve::kThreads, 0, h->stream>>>(P, S, h->sc, h->mpart);
+    sve::init_kernel<double><<<nbc, sve::kThreads, 0, h->stream>>>(P, S, h->sc, h->mpart);
     for (int s = 0; s < len; ++s) {
       rc = save_state(h, r->seg + (size_t)s * nst);
       if (!rc) rc = forward_step(h, r->dts[n0 + s]);
@@ -522,12 +525,11 @@ int sve_adjoint(sve_handle* h, const void* lam_h, const void* lam_hu, const void
       const double dt = r->dts[n0 + s];
       rc = load_state(h, r->seg + (size_t)s * nst);
       if (rc) return rc;
-      sve::init_kernel<double><<<h->nb_cell, sve::kThreads, 0, h->stream>>>(P, S, h->sc, h->mpart);
+      sve::init_kernel<double><<<nbc, sve::kThreads, 0, h->stream>>>(P, S, h->sc, h->mpart);
       // forward fluctuations of step n (needed for the pre-friction state)
       ADJ_TRY(cudaMemcpyAsync(h->fixed, &dt, sizeof(double), cudaMemcpyHostToDevice, h->stream));
       ADJ_TRY(cudaMemsetAsync(&h->sc->call_step, 0, sizeof(int), h->stream));
-      sve::interface_kernel<double><<<h->nb_iface, sve::kThreads, 0, h->stream>>>(P, S, h->sc, h->spart,
-                                                                                 h->fixed, h->dtlog, 1);
+      sve::interface_kernel<double><<<nbi, sve::kThreads, 0, h->stream>>>(P, S, h->sc, h->fixed, h->dtlog, 1);
       adj_friction_kernel<<<nb_c, kAdjThreads, 0, h->stream>>>(P, S, lam, r->mu, dt, r->gpart, r->gacc, r->done);
       adj_interface_kernel<<<nb_if, kAdjThreads, 0, h->stream>>>(P, S, r->mu, dt, h->cfg.A_g, h->cfg.m_g,
                                                                  r->gpart, r->gacc, r->done);

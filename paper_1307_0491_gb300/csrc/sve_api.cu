@@ -101,17 +101,37 @@ void make_params(const sve_config* c, DevParams* P) {
   P->newton_maxit = c->newton_maxit;
   P->nfx = (long long)(P->nx + 1) * P->ny;
   P->nfy = P->dim == 2 ? (long long)P->nx * (P->ny + 1) : 0;
-  P->nbx = (int)((P->nfx + sve::kThreads - 1) / sve::kThreads);
-  P->nby = (int)((P->nfy + sve::kThreads - 1) / sve::kThreads);
+  P->f.g = (float)P->g;
+  P->f.inv_2g = (float)P->inv_2g;
+  P->f.A_g = (float)P->A_g;
+  P->f.m_g = (float)P->m_g;
+  P->f.mpm_C = (float)P->mpm_C;
+  P->f.mpm_alpha = (float)P->mpm_alpha;
+  P->f.tau_cr = (float)P->tau_cr;
+  P->f.fric_c = (float)P->fric_c;
+  P->f.q_in = (float)P->q_in;
+  P->f.h_in = (float)P->h_in;
+  P->f.kappa_a = (float)P->kappa_a;
+  P->f.beta_min = (float)P->beta_min;
+  P->f.gamma_z = (float)P->gamma_z;
+  P->f.newton_tol = (float)P->newton_tol;
 }
 
 template <typename T>
 void launch_step(sve_handle* h, cudaStream_t st, int fixed, cudaEvent_t* ev) {
   DevState<T> S = state_of<T>(h);
+  const int nt = h->nt;
+  const unsigned nbi = (unsigned)sve::iface_blocks(h->P, nt), nbc = (unsigned)sve::cell_blocks(h->P, nt);
   if (ev) cudaEventRecord(ev[0], st);
-  sve::interface_kernel<T><<<h->nb_iface, sve::kThreads, 0, st>>>(h->P, S, h->sc, h->spart, h->fixed, h->dtlog, fixed);
+  if (nt == sve::kThreadsNarrow)
+    sve::interface_kernel<T, sve::kThreadsNarrow><<<nbi, nt, 0, st>>>(h->P, S, h->sc, h->fixed, h->dtlog, fixed);
+  else
+    sve::interface_kernel<T, sve::kThreads><<<nbi, nt, 0, st>>>(h->P, S, h->sc, h->fixed, h->dtlog, fixed);
   if (ev) cudaEventRecord(ev[1], st);
-  sve::cell_kernel<T><<<h->nb_cell, sve::kThreads, 0, st>>>(h->P, S, h->sc, h->mpart);
+  if (nt == sve::kThreadsNarrow)
+    sve::cell_kernel<T, sve::kThreadsNarrow><<<nbc, nt, 0, st>>>(h->P, S, h->sc, h->mpart);
+  else
+    sve::cell_kernel<T, sve::kThreads><<<nbc, nt, 0, st>>>(h->P, S, h->sc, h->mpart);
   if (ev) cudaEventRecord(ev[2], st);
 }
 
@@ -233,6 +253,10 @@ int enqueue_steps(sve_handle* h, int nsteps, int fixed) {
   return SVE_OK;
 }
 
+int auto_block_size(const sve_handle* h) {
+  return sve::iface_blocks(h->P, sve::kThreads) < 2LL * h->nsm ? sve::kThreadsNarrow : sve::kThreads;
+}
+
 int wait_status(sve_handle* h) {
   DevScalars s;
   SVE_TRY(cudaMemcpyAsync(&s, h->sc, sizeof(s), cudaMemcpyDeviceToHost, h->stream));
@@ -297,8 +321,15 @@ int sve_create(const sve_config* cfg, sve_handle** out) {
   if (cudaGetDevice(&h->device) != cudaSuccess) { delete h; return SVE_ERR_CUDA; }
   h->elem = cfg->precision == SVE_FP64 ? 8 : 4;
   h->next = (long long)(h->P.nx + 2) * (h->P.ny + 2);
-  h->nb_iface = h->P.nbx + h->P.nby;
-  h->nb_cell = (int)(((long long)h->P.nx * h->P.ny + sve::kThreads - 1) / sve::kThreads);
+  // block size of the two-kernel step: one warp per block while the grid is
+  // too small to give every SM two 256-thread blocks (GB300 issues ~2 FP64
+  // operations per clock per SM, so a small grid's FP64 work has to spread)
+  {
+    int nsm = 0;
+    if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, h->device) != cudaSuccess) nsm = 152;
+    h->nsm = nsm;
+  }
+  h->nt = auto_block_size(h);
   bool ok = true;
   for (int k = 0; k < 13 && ok; ++k) ok = cudaMalloc(&h->fields[k], h->elem * (size_t)h->next) == cudaSuccess;
   ok = ok && cudaMalloc(&h->fx, 8 * h->elem * (size_t)h->P.nfx) == cudaSuccess;
@@ -317,8 +348,8 @@ int sve_create(const sve_config* cfg, sve_handle** out) {
     h->fgrid_speed = (int)std::min<size_t>(nbf, (size_t)std::max(1, nsm * bs));
     h->fgrid_fused = (int)std::min<size_t>(nbf, (size_t)std::max(1, nsm * bf));
   }
-  const size_t nsp = std::max((size_t)h->nb_iface, 2 * nbf);
-  const size_t nmp = std::max(2 * (size_t)h->nb_cell, 2 * nbf);
+  const size_t nsp = 2 * nbf + 2;
+  const size_t nmp = std::max(2 * (size_t)sve::cell_blocks(h->P, sve::kThreadsNarrow), 2 * nbf);
   ok = ok && cudaMalloc(&h->spart, sizeof(double) * nsp) == cudaSuccess;
   ok = ok && cudaMalloc(&h->mpart, sizeof(double) * nmp) == cudaSuccess;
   if (h->fused)
@@ -358,9 +389,9 @@ int sve_set_state(sve_handle* h, const void* depth, const void* hu, const void* 
   }
   SVE_TRY(cudaMemsetAsync(h->sc, 0, sizeof(DevScalars), h->stream));
   if (h->cfg.precision == SVE_FP64)
-    sve::init_kernel<double><<<h->nb_cell, sve::kThreads, 0, h->stream>>>(P, state_of<double>(h), h->sc, h->mpart);
+    sve::init_kernel<double><<<(unsigned)sve::cell_blocks(h->P, sve::kThreads), sve::kThreads, 0, h->stream>>>(P, state_of<double>(h), h->sc, h->mpart);
   else
-    sve::init_kernel<float><<<h->nb_cell, sve::kThreads, 0, h->stream>>>(P, state_of<float>(h), h->sc, h->mpart);
+    sve::init_kernel<float><<<(unsigned)sve::cell_blocks(h->P, sve::kThreads), sve::kThreads, 0, h->stream>>>(P, state_of<float>(h), h->sc, h->mpart);
   SVE_TRY(cudaGetLastError());
   DevScalars s;
   SVE_TRY(cudaMemcpyAsync(&s, h->sc, sizeof(s), cudaMemcpyDeviceToHost, h->stream));
@@ -469,6 +500,20 @@ const char* sve_strerror(int code) {
     case SVE_ERR_NOALLOC_SIZE: return "grid too large for the static scratch of sve_step_noalloc";
     default: return "unknown error";
   }
+}
+
+int sve_set_block_size(sve_handle* h, int threads) {
+  if (!h) return SVE_ERR_ARG;
+  if (threads != 0 && threads != sve::kThreadsNarrow && threads != sve::kThreads) return SVE_ERR_ARG;
+  const int nt = threads == 0 ? auto_block_size(h) : threads;
+  if (nt != h->nt) drop_graphs(h);  // the captured steps hold the launch shape
+  h->nt = nt;
+  return SVE_OK;
+}
+
+int sve_get_block_size(sve_handle* h) {
+  if (!h) return SVE_ERR_ARG;
+  return h->nt;
 }
 
 long long sve_last_launch_count(sve_handle* h) { return h ? h->last_launches : -1; }

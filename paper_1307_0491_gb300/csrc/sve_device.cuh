@@ -45,8 +45,18 @@ struct DevParams {
   double kappa_a, beta_min, gamma_z, newton_tol;
   int newton_maxit;
   long long nfx, nfy;   // number of x- and y-interfaces
-  int nbx, nby;         // blocks of the interface kernel over x and y interfaces
+  // FP32 copies (rounded on the host) for the FP32-state kernels: converting
+  // a double inside a kernel is an FP64-pipe instruction, and GB300's FP64
+  // pipe is ~1/64 of its FP32 pipe
+  struct {
+    float g, inv_2g, A_g, m_g, mpm_C, mpm_alpha, tau_cr, fric_c, q_in, h_in, kappa_a, beta_min, gamma_z, newton_tol;
+  } f;
 };
+
+// Parameter x of DevParams in precision T: the double itself, or its FP32
+// copy P.f.x for float (same value as (float)x).
+template <typename T> __device__ __forceinline__ T par(double d, float) { return T(d); }
+template <> __device__ __forceinline__ float par<float>(double, float f) { return f; }
 
 // Device scalars of one handle.
 struct DevScalars {
@@ -58,6 +68,7 @@ struct DevScalars {
   unsigned int done_iface, done_cell;
   long long steps;      // total steps since the state was set
   unsigned long long newton_iters;  // Newton updates summed over all solves since the state was set
+  unsigned long long smax_bits[2];  // running max of the x / y wave speeds of the step (bit patterns; 0 between steps)
 };
 
 // Ghost-padded state and projection (SoA) of precision T.
@@ -88,6 +99,10 @@ __device__ __forceinline__ double tpow(double x, double y) { return pow(x, y); }
 __device__ __forceinline__ float tpow(float x, float y) { return powf(x, y); }
 __device__ __forceinline__ bool tfinite(double x) { return isfinite(x); }
 __device__ __forceinline__ bool tfinite(float x) { return isfinite(x); }
+// Whether a quotient is cheap enough to take several where one would do (FP32:
+// div.approx); in FP64 (and its dual numbers) divides are folded into one.
+template <typename T> struct cheap_div { static constexpr bool value = false; };
+template <> struct cheap_div<float> { static constexpr bool value = true; };
 
 // ---- FP64 arithmetic on GB300 -------------------------------------------
 // GB300 issues about two FP64 instructions per SM clock.  Measured costs in
@@ -153,7 +168,7 @@ template <typename T>
 __device__ __forceinline__ void closure(const DevParams& P, T H, T un, T ut, T& Q, T& dQ) {
   const T speed2 = un * un + ut * ut;
   if (P.bedload == 0) {
-    const T A = T(P.A_g);
+    const T A = par<T>(P.A_g, P.f.A_g);
     if (speed2 == T(0)) {
       Q = T(0);
       dQ = (P.m_int == 1) ? A : T(0);
@@ -167,7 +182,7 @@ __device__ __forceinline__ void closure(const DevParams& P, T H, T un, T ut, T& 
       case 4: { T sp = tsqrt(speed2); pm1 = speed2 * sp; second = T(3) * (un * un) * sp; } break;
       default: {
         T sp = tsqrt(speed2);
-        T m = T(P.m_g);
+        T m = par<T>(P.m_g, P.f.m_g);
         pm1 = tpow(sp, m - T(1));
         second = (m - T(1)) * (un * un) * tpow(sp, m - T(3));
       }
@@ -176,9 +191,9 @@ __device__ __forceinline__ void closure(const DevParams& P, T H, T un, T ut, T& 
     dQ = A * (pm1 + second);
     return;
   }
-  T alpha = T(P.mpm_alpha);
+  T alpha = par<T>(P.mpm_alpha, P.f.mpm_alpha);
   if (P.friction != 1) alpha = alpha * rcbrt64(H);
-  const T theta = alpha * speed2 - T(P.tau_cr);
+  const T theta = alpha * speed2 - par<T>(P.tau_cr, P.f.tau_cr);
   if (speed2 == T(0) || !(theta > T(0))) {
     Q = T(0);
     dQ = T(0);
@@ -188,7 +203,7 @@ __device__ __forceinline__ void closure(const DevParams& P, T H, T un, T ut, T& 
   const T isp = tdiv(T(1), sp);
   const T sth = tsqrt(theta);
   const T th32 = theta * sth;
-  const T C = T(P.mpm_C);
+  const T C = par<T>(P.mpm_C, P.f.mpm_C);
   Q = C * th32 * (un * isp);
   dQ = C * (T(3) * sth * alpha * (un * un) * isp + th32 * (ut * ut) * (isp * isp * isp));
 }
@@ -348,7 +363,7 @@ template <> __device__ __forceinline__ float newton_floor<float>() { return 64.0
 template <typename T>
 __device__ __forceinline__ bool newton_root(const DevParams& P, const NewtonConst<T>& c, const Cell<T>& L,
                                             const Cell<T>& R, T p0, NewtonEval<T>& e, int& iters) {
-  const T tol = tmax(T(P.newton_tol), newton_floor<T>());
+  const T tol = tmax(par<T>(P.newton_tol, P.f.newton_tol), newton_floor<T>());
   T p = p0;
   newton_eval(p, c, L, R, e);
   return newton_loop(c, L, R, p, e, P.newton_maxit, tol, iters);
@@ -359,13 +374,13 @@ __device__ __forceinline__ bool newton_root(const DevParams& P, const NewtonCons
 // K tau_min^2 >= gamma_z |dZ| (the sediment waves can carry the bed jump).
 template <typename T>
 __device__ __forceinline__ void celerities(const DevParams& P, const Cell<T>& L, const Cell<T>& R, T& a, T& b) {
-  const T g = T(P.g);
+  const T g = par<T>(P.g, P.f.g);
   const T a0 = nnmax(L.ca, R.ca);
   const T b0 = nnmax(L.cb, R.cb);
-  a = T(P.kappa_a) * nnmax(a0, b0);
-  b = nnmax(b0, T(P.beta_min) * a0);
+  a = par<T>(P.kappa_a, P.f.kappa_a) * nnmax(a0, b0);
+  b = nnmax(b0, par<T>(P.beta_min, P.f.beta_min) * a0);
   const T Hmax = nnmax(L.H, R.H);
-  const T need = b * b + T(2) * g * T(P.gamma_z) * absbits(R.Z - L.Z) * (Hmax * Hmax);
+  const T need = b * b + T(2) * g * par<T>(P.gamma_z, P.f.gamma_z) * absbits(R.Z - L.Z) * (Hmax * Hmax);
   if (a * a < need) a = tsqrt(need);
 }
 
@@ -374,18 +389,24 @@ __device__ __forceinline__ void celerities(const DevParams& P, const Cell<T>& L,
 template <typename T>
 __device__ __forceinline__ T newton_setup(const DevParams& P, const Cell<T>& L, const Cell<T>& R, T a, T b,
                                           NewtonConst<T>& c) {
-  const T g = T(P.g);
+  const T g = par<T>(P.g, P.f.g);
   // one divide for 1/a, 1/b and 1/K (a^2 - b^2 >= (1 - 1/kappa_a^2) a^2 > 0)
   const T ab = a * b;
   const T a2mb2 = a * a - b * b;
-  const T r = tdiv(T(1), ab * a2mb2);
-  const T rab = r * a2mb2;
+  T rab;
+  if constexpr (cheap_div<T>::value) {
+    rab = tdiv(T(1), ab);
+    c.inv_K = tdiv(T(2) * g, a2mb2);
+  } else {
+    const T r = tdiv(T(1), ab * a2mb2);
+    rab = r * a2mb2;
+    c.inv_K = (T(2) * g) * (ab * r);
+  }
   const T inv_a = b * rab;
   c.a = a;
   c.b = b;
   c.inv_b = a * rab;
-  c.K = a2mb2 * T(P.inv_2g);
-  c.inv_K = (T(2) * g) * (ab * r);
+  c.K = a2mb2 * par<T>(P.inv_2g, P.f.inv_2g);
   c.D = (R.tau - L.tau) + (R.Pi - L.Pi) * (inv_a * inv_a);
   const T du = R.un - L.un;
   c.C0 = du + a * (L.tau + R.tau);
@@ -406,7 +427,7 @@ __device__ __forceinline__ T newton_setup(const DevParams& P, const Cell<T>& L, 
 template <typename T>
 __device__ __forceinline__ void fan_fluctuations(const DevParams& P, const Cell<T>& L, const Cell<T>& R,
                                                  const NewtonConst<T>& c, const NewtonEval<T>& e, T Am[4], T Ap[4]) {
-  const T g = T(P.g);
+  const T g = par<T>(P.g, P.f.g);
   const T a = c.a, b = c.b;
   const T lam1 = L.un - a * L.tau;
   const T lam5 = R.un + a * R.tau;
@@ -441,13 +462,20 @@ __device__ __forceinline__ void fan_fluctuations(const DevParams& P, const Cell<
   // divide for 1/tau_k, 1/(tau1 + tau2) and 1/(tau3 + tau4)
   const T zj2 = e.Zs - L.Z, zj4 = R.Z - e.Zs;
   const T d12 = e.tau1 + e.tau2, d34 = e.tau3 + e.tau4;
-  const T d1234 = d12 * d34;
-  const T r = tdiv(T(1), tkv * d1234);
-  const T rt = r * tkv;
-  const T S2 = (T(2) * g * zj2) * (rt * d34);
-  const T S4 = (T(2) * g * zj4) * (rt * d12);
+  T S2, S4, Hk;
+  if constexpr (cheap_div<T>::value) {
+    S2 = tdiv(T(2) * g * zj2, d12);
+    S4 = tdiv(T(2) * g * zj4, d34);
+    Hk = tdiv(T(1), tkv);
+  } else {
+    const T d1234 = d12 * d34;
+    const T r = tdiv(T(1), tkv * d1234);
+    const T rt = r * tkv;
+    S2 = (T(2) * g * zj2) * (rt * d34);
+    S4 = (T(2) * g * zj4) * (rt * d12);
+    Hk = r * d1234;
+  }
   if (m != 0 && m != 5) {
-    const T Hk = r * d1234;
     Fh = Hk * ukv;
     Fq = Fh * ukv + Pkv;
     Fv = Fh * vkv;
@@ -494,8 +522,8 @@ __device__ __forceinline__ void ghost_state(const DevParams& P, int s, const T i
 #pragma unroll
   for (int c = 0; c < 4; ++c) out[c] = in[c];
   switch (P.bc[s]) {
-    case GHOST_INFLOW_Q: out[normal] = inward * T(P.q_in); out[tangent] = T(0); break;
-    case GHOST_INFLOW_QH: out[0] = T(P.h_in); out[normal] = inward * T(P.q_in); out[tangent] = T(0); break;
+    case GHOST_INFLOW_Q: out[normal] = inward * par<T>(P.q_in, P.f.q_in); out[tangent] = T(0); break;
+    case GHOST_INFLOW_QH: out[0] = par<T>(P.h_in, P.f.h_in); out[normal] = inward * par<T>(P.q_in, P.f.q_in); out[tangent] = T(0); break;
     case GHOST_WALL: out[normal] = -in[normal]; break;
     default: break;
   }
@@ -511,7 +539,7 @@ __device__ __forceinline__ void store_cell(const DevParams& P, const DevState<T>
   T Qx, dQx, Qy = T(0), dQy = T(0);
   closure(P, H, u, v, Qx, dQx);
   if (P.dim == 2) closure(P, H, v, u, Qy, dQy);
-  const T g = T(P.g);
+  const T g = par<T>(P.g, P.f.g);
   S.h[e] = H; S.hu[e] = s[1]; S.hv[e] = s[2]; S.z[e] = s[3];
   S.tau[e] = tau; S.u[e] = u; S.v[e] = v;
   S.pi[e] = T(0.5) * g * H * H;
@@ -615,7 +643,14 @@ __device__ __forceinline__ void reduce_partials(const double* mpart, unsigned nb
 
 // ---- kernels -------------------------------------------------------------
 
-constexpr int kThreads = 256;
+constexpr int kThreads = 256;  // block size of the grid kernels on large grids
+constexpr int kThreadsNarrow = 32;  // on small grids: one warp per block spreads the FP64 work over more SMs
+
+// Blocks of interface_kernel<T, NT> and cell_kernel<T, NT> for a grid.
+inline long long iface_blocks(const DevParams& P, int nt) {
+  return (P.nfx + nt - 1) / nt + (P.nfy + nt - 1) / nt;
+}
+inline long long cell_blocks(const DevParams& P, int nt) { return ((long long)P.nx * P.ny + nt - 1) / nt; }
 
 // Load the projected cell at ext index e in the x (ydir = false) or y frame.
 template <typename T>
@@ -691,60 +726,53 @@ __device__ __forceinline__ void block_maxbits_sum(double& v, int& n) {
   __syncthreads();
 }
 
-// One thread per interface.  Blocks [0, nbx) cover the x-interfaces
-// (i - 1/2, j), i in [0, nx], j in [0, ny); blocks [nbx, nbx + nby) cover the
-// y-interfaces (i, j - 1/2), i in [0, nx), j in [0, ny].  The last block to
-// finish reduces the per-block speeds into the time step of this step.
-template <typename T>
-__global__ void __launch_bounds__(kThreads) interface_kernel(DevParams P, DevState<T> S, DevScalars* sc,
-                                                             double* spart, const double* fixed_dts,
-                                                             double* dtlog, int fixed) {
-  __shared__ double sh[2 * (kThreads / 32)];
+// One thread per interface, NT threads per block.  Blocks [0, nbx) cover the
+// x-interfaces (i - 1/2, j), i in [0, nx], j in [0, ny); blocks [nbx, nbx +
+// nby) the y-interfaces (i, j - 1/2), i in [0, nx), j in [0, ny] (nbx, nby =
+// the interface counts over NT, rounded up).  The last block to finish turns
+// the step's maximal speeds into its time step.
+template <typename T, int NT = kThreads>
+__global__ void __launch_bounds__(NT) interface_kernel(DevParams P, DevState<T> S, DevScalars* sc,
+                                                       const double* fixed_dts, double* dtlog, int fixed) {
   __shared__ bool last;
-  const bool ydir = blockIdx.x >= (unsigned)P.nbx;
-  const long long k = (long long)(ydir ? blockIdx.x - P.nbx : blockIdx.x) * kThreads + threadIdx.x;
+  const unsigned nbx = (unsigned)((P.nfx + NT - 1) / NT);
+  const bool ydir = blockIdx.x >= nbx;
+  const long long k = (long long)(ydir ? blockIdx.x - nbx : blockIdx.x) * NT + threadIdx.x;
   double smax = 0.0;
   int iters = 0;
   if (k < (ydir ? P.nfy : P.nfx)) {
     if (!interface_item(P, S, ydir, k, smax, iters)) atomicOr(&sc->status, ST_RIEMANN);
   }
   // block max of the (non-negative) speeds and sum of the Newton updates,
-  // both on integers (off the FP64 pipe)
-  block_maxbits_sum<kThreads>(smax, iters);
+  // both on integers (off the FP64 pipe); the block max then goes into the
+  // step's running maximum by an atomic max on the bit pattern (integer
+  // order = IEEE order for non-negative doubles; a max is order-free, so
+  // the result does not depend on the order the blocks finish in)
+  block_maxbits_sum<NT>(smax, iters);
   if (threadIdx.x == 0) {
     atomicAdd(&sc->newton_iters, (unsigned long long)iters);
-    spart[blockIdx.x] = smax;
+    atomicMax(&sc->smax_bits[ydir ? 1 : 0], (unsigned long long)__double_as_longlong(smax));
     __threadfence();
     const unsigned int ticket = atomicAdd(&sc->done_iface, 1u);
     last = (ticket == gridDim.x - 1);
   }
   __syncthreads();
-  if (!last) return;
-  // last block: reduce the partials (L2 loads after the fence; integer max
-  // of the bit patterns of the non-negative speeds)
+  if (!last || threadIdx.x != 0) return;
+  // last block: take the maxima (and reset them for the next step)
   __threadfence();
-  const long long* bp = reinterpret_cast<const long long*>(spart);
-  long long bx = 0, by = 0;
-#pragma unroll 4
-  for (int b = threadIdx.x; b < P.nbx; b += kThreads) bx = max(bx, __ldcg(bp + b));
-#pragma unroll 4
-  for (int b = P.nbx + threadIdx.x; b < P.nbx + P.nby; b += kThreads) by = max(by, __ldcg(bp + b));
-  double sx = __longlong_as_double(bx), sy = __longlong_as_double(by);
-  sx = block_max<kThreads>(sx, sh);
-  sy = block_max<kThreads>(sy, sh);
-  if (threadIdx.x == 0) {
-    double dt;
-    const int cs = sc->call_step;
-    if (fixed) dt = fixed_dts[cs];
-    else if (P.dim == 1) dt = P.cfl * P.dx / sx;
-    else dt = P.cfl / (sx / P.dx + sy / P.dy);
-    if (!(dt > 0.0) || !isfinite(dt)) { atomicOr(&sc->status, ST_DT); dt = 0.0; }
-    sc->dt = dt;
-    sc->Sx = sx;
-    sc->Sy = sy;
-    dtlog[cs] = dt;
-    sc->done_iface = 0u;
-  }
+  const double sx = __longlong_as_double((long long)atomicExch(&sc->smax_bits[0], 0ull));
+  const double sy = __longlong_as_double((long long)atomicExch(&sc->smax_bits[1], 0ull));
+  double dt;
+  const int cs = sc->call_step;
+  if (fixed) dt = fixed_dts[cs];
+  else if (P.dim == 1) dt = P.cfl * P.dx / sx;
+  else dt = P.cfl / (sx / P.dx + sy / P.dy);
+  if (!(dt > 0.0) || !isfinite(dt)) { atomicOr(&sc->status, ST_DT); dt = 0.0; }
+  sc->dt = dt;
+  sc->Sx = sx;
+  sc->Sy = sy;
+  dtlog[cs] = dt;
+  sc->done_iface = 0u;
 }
 
 // One interior cell k = j nx + i of one grid: Godunov average in
@@ -792,7 +820,7 @@ __device__ __forceinline__ int cell_item(const DevParams& P, const DevState<T>& 
   // C = f / (8 h^2) (Darcy) or g / (K^2 h^(7/3)) (Strickler)
   if (P.friction != 0) {
     const T qn = tsqrt(s[1] * s[1] + s[2] * s[2]);
-    T C = T(P.fric_c) * (tau * tau);
+    T C = par<T>(P.fric_c, P.f.fric_c) * (tau * tau);
     if (P.friction == 2) C = C * rcbrt64(s[0]);
     const T rden = tdiv(T(1), T(1) + T(dt) * C * qn);
     s[1] = s[1] * rden;
@@ -810,18 +838,18 @@ __device__ __forceinline__ int cell_item(const DevParams& P, const DevState<T>& 
 
 // One thread per interior cell (i, j): Godunov average in fluctuation form,
 // friction, checks, projection of the new state, ghosts, mass partials.
-template <typename T>
-__global__ void __launch_bounds__(kThreads) cell_kernel(DevParams P, DevState<T> S, DevScalars* sc, double* mpart) {
-  __shared__ double sh[2 * (kThreads / 32)];
+template <typename T, int NT = kThreads>
+__global__ void __launch_bounds__(NT) cell_kernel(DevParams P, DevState<T> S, DevScalars* sc, double* mpart) {
+  __shared__ double sh[2 * (NT / 32)];
   __shared__ bool last;
-  const long long k = (long long)blockIdx.x * kThreads + threadIdx.x;
+  const long long k = (long long)blockIdx.x * NT + threadIdx.x;
   const long long ncell = (long long)P.nx * P.ny;
   double mh = 0.0, mz = 0.0;
   if (k < ncell) {
     const int st = cell_item(P, S, k, sc->dt, mh, mz);
     if (st) atomicOr(&sc->status, st);
   }
-  block_sum2<kThreads>(mh, mz, sh);
+  block_sum2<NT>(mh, mz, sh);
   if (threadIdx.x == 0) {
     mpart[2 * blockIdx.x] = mh;
     mpart[2 * blockIdx.x + 1] = mz;
@@ -833,7 +861,7 @@ __global__ void __launch_bounds__(kThreads) cell_kernel(DevParams P, DevState<T>
   if (!last) return;
   __threadfence();
   double sh_h, sh_z;
-  reduce_partials<kThreads>(mpart, gridDim.x, sh_h, sh_z, sh);
+  reduce_partials<NT>(mpart, gridDim.x, sh_h, sh_z, sh);
   if (threadIdx.x == 0) {
     const double cell = P.dx * (P.dim == 2 ? P.dy : 1.0);
     sc->mass_h = sh_h * cell;

@@ -48,7 +48,7 @@ __device__ __forceinline__ void project_into(const DevParams& P, T H, T Hu, T Hv
   c.tau = tdiv(T(1), H);
   c.u = Hu * c.tau;
   c.v = Hv * c.tau;
-  const T g = T(P.g);
+  const T g = par<T>(P.g, P.f.g);
   c.Pi = T(0.5) * g * H * H;
   T Qx, dQx, Qy = T(0), dQy = T(0);
   closure(P, H, c.u, c.v, Qx, dQx);
@@ -195,6 +195,19 @@ __device__ __forceinline__ void write_ghost_state(const DevParams& P, const Stat
   }
 }
 
+// Compensated (Neumaier) FP32 running sum: s + c carries the sum of the
+// values to O(n eps^2), so the per-thread mass partials need no FP64 adds
+// (an FP64 add per cell and field would load the FP64 pipe, ~1/64 of FP32).
+struct FSum {
+  float s = 0.0f, c = 0.0f;
+  __device__ __forceinline__ void add(float x) {
+    const float t = s + x;
+    c += fabsf(s) >= fabsf(x) ? (s - t) + x : (x - t) + s;
+    s = t;
+  }
+  __device__ __forceinline__ double value() const { return (double)s + (double)c; }
+};
+
 template <typename T>
 __global__ void __launch_bounds__(kFThreads, 3) fused_kernel(DevParams P, StateBuf<T> B, StateBuf<T> N,
                                                           DevScalars* sc, double* mpart, int ntiles, int tiles_x) {
@@ -207,10 +220,10 @@ __global__ void __launch_bounds__(kFThreads, 3) fused_kernel(DevParams P, StateB
   __shared__ double sh[2 * (kFThreads / 32)];
   __shared__ bool last;
   const double dt = sc->dt;
-  const T dtx = T(dt * P.inv_dx), dty = T(dt * P.inv_dy);
+  const T dtx = T(dt * P.inv_dx), dty = T(dt * P.inv_dy), dtT = T(dt);
   const int tx = threadIdx.x % kFTX, ty = threadIdx.x / kFTX;  // cell of this thread (ty < TY)
   int fail = 0, iters = 0, st = 0;
-  double mh = 0.0, mz = 0.0;
+  FSum sh_h, sh_z;
   for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
     const int i0 = (t % tiles_x) * kFTX, j0 = (t / tiles_x) * kFTY;
     stage_tile(P, B, i0, j0, cells);
@@ -250,9 +263,9 @@ __global__ void __launch_bounds__(kFThreads, 3) fused_kernel(DevParams P, StateB
       if (P.friction != 0) {
         const T tau = tdiv(T(1), s[0]);
         const T qn = tsqrt(s[1] * s[1] + s[2] * s[2]);
-        T C = T(P.fric_c) * (tau * tau);
+        T C = par<T>(P.fric_c, P.f.fric_c) * (tau * tau);
         if (P.friction == 2) C = C * rcbrt64(s[0]);
-        const T den = T(1) + T(dt) * C * qn;
+        const T den = T(1) + dtT * C * qn;
         s[1] = tdiv(s[1], den);
         s[2] = tdiv(s[2], den);
       }
@@ -261,8 +274,8 @@ __global__ void __launch_bounds__(kFThreads, 3) fused_kernel(DevParams P, StateB
       const long long e = ext_index(P, i, j);
       N.h[e] = s[0]; N.hu[e] = s[1]; N.hv[e] = s[2]; N.z[e] = s[3];
       write_ghost_state(P, N, i, j, s);
-      mh += (double)s[0];
-      mz += (double)s[3];
+      sh_h.add(s[0]);
+      sh_z.add(s[3]);
     }
     __syncthreads();  // the next tile overwrites cells and fluctuations
   }
@@ -271,6 +284,7 @@ __global__ void __launch_bounds__(kFThreads, 3) fused_kernel(DevParams P, StateB
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) iters += __shfl_xor_sync(0xffffffffu, iters, o);
   if ((threadIdx.x & 31) == 0 && iters) atomicAdd(&sc->newton_iters, (unsigned long long)iters);
+  double mh = sh_h.value(), mz = sh_z.value();
   block_sum2<kFThreads>(mh, mz, sh);
   if (threadIdx.x == 0) {
     mpart[2 * blockIdx.x] = mh;

@@ -28,7 +28,6 @@ struct sve_handle {
   int dtlog_cap = 0;
   double* fixed = nullptr;
   int fixed_cap = 0;
-  int nb_iface = 0, nb_cell = 0;
   cudaGraphExec_t graph[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};  // [fixed][parity]
   // FP32 state: the fused stencil with a double-buffered state; fields[0..3]
   // always point at the current buffer, other[0..3] at the next one
@@ -37,6 +36,8 @@ struct sve_handle {
   int parity = 0;  // flips with every step (0: fields hold the buffer allocated first)
   int fgx = 0, fgy = 0;  // tiles of the fused step in x and y
   int fgrid_speed = 0, fgrid_fused = 0;  // resident blocks of its two kernels (grid-stride over the tiles)
+  int nt = 256;   // threads per block of the two-kernel step (32 or 256)
+  int nsm = 152;  // SMs of the device
   long long last_launches = 0;
   int last_steps = 0;
   // kernel timing (sve_profile): 3 events per step, read back lazily

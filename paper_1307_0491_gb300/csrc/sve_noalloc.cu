@@ -54,17 +54,16 @@ size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 // Byte layout of the scratch for one configuration (offsets from the base).
 struct Layout {
-  size_t fields[13], fx, fy, spart, mpart, sc, dtlog, total;
+  size_t fields[13], fx, fy, mpart, sc, dtlog, total;
 };
 
-Layout layout_for(const sve::DevParams& P, size_t elem, int nb_iface, int nb_cell) {
+Layout layout_for(const sve::DevParams& P, size_t elem, int nb_cell) {
   Layout L;
   size_t off = 0;
   const size_t next = (size_t)(P.nx + 2) * (size_t)(P.ny + 2);
   for (int k = 0; k < 13; ++k) { L.fields[k] = off; off = align256(off + elem * next); }
   L.fx = off; off = align256(off + 8 * elem * (size_t)P.nfx);
   L.fy = off; off = align256(off + 8 * elem * (size_t)(P.nfy > 0 ? P.nfy : 1));
-  L.spart = off; off = align256(off + sizeof(double) * (size_t)nb_iface);
   L.mpart = off; off = align256(off + 2 * sizeof(double) * (size_t)nb_cell);
   L.sc = off; off = align256(off + sizeof(sve::DevScalars));
   L.dtlog = off; off = align256(off + sizeof(double) * kDtlogEntries);
@@ -88,7 +87,6 @@ int run(const sve::DevParams& P, unsigned char* base, const Layout& L, int nb_if
   for (int k = 0; k < 13; ++k) *f[k] = (T*)(base + L.fields[k]);
   S.fx = (T*)(base + L.fx);
   S.fy = (T*)(base + L.fy);
-  double* spart = (double*)(base + L.spart);
   double* mpart = (double*)(base + L.mpart);
   sve::DevScalars* sc = (sve::DevScalars*)(base + L.sc);
   double* dtlog = (double*)(base + L.dtlog);
@@ -115,7 +113,7 @@ int run(const sve::DevParams& P, unsigned char* base, const Layout& L, int nb_if
     const int chunk = nsteps - done < kDtlogEntries ? nsteps - done : kDtlogEntries;
     if (cudaMemsetAsync(&sc->call_step, 0, sizeof(int), st) != cudaSuccess) return SVE_ERR_CUDA;
     for (int s = 0; s < chunk; ++s) {
-      sve::interface_kernel<T><<<nb_iface, sve::kThreads, 0, st>>>(P, S, sc, spart, dtlog, dtlog, 0);
+      sve::interface_kernel<T><<<nb_iface, sve::kThreads, 0, st>>>(P, S, sc, dtlog, dtlog, 0);
       sve::cell_kernel<T><<<nb_cell, sve::kThreads, 0, st>>>(P, S, sc, mpart);
     }
     done += chunk;
@@ -150,9 +148,9 @@ extern "C" int sve_step_noalloc(const sve_config* cfg, void* depth, void* hu, vo
   sve::DevParams P;
   sve_internal_make_params(cfg, &P);
   const size_t elem = cfg->precision == SVE_FP64 ? 8 : 4;
-  const int nb_iface = P.nbx + P.nby;
-  const int nb_cell = (int)(((long long)P.nx * P.ny + sve::kThreads - 1) / sve::kThreads);
-  const Layout L = layout_for(P, elem, nb_iface, nb_cell);
+  const int nb_iface = (int)sve::iface_blocks(P, sve::kThreads);
+  const int nb_cell = (int)sve::cell_blocks(P, sve::kThreads);
+  const Layout L = layout_for(P, elem, nb_cell);
   if (L.total > (size_t)SVE_NOALLOC_SCRATCH_BYTES) return SVE_ERR_NOALLOC_SIZE;
   unsigned char* base = nullptr;
   rc = scratch_address(&base);

@@ -35,7 +35,7 @@ EXPORTS = ("sve_config_default", "sve_create", "sve_set_stream", "sve_set_state"
            "sve_batch_create", "sve_batch_set_stream", "sve_batch_set_state", "sve_batch_step",
            "sve_batch_step_async", "sve_batch_get_state", "sve_batch_get_diag", "sve_batch_get_counters",
            "sve_batch_autotune", "sve_batch_set_schedule", "sve_batch_last_launch_count", "sve_batch_destroy",
-           "sve_record_forward", "sve_adjoint")
+           "sve_record_forward", "sve_adjoint", "sve_set_block_size", "sve_get_block_size")
 
 
 class sve_config(ctypes.Structure):
@@ -106,6 +106,8 @@ def load() -> ctypes.CDLL:
         "sve_batch_destroy": ([vp], None),
         "sve_record_forward": ([vp, ip, ip], ip),
         "sve_adjoint": ([vp, vp, vp, vp, vp, ip, vp, vp, vp, vp, dp], ip),
+        "sve_set_block_size": ([vp, ip], ip),
+        "sve_get_block_size": ([vp], ip),
     }
     for name, (args, res) in sig.items():
         fn = getattr(L, name)
@@ -172,6 +174,14 @@ def sve_strerror(code: int) -> str:
 
 def sve_last_launch_count(h) -> int:
     return int(load().sve_last_launch_count(h))
+
+
+def sve_set_block_size(h, threads: int) -> int:
+    return load().sve_set_block_size(h, int(threads))
+
+
+def sve_get_block_size(h) -> int:
+    return int(load().sve_get_block_size(h))
 
 
 def sve_step_async(h, nsteps: int) -> int:
@@ -398,6 +408,14 @@ class Solver:
 
     def step_async(self, nsteps: int) -> None:
         _check(sve_step_async(self.h, nsteps), "sve_step_async")
+
+    def set_block_size(self, threads: int) -> None:
+        """Threads per block of the two-kernel step: 0 (automatic), 32 or 256."""
+        _check(sve_set_block_size(self.h, threads), "sve_set_block_size")
+
+    @property
+    def block_size(self) -> int:
+        return sve_get_block_size(self.h)
 
     def sync(self) -> None:
         _check(sve_sync(self.h), "sve_sync")

@@ -39,8 +39,10 @@ def rel_err(got, ref, scale=None):
     return float(np.max(np.abs(got - ref)) / s)
 
 
-def run_gpu(w, nsteps, precision="fp64", dts=None):
+def run_gpu(w, nsteps, precision="fp64", dts=None, block_size=None):
     s = sve.Solver(w["params"], precision)
+    if block_size is not None:
+        s.set_block_size(block_size)
     s.set_state(w["h"], w["hu"], w["hv"], w["z"])
     if dts is None:
         t = s.step(nsteps)
@@ -72,12 +74,14 @@ def assert_parity(got, ref, dim, tol=TOL64, ctx=""):
     return errs
 
 
-def test_c1_dune1d_full():
-    """1D dune, N = 1000, periodic, 5000 CFL steps (the full 1D config)."""
+@pytest.mark.parametrize("block_size", [32, 256])
+def test_c1_dune1d_full(block_size):
+    """1D dune, N = 1000, periodic, 5000 CFL steps (the full 1D config), with
+    one-warp blocks (the automatic choice on this grid) and 256-thread blocks."""
     w = W.dune1d()
-    got = run_gpu(w, 5000)
+    got = run_gpu(w, 5000, block_size=block_size)
     ref = run_orc(w, 5000)
-    assert_parity(got, ref, 1, ctx="C1")
+    assert_parity(got, ref, 1, ctx=f"C1 block {block_size}")
     assert abs(got["t"] - ref["t"]) <= 1e-10 * ref["t"]
     assert np.max(np.abs(got["dts"] - ref["dts"])) <= 1e-10 * np.max(ref["dts"])
     assert got["launches"] == 2 * 5000
