@@ -283,13 +283,13 @@ def run_small1d(args, sve, W, torch):
     """Small 1D grids, where a step is a few microseconds of work and its FP64
     work has to be spread over many SMs: the 1D dune (1000 cells, periodic,
     5000 CFL steps) and the 1D antidune of Sec. 5.2 at J = 2400 (5 cm bump),
-    with one-warp blocks (the automatic choice here) and 256-thread blocks."""
+    with one-warp blocks (the automatic choice here) and 128-thread blocks."""
     out = []
     for name, w, n in (("1D dune 1000 cells periodic, Grass A_g=1e-3 m_g=3, 5000 CFL steps", W.dune1d(), 5000),
                        ("1D antidune (Sec. 5.2) 2400 cells, 5 cm bump, supercritical inflow, 5000 CFL steps",
                         W.paper_antidune1d(nx=2400, bump=0.05), 5000)):
         row = {"workload": name, "steps": n}
-        for bs in (32, 256):
+        for bs in (32, 128):
             s = sve.Solver(w["params"], "fp64")
             s.set_block_size(bs)
             s.set_state(w["h"], w["hu"], w["hv"], w["z"])
@@ -302,7 +302,7 @@ def run_small1d(args, sve, W, torch):
             s.close()
             row[f"block{bs}"] = {"steps_per_s": n / (t1 - t0), "cell_updates_per_s": n * w["params"]["nx"] / (t1 - t0),
                                  "launches": launches}
-        row["narrow_vs_wide"] = row["block32"]["steps_per_s"] / row["block256"]["steps_per_s"]
+        row["narrow_vs_wide"] = row["block32"]["steps_per_s"] / row["block128"]["steps_per_s"]
         row["time"] = "wall clock around one host-synchronous sve_step call of all steps (CUDA graphs of 16 steps)"
         out.append(row)
     return out

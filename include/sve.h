@@ -186,18 +186,19 @@ int sve_get_counters(sve_handle* h, long long* steps, unsigned long long* newton
 
 /* ---- launch shape of the two-kernel step -------------------------------------
  * Threads per block of the step's two kernels (interface kernel, cell
- * kernel): 256, or 32 (one warp per block) so that a small grid's work is
- * spread over more SMs -- GB300 issues ~2 FP64 operations per clock per SM,
- * and a grid of a few thousand interfaces in 256-thread blocks would occupy
- * a handful of SMs.  threads = 0 (the default at sve_create) picks 32 while
- * the 256-thread interface launch would give fewer than two blocks per SM,
- * else 256.  Results do not depend on it beyond the order of the mass sums.
- * The 2D FP32 step (a fused shared-memory stencil with its own tiling) does
- * not use it.  The step is that of Sec. 3 for every shape; the paper has no
- * counterpart of this choice.  SVE_ERR_ARG for other values. */
+ * kernel): 128 (measured fastest on large grids), 256, or 32 (one warp per
+ * block) so that a small grid's work is spread over more SMs -- GB300
+ * issues ~2 FP64 operations per clock per SM, and a grid of a few thousand
+ * interfaces in large blocks would occupy a handful of SMs.  threads = 0
+ * (the default at sve_create) picks 32 while a 256-thread interface launch
+ * would give fewer than two blocks per SM, else 128.  Results do not depend
+ * on it beyond the order of the mass sums.  The 2D FP32 step (a fused
+ * shared-memory stencil with its own tiling) does not use it.  The step is
+ * that of Sec. 3 for every shape; the paper has no counterpart of this
+ * choice.  SVE_ERR_ARG for other values. */
 int sve_set_block_size(sve_handle* h, int threads);
 
-/* Threads per block the next step call will use (32 or 256). */
+/* Threads per block the next step call will use (32, 128 or 256). */
 int sve_get_block_size(sve_handle* h);
 
 /* ---- batches of independent runs ------------------------------------------

@@ -425,10 +425,10 @@ int forward_step(sve_handle* h, double dt) {
   ADJ_TRY(cudaMemcpyAsync(h->fixed, &dt, sizeof(double), cudaMemcpyHostToDevice, h->stream));
   ADJ_TRY(cudaMemsetAsync(&h->sc->call_step, 0, sizeof(int), h->stream));
   DevState<double> S = state_of<double>(h);
-  const unsigned nbi = (unsigned)sve::iface_blocks(h->P, sve::kThreads);
-  const unsigned nbc = (unsigned)sve::cell_blocks(h->P, sve::kThreads);
-  sve::interface_kernel<double><<<nbi, sve::kThreads, 0, h->stream>>>(h->P, S, h->sc, h->fixed, h->dtlog, 1);
-  sve::cell_kernel<double><<<nbc, sve::kThreads, 0, h->stream>>>(h->P, S, h->sc, h->mpart);
+  const unsigned nbi = (unsigned)sve::iface_blocks(h->P, sve::kThreadsStep);
+  const unsigned nbc = (unsigned)sve::cell_blocks(h->P, sve::kThreadsStep);
+  sve::interface_kernel<double><<<nbi, sve::kThreadsStep, 0, h->stream>>>(h->P, S, h->sc, h->fixed, h->dtlog, 1);
+  sve::cell_kernel<double><<<nbc, sve::kThreadsStep, 0, h->stream>>>(h->P, S, h->sc, h->mpart);
   return cudaGetLastError() == cudaSuccess ? SVE_OK : SVE_ERR_CUDA;
 }
 
@@ -505,7 +505,7 @@ int sve_adjoint(sve_handle* h, const void* lam_h, const void* lam_hu, const void
       ADJ_TRY(cudaMemsetAsync(lam + f * ncell, 0, sizeof(double) * ncell, h->stream));
   }
   DevState<double> S = state_of<double>(h);
-  const unsigned nbi = (unsigned)sve::iface_blocks(P, sve::kThreads);
+  const unsigned nbi = (unsigned)sve::iface_blocks(P, sve::kThreadsStep);
   const unsigned nbc = (unsigned)sve::cell_blocks(P, sve::kThreads);
   const int ncp = (int)r->checkpoints.size();
   for (int k = ncp - 1; k >= 0; --k) {
@@ -529,7 +529,7 @@ int sve_adjoint(sve_handle* h, const void* lam_h, const void* lam_hu, const void
       // forward fluctuations of step n (needed for the pre-friction state)
       ADJ_TRY(cudaMemcpyAsync(h->fixed, &dt, sizeof(double), cudaMemcpyHostToDevice, h->stream));
       ADJ_TRY(cudaMemsetAsync(&h->sc->call_step, 0, sizeof(int), h->stream));
-      sve::interface_kernel<double><<<nbi, sve::kThreads, 0, h->stream>>>(P, S, h->sc, h->fixed, h->dtlog, 1);
+      sve::interface_kernel<double><<<nbi, sve::kThreadsStep, 0, h->stream>>>(P, S, h->sc, h->fixed, h->dtlog, 1);
       adj_friction_kernel<<<nb_c, kAdjThreads, 0, h->stream>>>(P, S, lam, r->mu, dt, r->gpart, r->gacc, r->done);
       adj_interface_kernel<<<nb_if, kAdjThreads, 0, h->stream>>>(P, S, r->mu, dt, h->cfg.A_g, h->cfg.m_g,
                                                                  r->gpart, r->gacc, r->done);

@@ -125,11 +125,15 @@ void launch_step(sve_handle* h, cudaStream_t st, int fixed, cudaEvent_t* ev) {
   if (ev) cudaEventRecord(ev[0], st);
   if (nt == sve::kThreadsNarrow)
     sve::interface_kernel<T, sve::kThreadsNarrow><<<nbi, nt, 0, st>>>(h->P, S, h->sc, h->fixed, h->dtlog, fixed);
+  else if (nt == sve::kThreadsStep)
+    sve::interface_kernel<T, sve::kThreadsStep><<<nbi, nt, 0, st>>>(h->P, S, h->sc, h->fixed, h->dtlog, fixed);
   else
     sve::interface_kernel<T, sve::kThreads><<<nbi, nt, 0, st>>>(h->P, S, h->sc, h->fixed, h->dtlog, fixed);
   if (ev) cudaEventRecord(ev[1], st);
   if (nt == sve::kThreadsNarrow)
     sve::cell_kernel<T, sve::kThreadsNarrow><<<nbc, nt, 0, st>>>(h->P, S, h->sc, h->mpart);
+  else if (nt == sve::kThreadsStep)
+    sve::cell_kernel<T, sve::kThreadsStep><<<nbc, nt, 0, st>>>(h->P, S, h->sc, h->mpart);
   else
     sve::cell_kernel<T, sve::kThreads><<<nbc, nt, 0, st>>>(h->P, S, h->sc, h->mpart);
   if (ev) cudaEventRecord(ev[2], st);
@@ -253,8 +257,21 @@ int enqueue_steps(sve_handle* h, int nsteps, int fixed) {
   return SVE_OK;
 }
 
+// Mass sums of the last step (or upload) from its per-block partials, in a
+// fixed order (one block; launched when the diagnostics are read).
+__global__ void __launch_bounds__(sve::kThreads) mass_kernel(DevParams P, DevScalars* sc, const double* mpart) {
+  __shared__ double sh[2 * (sve::kThreads / 32)];
+  double a, b;
+  sve::reduce_partials<sve::kThreads>(mpart, sc->mass_parts, a, b, sh);
+  if (threadIdx.x == 0) {
+    const double cell = P.dx * (P.dim == 2 ? P.dy : 1.0);
+    sc->mass_h = a * cell;
+    sc->mass_z = b * cell;
+  }
+}
+
 int auto_block_size(const sve_handle* h) {
-  return sve::iface_blocks(h->P, sve::kThreads) < 2LL * h->nsm ? sve::kThreadsNarrow : sve::kThreads;
+  return sve::iface_blocks(h->P, sve::kThreads) < 2LL * h->nsm ? sve::kThreadsNarrow : sve::kThreadsStep;
 }
 
 int wait_status(sve_handle* h) {
@@ -321,9 +338,10 @@ int sve_create(const sve_config* cfg, sve_handle** out) {
   if (cudaGetDevice(&h->device) != cudaSuccess) { delete h; return SVE_ERR_CUDA; }
   h->elem = cfg->precision == SVE_FP64 ? 8 : 4;
   h->next = (long long)(h->P.nx + 2) * (h->P.ny + 2);
-  // block size of the two-kernel step: one warp per block while the grid is
-  // too small to give every SM two 256-thread blocks (GB300 issues ~2 FP64
-  // operations per clock per SM, so a small grid's FP64 work has to spread)
+  // block size of the two-kernel step: 128 threads, or one warp per block
+  // while the grid is too small to give every SM two 256-thread blocks
+  // (GB300 issues ~2 FP64 operations per clock per SM, so a small grid's FP64
+  // work has to spread over many SMs)
   {
     int nsm = 0;
     if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, h->device) != cudaSuccess) nsm = 152;
@@ -445,6 +463,9 @@ int sve_get_state(sve_handle* h, void* depth, void* hu, void* hv, void* zb, int 
 int sve_get_diag(sve_handle* h, double* mass_h, double* mass_z, double* t, double* last_dt) {
   if (!h) return SVE_ERR_ARG;
   if (!h->has_state) return SVE_ERR_STATE;
+  // the mass sums of the last step, from its per-block partials
+  mass_kernel<<<1, sve::kThreads, 0, h->stream>>>(h->P, h->sc, h->mpart);
+  SVE_TRY(cudaGetLastError());
   DevScalars s;
   SVE_TRY(cudaMemcpyAsync(&s, h->sc, sizeof(s), cudaMemcpyDeviceToHost, h->stream));
   SVE_TRY(cudaStreamSynchronize(h->stream));
@@ -504,7 +525,8 @@ const char* sve_strerror(int code) {
 
 int sve_set_block_size(sve_handle* h, int threads) {
   if (!h) return SVE_ERR_ARG;
-  if (threads != 0 && threads != sve::kThreadsNarrow && threads != sve::kThreads) return SVE_ERR_ARG;
+  if (threads != 0 && threads != sve::kThreadsNarrow && threads != sve::kThreadsStep && threads != sve::kThreads)
+    return SVE_ERR_ARG;
   const int nt = threads == 0 ? auto_block_size(h) : threads;
   if (nt != h->nt) drop_graphs(h);  // the captured steps hold the launch shape
   h->nt = nt;

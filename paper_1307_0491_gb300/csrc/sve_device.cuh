@@ -69,6 +69,7 @@ struct DevScalars {
   long long steps;      // total steps since the state was set
   unsigned long long newton_iters;  // Newton updates summed over all solves since the state was set
   unsigned long long smax_bits[2];  // running max of the x / y wave speeds of the step (bit patterns; 0 between steps)
+  unsigned int mass_parts;  // per-block (h, z) partials of the last step or upload, summed on read-out (mass_kernel)
 };
 
 // Ghost-padded state and projection (SoA) of precision T.
@@ -643,8 +644,13 @@ __device__ __forceinline__ void reduce_partials(const double* mpart, unsigned nb
 
 // ---- kernels -------------------------------------------------------------
 
-constexpr int kThreads = 256;  // block size of the grid kernels on large grids
+constexpr int kThreads = 256;       // block size of the one-off kernels (state upload, projection)
+constexpr int kThreadsStep = 128;   // the step's two kernels on large grids (measured best on GB300)
 constexpr int kThreadsNarrow = 32;  // on small grids: one warp per block spreads the FP64 work over more SMs
+// Occupancy hint of the interface kernel: at 128 threads, 5 blocks per SM
+// (<= 102 registers, 20 warps) measured 1.3 % faster than the unconstrained
+// 114 registers (4 blocks); 6 blocks (80 registers) spilled and lost 7 %.
+template <int NT> struct iface_min_blocks { static constexpr int value = NT == 128 ? 5 : 1; };
 
 // Blocks of interface_kernel<T, NT> and cell_kernel<T, NT> for a grid.
 inline long long iface_blocks(const DevParams& P, int nt) {
@@ -731,10 +737,15 @@ __device__ __forceinline__ void block_maxbits_sum(double& v, int& n) {
 // nby) the y-interfaces (i, j - 1/2), i in [0, nx), j in [0, ny] (nbx, nby =
 // the interface counts over NT, rounded up).  The last block to finish turns
 // the step's maximal speeds into its time step.
-template <typename T, int NT = kThreads>
-__global__ void __launch_bounds__(NT) interface_kernel(DevParams P, DevState<T> S, DevScalars* sc,
+template <typename T, int NT = kThreadsStep>
+__global__ void __launch_bounds__(NT, iface_min_blocks<NT>::value) interface_kernel(DevParams P, DevState<T> S, DevScalars* sc,
                                                        const double* fixed_dts, double* dtlog, int fixed) {
-  __shared__ bool last;
+  // block tallies: the block's maximal speed (bit pattern) and Newton
+  // updates, and how many of its warps have added theirs
+  __shared__ unsigned long long s_bits;
+  __shared__ unsigned int s_its, s_warps;
+  if (threadIdx.x == 0) { s_bits = 0ull; s_its = 0u; s_warps = 0u; }
+  __syncthreads();
   const unsigned nbx = (unsigned)((P.nfx + NT - 1) / NT);
   const bool ydir = blockIdx.x >= nbx;
   const long long k = (long long)(ydir ? blockIdx.x - nbx : blockIdx.x) * NT + threadIdx.x;
@@ -743,21 +754,33 @@ __global__ void __launch_bounds__(NT) interface_kernel(DevParams P, DevState<T> 
   if (k < (ydir ? P.nfy : P.nfx)) {
     if (!interface_item(P, S, ydir, k, smax, iters)) atomicOr(&sc->status, ST_RIEMANN);
   }
-  // block max of the (non-negative) speeds and sum of the Newton updates,
-  // both on integers (off the FP64 pipe); the block max then goes into the
-  // step's running maximum by an atomic max on the bit pattern (integer
-  // order = IEEE order for non-negative doubles; a max is order-free, so
-  // the result does not depend on the order the blocks finish in)
-  block_maxbits_sum<NT>(smax, iters);
-  if (threadIdx.x == 0) {
-    atomicAdd(&sc->newton_iters, (unsigned long long)iters);
-    atomicMax(&sc->smax_bits[ydir ? 1 : 0], (unsigned long long)__double_as_longlong(smax));
-    __threadfence();
-    const unsigned int ticket = atomicAdd(&sc->done_iface, 1u);
-    last = (ticket == gridDim.x - 1);
+  // Max of the (non-negative) speeds and sum of the Newton updates, on
+  // integers (off the FP64 pipe): over the warp by shuffles, over the block
+  // by shared-memory atomics, with no block barrier -- a warp whose Newton
+  // loops ended early retires instead of waiting for the slowest warp.  The
+  // last warp of the block folds the block's tallies into the step's running
+  // maximum (atomic max on the bit pattern: integer order = IEEE order for
+  // non-negative doubles; a max is order-free, so the result does not depend
+  // on the order the blocks finish in).
+  long long bits = __double_as_longlong(smax);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const long long ob = __shfl_xor_sync(0xffffffffu, bits, o);
+    bits = ob > bits ? ob : bits;
+    iters += __shfl_xor_sync(0xffffffffu, iters, o);
   }
-  __syncthreads();
-  if (!last || threadIdx.x != 0) return;
+  if ((threadIdx.x & 31) != 0) return;
+  atomicMax(&s_bits, (unsigned long long)bits);
+  atomicAdd(&s_its, (unsigned int)iters);
+  __threadfence_block();
+  if (atomicAdd(&s_warps, 1u) != NT / 32 - 1) return;
+  // last warp of the block
+  __threadfence_block();
+  const unsigned long long bb = atomicMax(&s_bits, 0ull);
+  atomicAdd(&sc->newton_iters, (unsigned long long)atomicAdd(&s_its, 0u));
+  atomicMax(&sc->smax_bits[ydir ? 1 : 0], bb);
+  __threadfence();
+  if (atomicAdd(&sc->done_iface, 1u) != gridDim.x - 1) return;
   // last block: take the maxima (and reset them for the next step)
   __threadfence();
   const double sx = __longlong_as_double((long long)atomicExch(&sc->smax_bits[0], 0ull));
@@ -838,10 +861,13 @@ __device__ __forceinline__ int cell_item(const DevParams& P, const DevState<T>& 
 
 // One thread per interior cell (i, j): Godunov average in fluctuation form,
 // friction, checks, projection of the new state, ghosts, mass partials.
-template <typename T, int NT = kThreads>
+template <typename T, int NT = kThreadsStep>
 __global__ void __launch_bounds__(NT) cell_kernel(DevParams P, DevState<T> S, DevScalars* sc, double* mpart) {
-  __shared__ double sh[2 * (NT / 32)];
-  __shared__ bool last;
+  // per-thread (h, z) of the new state, and how many warps have stored theirs
+  __shared__ double s_m[2][NT];
+  __shared__ unsigned int s_warps;
+  if (threadIdx.x == 0) s_warps = 0u;
+  __syncthreads();
   const long long k = (long long)blockIdx.x * NT + threadIdx.x;
   const long long ncell = (long long)P.nx * P.ny;
   double mh = 0.0, mz = 0.0;
@@ -849,29 +875,40 @@ __global__ void __launch_bounds__(NT) cell_kernel(DevParams P, DevState<T> S, De
     const int st = cell_item(P, S, k, sc->dt, mh, mz);
     if (st) atomicOr(&sc->status, st);
   }
-  block_sum2<NT>(mh, mz, sh);
-  if (threadIdx.x == 0) {
-    mpart[2 * blockIdx.x] = mh;
-    mpart[2 * blockIdx.x + 1] = mz;
-    __threadfence();
-    const unsigned int ticket = atomicAdd(&sc->done_cell, 1u);
-    last = (ticket == gridDim.x - 1);
+  // The block's mass partial, in a fixed order and with no block barrier:
+  // the last warp to store its values (shared-memory ticket) adds all NT
+  // (lane l: values l, l + 32, ..., then a shuffle tree) and writes the
+  // partial; the step's mass sums are taken from the partials on read-out.
+  s_m[0][threadIdx.x] = mh;
+  s_m[1][threadIdx.x] = mz;
+  __syncwarp();
+  unsigned int w = 0u;
+  if ((threadIdx.x & 31) == 0) {
+    __threadfence_block();
+    w = atomicAdd(&s_warps, 1u);
   }
-  __syncthreads();
-  if (!last) return;
+  w = __shfl_sync(0xffffffffu, w, 0);
+  if (w != NT / 32 - 1) return;
+  __threadfence_block();
+  const int lane = threadIdx.x & 31;
+  double a = 0.0, b = 0.0;
+#pragma unroll
+  for (int q = 0; q < NT / 32; ++q) { a += s_m[0][lane + 32 * q]; b += s_m[1][lane + 32 * q]; }
+  a = warp_sum(a);
+  b = warp_sum(b);
+  if (lane != 0) return;
+  mpart[2 * blockIdx.x] = a;
+  mpart[2 * blockIdx.x + 1] = b;
   __threadfence();
-  double sh_h, sh_z;
-  reduce_partials<NT>(mpart, gridDim.x, sh_h, sh_z, sh);
-  if (threadIdx.x == 0) {
-    const double cell = P.dx * (P.dim == 2 ? P.dy : 1.0);
-    sc->mass_h = sh_h * cell;
-    sc->mass_z = sh_z * cell;
-    sc->t += sc->dt;
-    sc->call_step += 1;
-    sc->steps += 1;
-    sc->done_cell = 0u;
-  }
+  if (atomicAdd(&sc->done_cell, 1u) != gridDim.x - 1) return;
+  // last block: the step is complete
+  sc->mass_parts = gridDim.x;
+  sc->t += sc->dt;
+  sc->call_step += 1;
+  sc->steps += 1;
+  sc->done_cell = 0u;
 }
+
 
 // Initialisation: every padded cell; interior cells are projected from the
 // state as stored, ghost cells get their rule from the adjacent / periodic
@@ -904,16 +941,9 @@ __global__ void __launch_bounds__(kThreads) init_kernel(DevParams P, DevState<T>
     last = (ticket == gridDim.x - 1);
   }
   __syncthreads();
-  if (!last) return;
-  __threadfence();
-  double sh_h, sh_z;
-  reduce_partials<kThreads>(mpart, gridDim.x, sh_h, sh_z, sh);
-  if (threadIdx.x == 0) {
-    const double cell = P.dx * (P.dim == 2 ? P.dy : 1.0);
-    sc->mass_h = sh_h * cell;
-    sc->mass_z = sh_z * cell;
-    sc->done_cell = 0u;
-  }
+  if (!last || threadIdx.x != 0) return;
+  sc->mass_parts = gridDim.x;
+  sc->done_cell = 0u;
 }
 
 }  // namespace sve

@@ -108,13 +108,13 @@ int run(const sve::DevParams& P, unsigned char* base, const Layout& L, int nb_if
     if (cudaMemcpy2DAsync(dst, pitch, user[k], row, row, P.ny, cudaMemcpyDeviceToDevice, st) != cudaSuccess)
       return SVE_ERR_CUDA;
   }
-  sve::init_kernel<T><<<nb_cell, sve::kThreads, 0, st>>>(P, S, sc, mpart);
+  sve::init_kernel<T><<<(unsigned)sve::cell_blocks(P, sve::kThreads), sve::kThreads, 0, st>>>(P, S, sc, mpart);
   for (int done = 0; done < nsteps;) {
     const int chunk = nsteps - done < kDtlogEntries ? nsteps - done : kDtlogEntries;
     if (cudaMemsetAsync(&sc->call_step, 0, sizeof(int), st) != cudaSuccess) return SVE_ERR_CUDA;
     for (int s = 0; s < chunk; ++s) {
-      sve::interface_kernel<T><<<nb_iface, sve::kThreads, 0, st>>>(P, S, sc, dtlog, dtlog, 0);
-      sve::cell_kernel<T><<<nb_cell, sve::kThreads, 0, st>>>(P, S, sc, mpart);
+      sve::interface_kernel<T><<<nb_iface, sve::kThreadsStep, 0, st>>>(P, S, sc, dtlog, dtlog, 0);
+      sve::cell_kernel<T><<<nb_cell, sve::kThreadsStep, 0, st>>>(P, S, sc, mpart);
     }
     done += chunk;
   }
@@ -148,8 +148,8 @@ extern "C" int sve_step_noalloc(const sve_config* cfg, void* depth, void* hu, vo
   sve::DevParams P;
   sve_internal_make_params(cfg, &P);
   const size_t elem = cfg->precision == SVE_FP64 ? 8 : 4;
-  const int nb_iface = (int)sve::iface_blocks(P, sve::kThreads);
-  const int nb_cell = (int)sve::cell_blocks(P, sve::kThreads);
+  const int nb_iface = (int)sve::iface_blocks(P, sve::kThreadsStep);
+  const int nb_cell = (int)sve::cell_blocks(P, sve::kThreadsStep);
   const Layout L = layout_for(P, elem, nb_cell);
   if (L.total > (size_t)SVE_NOALLOC_SCRATCH_BYTES) return SVE_ERR_NOALLOC_SIZE;
   unsigned char* base = nullptr;

@@ -410,7 +410,7 @@ class Solver:
         _check(sve_step_async(self.h, nsteps), "sve_step_async")
 
     def set_block_size(self, threads: int) -> None:
-        """Threads per block of the two-kernel step: 0 (automatic), 32 or 256."""
+        """Threads per block of the two-kernel step: 0 (automatic), 32, 128 or 256."""
         _check(sve_set_block_size(self.h, threads), "sve_set_block_size")
 
     @property

@@ -67,7 +67,7 @@ def parity(got, ref, dim, tol=TOL64, ctx=""):
 
 
 def test_automatic_block_size():
-    # 1001 interfaces: one warp per block; 1024 x 512: 256 threads
+    # 1001 interfaces: one warp per block; 1024 x 512: 128 threads
     s = sve.Solver(W.dune1d()["params"], "fp64")
     assert s.block_size == 32
     s.set_block_size(256)
@@ -79,7 +79,7 @@ def test_automatic_block_size():
     assert e.value.code == sve.SVE_ERR_ARG
     s.close()
     s = sve.Solver(W.dune2d()["params"], "fp64")
-    assert s.block_size == 256
+    assert s.block_size == 128
     s.close()
 
 
@@ -94,9 +94,12 @@ def test_block_sizes_match_oracle_and_each_other(w, n):
     dim = w["params"]["dim"]
     a = run(w, n, 32)
     b = run(w, n, 256)
+    c = run(w, n, 128)
     ref = orc_run(w, n)
     parity(a, ref, dim, ctx="32")
     parity(b, ref, dim, ctx="256")
+    parity(c, ref, dim, ctx="128")
+    assert rel(c["dts"], b["dts"]) <= 1e-13
     # the same per-item code: identical time steps, states to round-off
     assert rel(a["dts"], b["dts"]) <= 1e-13
     for k in ("h", "hu", "z"):
@@ -115,7 +118,7 @@ def test_block_size_change_between_calls():
     w = W.dune1d(nx=500)
     s = sve.Solver(w["params"], "fp64")
     s.set_state(w["h"], w["hu"], w["hv"], w["z"])
-    for bs in (32, 256, 32, 256):
+    for bs in (32, 256, 128, 32):
         s.set_block_size(bs)
         s.step(40)
     got = s.get_state()
