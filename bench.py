@@ -308,6 +308,30 @@ def run_small1d(args, sve, W, torch):
     return out
 
 
+def run_closures(args, sve, W, torch):
+    """Each Shields-parameter transport law of Sec. 2 on the antidune physics
+    (2048 x 1024 crop of the antidune config: supercritical inflow, random
+    bed, Darcy-Weisbach tau*, tau* ~ 1), FP64, 50 timed CFL steps after 20."""
+    out = []
+    for law in ("mpm", "flvb", "nielsen", "ribberink", "camenen"):
+        w = W.antidune2d(nx=2048, ny=1024, seed=0)
+        w["params"].update(bedload=law)
+        s = sve.Solver(w["params"], "fp64")
+        s.set_state(w["h"], w["hu"], w["hv"], w["z"])
+        s.step(20)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        s.step(50)
+        t1 = time.perf_counter()
+        its = s.counters()["newton_iters"]
+        s.close()
+        cells = 2048 * 1024
+        out.append({"law": law, "value": cells * 50 / (t1 - t0), "unit": UNIT, "ms_per_step": (t1 - t0) / 50 * 1e3,
+                    "newton_updates_per_solve": its / (70 * ((2049 * 1024) + (2048 * 1025)))})
+    return {"workload": "antidune physics 2048x1024 (24 x 12 m), FP64, per transport law", "steps": 50,
+            "time": "wall clock around one host-synchronous sve_step call", "laws": out}
+
+
 def run_ours(args, world, rank, local):
     import torch
 
@@ -446,6 +470,8 @@ def run_ours(args, world, rank, local):
             line["adjoint"] = run_adjoint(args, sve, W, torch)
         if not args.no_small1d:
             line["small1d"] = run_small1d(args, sve, W, torch)
+        if not args.no_closures:
+            line["closures"] = run_closures(args, sve, W, torch)
         if world == 1 and not args.no_cpu_baseline:
             rate, nsteps, secs = cpu_oracle_rate(w)
             line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
@@ -473,6 +499,7 @@ def main():
     ap.add_argument("--no-batch-fp32", action="store_true", help="skip the FP32-state ensemble")
     ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint measurement")
     ap.add_argument("--no-small1d", action="store_true", help="skip the small-1D measurement")
+    ap.add_argument("--no-closures", action="store_true", help="skip the per-transport-law measurement")
     ap.add_argument("--workload", choices=["dune2d", "antidune2d"], default="dune2d")
     ap.add_argument("--precision", choices=["fp64", "fp32"], default="fp64")
     ap.add_argument("--nx", type=int, default=0, help="grid override (profiling captures)")

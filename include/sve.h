@@ -55,7 +55,8 @@ enum {
 };
 
 enum { SVE_FP64 = 0, SVE_FP32 = 1 };                       /* state precision */
-enum { SVE_GRASS = 0, SVE_MPM = 1 };                       /* bedload law */
+/* bedload law: Grass, or a Shields-parameter law of Sec. 2 */
+enum { SVE_GRASS = 0, SVE_MPM = 1, SVE_FLVB = 2, SVE_NIELSEN = 3, SVE_RIBBERINK = 4, SVE_CAMENEN = 5 };
 enum { SVE_FRIC_NONE = 0, SVE_FRIC_DARCY = 1, SVE_FRIC_STRICKLER = 2 };
 enum { SVE_BC_PERIODIC = 0, SVE_BC_FREE = 1, SVE_BC_INFLOW_Q = 2, SVE_BC_INFLOW_QH = 3, SVE_BC_WALL = 4 };
 enum { SVE_HOST = 0, SVE_DEVICE = 1 };
@@ -71,10 +72,17 @@ enum { SVE_W = 0, SVE_E = 1, SVE_S = 2, SVE_N = 3 };
  *               the extreme relaxation wave speeds |u - a/h|, |u + a/h|.
  * precision     SVE_FP64 or SVE_FP32 (state storage and arithmetic).
  * bedload       SVE_GRASS: q_b = A_g u |u|^(m_g - 1) (Eq. bedload Grass, 2D:
- *               vector u); SVE_MPM: Meyer-Peter & Mueller (Eq. MPM) with
- *               tau* from the friction law (non-dimensional form of Sec. 2).
+ *               vector u).  The Shields-parameter laws (non-dimensional form
+ *               of Sec. 2: q_b = sqrt((s-1) g d_s^3) q*(tau*) along u/|u|,
+ *               tau* from the friction law), x = (tau* - tau_cr)_+:
+ *               SVE_MPM 8 x^1.5 (Eq. MPM); SVE_FLVB 5.7 x^1.5 (Eq. FLVB);
+ *               SVE_NIELSEN 12 sqrt(tau*) x (Eq. Nielsen); SVE_RIBBERINK
+ *               11 x^1.65 (Eq. Ribberink); SVE_CAMENEN 12 tau*^1.5
+ *               exp(-4.5 tau_cr / tau*) (Eq. Camenen).  They need a friction
+ *               law.
  * A_g, m_g      Grass constants (1 <= m_g <= 4).
- * s, d_s, tau_cr  MPM: relative density, grain diameter [m], critical Shields.
+ * s, d_s, tau_cr  Shields laws: relative density, grain diameter [m],
+ *               critical Shields number.
  * friction      SVE_FRIC_NONE / _DARCY (f_dw) / _STRICKLER (K_st = 1/n).
  * bc[4]         W, E, S, N ghost rules: PERIODIC (both sides of an axis),
  *               FREE (copy), INFLOW_Q (inward normal discharge q_in, h and

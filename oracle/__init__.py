@@ -37,7 +37,7 @@ _SRC = os.path.join(_HERE, "sve_oracle.c")
 _BUILD = os.path.join(_HERE, "_build")
 _LIB_PATH = os.path.join(_BUILD, "libsve_oracle.so")
 
-GRASS, MPM = 0, 1
+GRASS, MPM, FLVB, NIELSEN, RIBBERINK, CAMENEN = 0, 1, 2, 3, 4, 5
 FRIC_NONE, FRIC_DARCY, FRIC_STRICKLER = 0, 1, 2
 BC_PERIODIC, BC_FREE, BC_INFLOW_Q, BC_INFLOW_QH, BC_WALL = 0, 1, 2, 3, 4
 
@@ -128,7 +128,8 @@ class Params:
     def from_workload(d: dict) -> "Params":
         """Map a workload parameter dict (string-valued enums) to the
         oracle's own codes."""
-        bedload = {"grass": GRASS, "mpm": MPM}
+        bedload = {"grass": GRASS, "mpm": MPM, "flvb": FLVB, "nielsen": NIELSEN, "ribberink": RIBBERINK,
+                   "camenen": CAMENEN}
         friction = {"none": FRIC_NONE, "darcy": FRIC_DARCY, "strickler": FRIC_STRICKLER}
         bc = {"periodic": BC_PERIODIC, "free": BC_FREE, "inflow_q": BC_INFLOW_Q, "inflow_qh": BC_INFLOW_QH,
               "wall": BC_WALL}

@@ -78,7 +78,9 @@
  *   R8  Meyer-Peter & Mueller (Eq. MPM): q_b = sqrt((s-1) g d_s^3) *
  *       8 (tau* - tau*_cr)_+^(3/2) in the direction of the velocity, with
  *       tau* from the friction law: f |U|^2 / (8 g (s-1) d_s) (Darcy) or
- *       n^2 |U|^2 / ((s-1) d_s h^(1/3)) (Manning).
+ *       n^2 |U|^2 / ((s-1) d_s h^(1/3)) (Manning).  The other laws of the
+ *       list in Sec. 2 (Eqs. FLVB, Nielsen, Ribberink, Camenen) replace the
+ *       non-dimensional rate q* in the same way.
  */
 #include <math.h>
 #include <stddef.h>
@@ -86,7 +88,9 @@
 #include <stdlib.h>
 
 /* ---- parameters (own definition; mirrors nothing) ---------------------- */
-enum { ORC_GRASS = 0, ORC_MPM = 1 };
+/* transport laws of Sec. 2: Grass, then the Shields-parameter laws of
+ * Eqs. MPM, FLVB, Nielsen, Ribberink, Camenen */
+enum { ORC_GRASS = 0, ORC_MPM = 1, ORC_FLVB = 2, ORC_NIELSEN = 3, ORC_RIBBERINK = 4, ORC_CAMENEN = 5 };
 enum { ORC_FRIC_NONE = 0, ORC_FRIC_DARCY = 1, ORC_FRIC_STRICKLER = 2 };
 enum { ORC_BC_PERIODIC = 0, ORC_BC_FREE = 1, ORC_BC_INFLOW_Q = 2, ORC_BC_INFLOW_QH = 3, ORC_BC_WALL = 4 };
 enum {
@@ -128,12 +132,57 @@ static double orc_speed_pow(double speed2, double speed, double k) {
   return pow(speed, k);
 }
 
+/* Non-dimensional transport rate q*_b(tau*) of the laws listed in Sec. 2 and
+ * its derivative dq*_b/dtau*; tcr = tau*_cr.  (x)_+ = max(x, 0).
+ *   MPM (Eq. MPM):          q* = 8   (tau* - tcr)_+^(3/2)
+ *   FLvB (Eq. FLVB):        q* = 5.7 (tau* - tcr)_+^(3/2)
+ *   Nielsen (Eq. Nielsen):  q* = 12 sqrt(tau*) (tau* - tcr)_+
+ *   Ribberink (Eq. Ribberink): q* = 11 (tau* - tcr)_+^1.65
+ *   Camenen (Eq. Camenen):  q* = 12 tau*^(3/2) exp(-4.5 tcr / tau*)
+ * (no threshold; 0 at tau* = 0). */
+static void orc_qstar(int law, double ts, double tcr, double* q, double* dq) {
+  *q = 0.0;
+  *dq = 0.0;
+  if (law == ORC_CAMENEN) {
+    if (ts <= 0.0) return;
+    double e = exp(-4.5 * tcr / ts);
+    *q = 12.0 * ts * sqrt(ts) * e;
+    /* d/dts: 12 e [1.5 sqrt(ts) + ts^(3/2) 4.5 tcr / ts^2] */
+    *dq = 12.0 * e * (1.5 * sqrt(ts) + 4.5 * tcr / sqrt(ts));
+    return;
+  }
+  double x = ts - tcr;
+  if (x <= 0.0) return;
+  switch (law) {
+    case ORC_MPM:
+      *q = 8.0 * x * sqrt(x);
+      *dq = 8.0 * 1.5 * sqrt(x);
+      break;
+    case ORC_FLVB:
+      *q = 5.7 * x * sqrt(x);
+      *dq = 5.7 * 1.5 * sqrt(x);
+      break;
+    case ORC_NIELSEN:
+      *q = 12.0 * sqrt(ts) * x;
+      *dq = 12.0 * (x / (2.0 * sqrt(ts)) + sqrt(ts));
+      break;
+    case ORC_RIBBERINK:
+      *q = 11.0 * pow(x, 1.65);
+      *dq = 11.0 * 1.65 * pow(x, 0.65);
+      break;
+    default:
+      break;
+  }
+}
+
 /* Bedload flux normal component Omega = Q_s . n and its derivative with
  * respect to the normal velocity at fixed H (needed by the bound on b in
  * Eq. ab).  un, ut: normal and tangential velocity.
  *   Grass (Eq. bedload Grass, 2D form q_b = A_g U |U|^(m_g-1)):
  *     Q = A_g un |U|^(m-1),  dQ/dun = A_g (|U|^(m-1) + (m-1) un^2 |U|^(m-3))
- *   MPM (Eq. MPM with the non-dimensional form of Sec. 2), reading R8. */
+ *   Shields-parameter laws (Eqs. MPM, FLVB, Nielsen, Ribberink, Camenen
+ *     with the non-dimensional form of Sec. 2), reading R8:
+ *     Q = sqrt((s-1) g d_s^3) q*(tau*) un/|U|, tau* = alpha |U|^2. */
 static void orc_closure(const orc_params* P, double H, double un, double ut, double* Q, double* dQ) {
   double speed2 = un * un + ut * ut;
   if (P->bedload == ORC_GRASS) {
@@ -155,8 +204,10 @@ static void orc_closure(const orc_params* P, double H, double un, double ut, dou
     *dQ = P->A_g * (pm1 + second);
     return;
   }
-  /* Meyer-Peter & Mueller */
-  double alpha; /* tau* = alpha |U|^2 */
+  /* Shields-parameter laws: Q_b = q*(tau*) sqrt((s-1) g d_s^3) along U/|U|,
+   * tau* = tau_b / ((rho_s - rho) g d_s) with tau_b = rho g h S_f (Sec. 2),
+   * i.e. tau* = alpha |U|^2 for the friction law in use */
+  double alpha;
   double sm1 = P->s - 1.0;
   if (P->friction == ORC_FRIC_DARCY) {
     alpha = P->f_dw / (8.0 * P->g * sm1 * P->d_s);
@@ -165,22 +216,21 @@ static void orc_closure(const orc_params* P, double H, double un, double ut, dou
     alpha = (n * n) / (sm1 * P->d_s * cbrt(H));
   }
   double tstar = alpha * speed2;
-  double theta = tstar - P->tau_cr;
-  if (speed2 == 0.0 || theta <= 0.0) {
+  double qs, dqs; /* q* at tau* and its derivative in tau* */
+  orc_qstar(P->bedload, tstar, P->tau_cr, &qs, &dqs);
+  if (speed2 == 0.0 || (qs == 0.0 && dqs == 0.0)) {
     *Q = 0.0;
     *dQ = 0.0;
     return;
   }
   double speed = sqrt(speed2);
-  double Cm = 8.0 * sqrt(sm1 * P->g * P->d_s * P->d_s * P->d_s);
-  double sth = sqrt(theta);
-  double th32 = theta * sth;
-  *Q = Cm * th32 * (un / speed);
-  /* d/dun [theta^(3/2) un/|U|] = 3/2 theta^(1/2) (2 alpha un) un/|U|
-   *                            + theta^(3/2) ut^2/|U|^3 */
-  double d1 = 3.0 * sth * alpha * (un * un) / speed;
-  double d2 = th32 * (ut * ut) / (speed2 * speed);
-  *dQ = Cm * (d1 + d2);
+  double Cs = sqrt(sm1 * P->g * P->d_s * P->d_s * P->d_s);
+  *Q = Cs * qs * (un / speed);
+  /* d/dun [q*(alpha |U|^2) un/|U|] = q*'(tau*) (2 alpha un) un/|U|
+   *                                 + q*(tau*) ut^2/|U|^3 */
+  double d1 = 2.0 * dqs * alpha * (un * un) / speed;
+  double d2 = qs * (ut * ut) / (speed2 * speed);
+  *dQ = Cs * (d1 + d2);
 }
 
 /* ---- equilibrium projection (lambda -> 0 in Eqs. relaxpi, relaxqs) ---- */
@@ -680,9 +730,10 @@ static int orc_check_params(const orc_params* P) {
   if (!(P->kappa_a > 1.0) || !(P->beta_min > 0.0) || !(P->gamma_z >= 0.0) || !(P->newton_tol > 0.0) ||
       P->newton_maxit < 1)
     return ORC_ERR_ARG;
-  if (P->bedload != ORC_GRASS && P->bedload != ORC_MPM) return ORC_ERR_ARG;
+  if (P->bedload < ORC_GRASS || P->bedload > ORC_CAMENEN) return ORC_ERR_ARG;
   if (P->bedload == ORC_GRASS && (P->m_g < 1.0 || P->A_g < 0.0)) return ORC_ERR_ARG;
-  if (P->bedload == ORC_MPM && P->friction == ORC_FRIC_NONE) return ORC_ERR_ARG;
+  if (P->bedload != ORC_GRASS && (P->friction == ORC_FRIC_NONE || !(P->s > 1.0) || !(P->d_s > 0.0)))
+    return ORC_ERR_ARG;
   if (P->friction == ORC_FRIC_STRICKLER && !(P->K_st > 0.0)) return ORC_ERR_ARG;
   for (int s = 0; s < (P->dim == 2 ? 4 : 2); ++s) {
     if (P->bc[s] < 0 || P->bc[s] > ORC_BC_WALL) return ORC_ERR_ARG;

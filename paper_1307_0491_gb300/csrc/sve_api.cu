@@ -46,10 +46,10 @@ int validate(const sve_config* c) {
   if ((long long)c->nx * c->ny > (1LL << 31) - 1) return SVE_ERR_ARG;
   if (!(c->lx > 0) || (c->dim == 2 && !(c->ly > 0)) || !(c->g > 0) || !(c->cfl > 0)) return SVE_ERR_ARG;
   if (c->precision != SVE_FP64 && c->precision != SVE_FP32) return SVE_ERR_ARG;
-  if (c->bedload != SVE_GRASS && c->bedload != SVE_MPM) return SVE_ERR_ARG;
+  if (c->bedload < SVE_GRASS || c->bedload > SVE_CAMENEN) return SVE_ERR_ARG;
   if (c->bedload == SVE_GRASS && (!(c->m_g >= 1.0) || !(c->m_g <= 4.0) || !(c->A_g >= 0.0))) return SVE_ERR_ARG;
   if (c->friction < SVE_FRIC_NONE || c->friction > SVE_FRIC_STRICKLER) return SVE_ERR_ARG;
-  if (c->bedload == SVE_MPM && (c->friction == SVE_FRIC_NONE || !(c->s > 1.0) || !(c->d_s > 0.0))) return SVE_ERR_ARG;
+  if (c->bedload != SVE_GRASS && (c->friction == SVE_FRIC_NONE || !(c->s > 1.0) || !(c->d_s > 0.0))) return SVE_ERR_ARG;
   if (c->friction == SVE_FRIC_STRICKLER && !(c->K_st > 0)) return SVE_ERR_ARG;
   if (c->friction == SVE_FRIC_DARCY && !(c->f_dw >= 0)) return SVE_ERR_ARG;
   const int nsides = c->dim == 2 ? 4 : 2;
@@ -80,7 +80,7 @@ void make_params(const sve_config* c, DevParams* P) {
   P->m_g = c->m_g;
   P->m_int = (c->m_g == 1.0 || c->m_g == 2.0 || c->m_g == 3.0 || c->m_g == 4.0) ? (int)c->m_g : 0;
   const double sm1 = c->s - 1.0;
-  P->mpm_C = 8.0 * sqrt(sm1 * c->g * c->d_s * c->d_s * c->d_s);
+  P->qs_scale = sqrt(sm1 * c->g * c->d_s * c->d_s * c->d_s);
   if (c->friction == SVE_FRIC_DARCY) {
     P->mpm_alpha = c->f_dw / (8.0 * c->g * sm1 * c->d_s);
   } else if (c->friction == SVE_FRIC_STRICKLER) {
@@ -105,7 +105,7 @@ void make_params(const sve_config* c, DevParams* P) {
   P->f.inv_2g = (float)P->inv_2g;
   P->f.A_g = (float)P->A_g;
   P->f.m_g = (float)P->m_g;
-  P->f.mpm_C = (float)P->mpm_C;
+  P->f.qs_scale = (float)P->qs_scale;
   P->f.mpm_alpha = (float)P->mpm_alpha;
   P->f.tau_cr = (float)P->tau_cr;
   P->f.fric_c = (float)P->fric_c;

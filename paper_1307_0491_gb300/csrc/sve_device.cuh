@@ -31,11 +31,11 @@ enum : int { GHOST_PERIODIC = 0, GHOST_FREE = 1, GHOST_INFLOW_Q = 2, GHOST_INFLO
 struct DevParams {
   int dim, nx, ny, ex;  // ex = nx + 2 (padded row length)
   double dx, dy, inv_dx, inv_dy, g, cfl, inv_2g;
-  int bedload;          // 0 Grass, 1 MPM
+  int bedload;          // 0 Grass; 1 MPM, 2 FLvB, 3 Nielsen, 4 Ribberink, 5 Camenen
   double A_g, m_g;
   int m_int;            // m_g if it is 1, 2, 3 or 4, else 0 (pow path)
-  double mpm_C;         // 8 sqrt((s-1) g d_s^3)
-  double mpm_alpha;     // Darcy: f / (8 g (s-1) d_s);  Manning: n^2 / ((s-1) d_s)  (divided by h^(1/3))
+  double qs_scale;      // sqrt((s-1) g d_s^3): q_b = qs_scale q*(tau*) (Shields laws)
+  double mpm_alpha;     // tau* = alpha |U|^2; Darcy: f / (8 g (s-1) d_s);  Manning: n^2 / ((s-1) d_s) (over h^(1/3))
   double tau_cr;
   int friction;         // 0 none, 1 Darcy, 2 Strickler
   double fric_c;        // Darcy: f / 8;  Strickler: g / K^2
@@ -49,7 +49,7 @@ struct DevParams {
   // a double inside a kernel is an FP64-pipe instruction, and GB300's FP64
   // pipe is ~1/64 of its FP32 pipe
   struct {
-    float g, inv_2g, A_g, m_g, mpm_C, mpm_alpha, tau_cr, fric_c, q_in, h_in, kappa_a, beta_min, gamma_z, newton_tol;
+    float g, inv_2g, A_g, m_g, qs_scale, mpm_alpha, tau_cr, fric_c, q_in, h_in, kappa_a, beta_min, gamma_z, newton_tol;
   } f;
 };
 
@@ -97,6 +97,8 @@ __device__ __forceinline__ float tdiv(float a, float b) { return __fdividef(a, b
 __device__ __forceinline__ double tcbrt(double x) { return cbrt(x); }
 __device__ __forceinline__ float tcbrt(float x) { return cbrtf(x); }
 __device__ __forceinline__ double tpow(double x, double y) { return pow(x, y); }
+__device__ __forceinline__ double texp(double x) { return exp(x); }
+__device__ __forceinline__ float texp(float x) { return expf(x); }
 __device__ __forceinline__ float tpow(float x, float y) { return powf(x, y); }
 __device__ __forceinline__ bool tfinite(double x) { return isfinite(x); }
 __device__ __forceinline__ bool tfinite(float x) { return isfinite(x); }
@@ -161,10 +163,46 @@ __device__ __forceinline__ bool same_bits(double a, double b) {
 __device__ __forceinline__ bool same_bits(float a, float b) { return __float_as_int(a) == __float_as_int(b); }
 
 // ---- closures (Sec. 2) -----------------------------------------------------
+// Non-dimensional rate q*(tau*) of the Shields-parameter laws listed in
+// Sec. 2 and dq*/dtau*, x = tau* - tau*_cr; false where the law carries
+// nothing (below the threshold; tau* = 0 for Camenen's).
+//   1 MPM (Eq. MPM)             8 x^1.5
+//   2 FLvB (Eq. FLVB)           5.7 x^1.5
+//   3 Nielsen (Eq. Nielsen)     12 sqrt(tau*) x
+//   4 Ribberink (Eq. Ribberink) 11 x^1.65
+//   5 Camenen (Eq. Camenen)     12 tau*^1.5 exp(-4.5 tau*_cr / tau*)
+template <typename T>
+__device__ __forceinline__ bool shields_rate(const DevParams& P, T ts, T& q, T& dq) {
+  const T tcr = par<T>(P.tau_cr, P.f.tau_cr);
+  if (P.bedload == 5) {
+    if (!(ts > T(0))) return false;
+    const T r = tdiv(tcr, ts);
+    const T sts = tsqrt(ts);
+    const T e = texp(T(-4.5) * r);
+    q = T(12) * ts * sts * e;
+    dq = T(12) * e * (T(1.5) * sts + T(4.5) * tcr * tdiv(T(1), sts));
+    return true;
+  }
+  const T x = ts - tcr;
+  if (!(x > T(0))) return false;
+  switch (P.bedload) {
+    case 1: { const T sx = tsqrt(x); q = T(8) * x * sx; dq = T(8) * T(1.5) * sx; return true; }
+    case 2: { const T sx = tsqrt(x); q = T(5.7) * x * sx; dq = T(5.7) * T(1.5) * sx; return true; }
+    case 3: {
+      const T sts = tsqrt(ts);
+      q = T(12) * sts * x;
+      dq = T(12) * (tdiv(x, T(2) * sts) + sts);
+      return true;
+    }
+    case 4: { q = T(11) * tpow(x, T(1.65)); dq = T(1.65) * tdiv(q, x); return true; }
+    default: return false;
+  }
+}
 // Normal bedload flux Q = q_b . n and dQ/du_n at fixed h.
 // Grass (Eq. bedload Grass, 2D form): Q = A_g un |U|^(m-1),
 //   dQ/dun = A_g (|U|^(m-1) + (m-1) un^2 |U|^(m-3)).
-// MPM (Eq. MPM): Q = C (tau* - tau*_cr)_+^(3/2) un/|U|, tau* = alpha |U|^2.
+// Shields-parameter laws: Q = sqrt((s-1) g d_s^3) q*(tau*) un/|U|,
+// tau* = alpha |U|^2 (q* above).
 template <typename T>
 __device__ __forceinline__ void closure(const DevParams& P, T H, T un, T ut, T& Q, T& dQ) {
   const T speed2 = un * un + ut * ut;
@@ -194,19 +232,18 @@ __device__ __forceinline__ void closure(const DevParams& P, T H, T un, T ut, T& 
   }
   T alpha = par<T>(P.mpm_alpha, P.f.mpm_alpha);
   if (P.friction != 1) alpha = alpha * rcbrt64(H);
-  const T theta = alpha * speed2 - par<T>(P.tau_cr, P.f.tau_cr);
-  if (speed2 == T(0) || !(theta > T(0))) {
+  T q, dq;
+  if (speed2 == T(0) || !shields_rate(P, alpha * speed2, q, dq)) {
     Q = T(0);
     dQ = T(0);
     return;
   }
   const T sp = tsqrt(speed2);
   const T isp = tdiv(T(1), sp);
-  const T sth = tsqrt(theta);
-  const T th32 = theta * sth;
-  const T C = par<T>(P.mpm_C, P.f.mpm_C);
-  Q = C * th32 * (un * isp);
-  dQ = C * (T(3) * sth * alpha * (un * un) * isp + th32 * (ut * ut) * (isp * isp * isp));
+  const T C = par<T>(P.qs_scale, P.f.qs_scale);
+  Q = C * q * (un * isp);
+  // d/dun [q*(alpha |U|^2) un/|U|] = q*' 2 alpha un^2/|U| + q* ut^2/|U|^3
+  dQ = C * (T(2) * dq * alpha * (un * un) * isp + q * (ut * ut) * (isp * isp * isp));
 }
 
 // Projected cell in the frame of one interface: n = normal, t = tangential.

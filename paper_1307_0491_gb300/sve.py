@@ -23,7 +23,7 @@ SVE_ERR_NEG_DEPTH, SVE_ERR_RIEMANN, SVE_ERR_NAN, SVE_ERR_DT, SVE_ERR_STATE = -4,
 SVE_ERR_NOALLOC_SIZE = -9
 SVE_NOALLOC_SCRATCH_BYTES = 8 << 20
 SVE_FP64, SVE_FP32 = 0, 1
-SVE_GRASS, SVE_MPM = 0, 1
+SVE_GRASS, SVE_MPM, SVE_FLVB, SVE_NIELSEN, SVE_RIBBERINK, SVE_CAMENEN = 0, 1, 2, 3, 4, 5
 SVE_FRIC_NONE, SVE_FRIC_DARCY, SVE_FRIC_STRICKLER = 0, 1, 2
 SVE_BC_PERIODIC, SVE_BC_FREE, SVE_BC_INFLOW_Q, SVE_BC_INFLOW_QH, SVE_BC_WALL = 0, 1, 2, 3, 4
 SVE_HOST, SVE_DEVICE = 0, 1
@@ -304,7 +304,8 @@ def _check(rc: int, where: str) -> int:
     return rc
 
 
-_BEDLOAD = {"grass": SVE_GRASS, "mpm": SVE_MPM}
+_BEDLOAD = {"grass": SVE_GRASS, "mpm": SVE_MPM, "flvb": SVE_FLVB, "nielsen": SVE_NIELSEN,
+            "ribberink": SVE_RIBBERINK, "camenen": SVE_CAMENEN}
 _FRICTION = {"none": SVE_FRIC_NONE, "darcy": SVE_FRIC_DARCY, "strickler": SVE_FRIC_STRICKLER}
 _BC = {"periodic": SVE_BC_PERIODIC, "free": SVE_BC_FREE, "inflow_q": SVE_BC_INFLOW_Q,
        "inflow_qh": SVE_BC_INFLOW_QH, "wall": SVE_BC_WALL}

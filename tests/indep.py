@@ -3,8 +3,10 @@
 Nothing here imports the oracle.  Each routine restates a piece of the
 method from its definition in a different form than ``oracle/sve_oracle.c``:
 
-* ``closure``            -- Grass (Eq. bedload Grass) and MPM (Eq. MPM with
-                            the non-dimensional form of Sec. 2) in closed form.
+* ``closure``            -- Grass (Eq. bedload Grass) and the Shields-
+                            parameter laws (Eqs. MPM, FLVB, Nielsen, Ribberink,
+                            Camenen with the non-dimensional form of Sec. 2)
+                            in closed form (``qstar``: the laws' rates).
 * ``celerities``         -- the bounds of Eq. (ab) with reading R1 (incl. the
                             bed-step term gamma_z).
 * ``suliciu_fluct``      -- the textbook Suliciu relaxation solver for shallow
@@ -42,14 +44,34 @@ def closure(p: dict, H, un, ut, lib=math):
     else:
         n = 1 / p["K_st"]
         alpha = n * n / (sm1 * p["d_s"] * H ** (lib.mpf(1) / 3 if lib is not math else 1.0 / 3.0))
-    theta = alpha * speed2 - p["tau_cr"]
-    if speed2 == 0 or theta <= 0:
+    q, dq = qstar(p["bedload"], alpha * speed2, p["tau_cr"], lib)
+    if speed2 == 0 or (q == 0 and dq == 0):
         return 0 * H, 0 * H
     sp = lib.sqrt(speed2)
-    C = 8 * lib.sqrt(sm1 * g * p["d_s"] ** 3)
-    Q = C * theta ** 1.5 * un / sp if lib is math else C * theta ** (lib.mpf(3) / 2) * un / sp
-    dQ = C * (3 * lib.sqrt(theta) * alpha * un * un / sp + theta * lib.sqrt(theta) * ut * ut / sp ** 3)
+    C = lib.sqrt(sm1 * g * p["d_s"] ** 3)
+    Q = C * q * un / sp
+    dQ = C * (2 * alpha * dq * un * un / sp + q * ut * ut / sp ** 3)
     return Q, dQ
+
+
+def qstar(law: str, ts, tcr, lib=math):
+    """(q*, dq*/dtau*) of the Shields-parameter laws listed in Sec. 2 (Eqs.
+    MPM, FLVB, Nielsen, Ribberink, Camenen); the derivative from each law's
+    logarithmic derivative."""
+    if law == "camenen":
+        if ts <= 0:
+            return 0 * ts, 0 * ts
+        q = 12 * ts * lib.sqrt(ts) * lib.exp(-4.5 * tcr / ts)
+        return q, q * (1.5 / ts + 4.5 * tcr / (ts * ts))
+    x = ts - tcr
+    if x <= 0:
+        return 0 * ts, 0 * ts
+    if law == "nielsen":
+        q = 12 * lib.sqrt(ts) * x
+        return q, q * (1 / (2 * ts) + 1 / x)
+    K, pw = {"mpm": (8, 1.5), "flvb": (5.7, 1.5), "ribberink": (11, 1.65)}[law]
+    q = K * x ** pw
+    return q, q * pw / x
 
 
 def celerities(p: dict, L, R, lib=math):

@@ -139,6 +139,35 @@ def test_c3_antidune_mpm_darcy_reduced_grid():
     assert_parity(got, ref, 2, ctx="C3 physics")
 
 
+@pytest.mark.parametrize("law,fric", [("flvb", "darcy"), ("nielsen", "darcy"), ("ribberink", "darcy"),
+                                      ("camenen", "darcy"), ("camenen", "strickler"), ("ribberink", "strickler")])
+def test_shields_laws_2d(law, fric):
+    """The other transport laws of Sec. 2 (Eqs. FLVB, Nielsen, Ribberink,
+    Camenen) on the antidune physics (supercritical inflow, random bed,
+    tau* ~ 1), with the Darcy-Weisbach or the Manning (Strickler) form of
+    tau*: 192 x 96, 100 steps."""
+    w = W.antidune2d(nx=192, ny=96, seed=1)
+    w["params"].update(bedload=law)
+    if fric == "strickler":
+        w["params"].update(friction="strickler", K_st=40.0)
+    got = run_gpu(w, 100)
+    ref = run_orc(w, 100)
+    assert_parity(got, ref, 2, ctx=f"{law}/{fric}")
+    assert np.max(np.abs(ref["z"] - w["z"])) > 1e-6  # the bed moved
+
+
+@pytest.mark.parametrize("law", ["nielsen", "camenen"])
+def test_shields_laws_fp32_state(law):
+    w = W.antidune2d(nx=256, ny=128, seed=4)
+    w["params"].update(bedload=law)
+    got = run_gpu(w, 200, precision="fp32")
+    ref = run_orc(w, 200)
+    qscale = max(np.max(np.abs(ref["hu"])), np.max(np.abs(ref["hv"])))
+    assert rel_err(got["h"], ref["h"]) <= 1e-4
+    assert rel_err(got["z"], ref["z"], scale=max(np.max(np.abs(ref["z"])), 1e-2)) <= 1e-4
+    assert rel_err(got["hu"], ref["hu"], qscale) <= 1e-3
+
+
 def test_c3_full_grid_first_dt():
     """The full antidune grid (8192 x 4096): the first CFL step equals the
     oracle's CFL step of the initial state, and one step stays finite and

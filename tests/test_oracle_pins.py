@@ -94,6 +94,63 @@ def test_mpm_closure_closed_form(orc, fric):
         assert c["dOm"] == pytest.approx((qp - qm) / (2 * e), rel=1e-6, abs=1e-12)
 
 
+SHIELDS_LAWS = ["mpm", "flvb", "nielsen", "ribberink", "camenen"]
+
+
+@pytest.mark.parametrize("fric", ["darcy", "strickler"])
+def test_shields_laws_against_mpm(orc, fric):
+    """The transport laws listed in Sec. 2 (Eqs. FLVB, Nielsen, Ribberink,
+    Camenen) against Meyer-Peter & Mueller (Eq. MPM, pinned in closed form
+    above) on the same states, through the relations their formulas fix:
+    FLvB = 5.7/8 MPM; Ribberink = (11/8) x^0.15 MPM and Nielsen = (12/8)
+    sqrt(tau* / x) MPM with x = tau* - tau*_cr; Camenen = (12/8)
+    exp(-4.5 tau*_cr / tau*) times MPM at tau*_cr = 0.  tau* from tau_b = rho g
+    h S_f with the Darcy-Weisbach or Manning S_f of Sec. 2.  Below the
+    threshold every law but Camenen's (which has none) carries nothing."""
+    base = dict(friction=fric, f_dw=0.02, K_st=30.0)
+    P = {law: oracle.Params.from_workload(wl_params(bedload=law, **base)) for law in SHIELDS_LAWS}
+    P0 = oracle.Params.from_workload(wl_params(bedload="mpm", tau_cr=0.0, **base))
+    for (H, un, ut) in [(0.5, 3.0, 0.4), (0.7, -2.5, 1.0), (0.4, 2.0, 0.0), (1.2, 3.5, -0.8)]:
+        sp = math.hypot(un, ut)
+        Sf = 0.02 * sp * sp / (8 * G * H) if fric == "darcy" else (1 / 30.0) ** 2 * sp * sp / H ** (4 / 3)
+        ts = G * H * Sf / (1.65 * G * 1e-3)
+        x = ts - 0.05
+        assert x > 0
+        c = {law: orc.cell_project(P[law], (H, H * un, H * ut, 0.0)) for law in SHIELDS_LAWS}
+        m0 = orc.cell_project(P0, (H, H * un, H * ut, 0.0))
+        mpm = c["mpm"]["Om"]
+        assert c["flvb"]["Om"] == pytest.approx(5.7 / 8 * mpm, rel=1e-14)
+        assert c["flvb"]["dOm"] == pytest.approx(5.7 / 8 * c["mpm"]["dOm"], rel=1e-14)
+        assert c["ribberink"]["Om"] == pytest.approx(11 / 8 * x ** 0.15 * mpm, rel=1e-12)
+        assert c["nielsen"]["Om"] == pytest.approx(12 / 8 * math.sqrt(ts / x) * mpm, rel=1e-12)
+        assert c["camenen"]["Om"] == pytest.approx(12 / 8 * math.exp(-4.5 * 0.05 / ts) * m0["Om"], rel=1e-12)
+    # below the threshold (tau* < tau*_cr)
+    H, un = 1.0, 0.05
+    for law in SHIELDS_LAWS:
+        om = orc.cell_project(P[law], (H, H * un, 0.0, 0.0))["Om"]
+        if law == "camenen":
+            assert om > 0
+        else:
+            assert om == 0.0
+
+
+@pytest.mark.parametrize("law", SHIELDS_LAWS)
+def test_shields_laws_derivative(orc, law):
+    """dQ/du_n (the b bound of Eq. ab) against central differences of Q, and
+    the closure against the independent restatement."""
+    pw = wl_params(bedload=law, friction="strickler", K_st=30.0)
+    P = oracle.Params.from_workload(pw)
+    for (H, un, ut) in [(0.5, 3.0, 0.4), (0.7, -2.5, 1.0), (0.4, 2.0, 0.0), (0.9, 1.2, 0.3)]:
+        c = orc.cell_project(P, (H, H * un, H * ut, 0.0))
+        e = 1e-6
+        qp = orc.cell_project(P, (H, H * (un + e), H * ut, 0.0))["Om"]
+        qm = orc.cell_project(P, (H, H * (un - e), H * ut, 0.0))["Om"]
+        assert c["dOm"] == pytest.approx((qp - qm) / (2 * e), rel=1e-6, abs=1e-12)
+        Q, dQ = indep.closure(pw, H, un, ut)
+        assert c["Om"] == pytest.approx(Q, rel=1e-13)
+        assert c["dOm"] == pytest.approx(dQ, rel=1e-12)
+
+
 # ---------------------------------------------------------------------------
 # one interface
 
@@ -157,16 +214,16 @@ def _invariant_residuals(res, pw, Lc, Rc):
     return max(worst, max(abs(x) for x in rel))
 
 
-@pytest.mark.parametrize("bedload", ["grass", "mpm"])
+@pytest.mark.parametrize("bedload", ["grass", "mpm", "flvb", "nielsen", "ribberink", "camenen"])
 def test_riemann_invariants_and_order(orc, bedload):
     """All Riemann invariants of the five linearly degenerate waves (derived
     from Eqs. relaxh--relaxqs) hold across the computed fan; the specific
     volumes are positive and the speeds ordered (Sec. 3: positivity)."""
-    extra = dict(friction="darcy", f_dw=0.02) if bedload == "mpm" else dict(A_g=0.05, m_g=3.0)
+    extra = dict(friction="darcy", f_dw=0.02) if bedload != "grass" else dict(A_g=0.05, m_g=3.0)
     pw = wl_params(bedload=bedload, **extra)
     P = oracle.Params.from_workload(pw)
     pairs = rand_pairs(1, 300, jump=0.2)
-    if bedload == "mpm":  # supercritical flows so that the threshold is exceeded
+    if bedload != "grass":  # supercritical flows so that the threshold is exceeded
         pairs = [((L[0], L[1] + 2.5 * L[0], L[2], L[3]), (R[0], R[1] + 2.5 * R[0], R[2], R[3])) for L, R in pairs]
     worst = 0.0
     for L, R in pairs:
@@ -344,6 +401,23 @@ def test_mass_conservation(orc, case):
     m0z = np.sum(np.asarray(w["z"])) * cell
     assert np.max(np.abs(r["diag"][:, 0] - m0h)) / m0h < 1e-13
     assert np.max(np.abs(r["diag"][:, 1] - m0z)) / m0z < 1e-13
+    assert np.all(r["h"] > 0)
+
+
+@pytest.mark.parametrize("law", SHIELDS_LAWS)
+def test_mass_conservation_shields_laws(orc, law):
+    """Water and sediment masses are conserved on a periodic domain under each
+    transport law of Sec. 2 (flow well above the threshold: tau* ~ 1)."""
+    w = W.random_smooth(24, 16, seed=21, bc=("periodic",) * 4, bedload=law, friction="darcy", f_dw=0.05)
+    w["hu"] = w["hu"] + 1.5 * w["h"]
+    r = _run(orc, w, 150)
+    p = w["params"]
+    cell = (p["lx"] / p["nx"]) * (p["ly"] / p["ny"])
+    m0h = np.sum(np.asarray(w["h"])) * cell
+    m0z = np.sum(np.asarray(w["z"])) * cell
+    assert np.max(np.abs(r["diag"][:, 0] - m0h)) / m0h < 1e-13
+    assert np.max(np.abs(r["diag"][:, 1] - m0z)) / m0z < 1e-13
+    assert np.max(np.abs(r["z"] - w["z"])) > 1e-6  # the bed did move
     assert np.all(r["h"] > 0)
 
 

@@ -39,8 +39,13 @@ MUTANTS = [
     ("grass_derivative_power", "second = (m - 1.0) * (un * un) * pm3;", "second = (m - 1.0) * un * pm3;"),
     ("D_uses_a_not_a2", "double D = (R->tau - L->tau) + (R->Pi - L->Pi) / (a * a);",
      "double D = (R->tau - L->tau) + (R->Pi - L->Pi) / a;"),
-    ("mpm_derivative_factor", "double d1 = 3.0 * sth * alpha * (un * un) / speed;",
-     "double d1 = 1.5 * sth * alpha * (un * un) / speed;"),
+    ("mpm_derivative_factor", "*dq = 8.0 * 1.5 * sqrt(x);", "*dq = 8.0 * sqrt(x);"),
+    ("shields_chain_rule", "double d1 = 2.0 * dqs * alpha * (un * un) / speed;",
+     "double d1 = dqs * alpha * (un * un) / speed;"),
+    ("flvb_coefficient", "*q = 5.7 * x * sqrt(x);", "*q = 8.0 * x * sqrt(x);"),
+    ("ribberink_exponent", "*q = 11.0 * pow(x, 1.65);", "*q = 11.0 * pow(x, 1.5);"),
+    ("nielsen_uses_excess", "*q = 12.0 * sqrt(ts) * x;", "*q = 12.0 * sqrt(x) * x;"),
+    ("camenen_sign", "double e = exp(-4.5 * tcr / ts);", "double e = exp(4.5 * tcr / ts);"),
     ("tangential_velocity_side", "o->v[3] = R->ut;", "o->v[3] = L->ut;"),
     ("bed_update_sign", "double Zn = X->Z[k] - dt * a[3];", "double Zn = X->Z[k] + dt * a[3];"),
     ("wall_not_mirrored", "out[normal] = -in[normal];", "out[normal] = in[normal];"),
@@ -56,6 +61,7 @@ PINS = [
     (pins.test_grass_closure_closed_form, (2.0,)),
     (pins.test_grass_closure_closed_form, (3.0,)),
     (pins.test_mpm_closure_closed_form, ("darcy",)),
+    (pins.test_shields_laws_against_mpm, ("darcy",)),
     (pins.test_single_step_50_digit, (1,)),
     (pins.test_single_step_50_digit, (2,)),
     (pins.test_mass_conservation, ("walls2d",)),
