@@ -6,8 +6,9 @@
 // tile table lists the tiles of all runs in a schedule order, and each
 // launch covers the whole table, so runs of uneven size share the GPU
 // without one launch per run.  Each run's last tile to finish (an atomic
-// ticket per run, no waiting) turns that run's per-tile partials into its
-// time step (interface launch) or its mass sums and time (cell launch).  The
+// ticket per run, no waiting) turns that run's running speed maxima into its
+// time step (interface launch) or advances its time (cell launch); mass
+// sums are reduced from per-tile partials when they are read.  The
 // per-interface and per-cell arithmetic is the single-run code
 // (interface_item, cell_item of sve_device.cuh), so every run of a batch
 // steps as it would alone, up to the compiler's FMA contraction choices in
@@ -49,13 +50,15 @@ __device__ __forceinline__ void load_run(const BatchRun<T>* runs, int r, BatchRu
 }
 
 template <typename T, int NT>
-__global__ void __launch_bounds__(NT) batch_interface_kernel(const BatchRun<T>* runs, const int2* tiles,
-                                                             DevScalars* sc, double* spart) {
+__global__ void __launch_bounds__(NT, sve::iface_min_blocks<NT>::value)
+    batch_interface_kernel(const BatchRun<T>* runs, const int2* tiles, DevScalars* sc) {
   __shared__ BatchRun<T> R;
-  __shared__ bool last;
-  __shared__ double sh[2 * (NT / 32)];
+  // block tallies: maximal x / y speed (bit patterns), Newton updates, warps done
+  __shared__ unsigned long long s_bits[2];
+  __shared__ unsigned int s_its, s_warps;
   const int2 t = tiles[blockIdx.x];
-  load_run(runs, t.x, &R);
+  if (threadIdx.x == 0) { s_bits[0] = 0ull; s_bits[1] = 0ull; s_its = 0u; s_warps = 0u; }
+  load_run(runs, t.x, &R);  // ends with a barrier
   const DevParams& P = R.P;
   const long long item = (long long)t.y * NT + threadIdx.x;
   double sx = 0.0, sy = 0.0;
@@ -67,50 +70,51 @@ __global__ void __launch_bounds__(NT) batch_interface_kernel(const BatchRun<T>* 
     fail = !sve::interface_item(P, R.S, true, item - P.nfx, sy, iters);
   }
   if (fail) atomicOr(&sc[t.x].status, sve::ST_RIEMANN);
-  int dummy = 0;
-  sve::block_maxbits_sum<NT>(sx, iters);
-  sve::block_maxbits_sum<NT>(sy, dummy);
-  if (threadIdx.x == 0) {
-    atomicAdd(&sc[t.x].newton_iters, (unsigned long long)iters);
-    spart[2 * (R.part_if + t.y)] = sx;
-    spart[2 * (R.part_if + t.y) + 1] = sy;
-    __threadfence();
-    const unsigned int ticket = atomicAdd(&sc[t.x].done_iface, 1u);
-    last = (ticket == (unsigned)R.ntile_if - 1);
+  // as in interface_kernel: warp shuffles, shared-memory atomics, no block
+  // barrier; the block's last warp folds the tallies into the run's running
+  // maxima (atomic max on the bit patterns: order-free), the run's last tile
+  // turns them into its time step
+  long long bx = __double_as_longlong(sx), by = __double_as_longlong(sy);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const long long ox = __shfl_xor_sync(0xffffffffu, bx, o), oy = __shfl_xor_sync(0xffffffffu, by, o);
+    bx = ox > bx ? ox : bx;
+    by = oy > by ? oy : by;
+    iters += __shfl_xor_sync(0xffffffffu, iters, o);
   }
-  __syncthreads();
-  if (!last) return;
+  if ((threadIdx.x & 31) != 0) return;
+  atomicMax(&s_bits[0], (unsigned long long)bx);
+  atomicMax(&s_bits[1], (unsigned long long)by);
+  atomicAdd(&s_its, (unsigned int)iters);
+  __threadfence_block();
+  if (atomicAdd(&s_warps, 1u) != NT / 32 - 1) return;
+  __threadfence_block();
+  DevScalars& S = sc[t.x];
+  atomicAdd(&S.newton_iters, (unsigned long long)atomicAdd(&s_its, 0u));
+  atomicMax(&S.smax_bits[0], atomicMax(&s_bits[0], 0ull));
+  atomicMax(&S.smax_bits[1], atomicMax(&s_bits[1], 0ull));
   __threadfence();
-  // L2 loads after the fence; integer max of the bit patterns of the
-  // non-negative speeds
-  const long long* bp = reinterpret_cast<const long long*>(spart) + 2 * (size_t)R.part_if;
-  long long bx = 0, by = 0;
-#pragma unroll 4
-  for (int b = threadIdx.x; b < R.ntile_if; b += NT) {
-    bx = max(bx, __ldcg(bp + 2 * b));
-    by = max(by, __ldcg(bp + 2 * b + 1));
-  }
-  double mx = __longlong_as_double(bx), my = __longlong_as_double(by);
-  mx = sve::block_max<NT>(mx, sh);
-  my = sve::block_max<NT>(my, sh);
-  if (threadIdx.x == 0) {
-    double dt = (P.dim == 1) ? P.cfl * P.dx / mx : P.cfl / (mx / P.dx + my / P.dy);
-    if (!(dt > 0.0) || !isfinite(dt)) { atomicOr(&sc[t.x].status, sve::ST_DT); dt = 0.0; }
-    sc[t.x].dt = dt;
-    sc[t.x].Sx = mx;
-    sc[t.x].Sy = my;
-    sc[t.x].done_iface = 0u;
-  }
+  if (atomicAdd(&S.done_iface, 1u) != (unsigned)R.ntile_if - 1) return;
+  __threadfence();
+  const double mx = __longlong_as_double((long long)atomicExch(&S.smax_bits[0], 0ull));
+  const double my = __longlong_as_double((long long)atomicExch(&S.smax_bits[1], 0ull));
+  double dt = (P.dim == 1) ? P.cfl * P.dx / mx : P.cfl / (mx / P.dx + my / P.dy);
+  if (!(dt > 0.0) || !isfinite(dt)) { atomicOr(&S.status, sve::ST_DT); dt = 0.0; }
+  S.dt = dt;
+  S.Sx = mx;
+  S.Sy = my;
+  S.done_iface = 0u;
 }
 
 template <typename T, int NT>
 __global__ void __launch_bounds__(NT) batch_cell_kernel(const BatchRun<T>* runs, const int2* tiles, DevScalars* sc,
                                                         double* mpart) {
   __shared__ BatchRun<T> R;
-  __shared__ bool last;
-  __shared__ double sh[2 * (NT / 32)];
+  __shared__ double s_m[2][NT];
+  __shared__ unsigned int s_warps;
   const int2 t = tiles[blockIdx.x];
-  load_run(runs, t.x, &R);
+  if (threadIdx.x == 0) s_warps = 0u;
+  load_run(runs, t.x, &R);  // ends with a barrier
   const DevParams& P = R.P;
   const long long k = (long long)t.y * NT + threadIdx.x;
   double mh = 0.0, mz = 0.0;
@@ -118,26 +122,46 @@ __global__ void __launch_bounds__(NT) batch_cell_kernel(const BatchRun<T>* runs,
     const int st = sve::cell_item(P, R.S, k, sc[t.x].dt, mh, mz);
     if (st) atomicOr(&sc[t.x].status, st);
   }
-  sve::block_sum2<NT>(mh, mz, sh);
-  if (threadIdx.x == 0) {
-    mpart[2 * (R.part_cell + t.y)] = mh;
-    mpart[2 * (R.part_cell + t.y) + 1] = mz;
-    __threadfence();
-    const unsigned int ticket = atomicAdd(&sc[t.x].done_cell, 1u);
-    last = (ticket == (unsigned)R.ntile_cell - 1);
+  // the tile's mass partial in a fixed order by the block's last warp (as in
+  // cell_kernel); the run's sums are reduced from the partials on read-out
+  s_m[0][threadIdx.x] = mh;
+  s_m[1][threadIdx.x] = mz;
+  __syncwarp();
+  unsigned int w = 0u;
+  if ((threadIdx.x & 31) == 0) {
+    __threadfence_block();
+    w = atomicAdd(&s_warps, 1u);
   }
-  __syncthreads();
-  if (!last) return;
+  w = __shfl_sync(0xffffffffu, w, 0);
+  if (w != NT / 32 - 1) return;
+  __threadfence_block();
+  const int lane = threadIdx.x & 31;
+  double a = 0.0, b = 0.0;
+#pragma unroll
+  for (int q = 0; q < NT / 32; ++q) { a += s_m[0][lane + 32 * q]; b += s_m[1][lane + 32 * q]; }
+  a = sve::warp_sum(a);
+  b = sve::warp_sum(b);
+  if (lane != 0) return;
+  mpart[2 * (R.part_cell + t.y)] = a;
+  mpart[2 * (R.part_cell + t.y) + 1] = b;
   __threadfence();
+  DevScalars& S = sc[t.x];
+  if (atomicAdd(&S.done_cell, 1u) != (unsigned)R.ntile_cell - 1) return;
+  S.mass_parts = (unsigned)R.ntile_cell;
+  S.t += S.dt;
+  S.steps += 1;
+  S.done_cell = 0u;
+}
+
+// Mass sums of one run from its per-tile (or, after an upload, per-block)
+// partials, in a fixed order (one block; launched when they are read).
+__global__ void __launch_bounds__(sve::kThreads) batch_mass_kernel(const double* part, DevScalars* S, double cell) {
+  __shared__ double sh[2 * (sve::kThreads / 32)];
   double a, b;
-  sve::reduce_partials<NT>(mpart + 2 * R.part_cell, (unsigned)R.ntile_cell, a, b, sh);
+  sve::reduce_partials<sve::kThreads>(part, S->mass_parts, a, b, sh);
   if (threadIdx.x == 0) {
-    const double cell = P.dx * (P.dim == 2 ? P.dy : 1.0);
-    sc[t.x].mass_h = a * cell;
-    sc[t.x].mass_z = b * cell;
-    sc[t.x].t += sc[t.x].dt;
-    sc[t.x].steps += 1;
-    sc[t.x].done_cell = 0u;
+    S->mass_h = a * cell;
+    S->mass_z = b * cell;
   }
 }
 
@@ -165,10 +189,14 @@ struct sve_batch {
   int2* d_tiles_cell = nullptr;
   int nt_if = 0, nt_cell = 0;
   DevScalars* d_sc = nullptr;
-  double* d_spart = nullptr;
   double* d_mpart = nullptr;
   double* d_init_part = nullptr;     // partials for the per-run init kernel
-  int tile = 256, schedule = 0;
+  std::vector<int> part_cell;        // first cell partial of each run at the current tile size
+  // where a run's mass sums come from when read: 0 the upload's partials
+  // (d_init_part, transient: reduced at once), 1 the last step's partials
+  // (d_mpart), 2 the scalars themselves (already reduced)
+  std::vector<int> mass_src;
+  int tile = 128, schedule = 0;
   cudaStream_t stream = nullptr;
   cudaStream_t capture = nullptr;
   cudaGraphExec_t graph = nullptr;
@@ -256,6 +284,8 @@ int build_tables(sve_batch* b, int tile, int schedule) {
     return SVE_ERR_CUDA;
   b->nt_if = (int)tif.size();
   b->nt_cell = (int)tcell.size();
+  b->part_cell.resize(n);
+  for (int r = 0; r < n; ++r) b->part_cell[r] = runs[r].part_cell;
   b->tile = tile;
   b->schedule = schedule;
   if (b->graph) cudaGraphExecDestroy(b->graph);
@@ -271,10 +301,10 @@ template <typename T>
 void launch_batch_step(sve_batch* b, cudaStream_t st) {
   const BatchRun<T>* runs = (const BatchRun<T>*)b->d_runs;
   if (b->tile == 128) {
-    batch_interface_kernel<T, 128><<<b->nt_if, 128, 0, st>>>(runs, b->d_tiles_if, b->d_sc, b->d_spart);
+    batch_interface_kernel<T, 128><<<b->nt_if, 128, 0, st>>>(runs, b->d_tiles_if, b->d_sc);
     batch_cell_kernel<T, 128><<<b->nt_cell, 128, 0, st>>>(runs, b->d_tiles_cell, b->d_sc, b->d_mpart);
   } else {
-    batch_interface_kernel<T, 256><<<b->nt_if, 256, 0, st>>>(runs, b->d_tiles_if, b->d_sc, b->d_spart);
+    batch_interface_kernel<T, 256><<<b->nt_if, 256, 0, st>>>(runs, b->d_tiles_if, b->d_sc);
     batch_cell_kernel<T, 256><<<b->nt_cell, 256, 0, st>>>(runs, b->d_tiles_cell, b->d_sc, b->d_mpart);
   }
 }
@@ -303,8 +333,18 @@ int enqueue_batch(sve_batch* b, int nsteps) {
   }
   for (; done < nsteps; ++done) launch_batch_step_any(b, b->stream);
   if (cudaGetLastError() != cudaSuccess) return SVE_ERR_CUDA;
+  if (nsteps > 0) std::fill(b->mass_src.begin(), b->mass_src.end(), 1);
   b->last_launches = 2LL * nsteps;
   return SVE_OK;
+}
+
+// Reduce run r's mass sums into its scalars from where they currently are.
+int reduce_mass(sve_batch* b, int r) {
+  if (!b->has_state[r] || b->mass_src[r] == 2) return SVE_OK;
+  const DevParams& P = b->P[r];
+  const double* part = b->mass_src[r] == 1 ? b->d_mpart + 2 * (size_t)b->part_cell[r] : b->d_init_part;
+  batch_mass_kernel<<<1, sve::kThreads, 0, b->stream>>>(part, b->d_sc + r, P.dx * (P.dim == 2 ? P.dy : 1.0));
+  return cudaGetLastError() == cudaSuccess ? SVE_OK : SVE_ERR_CUDA;
 }
 
 int batch_status(sve_batch* b, std::vector<DevScalars>* out = nullptr) {
@@ -342,13 +382,13 @@ int sve_batch_create(const sve_config* cfgs, int nruns, sve_batch** out) {
   b->P.resize(nruns);
   b->off.resize(nruns);
   b->has_state.assign(nruns, 0);
+  b->mass_src.assign(nruns, 0);
   size_t bytes = 0;
-  long long part_if = 0, part_cell = 0;
+  long long part_cell = 0;
   for (int r = 0; r < nruns; ++r) {
     sve_internal_make_params(&cfgs[r], &b->P[r]);
     b->off[r] = bytes;
     bytes += run_bytes(b->P[r], b->elem);
-    part_if += tiles_of(b->P[r].nfx + b->P[r].nfy, kTileSizes[0]);
     part_cell += tiles_of((long long)b->P[r].nx * b->P[r].ny, kTileSizes[0]);
   }
   b->arena_bytes = bytes;
@@ -356,14 +396,13 @@ int sve_batch_create(const sve_config* cfgs, int nruns, sve_batch** out) {
   const size_t rec = b->precision == SVE_FP64 ? sizeof(BatchRun<double>) : sizeof(BatchRun<float>);
   ok = ok && cudaMalloc(&b->d_runs, rec * nruns) == cudaSuccess;
   ok = ok && cudaMalloc(&b->d_sc, sizeof(DevScalars) * nruns) == cudaSuccess;
-  ok = ok && cudaMalloc(&b->d_spart, 2 * sizeof(double) * (size_t)part_if) == cudaSuccess;
   ok = ok && cudaMalloc(&b->d_mpart, 2 * sizeof(double) * (size_t)part_cell) == cudaSuccess;
   ok = ok && cudaMalloc(&b->d_init_part, 2 * sizeof(double) * (size_t)part_cell) == cudaSuccess;
   if (!ok) { sve_batch_destroy(b); return SVE_ERR_OOM; }
   if (cudaStreamCreateWithFlags(&b->capture, cudaStreamNonBlocking) != cudaSuccess) { sve_batch_destroy(b); return SVE_ERR_CUDA; }
   cudaMemset(b->arena, 0, bytes);
   cudaMemset(b->d_sc, 0, sizeof(DevScalars) * nruns);
-  const int rc = build_tables_any(b, 256, 0);
+  const int rc = build_tables_any(b, 128, 0);
   if (rc || cudaDeviceSynchronize() != cudaSuccess) { sve_batch_destroy(b); return rc ? rc : SVE_ERR_CUDA; }
   *out = b;
   return SVE_OK;
@@ -411,11 +450,15 @@ int sve_batch_set_state(sve_batch* b, int run, const void* depth, const void* hu
     sve::init_kernel<float><<<nb, sve::kThreads, 0, b->stream>>>(P, run_state<float>(b, run), b->d_sc + run,
                                                                 b->d_init_part);
   if (cudaGetLastError() != cudaSuccess) return SVE_ERR_CUDA;
+  // the upload's mass sums now: the init partials buffer is shared by the runs
+  b->has_state[run] = 1;
+  b->mass_src[run] = 0;
+  if (reduce_mass(b, run)) return SVE_ERR_CUDA;
+  b->mass_src[run] = 2;
   DevScalars s;
   if (cudaMemcpyAsync(&s, b->d_sc + run, sizeof(s), cudaMemcpyDeviceToHost, b->stream) != cudaSuccess)
     return SVE_ERR_CUDA;
   if (cudaStreamSynchronize(b->stream) != cudaSuccess) return SVE_ERR_CUDA;
-  b->has_state[run] = 1;
   if (s.status & sve::ST_NAN) return SVE_ERR_NAN;
   if (s.status & sve::ST_NEG_DEPTH) return SVE_ERR_NEG_DEPTH;
   return SVE_OK;
@@ -461,6 +504,7 @@ int sve_batch_get_state(sve_batch* b, int run, void* depth, void* hu, void* hv, 
 
 int sve_batch_get_diag(sve_batch* b, int run, double* mass_h, double* mass_z, double* t, double* last_dt) {
   if (!b || run < 0 || run >= b->nruns) return SVE_ERR_ARG;
+  if (reduce_mass(b, run)) return SVE_ERR_CUDA;
   std::vector<DevScalars> s;
   const int rc = batch_status(b, &s);
   if (rc == SVE_ERR_CUDA) return rc;
@@ -488,7 +532,12 @@ int sve_batch_autotune(sve_batch* b, int trial_steps, int* tile, int* schedule) 
   if (!b || trial_steps < 1) return SVE_ERR_ARG;
   for (int r = 0; r < b->nruns; ++r)
     if (!b->has_state[r]) return SVE_ERR_STATE;
-  // trials advance the runs: keep the state and scalars and restore them
+  // trials advance the runs: keep the state and scalars (with the mass sums
+  // reduced first, since the trials overwrite the partials) and restore them
+  for (int r = 0; r < b->nruns; ++r) {
+    if (reduce_mass(b, r)) return SVE_ERR_CUDA;
+    b->mass_src[r] = 2;
+  }
   void* save = nullptr;
   std::vector<DevScalars> sc0(b->nruns);
   if (cudaMalloc(&save, b->arena_bytes) != cudaSuccess) return SVE_ERR_OOM;
@@ -547,7 +596,6 @@ void sve_batch_destroy(sve_batch* b) {
   if (b->d_tiles_if) cudaFree(b->d_tiles_if);
   if (b->d_tiles_cell) cudaFree(b->d_tiles_cell);
   if (b->d_sc) cudaFree(b->d_sc);
-  if (b->d_spart) cudaFree(b->d_spart);
   if (b->d_mpart) cudaFree(b->d_mpart);
   if (b->d_init_part) cudaFree(b->d_init_part);
   if (b->capture) cudaStreamDestroy(b->capture);

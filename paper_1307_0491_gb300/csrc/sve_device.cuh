@@ -246,6 +246,58 @@ __device__ __forceinline__ void closure(const DevParams& P, T H, T un, T ut, T& 
   dQ = C * (T(2) * dq * alpha * (un * un) * isp + q * (ut * ut) * (isp * isp * isp));
 }
 
+// Both normal directions of a 2D cell at once: (Qx, dQx/du) along x and
+// (Qy, dQy/dv) along y share |U|, the Grass power or tau*, q*(tau*) and
+// 1/|U|; only the final products differ.  Same values as two closure()
+// calls up to rounding order.
+template <typename T>
+__device__ __forceinline__ void closure2(const DevParams& P, T H, T u, T v, T& Qx, T& dQx, T& Qy, T& dQy) {
+  const T speed2 = u * u + v * v;
+  if (P.bedload == 0) {
+    const T A = par<T>(P.A_g, P.f.A_g);
+    if (speed2 == T(0)) {
+      Qx = T(0);
+      Qy = T(0);
+      dQx = dQy = (P.m_int == 1) ? A : T(0);
+      return;
+    }
+    T pm1, f;  // |U|^(m-1) and (m-1) |U|^(m-3)
+    switch (P.m_int) {
+      case 1: pm1 = T(1); f = T(0); break;
+      case 2: { T sp = tsqrt(speed2); pm1 = sp; f = tdiv(T(1), sp); } break;
+      case 3: pm1 = speed2; f = T(2); break;
+      case 4: { T sp = tsqrt(speed2); pm1 = speed2 * sp; f = T(3) * sp; } break;
+      default: {
+        T sp = tsqrt(speed2);
+        T m = par<T>(P.m_g, P.f.m_g);
+        pm1 = tpow(sp, m - T(1));
+        f = (m - T(1)) * tpow(sp, m - T(3));
+      }
+    }
+    Qx = A * u * pm1;
+    dQx = A * (pm1 + (u * u) * f);
+    Qy = A * v * pm1;
+    dQy = A * (pm1 + (v * v) * f);
+    return;
+  }
+  T alpha = par<T>(P.mpm_alpha, P.f.mpm_alpha);
+  if (P.friction != 1) alpha = alpha * rcbrt64(H);
+  T q, dq;
+  if (speed2 == T(0) || !shields_rate(P, alpha * speed2, q, dq)) {
+    Qx = Qy = dQx = dQy = T(0);
+    return;
+  }
+  const T sp = tsqrt(speed2);
+  const T isp = tdiv(T(1), sp);
+  const T C = par<T>(P.qs_scale, P.f.qs_scale);
+  const T isp3 = isp * isp * isp;
+  const T cq = C * q, c2 = C * (T(2) * dq * alpha) * isp;
+  Qx = cq * (u * isp);
+  Qy = cq * (v * isp);
+  dQx = c2 * (u * u) + cq * (v * v) * isp3;
+  dQy = c2 * (v * v) + cq * (u * u) * isp3;
+}
+
 // Projected cell in the frame of one interface: n = normal, t = tangential.
 template <typename T>
 struct Cell {
@@ -575,8 +627,8 @@ __device__ __forceinline__ void store_cell(const DevParams& P, const DevState<T>
   const T u = s[1] * tau;
   const T v = s[2] * tau;
   T Qx, dQx, Qy = T(0), dQy = T(0);
-  closure(P, H, u, v, Qx, dQx);
-  if (P.dim == 2) closure(P, H, v, u, Qy, dQy);
+  if (P.dim == 2) closure2(P, H, u, v, Qx, dQx, Qy, dQy);
+  else closure(P, H, u, v, Qx, dQx);
   const T g = par<T>(P.g, P.f.g);
   S.h[e] = H; S.hu[e] = s[1]; S.hv[e] = s[2]; S.z[e] = s[3];
   S.tau[e] = tau; S.u[e] = u; S.v[e] = v;

@@ -51,8 +51,8 @@ __device__ __forceinline__ void project_into(const DevParams& P, T H, T Hu, T Hv
   const T g = par<T>(P.g, P.f.g);
   c.Pi = T(0.5) * g * H * H;
   T Qx, dQx, Qy = T(0), dQy = T(0);
-  closure(P, H, c.u, c.v, Qx, dQx);
-  if (P.dim == 2) closure(P, H, c.v, c.u, Qy, dQy);
+  if (P.dim == 2) closure2(P, H, c.u, c.v, Qx, dQx, Qy, dQy);
+  else closure(P, H, c.u, c.v, Qx, dQx);
   c.omx = Qx;
   c.omy = Qy;
   c.ca = H * tsqrt(g * H);
@@ -114,7 +114,7 @@ __device__ __forceinline__ unsigned block_max_u32(unsigned v, unsigned* sh) {
 }
 
 template <typename T>
-__global__ void __launch_bounds__(kFThreads) speed_kernel(DevParams P, StateBuf<T> B, DevScalars* sc,
+__global__ void __launch_bounds__(kFThreads, 7) speed_kernel(DevParams P, StateBuf<T> B, DevScalars* sc,
                                                           double* spart, const double* fixed_dts, double* dtlog,
                                                           int fixed, int ntiles, int tiles_x) {
   static_assert(sizeof(T) == 4, "the fused step is the FP32 form");

@@ -122,3 +122,41 @@ def test_batch_error_latched():
         b.step(1)  # run 1 has no state
     assert e.value.code == sve.SVE_ERR_STATE
     b.close()
+
+
+def test_batch_mass_sums():
+    """Per-run mass sums: right after the upload they equal the uploaded
+    sums; on periodic runs they are conserved by the steps; they equal the
+    single runs' sums; an autotune (whose trial steps are undone) leaves the
+    values read before it."""
+    runs = [W.random_smooth(40, 24, seed=30, bc=("periodic",) * 4, A_g=0.02),
+            W.random_smooth(57, 31, seed=31, bc=("periodic",) * 4, A_g=0.01)]
+    b = sve.Batch([r["params"] for r in runs])
+    m0 = []
+    for i, r in enumerate(runs):
+        b.set_state(i, r["h"], r["hu"], r["hv"], r["z"])
+    for i, r in enumerate(runs):
+        p = r["params"]
+        cell = (p["lx"] / p["nx"]) * (p["ly"] / p["ny"])
+        d = b.diag(i)
+        assert d["mass_h"] == pytest.approx(np.sum(r["h"]) * cell, rel=1e-13)
+        assert d["mass_z"] == pytest.approx(np.sum(r["z"]) * cell, rel=1e-13)
+        m0.append(d)
+    b.step(30)
+    after = [b.diag(i) for i in range(len(runs))]
+    for i, r in enumerate(runs):
+        assert after[i]["mass_h"] == pytest.approx(m0[i]["mass_h"], rel=1e-13)
+        assert after[i]["mass_z"] == pytest.approx(m0[i]["mass_z"], rel=1e-13)
+        s = sve.Solver(r["params"], "fp64")
+        s.set_state(r["h"], r["hu"], r["hv"], r["z"])
+        s.step(30)
+        d = s.diag()
+        s.close()
+        assert after[i]["mass_h"] == pytest.approx(d["mass_h"], rel=1e-13)
+        assert after[i]["mass_z"] == pytest.approx(d["mass_z"], rel=1e-13)
+    b.autotune(2)
+    for i in range(len(runs)):
+        d = b.diag(i)
+        assert d["mass_h"] == after[i]["mass_h"] and d["mass_z"] == after[i]["mass_z"]
+        assert d["t"] == after[i]["t"]
+    b.close()
