@@ -332,6 +332,116 @@ def run_closures(args, sve, W, torch):
             "time": "wall clock around one host-synchronous sve_step call", "laws": out}
 
 
+def run_fp32_error(args, sve, W, torch):
+    """Error of the FP32-state path per config after the config's step
+    count: the 2D dune (1024 x 512, 2000 steps) and the 2D antidune (8192 x
+    4096, 1000 steps), against the FP64 path from the same initial state
+    (the FP64 path equals the FP64 oracle to 1e-10 relative, tested).  Per
+    field: relative L-infinity (max |d| / max |ref|) and relative L1
+    (sum |d| / sum |ref|); discharges are scaled by the largest discharge."""
+    out = []
+    for name, w, n in (("2D dune 1024x512, 2000 steps", W.dune2d(), 2000),
+                       ("2D antidune 8192x4096, 1000 steps", W.antidune2d(), 1000)):
+        res = {}
+        for prec in ("fp64", "fp32"):
+            s = sve.Solver(w["params"], prec)
+            s.set_state(w["h"], w["hu"], w["hv"], w["z"])
+            t = s.step(n)
+            res[prec] = dict(s.get_state(), t=t)
+            s.close()
+        a, b = res["fp32"], res["fp64"]
+        qs = max(float(np.max(np.abs(b["hu"]))), float(np.max(np.abs(b["hv"]))))
+        errs = {}
+        for k in ("h", "hu", "hv", "z"):
+            d = np.abs(a[k].astype(np.float64) - b[k])
+            linf_scale = qs if k in ("hu", "hv") else float(np.max(np.abs(b[k])))
+            l1_scale = float(np.sum(np.abs(b["hu"])) + np.sum(np.abs(b["hv"]))) if k in ("hu", "hv") else float(np.sum(np.abs(b[k])))
+            errs[k] = {"linf": float(np.max(d)) / linf_scale, "l1": float(np.sum(d)) / l1_scale}
+        out.append({"workload": name, "steps": n, "errors": errs, "t_fp64": b["t"], "t_fp32": a["t"]})
+    return out
+
+
+def advance_to(s, T, chunk=2000):
+    """CFL steps until the simulated time reaches T exactly: bulk steps while
+    more than two CFL steps remain, single steps after that, and a last
+    fixed step with the remaining time once it is below the last CFL step
+    (the CFL step changes little from one step to the next).  Returns the
+    number of steps."""
+    n = 0
+    while True:
+        d = s.diag()
+        rest = T - d["t"]
+        if rest <= 0.0:
+            return n
+        if n == 0:
+            s.step(1)
+            n = 1
+            continue
+        dt = d["dt"]
+        if rest <= 0.99 * dt:
+            s.step_dt(np.array([rest]))
+            return n + 1
+        k = int(rest / dt) - 2
+        if k >= 1:
+            k = min(k, chunk)
+            s.step(k)
+            n += k
+        else:
+            s.step(1)
+            n += 1
+
+
+def run_paper_bump(args, sve, W, torch):
+    """The 2D bump of Sec. 5.3 at the paper's resolution (4000 x 4000 over
+    1000 x 1000 m, q0 = 10, 2D Grass m_g = 3): A_g = 1 to T = 500 s and
+    A_g = 0.1 to T = 1000 s in FP32 state (wall clock of the whole run), and
+    the FP64 rate at full size over a bounded number of steps.  The paper's
+    own timings are in a stripped figure: no comparison number exists."""
+    out = []
+    x = (np.arange(4000) + 0.5) * 0.25
+
+    def centroid(z):
+        dz = np.clip(np.asarray(z, np.float64) - 0.1, 0.0, None)
+        return float(np.sum(dz * x[None, :]) / max(float(np.sum(dz)), 1e-300))
+
+    developed = None
+    for A_g, T in ((1.0, 500.0), (0.1, 1000.0)):
+        w = W.paper_bump2d(A_g=A_g)
+        s = sve.Solver(w["params"], "fp32")
+        s.set_state(w["h"], w["hu"], w["hv"], w["z"])
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        n = advance_to(s, T)
+        wall = time.perf_counter() - t0
+        st = s.get_state()
+        t_end = s.diag()["t"]
+        s.close()
+        if developed is None:
+            developed = st
+        out.append({"A_g": A_g, "T": T, "precision": "fp32", "steps": n, "t_end": t_end, "wall_s": wall,
+                    "value": 16e6 * n / wall, "unit": UNIT,
+                    "bump_centroid_x_m": [centroid(w["z"]), centroid(st["z"])],
+                    "z_max_m": [float(np.max(w["z"])), float(np.max(st["z"]))]})
+    # FP64 from the developed flow at T = 500 s (A_g = 1): early steps are
+    # not representative, most neighbours are still identical there and
+    # their interfaces need no solve
+    w = W.paper_bump2d(A_g=1.0)
+    s = sve.Solver(w["params"], "fp64")
+    s.set_state(*(developed[k].astype(np.float64) for k in ("h", "hu", "hv", "z")))
+    s.step(20)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    s.step(200)
+    wall = time.perf_counter() - t0
+    dt = s.diag()["dt"]
+    s.close()
+    out.append({"A_g": 1.0, "precision": "fp64", "steps": 200, "from": "the FP32 state at T = 500 s",
+                "value": 16e6 * 200 / wall, "unit": UNIT, "ms_per_step": wall / 200 * 1e3, "cfl_dt_s": dt,
+                "T500_estimate_s": 500.0 / dt * wall / 200})
+    return {"workload": "2D bump (Sec. 5.3), 4000 x 4000 cells over 1000 x 1000 m", "runs": out,
+            "time": "wall clock around host-synchronous sve_step calls"}
+
+
 def run_ours(args, world, rank, local):
     import torch
 
@@ -472,6 +582,10 @@ def run_ours(args, world, rank, local):
             line["small1d"] = run_small1d(args, sve, W, torch)
         if not args.no_closures:
             line["closures"] = run_closures(args, sve, W, torch)
+        if args.fp32_error:
+            line["fp32_error"] = run_fp32_error(args, sve, W, torch)
+        if args.paper_bump2d:
+            line["paper_bump2d"] = run_paper_bump(args, sve, W, torch)
         if world == 1 and not args.no_cpu_baseline:
             rate, nsteps, secs = cpu_oracle_rate(w)
             line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
@@ -500,6 +614,10 @@ def main():
     ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint measurement")
     ap.add_argument("--no-small1d", action="store_true", help="skip the small-1D measurement")
     ap.add_argument("--no-closures", action="store_true", help="skip the per-transport-law measurement")
+    ap.add_argument("--paper-bump2d", action="store_true",
+                    help="also run the 2D bump of Sec. 5.3 at 4000 x 4000 to the paper's end times (FP32; ~4 min)")
+    ap.add_argument("--fp32-error", action="store_true",
+                    help="also state the FP32-state error per config (full step counts; ~1 min)")
     ap.add_argument("--workload", choices=["dune2d", "antidune2d"], default="dune2d")
     ap.add_argument("--precision", choices=["fp64", "fp32"], default="fp64")
     ap.add_argument("--nx", type=int, default=0, help="grid override (profiling captures)")

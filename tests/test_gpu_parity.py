@@ -168,6 +168,17 @@ def test_shields_laws_fp32_state(law):
     assert rel_err(got["hu"], ref["hu"], qscale) <= 1e-3
 
 
+@pytest.mark.parametrize("A_g", [1.0, 0.1])
+def test_paper_bump2d_reduced_grid(A_g):
+    """The 2D bump of Sec. 5.3 (1000 x 1000 m, q0 = 10, 2D Grass m_g = 3,
+    inflow upstream, free flow elsewhere) on a 200 x 200 grid, 200 steps."""
+    w = W.paper_bump2d(nx=200, ny=200, A_g=A_g)
+    got = run_gpu(w, 200)
+    ref = run_orc(w, 200)
+    assert_parity(got, ref, 2, ctx=f"bump A_g={A_g}")
+    assert abs(got["t"] - ref["t"]) <= 1e-10 * ref["t"]
+
+
 def test_c3_full_grid_first_dt():
     """The full antidune grid (8192 x 4096): the first CFL step equals the
     oracle's CFL step of the initial state, and one step stays finite and
