@@ -6,13 +6,16 @@
 // reverse sweep propagates lambda^n = (dU^{n+1}/dU^n)^T lambda^{n+1}:
 //   adj_friction_kernel  mu = (dFric/dU~)^T lambda^{n+1} per cell (closed form),
 //                        and the friction coefficient's gradient;
-//   adj_interface_kernel per interface, the Jacobian of (A-, A+) with respect
-//                        to both cells' conserved states, A_g and m_g, by
-//                        forward-mode dual numbers through the very templates
-//                        the step uses (projection, celerities, Newton
-//                        constants, fan); the Newton root enters through the
-//                        implicit function theorem, dp = -F_theta / F_p, at
-//                        the converged p; contracted with mu of both cells;
+//   adj_interface_kernel per interface, the product of the transposed
+//                        Jacobian of (A-, A+) -- with respect to both cells'
+//                        conserved states, A_g and m_g -- with mu of both
+//                        cells, in reverse mode (interface_vjp of
+//                        sve_adjoint_jac.cuh: one value pass through the
+//                        step's own templates, one hand-written backward
+//                        sweep; the Newton root enters through the implicit
+//                        function theorem at the converged p); tested
+//                        against forward-mode dual numbers through the same
+//                        templates;
 //   adj_gather_kernel    lambda^n = mu + the contributions of the cell's four
 //                        interfaces, ghost cells routed back to the cells they
 //                        copy (the transposed ghost rule).
@@ -28,7 +31,7 @@
 
 #include "../../include/sve.h"
 #include "sve_device.cuh"
-#include "sve_dual.cuh"
+#include "sve_adjoint_jac.cuh"
 #include "sve_handle.h"
 
 using sve::Cell;
@@ -58,75 +61,6 @@ struct sve_adjoint_rec {
 namespace {
 
 constexpr int kAdjThreads = 128;
-
-// Projection of a conserved state (H, Hn, Ht, Z) in an interface frame with the
-// Grass law written through pow, so that A_g and m_g can carry derivatives.
-template <typename T>
-__device__ __forceinline__ Cell<T> project_grass(const DevParams& P, T H, T Hn, T Ht, T Z, T A, T m) {
-  Cell<T> c;
-  c.H = H; c.Hn = Hn; c.Ht = Ht; c.Z = Z;
-  c.tau = T(1) / H;
-  c.un = Hn * c.tau;
-  c.ut = Ht * c.tau;
-  const T g = sve::par<T>(P.g, P.f.g);
-  c.Pi = T(0.5) * g * H * H;
-  const T speed2 = c.un * c.un + c.ut * c.ut;
-  T Q, dQ;
-  if (speed2 == T(0)) {
-    Q = T(0);
-    dQ = (m == T(1)) ? A : T(0);
-  } else {
-    const T sp = sve::tsqrt(speed2);
-    const T pm1 = sve::tpow(sp, m - T(1));
-    const T second = (m - T(1)) * (c.un * c.un) * sve::tpow(sp, m - T(3));
-    Q = A * c.un * pm1;
-    dQ = A * (pm1 + second);
-  }
-  c.Om = Q;
-  c.ca = H * sve::tsqrt(g * H);
-  c.cb = sve::tsqrt(Hn * Hn + g * H * H * dQ);
-  return c;
-}
-
-// One Jacobian pass with 5 dual directions: PASS 0 = the left state's four
-// components and A_g; PASS 1 = the right state's four and m_g.  out[k]
-// (k = 0..7 state components in frame order, 8 = A_g, 9 = m_g) receives
-// w * sum_c (muL_c dA-_c/dx_k + muR_c dA+_c/dx_k).
-template <int PASS>
-__device__ __forceinline__ void jac_pass(const DevParams& P, const double u[8], double A, double m, double pstar,
-                                         double Fp, const double muL[4], const double muR[4], double w,
-                                         double out[10]) {
-  using D = Dual<5>;
-  D x[10];
-#pragma unroll
-  for (int k = 0; k < 8; ++k) x[k] = D(u[k]);
-  x[8] = D(A);
-  x[9] = D(m);
-#pragma unroll
-  for (int j = 0; j < 4; ++j) x[PASS * 4 + j].d[j] = 1.0;
-  x[8 + PASS].d[4] = 1.0;
-  const Cell<D> L = project_grass(P, x[0], x[1], x[2], x[3], x[8], x[9]);
-  const Cell<D> R = project_grass(P, x[4], x[5], x[6], x[7], x[8], x[9]);
-  D a, b;
-  sve::celerities(P, L, R, a, b);
-  NewtonConst<D> c;
-  sve::newton_setup(P, L, R, a, b, c);
-  NewtonEval<D> e;
-  D p(pstar);
-  sve::newton_eval(p, c, L, R, e);  // F and its derivatives at the fixed root
-#pragma unroll
-  for (int j = 0; j < 5; ++j) p.d[j] = -e.F.d[j] / Fp;  // implicit function theorem
-  sve::newton_eval(p, c, L, R, e);
-  D Am[4], Ap[4];
-  sve::fan_fluctuations(P, L, R, c, e, Am, Ap);
-#pragma unroll
-  for (int j = 0; j < 5; ++j) {
-    double s = 0.0;
-#pragma unroll
-    for (int cc = 0; cc < 4; ++cc) s += muL[cc] * Am[cc].d[j] + muR[cc] * Ap[cc].d[j];
-    out[j < 4 ? PASS * 4 + j : 8 + PASS] = w * s;
-  }
-}
 
 // Deterministic sum of per-block partials (nper <= 2 per block) into
 // acc[0..nper-1] by the last block of the launch: thread t adds blocks t,
@@ -268,21 +202,20 @@ __global__ void __launch_bounds__(kAdjThreads) adj_interface_kernel(DevParams P,
       const double* hn = ydir ? S.hv : S.hu;
       const double* ht = ydir ? S.hu : S.hv;
       const double u[8] = {S.h[eL], hn[eL], ht[eL], S.z[eL], S.h[eR], hn[eR], ht[eR], S.z[eR]};
-      // value pass: the root p* of this interface
-      const Cell<double> Lv = project_grass<double>(P, u[0], u[1], u[2], u[3], A, m);
-      const Cell<double> Rv = project_grass<double>(P, u[4], u[5], u[6], u[7], A, m);
-      double av, bv;
-      sve::celerities(P, Lv, Rv, av, bv);
-      NewtonConst<double> cv;
-      double p = sve::newton_setup(P, Lv, Rv, av, bv, cv);
-      NewtonEval<double> ev;
-      sve::newton_eval(p, cv, Lv, Rv, ev);
-      int its = 0;
-      sve::newton_loop(cv, Lv, Rv, p, ev, P.newton_maxit, fmax(P.newton_tol, 16.0 * 2.220446049250313e-16), its);
-      const double Fp = sve::newton_deriv(cv, ev);
+      // reverse mode: the transposed Jacobian of the fluctuations applied
+      // to -dt/dx (mu of the left cell, mu of the right cell)
       const double w = -dt * (ydir ? P.inv_dy : P.inv_dx);
-      jac_pass<0>(P, u, A, m, p, Fp, muL, muR, w, out);
-      jac_pass<1>(P, u, A, m, p, Fp, muL, muR, w, out);
+      double Amb[4], Apb[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) { Amb[q] = w * muL[q]; Apb[q] = w * muR[q]; }
+      double ub[8] = {0, 0, 0, 0, 0, 0, 0, 0}, Ab = 0.0, mb = 0.0;
+      // (the forward run solved this interface at this state; a failure
+      // here leaves its contribution at zero, as the value pass did before)
+      sve::interface_vjp(P, u, A, m, Amb, Apb, ub, Ab, mb);
+#pragma unroll
+      for (int q = 0; q < 8; ++q) out[q] = ub[q];
+      out[8] = Ab;
+      out[9] = mb;
     }
     double* v = ydir ? S.fy : S.fx;
     const long long nf = ydir ? P.nfy : P.nfx;

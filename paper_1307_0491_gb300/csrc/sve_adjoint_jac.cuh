@@ -1,0 +1,431 @@
+// sve_adjoint_jac.cuh -- the transposed Jacobian of one interface's
+// fluctuations, for the discrete adjoint (sve_adjoint.cu).
+//
+// The fluctuations (A-, A+) of an interface are a function of its two cells'
+// conserved states (H, Hn, Ht, Z) in the interface frame and of the Grass
+// constants A_g, m_g, through the projection (Grass law written with pow so
+// that m_g carries a derivative), the celerity bounds, the Newton constants,
+// the root p* of F(p) = 0 and the fan.  The adjoint needs the product of the
+// transposed Jacobian with the cotangents (Ab-, Ab+) of the two cells:
+//   interface_vjp   reverse mode, written out by hand stage by stage (one
+//                   value pass, one backward sweep; the root enters through
+//                   the implicit function theorem: the cotangent of p*,
+//                   pbar, becomes Fbar = -pbar / F_p on F at fixed p);
+//   jac_pass        forward mode with dual numbers through the same
+//                   templates the step uses (two passes of five directions):
+//                   the reference the reverse mode is tested against.
+// Branches (max of the celerity bounds, signs of the wave speeds) follow the
+// values, as in the step.
+#pragma once
+#include "sve_device.cuh"
+#include "sve_dual.cuh"
+
+namespace sve {
+
+// Projection of a conserved state (H, Hn, Ht, Z) in an interface frame with the
+// Grass law written through pow, so that A_g and m_g can carry derivatives.
+template <typename T>
+__device__ __forceinline__ Cell<T> project_grass(const DevParams& P, T H, T Hn, T Ht, T Z, T A, T m) {
+  Cell<T> c;
+  c.H = H; c.Hn = Hn; c.Ht = Ht; c.Z = Z;
+  c.tau = T(1) / H;
+  c.un = Hn * c.tau;
+  c.ut = Ht * c.tau;
+  const T g = par<T>(P.g, P.f.g);
+  c.Pi = T(0.5) * g * H * H;
+  const T speed2 = c.un * c.un + c.ut * c.ut;
+  T Q, dQ;
+  if (speed2 == T(0)) {
+    Q = T(0);
+    dQ = (m == T(1)) ? A : T(0);
+  } else {
+    const T sp = tsqrt(speed2);
+    const T pm1 = tpow(sp, m - T(1));
+    const T second = (m - T(1)) * (c.un * c.un) * tpow(sp, m - T(3));
+    Q = A * c.un * pm1;
+    dQ = A * (pm1 + second);
+  }
+  c.Om = Q;
+  c.ca = H * tsqrt(g * H);
+  c.cb = tsqrt(Hn * Hn + g * H * H * dQ);
+  return c;
+}
+
+// One Jacobian pass with 5 dual directions: PASS 0 = the left state's four
+// components and A_g; PASS 1 = the right state's four and m_g.  out[k]
+// (k = 0..7 state components in frame order, 8 = A_g, 9 = m_g) receives
+// w * sum_c (muL_c dA-_c/dx_k + muR_c dA+_c/dx_k).
+template <int PASS>
+__device__ __forceinline__ void jac_pass(const DevParams& P, const double u[8], double A, double m, double pstar,
+                                         double Fp, const double muL[4], const double muR[4], double w,
+                                         double out[10]) {
+  using D = Dual<5>;
+  D x[10];
+#pragma unroll
+  for (int k = 0; k < 8; ++k) x[k] = D(u[k]);
+  x[8] = D(A);
+  x[9] = D(m);
+#pragma unroll
+  for (int j = 0; j < 4; ++j) x[PASS * 4 + j].d[j] = 1.0;
+  x[8 + PASS].d[4] = 1.0;
+  const Cell<D> L = project_grass(P, x[0], x[1], x[2], x[3], x[8], x[9]);
+  const Cell<D> R = project_grass(P, x[4], x[5], x[6], x[7], x[8], x[9]);
+  D a, b;
+  celerities(P, L, R, a, b);
+  NewtonConst<D> c;
+  newton_setup(P, L, R, a, b, c);
+  NewtonEval<D> e;
+  D p(pstar);
+  newton_eval(p, c, L, R, e);  // F and its derivatives at the fixed root
+#pragma unroll
+  for (int j = 0; j < 5; ++j) p.d[j] = -e.F.d[j] / Fp;  // implicit function theorem
+  newton_eval(p, c, L, R, e);
+  D Am[4], Ap[4];
+  fan_fluctuations(P, L, R, c, e, Am, Ap);
+#pragma unroll
+  for (int j = 0; j < 5; ++j) {
+    double s = 0.0;
+#pragma unroll
+    for (int cc = 0; cc < 4; ++cc) s += muL[cc] * Am[cc].d[j] + muR[cc] * Ap[cc].d[j];
+    out[j < 4 ? PASS * 4 + j : 8 + PASS] = w * s;
+  }
+}
+
+
+// ---- reverse mode ---------------------------------------------------------
+
+// Values of the projection of one side kept for its backward sweep.
+struct ProjRec {
+  double H, Hn, Ht, tau, un, ut, sp, pm1, pm3, dQ, ca, cb;
+  bool still;  // |U| = 0
+};
+
+// Cotangents of one side's projected cell.
+struct CellBar {
+  double H, Hn, Ht, Z, tau, un, ut, Pi, Om, ca, cb;
+};
+
+__device__ __forceinline__ Cell<double> project_grass_rec(const DevParams& P, double H, double Hn, double Ht,
+                                                          double Z, double A, double m, ProjRec& r) {
+  Cell<double> c;
+  c.H = H; c.Hn = Hn; c.Ht = Ht; c.Z = Z;
+  c.tau = 1.0 / H;
+  c.un = Hn * c.tau;
+  c.ut = Ht * c.tau;
+  c.Pi = 0.5 * P.g * H * H;
+  const double s2 = c.un * c.un + c.ut * c.ut;
+  r.still = s2 == 0.0;
+  double Q, dQ;
+  if (r.still) {
+    Q = 0.0;
+    dQ = (m == 1.0) ? A : 0.0;
+    r.sp = r.pm1 = r.pm3 = 0.0;
+  } else {
+    r.sp = sqrt(s2);
+    r.pm1 = pow(r.sp, m - 1.0);
+    r.pm3 = pow(r.sp, m - 3.0);
+    Q = A * c.un * r.pm1;
+    dQ = A * (r.pm1 + (m - 1.0) * (c.un * c.un) * r.pm3);
+  }
+  c.Om = Q;
+  c.ca = H * sqrt(P.g * H);
+  c.cb = sqrt(Hn * Hn + P.g * H * H * dQ);
+  r.H = H; r.Hn = Hn; r.Ht = Ht; r.tau = c.tau; r.un = c.un; r.ut = c.ut; r.dQ = dQ; r.ca = c.ca; r.cb = c.cb;
+  return c;
+}
+
+// Backward sweep of project_grass: cotangents of the cell's fields -> of
+// (H, Hn, Ht, Z) in ub[0..3], A_g, m_g.
+__device__ __forceinline__ void project_grass_bar(const DevParams& P, const ProjRec& r, double A, double m,
+                                                  CellBar cb, double ub[4], double& Ab, double& mb) {
+  double Hb = cb.H, Hnb = cb.Hn, Htb = cb.Ht, taub = cb.tau, unb = cb.un, utb = cb.ut;
+  // cb = sqrt(Hn^2 + g H^2 dQ)
+  double dQb = 0.0;
+  if (r.cb > 0.0) {
+    const double Xb = cb.cb / (2.0 * r.cb);
+    Hnb += Xb * 2.0 * r.Hn;
+    Hb += Xb * 2.0 * P.g * r.H * r.dQ;
+    dQb = Xb * P.g * r.H * r.H;
+  }
+  // ca = H sqrt(g H)
+  Hb += cb.ca * 1.5 * r.ca / r.H;
+  // Pi = g H^2 / 2
+  Hb += cb.Pi * P.g * r.H;
+  // Om = Q = A un |U|^(m-1); dQ = A (|U|^(m-1) + (m-1) un^2 |U|^(m-3))
+  if (r.still) {
+    if (m == 1.0) Ab += dQb;
+  } else {
+    const double Qb = cb.Om;
+    const double un2 = r.un * r.un;
+    const double second = (m - 1.0) * un2 * r.pm3;
+    Ab += Qb * r.un * r.pm1 + dQb * (r.pm1 + second);
+    unb += Qb * A * r.pm1;
+    double pm1b = Qb * A * r.un + dQb * A;
+    const double secondb = dQb * A;
+    mb += secondb * un2 * r.pm3;
+    unb += secondb * (m - 1.0) * 2.0 * r.un * r.pm3;
+    const double pm3b = secondb * (m - 1.0) * un2;
+    const double lsp = log(r.sp);
+    double spb = pm1b * (m - 1.0) * r.pm1 / r.sp + pm3b * (m - 3.0) * r.pm3 / r.sp;
+    mb += pm1b * r.pm1 * lsp + pm3b * r.pm3 * lsp;
+    const double s2b = spb / (2.0 * r.sp);
+    unb += s2b * 2.0 * r.un;
+    utb += s2b * 2.0 * r.ut;
+  }
+  // un = Hn tau, ut = Ht tau, tau = 1/H
+  Hnb += unb * r.tau;
+  taub += unb * r.Hn;
+  Htb += utb * r.tau;
+  taub += utb * r.Ht;
+  Hb -= taub * r.tau * r.tau;
+  ub[0] += Hb;
+  ub[1] += Hnb;
+  ub[2] += Htb;
+  ub[3] += cb.Z;
+}
+
+// Cotangents of the Newton constants used by the evaluation and the fan.
+struct ConstBar {
+  double a, b, K, inv_b, inv_K, D, C0, dZ;
+};
+
+// Cotangents of the evaluated states.
+struct EvalBar {
+  double tau1, tau2, tau3, tau4, u1, u4, lam2, lam4, Zs, F;
+};
+
+// Backward sweep of newton_eval at fixed constants: eb -> pbar and the
+// cotangents of the constants and of both cells' fields.
+__device__ __forceinline__ void newton_eval_bar(const NewtonConst<double>& c, const NewtonEval<double>& e,
+                                                double p, const Cell<double>& L, const Cell<double>& R,
+                                                EvalBar eb, double& pb, ConstBar& cb, CellBar& Lb, CellBar& Rb) {
+  // F = (OmL - OmR) + lam2 zl - lam4 zr
+  Lb.Om += eb.F;
+  Rb.Om -= eb.F;
+  eb.lam2 += eb.F * e.zl;
+  eb.lam4 -= eb.F * e.zr;
+  double zlb = eb.F * e.lam2, zrb = -eb.F * e.lam4;
+  // zl = Zs - ZL, zr = Zs - ZR
+  eb.Zs += zlb + zrb;
+  Lb.Z -= zlb;
+  Rb.Z -= zrb;
+  // Zs = ZL + K (tau2^2 - tau1^2)
+  Lb.Z += eb.Zs;
+  cb.K += eb.Zs * (e.tau2 * e.tau2 - e.tau1 * e.tau1);
+  eb.tau2 += eb.Zs * 2.0 * c.K * e.tau2;
+  eb.tau1 -= eb.Zs * 2.0 * c.K * e.tau1;
+  // lam4 = u4 + b tau4, lam2 = u1 - b tau1
+  eb.u4 += eb.lam4;
+  cb.b += eb.lam4 * e.tau4 - eb.lam2 * e.tau1;
+  eb.tau4 += eb.lam4 * c.b;
+  eb.u1 += eb.lam2;
+  eb.tau1 -= eb.lam2 * c.b;
+  // u4 = uR - a (tau4 - tauR), u1 = uL + a (tau1 - tauL)
+  Rb.un += eb.u4;
+  cb.a += -eb.u4 * (e.tau4 - R.tau) + eb.u1 * (e.tau1 - L.tau);
+  eb.tau4 -= eb.u4 * c.a;
+  Rb.tau += eb.u4 * c.a;
+  Lb.un += eb.u1;
+  eb.tau1 += eb.u1 * c.a;
+  Lb.tau -= eb.u1 * c.a;
+  // tau1 = (p + mm)/2, tau4 = (p - mm)/2
+  pb += 0.5 * (eb.tau1 + eb.tau4);
+  const double mmb = 0.5 * (eb.tau1 - eb.tau4);
+  // mm = -N ip inv_K, ip = 1/p, N = dZ + K D sigma
+  const double N = c.dZ + c.K * c.D * (e.tau2 + e.tau3);
+  const double Nb = -mmb * e.ip * c.inv_K;
+  const double ipb = -mmb * N * c.inv_K;
+  cb.inv_K -= mmb * N * e.ip;
+  pb -= ipb * e.ip * e.ip;
+  const double sigma = e.tau2 + e.tau3;
+  cb.dZ += Nb;
+  cb.K += Nb * c.D * sigma;
+  cb.D += Nb * c.K * sigma;
+  double sigmab = Nb * c.K * c.D;
+  // tau2 = (sigma - D)/2, tau3 = (sigma + D)/2
+  sigmab += 0.5 * (eb.tau2 + eb.tau3);
+  cb.D += 0.5 * (eb.tau3 - eb.tau2);
+  // sigma = (C0 - (a - b) p) inv_b
+  cb.C0 += sigmab * c.inv_b;
+  cb.a -= sigmab * p * c.inv_b;
+  cb.b += sigmab * p * c.inv_b;
+  pb -= sigmab * (c.a - c.b) * c.inv_b;
+  cb.inv_b += sigmab * (c.C0 - (c.a - c.b) * p);
+}
+
+// Product of the transposed Jacobian of one interface's fluctuations with
+// the cotangents Amb (of A-) and Apb (of A+), added to ub[0..7] (left then
+// right state, frame order), Ab, mb (A_g, m_g).  u, A, m: as jac_pass.  The
+// value pass solves for the root as the step does; false if it fails.
+__device__ __forceinline__ bool interface_vjp(const DevParams& P, const double u[8], double A, double m,
+                                              const double Amb[4], const double Apb[4], double ub[8], double& Ab,
+                                              double& mb) {
+  // ---- value pass
+  ProjRec rL, rR;
+  const Cell<double> L = project_grass_rec(P, u[0], u[1], u[2], u[3], A, m, rL);
+  const Cell<double> R = project_grass_rec(P, u[4], u[5], u[6], u[7], A, m, rR);
+  const double g = P.g;
+  // celerities (as celerities(), keeping the branches)
+  const bool a0L = L.ca >= R.ca, b0L = L.cb >= R.cb;
+  const double a0 = a0L ? L.ca : R.ca, b0 = b0L ? L.cb : R.cb;
+  const bool aIsA0 = a0 >= b0;
+  double a = P.kappa_a * (aIsA0 ? a0 : b0);
+  const bool bIsB0 = b0 >= P.beta_min * a0;
+  const double b = bIsB0 ? b0 : P.beta_min * a0;
+  const bool hL = L.H >= R.H;
+  const double Hmax = hL ? L.H : R.H;
+  const double dZ = R.Z - L.Z;
+  const double adZ = dZ < 0.0 ? -dZ : dZ;
+  const double need = b * b + 2.0 * g * P.gamma_z * adZ * (Hmax * Hmax);
+  const bool step = a * a < need;
+  if (step) a = sqrt(need);
+  NewtonConst<double> c;
+  double pstar = newton_setup(P, L, R, a, b, c);
+  NewtonEval<double> e;
+  newton_eval(pstar, c, L, R, e);
+  int its = 0;
+  if (!newton_loop(c, L, R, pstar, e, P.newton_maxit, fmax(P.newton_tol, 16.0 * 2.220446049250313e-16), its))
+    return false;
+  const double Fp = newton_deriv(c, e);
+  newton_eval(pstar, c, L, R, e);  // the states at the root, by a full evaluation
+  // fan (as fan_fluctuations, keeping the branches)
+  const double lam1 = L.un - a * L.tau, lam5 = R.un + a * R.tau;
+  const double us = e.u1 + b * (e.tau2 - e.tau1);
+  const int mi = (int)negative(lam1) + (int)negative(e.lam2) + (int)negative(us) + (int)negative(e.lam4) +
+                 (int)negative(lam5);
+  const double a2 = a * a;
+  const bool left = mi <= 2;
+  const double tk = mi == 1 ? e.tau1 : (mi == 2 ? e.tau2 : (mi == 3 ? e.tau3 : e.tau4));
+  const double uk = mi == 1 ? e.u1 : (mi == 4 ? e.u4 : us);
+  const double vk = left ? L.ut : R.ut;
+  const double Hk = 1.0 / tk;
+  const double Fh = Hk * uk;
+  const double zj2 = e.Zs - L.Z, zj4 = R.Z - e.Zs;
+  const double d12 = e.tau1 + e.tau2, d34 = e.tau3 + e.tau4;
+  const double S2 = 2.0 * g * zj2 / d12, S4 = 2.0 * g * zj4 / d34;
+  const bool n2 = negative(e.lam2), n4 = negative(e.lam4);
+
+  // ---- backward sweep
+  CellBar Lb = {}, Rb = {};
+  ConstBar cb = {};
+  EvalBar eb = {};
+  double ab = 0.0, bb = 0.0;
+  // fluctuations
+  const double Fhb = Amb[0] - Apb[0], Fqb = Amb[1] - Apb[1], Fvb = Amb[2] - Apb[2];
+  // FhX = X.Hn, FqX = X.Hn X.un + X.Pi, FvX = X.Hn X.ut
+  double FhLb = -Amb[0], FqLb = -Amb[1], FvLb = -Amb[2];
+  double FhRb = Apb[0], FqRb = Apb[1], FvRb = Apb[2];
+  const double S2b = n2 ? Amb[1] : Apb[1], S4b = n4 ? Amb[1] : Apb[1];
+  const double P2b = n2 ? Amb[3] : Apb[3], P4b = n4 ? Amb[3] : Apb[3];
+  eb.lam2 += P2b * zj2;
+  eb.lam4 += P4b * zj4;
+  double zj2b = P2b * e.lam2 + S2b * 2.0 * g / d12;
+  double zj4b = P4b * e.lam4 + S4b * 2.0 * g / d34;
+  const double d12b = -S2b * S2 / d12, d34b = -S4b * S4 / d34;
+  eb.tau1 += d12b;
+  eb.tau2 += d12b;
+  eb.tau3 += d34b;
+  eb.tau4 += d34b;
+  eb.Zs += zj2b - zj4b;
+  Lb.Z -= zj2b;
+  Rb.Z += zj4b;
+  // the flux at x/t = 0: state mi
+  if (mi == 0) {
+    FhLb += Fhb; FqLb += Fqb; FvLb += Fvb;
+  } else if (mi == 5) {
+    FhRb += Fhb; FqRb += Fqb; FvRb += Fvb;
+  } else {
+    // Fv = Fh vk, Fq = Fh uk + Pk, Fh = Hk uk, Hk = 1/tk,
+    // Pk = X.Pi + a^2 (X.tau - tk)
+    double Fhb2 = Fhb + Fvb * vk + Fqb * uk;
+    const double vkb = Fvb * Fh;
+    double ukb = Fqb * Fh + Fhb2 * Hk;
+    const double Hkb = Fhb2 * uk;
+    const double Pkb = Fqb;
+    double tkb = -Hkb * Hk * Hk - Pkb * a2;
+    CellBar& X = left ? Lb : Rb;
+    const Cell<double>& Xc = left ? L : R;
+    X.Pi += Pkb;
+    X.tau += Pkb * a2;
+    ab += 2.0 * a * Pkb * (Xc.tau - tk);
+    X.ut += vkb;
+    if (mi == 1) eb.u1 += ukb;
+    else if (mi == 4) eb.u4 += ukb;
+    else {  // us = u1 + b (tau2 - tau1)
+      eb.u1 += ukb;
+      bb += ukb * (e.tau2 - e.tau1);
+      eb.tau2 += ukb * b;
+      eb.tau1 -= ukb * b;
+    }
+    if (mi == 1) eb.tau1 += tkb;
+    else if (mi == 2) eb.tau2 += tkb;
+    else if (mi == 3) eb.tau3 += tkb;
+    else eb.tau4 += tkb;
+  }
+  Lb.Hn += FhLb + FqLb * L.un + FvLb * L.ut;
+  Lb.un += FqLb * L.Hn;
+  Lb.Pi += FqLb;
+  Lb.ut += FvLb * L.Hn;
+  Rb.Hn += FhRb + FqRb * R.un + FvRb * R.ut;
+  Rb.un += FqRb * R.Hn;
+  Rb.Pi += FqRb;
+  Rb.ut += FvRb * R.Hn;
+  // the evaluation at p*: direct part, then the root through F (implicit
+  // function theorem: Fbar = -pbar / F_p, at fixed p)
+  double pb = 0.0;
+  newton_eval_bar(c, e, pstar, L, R, eb, pb, cb, Lb, Rb);
+  EvalBar fb = {};
+  fb.F = -pb / Fp;
+  double pb_unused = 0.0;
+  newton_eval_bar(c, e, pstar, L, R, fb, pb_unused, cb, Lb, Rb);
+  // Newton constants: a, b, K = (a^2 - b^2)/(2g), inv_b = 1/b,
+  // inv_K = 2g/(a^2 - b^2), D = dtau + dPi/a^2, C0 = du + a (tauL + tauR), dZ
+  ab += cb.a;
+  bb += cb.b;
+  ab += cb.K * a / g;
+  bb -= cb.K * b / g;
+  bb -= cb.inv_b / (b * b);
+  ab -= cb.inv_K * c.inv_K * c.inv_K * a / g;
+  bb += cb.inv_K * c.inv_K * c.inv_K * b / g;
+  Rb.tau += cb.D;
+  Lb.tau -= cb.D;
+  const double ia2 = 1.0 / (a * a);
+  Rb.Pi += cb.D * ia2;
+  Lb.Pi -= cb.D * ia2;
+  ab -= cb.D * (R.Pi - L.Pi) * 2.0 * ia2 / a;
+  Rb.un += cb.C0;
+  Lb.un -= cb.C0;
+  ab += cb.C0 * (L.tau + R.tau);
+  Lb.tau += cb.C0 * a;
+  Rb.tau += cb.C0 * a;
+  Rb.Z += cb.dZ;
+  Lb.Z -= cb.dZ;
+  // celerities, along the branches taken
+  double a0b = 0.0, b0b = 0.0;
+  if (step) {
+    const double needb = ab / (2.0 * a);
+    bb += needb * 2.0 * b;
+    const double sgn = dZ < 0.0 ? -1.0 : 1.0;
+    const double dZb = needb * 2.0 * g * P.gamma_z * (Hmax * Hmax) * sgn;
+    Rb.Z += dZb;
+    Lb.Z -= dZb;
+    const double Hmb = needb * 2.0 * g * P.gamma_z * adZ * 2.0 * Hmax;
+    if (hL) Lb.H += Hmb;
+    else Rb.H += Hmb;
+  } else {
+    if (aIsA0) a0b += P.kappa_a * ab;
+    else b0b += P.kappa_a * ab;
+  }
+  if (bIsB0) b0b += bb;
+  else a0b += P.beta_min * bb;
+  if (a0L) Lb.ca += a0b;
+  else Rb.ca += a0b;
+  if (b0L) Lb.cb += b0b;
+  else Rb.cb += b0b;
+  // projections
+  project_grass_bar(P, rL, A, m, Lb, ub, Ab, mb);
+  project_grass_bar(P, rR, A, m, Rb, ub + 4, Ab, mb);
+  return true;
+}
+
+}  // namespace sve

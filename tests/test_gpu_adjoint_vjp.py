@@ -1,0 +1,77 @@
+"""The reverse-mode transposed-Jacobian product of one interface's
+fluctuations (interface_vjp, used by the adjoint) against the forward-mode
+dual-number Jacobian through the step's own templates (jac_pass), on random
+interfaces that reach every fan state that occurs (1..4 waves of negative
+speed), the bed-step branch of the celerities and both signs of the
+b-waves."""
+from __future__ import annotations
+
+import os
+import shutil
+import subprocess
+import tempfile
+
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+
+
+def _inputs(n=6000, seed=5):
+    rng = np.random.default_rng(seed)
+    rows = []
+    for k in range(n):
+        HL, HR = rng.uniform(0.2, 3.0, 2)
+        cL, cR = np.sqrt(9.81 * HL), np.sqrt(9.81 * HR)
+        kind = k % 4
+        if kind == 0:  # subcritical
+            uL, uR = rng.uniform(-0.6, 0.6, 2) * (cL, cR)
+        elif kind == 1:  # supercritical to the right / to the left, similar depths
+            HR = HL * rng.uniform(0.95, 1.05)
+            cR = np.sqrt(9.81 * HR)
+            s = 1 if rng.random() < 0.5 else -1
+            uL, uR = s * rng.uniform(1.6, 3.0, 2) * (cL, cR)
+        elif kind == 2:  # shocks and rarefactions
+            uL, uR = rng.uniform(-2.0, 2.0, 2) * (cL, cR)
+        else:  # near-critical over a bed step
+            uL, uR = rng.uniform(0.8, 1.2, 2) * (cL, cR)
+        vL, vR = rng.uniform(-0.5, 0.5, 2)
+        ZL = rng.uniform(0.0, 0.3)
+        ZR = ZL + (rng.uniform(-0.4, 0.4) * min(HL, HR) if kind == 3 else rng.uniform(-0.05, 0.05))
+        A = 10.0 ** rng.uniform(-3, -0.5)
+        m = rng.choice([1.5, 2.0, 2.5, 3.0, 3.3, 4.0])
+        bars = rng.standard_normal(8)
+        rows.append([HL, HL * uL, HL * vL, ZL, HR, HR * uR, HR * vR, ZR, A, m, *bars])
+    return np.array(rows)
+
+
+def test_reverse_mode_matches_dual_numbers():
+    import torch
+
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    nvcc = shutil.which("nvcc") or "/usr/local/cuda/bin/nvcc"
+    x = _inputs()
+    with tempfile.TemporaryDirectory() as tmp:
+        exe = os.path.join(tmp, "probe")
+        subprocess.run([nvcc, "-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-std=c++17", "-o", exe,
+                        os.path.join(HERE, "gpu_adjoint_probe.cu")], check=True)
+        r = subprocess.run([exe], input="\n".join(" ".join(repr(float(v)) for v in row) for row in x),
+                           capture_output=True, text=True, check=True)
+    out = np.array([[float(t) for t in line.split()] for line in r.stdout.splitlines()])
+    assert out.shape == (x.shape[0], 24)
+    ok = out[:, 0] == 1.0
+    assert ok.mean() > 0.9
+    fwd, rev = out[ok, 1:11], out[ok, 11:21]
+    # every fan state that can occur and the bed-step branch are covered: the
+    # outer waves always straddle x/t = 0 (a >= kappa_a b0 >= kappa_a |H u_n|,
+    # so a tau > |u_n|), so 1..4 waves have negative speed, never 0 or 5
+    states = set(out[ok, 21].astype(int).tolist())
+    assert states == {1, 2, 3, 4}, states
+    assert np.any(out[ok, 22] == 1.0)
+    scale = np.maximum(np.max(np.abs(fwd), axis=1, keepdims=True), 1e-300)
+    rel = np.max(np.abs(rev - fwd) / scale, axis=1)
+    assert np.max(rel) <= 1e-10, (np.max(rel), np.argmax(rel))
+    assert np.median(rel) <= 1e-13
