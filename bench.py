@@ -531,10 +531,13 @@ def run_ours(args, world, rank, local):
     if prec == "fp32":
         roofline = roofline_fp32
 
-    # end to end through the C ABI from pinned host memory
+    # end to end through the C ABI from pinned host memory: every step uploads
+    # the state reached by the timed steps (the same regime as `value`),
+    # steps once and reads the new state back
     e2e_steps = min(args.steps, 10)
     npdt = np.float64 if prec == "fp64" else np.float32
-    host_in = {k: torch.from_numpy(np.ascontiguousarray(w[k], dtype=npdt)).pin_memory() for k in ("h", "hu", "hv", "z")}
+    st = solver.get_state()
+    host_in = {k: torch.from_numpy(np.ascontiguousarray(st[k], dtype=npdt)).pin_memory() for k in ("h", "hu", "hv", "z")}
     host_out = {k: torch.empty_like(host_in[k]).pin_memory() for k in host_in}
     ptr = {k: host_in[k].data_ptr() for k in host_in}
     optr = {k: host_out[k].data_ptr() for k in host_out}
