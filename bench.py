@@ -16,6 +16,7 @@ scaling); the time is the max over ranks.
 from __future__ import annotations
 
 import argparse
+import datetime
 import json
 import math
 import os
@@ -85,9 +86,10 @@ def peaks():
 
 
 class ClockSampler:
-    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+    """nvidia-smi clocks and throttle reasons, sampled every 50 ms; only the
+    samples stamped inside the marked region count."""
 
-    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+    FIELDS = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
@@ -95,40 +97,71 @@ class ClockSampler:
         self.dev = device_index
         self.proc = None
         self.path = None
+        self.t0 = self.t1 = None
 
-    def start(self):
+    def start(self, wait_s: float = 5.0):
+        """Start sampling and wait for the first sample (so that the region
+        marked next is covered)."""
         fd, self.path = tempfile.mkstemp(suffix=".csv")
         os.close(fd)
         try:
             self.proc = subprocess.Popen(
-                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "200",
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "50",
                  "-i", str(self.dev)], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
+            return
+        end = time.time() + wait_s
+        while time.time() < end and os.path.getsize(self.path) == 0:
+            time.sleep(0.01)
+
+    def mark_start(self):
+        self.t0 = datetime.datetime.now()
+
+    def mark_end(self):
+        self.t1 = datetime.datetime.now()
 
     def stop(self) -> dict:
         if self.proc is None:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
-        time.sleep(0.25)
+        time.sleep(0.1)
         self.proc.terminate()
         try:
             self.proc.wait(timeout=5)
         except Exception:
             self.proc.kill()
-        rows = []
+        rows, unstamped = [], []
         for line in open(self.path):
             parts = [p.strip() for p in line.split(",")]
-            if len(parts) >= 9:
-                rows.append(parts)
+            if len(parts) < 10:
+                continue
+            try:
+                ts = datetime.datetime.strptime(parts[0], "%Y/%m/%d %H:%M:%S.%f")
+            except ValueError:
+                unstamped.append(parts[1:])
+                continue
+            rows.append((ts, parts[1:]))
         os.remove(self.path)
-        if not rows:
+        if not rows and unstamped:  # timestamps in an unexpected format: every sample
+            rows = [(None, r) for r in unstamped]
+            self.t0 = None
+        inside = [r for ts, r in rows if self.t0 is not None and self.t0 <= ts <= self.t1]
+        use = inside
+        if not use and rows:
+            if self.t0 is None:
+                use = [r for _, r in rows]
+            else:  # region shorter than a sample interval: the nearest sample
+                mid = self.t0 + (self.t1 - self.t0) / 2
+                use = [min(rows, key=lambda x: abs((x[0] - mid).total_seconds()))[1]]
+        if not use:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
-        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
-        smax = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        sm = [float(r[1]) for r in use if r[1].replace(".", "").isdigit()]
+        smax = [float(r[2]) for r in use if r[2].replace(".", "").isdigit()]
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower().startswith("active")})
+        reasons = sorted({names[k] for r in use for k in range(4) if r[5 + k].lower().startswith("active")})
         return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(smax) if smax else None,
-                "reasons": reasons, "samples": len(rows)}
+                "reasons": reasons, "samples": len(use), "samples_in_region": len(inside),
+                "interval_ms": 50}
 
 
 def dist_setup():
@@ -481,12 +514,14 @@ def run_ours(args, world, rank, local):
 
         dist.barrier()
     torch.cuda.synchronize()
+    clocks.mark_start()
     for k in range(args.steps):
         flush.zero_()                      # L2 flush between timed steps (outside the events)
         ev[k][0].record(stream)
         solver.step_async(1)
         ev[k][1].record(stream)
     torch.cuda.synchronize()
+    clocks.mark_end()
     if world > 1:
         dist.barrier()
     clk = clocks.stop()
@@ -604,7 +639,7 @@ def run_ours(args, world, rank, local):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--steps", type=int, default=500)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")

@@ -139,26 +139,21 @@ void launch_step(sve_handle* h, cudaStream_t st, int fixed, cudaEvent_t* ev) {
   if (ev) cudaEventRecord(ev[2], st);
 }
 
-// FP32 state: speed pass + fused stencil from the current to the next
-// buffer, then the host's pointers swap (also while capturing: a captured
-// sequence of an even number of steps returns to the same buffers).
+// FP32 state in 2D: the solve pass (fluctuations on chip, net fluctuation
+// per cell out, time step from the solves) and the in-place apply pass.
 void launch_fused_step(sve_handle* h, cudaStream_t st, int fixed, cudaEvent_t* ev) {
-  sve::StateBuf<float> B, N;
+  sve::StateBuf<float> B;
   B.h = (float*)h->fields[0]; B.hu = (float*)h->fields[1]; B.hv = (float*)h->fields[2]; B.z = (float*)h->fields[3];
-  N.h = (float*)h->other[0]; N.hu = (float*)h->other[1]; N.hv = (float*)h->other[2]; N.z = (float*)h->other[3];
+  const size_t ncell = (size_t)h->P.nx * (size_t)h->P.ny;
+  sve::NetFluct<float> D;  // in the fluctuation planes of the two-kernel form (8 (nx+1) ny >= 4 nx ny floats)
+  D.h = (float*)h->fx; D.hu = D.h + ncell; D.hv = D.hu + ncell; D.z = D.hv + ncell;
   const int ntiles = h->fgx * h->fgy;
   if (ev) cudaEventRecord(ev[0], st);
-  sve::speed_kernel<float><<<h->fgrid_speed, sve::kFThreads, 0, st>>>(h->P, B, h->sc, h->spart, h->fixed, h->dtlog,
-                                                                      fixed, ntiles, h->fgx);
+  sve::solve_kernel<float><<<h->fgrid_solve, sve::kFThreads, 0, st>>>(h->P, B, D, h->sc, h->fixed, h->dtlog, fixed,
+                                                                      ntiles, h->fgx);
   if (ev) cudaEventRecord(ev[1], st);
-  sve::fused_kernel<float><<<h->fgrid_fused, sve::kFThreads, 0, st>>>(h->P, B, N, h->sc, h->mpart, ntiles, h->fgx);
+  sve::apply_kernel<float><<<dim3(h->agx, h->agy), sve::kAThreads, 0, st>>>(h->P, B, D, h->sc, h->mpart);
   if (ev) cudaEventRecord(ev[2], st);
-  for (int f = 0; f < 4; ++f) {
-    void* t = h->fields[f];
-    h->fields[f] = h->other[f];
-    h->other[f] = t;
-  }
-  h->parity ^= 1;
 }
 
 void launch_step_any(sve_handle* h, cudaStream_t st, int fixed, cudaEvent_t* ev = nullptr) {
@@ -207,7 +202,7 @@ int ensure_capacity(double** buf, int* cap, int n) {
 }
 
 int get_graph(sve_handle* h, int fixed, cudaGraphExec_t* out) {
-  cudaGraphExec_t& G = h->graph[fixed ? 1 : 0][h->parity];
+  cudaGraphExec_t& G = h->graph[fixed ? 1 : 0];
   if (!G) {
     cudaGraph_t g = nullptr;
     SVE_TRY(cudaStreamBeginCapture(h->capture, cudaStreamCaptureModeThreadLocal));
@@ -223,10 +218,9 @@ int get_graph(sve_handle* h, int fixed, cudaGraphExec_t* out) {
 }
 
 void drop_graphs(sve_handle* h) {
-  for (auto& row : h->graph)
-    for (auto& G : row) {
-      if (G) cudaGraphExecDestroy(G);
-      G = nullptr;
+  for (auto& G : h->graph) {
+    if (G) cudaGraphExecDestroy(G);
+    G = nullptr;
   }
 }
 
@@ -357,29 +351,22 @@ int sve_create(const sve_config* cfg, sve_handle** out) {
   h->fgy = (h->P.ny + sve::kFTY - 1) / sve::kFTY;
   const size_t nbf = (size_t)h->fgx * (size_t)h->fgy;
   if (h->fused) {
-    int nsm = 0, bs = 0, bf = 0;
-    ok = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, h->device) == cudaSuccess &&
-         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bs, sve::speed_kernel<float>, sve::kFThreads, 0) ==
-             cudaSuccess &&
-         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bf, sve::fused_kernel<float>, sve::kFThreads, 0) ==
-             cudaSuccess;
-    h->fgrid_speed = (int)std::min<size_t>(nbf, (size_t)std::max(1, nsm * bs));
-    h->fgrid_fused = (int)std::min<size_t>(nbf, (size_t)std::max(1, nsm * bf));
+    int bs = 0;
+    ok = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bs, sve::solve_kernel<float>, sve::kFThreads, 0) ==
+         cudaSuccess;
+    h->fgrid_solve = (int)std::min<size_t>(nbf, (size_t)std::max(1, h->nsm * bs));
+    h->agx = (h->P.nx + sve::kAThreads - 1) / sve::kAThreads;
+    h->agy = std::min(h->P.ny, std::max(1, (h->nsm * (2048 / sve::kAThreads) + h->agx - 1) / h->agx));
   }
-  const size_t nsp = 2 * nbf + 2;
-  const size_t nmp = std::max(2 * (size_t)sve::cell_blocks(h->P, sve::kThreadsNarrow), 2 * nbf);
-  ok = ok && cudaMalloc(&h->spart, sizeof(double) * nsp) == cudaSuccess;
+  const size_t nmp = std::max(2 * (size_t)sve::cell_blocks(h->P, sve::kThreadsNarrow),
+                              2 * (size_t)std::max(1, h->agx * h->agy));
   ok = ok && cudaMalloc(&h->mpart, sizeof(double) * nmp) == cudaSuccess;
-  if (h->fused)
-    for (int k = 0; k < 4 && ok; ++k) ok = cudaMalloc(&h->other[k], h->elem * (size_t)h->next) == cudaSuccess;
   ok = ok && cudaMalloc(&h->sc, sizeof(DevScalars)) == cudaSuccess;
   if (!ok) { sve_destroy(h); return SVE_ERR_OOM; }
   if (ensure_capacity(&h->dtlog, &h->dtlog_cap, 1024)) { sve_destroy(h); return SVE_ERR_OOM; }
   if (ensure_capacity(&h->fixed, &h->fixed_cap, 1024)) { sve_destroy(h); return SVE_ERR_OOM; }
   if (cudaStreamCreateWithFlags(&h->capture, cudaStreamNonBlocking) != cudaSuccess) { sve_destroy(h); return SVE_ERR_CUDA; }
   for (int k = 0; k < 13; ++k) cudaMemset(h->fields[k], 0, h->elem * (size_t)h->next);
-  if (h->fused)
-    for (int k = 0; k < 4; ++k) cudaMemset(h->other[k], 0, h->elem * (size_t)h->next);
   cudaMemset(h->sc, 0, sizeof(DevScalars));
   if (cudaDeviceSynchronize() != cudaSuccess) { sve_destroy(h); return SVE_ERR_CUDA; }
   *out = h;
@@ -494,11 +481,8 @@ void sve_destroy(sve_handle* h) {
   for (auto e : h->events) cudaEventDestroy(e);
   for (auto& f : h->fields)
     if (f) cudaFree(f);
-  for (auto& f : h->other)
-    if (f) cudaFree(f);
   if (h->fx) cudaFree(h->fx);
   if (h->fy) cudaFree(h->fy);
-  if (h->spart) cudaFree(h->spart);
   if (h->mpart) cudaFree(h->mpart);
   if (h->sc) cudaFree(h->sc);
   if (h->dtlog) cudaFree(h->dtlog);

@@ -2,23 +2,25 @@
 //
 // In FP32 the two-launch layout of sve_device.cuh (projection and
 // fluctuations through global memory) is bound by its load/store stream, not
-// by arithmetic; this form keeps everything but the state on chip.  Per step:
-//   speed_kernel   a tile of TX x TY cells plus its one-cell halo is staged
-//                  and projected in shared memory; the extreme wave speeds of
-//                  the tile's interfaces give per-block maxima; the last block
-//                  to finish turns them into the time step (as the interface
-//                  kernel of the two-launch form does);
-//   fused_kernel   the same tile is staged and projected again, every x- and
-//                  y-interface of the tile is solved once (the Riemann solver
-//                  of sve_device.cuh), the fluctuations stay in shared memory,
-//                  and each cell is updated, friction applied and the new
-//                  state (and its ghosts) written to the other buffer of a
-//                  double-buffered state; per-block mass partials.
+// by arithmetic; this form keeps the projection and the fluctuations on
+// chip.  Per step:
+//   solve_kernel   a tile of TX x TY cells plus its one-cell halo is staged
+//                  and projected in shared memory; every x- and y-interface
+//                  of the tile is solved once (the Riemann solver of
+//                  sve_device.cuh), its fluctuations kept in shared memory,
+//                  and each cell's net fluctuation dF = (A+ of the left and
+//                  lower interface + A- of the right and upper one) / dx, dy
+//                  is written out (16 B per cell; it does not depend on the
+//                  time step).  The extreme wave speeds come from the solves
+//                  themselves; the last block to finish turns their running
+//                  maximum into the time step, as interface_kernel does;
+//   apply_kernel   U <- U - dt dF per cell, semi-implicit friction, checks,
+//                  the ghosts, per-block mass partials; in place, bound by
+//                  its 48 B per cell of HBM traffic.
 // Both kernels are launched with as many blocks as fit on the GPU at once and
-// walk the tiles with a grid stride, so that the per-block partials (and the
-// serial work of the last block, which reduces them) stay small.
-// Interfaces on tile edges are solved by both neighbouring tiles (8 % more
-// solves at 32 x 8), the price of keeping fluctuations out of global memory.
+// walk their tiles / cells with a grid stride, so that the per-block partials
+// stay few.  Interfaces on tile edges are solved by both neighbouring tiles
+// (8 % more solves at 32 x 8), the price of keeping fluctuations off HBM.
 #pragma once
 #include "sve_device.cuh"
 
@@ -113,69 +115,6 @@ __device__ __forceinline__ unsigned block_max_u32(unsigned v, unsigned* sh) {
   return r;
 }
 
-template <typename T>
-__global__ void __launch_bounds__(kFThreads, 7) speed_kernel(DevParams P, StateBuf<T> B, DevScalars* sc,
-                                                          double* spart, const double* fixed_dts, double* dtlog,
-                                                          int fixed, int ntiles, int tiles_x) {
-  static_assert(sizeof(T) == 4, "the fused step is the FP32 form");
-  __shared__ SCell<T> cells[kFSY][kFSX];
-  __shared__ unsigned sh[kFThreads / 32];
-  __shared__ bool last;
-  unsigned mx = 0u, my = 0u;
-  for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
-    const int i0 = (t % tiles_x) * kFTX, j0 = (t / tiles_x) * kFTY;
-    stage_tile(P, B, i0, j0, cells);
-    for (int k = threadIdx.x; k < kFNX + kFNY; k += kFThreads) {
-      bool ydir;
-      int li, lj;
-      if (!tile_interface(P, i0, j0, k, ydir, li, lj)) continue;
-      const Cell<T> L = frame_cell(!ydir ? cells[lj][li - 1] : cells[lj - 1][li], ydir);
-      const Cell<T> R = frame_cell(cells[lj][li], ydir);
-      T a, b;
-      celerities(P, L, R, a, b);
-      const unsigned s = __float_as_uint(nnmax(absbits(L.un - a * L.tau), absbits(R.un + a * R.tau)));
-      if (!ydir) mx = max(mx, s);
-      else my = max(my, s);
-    }
-    __syncthreads();  // the next tile overwrites the staged cells
-  }
-  mx = block_max_u32(mx, sh);
-  my = block_max_u32(my, sh);
-  unsigned* up = reinterpret_cast<unsigned*>(spart);
-  if (threadIdx.x == 0) {
-    up[2 * blockIdx.x] = mx;
-    up[2 * blockIdx.x + 1] = my;
-    __threadfence();
-    last = atomicAdd(&sc->done_iface, 1u) == gridDim.x - 1;
-  }
-  __syncthreads();
-  if (!last) return;
-  __threadfence();
-  mx = 0u;
-  my = 0u;
-#pragma unroll 4
-  for (unsigned q = threadIdx.x; q < gridDim.x; q += kFThreads) {
-    mx = max(mx, __ldcg(up + 2 * q));
-    my = max(my, __ldcg(up + 2 * q + 1));
-  }
-  mx = block_max_u32(mx, sh);
-  my = block_max_u32(my, sh);
-  if (threadIdx.x == 0) {
-    const double sx = (double)__uint_as_float(mx), sy = (double)__uint_as_float(my);
-    const int cs = sc->call_step;
-    double dt;
-    if (fixed) dt = fixed_dts[cs];
-    else if (P.dim == 1) dt = P.cfl * P.dx / sx;
-    else dt = P.cfl / (sx / P.dx + sy / P.dy);
-    if (!(dt > 0.0) || !isfinite(dt)) { atomicOr(&sc->status, ST_DT); dt = 0.0; }
-    sc->dt = dt;
-    sc->Sx = sx;
-    sc->Sy = sy;
-    dtlog[cs] = dt;
-    sc->done_iface = 0u;
-  }
-}
-
 // Ghost cells of the new state fed by cell (i, j) (conserved fields only).
 template <typename T>
 __device__ __forceinline__ void write_ghost_state(const DevParams& P, const StateBuf<T>& B, int i, int j,
@@ -195,6 +134,103 @@ __device__ __forceinline__ void write_ghost_state(const DevParams& P, const Stat
   }
 }
 
+
+// Net fluctuation planes of the solve (unpadded nx x ny, component-major).
+template <typename T>
+struct NetFluct {
+  T *h, *hu, *hv, *z;
+};
+
+template <typename T>
+__global__ void __launch_bounds__(kFThreads, 3) solve_kernel(DevParams P, StateBuf<T> B, NetFluct<T> D,
+                                                             DevScalars* sc, const double* fixed_dts,
+                                                             double* dtlog, int fixed, int ntiles, int tiles_x) {
+  static_assert(sizeof(T) == 4, "the fused step is the FP32 form");
+  __shared__ SCell<T> cells[kFSY][kFSX];
+  // fluctuations, component-major so that neighbouring threads hit
+  // neighbouring banks: [c] = A- (c < 4) and A+ (c >= 4) of (H, Hn, Ht, Z)
+  __shared__ T fx[8][kFTY][kFTX + 1];
+  __shared__ T fy[8][kFTY + 1][kFTX];
+  __shared__ unsigned int s_sx, s_sy, s_its, s_warps;
+  if (threadIdx.x == 0) { s_sx = 0u; s_sy = 0u; s_its = 0u; s_warps = 0u; }
+  __syncthreads();
+  const T idx = par<T>(P.inv_dx, (float)P.inv_dx), idy = par<T>(P.inv_dy, (float)P.inv_dy);
+  const int tx = threadIdx.x % kFTX, ty = threadIdx.x / kFTX;  // cell of this thread (ty < TY)
+  int fail = 0, iters = 0;
+  unsigned int mx = 0u, my = 0u;  // speed maxima (bit patterns of non-negative floats)
+  for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    const int i0 = (t % tiles_x) * kFTX, j0 = (t / tiles_x) * kFTY;
+    stage_tile(P, B, i0, j0, cells);  // ends with a barrier
+    for (int k = threadIdx.x; k < kFNX + kFNY; k += kFThreads) {
+      bool ydir;
+      int li, lj;
+      if (!tile_interface(P, i0, j0, k, ydir, li, lj)) continue;
+      const Cell<T> L = frame_cell(!ydir ? cells[lj][li - 1] : cells[lj - 1][li], ydir);
+      const Cell<T> R = frame_cell(cells[lj][li], ydir);
+      T Am[4], Ap[4], smax;
+      int its = 0;
+      if (!riemann_solve(P, L, R, Am, Ap, smax, its)) fail = 1;
+      iters += its;
+      const unsigned int sb = __float_as_uint(smax);
+      if (!ydir) {
+        mx = max(mx, sb);
+#pragma unroll
+        for (int c = 0; c < 4; ++c) { fx[c][lj - 1][li - 1] = Am[c]; fx[4 + c][lj - 1][li - 1] = Ap[c]; }
+      } else {
+        my = max(my, sb);
+#pragma unroll
+        for (int c = 0; c < 4; ++c) { fy[c][lj - 1][li - 1] = Am[c]; fy[4 + c][lj - 1][li - 1] = Ap[c]; }
+      }
+    }
+    __syncthreads();
+    const int i = i0 + tx, j = j0 + ty;
+    if (ty < kFTY && i < P.nx && j < P.ny) {
+      // A+ of the interface on the left / bottom plus A- of the one on the
+      // right / top (the y fluctuations are in the y frame: Hn = Hv)
+      const long long o = (long long)j * P.nx + i;
+      D.h[o] = (fx[4][ty][tx] + fx[0][ty][tx + 1]) * idx + (fy[4][ty][tx] + fy[0][ty + 1][tx]) * idy;
+      D.hu[o] = (fx[5][ty][tx] + fx[1][ty][tx + 1]) * idx + (fy[6][ty][tx] + fy[2][ty + 1][tx]) * idy;
+      D.hv[o] = (fx[6][ty][tx] + fx[2][ty][tx + 1]) * idx + (fy[5][ty][tx] + fy[1][ty + 1][tx]) * idy;
+      D.z[o] = (fx[7][ty][tx] + fx[3][ty][tx + 1]) * idx + (fy[7][ty][tx] + fy[3][ty + 1][tx]) * idy;
+    }
+    __syncthreads();  // the next tile overwrites cells and fluctuations
+  }
+  if (fail) atomicOr(&sc->status, ST_RIEMANN);
+  // tallies: warp shuffles, shared-memory atomics, the block's last warp
+  // folds them into the step's running maxima (as interface_kernel does)
+  mx = __reduce_max_sync(0xffffffffu, mx);
+  my = __reduce_max_sync(0xffffffffu, my);
+  iters = __reduce_add_sync(0xffffffffu, iters);
+  if ((threadIdx.x & 31) != 0) return;
+  atomicMax(&s_sx, mx);
+  atomicMax(&s_sy, my);
+  atomicAdd(&s_its, (unsigned int)iters);
+  __threadfence_block();
+  if (atomicAdd(&s_warps, 1u) != kFThreads / 32 - 1) return;
+  __threadfence_block();
+  const double bx = (double)__uint_as_float(atomicMax(&s_sx, 0u));
+  const double by = (double)__uint_as_float(atomicMax(&s_sy, 0u));
+  atomicAdd(&sc->newton_iters, (unsigned long long)atomicAdd(&s_its, 0u));
+  atomicMax(&sc->smax_bits[0], (unsigned long long)__double_as_longlong(bx));
+  atomicMax(&sc->smax_bits[1], (unsigned long long)__double_as_longlong(by));
+  __threadfence();
+  if (atomicAdd(&sc->done_iface, 1u) != gridDim.x - 1) return;
+  __threadfence();
+  const double sx = __longlong_as_double((long long)atomicExch(&sc->smax_bits[0], 0ull));
+  const double sy = __longlong_as_double((long long)atomicExch(&sc->smax_bits[1], 0ull));
+  const int cs = sc->call_step;
+  double dt;
+  if (fixed) dt = fixed_dts[cs];
+  else if (P.dim == 1) dt = P.cfl * P.dx / sx;
+  else dt = P.cfl / (sx / P.dx + sy / P.dy);
+  if (!(dt > 0.0) || !isfinite(dt)) { atomicOr(&sc->status, ST_DT); dt = 0.0; }
+  sc->dt = dt;
+  sc->Sx = sx;
+  sc->Sy = sy;
+  dtlog[cs] = dt;
+  sc->done_iface = 0u;
+}
+
 // Compensated (Neumaier) FP32 running sum: s + c carries the sum of the
 // values to O(n eps^2), so the per-thread mass partials need no FP64 adds
 // (an FP64 add per cell and field would load the FP64 pipe, ~1/64 of FP32).
@@ -208,94 +244,68 @@ struct FSum {
   __device__ __forceinline__ double value() const { return (double)s + (double)c; }
 };
 
+constexpr int kAThreads = 256;
+
 template <typename T>
-__global__ void __launch_bounds__(kFThreads, 3) fused_kernel(DevParams P, StateBuf<T> B, StateBuf<T> N,
-                                                          DevScalars* sc, double* mpart, int ntiles, int tiles_x) {
+__global__ void __launch_bounds__(kAThreads) apply_kernel(DevParams P, StateBuf<T> B, NetFluct<T> D,
+                                                          DevScalars* sc, double* mpart) {
   static_assert(sizeof(T) == 4, "the fused step is the FP32 form");
-  __shared__ SCell<T> cells[kFSY][kFSX];
-  // fluctuations, component-major so that neighbouring threads hit
-  // neighbouring banks: [c] = A- (c < 4) and A+ (c >= 4) of (H, Hn, Ht, Z)
-  __shared__ T fx[8][kFTY][kFTX + 1];
-  __shared__ T fy[8][kFTY + 1][kFTX];
-  __shared__ double sh[2 * (kFThreads / 32)];
-  __shared__ bool last;
-  const double dt = sc->dt;
-  const T dtx = T(dt * P.inv_dx), dty = T(dt * P.inv_dy), dtT = T(dt);
-  const int tx = threadIdx.x % kFTX, ty = threadIdx.x / kFTX;  // cell of this thread (ty < TY)
-  int fail = 0, iters = 0, st = 0;
+  __shared__ double s_m[2][kAThreads];
+  __shared__ unsigned int s_warps;
+  if (threadIdx.x == 0) s_warps = 0u;
+  __syncthreads();
+  const T dt = T(sc->dt);
+  int st = 0;
   FSum sh_h, sh_z;
-  for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
-    const int i0 = (t % tiles_x) * kFTX, j0 = (t / tiles_x) * kFTY;
-    stage_tile(P, B, i0, j0, cells);
-    for (int k = threadIdx.x; k < kFNX + kFNY; k += kFThreads) {
-      bool ydir;
-      int li, lj;
-      if (!tile_interface(P, i0, j0, k, ydir, li, lj)) continue;
-      const Cell<T> L = frame_cell(!ydir ? cells[lj][li - 1] : cells[lj - 1][li], ydir);
-      const Cell<T> R = frame_cell(cells[lj][li], ydir);
-      T Am[4], Ap[4], s;
-      int its = 0;
-      if (!riemann_solve(P, L, R, Am, Ap, s, its)) fail = 1;
-      iters += its;
-      if (!ydir) {
-#pragma unroll
-        for (int c = 0; c < 4; ++c) { fx[c][lj - 1][li - 1] = Am[c]; fx[4 + c][lj - 1][li - 1] = Ap[c]; }
-      } else {
-#pragma unroll
-        for (int c = 0; c < 4; ++c) { fy[c][lj - 1][li - 1] = Am[c]; fy[4 + c][lj - 1][li - 1] = Ap[c]; }
-      }
-    }
-    __syncthreads();
-    const int i = i0 + tx, j = j0 + ty;
-    if (ty < kFTY && i < P.nx && j < P.ny) {
-      const SCell<T>& c0 = cells[ty + 1][tx + 1];
-      // A+ of the interface on the left / bottom plus A- of the one on the
-      // right / top (the y fluctuations are in the y frame: Hn = Hv)
-      T s[4] = {c0.H, c0.Hu, c0.Hv, c0.Z};
-      const T ax0 = fx[4][ty][tx] + fx[0][ty][tx + 1], ax1 = fx[5][ty][tx] + fx[1][ty][tx + 1];
-      const T ax2 = fx[6][ty][tx] + fx[2][ty][tx + 1], ax3 = fx[7][ty][tx] + fx[3][ty][tx + 1];
-      const T ay0 = fy[4][ty][tx] + fy[0][ty + 1][tx], ay1 = fy[5][ty][tx] + fy[1][ty + 1][tx];
-      const T ay2 = fy[6][ty][tx] + fy[2][ty + 1][tx], ay3 = fy[7][ty][tx] + fy[3][ty + 1][tx];
-      s[0] = s[0] - (dtx * ax0 + dty * ay0);
-      s[1] = s[1] - (dtx * ax1 + dty * ay2);
-      s[2] = s[2] - (dtx * ax2 + dty * ay1);
-      s[3] = s[3] - (dtx * ax3 + dty * ay3);
+  // rows by a grid stride in y, columns by a grid stride in x
+  for (int j = blockIdx.y; j < P.ny; j += gridDim.y) {
+    for (int i = blockIdx.x * kAThreads + threadIdx.x; i < P.nx; i += gridDim.x * kAThreads) {
+      const long long e = ext_index(P, i, j), k = (long long)j * P.nx + i;
+      T s[4] = {B.h[e] - dt * D.h[k], B.hu[e] - dt * D.hu[k], B.hv[e] - dt * D.hv[k], B.z[e] - dt * D.z[k]};
       if (P.friction != 0) {
         const T tau = tdiv(T(1), s[0]);
         const T qn = tsqrt(s[1] * s[1] + s[2] * s[2]);
         T C = par<T>(P.fric_c, P.f.fric_c) * (tau * tau);
         if (P.friction == 2) C = C * rcbrt64(s[0]);
-        const T den = T(1) + dtT * C * qn;
+        const T den = T(1) + dt * C * qn;
         s[1] = tdiv(s[1], den);
         s[2] = tdiv(s[2], den);
       }
       if (!(finite_bits(s[0]) && finite_bits(s[1]) && finite_bits(s[2]) && finite_bits(s[3]))) st |= ST_NAN;
       else if (!positive(s[0])) st |= ST_NEG_DEPTH;
-      const long long e = ext_index(P, i, j);
-      N.h[e] = s[0]; N.hu[e] = s[1]; N.hv[e] = s[2]; N.z[e] = s[3];
-      write_ghost_state(P, N, i, j, s);
+      B.h[e] = s[0]; B.hu[e] = s[1]; B.hv[e] = s[2]; B.z[e] = s[3];
+      write_ghost_state(P, B, i, j, s);
       sh_h.add(s[0]);
       sh_z.add(s[3]);
     }
-    __syncthreads();  // the next tile overwrites cells and fluctuations
   }
-  if (fail) atomicOr(&sc->status, ST_RIEMANN);
   if (st) atomicOr(&sc->status, st);
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) iters += __shfl_xor_sync(0xffffffffu, iters, o);
-  if ((threadIdx.x & 31) == 0 && iters) atomicAdd(&sc->newton_iters, (unsigned long long)iters);
-  double mh = sh_h.value(), mz = sh_z.value();
-  block_sum2<kFThreads>(mh, mz, sh);
-  if (threadIdx.x == 0) {
-    mpart[2 * blockIdx.x] = mh;
-    mpart[2 * blockIdx.x + 1] = mz;
-    __threadfence();
-    last = atomicAdd(&sc->done_cell, 1u) == gridDim.x - 1;
+  // the block's mass partial in a fixed order by its last warp (as in cell_kernel)
+  s_m[0][threadIdx.x] = sh_h.value();
+  s_m[1][threadIdx.x] = sh_z.value();
+  __syncwarp();
+  unsigned int w = 0u;
+  if ((threadIdx.x & 31) == 0) {
+    __threadfence_block();
+    w = atomicAdd(&s_warps, 1u);
   }
-  __syncthreads();
-  if (!last || threadIdx.x != 0) return;
+  w = __shfl_sync(0xffffffffu, w, 0);
+  if (w != kAThreads / 32 - 1) return;
+  __threadfence_block();
+  const int lane = threadIdx.x & 31;
+  double a = 0.0, b = 0.0;
+#pragma unroll
+  for (int q = 0; q < kAThreads / 32; ++q) { a += s_m[0][lane + 32 * q]; b += s_m[1][lane + 32 * q]; }
+  a = warp_sum(a);
+  b = warp_sum(b);
+  if (lane != 0) return;
+  const unsigned int bid = blockIdx.y * gridDim.x + blockIdx.x, nb = gridDim.x * gridDim.y;
+  mpart[2 * bid] = a;
+  mpart[2 * bid + 1] = b;
+  __threadfence();
+  if (atomicAdd(&sc->done_cell, 1u) != nb - 1) return;
   // the step is complete (mass sums: from the partials on read-out)
-  sc->mass_parts = gridDim.x;
+  sc->mass_parts = nb;
   sc->t += sc->dt;
   sc->call_step += 1;
   sc->steps += 1;

@@ -21,21 +21,18 @@ struct sve_handle {
   void* fields[13] = {};           // h hu hv z tau u v pi omx omy ca cbx cby
   void* fx = nullptr;
   void* fy = nullptr;
-  double* spart = nullptr;
   double* mpart = nullptr;
   sve::DevScalars* sc = nullptr;
   double* dtlog = nullptr;
   int dtlog_cap = 0;
   double* fixed = nullptr;
   int fixed_cap = 0;
-  cudaGraphExec_t graph[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};  // [fixed][parity]
-  // FP32 state: the fused stencil with a double-buffered state; fields[0..3]
-  // always point at the current buffer, other[0..3] at the next one
+  cudaGraphExec_t graph[2] = {nullptr, nullptr};  // [fixed]
+  // FP32 state in 2D: the fused stencil (solve pass over 32 x 8 tiles, apply pass)
   bool fused = false;
-  void* other[4] = {};
-  int parity = 0;  // flips with every step (0: fields hold the buffer allocated first)
-  int fgx = 0, fgy = 0;  // tiles of the fused step in x and y
-  int fgrid_speed = 0, fgrid_fused = 0;  // resident blocks of its two kernels (grid-stride over the tiles)
+  int fgx = 0, fgy = 0;    // tiles in x and y
+  int fgrid_solve = 0;     // resident blocks of the solve pass (grid stride over the tiles)
+  int agx = 0, agy = 0;    // apply pass grid (grid stride over columns and rows)
   int nt = 256;   // threads per block of the two-kernel step (32 or 256)
   int nsm = 152;  // SMs of the device
   long long last_launches = 0;
