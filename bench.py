@@ -207,23 +207,39 @@ def run_reference(args, world, rank):
     o = oracle.get()
     P = oracle.Params.from_workload(w["params"])
     st = (w["h"], w["hu"], w["hv"], w["z"])
-    for _ in range(args.warmup):
-        r = o.run(P, 1, *st)
-        st = (r["h"], r["hu"], r["hv"], r["z"])
+    # one full-grid step sets the size of the sample: if all steps on the
+    # full grid would take more than ~2 minutes, every step runs on the first
+    # ny' rows of the workload (same physics and boundary types)
     t0 = time.perf_counter()
-    for _ in range(args.steps):
-        r = o.run(P, 1, *st)
-        st = (r["h"], r["hu"], r["hv"], r["z"])
+    o.run(P, 1, *st)
+    t_full = time.perf_counter() - t0
+    budget = 120.0
+    ny_full = ny
+    sample = f"full {nx}x{ny} grid"
+    if (args.steps + args.warmup) * t_full > budget and w["params"]["dim"] == 2:
+        nys = max(8, int(ny * budget / ((args.steps + args.warmup) * t_full)))
+        p2 = dict(w["params"], ny=nys, ly=w["params"]["ly"] * nys / ny)
+        w = dict(w, params=p2, h=w["h"][:nys], hu=w["hu"][:nys], hv=w["hv"][:nys], z=w["z"][:nys])
+        ny = nys
+        P = oracle.Params.from_workload(p2)
+        st = (w["h"], w["hu"], w["hv"], w["z"])
+        sample = f"rows 0..{nys - 1} of the {nx}x{ny_full} grid"
+    # the warm-up and the timed steps as one oracle call each (the oracle's
+    # own stepping loop, no per-step marshalling in the timed region)
+    r = o.run(P, args.warmup, *st)
+    st = (r["h"], r["hu"], r["hv"], r["z"])
+    t0 = time.perf_counter()
+    o.run(P, args.steps, *st)
     secs = time.perf_counter() - t0
     value = nx * ny * args.steps / secs
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": secs / args.steps * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": workload_desc(nx, ny, args.workload, args.precision), "nx": nx, "ny": ny,
+        "config": {"workload": workload_desc(nx, ny_full, args.workload, args.precision), "nx": nx, "ny": ny_full,
                    "precision": args.precision},
         "cpu_baseline": {"kind": "oracle", "cores": 1, "value": value, "unit": UNIT,
-                         "sample": f"full {nx}x{ny} grid, {args.steps} steps after {args.warmup} warm-up steps, "
+                         "sample": f"{sample}, {args.steps} steps after {args.warmup} warm-up steps, "
                                    f"single-threaded C oracle (-O2, no FMA contraction)"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
