@@ -186,6 +186,31 @@ def test_fp32_state_ragged_tiles_and_boundaries(nx, ny, bc, extra):
         assert got["diag"]["mass_z"] == pytest.approx(np.sum(w["z"]) * cell, rel=1e-5)
 
 
+def test_fp32_state_fixed_steps_and_errors():
+    """The FP32 2D step with recorded time steps (sve_step_dt) follows the
+    FP64 oracle run with the same steps; a step far above the CFL limit
+    latches a state error (no trap) and the handle stays usable."""
+    w = W.random_smooth(70, 37, seed=3, bc=("inflow_q", "free", "wall", "free"), A_g=0.02, q_in=0.3)
+    dts = np.full(120, 0.05)
+    got = run_gpu(w, 120, precision="fp32", dts=dts)
+    ref = run_orc(w, 120, dts=dts)
+    assert np.array_equal(got["dts"], dts)
+    qscale = max(np.max(np.abs(ref["hu"])), np.max(np.abs(ref["hv"])))
+    assert rel_err(got["h"], ref["h"]) <= 1e-4
+    assert rel_err(got["z"], ref["z"]) <= 1e-4
+    assert rel_err(got["hu"], ref["hu"], qscale) <= 1e-3
+    s = sve.Solver(w["params"], "fp32")
+    s.set_state(w["h"], w["hu"], w["hv"], w["z"])
+    with pytest.raises(sve.SveError) as e:
+        s.step_dt(np.full(4, 60.0))
+    assert e.value.code in (sve.SVE_ERR_NEG_DEPTH, sve.SVE_ERR_NAN, sve.SVE_ERR_RIEMANN, sve.SVE_ERR_DT)
+    s.set_state(w["h"], w["hu"], w["hv"], w["z"])
+    s.step(10)
+    out = s.get_state()
+    s.close()
+    assert np.all(np.isfinite(out["h"])) and np.all(out["h"] > 0)
+
+
 @pytest.mark.parametrize("law", ["nielsen", "camenen"])
 def test_shields_laws_fp32_state(law):
     w = W.antidune2d(nx=256, ny=128, seed=4)
