@@ -272,7 +272,81 @@ int wait_status(sve_handle* h) {
   DevScalars s;
   SVE_TRY(cudaMemcpyAsync(&s, h->sc, sizeof(s), cudaMemcpyDeviceToHost, h->stream));
   SVE_TRY(cudaStreamSynchronize(h->stream));
+  h->last_t = s.t;
   return status_to_code(s.status);
+}
+
+// Projection, checks, ghosts and mass partials of the cells k0..k1-1 (a
+// band of whole rows) after an upload: init_kernel for a part of the grid.
+// Blocks b0.. of nb_total over all bands write the partials; the last of
+// all of them records the partial count.
+template <typename T>
+__global__ void __launch_bounds__(sve::kThreads) init_rows_kernel(DevParams P, DevState<T> S, DevScalars* sc,
+                                                                  double* mpart, long long k0, long long k1,
+                                                                  unsigned b0, unsigned nb_total) {
+  __shared__ double sh[2 * (sve::kThreads / 32)];
+  __shared__ bool last;
+  const long long k = k0 + (long long)blockIdx.x * sve::kThreads + threadIdx.x;
+  double mh = 0.0, mz = 0.0;
+  if (k < k1) {
+    const int j = (int)(k / P.nx);
+    const int i = (int)(k - (long long)j * P.nx);
+    const long long e = sve::ext_index(P, i, j);
+    T s[4] = {S.h[e], S.hu[e], P.dim == 2 ? S.hv[e] : T(0), S.z[e]};
+    if (!(sve::tfinite(s[0]) && sve::tfinite(s[1]) && sve::tfinite(s[2]) && sve::tfinite(s[3])))
+      atomicOr(&sc->status, sve::ST_NAN);
+    else if (!sve::positive(s[0])) atomicOr(&sc->status, sve::ST_NEG_DEPTH);
+    sve::store_cell(P, S, e, s, sve::tdiv(T(1), s[0]));
+    sve::write_ghosts(P, S, i, j, s);
+    mh = (double)s[0];
+    mz = (double)s[3];
+  }
+  sve::block_sum2<sve::kThreads>(mh, mz, sh);
+  if (threadIdx.x == 0) {
+    mpart[2 * (b0 + blockIdx.x)] = mh;
+    mpart[2 * (b0 + blockIdx.x) + 1] = mz;
+    __threadfence();
+    last = atomicAdd(&sc->done_cell, 1u) == nb_total - 1;
+  }
+  __syncthreads();
+  if (!last || threadIdx.x != 0) return;
+  sc->mass_parts = nb_total;
+  sc->done_cell = 0u;
+}
+
+// Host upload of the interior state in bands of rows on the upload stream,
+// each band projected on the handle's stream as soon as it has arrived.
+int upload_in_bands(sve_handle* h, const void* const src[4], int nbands) {
+  const DevParams& P = h->P;
+  const size_t row = h->elem * (size_t)P.nx, pitch = h->elem * (size_t)P.ex;
+  SVE_TRY(cudaMemsetAsync(h->sc, 0, sizeof(DevScalars), h->stream));
+  SVE_TRY(cudaEventRecord(h->up_ev[0], h->stream));  // the state may still be in use
+  SVE_TRY(cudaStreamWaitEvent(h->upload, h->up_ev[0], 0));
+  unsigned nb_total = 0;
+  for (int c = 0; c < nbands; ++c) {
+    const long long r0 = (long long)P.ny * c / nbands, r1 = (long long)P.ny * (c + 1) / nbands;
+    nb_total += (unsigned)(((r1 - r0) * P.nx + sve::kThreads - 1) / sve::kThreads);
+  }
+  unsigned b0 = 0;
+  for (int c = 0; c < nbands; ++c) {
+    const long long r0 = (long long)P.ny * c / nbands, r1 = (long long)P.ny * (c + 1) / nbands;
+    for (int f = 0; f < 4; ++f) {
+      char* dst = (char*)h->fields[f] + h->elem * (size_t)(P.ex * (r0 + 1) + 1);
+      const char* from = (const char*)src[f] + row * (size_t)r0;
+      SVE_TRY(cudaMemcpy2DAsync(dst, pitch, from, row, row, (size_t)(r1 - r0), cudaMemcpyHostToDevice, h->upload));
+    }
+    SVE_TRY(cudaEventRecord(h->up_ev[1 + c], h->upload));
+    SVE_TRY(cudaStreamWaitEvent(h->stream, h->up_ev[1 + c], 0));
+    const unsigned nb = (unsigned)(((r1 - r0) * P.nx + sve::kThreads - 1) / sve::kThreads);
+    if (h->cfg.precision == SVE_FP64)
+      init_rows_kernel<double><<<nb, sve::kThreads, 0, h->stream>>>(P, state_of<double>(h), h->sc, h->mpart,
+                                                                     r0 * P.nx, r1 * P.nx, b0, nb_total);
+    else
+      init_rows_kernel<float><<<nb, sve::kThreads, 0, h->stream>>>(P, state_of<float>(h), h->sc, h->mpart,
+                                                                    r0 * P.nx, r1 * P.nx, b0, nb_total);
+    b0 += nb;
+  }
+  return cudaGetLastError() == cudaSuccess ? SVE_OK : SVE_ERR_CUDA;
 }
 
 int run_steps(sve_handle* h, int nsteps, int fixed) {
@@ -365,7 +439,13 @@ int sve_create(const sve_config* cfg, sve_handle** out) {
   if (!ok) { sve_destroy(h); return SVE_ERR_OOM; }
   if (ensure_capacity(&h->dtlog, &h->dtlog_cap, 1024)) { sve_destroy(h); return SVE_ERR_OOM; }
   if (ensure_capacity(&h->fixed, &h->fixed_cap, 1024)) { sve_destroy(h); return SVE_ERR_OOM; }
-  if (cudaStreamCreateWithFlags(&h->capture, cudaStreamNonBlocking) != cudaSuccess) { sve_destroy(h); return SVE_ERR_CUDA; }
+  if (cudaStreamCreateWithFlags(&h->capture, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&h->upload, cudaStreamNonBlocking) != cudaSuccess) {
+    sve_destroy(h);
+    return SVE_ERR_CUDA;
+  }
+  for (auto& e : h->up_ev)
+    if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) { sve_destroy(h); return SVE_ERR_CUDA; }
   for (int k = 0; k < 13; ++k) cudaMemset(h->fields[k], 0, h->elem * (size_t)h->next);
   cudaMemset(h->sc, 0, sizeof(DevScalars));
   if (cudaDeviceSynchronize() != cudaSuccess) { sve_destroy(h); return SVE_ERR_CUDA; }
@@ -387,16 +467,24 @@ int sve_set_state(sve_handle* h, const void* depth, const void* hu, const void* 
   const size_t pitch = h->elem * (size_t)P.ex;
   const cudaMemcpyKind kind = where == SVE_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
   const void* src[4] = {depth, hu, h->cfg.dim == 2 ? hv : nullptr, zb};
-  for (int f = 0; f < 4; ++f) {
-    char* dst = (char*)h->fields[f] + h->elem * (size_t)(P.ex + 1);
-    if (src[f]) SVE_TRY(cudaMemcpy2DAsync(dst, pitch, src[f], row, row, P.ny, kind, h->stream));
-    else SVE_TRY(cudaMemsetAsync(h->fields[f], 0, h->elem * (size_t)h->next, h->stream));
+  // large 2D grids from the host: four bands of rows, each projected while
+  // the next one is still arriving
+  const int nbands = (where == SVE_HOST && h->cfg.dim == 2 && P.ny >= 64 && (long long)P.nx * P.ny >= (1LL << 18)) ? 4 : 1;
+  if (nbands > 1) {
+    const int urc = upload_in_bands(h, src, nbands);
+    if (urc) return urc;
+  } else {
+    for (int f = 0; f < 4; ++f) {
+      char* dst = (char*)h->fields[f] + h->elem * (size_t)(P.ex + 1);
+      if (src[f]) SVE_TRY(cudaMemcpy2DAsync(dst, pitch, src[f], row, row, P.ny, kind, h->stream));
+      else SVE_TRY(cudaMemsetAsync(h->fields[f], 0, h->elem * (size_t)h->next, h->stream));
+    }
+    SVE_TRY(cudaMemsetAsync(h->sc, 0, sizeof(DevScalars), h->stream));
+    if (h->cfg.precision == SVE_FP64)
+      sve::init_kernel<double><<<(unsigned)sve::cell_blocks(h->P, sve::kThreads), sve::kThreads, 0, h->stream>>>(P, state_of<double>(h), h->sc, h->mpart);
+    else
+      sve::init_kernel<float><<<(unsigned)sve::cell_blocks(h->P, sve::kThreads), sve::kThreads, 0, h->stream>>>(P, state_of<float>(h), h->sc, h->mpart);
   }
-  SVE_TRY(cudaMemsetAsync(h->sc, 0, sizeof(DevScalars), h->stream));
-  if (h->cfg.precision == SVE_FP64)
-    sve::init_kernel<double><<<(unsigned)sve::cell_blocks(h->P, sve::kThreads), sve::kThreads, 0, h->stream>>>(P, state_of<double>(h), h->sc, h->mpart);
-  else
-    sve::init_kernel<float><<<(unsigned)sve::cell_blocks(h->P, sve::kThreads), sve::kThreads, 0, h->stream>>>(P, state_of<float>(h), h->sc, h->mpart);
   SVE_TRY(cudaGetLastError());
   DevScalars s;
   SVE_TRY(cudaMemcpyAsync(&s, h->sc, sizeof(s), cudaMemcpyDeviceToHost, h->stream));
@@ -409,10 +497,7 @@ int sve_set_state(sve_handle* h, const void* depth, const void* hu, const void* 
 int sve_step(sve_handle* h, int nsteps, double* t_out) {
   if (!h || nsteps < 0) return SVE_ERR_ARG;
   int rc = run_steps(h, nsteps, 0);
-  if (t_out && rc != SVE_ERR_CUDA) {
-    double t = 0;
-    if (cudaMemcpy(&t, &h->sc->t, sizeof(double), cudaMemcpyDeviceToHost) == cudaSuccess) *t_out = t;
-  }
+  if (t_out && rc != SVE_ERR_CUDA) *t_out = h->last_t;  // read back with the status
   return rc;
 }
 
@@ -488,6 +573,9 @@ void sve_destroy(sve_handle* h) {
   if (h->dtlog) cudaFree(h->dtlog);
   if (h->fixed) cudaFree(h->fixed);
   if (h->capture) cudaStreamDestroy(h->capture);
+  if (h->upload) cudaStreamDestroy(h->upload);
+  for (auto& e : h->up_ev)
+    if (e) cudaEventDestroy(e);
   delete h;
 }
 

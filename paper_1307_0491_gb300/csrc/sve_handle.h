@@ -15,6 +15,9 @@ struct sve_handle {
   int device = 0;
   cudaStream_t stream = nullptr;   // user stream (nullptr = legacy default)
   cudaStream_t capture = nullptr;  // private stream used only to capture graphs
+  cudaStream_t upload = nullptr;   // private stream for host uploads in row chunks (overlapped with their projection)
+  cudaEvent_t up_ev[5] = {};       // [0]: prior work of the handle's stream; [1..4]: the chunks
+  double last_t = 0.0;             // simulated time read back with the status of the last blocking call
   bool has_state = false;
   size_t elem = 8;                 // bytes per state element
   long long next = 0;              // padded cells
