@@ -49,6 +49,8 @@ struct sve_adjoint_rec {
   std::vector<double*> checkpoints;  // padded (h, hu, hv, z) at steps 0, C, 2C, ...
   double* seg = nullptr;            // padded states of one segment (C of them)
   size_t seg_cap = 0;
+  double* segc = nullptr;           // their convected (pre-friction) interior states, 4 planes each
+  size_t segc_cap = 0;
   double* lam = nullptr;            // 2 x 4 interior planes (current, next)
   double* mu = nullptr;             // 4 interior planes
   double* gpart = nullptr;          // per-block parameter partials
@@ -102,9 +104,25 @@ __device__ __forceinline__ double block_sum(double v, double* sh) {
   return r;
 }
 
-// mu = (dFric/dU~)^T lambda^{n+1} per interior cell; gradient of the friction
-// coefficient.  Fric: q <- q / den, den = 1 + dt C(h) |q|.
-__global__ void __launch_bounds__(kAdjThreads) adj_friction_kernel(DevParams P, DevState<double> S,
+// The convected (pre-friction) state U~ of every interior cell for the step
+// of size dt whose fluctuations the planes of S hold (4 planes of nx ny),
+// kept while a segment is recomputed for the friction adjoint.
+__global__ void __launch_bounds__(kAdjThreads) convect_save_kernel(DevParams P, DevState<double> S, double dt,
+                                                                   double* out) {
+  const long long ncell = (long long)P.nx * P.ny;
+  const long long k = (long long)blockIdx.x * kAdjThreads + threadIdx.x;
+  if (k >= ncell) return;
+  const int j = (int)(k / P.nx), i = (int)(k - (long long)j * P.nx);
+  double s[4];
+  sve::convect_cell(P, S, i, j, sve::ext_index(P, i, j), dt, s);
+#pragma unroll
+  for (int f = 0; f < 4; ++f) out[f * ncell + k] = s[f];
+}
+
+// mu = (dFric/dU~)^T lambda^{n+1} per interior cell, U~ = conv (the saved
+// convected state of the step); gradient of the friction coefficient.
+// Fric: q <- q / den, den = 1 + dt C(h) |q|.
+__global__ void __launch_bounds__(kAdjThreads) adj_friction_kernel(DevParams P, const double* conv,
                                                                    const double* lam, double* mu, double dt,
                                                                    double* gpart, double* gacc,
                                                                    unsigned int* done) {
@@ -113,9 +131,7 @@ __global__ void __launch_bounds__(kAdjThreads) adj_friction_kernel(DevParams P, 
   const long long k = (long long)blockIdx.x * kAdjThreads + threadIdx.x;
   double gk = 0.0;
   if (k < ncell) {
-    const int j = (int)(k / P.nx), i = (int)(k - (long long)j * P.nx);
-    double s[4];
-    sve::convect_cell(P, S, i, j, sve::ext_index(P, i, j), dt, s);
+    const double s[4] = {conv[k], conv[ncell + k], conv[2 * ncell + k], conv[3 * ncell + k]};
     const double lh = lam[k], l1 = lam[ncell + k], l2 = lam[2 * ncell + k], lz = lam[3 * ncell + k];
     double mh = lh, m1 = l1, m2 = l2;
     if (P.friction != 0) {
@@ -345,6 +361,7 @@ void free_rec(sve_adjoint_rec* r) {
   if (!r) return;
   for (double* c : r->checkpoints) cudaFree(c);
   if (r->seg) cudaFree(r->seg);
+  if (r->segc) cudaFree(r->segc);
   if (r->lam) cudaFree(r->lam);
   if (r->mu) cudaFree(r->mu);
   if (r->gpart) cudaFree(r->gpart);
@@ -353,14 +370,20 @@ void free_rec(sve_adjoint_rec* r) {
   delete r;
 }
 
-// one forward step of size dt with the handle's kernels (fixed-dt mode)
-int forward_step(sve_handle* h, double dt) {
+// one forward step of size dt with the handle's kernels (fixed-dt mode);
+// with conv, the step's convected (pre-friction) interior state is kept there
+int forward_step(sve_handle* h, double dt, double* conv = nullptr) {
   ADJ_TRY(cudaMemcpyAsync(h->fixed, &dt, sizeof(double), cudaMemcpyHostToDevice, h->stream));
   ADJ_TRY(cudaMemsetAsync(&h->sc->call_step, 0, sizeof(int), h->stream));
   DevState<double> S = state_of<double>(h);
   const unsigned nbi = (unsigned)sve::iface_blocks(h->P, sve::kThreadsStep);
   const unsigned nbc = (unsigned)sve::cell_blocks(h->P, sve::kThreadsStep);
   sve::interface_kernel<double><<<nbi, sve::kThreadsStep, 0, h->stream>>>(h->P, S, h->sc, h->fixed, h->dtlog, 1);
+  if (conv) {
+    const long long ncell = (long long)h->P.nx * h->P.ny;
+    convect_save_kernel<<<(unsigned)((ncell + kAdjThreads - 1) / kAdjThreads), kAdjThreads, 0, h->stream>>>(
+        h->P, S, dt, conv);
+  }
   sve::cell_kernel<double><<<nbc, sve::kThreadsStep, 0, h->stream>>>(h->P, S, h->sc, h->mpart);
   return cudaGetLastError() == cudaSuccess ? SVE_OK : SVE_ERR_CUDA;
 }
@@ -425,6 +448,8 @@ int sve_adjoint(sve_handle* h, const void* lam_h, const void* lam_hu, const void
   if (rc) return rc;
   rc = grow(&r->seg, &r->seg_cap, nst * (size_t)r->every);
   if (rc) return rc;
+  rc = grow(&r->segc, &r->segc_cap, 4 * (size_t)ncell * (size_t)r->every);
+  if (rc) return rc;
   double* lam = r->lam;             // lambda^{n+1}
   double* lam_next = r->lam + 4 * ncell;
   ADJ_TRY(cudaMemsetAsync(r->gacc, 0, sizeof(double) * 4, h->stream));
@@ -438,7 +463,6 @@ int sve_adjoint(sve_handle* h, const void* lam_h, const void* lam_hu, const void
       ADJ_TRY(cudaMemsetAsync(lam + f * ncell, 0, sizeof(double) * ncell, h->stream));
   }
   DevState<double> S = state_of<double>(h);
-  const unsigned nbi = (unsigned)sve::iface_blocks(P, sve::kThreadsStep);
   const unsigned nbc = (unsigned)sve::cell_blocks(P, sve::kThreads);
   const int ncp = (int)r->checkpoints.size();
   for (int k = ncp - 1; k >= 0; --k) {
@@ -450,20 +474,17 @@ int sve_adjoint(sve_handle* h, const void* lam_h, const void* lam_hu, const void
     sve::init_kernel<double><<<nbc, sve::kThreads, 0, h->stream>>>(P, S, h->sc, h->mpart);
     for (int s = 0; s < len; ++s) {
       rc = save_state(h, r->seg + (size_t)s * nst);
-      if (!rc) rc = forward_step(h, r->dts[n0 + s]);
+      if (!rc) rc = forward_step(h, r->dts[n0 + s], r->segc + (size_t)s * 4 * (size_t)ncell);
       if (rc) return rc;
     }
-    // reverse through the segment
+    // reverse through the segment: the saved padded state U^n (its ghosts
+    // included) and its convected state are all the adjoint kernels read
     for (int s = len - 1; s >= 0; --s) {
       const double dt = r->dts[n0 + s];
       rc = load_state(h, r->seg + (size_t)s * nst);
       if (rc) return rc;
-      sve::init_kernel<double><<<nbc, sve::kThreads, 0, h->stream>>>(P, S, h->sc, h->mpart);
-      // forward fluctuations of step n (needed for the pre-friction state)
-      ADJ_TRY(cudaMemcpyAsync(h->fixed, &dt, sizeof(double), cudaMemcpyHostToDevice, h->stream));
-      ADJ_TRY(cudaMemsetAsync(&h->sc->call_step, 0, sizeof(int), h->stream));
-      sve::interface_kernel<double><<<nbi, sve::kThreadsStep, 0, h->stream>>>(P, S, h->sc, h->fixed, h->dtlog, 1);
-      adj_friction_kernel<<<nb_c, kAdjThreads, 0, h->stream>>>(P, S, lam, r->mu, dt, r->gpart, r->gacc, r->done);
+      adj_friction_kernel<<<nb_c, kAdjThreads, 0, h->stream>>>(P, r->segc + (size_t)s * 4 * (size_t)ncell, lam,
+                                                              r->mu, dt, r->gpart, r->gacc, r->done);
       adj_interface_kernel<<<nb_if, kAdjThreads, 0, h->stream>>>(P, S, r->mu, dt, h->cfg.A_g, h->cfg.m_g,
                                                                  r->gpart, r->gacc, r->done);
       adj_gather_kernel<<<nb_c, kAdjThreads, 0, h->stream>>>(P, S, r->mu, lam_next);
@@ -473,6 +494,9 @@ int sve_adjoint(sve_handle* h, const void* lam_h, const void* lam_hu, const void
       lam_next = t;
     }
   }
+  // the handle holds U^0 again (the last state loaded): project it, so that
+  // stepping on from here starts from a consistent state
+  sve::init_kernel<double><<<nbc, sve::kThreads, 0, h->stream>>>(P, S, h->sc, h->mpart);
   rc = status_of(h);
   if (rc) return rc;
   const cudaMemcpyKind kout = where == SVE_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;

@@ -154,3 +154,25 @@ def test_gpu_adjoint_equals_oracle_adjoint(bc, friction):
     print("adjoint vs oracle adjoint:", errs, perr)
     assert max(errs.values()) <= 1e-10, errs
     assert max(perr) <= 1e-10, (gp, og["params"])
+
+
+def test_stepping_after_the_adjoint():
+    """After sve_adjoint the handle holds the recorded run's initial state:
+    stepping on from there equals stepping from that state afresh."""
+    w, target = case()
+    p = w["params"]
+    s = sve.Solver(p, "fp64")
+    s.set_state(w["h"], w["hu"], w["hv"], w["z"])
+    s.record_forward(25, 5)
+    fin = s.get_state()
+    s.adjoint(lam_z=2.0 * (fin["z"] - target))
+    s.step(15)
+    after = s.get_state()
+    s.close()
+    s2 = sve.Solver(p, "fp64")
+    s2.set_state(w["h"], w["hu"], w["hv"], w["z"])
+    s2.step(15)
+    ref = s2.get_state()
+    s2.close()
+    for k in ("h", "hu", "hv", "z"):
+        assert np.max(np.abs(after[k] - ref[k])) <= 1e-12 * max(np.max(np.abs(ref[k])), 1e-300), k
