@@ -122,8 +122,13 @@ __device__ __forceinline__ Cell<double> project_grass_rec(const DevParams& P, do
     r.sp = r.pm1 = r.pm3 = 0.0;
   } else {
     r.sp = sqrt(s2);
-    r.pm1 = pow(r.sp, m - 1.0);
-    r.pm3 = pow(r.sp, m - 3.0);
+    // |U|^(m-1), |U|^(m-3): products for the integer exponents of the
+    // Grass law in use, pow otherwise
+    if (m == 3.0) { r.pm1 = s2; r.pm3 = 1.0; }
+    else if (m == 2.0) { r.pm1 = r.sp; r.pm3 = 1.0 / r.sp; }
+    else if (m == 4.0) { r.pm1 = s2 * r.sp; r.pm3 = r.sp; }
+    else if (m == 1.0) { r.pm1 = 1.0; r.pm3 = 1.0 / s2; }
+    else { r.pm1 = pow(r.sp, m - 1.0); r.pm3 = pow(r.sp, m - 3.0); }
     Q = A * c.un * r.pm1;
     dQ = A * (r.pm1 + (m - 1.0) * (c.un * c.un) * r.pm3);
   }
