@@ -172,35 +172,57 @@ def dist_setup():
     return world, rank, local
 
 
-def cpu_oracle_rate(w, budget_s: float = 10.0, max_steps: int = 20):
+def _oracle_stepper(o, P, st, threads: int):
+    """A callable advancing the oracle state by n steps: the whole-grid
+    stepper on one thread, or the row-banded oracle on ``threads`` threads
+    (2D; bit-identical results)."""
+    from oracle.banded import BandedRun
+
+    if threads > 1 and P.dim == 2:
+        run = BandedRun(o, P, *st, nbands=threads, threads=threads)
+        return run.step, run.close
+    cur = {"st": st}
+
+    def step(n):
+        r = o.run(P, n, *cur["st"])
+        cur["st"] = (r["h"], r["hu"], r["hv"], r["z"])
+
+    return step, (lambda: None)
+
+
+def cpu_oracle_rate(w, threads: int, budget_s: float = 10.0, max_steps: int = 40):
     """The FP64 oracle on the host, as it stands, on the full grid of the
-    workload for as many steps as fit in about budget_s (at least 1)."""
+    workload for as many steps as fit in about budget_s (at least 1), on
+    ``threads`` threads (row bands of the oracle's block API when > 1)."""
     import oracle
 
     o = oracle.get()
     P = oracle.Params.from_workload(w["params"])
     cells = w["params"]["nx"] * w["params"]["ny"]
-    t0 = time.perf_counter()
-    r = o.run(P, 1, w["h"], w["hu"], w["hv"], w["z"])
-    t1 = time.perf_counter()
-    first = t1 - t0
-    more = int(max(0, min(max_steps - 1, math.floor(budget_s / max(first, 1e-9)) - 1)))
-    if more > 0:
-        t2 = time.perf_counter()
-        o.run(P, more, r["h"], r["hu"], r["hv"], r["z"])
-        t3 = time.perf_counter()
-        steps, secs = more, t3 - t2
-    else:
-        steps, secs = 1, first
+    step, close = _oracle_stepper(o, P, (w["h"], w["hu"], w["hv"], w["z"]), threads)
+    try:
+        t0 = time.perf_counter()
+        step(1)
+        first = time.perf_counter() - t0
+        more = int(max(0, min(max_steps - 1, math.floor(budget_s / max(first, 1e-9)) - 1)))
+        if more > 0:
+            t2 = time.perf_counter()
+            step(more)
+            steps, secs = more, time.perf_counter() - t2
+        else:
+            steps, secs = 1, first
+    finally:
+        close()
     return cells * steps / secs, steps, secs
 
 
 def run_reference(args, world, rank):
-    """Reference arm: the FP64 CPU oracle timed on the host cores, one full
-    grid step per step."""
+    """Reference arm: the FP64 CPU oracle timed on all host cores (row bands
+    of the oracle's block API on threads), one full-grid step per step."""
     if rank != 0:
         return 0
     import oracle
+    from oracle.banded import host_threads
     from paper_1307_0491_gb300 import workloads as W
 
     w = make_workload(args, W)
@@ -208,40 +230,46 @@ def run_reference(args, world, rank):
     o = oracle.get()
     P = oracle.Params.from_workload(w["params"])
     st = (w["h"], w["hu"], w["hv"], w["z"])
+    threads = host_threads()
     # one full-grid step sets the size of the sample: if all steps on the
     # full grid would take more than ~2 minutes, every step runs on the first
     # ny' rows of the workload (same physics and boundary types)
+    step, close = _oracle_stepper(o, P, st, threads)
     t0 = time.perf_counter()
-    o.run(P, 1, *st)
+    step(1)
     t_full = time.perf_counter() - t0
+    close()
     budget = 120.0
     ny_full = ny
     sample = f"full {nx}x{ny} grid"
     if (args.steps + args.warmup) * t_full > budget and w["params"]["dim"] == 2:
-        nys = max(8, int(ny * budget / ((args.steps + args.warmup) * t_full)))
+        nys = max(8 * threads, int(ny * budget / ((args.steps + args.warmup) * t_full)))
+        nys = min(nys, ny)
         p2 = dict(w["params"], ny=nys, ly=w["params"]["ly"] * nys / ny)
         w = dict(w, params=p2, h=w["h"][:nys], hu=w["hu"][:nys], hv=w["hv"][:nys], z=w["z"][:nys])
         ny = nys
         P = oracle.Params.from_workload(p2)
         st = (w["h"], w["hu"], w["hv"], w["z"])
         sample = f"rows 0..{nys - 1} of the {nx}x{ny_full} grid"
-    # the warm-up and the timed steps as one oracle call each (the oracle's
-    # own stepping loop, no per-step marshalling in the timed region)
-    r = o.run(P, args.warmup, *st)
-    st = (r["h"], r["hu"], r["hv"], r["z"])
-    t0 = time.perf_counter()
-    o.run(P, args.steps, *st)
-    secs = time.perf_counter() - t0
+    step, close = _oracle_stepper(o, P, st, threads)
+    try:
+        step(args.warmup)
+        t0 = time.perf_counter()
+        step(args.steps)
+        secs = time.perf_counter() - t0
+    finally:
+        close()
     value = nx * ny * args.steps / secs
+    how = (f"C oracle (-O2, no FMA contraction) on {threads} threads, row bands of its block API"
+           if threads > 1 and P.dim == 2 else "single-threaded C oracle (-O2, no FMA contraction)")
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": secs / args.steps * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": workload_desc(nx, ny_full, args.workload, args.precision), "nx": nx, "ny": ny_full,
                    "precision": args.precision},
-        "cpu_baseline": {"kind": "oracle", "cores": 1, "value": value, "unit": UNIT,
-                         "sample": f"{sample}, {args.steps} steps after {args.warmup} warm-up steps, "
-                                   f"single-threaded C oracle (-O2, no FMA contraction)"},
+        "cpu_baseline": {"kind": "oracle", "cores": threads if P.dim == 2 else 1, "value": value, "unit": UNIT,
+                         "sample": f"{sample}, {args.steps} steps after {args.warmup} warm-up steps, {how}"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -652,10 +680,17 @@ def run_ours(args, world, rank, local):
         if args.paper_bump2d:
             line["paper_bump2d"] = run_paper_bump(args, sve, W, torch)
         if world == 1 and not args.no_cpu_baseline:
-            rate, nsteps, secs = cpu_oracle_rate(w)
-            line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
+            from oracle.banded import host_threads
+
+            cores = host_threads()
+            rate, nsteps, secs = cpu_oracle_rate(w, cores)
+            line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
                                     "sample": f"full {nx}x{ny} grid, {nsteps} step(s) in {secs:.1f} s, "
-                                              f"single-threaded C oracle"}
+                                              f"C oracle on {cores} threads (row bands of its block API)"}
+            rate1, nsteps1, secs1 = cpu_oracle_rate(w, 1)
+            line["cpu_baseline"]["single_thread"] = {
+                "value": rate1, "cores": 1,
+                "sample": f"full {nx}x{ny} grid, {nsteps1} step(s) in {secs1:.1f} s, single-threaded C oracle"}
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.barrier()
