@@ -618,6 +618,10 @@ def run_ours(args, world, rank, local):
                 "iface_ms": iface_ms, "cell_ms": cell_ms,
                 "hbm_frac_of_step": (bytes_per_cell * cells / (ms_per_step * 1e-3)) / (hbm * 1e9),
                 "hbm_peak_gbs": hbm}
+    if roofline["traffic"]:
+        # the kernel's DRAM throughput from its ncu byte count and its event time
+        roofline["dram_gbs"] = roofline["traffic"] / (iface_ms * 1e-3) / 1e9
+        roofline["dram_frac"] = roofline["dram_gbs"] / hbm
     if prec == "fp32":
         roofline = roofline_fp32
 
