@@ -149,6 +149,29 @@ int sve_step_dt(sve_handle* h, int nsteps, const double* dts);
  * until the copy is done. */
 int sve_get_state(sve_handle* h, void* depth, void* hu, void* hv, void* zb, int where);
 
+/* From a caller's state to a caller's state in one call: sve_set_state of
+ * (depth_in, hu_in, hv_in, zb_in), nsteps >= 1 CFL steps (Sec. 3: the time
+ * step of each from the CFL condition of its state), then the interior state
+ * into (depth_out, hu_out, hv_out, zb_out); row-major ny x nx arrays of the
+ * handle's precision, all in the memory `where` names (SVE_HOST or
+ * SVE_DEVICE; hv_in / hv_out may be NULL in 1D).  The caller owns all eight
+ * buffers; in and out may be the same buffers.  Output buffers in device
+ * memory, and in page-locked host memory (cudaHostAlloc, cudaHostRegister)
+ * for the two-kernel step (FP64, and FP32 in 1D), are written by the last
+ * step's cell update itself, so that with host buffers the result crosses
+ * the host link while that kernel computes; other host buffers (pageable,
+ * or for the FP32 2D step, whose memory-bound update pass the link would
+ * slow down) are copied after the last step.  *t_out (nullable)
+ * receives the simulated time (the state's time starts at 0).  Blocks until
+ * the result is in place.  Returns SVE_ERR_ARG for a NULL handle or buffer,
+ * nsteps < 1 or an unknown `where`, SVE_ERR_CUDA for a failed CUDA call,
+ * else the first device error latched by the upload checks or the steps
+ * (SVE_ERR_NEG_DEPTH, SVE_ERR_NAN, SVE_ERR_RIEMANN, SVE_ERR_DT); the output
+ * buffers then hold the state the steps reached. */
+int sve_advance(sve_handle* h, int nsteps, const void* depth_in, const void* hu_in, const void* hv_in,
+                const void* zb_in, void* depth_out, void* hu_out, void* hv_out, void* zb_out, int where,
+                double* t_out);
+
 /* Diagnostics after the last step: mass_h = sum h dx dy, mass_z = sum zb dx dy
  * (FP64, summed in a fixed order), the simulated time and the last time step.
  * Any pointer may be NULL.  Blocks. */

@@ -384,7 +384,8 @@ int forward_step(sve_handle* h, double dt, double* conv = nullptr) {
     convect_save_kernel<<<(unsigned)((ncell + kAdjThreads - 1) / kAdjThreads), kAdjThreads, 0, h->stream>>>(
         h->P, S, dt, conv);
   }
-  sve::cell_kernel<double><<<nbc, sve::kThreadsStep, 0, h->stream>>>(h->P, S, h->sc, h->mpart);
+  sve::cell_kernel<double><<<nbc, sve::kThreadsStep, 0, h->stream>>>(h->P, S, h->sc, h->mpart,
+                                                                     sve::Mirror<double>{});
   return cudaGetLastError() == cudaSuccess ? SVE_OK : SVE_ERR_CUDA;
 }
 

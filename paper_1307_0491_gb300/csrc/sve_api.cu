@@ -118,8 +118,10 @@ void make_params(const sve_config* c, DevParams* P) {
 }
 
 template <typename T>
-void launch_step(sve_handle* h, cudaStream_t st, int fixed, cudaEvent_t* ev) {
+void launch_step(sve_handle* h, cudaStream_t st, int fixed, cudaEvent_t* ev, const void* const* mirror) {
   DevState<T> S = state_of<T>(h);
+  sve::Mirror<T> out{};
+  if (mirror) out = {(T*)mirror[0], (T*)mirror[1], (T*)mirror[2], (T*)mirror[3]};
   const int nt = h->nt;
   const unsigned nbi = (unsigned)sve::iface_blocks(h->P, nt), nbc = (unsigned)sve::cell_blocks(h->P, nt);
   if (ev) cudaEventRecord(ev[0], st);
@@ -131,17 +133,17 @@ void launch_step(sve_handle* h, cudaStream_t st, int fixed, cudaEvent_t* ev) {
     sve::interface_kernel<T, sve::kThreads><<<nbi, nt, 0, st>>>(h->P, S, h->sc, h->fixed, h->dtlog, fixed);
   if (ev) cudaEventRecord(ev[1], st);
   if (nt == sve::kThreadsNarrow)
-    sve::cell_kernel<T, sve::kThreadsNarrow><<<nbc, nt, 0, st>>>(h->P, S, h->sc, h->mpart);
+    sve::cell_kernel<T, sve::kThreadsNarrow><<<nbc, nt, 0, st>>>(h->P, S, h->sc, h->mpart, out);
   else if (nt == sve::kThreadsStep)
-    sve::cell_kernel<T, sve::kThreadsStep><<<nbc, nt, 0, st>>>(h->P, S, h->sc, h->mpart);
+    sve::cell_kernel<T, sve::kThreadsStep><<<nbc, nt, 0, st>>>(h->P, S, h->sc, h->mpart, out);
   else
-    sve::cell_kernel<T, sve::kThreads><<<nbc, nt, 0, st>>>(h->P, S, h->sc, h->mpart);
+    sve::cell_kernel<T, sve::kThreads><<<nbc, nt, 0, st>>>(h->P, S, h->sc, h->mpart, out);
   if (ev) cudaEventRecord(ev[2], st);
 }
 
 // FP32 state in 2D: the solve pass (fluctuations on chip, net fluctuation
 // per cell out, time step from the solves) and the in-place apply pass.
-void launch_fused_step(sve_handle* h, cudaStream_t st, int fixed, cudaEvent_t* ev) {
+void launch_fused_step(sve_handle* h, cudaStream_t st, int fixed, cudaEvent_t* ev, const void* const* mirror) {
   sve::StateBuf<float> B;
   B.h = (float*)h->fields[0]; B.hu = (float*)h->fields[1]; B.hv = (float*)h->fields[2]; B.z = (float*)h->fields[3];
   const size_t ncell = (size_t)h->P.nx * (size_t)h->P.ny;
@@ -152,14 +154,19 @@ void launch_fused_step(sve_handle* h, cudaStream_t st, int fixed, cudaEvent_t* e
   sve::solve_kernel<float><<<h->fgrid_solve, sve::kFThreads, 0, st>>>(h->P, B, D, h->sc, h->fixed, h->dtlog, fixed,
                                                                       ntiles, h->fgx);
   if (ev) cudaEventRecord(ev[1], st);
-  sve::apply_kernel<float><<<dim3(h->agx, h->agy), sve::kAThreads, 0, st>>>(h->P, B, D, h->sc, h->mpart);
+  sve::Mirror<float> out{};
+  if (mirror) out = {(float*)mirror[0], (float*)mirror[1], (float*)mirror[2], (float*)mirror[3]};
+  sve::apply_kernel<float><<<dim3(h->agx, h->agy), sve::kAThreads, 0, st>>>(h->P, B, D, h->sc, h->mpart, out);
   if (ev) cudaEventRecord(ev[2], st);
 }
 
-void launch_step_any(sve_handle* h, cudaStream_t st, int fixed, cudaEvent_t* ev = nullptr) {
-  if (h->cfg.precision == SVE_FP64) launch_step<double>(h, st, fixed, ev);
-  else if (h->fused) launch_fused_step(h, st, fixed, ev);
-  else launch_step<float>(h, st, fixed, ev);
+// mirror: null, or four row-major destinations (device-accessible) that the
+// step's cell update also writes the new interior state to.
+void launch_step_any(sve_handle* h, cudaStream_t st, int fixed, cudaEvent_t* ev = nullptr,
+                     const void* const* mirror = nullptr) {
+  if (h->cfg.precision == SVE_FP64) launch_step<double>(h, st, fixed, ev, mirror);
+  else if (h->fused) launch_fused_step(h, st, fixed, ev, mirror);
+  else launch_step<float>(h, st, fixed, ev, mirror);
 }
 
 // Three events for one profiled step (grown on demand).
@@ -226,7 +233,7 @@ void drop_graphs(sve_handle* h) {
 
 // Enqueue nsteps steps on the handle's stream (graphs of kGraphSteps steps
 // where possible; single launches with events when profiling).
-int enqueue_steps(sve_handle* h, int nsteps, int fixed) {
+int enqueue_steps(sve_handle* h, int nsteps, int fixed, const void* const* mirror = nullptr) {
   if (!h->has_state) return SVE_ERR_STATE;
   double* old = h->dtlog;
   int rc = ensure_capacity(&h->dtlog, &h->dtlog_cap, nsteps > 0 ? nsteps : 1);
@@ -234,16 +241,18 @@ int enqueue_steps(sve_handle* h, int nsteps, int fixed) {
   if (h->dtlog != old) drop_graphs(h);  // graphs hold the dtlog pointer
   SVE_TRY(cudaMemsetAsync(&h->sc->call_step, 0, sizeof(int), h->stream));
   int done = 0;
-  if (nsteps >= kGraphSteps && !h->profiling) {
+  // with a mirror the last step is a single launch (the graphs write no mirror)
+  const int graphed = mirror ? nsteps - 1 : nsteps;
+  if (graphed >= kGraphSteps && !h->profiling) {
     cudaGraphExec_t ex;
     rc = get_graph(h, fixed, &ex);
     if (rc) return rc;
-    for (; done + kGraphSteps <= nsteps; done += kGraphSteps) SVE_TRY(cudaGraphLaunch(ex, h->stream));
+    for (; done + kGraphSteps <= graphed; done += kGraphSteps) SVE_TRY(cudaGraphLaunch(ex, h->stream));
   }
   for (; done < nsteps; ++done) {
     cudaEvent_t* ev = h->profiling ? next_events(h) : nullptr;
     if (h->profiling && !ev) return SVE_ERR_CUDA;
-    launch_step_any(h, h->stream, fixed, ev);
+    launch_step_any(h, h->stream, fixed, ev, done == nsteps - 1 ? mirror : nullptr);
   }
   SVE_TRY(cudaGetLastError());
   h->last_launches = 2LL * nsteps;
@@ -355,6 +364,11 @@ int run_steps(sve_handle* h, int nsteps, int fixed) {
   return wait_status(h);
 }
 
+// Upload, projection, checks and ghosts of a caller's state, enqueued on the
+// handle's stream (status bits latched in the scalars, not read).
+int enqueue_set_state(sve_handle* h, const void* depth, const void* hu, const void* hv, const void* zb, int where);
+void* direct_ptr(void* p, int where);
+
 }  // namespace
 
 // Shared with sve_noalloc.cu (not part of the C ABI).
@@ -460,6 +474,55 @@ int sve_set_stream(sve_handle* h, void* stream) {
 }
 
 int sve_set_state(sve_handle* h, const void* depth, const void* hu, const void* hv, const void* zb, int where) {
+  const int rc = enqueue_set_state(h, depth, hu, hv, zb, where);
+  if (rc) return rc;
+  DevScalars s;
+  SVE_TRY(cudaMemcpyAsync(&s, h->sc, sizeof(s), cudaMemcpyDeviceToHost, h->stream));
+  SVE_TRY(cudaStreamSynchronize(h->stream));
+  return status_to_code(s.status);
+}
+
+int sve_advance(sve_handle* h, int nsteps, const void* depth_in, const void* hu_in, const void* hv_in,
+                const void* zb_in, void* depth_out, void* hu_out, void* hv_out, void* zb_out, int where,
+                double* t_out) {
+  if (!h || nsteps < 1) return SVE_ERR_ARG;
+  if (!depth_out || !hu_out || !zb_out || (h->cfg.dim == 2 && !hv_out)) return SVE_ERR_ARG;
+  int rc = enqueue_set_state(h, depth_in, hu_in, hv_in, zb_in, where);
+  if (rc) return rc;
+  void* out[4] = {depth_out, hu_out, h->cfg.dim == 2 ? hv_out : nullptr, zb_out};
+  const void* mirror[4] = {nullptr, nullptr, nullptr, nullptr};
+  // Direct stores from the last cell update: into device memory always; into
+  // page-locked host memory when that update is the FP64-bound cell kernel,
+  // whose run time covers the host-link time of its stores.  The FP32 fused
+  // step's apply pass is memory-bound, and host stores from it make it
+  // link-bound (slower than a copy after it).
+  bool direct = where == SVE_DEVICE || !h->fused;
+  for (int f = 0; f < 4; ++f) {
+    if (!out[f]) continue;
+    mirror[f] = direct_ptr(out[f], where);
+    direct = direct && mirror[f];
+  }
+  rc = enqueue_steps(h, nsteps, 0, direct ? mirror : nullptr);
+  if (rc) return rc;
+  if (!direct) {
+    const DevParams& P = h->P;
+    const size_t row = h->elem * (size_t)P.nx, pitch = h->elem * (size_t)P.ex;
+    for (int f = 0; f < 4; ++f) {
+      if (!out[f]) continue;
+      const char* src = (const char*)h->fields[f] + h->elem * (size_t)(P.ex + 1);
+      SVE_TRY(cudaMemcpy2DAsync(out[f], row, src, pitch, row, P.ny, cudaMemcpyDefault, h->stream));
+    }
+  }
+  rc = wait_status(h);
+  if (t_out && rc != SVE_ERR_CUDA) *t_out = h->last_t;
+  return rc;
+}
+
+}  // extern "C"
+
+namespace {
+
+int enqueue_set_state(sve_handle* h, const void* depth, const void* hu, const void* hv, const void* zb, int where) {
   if (!h || !depth || !hu || !zb || (h->cfg.dim == 2 && !hv)) return SVE_ERR_ARG;
   if (where != SVE_HOST && where != SVE_DEVICE) return SVE_ERR_ARG;
   const DevParams& P = h->P;
@@ -486,13 +549,27 @@ int sve_set_state(sve_handle* h, const void* depth, const void* hu, const void* 
       sve::init_kernel<float><<<(unsigned)sve::cell_blocks(h->P, sve::kThreads), sve::kThreads, 0, h->stream>>>(P, state_of<float>(h), h->sc, h->mpart);
   }
   SVE_TRY(cudaGetLastError());
-  DevScalars s;
-  SVE_TRY(cudaMemcpyAsync(&s, h->sc, sizeof(s), cudaMemcpyDeviceToHost, h->stream));
-  SVE_TRY(cudaStreamSynchronize(h->stream));
   h->has_state = true;
   h->last_steps = 0;
-  return status_to_code(s.status);
+  return SVE_OK;
 }
+
+// Device-accessible address of a caller's output buffer for direct stores
+// from the kernels: device memory as it is, page-locked host memory through
+// its device mapping; null for pageable host memory (copied instead).
+void* direct_ptr(void* p, int where) {
+  if (where == SVE_DEVICE) return p;
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return (a.type == cudaMemoryTypeHost && a.devicePointer) ? a.devicePointer : nullptr;
+}
+
+}  // namespace
+
+extern "C" {
 
 int sve_step(sve_handle* h, int nsteps, double* t_out) {
   if (!h || nsteps < 0) return SVE_ERR_ARG;

@@ -80,6 +80,15 @@ struct DevState {
   T *fx, *fy;                                // fluctuations: 8 planes (A- H,qn,qt,Z, A+ H,qn,qt,Z)
 };
 
+// Optional second destination of a step's new interior state: row-major
+// ny x nx arrays (h is null when unused; hv unused in 1D).  A caller's
+// page-locked host buffers go here, so that the last step of a host-to-host
+// call stores its result over the host link from the cell update itself.
+template <typename T>
+struct Mirror {
+  T *h, *hu, *hv, *z;
+};
+
 template <typename T> __device__ __forceinline__ T tmax(T a, T b) { return a > b ? a : b; }
 template <typename T> __device__ __forceinline__ T tabs(T a) { return a < T(0) ? -a : a; }
 // Quotients and square roots: IEEE in FP64; in the FP32-state path the
@@ -921,7 +930,7 @@ __device__ __forceinline__ void convect_cell(const DevParams& P, const DevState<
 
 template <typename T>
 __device__ __forceinline__ int cell_item(const DevParams& P, const DevState<T>& S, long long k, double dt,
-                                         double& mh, double& mz) {
+                                         double& mh, double& mz, const Mirror<T>& out = Mirror<T>{}) {
   const int j = (int)(k / P.nx);
   const int i = (int)(k - (long long)j * P.nx);
   const long long e = ext_index(P, i, j);
@@ -943,6 +952,12 @@ __device__ __forceinline__ int cell_item(const DevParams& P, const DevState<T>& 
   else if (!positive(s[0])) st = ST_NEG_DEPTH;
   store_cell(P, S, e, s, tau);
   write_ghosts(P, S, i, j, s);
+  if (out.h) {
+    out.h[k] = s[0];
+    out.hu[k] = s[1];
+    if (P.dim == 2) out.hv[k] = s[2];
+    out.z[k] = s[3];
+  }
   mh = (double)s[0];
   mz = (double)s[3];
   return st;
@@ -951,7 +966,8 @@ __device__ __forceinline__ int cell_item(const DevParams& P, const DevState<T>& 
 // One thread per interior cell (i, j): Godunov average in fluctuation form,
 // friction, checks, projection of the new state, ghosts, mass partials.
 template <typename T, int NT = kThreadsStep>
-__global__ void __launch_bounds__(NT) cell_kernel(DevParams P, DevState<T> S, DevScalars* sc, double* mpart) {
+__global__ void __launch_bounds__(NT) cell_kernel(DevParams P, DevState<T> S, DevScalars* sc, double* mpart,
+                                                   Mirror<T> out) {
   // per-thread (h, z) of the new state, and how many warps have stored theirs
   __shared__ double s_m[2][NT];
   __shared__ unsigned int s_warps;
@@ -961,7 +977,7 @@ __global__ void __launch_bounds__(NT) cell_kernel(DevParams P, DevState<T> S, De
   const long long ncell = (long long)P.nx * P.ny;
   double mh = 0.0, mz = 0.0;
   if (k < ncell) {
-    const int st = cell_item(P, S, k, sc->dt, mh, mz);
+    const int st = cell_item(P, S, k, sc->dt, mh, mz, out);
     if (st) atomicOr(&sc->status, st);
   }
   // The block's mass partial, in a fixed order and with no block barrier:

@@ -248,7 +248,7 @@ constexpr int kAThreads = 256;
 
 template <typename T>
 __global__ void __launch_bounds__(kAThreads) apply_kernel(DevParams P, StateBuf<T> B, NetFluct<T> D,
-                                                          DevScalars* sc, double* mpart) {
+                                                          DevScalars* sc, double* mpart, Mirror<T> out) {
   static_assert(sizeof(T) == 4, "the fused step is the FP32 form");
   __shared__ double s_m[2][kAThreads];
   __shared__ unsigned int s_warps;
@@ -274,6 +274,7 @@ __global__ void __launch_bounds__(kAThreads) apply_kernel(DevParams P, StateBuf<
       if (!(finite_bits(s[0]) && finite_bits(s[1]) && finite_bits(s[2]) && finite_bits(s[3]))) st |= ST_NAN;
       else if (!positive(s[0])) st |= ST_NEG_DEPTH;
       B.h[e] = s[0]; B.hu[e] = s[1]; B.hv[e] = s[2]; B.z[e] = s[3];
+      if (out.h) { out.h[k] = s[0]; out.hu[k] = s[1]; out.hv[k] = s[2]; out.z[k] = s[3]; }
       write_ghost_state(P, B, i, j, s);
       sh_h.add(s[0]);
       sh_z.add(s[3]);

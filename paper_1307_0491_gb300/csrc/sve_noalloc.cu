@@ -114,7 +114,7 @@ int run(const sve::DevParams& P, unsigned char* base, const Layout& L, int nb_if
     if (cudaMemsetAsync(&sc->call_step, 0, sizeof(int), st) != cudaSuccess) return SVE_ERR_CUDA;
     for (int s = 0; s < chunk; ++s) {
       sve::interface_kernel<T><<<nb_iface, sve::kThreadsStep, 0, st>>>(P, S, sc, dtlog, dtlog, 0);
-      sve::cell_kernel<T><<<nb_cell, sve::kThreadsStep, 0, st>>>(P, S, sc, mpart);
+      sve::cell_kernel<T><<<nb_cell, sve::kThreadsStep, 0, st>>>(P, S, sc, mpart, sve::Mirror<T>{});
     }
     done += chunk;
   }

@@ -35,7 +35,7 @@ EXPORTS = ("sve_config_default", "sve_create", "sve_set_stream", "sve_set_state"
            "sve_batch_create", "sve_batch_set_stream", "sve_batch_set_state", "sve_batch_step",
            "sve_batch_step_async", "sve_batch_get_state", "sve_batch_get_diag", "sve_batch_get_counters",
            "sve_batch_autotune", "sve_batch_set_schedule", "sve_batch_last_launch_count", "sve_batch_destroy",
-           "sve_record_forward", "sve_adjoint", "sve_set_block_size", "sve_get_block_size")
+           "sve_record_forward", "sve_adjoint", "sve_set_block_size", "sve_get_block_size", "sve_advance")
 
 
 class sve_config(ctypes.Structure):
@@ -81,6 +81,7 @@ def load() -> ctypes.CDLL:
         "sve_step": ([vp, ip, dp], ip),
         "sve_step_dt": ([vp, ip, dp], ip),
         "sve_get_state": ([vp, vp, vp, vp, vp, ip], ip),
+        "sve_advance": ([vp, ip, vp, vp, vp, vp, vp, vp, vp, vp, ip, dp], ip),
         "sve_get_diag": ([vp, dp, dp, dp, dp], ip),
         "sve_get_dts": ([vp, dp, ip], ip),
         "sve_destroy": ([vp], None),
@@ -150,6 +151,13 @@ def sve_step_dt(h, dts) -> int:
 
 def sve_get_state(h, depth: int, hu: int, hv: int | None, zb: int, where: int) -> int:
     return load().sve_get_state(h, depth, hu, hv, zb, where)
+
+
+def sve_advance(h, nsteps: int, inp, out, where: int) -> tuple[int, float]:
+    """inp, out: four buffer addresses each (h, hu, hv or None, z)."""
+    t = ctypes.c_double(0.0)
+    rc = load().sve_advance(h, int(nsteps), *inp, *out, where, ctypes.byref(t))
+    return rc, t.value
 
 
 def sve_get_diag(h) -> tuple[int, dict]:
@@ -388,6 +396,29 @@ class Solver:
                              out["hv"].ctypes.data if out["hv"] is not None else None, out["z"].ctypes.data,
                              SVE_HOST), "sve_get_state")
         return out
+
+    def advance(self, nsteps: int, inp: dict, out: dict) -> float:
+        """sve_advance from the arrays of ``inp`` to those of ``out`` (keys
+        h, hu, hv, z; numpy arrays -- page-locked if they come from a pinned
+        torch tensor's ``.numpy()`` -- or CUDA tensors, all of one kind, of
+        the state dtype, contiguous); returns the simulated time."""
+        def addr(a):
+            if a is None:
+                return None
+            if hasattr(a, "data_ptr"):
+                return a.data_ptr()
+            if not (a.flags["C_CONTIGUOUS"] and a.dtype == self.dtype):
+                raise ValueError("sve_advance: contiguous arrays of the state dtype required")
+            return a.ctypes.data
+        keys = ("h", "hu", "hv", "z")
+        on_dev = [bool(getattr(x[k], "is_cuda", False)) for x in (inp, out) for k in keys if x.get(k) is not None]
+        if any(on_dev) and not all(on_dev):
+            raise ValueError("sve_advance: all buffers on the host or all on the device")
+        where = SVE_DEVICE if on_dev and on_dev[0] else SVE_HOST
+        rc, t = sve_advance(self.h, nsteps, [addr(inp.get(k)) for k in keys], [addr(out.get(k)) for k in keys],
+                            where)
+        _check(rc, "sve_advance")
+        return t
 
     def get_state_device(self, h, hu, hv, z) -> None:
         """Copy the state into CUDA tensors (contiguous, state dtype)."""
