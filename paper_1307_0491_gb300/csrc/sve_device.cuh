@@ -363,15 +363,22 @@ __device__ __forceinline__ void newton_sigma(T p, const NewtonConst<T>& c, Newto
   e.tau3 = T(0.5) * (sigma + c.D);
 }
 
+// The states and F at p, with ip = 1/p given.
 template <typename T>
-__device__ __forceinline__ void newton_eval(T p, const NewtonConst<T>& c, const Cell<T>& L, const Cell<T>& R,
-                                            NewtonEval<T>& e) {
+__device__ __forceinline__ void newton_eval_ip(T p, T ip, const NewtonConst<T>& c, const Cell<T>& L,
+                                               const Cell<T>& R, NewtonEval<T>& e) {
   T sigma;
   newton_sigma(p, c, e, sigma);
   const T N = c.dZ + c.K * c.D * sigma;
-  e.ip = tdiv(T(1), p);
+  e.ip = ip;
   e.m = -N * e.ip * c.inv_K;                        // from Z* continuity
   newton_states(p, c, L, R, e);
+}
+
+template <typename T>
+__device__ __forceinline__ void newton_eval(T p, const NewtonConst<T>& c, const Cell<T>& L, const Cell<T>& R,
+                                            NewtonEval<T>& e) {
+  newton_eval_ip(p, tdiv(T(1), p), c, L, R, e);
 }
 
 // Analytic F'(p) at an evaluated point.
@@ -459,12 +466,13 @@ template <> __device__ __forceinline__ float newton_floor<float>() { return 64.0
 
 // Root of F for one interface, from p0 (the root of the fluid part alone).
 // Returns false if no root with positive tau_k was reached.
+// ip0 = 1/p0.
 template <typename T>
 __device__ __forceinline__ bool newton_root(const DevParams& P, const NewtonConst<T>& c, const Cell<T>& L,
-                                            const Cell<T>& R, T p0, NewtonEval<T>& e, int& iters) {
+                                            const Cell<T>& R, T p0, T ip0, NewtonEval<T>& e, int& iters) {
   const T tol = tmax(par<T>(P.newton_tol, P.f.newton_tol), newton_floor<T>());
   T p = p0;
-  newton_eval(p, c, L, R, e);
+  newton_eval_ip(p, ip0, c, L, R, e);
   return newton_loop(c, L, R, p, e, P.newton_maxit, tol, iters);
 }
 
@@ -484,19 +492,30 @@ __device__ __forceinline__ void celerities(const DevParams& P, const Cell<T>& L,
 }
 
 // Constants of the Newton iteration; returns its start p0, the root of the
-// fluid part alone (Suliciu), p = sigma.
+// fluid part alone (Suliciu), p = sigma; *ip0 (if given) receives 1/p0.
 template <typename T>
 __device__ __forceinline__ T newton_setup(const DevParams& P, const Cell<T>& L, const Cell<T>& R, T a, T b,
-                                          NewtonConst<T>& c) {
+                                          NewtonConst<T>& c, T* ip0 = nullptr) {
   const T g = par<T>(P.g, P.f.g);
-  // one divide for 1/a, 1/b and 1/K (a^2 - b^2 >= (1 - 1/kappa_a^2) a^2 > 0)
   const T ab = a * b;
   const T a2mb2 = a * a - b * b;
+  const T du = R.un - L.un;
+  c.C0 = du + a * (L.tau + R.tau);  // a p0
   T rab;
   if constexpr (cheap_div<T>::value) {
     rab = tdiv(T(1), ab);
     c.inv_K = tdiv(T(2) * g, a2mb2);
+  } else if (ip0) {
+    // one divide for 1/a, 1/b, 1/K (a^2 - b^2 >= (1 - 1/kappa_a^2) a^2 > 0)
+    // and 1/p0 = a / C0
+    const T q = ab * a2mb2;
+    const T r = tdiv(T(1), q * c.C0);
+    const T rq = r * c.C0;
+    rab = rq * a2mb2;
+    c.inv_K = (T(2) * g) * (ab * rq);
+    *ip0 = a * (r * q);
   } else {
+    // one divide for 1/a, 1/b and 1/K
     const T r = tdiv(T(1), ab * a2mb2);
     rab = r * a2mb2;
     c.inv_K = (T(2) * g) * (ab * r);
@@ -507,12 +526,14 @@ __device__ __forceinline__ T newton_setup(const DevParams& P, const Cell<T>& L, 
   c.inv_b = a * rab;
   c.K = a2mb2 * par<T>(P.inv_2g, P.f.inv_2g);
   c.D = (R.tau - L.tau) + (R.Pi - L.Pi) * (inv_a * inv_a);
-  const T du = R.un - L.un;
-  c.C0 = du + a * (L.tau + R.tau);
   c.dZ = R.Z - L.Z;
   c.dsig = -(a - b) * c.inv_b;
   c.dN = c.K * c.D * c.dsig;
-  return L.tau + R.tau + du * inv_a;
+  const T p0 = L.tau + R.tau + du * inv_a;
+  if constexpr (cheap_div<T>::value) {
+    if (ip0) *ip0 = tdiv(T(1), p0);
+  }
+  return p0;
 }
 
 // Fluctuations A- = sum_{lam_k < 0} lam_k [U]_k and A+ = sum_{lam_k >= 0}
@@ -602,9 +623,10 @@ __device__ bool riemann_solve(const DevParams& P, const Cell<T>& L, const Cell<T
   for (int c = 0; c < 4; ++c) { Am[c] = T(0); Ap[c] = T(0); }
   if (same_bits(L.H, R.H) && same_bits(L.Hn, R.Hn) && same_bits(L.Ht, R.Ht) && same_bits(L.Z, R.Z)) return true;
   NewtonConst<T> c;
-  const T p0 = newton_setup(P, L, R, a, b, c);
+  T ip0;
+  const T p0 = newton_setup(P, L, R, a, b, c, &ip0);
   NewtonEval<T> e;
-  const bool ok = newton_root(P, c, L, R, p0, e, iters);
+  const bool ok = newton_root(P, c, L, R, p0, ip0, e, iters);
   if (!ok || !newton_positive(e)) return false;
   fan_fluctuations(P, L, R, c, e, Am, Ap);
   return true;
@@ -745,10 +767,11 @@ __device__ __forceinline__ void reduce_partials(const double* mpart, unsigned nb
 constexpr int kThreads = 256;       // block size of the one-off kernels (state upload, projection)
 constexpr int kThreadsStep = 128;   // the step's two kernels on large grids (measured best on GB300)
 constexpr int kThreadsNarrow = 32;  // on small grids: one warp per block spreads the FP64 work over more SMs
-// Occupancy hint of the interface kernel: at 128 threads, 5 blocks per SM
-// (<= 102 registers, 20 warps) measured 1.3 % faster than the unconstrained
-// 114 registers (4 blocks); 6 blocks (80 registers) spilled and lost 7 %.
-template <int NT> struct iface_min_blocks { static constexpr int value = NT == 128 ? 5 : 1; };
+// Occupancy hint of the interface kernel: at 128 threads, 4 blocks per SM
+// (the unconstrained 114 registers, 16 warps) measured 1.4 % faster than 5
+// blocks (<= 102 registers, which spill 80 bytes a thread); 6 blocks (80
+// registers) spilled more and lost 7 %.
+template <int NT> struct iface_min_blocks { static constexpr int value = NT == 128 ? 4 : 1; };
 
 // Blocks of interface_kernel<T, NT> and cell_kernel<T, NT> for a grid.
 inline long long iface_blocks(const DevParams& P, int nt) {
