@@ -278,8 +278,12 @@ void sve_batch_destroy(sve_batch* b);
  *
  * sve_record_forward advances the handle's current state by nsteps CFL
  * steps (as sve_step) and records the time steps and a checkpoint of the
- * conserved state every checkpoint_every steps (<= 0: ceil(sqrt(nsteps))).
- * The handle then holds U^N.
+ * conserved state every checkpoint_every steps.  With checkpoint_every <= 0
+ * the choice is automatic: when every step's padded state and its convected
+ * (pre-friction) state fit in half of the free device memory (2 x 32 bytes
+ * a cell a step in 2D), all of them are kept and the adjoint recomputes
+ * nothing; otherwise a checkpoint every ceil(sqrt(nsteps)) steps.  The
+ * handle then holds U^N.
  *
  * sve_adjoint propagates a cotangent of the final state back to the
  * recorded run's initial state: lam_h, lam_hu, lam_hv, lam_z = dL/dU^N
@@ -287,10 +291,16 @@ void sve_batch_destroy(sve_batch* b);
  * g_h0 .. g_z0 (nullable, same layout and memory) receive dL/dU^0 and
  * g_params[3] (host, nullable) = dL/dA_g, dL/dm_g, dL/d(friction
  * coefficient: K for Strickler, f for Darcy-Weisbach; 0 without friction).
- * The forward states are recomputed per checkpoint segment.  Afterwards the
- * handle holds the recorded run's initial state.  SVE_ERR_STATE if nothing
- * was recorded; SVE_ERR_ARG for FP32 or MPM handles. */
+ * The forward states are recomputed per checkpoint segment unless the
+ * recording kept them all.  Afterwards the handle holds the recorded run's
+ * initial state.  SVE_ERR_STATE if nothing was recorded; SVE_ERR_ARG for
+ * FP32 or MPM handles.
+ *
+ * sve_get_checkpoint_every returns the recording's checkpoint interval
+ * (nsteps when every step was kept), SVE_ERR_STATE if nothing was recorded,
+ * SVE_ERR_ARG for a NULL handle. */
 int sve_record_forward(sve_handle* h, int nsteps, int checkpoint_every);
+int sve_get_checkpoint_every(sve_handle* h);
 int sve_adjoint(sve_handle* h, const void* lam_h, const void* lam_hu, const void* lam_hv, const void* lam_z,
                 int where, void* g_h0, void* g_hu0, void* g_hv0, void* g_z0, double* g_params);
 

@@ -45,6 +45,7 @@ using sve::NewtonEval;
 struct sve_adjoint_rec {
   int nsteps = 0;
   int every = 0;
+  bool stored = false;              // every step's states kept by the recording (no recompute)
   std::vector<double> dts;          // dt of each recorded step
   std::vector<double*> checkpoints;  // padded (h, hu, hv, z) at steps 0, C, 2C, ...
   double* seg = nullptr;            // padded states of one segment (C of them)
@@ -105,13 +106,14 @@ __device__ __forceinline__ double block_sum(double v, double* sh) {
 }
 
 // The convected (pre-friction) state U~ of every interior cell for the step
-// of size dt whose fluctuations the planes of S hold (4 planes of nx ny),
-// kept while a segment is recomputed for the friction adjoint.
-__global__ void __launch_bounds__(kAdjThreads) convect_save_kernel(DevParams P, DevState<double> S, double dt,
-                                                                   double* out) {
+// whose fluctuations the planes of S hold (4 planes of nx ny) and whose time
+// step the interface pass left in sc->dt, kept for the friction adjoint.
+__global__ void __launch_bounds__(kAdjThreads) convect_save_kernel(DevParams P, DevState<double> S,
+                                                                   const DevScalars* sc, double* out) {
   const long long ncell = (long long)P.nx * P.ny;
   const long long k = (long long)blockIdx.x * kAdjThreads + threadIdx.x;
   if (k >= ncell) return;
+  const double dt = sc->dt;
   const int j = (int)(k / P.nx), i = (int)(k - (long long)j * P.nx);
   double s[4];
   sve::convect_cell(P, S, i, j, sve::ext_index(P, i, j), dt, s);
@@ -370,19 +372,24 @@ void free_rec(sve_adjoint_rec* r) {
   delete r;
 }
 
-// one forward step of size dt with the handle's kernels (fixed-dt mode);
-// with conv, the step's convected (pre-friction) interior state is kept there
-int forward_step(sve_handle* h, double dt, double* conv = nullptr) {
-  ADJ_TRY(cudaMemcpyAsync(h->fixed, &dt, sizeof(double), cudaMemcpyHostToDevice, h->stream));
-  ADJ_TRY(cudaMemsetAsync(&h->sc->call_step, 0, sizeof(int), h->stream));
+// One forward step with the handle's kernels: of size dt (fixed-dt mode),
+// or with cfl set of the CFL size, logged in the handle's time-step log at
+// the call's step counter.  With conv, the step's convected (pre-friction)
+// interior state is kept there.
+int forward_step(sve_handle* h, double dt, double* conv = nullptr, bool cfl = false) {
+  if (!cfl) {
+    ADJ_TRY(cudaMemcpyAsync(h->fixed, &dt, sizeof(double), cudaMemcpyHostToDevice, h->stream));
+    ADJ_TRY(cudaMemsetAsync(&h->sc->call_step, 0, sizeof(int), h->stream));
+  }
   DevState<double> S = state_of<double>(h);
   const unsigned nbi = (unsigned)sve::iface_blocks(h->P, sve::kThreadsStep);
   const unsigned nbc = (unsigned)sve::cell_blocks(h->P, sve::kThreadsStep);
-  sve::interface_kernel<double><<<nbi, sve::kThreadsStep, 0, h->stream>>>(h->P, S, h->sc, h->fixed, h->dtlog, 1);
+  sve::interface_kernel<double><<<nbi, sve::kThreadsStep, 0, h->stream>>>(h->P, S, h->sc, h->fixed, h->dtlog,
+                                                                          cfl ? 0 : 1);
   if (conv) {
     const long long ncell = (long long)h->P.nx * h->P.ny;
     convect_save_kernel<<<(unsigned)((ncell + kAdjThreads - 1) / kAdjThreads), kAdjThreads, 0, h->stream>>>(
-        h->P, S, dt, conv);
+        h->P, S, h->sc, conv);
   }
   sve::cell_kernel<double><<<nbc, sve::kThreadsStep, 0, h->stream>>>(h->P, S, h->sc, h->mpart,
                                                                      sve::Mirror<double>{});
@@ -409,14 +416,47 @@ int sve_record_forward(sve_handle* h, int nsteps, int checkpoint_every) {
   sve_adjoint_rec* r = new sve_adjoint_rec();
   h->adj = r;
   r->nsteps = nsteps;
-  r->every = checkpoint_every > 0 ? checkpoint_every : (int)ceil(sqrt((double)nsteps));
-  if (r->every > nsteps) r->every = nsteps;
-  const int ncp = (nsteps + r->every - 1) / r->every;
   const size_t n = 4 * (size_t)h->next;
+  const long long ncell = (long long)h->P.nx * h->P.ny;
   double t0 = 0.0;
   ADJ_TRY(cudaMemcpy(&t0, &h->sc->t, sizeof(double), cudaMemcpyDeviceToHost));
   r->t0 = t0;
   r->dts.resize(nsteps);
+  // Automatic checkpointing: when every step's padded state and convected
+  // state fit in half of the free device memory, the recording keeps them
+  // all and the adjoint recomputes nothing; otherwise checkpoints every
+  // ceil(sqrt(N)) steps, each segment recomputed once before its reverse sweep.
+  if (checkpoint_every <= 0) {
+    size_t free_b = 0, total_b = 0;
+    ADJ_TRY(cudaMemGetInfo(&free_b, &total_b));
+    const double need = (double)sizeof(double) * ((double)n + 4.0 * (double)ncell) * (double)nsteps;
+    r->stored = need <= 0.5 * (double)free_b;
+  }
+  if (r->stored) {
+    r->every = nsteps;
+    double* c = nullptr;
+    int rc = cudaMalloc(&c, sizeof(double) * n) == cudaSuccess ? SVE_OK : SVE_ERR_OOM;
+    if (!rc) r->checkpoints.push_back(c);
+    if (!rc) rc = save_state(h, c);
+    if (!rc) rc = grow(&r->seg, &r->seg_cap, n * (size_t)nsteps);
+    if (!rc) rc = grow(&r->segc, &r->segc_cap, 4 * (size_t)ncell * (size_t)nsteps);
+    if (!rc) rc = sve_internal_reserve_dtlog(h, nsteps);
+    if (!rc && cudaMemsetAsync(&h->sc->call_step, 0, sizeof(int), h->stream) != cudaSuccess) rc = SVE_ERR_CUDA;
+    for (int s = 0; s < nsteps && !rc; ++s) {
+      rc = save_state(h, r->seg + (size_t)s * n);
+      if (!rc) rc = forward_step(h, 0.0, r->segc + (size_t)s * 4 * (size_t)ncell, true);
+    }
+    if (!rc) rc = status_of(h);
+    if (!rc && cudaMemcpy(r->dts.data(), h->dtlog, sizeof(double) * (size_t)nsteps, cudaMemcpyDeviceToHost) !=
+                   cudaSuccess)
+      rc = SVE_ERR_CUDA;
+    if (rc) { sve_internal_adjoint_free(h); return rc; }
+    h->last_steps = nsteps;
+    return SVE_OK;
+  }
+  r->every = checkpoint_every > 0 ? checkpoint_every : (int)ceil(sqrt((double)nsteps));
+  if (r->every > nsteps) r->every = nsteps;
+  const int ncp = (nsteps + r->every - 1) / r->every;
   for (int k = 0; k < ncp; ++k) {
     double* c = nullptr;
     if (cudaMalloc(&c, sizeof(double) * n) != cudaSuccess) { sve_internal_adjoint_free(h); return SVE_ERR_OOM; }
@@ -428,6 +468,12 @@ int sve_record_forward(sve_handle* h, int nsteps, int checkpoint_every) {
     if (sve_get_dts(h, r->dts.data() + (size_t)k * r->every, len) != len) { sve_internal_adjoint_free(h); return SVE_ERR_CUDA; }
   }
   return SVE_OK;
+}
+
+int sve_get_checkpoint_every(sve_handle* h) {
+  if (!h) return SVE_ERR_ARG;
+  if (!h->adj) return SVE_ERR_STATE;
+  return h->adj->every;
 }
 
 int sve_adjoint(sve_handle* h, const void* lam_h, const void* lam_hu, const void* lam_hv, const void* lam_z,
@@ -469,14 +515,17 @@ int sve_adjoint(sve_handle* h, const void* lam_h, const void* lam_hu, const void
   for (int k = ncp - 1; k >= 0; --k) {
     const int n0 = k * r->every;
     const int len = (k + 1) * r->every <= r->nsteps ? r->every : r->nsteps - n0;
-    // recompute the segment's states U^{n0} .. U^{n0 + len - 1}
-    rc = load_state(h, r->checkpoints[k]);
-    if (rc) return rc;
-    sve::init_kernel<double><<<nbc, sve::kThreads, 0, h->stream>>>(P, S, h->sc, h->mpart);
-    for (int s = 0; s < len; ++s) {
-      rc = save_state(h, r->seg + (size_t)s * nst);
-      if (!rc) rc = forward_step(h, r->dts[n0 + s], r->segc + (size_t)s * 4 * (size_t)ncell);
+    // recompute the segment's states U^{n0} .. U^{n0 + len - 1} (kept by
+    // the recording when it stored every step)
+    if (!r->stored) {
+      rc = load_state(h, r->checkpoints[k]);
       if (rc) return rc;
+      sve::init_kernel<double><<<nbc, sve::kThreads, 0, h->stream>>>(P, S, h->sc, h->mpart);
+      for (int s = 0; s < len; ++s) {
+        rc = save_state(h, r->seg + (size_t)s * nst);
+        if (!rc) rc = forward_step(h, r->dts[n0 + s], r->segc + (size_t)s * 4 * (size_t)ncell);
+        if (rc) return rc;
+      }
     }
     // reverse through the segment: the saved padded state U^n (its ghosts
     // included) and its convected state are all the adjoint kernels read

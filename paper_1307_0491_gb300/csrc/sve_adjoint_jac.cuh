@@ -144,16 +144,27 @@ __device__ __forceinline__ Cell<double> project_grass_rec(const DevParams& P, do
 __device__ __forceinline__ void project_grass_bar(const DevParams& P, const ProjRec& r, double A, double m,
                                                   CellBar cb, double ub[4], double& Ab, double& mb) {
   double Hb = cb.H, Hnb = cb.Hn, Htb = cb.Ht, taub = cb.tau, unb = cb.un, utb = cb.ut;
+  // 1/cb and 1/|U| from one divide where both are needed
+  double icb = 0.0, isp = 0.0;
+  if (r.cb > 0.0 && !r.still) {
+    const double q = 1.0 / (r.cb * r.sp);
+    icb = q * r.sp;
+    isp = q * r.cb;
+  } else if (r.cb > 0.0) {
+    icb = 1.0 / r.cb;
+  } else if (!r.still) {
+    isp = 1.0 / r.sp;
+  }
   // cb = sqrt(Hn^2 + g H^2 dQ)
   double dQb = 0.0;
   if (r.cb > 0.0) {
-    const double Xb = cb.cb / (2.0 * r.cb);
+    const double Xb = cb.cb * 0.5 * icb;
     Hnb += Xb * 2.0 * r.Hn;
     Hb += Xb * 2.0 * P.g * r.H * r.dQ;
     dQb = Xb * P.g * r.H * r.H;
   }
   // ca = H sqrt(g H)
-  Hb += cb.ca * 1.5 * r.ca / r.H;
+  Hb += cb.ca * 1.5 * r.ca * r.tau;
   // Pi = g H^2 / 2
   Hb += cb.Pi * P.g * r.H;
   // Om = Q = A un |U|^(m-1); dQ = A (|U|^(m-1) + (m-1) un^2 |U|^(m-3))
@@ -171,9 +182,9 @@ __device__ __forceinline__ void project_grass_bar(const DevParams& P, const Proj
     unb += secondb * (m - 1.0) * 2.0 * r.un * r.pm3;
     const double pm3b = secondb * (m - 1.0) * un2;
     const double lsp = log(r.sp);
-    double spb = pm1b * (m - 1.0) * r.pm1 / r.sp + pm3b * (m - 3.0) * r.pm3 / r.sp;
+    double spb = (pm1b * (m - 1.0) * r.pm1 + pm3b * (m - 3.0) * r.pm3) * isp;
     mb += pm1b * r.pm1 * lsp + pm3b * r.pm3 * lsp;
-    const double s2b = spb / (2.0 * r.sp);
+    const double s2b = spb * 0.5 * isp;
     unb += s2b * 2.0 * r.un;
     utb += s2b * 2.0 * r.ut;
   }
@@ -285,9 +296,10 @@ __device__ __forceinline__ bool interface_vjp(const DevParams& P, const double u
   const bool step = a * a < need;
   if (step) a = sqrt(need);
   NewtonConst<double> c;
-  double pstar = newton_setup(P, L, R, a, b, c);
+  double ip0;
+  double pstar = newton_setup(P, L, R, a, b, c, &ip0);  // as the step: the same iterates
   NewtonEval<double> e;
-  newton_eval(pstar, c, L, R, e);
+  newton_eval_ip(pstar, ip0, c, L, R, e);
   int its = 0;
   if (!newton_loop(c, L, R, pstar, e, P.newton_maxit, fmax(P.newton_tol, 16.0 * 2.220446049250313e-16), its))
     return false;
@@ -303,11 +315,16 @@ __device__ __forceinline__ bool interface_vjp(const DevParams& P, const double u
   const double tk = mi == 1 ? e.tau1 : (mi == 2 ? e.tau2 : (mi == 3 ? e.tau3 : e.tau4));
   const double uk = mi == 1 ? e.u1 : (mi == 4 ? e.u4 : us);
   const double vk = left ? L.ut : R.ut;
-  const double Hk = 1.0 / tk;
-  const double Fh = Hk * uk;
   const double zj2 = e.Zs - L.Z, zj4 = R.Z - e.Zs;
   const double d12 = e.tau1 + e.tau2, d34 = e.tau3 + e.tau4;
-  const double S2 = 2.0 * g * zj2 / d12, S4 = 2.0 * g * zj4 / d34;
+  // one divide for 1/F_p, 1/tau_k, 1/(tau1 + tau2) and 1/(tau3 + tau4)
+  const double t1234 = tk * (d12 * d34);
+  const double rr = 1.0 / (Fp * t1234);
+  const double iFp = rr * t1234, rt = rr * Fp;
+  const double Hk = rt * (d12 * d34);
+  const double r12 = rt * (tk * d34), r34 = rt * (tk * d12);
+  const double Fh = Hk * uk;
+  const double S2 = 2.0 * g * zj2 * r12, S4 = 2.0 * g * zj4 * r34;
   const bool n2 = negative(e.lam2), n4 = negative(e.lam4);
 
   // ---- backward sweep
@@ -324,9 +341,9 @@ __device__ __forceinline__ bool interface_vjp(const DevParams& P, const double u
   const double P2b = n2 ? Amb[3] : Apb[3], P4b = n4 ? Amb[3] : Apb[3];
   eb.lam2 += P2b * zj2;
   eb.lam4 += P4b * zj4;
-  double zj2b = P2b * e.lam2 + S2b * 2.0 * g / d12;
-  double zj4b = P4b * e.lam4 + S4b * 2.0 * g / d34;
-  const double d12b = -S2b * S2 / d12, d34b = -S4b * S4 / d34;
+  double zj2b = P2b * e.lam2 + S2b * 2.0 * g * r12;
+  double zj4b = P4b * e.lam4 + S4b * 2.0 * g * r34;
+  const double d12b = -S2b * S2 * r12, d34b = -S4b * S4 * r34;
   eb.tau1 += d12b;
   eb.tau2 += d12b;
   eb.tau3 += d34b;
@@ -380,24 +397,25 @@ __device__ __forceinline__ bool interface_vjp(const DevParams& P, const double u
   double pb = 0.0;
   newton_eval_bar(c, e, pstar, L, R, eb, pb, cb, Lb, Rb);
   EvalBar fb = {};
-  fb.F = -pb / Fp;
+  fb.F = -pb * iFp;
   double pb_unused = 0.0;
   newton_eval_bar(c, e, pstar, L, R, fb, pb_unused, cb, Lb, Rb);
   // Newton constants: a, b, K = (a^2 - b^2)/(2g), inv_b = 1/b,
   // inv_K = 2g/(a^2 - b^2), D = dtau + dPi/a^2, C0 = du + a (tauL + tauR), dZ
   ab += cb.a;
   bb += cb.b;
-  ab += cb.K * a / g;
-  bb -= cb.K * b / g;
-  bb -= cb.inv_b / (b * b);
-  ab -= cb.inv_K * c.inv_K * c.inv_K * a / g;
-  bb += cb.inv_K * c.inv_K * c.inv_K * b / g;
+  const double ig = 2.0 * P.inv_2g;
+  ab += cb.K * a * ig;
+  bb -= cb.K * b * ig;
+  bb -= cb.inv_b * (c.inv_b * c.inv_b);
+  ab -= cb.inv_K * c.inv_K * c.inv_K * a * ig;
+  bb += cb.inv_K * c.inv_K * c.inv_K * b * ig;
   Rb.tau += cb.D;
   Lb.tau -= cb.D;
-  const double ia2 = 1.0 / (a * a);
+  const double ia2 = c.inv_a * c.inv_a;
   Rb.Pi += cb.D * ia2;
   Lb.Pi -= cb.D * ia2;
-  ab -= cb.D * (R.Pi - L.Pi) * 2.0 * ia2 / a;
+  ab -= cb.D * (R.Pi - L.Pi) * 2.0 * ia2 * c.inv_a;
   Rb.un += cb.C0;
   Lb.un -= cb.C0;
   ab += cb.C0 * (L.tau + R.tau);
@@ -408,7 +426,7 @@ __device__ __forceinline__ bool interface_vjp(const DevParams& P, const double u
   // celerities, along the branches taken
   double a0b = 0.0, b0b = 0.0;
   if (step) {
-    const double needb = ab / (2.0 * a);
+    const double needb = ab * 0.5 * c.inv_a;
     bb += needb * 2.0 * b;
     const double sgn = dZ < 0.0 ? -1.0 : 1.0;
     const double dZb = needb * 2.0 * g * P.gamma_z * (Hmax * Hmax) * sgn;

@@ -371,8 +371,14 @@ void* direct_ptr(void* p, int where);
 
 }  // namespace
 
-// Shared with sve_noalloc.cu (not part of the C ABI).
+// Shared with sve_noalloc.cu and sve_adjoint.cu (not part of the C ABI).
 __attribute__((visibility("hidden"))) int sve_internal_validate(const sve_config* c) { return validate(c); }
+__attribute__((visibility("hidden"))) int sve_internal_reserve_dtlog(sve_handle* h, int n) {
+  double* old = h->dtlog;
+  const int rc = ensure_capacity(&h->dtlog, &h->dtlog_cap, n > 0 ? n : 1);
+  if (h->dtlog != old) drop_graphs(h);  // graphs hold the dtlog pointer
+  return rc;
+}
 __attribute__((visibility("hidden"))) void sve_internal_make_params(const sve_config* c, DevParams* P) {
   make_params(c, P);
 }

@@ -328,7 +328,7 @@ struct Cell {
 // Per-interface constants of the Newton iteration.
 template <typename T>
 struct NewtonConst {
-  T a, b, K, inv_b, inv_K, D, C0, dZ, dsig, dN;
+  T a, b, K, inv_a, inv_b, inv_K, D, C0, dZ, dsig, dN;
 };
 
 // The intermediate states as functions of p (every invariant relation of the
@@ -523,6 +523,7 @@ __device__ __forceinline__ T newton_setup(const DevParams& P, const Cell<T>& L, 
   const T inv_a = b * rab;
   c.a = a;
   c.b = b;
+  c.inv_a = inv_a;
   c.inv_b = a * rab;
   c.K = a2mb2 * par<T>(P.inv_2g, P.f.inv_2g);
   c.D = (R.tau - L.tau) + (R.Pi - L.Pi) * (inv_a * inv_a);

@@ -62,3 +62,6 @@ inline sve::DevState<T> state_of(const sve_handle* h) {
 
 // Implemented in sve_adjoint.cu: releases the recorded forward run.
 __attribute__((visibility("hidden"))) void sve_internal_adjoint_free(sve_handle* h);
+// Implemented in sve_api.cu: the time-step log holds >= n steps (the step
+// graphs are rebuilt if it moves).
+__attribute__((visibility("hidden"))) int sve_internal_reserve_dtlog(sve_handle* h, int n);

@@ -35,7 +35,8 @@ EXPORTS = ("sve_config_default", "sve_create", "sve_set_stream", "sve_set_state"
            "sve_batch_create", "sve_batch_set_stream", "sve_batch_set_state", "sve_batch_step",
            "sve_batch_step_async", "sve_batch_get_state", "sve_batch_get_diag", "sve_batch_get_counters",
            "sve_batch_autotune", "sve_batch_set_schedule", "sve_batch_last_launch_count", "sve_batch_destroy",
-           "sve_record_forward", "sve_adjoint", "sve_set_block_size", "sve_get_block_size", "sve_advance")
+           "sve_record_forward", "sve_adjoint", "sve_set_block_size", "sve_get_block_size", "sve_advance",
+           "sve_get_checkpoint_every")
 
 
 class sve_config(ctypes.Structure):
@@ -106,6 +107,7 @@ def load() -> ctypes.CDLL:
         "sve_batch_last_launch_count": ([vp], ctypes.c_longlong),
         "sve_batch_destroy": ([vp], None),
         "sve_record_forward": ([vp, ip, ip], ip),
+        "sve_get_checkpoint_every": ([vp], ip),
         "sve_adjoint": ([vp, vp, vp, vp, vp, ip, vp, vp, vp, vp, dp], ip),
         "sve_set_block_size": ([vp, ip], ip),
         "sve_get_block_size": ([vp], ip),
@@ -464,6 +466,12 @@ class Solver:
         rc, steps, its = sve_get_counters(self.h)
         _check(rc, "sve_get_counters")
         return dict(steps=steps, newton_iters=its)
+
+    def checkpoint_every(self) -> int:
+        """The recording's checkpoint interval (nsteps: every step kept)."""
+        n = load().sve_get_checkpoint_every(self.h)
+        _check(min(n, 0), "sve_get_checkpoint_every")
+        return n
 
     def record_forward(self, nsteps: int, checkpoint_every: int = 0) -> None:
         _check(sve_record_forward(self.h, nsteps, checkpoint_every), "sve_record_forward")

@@ -176,3 +176,33 @@ def test_stepping_after_the_adjoint():
     s2.close()
     for k in ("h", "hu", "hv", "z"):
         assert np.max(np.abs(after[k] - ref[k])) <= 1e-12 * max(np.max(np.abs(ref[k])), 1e-300), k
+
+
+def test_stored_and_checkpointed_recordings_agree():
+    """The automatic recording keeps every step on a grid this small
+    (checkpoint interval = nsteps, no recompute); with checkpoints every 5 or
+    23 steps the segments are recomputed in fixed-dt mode.  The same kernels
+    with the same time steps: final states and gradients equal bit for bit,
+    and the handle steps on from U^0 afterwards in each mode."""
+    w, target = case()
+    p = w["params"]
+    n = 23
+    out = {}
+    for every in (0, 5, 23):
+        s = sve.Solver(p, "fp64")
+        s.set_state(w["h"], w["hu"], w["hv"], w["z"])
+        s.record_forward(n, every)
+        ce = s.checkpoint_every()
+        fin = s.get_state()
+        grads, gp = s.adjoint(lam_z=2.0 * (fin["z"] - target))
+        s.step(4)
+        after = s.get_state()
+        s.close()
+        out[every] = (ce, fin, grads, gp, after)
+    assert out[0][0] == n and out[5][0] == 5 and out[23][0] == 23
+    for every in (5, 23):
+        for k in ("h", "hu", "hv", "z"):
+            assert np.array_equal(out[every][1][k], out[0][1][k]), (every, k)
+            assert np.array_equal(out[every][2][k], out[0][2][k]), (every, k)
+            assert np.array_equal(out[every][4][k], out[0][4][k]), (every, k)
+        assert list(out[every][3]) == list(out[0][3])
