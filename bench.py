@@ -381,16 +381,20 @@ def run_adjoint(args, sve, W, torch):
 def run_small1d(args, sve, W, torch):
     """Small 1D grids, where a step is a few microseconds of work and its FP64
     work has to be spread over many SMs: the 1D dune (1000 cells, periodic,
-    5000 CFL steps) and the 1D antidune of Sec. 5.2 at J = 2400 (5 cm bump),
-    with one-warp blocks (the automatic choice here) and 128-thread blocks."""
+    5000 CFL steps) and the 1D antidune of Sec. 5.2 at J = 2400 (5 cm bump):
+    the two-kernel step from CUDA graphs of 16 steps with one-warp blocks
+    (the automatic choice here) and with 128-thread blocks, and the opt-in
+    persistent cooperative step (up to 4096 steps per launch)."""
     out = []
     for name, w, n in (("1D dune 1000 cells periodic, Grass A_g=1e-3 m_g=3, 5000 CFL steps", W.dune1d(), 5000),
                        ("1D antidune (Sec. 5.2) 2400 cells, 5 cm bump, supercritical inflow, 5000 CFL steps",
                         W.paper_antidune1d(nx=2400, bump=0.05), 5000)):
         row = {"workload": name, "steps": n}
-        for bs in (32, 128):
+        for key, bs, pers in (("persistent", 32, 1), ("block32", 32, 0), ("block128", 128, 0)):
             s = sve.Solver(w["params"], "fp64")
             s.set_block_size(bs)
+            s.set_persistent(pers)
+            used = s.persistent()
             s.set_state(w["h"], w["hu"], w["hv"], w["z"])
             s.step(200)
             torch.cuda.synchronize()
@@ -399,10 +403,11 @@ def run_small1d(args, sve, W, torch):
             t1 = time.perf_counter()
             launches = s.launches()
             s.close()
-            row[f"block{bs}"] = {"steps_per_s": n / (t1 - t0), "cell_updates_per_s": n * w["params"]["nx"] / (t1 - t0),
-                                 "launches": launches}
+            row[key] = {"steps_per_s": n / (t1 - t0), "cell_updates_per_s": n * w["params"]["nx"] / (t1 - t0),
+                        "launches": launches, "persistent": used}
+        row["persistent_vs_graphs"] = row["persistent"]["steps_per_s"] / row["block32"]["steps_per_s"]
         row["narrow_vs_wide"] = row["block32"]["steps_per_s"] / row["block128"]["steps_per_s"]
-        row["time"] = "wall clock around one host-synchronous sve_step call of all steps (CUDA graphs of 16 steps)"
+        row["time"] = "wall clock around one host-synchronous sve_step call of all steps"
         out.append(row)
     return out
 

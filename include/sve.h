@@ -51,7 +51,9 @@ enum {
   SVE_ERR_NAN = -6,       /* a non-finite value appeared in the state */
   SVE_ERR_DT = -7,        /* a time step was <= 0 or non-finite */
   SVE_ERR_STATE = -8,     /* no state has been set on the handle */
-  SVE_ERR_NOALLOC_SIZE = -9 /* the grid does not fit the static scratch of sve_step_noalloc */
+  SVE_ERR_NOALLOC_SIZE = -9, /* the grid does not fit the static scratch of sve_step_noalloc */
+  SVE_ERR_SYNC = -10        /* a grid-wide wait of the persistent small-grid step ran out (the
+                               context stays usable; latched until the next sve_set_state) */
 };
 
 enum { SVE_FP64 = 0, SVE_FP32 = 1 };                       /* state precision */
@@ -228,6 +230,32 @@ int sve_get_counters(sve_handle* h, long long* steps, unsigned long long* newton
  * that of Sec. 3 for every shape; the paper has no counterpart of this
  * choice.  SVE_ERR_ARG for other values. */
 int sve_set_block_size(sve_handle* h, int threads);
+
+/* ---- persistent step of small grids (opt-in) -------------------------------
+ * With on = 1 the steps of one call run as cooperative launches of one-warp
+ * blocks (all co-resident, spread over the SMs), up to 4096 steps each:
+ * per step every interface is solved, a grid-wide barrier, every block
+ * takes the same CFL dt, every cell is updated, a grid-wide barrier (Sec.
+ * 3's step with the same per-interface and per-cell functions as the
+ * two-kernel form: the states and time steps agree to round-off, each kernel
+ * being compiled on its own).  Eligible: the two-kernel form (FP64, or FP32
+ * in 1D) with at most 4 x SMs one-warp blocks of 32 interfaces or cells,
+ * co-resident; otherwise, and for profiled steps (sve_profile), the
+ * two-kernel form runs.  on = 0 (the default) restores the two kernels from
+ * CUDA graphs, which measured as fast on GB300 (a step of a small grid is
+ * bound by one warp's chain of FP64 instructions, not by its launches).
+ * Every barrier wait is bounded (~0.5 s of polling); past it the step ends
+ * with SVE_ERR_SYNC.  SVE_ERR_ARG for other values.  sve_get_persistent
+ * returns 1 if the next steps use it, else 0.
+ *
+ * sve_check_sync_timeout checks that bounded wait: one persistent launch
+ * whose barrier expects one block more than it has, each wait bounded by
+ * `polls` polls (~100 ns each); returns SVE_ERR_SYNC as the step would
+ * (the state is not advanced), SVE_ERR_ARG if the grid is not eligible,
+ * SVE_ERR_STATE without a state. */
+int sve_set_persistent(sve_handle* h, int on);
+int sve_get_persistent(sve_handle* h);
+int sve_check_sync_timeout(sve_handle* h, long long polls);
 
 /* Threads per block the next step call will use (32, 128 or 256). */
 int sve_get_block_size(sve_handle* h);

@@ -13,6 +13,7 @@
 #include "../../include/sve.h"
 #include "sve_device.cuh"
 #include "sve_fused.cuh"
+#include "sve_persist.cuh"
 #include "sve_handle.h"
 
 using sve::DevParams;
@@ -36,6 +37,7 @@ int status_to_code(int st) {
   if (st & sve::ST_NEG_DEPTH) return SVE_ERR_NEG_DEPTH;
   if (st & sve::ST_RIEMANN) return SVE_ERR_RIEMANN;
   if (st & sve::ST_DT) return SVE_ERR_DT;
+  if (st & sve::ST_SYNC) return SVE_ERR_SYNC;
   return SVE_OK;
 }
 
@@ -231,8 +233,44 @@ void drop_graphs(sve_handle* h) {
   }
 }
 
+// Whether steps run as persistent cooperative launches (opt-in: measured no
+// faster than the two kernels from CUDA graphs, whose launches overlap the
+// steps' FP64 latency chains).
+bool use_persistent(const sve_handle* h) { return h->persist_ok && !h->profiling && h->persist_mode == 1; }
+
+constexpr int kPersistChunk = 4096;  // steps per persistent launch
+
+// One persistent cooperative launch of nsteps steps (expected / polls: the
+// barrier's arrivals and wait bound).
+int launch_persistent(sve_handle* h, int nsteps, int fixed, unsigned int expected, long long polls) {
+  SVE_TRY(cudaMemsetAsync(h->ps, 0, sizeof(sve::PersistScratch), h->stream));
+  void* args[11];
+  DevParams P = h->P;
+  int fx = fixed, ns = nsteps;
+  const double* fd = h->fixed;
+  double* dl = h->dtlog;
+  double* mp = h->mpart;
+  sve::DevScalars* sc = h->sc;
+  sve::PersistScratch* ps = h->ps;
+  if (h->cfg.precision == SVE_FP64) {
+    DevState<double> S = state_of<double>(h);
+    void* a[11] = {&P, &S, &sc, &ps, &fd, &dl, &fx, &ns, &mp, &expected, &polls};
+    for (int k = 0; k < 11; ++k) args[k] = a[k];
+    SVE_TRY(cudaLaunchCooperativeKernel((const void*)sve::persistent_kernel<double>, dim3(h->pgrid),
+                                        dim3(sve::kPersistThreads), args, 0, h->stream));
+  } else {
+    DevState<float> S = state_of<float>(h);
+    void* a[11] = {&P, &S, &sc, &ps, &fd, &dl, &fx, &ns, &mp, &expected, &polls};
+    for (int k = 0; k < 11; ++k) args[k] = a[k];
+    SVE_TRY(cudaLaunchCooperativeKernel((const void*)sve::persistent_kernel<float>, dim3(h->pgrid),
+                                        dim3(sve::kPersistThreads), args, 0, h->stream));
+  }
+  return SVE_OK;
+}
+
 // Enqueue nsteps steps on the handle's stream (graphs of kGraphSteps steps
-// where possible; single launches with events when profiling).
+// where possible; single launches with events when profiling; persistent
+// cooperative launches of up to kPersistChunk steps on small grids).
 int enqueue_steps(sve_handle* h, int nsteps, int fixed, const void* const* mirror = nullptr) {
   if (!h->has_state) return SVE_ERR_STATE;
   double* old = h->dtlog;
@@ -241,6 +279,26 @@ int enqueue_steps(sve_handle* h, int nsteps, int fixed, const void* const* mirro
   if (h->dtlog != old) drop_graphs(h);  // graphs hold the dtlog pointer
   SVE_TRY(cudaMemsetAsync(&h->sc->call_step, 0, sizeof(int), h->stream));
   int done = 0;
+  long long launches = 0;
+  if (use_persistent(h)) {
+    // with a mirror the last step is a single two-kernel step
+    const int np = mirror ? nsteps - 1 : nsteps;
+    for (; done < np; done += kPersistChunk) {
+      rc = launch_persistent(h, std::min(kPersistChunk, np - done), fixed, (unsigned int)h->pgrid,
+                             sve::kBarrierPolls);
+      if (rc) return rc;
+      ++launches;
+    }
+    done = np;
+    if (done < nsteps) {
+      launch_step_any(h, h->stream, fixed, nullptr, mirror);
+      launches += 2;
+    }
+    SVE_TRY(cudaGetLastError());
+    h->last_launches = launches;
+    h->last_steps = nsteps;
+    return SVE_OK;
+  }
   // with a mirror the last step is a single launch (the graphs write no mirror)
   const int graphed = mirror ? nsteps - 1 : nsteps;
   if (graphed >= kGraphSteps && !h->profiling) {
@@ -452,10 +510,30 @@ int sve_create(const sve_config* cfg, sve_handle** out) {
     h->agx = (h->P.nx + sve::kAThreads - 1) / sve::kAThreads;
     h->agy = std::min(h->P.ny, std::max(1, (h->nsm * (2048 / sve::kAThreads) + h->agx - 1) / h->agx));
   }
-  const size_t nmp = std::max(2 * (size_t)sve::cell_blocks(h->P, sve::kThreadsNarrow),
-                              2 * (size_t)std::max(1, h->agx * h->agy));
+  // persistent small-grid step: one-warp blocks covering the larger of the
+  // interface and cell counts, if that many are co-resident
+  if (!h->fused) {
+    const long long units = std::max((long long)h->P.nfx + h->P.nfy, (long long)h->P.nx * h->P.ny);
+    const long long want = (units + sve::kPersistThreads - 1) / sve::kPersistThreads;
+    int bs = 0;
+    const cudaError_t oe =
+        cfg->precision == SVE_FP64
+            ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bs, sve::persistent_kernel<double>, sve::kPersistThreads, 0)
+            : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bs, sve::persistent_kernel<float>, sve::kPersistThreads, 0);
+    int coop = 0;
+    cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, h->device);
+    h->pmax = (int)std::min<long long>((long long)bs * h->nsm, 4LL * h->nsm);
+    if (oe == cudaSuccess && coop && bs > 0 && want <= h->pmax) {
+      h->persist_ok = true;
+      h->pgrid = (int)want;
+    }
+    cudaGetLastError();
+  }
+  const size_t nmp = std::max({2 * (size_t)sve::cell_blocks(h->P, sve::kThreadsNarrow),
+                               2 * (size_t)std::max(1, h->agx * h->agy), 2 * (size_t)std::max(1, h->pmax)});
   ok = ok && cudaMalloc(&h->mpart, sizeof(double) * nmp) == cudaSuccess;
   ok = ok && cudaMalloc(&h->sc, sizeof(DevScalars)) == cudaSuccess;
+  ok = ok && cudaMalloc(&h->ps, sizeof(sve::PersistScratch)) == cudaSuccess;
   if (!ok) { sve_destroy(h); return SVE_ERR_OOM; }
   if (ensure_capacity(&h->dtlog, &h->dtlog_cap, 1024)) { sve_destroy(h); return SVE_ERR_OOM; }
   if (ensure_capacity(&h->fixed, &h->fixed_cap, 1024)) { sve_destroy(h); return SVE_ERR_OOM; }
@@ -653,6 +731,7 @@ void sve_destroy(sve_handle* h) {
   if (h->fy) cudaFree(h->fy);
   if (h->mpart) cudaFree(h->mpart);
   if (h->sc) cudaFree(h->sc);
+  if (h->ps) cudaFree(h->ps);
   if (h->dtlog) cudaFree(h->dtlog);
   if (h->fixed) cudaFree(h->fixed);
   if (h->capture) cudaStreamDestroy(h->capture);
@@ -674,6 +753,7 @@ const char* sve_strerror(int code) {
     case SVE_ERR_DT: return "invalid time step";
     case SVE_ERR_STATE: return "no state set";
     case SVE_ERR_NOALLOC_SIZE: return "grid too large for the static scratch of sve_step_noalloc";
+    case SVE_ERR_SYNC: return "a grid-wide wait of the persistent step ran out";
     default: return "unknown error";
   }
 }
@@ -691,6 +771,30 @@ int sve_set_block_size(sve_handle* h, int threads) {
 int sve_get_block_size(sve_handle* h) {
   if (!h) return SVE_ERR_ARG;
   return h->nt;
+}
+
+int sve_set_persistent(sve_handle* h, int on) {
+  if (!h || on < 0 || on > 1) return SVE_ERR_ARG;
+  h->persist_mode = on;
+  return SVE_OK;
+}
+
+int sve_get_persistent(sve_handle* h) {
+  if (!h) return SVE_ERR_ARG;
+  return use_persistent(h) ? 1 : 0;
+}
+
+int sve_check_sync_timeout(sve_handle* h, long long polls) {
+  if (!h || polls < 1) return SVE_ERR_ARG;
+  if (!h->has_state) return SVE_ERR_STATE;
+  if (!h->persist_ok) return SVE_ERR_ARG;
+  SVE_TRY(cudaMemsetAsync(&h->sc->call_step, 0, sizeof(int), h->stream));
+  // one arrival more than there are blocks: the first barrier never opens
+  const int rc = launch_persistent(h, 1, 0, (unsigned int)h->pgrid + 1u, polls);
+  if (rc) return rc;
+  h->last_launches = 1;
+  h->last_steps = 0;
+  return wait_status(h);
 }
 
 long long sve_last_launch_count(sve_handle* h) { return h ? h->last_launches : -1; }

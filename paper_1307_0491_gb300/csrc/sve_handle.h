@@ -6,6 +6,7 @@
 
 #include "../../include/sve.h"
 #include "sve_device.cuh"
+#include "sve_persist.cuh"
 
 struct sve_adjoint_rec;  // recorded forward run (sve_adjoint.cu)
 
@@ -38,6 +39,12 @@ struct sve_handle {
   int agx = 0, agy = 0;    // apply pass grid (grid stride over columns and rows)
   int nt = 256;   // threads per block of the two-kernel step (32 or 256)
   int nsm = 152;  // SMs of the device
+  // small grids: many steps per cooperative launch (sve_persist.cuh)
+  sve::PersistScratch* ps = nullptr;
+  int persist_mode = 0;    // 1: persistent launches when eligible (sve_set_persistent)
+  bool persist_ok = false; // eligible: two-kernel form and the launch fits co-resident
+  int pgrid = 0;           // one-warp blocks of the persistent launch
+  int pmax = 0;            // most co-resident one-warp blocks allowed
   long long last_launches = 0;
   int last_steps = 0;
   // kernel timing (sve_profile): 3 events per step, read back lazily

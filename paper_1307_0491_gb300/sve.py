@@ -21,6 +21,7 @@ SVE_OK = 0
 SVE_ERR_ARG, SVE_ERR_CUDA, SVE_ERR_OOM = -1, -2, -3
 SVE_ERR_NEG_DEPTH, SVE_ERR_RIEMANN, SVE_ERR_NAN, SVE_ERR_DT, SVE_ERR_STATE = -4, -5, -6, -7, -8
 SVE_ERR_NOALLOC_SIZE = -9
+SVE_ERR_SYNC = -10
 SVE_NOALLOC_SCRATCH_BYTES = 8 << 20
 SVE_FP64, SVE_FP32 = 0, 1
 SVE_GRASS, SVE_MPM, SVE_FLVB, SVE_NIELSEN, SVE_RIBBERINK, SVE_CAMENEN = 0, 1, 2, 3, 4, 5
@@ -36,7 +37,7 @@ EXPORTS = ("sve_config_default", "sve_create", "sve_set_stream", "sve_set_state"
            "sve_batch_step_async", "sve_batch_get_state", "sve_batch_get_diag", "sve_batch_get_counters",
            "sve_batch_autotune", "sve_batch_set_schedule", "sve_batch_last_launch_count", "sve_batch_destroy",
            "sve_record_forward", "sve_adjoint", "sve_set_block_size", "sve_get_block_size", "sve_advance",
-           "sve_get_checkpoint_every")
+           "sve_get_checkpoint_every", "sve_set_persistent", "sve_get_persistent", "sve_check_sync_timeout")
 
 
 class sve_config(ctypes.Structure):
@@ -108,6 +109,9 @@ def load() -> ctypes.CDLL:
         "sve_batch_destroy": ([vp], None),
         "sve_record_forward": ([vp, ip, ip], ip),
         "sve_get_checkpoint_every": ([vp], ip),
+        "sve_set_persistent": ([vp, ip], ip),
+        "sve_get_persistent": ([vp], ip),
+        "sve_check_sync_timeout": ([vp, ctypes.c_longlong], ip),
         "sve_adjoint": ([vp, vp, vp, vp, vp, ip, vp, vp, vp, vp, dp], ip),
         "sve_set_block_size": ([vp, ip], ip),
         "sve_get_block_size": ([vp], ip),
@@ -442,6 +446,14 @@ class Solver:
 
     def step_async(self, nsteps: int) -> None:
         _check(sve_step_async(self.h, nsteps), "sve_step_async")
+
+    def set_persistent(self, on: int) -> None:
+        """1: persistent cooperative launches when eligible, 0: the two
+        kernels from CUDA graphs (the default) -- sve_set_persistent."""
+        _check(load().sve_set_persistent(self.h, int(on)), "sve_set_persistent")
+
+    def persistent(self) -> bool:
+        return load().sve_get_persistent(self.h) == 1
 
     def set_block_size(self, threads: int) -> None:
         """Threads per block of the two-kernel step: 0 (automatic), 32, 128 or 256."""

@@ -35,9 +35,10 @@ def rel(got, ref, scale=None):
     return float(np.max(np.abs(np.asarray(got, np.float64) - np.asarray(ref, np.float64))) / s)
 
 
-def run(w, nsteps, block_size, precision="fp64", dts=None):
+def run(w, nsteps, block_size, precision="fp64", dts=None, persistent=0):
     s = sve.Solver(w["params"], precision)
     s.set_block_size(block_size)
+    s.set_persistent(persistent)
     assert s.block_size == block_size
     s.set_state(w["h"], w["hu"], w["hv"], w["z"])
     if dts is None:
@@ -106,6 +107,13 @@ def test_block_sizes_match_oracle_and_each_other(w, n):
         assert rel(a[k], b[k]) <= 1e-12, k
     assert a["launches"] == b["launches"] == 2 * n
     assert a["counters"]["steps"] == b["counters"]["steps"] == n
+    # the persistent step where the grid is eligible (small)
+    d = run(w, n, 32, persistent=1)
+    parity(d, ref, dim, ctx="automatic")
+    assert rel(d["dts"], b["dts"]) <= 1e-13
+    assert d["counters"]["steps"] == n
+    small = w["params"]["nx"] * w["params"]["ny"] <= 5000
+    assert d["launches"] == (1 if small else 2 * n), d["launches"]
     ia, ib = a["counters"]["newton_iters"], b["counters"]["newton_iters"]
     assert abs(ia - ib) <= 1e-3 * ib + 2, (ia, ib)
     assert abs(a["diag"]["mass_h"] - b["diag"]["mass_h"]) <= 1e-13 * abs(b["diag"]["mass_h"])

@@ -39,10 +39,12 @@ def rel_err(got, ref, scale=None):
     return float(np.max(np.abs(got - ref)) / s)
 
 
-def run_gpu(w, nsteps, precision="fp64", dts=None, block_size=None):
+def run_gpu(w, nsteps, precision="fp64", dts=None, block_size=None, persistent=None):
     s = sve.Solver(w["params"], precision)
     if block_size is not None:
         s.set_block_size(block_size)
+    if persistent is not None:
+        s.set_persistent(persistent)
     s.set_state(w["h"], w["hu"], w["hv"], w["z"])
     if dts is None:
         t = s.step(nsteps)
@@ -74,17 +76,19 @@ def assert_parity(got, ref, dim, tol=TOL64, ctx=""):
     return errs
 
 
-@pytest.mark.parametrize("block_size", [32, 256])
-def test_c1_dune1d_full(block_size):
-    """1D dune, N = 1000, periodic, 5000 CFL steps (the full 1D config), with
-    one-warp blocks (the automatic choice on this grid) and 256-thread blocks."""
+@pytest.mark.parametrize("block_size,persistent,launches", [(32, 1, 2), (32, 0, 2 * 5000), (256, 0, 2 * 5000)])
+def test_c1_dune1d_full(block_size, persistent, launches):
+    """1D dune, N = 1000, periodic, 5000 CFL steps (the full 1D config): the
+    persistent step (two cooperative launches of 4096 + 904 steps), and the
+    two-kernel step with one-warp blocks (the automatic shape on this grid)
+    and with 256-thread blocks."""
     w = W.dune1d()
-    got = run_gpu(w, 5000, block_size=block_size)
+    got = run_gpu(w, 5000, block_size=block_size, persistent=persistent)
     ref = run_orc(w, 5000)
-    assert_parity(got, ref, 1, ctx=f"C1 block {block_size}")
+    assert_parity(got, ref, 1, ctx=f"C1 block {block_size} persistent {persistent}")
     assert abs(got["t"] - ref["t"]) <= 1e-10 * ref["t"]
     assert np.max(np.abs(got["dts"] - ref["dts"])) <= 1e-10 * np.max(ref["dts"])
-    assert got["launches"] == 2 * 5000
+    assert got["launches"] == launches
 
 
 @pytest.mark.parametrize("nx,ny,bc,extra", [
