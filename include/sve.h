@@ -302,7 +302,8 @@ void sve_batch_destroy(sve_batch* b);
  * Gradients through nsteps steps of the scheme, with the time steps of the
  * forward run recorded and held fixed: the adjoint of the discrete map
  * U^n -> U^{n+1} (the paper gives the scheme, Sec. 3; its adjoint is this
- * library's addition).  FP64 state and the Grass law only.
+ * library's addition).  FP64 state; every transport law (Grass, and the
+ * Shields-parameter laws with tau* through the friction law).
  *
  * sve_record_forward advances the handle's current state by nsteps CFL
  * steps (as sve_step) and records the time steps and a checkpoint of the
@@ -318,11 +319,13 @@ void sve_batch_destroy(sve_batch* b);
  * (nx*ny doubles each, NULL = zero; hv ignored in 1D) in memory `where`;
  * g_h0 .. g_z0 (nullable, same layout and memory) receive dL/dU^0 and
  * g_params[3] (host, nullable) = dL/dA_g, dL/dm_g, dL/d(friction
- * coefficient: K for Strickler, f for Darcy-Weisbach; 0 without friction).
+ * coefficient: K for Strickler, f for Darcy-Weisbach; 0 without friction);
+ * with a Shields-parameter law the first two are 0 and the third includes
+ * the coefficient's effect through tau*.
  * The forward states are recomputed per checkpoint segment unless the
  * recording kept them all.  Afterwards the handle holds the recorded run's
  * initial state.  SVE_ERR_STATE if nothing was recorded; SVE_ERR_ARG for
- * FP32 or MPM handles.
+ * FP32 handles.
  *
  * sve_get_checkpoint_every returns the recording's checkpoint interval
  * (nsteps when every step was kept), SVE_ERR_STATE if nothing was recorded,

@@ -5,8 +5,10 @@ differentiated by torch.autograd.
 TEST INFRASTRUCTURE ONLY (like the rest of ``oracle/``).  It follows the
 same procedure and readings as the C oracle (Sec. 3: equilibrium projection,
 one relaxation Riemann solve per interface, Godunov average; friction, CFL,
-ghosts as readings R1--R8 there), with the Grass law (the adjoint's scope)
-written through exp/log so that A_g and m_g carry derivatives.  The Newton
+ghosts as readings R1--R8 there), with the Grass law written through
+exp/log so that A_g and m_g carry derivatives, and the Shields-parameter
+laws (q*(tau*) of Sec. 2, tau* through the friction coefficient, which then
+carries a derivative through the closure as well as through the friction).  The Newton
 iteration runs without gradients to convergence; one final Newton update
 with the derivative F'(p) held constant makes the root's derivative the one
 of the implicit function theorem, dp = -F_theta / F_p.
@@ -64,7 +66,39 @@ def _ghosts(p: dict, H, Hu, Hv, Z):
     return X
 
 
-def _project(p, H, Hn, Ht, Z, A, m):
+def _qstar(law: str, ts, tcr: float):
+    """q*(tau*) and dq*/dtau* of the Shields-parameter laws of Sec. 2 (as
+    orc_qstar), zero below the threshold; the unused branch is evaluated at
+    a safe point so that its derivative stays finite."""
+    one = torch.ones_like(ts)
+    if law == "camenen":
+        on = ts > 0
+        t = torch.where(on, ts, one)
+        e = torch.exp(-4.5 * tcr / t)
+        q = 12.0 * t * torch.sqrt(t) * e
+        dq = 12.0 * e * (1.5 * torch.sqrt(t) + 4.5 * tcr / torch.sqrt(t))
+    else:
+        x = ts - tcr
+        on = x > 0
+        xs = torch.where(on, x, one)
+        t = torch.where(on, ts, one)
+        if law in ("mpm", "flvb"):
+            c = 8.0 if law == "mpm" else 5.7
+            q = c * xs * torch.sqrt(xs)
+            dq = c * 1.5 * torch.sqrt(xs)
+        elif law == "nielsen":
+            q = 12.0 * torch.sqrt(t) * xs
+            dq = 12.0 * (xs / (2.0 * torch.sqrt(t)) + torch.sqrt(t))
+        elif law == "ribberink":
+            q = 11.0 * torch.pow(xs, 1.65)
+            dq = 11.0 * 1.65 * torch.pow(xs, 0.65)
+        else:
+            raise ValueError(law)
+    zero = torch.zeros_like(ts)
+    return torch.where(on, q, zero), torch.where(on, dq, zero)
+
+
+def _project(p, H, Hn, Ht, Z, A, m, K):
     g = p["g"]
     tau = 1.0 / H
     un = Hn * tau
@@ -73,11 +107,27 @@ def _project(p, H, Hn, Ht, Z, A, m):
     speed2 = un * un + ut * ut
     zero = speed2 == 0
     sp = torch.sqrt(torch.where(zero, torch.ones_like(speed2), speed2))
-    lsp = torch.log(sp)
-    pm1 = torch.exp((m - 1.0) * lsp)
-    pm3 = torch.exp((m - 3.0) * lsp)
-    Q = torch.where(zero, torch.zeros_like(speed2), A * un * pm1)
-    dQ = torch.where(zero, torch.zeros_like(speed2), A * (pm1 + (m - 1.0) * un * un * pm3))
+    law = p.get("bedload", "grass")
+    if law == "grass":
+        lsp = torch.log(sp)
+        pm1 = torch.exp((m - 1.0) * lsp)
+        pm3 = torch.exp((m - 3.0) * lsp)
+        Q = torch.where(zero, torch.zeros_like(speed2), A * un * pm1)
+        dQ = torch.where(zero, torch.zeros_like(speed2), A * (pm1 + (m - 1.0) * un * un * pm3))
+    else:
+        # tau* = alpha |U|^2 for the friction law in use (K: its coefficient)
+        sm1 = p["s"] - 1.0
+        if p["friction"] == "darcy":
+            alpha = K / (8.0 * g * sm1 * p["d_s"])
+        else:
+            n = 1.0 / K
+            alpha = (n * n) / (sm1 * p["d_s"] * torch.pow(H, 1.0 / 3.0))
+        q, dq = _qstar(law, alpha * speed2, p["tau_cr"])
+        on = (~zero) & ((q != 0) | (dq != 0))
+        Cs = (sm1 * g * p["d_s"] ** 3) ** 0.5
+        Q = torch.where(on, Cs * q * (un / sp), torch.zeros_like(speed2))
+        dQ = torch.where(on, Cs * (2.0 * dq * alpha * (un * un) / sp + q * (ut * ut) / (speed2 * sp)),
+                         torch.zeros_like(speed2))
     ca = H * torch.sqrt(g * H)
     cb = torch.sqrt(Hn * Hn + g * H * H * dQ)
     return dict(H=H, Hn=Hn, Ht=Ht, Z=Z, tau=tau, un=un, ut=ut, Pi=Pi, Om=Q, ca=ca, cb=cb)
@@ -191,14 +241,14 @@ def step(p: dict, h, hu, hv, z, dt: float, A, m, K):
     H, Hu, Hv, Z = _ghosts(p, h, hu, hv, z)
     # x-interfaces: rows 1..ny, columns (i-1, i) for i = 0..nx
     r = slice(1, ny + 1)
-    L = _project(p, H[r, :-1], Hu[r, :-1], Hv[r, :-1], Z[r, :-1], A, m)
-    R = _project(p, H[r, 1:], Hu[r, 1:], Hv[r, 1:], Z[r, 1:], A, m)
+    L = _project(p, H[r, :-1], Hu[r, :-1], Hv[r, :-1], Z[r, :-1], A, m, K)
+    R = _project(p, H[r, 1:], Hu[r, 1:], Hv[r, 1:], Z[r, 1:], A, m, K)
     Amx, Apx = riemann(p, L, R)
     acc = [(Apx[c][:, :nx] + Amx[c][:, 1:]) / dx for c in range(4)]
     if dim == 2:
         cs = slice(1, nx + 1)
-        L = _project(p, H[:-1, cs], Hv[:-1, cs], Hu[:-1, cs], Z[:-1, cs], A, m)
-        R = _project(p, H[1:, cs], Hv[1:, cs], Hu[1:, cs], Z[1:, cs], A, m)
+        L = _project(p, H[:-1, cs], Hv[:-1, cs], Hu[:-1, cs], Z[:-1, cs], A, m, K)
+        R = _project(p, H[1:, cs], Hv[1:, cs], Hu[1:, cs], Z[1:, cs], A, m, K)
         Amy, Apy = riemann(p, L, R)
         ay = [(Apy[c][:ny, :] + Amy[c][1:, :]) / dy for c in range(4)]
         acc = [acc[0] + ay[0], acc[1] + ay[2], acc[2] + ay[1], acc[3] + ay[3]]

@@ -175,6 +175,7 @@ __global__ void __launch_bounds__(kAdjThreads) adj_friction_kernel(DevParams P, 
 // its two cells (a ghost side has mu = 0), stored in the fluctuation planes
 // (8 values: left state then right state, interface frame); A_g and m_g
 // gradients accumulated.
+template <bool GRASS>
 __global__ void __launch_bounds__(kAdjThreads) adj_interface_kernel(DevParams P, DevState<double> S,
                                                                     const double* mu, double dt, double A,
                                                                     double m, double* gpart, double* gacc,
@@ -226,13 +227,15 @@ __global__ void __launch_bounds__(kAdjThreads) adj_interface_kernel(DevParams P,
       double Amb[4], Apb[4];
 #pragma unroll
       for (int q = 0; q < 4; ++q) { Amb[q] = w * muL[q]; Apb[q] = w * muR[q]; }
-      double ub[8] = {0, 0, 0, 0, 0, 0, 0, 0}, Ab = 0.0, mb = 0.0;
+      double ub[8] = {0, 0, 0, 0, 0, 0, 0, 0}, Ab = 0.0, mb = 0.0, Kb = 0.0;
       // (the forward run solved this interface at this state; a failure
       // here leaves its contribution at zero, as the value pass did before)
-      sve::interface_vjp(P, u, A, m, Amb, Apb, ub, Ab, mb);
+      sve::interface_vjp<GRASS>(P, u, A, m, Amb, Apb, ub, Ab, mb, Kb);
 #pragma unroll
       for (int q = 0; q < 8; ++q) out[q] = ub[q];
-      out[8] = Ab;
+      // Grass: the A_g and m_g gradients; Shields laws: the friction
+      // coefficient's (through tau*)
+      out[8] = GRASS ? Ab : Kb;
       out[9] = mb;
     }
     double* v = ydir ? S.fy : S.fx;
@@ -244,11 +247,16 @@ __global__ void __launch_bounds__(kAdjThreads) adj_interface_kernel(DevParams P,
   }
   const double bA = block_sum(gA, sh);
   const double bm = block_sum(gm, sh);
-  if (threadIdx.x == 0) {
-    gpart[2 * blockIdx.x] = bA;
-    gpart[2 * blockIdx.x + 1] = bm;
+  if (GRASS) {
+    if (threadIdx.x == 0) {
+      gpart[2 * blockIdx.x] = bA;
+      gpart[2 * blockIdx.x + 1] = bm;
+    }
+    finish_partials<kAdjThreads>(gpart, 2, gacc, done);
+  } else {
+    if (threadIdx.x == 0) gpart[blockIdx.x] = bA;  // d/d(friction coefficient) through tau*
+    finish_partials<kAdjThreads>(gpart, 1, gacc + 2, done);
   }
-  finish_partials<kAdjThreads>(gpart, 2, gacc, done);
 }
 
 // Transposed ghost rule of side s in the side's frame (h, normal, tangential,
@@ -411,7 +419,7 @@ extern "C" {
 int sve_record_forward(sve_handle* h, int nsteps, int checkpoint_every) {
   if (!h || nsteps < 1) return SVE_ERR_ARG;
   if (!h->has_state) return SVE_ERR_STATE;
-  if (h->cfg.precision != SVE_FP64 || h->cfg.bedload != SVE_GRASS) return SVE_ERR_ARG;
+  if (h->cfg.precision != SVE_FP64) return SVE_ERR_ARG;
   sve_internal_adjoint_free(h);
   sve_adjoint_rec* r = new sve_adjoint_rec();
   h->adj = r;
@@ -535,8 +543,12 @@ int sve_adjoint(sve_handle* h, const void* lam_h, const void* lam_hu, const void
       if (rc) return rc;
       adj_friction_kernel<<<nb_c, kAdjThreads, 0, h->stream>>>(P, r->segc + (size_t)s * 4 * (size_t)ncell, lam,
                                                               r->mu, dt, r->gpart, r->gacc, r->done);
-      adj_interface_kernel<<<nb_if, kAdjThreads, 0, h->stream>>>(P, S, r->mu, dt, h->cfg.A_g, h->cfg.m_g,
-                                                                 r->gpart, r->gacc, r->done);
+      if (P.bedload == 0)
+        adj_interface_kernel<true><<<nb_if, kAdjThreads, 0, h->stream>>>(P, S, r->mu, dt, h->cfg.A_g, h->cfg.m_g,
+                                                                         r->gpart, r->gacc, r->done);
+      else
+        adj_interface_kernel<false><<<nb_if, kAdjThreads, 0, h->stream>>>(P, S, r->mu, dt, h->cfg.A_g, h->cfg.m_g,
+                                                                          r->gpart, r->gacc, r->done);
       adj_gather_kernel<<<nb_c, kAdjThreads, 0, h->stream>>>(P, S, r->mu, lam_next);
       if (cudaGetLastError() != cudaSuccess) return SVE_ERR_CUDA;
       double* t = lam;

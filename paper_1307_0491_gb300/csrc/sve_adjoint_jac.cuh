@@ -98,7 +98,83 @@ __device__ __forceinline__ void jac_pass(const DevParams& P, const double u[8], 
 struct ProjRec {
   double H, Hn, Ht, tau, un, ut, sp, pm1, pm3, dQ, ca, cb;
   bool still;  // |U| = 0
+  // Shields-parameter laws: tau* = alpha |U|^2, q*, its first two derivatives
+  double s2, isp, alpha, q, dq, ddq;
+  bool active;  // |U| > 0 and above the threshold
 };
+
+// q*, dq*/dtau* and d2q*/dtau*2 of the Shields-parameter laws (the forms of
+// shields_rate); false where q* = 0 (below the threshold).
+__device__ __forceinline__ bool shields_rate2(const DevParams& P, double ts, double& q, double& dq, double& ddq) {
+  const double tcr = P.tau_cr;
+  if (P.bedload == 5) {  // Camenen: 12 ts^1.5 exp(-4.5 tcr / ts)
+    if (!(ts > 0.0)) return false;
+    const double sts = sqrt(ts), its = 1.0 / ts, isq = 1.0 / sts;
+    const double e = exp(-4.5 * tcr * its);
+    const double g1 = 1.5 * sts + 4.5 * tcr * isq;  // dq = 12 e g1
+    q = 12.0 * ts * sts * e;
+    dq = 12.0 * e * g1;
+    ddq = 12.0 * e * (4.5 * tcr * its * its * g1 + 0.75 * isq - 2.25 * tcr * its * isq);
+    return true;
+  }
+  const double x = ts - tcr;
+  if (!(x > 0.0)) return false;
+  switch (P.bedload) {
+    case 1:    // Meyer-Peter & Mueller: 8 x^1.5
+    case 2: {  // Fernandez Luque & Van Beek: 5.7 x^1.5
+      const double c = P.bedload == 1 ? 8.0 : 5.7;
+      const double sx = sqrt(x);
+      q = c * x * sx;
+      dq = 1.5 * c * sx;
+      ddq = 0.75 * c / sx;
+      return true;
+    }
+    case 3: {  // Nielsen: 12 sqrt(ts) x
+      const double sts = sqrt(ts), isq = 1.0 / sts;
+      q = 12.0 * sts * x;
+      dq = 12.0 * (0.5 * x * isq + sts);
+      ddq = 12.0 * (isq - 0.25 * x * isq / ts);
+      return true;
+    }
+    case 4: {  // Ribberink: 11 x^1.65
+      q = 11.0 * pow(x, 1.65);
+      dq = 1.65 * q / x;
+      ddq = 0.65 * dq / x;
+      return true;
+    }
+    default: return false;
+  }
+}
+
+// Projection of one side with a Shields-parameter law (as closure() in the
+// interface frame), keeping its record.
+__device__ __forceinline__ Cell<double> project_shields_rec(const DevParams& P, double H, double Hn, double Ht,
+                                                            double Z, ProjRec& r) {
+  Cell<double> c;
+  c.H = H; c.Hn = Hn; c.Ht = Ht; c.Z = Z;
+  c.tau = 1.0 / H;
+  c.un = Hn * c.tau;
+  c.ut = Ht * c.tau;
+  c.Pi = 0.5 * P.g * H * H;
+  r.s2 = c.un * c.un + c.ut * c.ut;
+  r.alpha = P.mpm_alpha;
+  if (P.friction != 1) r.alpha = r.alpha * rcbrt64(H);  // Manning: tau* over h^(1/3)
+  r.active = r.s2 > 0.0 && shields_rate2(P, r.alpha * r.s2, r.q, r.dq, r.ddq);
+  double Q = 0.0, dQ = 0.0;
+  if (r.active) {
+    r.isp = 1.0 / sqrt(r.s2);
+    const double C = P.qs_scale;
+    Q = C * r.q * (c.un * r.isp);
+    dQ = C * (2.0 * r.dq * r.alpha * (c.un * c.un) * r.isp + r.q * (c.ut * c.ut) * (r.isp * r.isp * r.isp));
+  }
+  c.Om = Q;
+  c.ca = H * sqrt(P.g * H);
+  c.cb = sqrt(Hn * Hn + P.g * H * H * dQ);
+  r.still = r.s2 == 0.0;
+  r.sp = 0.0;
+  r.H = H; r.Hn = Hn; r.Ht = Ht; r.tau = c.tau; r.un = c.un; r.ut = c.ut; r.dQ = dQ; r.ca = c.ca; r.cb = c.cb;
+  return c;
+}
 
 // Cotangents of one side's projected cell.
 struct CellBar {
@@ -200,6 +276,61 @@ __device__ __forceinline__ void project_grass_bar(const DevParams& P, const Proj
   ub[3] += cb.Z;
 }
 
+// Backward sweep of project_shields_rec: cotangents of the cell's fields ->
+// of (H, Hn, Ht, Z) in ub[0..3] and of the friction coefficient (Kb:
+// through alpha = f / (8 g (s-1) d_s) for Darcy, n^2 / ((s-1) d_s) h^(-1/3)
+// with n = 1/K for Strickler).
+__device__ __forceinline__ void project_shields_bar(const DevParams& P, const ProjRec& r, CellBar cb, double ub[4],
+                                                    double& Kb) {
+  double Hb = cb.H, Hnb = cb.Hn, Htb = cb.Ht, taub = cb.tau, unb = cb.un, utb = cb.ut;
+  double dQb = 0.0;
+  if (r.cb > 0.0) {
+    const double Xb = cb.cb * 0.5 / r.cb;
+    Hnb += Xb * 2.0 * r.Hn;
+    Hb += Xb * 2.0 * P.g * r.H * r.dQ;
+    dQb = Xb * P.g * r.H * r.H;
+  }
+  Hb += cb.ca * 1.5 * r.ca * r.tau;  // ca = H sqrt(g H)
+  Hb += cb.Pi * P.g * r.H;           // Pi = g H^2 / 2
+  if (r.active) {
+    const double C = P.qs_scale, isp = r.isp, isp3 = isp * isp * isp;
+    const double un = r.un, ut = r.ut;
+    // Q = C q un isp
+    const double Qb = cb.Om;
+    double qb = Qb * C * un * isp;
+    unb += Qb * C * r.q * isp;
+    double ispb = Qb * C * r.q * un;
+    // dQ = C (2 dq alpha un^2 isp + q ut^2 isp^3)
+    const double dqb = dQb * C * 2.0 * r.alpha * un * un * isp;
+    double alphab = dQb * C * 2.0 * r.dq * un * un * isp;
+    unb += dQb * C * 4.0 * r.dq * r.alpha * un * isp;
+    ispb += dQb * C * (2.0 * r.dq * r.alpha * un * un + 3.0 * r.q * ut * ut * isp * isp);
+    qb += dQb * C * ut * ut * isp3;
+    utb += dQb * C * 2.0 * r.q * ut * isp3;
+    // q(ts), dq(ts), ts = alpha s2; isp = s2^(-1/2)
+    const double tsb = qb * r.dq + dqb * r.ddq;
+    alphab += tsb * r.s2;
+    const double s2b = tsb * r.alpha - 0.5 * ispb * isp3;
+    unb += 2.0 * un * s2b;
+    utb += 2.0 * ut * s2b;
+    if (P.friction == 1) {
+      Kb += alphab * r.alpha / P.fric_coef;
+    } else {
+      Kb -= alphab * 2.0 * r.alpha / P.fric_coef;
+      Hb -= alphab * r.alpha * r.tau * (1.0 / 3.0);
+    }
+  }
+  Hnb += unb * r.tau;
+  taub += unb * r.Hn;
+  Htb += utb * r.tau;
+  taub += utb * r.Ht;
+  Hb -= taub * r.tau * r.tau;
+  ub[0] += Hb;
+  ub[1] += Hnb;
+  ub[2] += Htb;
+  ub[3] += cb.Z;
+}
+
 // Cotangents of the Newton constants used by the evaluation and the fan.
 struct ConstBar {
   double a, b, K, inv_b, inv_K, D, C0, dZ;
@@ -273,13 +404,19 @@ __device__ __forceinline__ void newton_eval_bar(const NewtonConst<double>& c, co
 // the cotangents Amb (of A-) and Apb (of A+), added to ub[0..7] (left then
 // right state, frame order), Ab, mb (A_g, m_g).  u, A, m: as jac_pass.  The
 // value pass solves for the root as the step does; false if it fails.
+// GRASS: the Grass law (else a Shields-parameter law), compiled separately
+// to keep each form's registers.
+template <bool GRASS = true>
 __device__ __forceinline__ bool interface_vjp(const DevParams& P, const double u[8], double A, double m,
                                               const double Amb[4], const double Apb[4], double ub[8], double& Ab,
-                                              double& mb) {
+                                              double& mb, double& Kb) {
   // ---- value pass
   ProjRec rL, rR;
-  const Cell<double> L = project_grass_rec(P, u[0], u[1], u[2], u[3], A, m, rL);
-  const Cell<double> R = project_grass_rec(P, u[4], u[5], u[6], u[7], A, m, rR);
+  constexpr bool grass = GRASS;
+  const Cell<double> L = grass ? project_grass_rec(P, u[0], u[1], u[2], u[3], A, m, rL)
+                               : project_shields_rec(P, u[0], u[1], u[2], u[3], rL);
+  const Cell<double> R = grass ? project_grass_rec(P, u[4], u[5], u[6], u[7], A, m, rR)
+                               : project_shields_rec(P, u[4], u[5], u[6], u[7], rR);
   const double g = P.g;
   // celerities (as celerities(), keeping the branches)
   const bool a0L = L.ca >= R.ca, b0L = L.cb >= R.cb;
@@ -446,8 +583,13 @@ __device__ __forceinline__ bool interface_vjp(const DevParams& P, const double u
   if (b0L) Lb.cb += b0b;
   else Rb.cb += b0b;
   // projections
-  project_grass_bar(P, rL, A, m, Lb, ub, Ab, mb);
-  project_grass_bar(P, rR, A, m, Rb, ub + 4, Ab, mb);
+  if constexpr (grass) {
+    project_grass_bar(P, rL, A, m, Lb, ub, Ab, mb);
+    project_grass_bar(P, rR, A, m, Rb, ub + 4, Ab, mb);
+  } else {
+    project_shields_bar(P, rL, Lb, ub, Kb);
+    project_shields_bar(P, rR, Rb, ub + 4, Kb);
+  }
   return true;
 }
 

@@ -40,8 +40,8 @@ __global__ void probe(DevParams P, const double* in, double* out, int n) {
   double fwd[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
   jac_pass<0>(P, u, A, m, p, Fp, Amb, Apb, 1.0, fwd);
   jac_pass<1>(P, u, A, m, p, Fp, Amb, Apb, 1.0, fwd);
-  double ub[8] = {0, 0, 0, 0, 0, 0, 0, 0}, Ab = 0.0, mb = 0.0;
-  if (!interface_vjp(P, u, A, m, Amb, Apb, ub, Ab, mb)) o[0] = 0.0;
+  double ub[8] = {0, 0, 0, 0, 0, 0, 0, 0}, Ab = 0.0, mb = 0.0, Kb = 0.0;
+  if (!interface_vjp(P, u, A, m, Amb, Apb, ub, Ab, mb, Kb)) o[0] = 0.0;
   for (int k = 0; k < 10; ++k) o[1 + k] = fwd[k];
   for (int k = 0; k < 8; ++k) o[11 + k] = ub[k];
   o[19] = Ab;

@@ -206,3 +206,89 @@ def test_stored_and_checkpointed_recordings_agree():
             assert np.array_equal(out[every][2][k], out[0][2][k]), (every, k)
             assert np.array_equal(out[every][4][k], out[0][4][k]), (every, k)
         assert list(out[every][3]) == list(out[0][3])
+
+
+def shields_case(law, friction, bc):
+    """A Shields-parameter law on a supercritical channel with a rippled bed,
+    a small random transverse flow and a depth perturbed by 0.1 mm (tau*
+    around 1: above the threshold).  The antidune config's uniform depth
+    would make the celerity maxima of Eq. (ab) tie at every interface, where
+    the discrete map has kinks in h and the adjoint and the oracle's autograd
+    take different one-sided derivatives."""
+    w = W.antidune2d(nx=40, ny=24, seed=51)
+    w["params"].update(bedload=law, friction=friction, f_dw=0.02, K_st=40.0, bc=bc)
+    rng = np.random.default_rng(52)
+    w["hv"] = 0.02 * rng.standard_normal(np.shape(w["h"]))
+    w["h"] = w["h"] + 1e-4 * rng.standard_normal(np.shape(w["h"]))
+    target = w["z"] + 0.002 * rng.standard_normal(np.shape(w["z"]))
+    return w, target
+
+
+@pytest.mark.parametrize("law,friction,bc", [
+    ("mpm", "darcy", ("inflow_qh", "free", "wall", "free")),
+    ("mpm", "strickler", ("periodic",) * 4),
+    ("flvb", "darcy", ("periodic",) * 4),
+    ("nielsen", "strickler", ("inflow_qh", "free", "free", "free")),
+    ("ribberink", "darcy", ("periodic",) * 4),
+    ("camenen", "strickler", ("periodic",) * 4),
+])
+def test_shields_adjoint_equals_oracle_adjoint(law, friction, bc):
+    """The Shields-parameter laws in the adjoint (their q*, dq*/dtau* and
+    d2q*/dtau*2 in the reverse sweep; tau* through the friction
+    coefficient): GPU against the oracle-side adjoint, 1e-10 relative."""
+    import oracle
+    from oracle import adjoint as OA
+
+    w, target = shields_case(law, friction, bc)
+    p = w["params"]
+    n = 15
+    s = sve.Solver(p, "fp64")
+    s.set_state(w["h"], w["hu"], w["hv"], w["z"])
+    s.record_forward(n, 0)
+    fin = s.get_state()
+    grads, gp = s.adjoint(lam_z=2.0 * (fin["z"] - target))
+    s.close()
+    ref = oracle.get().run(oracle.Params.from_workload(p), n, w["h"], w["hu"], w["hv"], w["z"])
+    og = OA.gradients(p, w, ref["dts"], 2.0 * (np.asarray(ref["z"]) - target))
+    scale = max(np.max(np.abs(og["z"])), np.max(np.abs(og["h"])))
+    errs = {f: float(np.max(np.abs(grads[f] - og[f])) / scale) for f in ("z", "h")}
+    assert max(errs.values()) <= 1e-10, errs
+    assert gp[0] == 0.0 and gp[1] == 0.0
+    assert abs(gp[2] - og["params"][2]) <= 1e-10 * abs(og["params"][2]), (gp, og["params"])
+
+
+def test_shields_adjoint_vs_central_differences():
+    """MPM with Strickler friction (tau* with h^(-1/3)): the friction
+    coefficient's gradient (through the friction and through tau*) and a bed
+    direction against central differences of the GPU forward run."""
+    w, target = shields_case("mpm", "strickler", ("periodic",) * 4)
+    p = w["params"]
+    n = 15
+    s = sve.Solver(p, "fp64")
+    s.set_state(w["h"], w["hu"], w["hv"], w["z"])
+    s.record_forward(n, 4)
+    fin = s.get_state()
+    grads, gp = s.adjoint(lam_z=2.0 * (fin["z"] - target))
+    s.close()
+    s2 = sve.Solver(p, "fp64")
+    s2.set_state(w["h"], w["hu"], w["hv"], w["z"])
+    s2.step(n)
+    dts = s2.dts(n)
+    s2.close()
+    v = p["K_st"]
+    e = 1e-5 * v
+    pp, pm = dict(p), dict(p)
+    pp["K_st"], pm["K_st"] = v + e, v - e
+    fd = (loss(forward_fixed(w, pp, dts), target) - loss(forward_fixed(w, pm, dts), target)) / (2 * e)
+    assert abs(gp[2] - fd) <= 1e-6 * abs(fd), (gp[2], fd)
+    rng = np.random.default_rng(53)
+    d = rng.uniform(-1, 1, np.shape(w["z"]))
+    # a small step: with the small transverse flow the contact speed of some
+    # y-interfaces is near zero, where the fan's wave count (and the map's
+    # slope) changes; the difference quotient's error from such crossings
+    # shrinks with the step (as in the oracle-side checks)
+    e = 1e-8
+    fd = (loss(forward_fixed(w, p, dts, z0=w["z"] + e * d), target) -
+          loss(forward_fixed(w, p, dts, z0=w["z"] - e * d), target)) / (2 * e)
+    ad = float(np.sum(grads["z"] * d))
+    assert abs(ad - fd) <= 1e-6 * abs(fd), (ad, fd)
