@@ -329,6 +329,11 @@ struct Cell {
 template <typename T>
 struct NewtonConst {
   T a, b, K, inv_a, inv_b, inv_K, D, C0, dZ, dsig, dN;
+  // combinations the evaluation uses as they are (loop invariants of the
+  // Newton iteration): sigma = s0 + dsig p, tau2,3 = sigma/2 -+ hD,
+  // N = dZ + KD sigma, u1 = lam1 + a tau1, u4 = lam5 - a tau4,
+  // F = dOm + lam2 zl - lam4 zr, F' uses amb = a - b
+  T s0, hD, KD, lam1, lam5, dOm, amb;
 };
 
 // The intermediate states as functions of p (every invariant relation of the
@@ -341,26 +346,28 @@ struct NewtonEval {
 };
 
 // The states at p given m = tau1 - tau4 and 1/p (e.tau2, e.tau3 set).
+// (u1 = uL + a (tau1 - tauL) = lam1 + a tau1, u4 = lam5 - a tau4.)
 template <typename T>
 __device__ __forceinline__ void newton_states(T p, const NewtonConst<T>& c, const Cell<T>& L, const Cell<T>& R,
                                               NewtonEval<T>& e) {
-  e.tau1 = T(0.5) * (p + e.m);
-  e.tau4 = T(0.5) * (p - e.m);
-  e.u1 = L.un + c.a * (e.tau1 - L.tau);
-  e.u4 = R.un - c.a * (e.tau4 - R.tau);
+  const T hp = T(0.5) * p;
+  e.tau1 = hp + T(0.5) * e.m;
+  e.tau4 = hp - T(0.5) * e.m;
+  e.u1 = c.lam1 + c.a * e.tau1;
+  e.u4 = c.lam5 - c.a * e.tau4;
   e.lam2 = e.u1 - c.b * e.tau1;
   e.lam4 = e.u4 + c.b * e.tau4;
   e.Zs = L.Z + c.K * (e.tau2 * e.tau2 - e.tau1 * e.tau1);
   e.zl = e.Zs - L.Z;
   e.zr = e.Zs - R.Z;
-  e.F = (L.Om - R.Om) + e.lam2 * e.zl - e.lam4 * e.zr;
+  e.F = c.dOm + e.lam2 * e.zl - e.lam4 * e.zr;
 }
 
 template <typename T>
 __device__ __forceinline__ void newton_sigma(T p, const NewtonConst<T>& c, NewtonEval<T>& e, T& sigma) {
-  sigma = (c.C0 - (c.a - c.b) * p) * c.inv_b;       // from u* continuity
-  e.tau2 = T(0.5) * (sigma - c.D);                  // from Pi continuity
-  e.tau3 = T(0.5) * (sigma + c.D);
+  sigma = c.s0 + c.dsig * p;                        // from u* continuity: (C0 - (a - b) p) / b
+  e.tau2 = T(0.5) * sigma - c.hD;                   // from Pi continuity: (sigma -+ D) / 2
+  e.tau3 = T(0.5) * sigma + c.hD;
 }
 
 // The states and F at p, with ip = 1/p given.
@@ -369,7 +376,7 @@ __device__ __forceinline__ void newton_eval_ip(T p, T ip, const NewtonConst<T>& 
                                                const Cell<T>& R, NewtonEval<T>& e) {
   T sigma;
   newton_sigma(p, c, e, sigma);
-  const T N = c.dZ + c.K * c.D * sigma;
+  const T N = c.dZ + c.KD * sigma;
   e.ip = ip;
   e.m = -N * e.ip * c.inv_K;                        // from Z* continuity
   newton_states(p, c, L, R, e);
@@ -384,13 +391,13 @@ __device__ __forceinline__ void newton_eval(T p, const NewtonConst<T>& c, const 
 // Analytic F'(p) at an evaluated point.
 template <typename T>
 __device__ __forceinline__ T newton_deriv(const NewtonConst<T>& c, const NewtonEval<T>& e, T& dm) {
-  const T amb = c.a - c.b;
   dm = -c.dN * e.ip * c.inv_K - e.m * e.ip;
-  const T dtau1 = T(0.5) * (T(1) + dm);
-  const T dtau4 = T(0.5) * (T(1) - dm);
+  const T dtau1 = T(0.5) + T(0.5) * dm;
+  const T dtau4 = T(0.5) - T(0.5) * dm;
   const T dtau2 = T(0.5) * c.dsig;
   const T dZs = T(2) * c.K * (e.tau2 * dtau2 - e.tau1 * dtau1);
-  return amb * dtau1 * e.zl + e.lam2 * dZs + amb * dtau4 * e.zr - e.lam4 * dZs;
+  // (a - b) (dtau1 zl + dtau4 zr) + (lam2 - lam4) dZs
+  return c.amb * (dtau1 * e.zl + dtau4 * e.zr) + (e.lam2 - e.lam4) * dZs;
 }
 
 template <typename T>
@@ -528,8 +535,15 @@ __device__ __forceinline__ T newton_setup(const DevParams& P, const Cell<T>& L, 
   c.K = a2mb2 * par<T>(P.inv_2g, P.f.inv_2g);
   c.D = (R.tau - L.tau) + (R.Pi - L.Pi) * (inv_a * inv_a);
   c.dZ = R.Z - L.Z;
-  c.dsig = -(a - b) * c.inv_b;
-  c.dN = c.K * c.D * c.dsig;
+  c.amb = a - b;
+  c.dsig = -c.amb * c.inv_b;
+  c.KD = c.K * c.D;
+  c.dN = c.KD * c.dsig;
+  c.s0 = c.C0 * c.inv_b;
+  c.hD = T(0.5) * c.D;
+  c.lam1 = L.un - a * L.tau;
+  c.lam5 = R.un + a * R.tau;
+  c.dOm = L.Om - R.Om;
   const T p0 = L.tau + R.tau + du * inv_a;
   if constexpr (cheap_div<T>::value) {
     if (ip0) *ip0 = tdiv(T(1), p0);
@@ -550,8 +564,8 @@ __device__ __forceinline__ void fan_fluctuations(const DevParams& P, const Cell<
                                                  const NewtonConst<T>& c, const NewtonEval<T>& e, T Am[4], T Ap[4]) {
   const T g = par<T>(P.g, P.f.g);
   const T a = c.a, b = c.b;
-  const T lam1 = L.un - a * L.tau;
-  const T lam5 = R.un + a * R.tau;
+  const T lam1 = c.lam1;
+  const T lam5 = c.lam5;
   const T us = e.u1 + b * (e.tau2 - e.tau1);
   const T lam2 = e.lam2, lam4 = e.lam4;
   const int m = (int)negative(lam1) + (int)negative(lam2) + (int)negative(us) + (int)negative(lam4) +
