@@ -101,6 +101,8 @@ void make_params(const sve_config* c, DevParams* P) {
   P->gamma_z = c->gamma_z;
   P->newton_tol = c->newton_tol;
   P->newton_maxit = c->newton_maxit;
+  P->two_g = 2.0 * c->g;
+  P->two_g_gamma = 2.0 * c->g * c->gamma_z;
   P->nfx = (long long)(P->nx + 1) * P->ny;
   P->nfy = P->dim == 2 ? (long long)P->nx * (P->ny + 1) : 0;
   P->f.g = (float)P->g;
@@ -117,6 +119,8 @@ void make_params(const sve_config* c, DevParams* P) {
   P->f.beta_min = (float)P->beta_min;
   P->f.gamma_z = (float)P->gamma_z;
   P->f.newton_tol = (float)P->newton_tol;
+  P->f.two_g = (float)P->two_g;
+  P->f.two_g_gamma = (float)P->two_g_gamma;
 }
 
 template <typename T>

@@ -43,6 +43,7 @@ struct DevParams {
   int bc[4];
   double q_in, h_in;
   double kappa_a, beta_min, gamma_z, newton_tol;
+  double two_g, two_g_gamma;  // 2 g and 2 g gamma_z (products the solver uses)
   int newton_maxit;
   long long nfx, nfy;   // number of x- and y-interfaces
   // FP32 copies (rounded on the host) for the FP32-state kernels: converting
@@ -50,6 +51,7 @@ struct DevParams {
   // pipe is ~1/64 of its FP32 pipe
   struct {
     float g, inv_2g, A_g, m_g, qs_scale, mpm_alpha, tau_cr, fric_c, q_in, h_in, kappa_a, beta_min, gamma_z, newton_tol;
+    float two_g, two_g_gamma;
   } f;
 };
 
@@ -494,7 +496,7 @@ __device__ __forceinline__ void celerities(const DevParams& P, const Cell<T>& L,
   a = par<T>(P.kappa_a, P.f.kappa_a) * nnmax(a0, b0);
   b = nnmax(b0, par<T>(P.beta_min, P.f.beta_min) * a0);
   const T Hmax = nnmax(L.H, R.H);
-  const T need = b * b + T(2) * g * par<T>(P.gamma_z, P.f.gamma_z) * absbits(R.Z - L.Z) * (Hmax * Hmax);
+  const T need = b * b + par<T>(P.two_g_gamma, P.f.two_g_gamma) * (absbits(R.Z - L.Z) * (Hmax * Hmax));
   if (a * a < need) a = tsqrt(need);
 }
 
@@ -511,7 +513,7 @@ __device__ __forceinline__ T newton_setup(const DevParams& P, const Cell<T>& L, 
   T rab;
   if constexpr (cheap_div<T>::value) {
     rab = tdiv(T(1), ab);
-    c.inv_K = tdiv(T(2) * g, a2mb2);
+    c.inv_K = tdiv(par<T>(P.two_g, P.f.two_g), a2mb2);
   } else if (ip0) {
     // one divide for 1/a, 1/b, 1/K (a^2 - b^2 >= (1 - 1/kappa_a^2) a^2 > 0)
     // and 1/p0 = a / C0
@@ -519,13 +521,13 @@ __device__ __forceinline__ T newton_setup(const DevParams& P, const Cell<T>& L, 
     const T r = tdiv(T(1), q * c.C0);
     const T rq = r * c.C0;
     rab = rq * a2mb2;
-    c.inv_K = (T(2) * g) * (ab * rq);
+    c.inv_K = par<T>(P.two_g, P.f.two_g) * (ab * rq);
     *ip0 = a * (r * q);
   } else {
     // one divide for 1/a, 1/b and 1/K
     const T r = tdiv(T(1), ab * a2mb2);
     rab = r * a2mb2;
-    c.inv_K = (T(2) * g) * (ab * r);
+    c.inv_K = par<T>(P.two_g, P.f.two_g) * (ab * r);
   }
   const T inv_a = b * rab;
   c.a = a;
@@ -595,19 +597,20 @@ __device__ __forceinline__ void fan_fluctuations(const DevParams& P, const Cell<
   }
   // b-waves: bed jumps and the non-conservative source g Hbar [Z]; one
   // divide for 1/tau_k, 1/(tau1 + tau2) and 1/(tau3 + tau4)
-  const T zj2 = e.Zs - L.Z, zj4 = R.Z - e.Zs;
+  const T zj2 = e.zl, zj4 = -e.zr;  // Z* - ZL, ZR - Z*
   const T d12 = e.tau1 + e.tau2, d34 = e.tau3 + e.tau4;
+  const T g2 = par<T>(P.two_g, P.f.two_g);
   T S2, S4, Hk;
   if constexpr (cheap_div<T>::value) {
-    S2 = tdiv(T(2) * g * zj2, d12);
-    S4 = tdiv(T(2) * g * zj4, d34);
+    S2 = tdiv(g2 * zj2, d12);
+    S4 = tdiv(g2 * zj4, d34);
     Hk = tdiv(T(1), tkv);
   } else {
     const T d1234 = d12 * d34;
     const T r = tdiv(T(1), tkv * d1234);
     const T rt = r * tkv;
-    S2 = (T(2) * g * zj2) * (rt * d34);
-    S4 = (T(2) * g * zj4) * (rt * d12);
+    S2 = (g2 * zj2) * (rt * d34);
+    S4 = (g2 * zj4) * (rt * d12);
     Hk = r * d1234;
   }
   if (m != 0 && m != 5) {
@@ -676,13 +679,14 @@ __device__ __forceinline__ void store_cell(const DevParams& P, const DevState<T>
   if (P.dim == 2) closure2(P, H, u, v, Qx, dQx, Qy, dQy);
   else closure(P, H, u, v, Qx, dQx);
   const T g = par<T>(P.g, P.f.g);
+  const T gH = g * H, gHH = gH * H;
   S.h[e] = H; S.hu[e] = s[1]; S.hv[e] = s[2]; S.z[e] = s[3];
   S.tau[e] = tau; S.u[e] = u; S.v[e] = v;
-  S.pi[e] = T(0.5) * g * H * H;
+  S.pi[e] = T(0.5) * gHH;
   S.omx[e] = Qx; S.omy[e] = Qy;
-  S.ca[e] = H * tsqrt(g * H);
-  S.cbx[e] = tsqrt(s[1] * s[1] + g * H * H * dQx);
-  S.cby[e] = P.dim == 2 ? tsqrt(s[2] * s[2] + g * H * H * dQy) : T(0);
+  S.ca[e] = H * tsqrt(gH);
+  S.cbx[e] = tsqrt(s[1] * s[1] + gHH * dQx);
+  S.cby[e] = P.dim == 2 ? tsqrt(s[2] * s[2] + gHH * dQy) : T(0);
 }
 
 __device__ __forceinline__ long long ext_index(const DevParams& P, int i, int j) {

@@ -70,6 +70,8 @@ int main() {
   P.kappa_a = 1.1;
   P.beta_min = 0.01;
   P.gamma_z = 2.0;
+  P.two_g = 2.0 * 9.81;
+  P.two_g_gamma = 2.0 * 9.81 * 2.0;
   P.newton_tol = 1e-9;
   P.newton_maxit = 30;
   P.bedload = 0;
