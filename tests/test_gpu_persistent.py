@@ -161,3 +161,24 @@ def test_bounded_barrier_wait():
     ref = run(w, 50, False)
     for k in ("h", "hu", "z"):
         assert np.array_equal(got[k], ref[k]), k
+
+
+def test_persistent_then_host_mirror():
+    """sve_advance with the persistent step: the steps before the last run
+    persistent, the last one as the two-kernel step that stores into the
+    page-locked host buffers."""
+    import torch
+
+    w = W.dune1d(nx=400)
+    r = run(w, 60, False)
+    s = sve.Solver(w["params"], "fp64")
+    s.set_persistent(1)
+    keys = ("h", "hu", "z")
+    inp = {k: torch.from_numpy(np.ascontiguousarray(w[k], dtype=np.float64)).pin_memory().numpy() for k in keys}
+    out = {k: torch.empty(np.shape(w[k]), dtype=torch.float64).pin_memory().numpy() for k in keys}
+    t = s.advance(60, inp, out)
+    assert s.launches() == 3  # one persistent launch, then the last step's two kernels
+    s.close()
+    errs = {k: float(np.max(np.abs(out[k] - r[k])) / np.max(np.abs(r[k]))) for k in keys}
+    assert max(errs.values()) <= 1e-12, errs
+    assert abs(t - r["t"]) <= 1e-12 * r["t"]
