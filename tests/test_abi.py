@@ -94,3 +94,17 @@ def test_config_mapping_from_workload(lib):
     assert c.bedload == sve.SVE_MPM and c.friction == sve.SVE_FRIC_DARCY and c.precision == sve.SVE_FP32
     assert list(c.bc) == [sve.SVE_BC_INFLOW_QH, sve.SVE_BC_FREE, sve.SVE_BC_FREE, sve.SVE_BC_FREE]
     assert c.h_in == 0.5 and c.f_dw == 0.02 and c.nx == 16 and c.ny == 8
+
+
+def test_null_handle_checks_of_later_calls(lib):
+    """The host-to-host call, the persistent-step switch, its bounded-wait
+    check and the recording query answer SVE_ERR_ARG for a NULL handle on
+    the host, before any device call."""
+    null = ctypes.c_void_p(None)
+    z = [None, None, None, None]
+    rc, _ = sve.sve_advance(null, 1, z, z, sve.SVE_HOST)
+    assert rc == sve.SVE_ERR_ARG
+    assert lib.sve_set_persistent(null, 1) == sve.SVE_ERR_ARG
+    assert lib.sve_get_persistent(null) == sve.SVE_ERR_ARG
+    assert lib.sve_check_sync_timeout(null, 100) == sve.SVE_ERR_ARG
+    assert lib.sve_get_checkpoint_every(null) == sve.SVE_ERR_ARG
