@@ -108,3 +108,12 @@ def test_null_handle_checks_of_later_calls(lib):
     assert lib.sve_get_persistent(null) == sve.SVE_ERR_ARG
     assert lib.sve_check_sync_timeout(null, 100) == sve.SVE_ERR_ARG
     assert lib.sve_get_checkpoint_every(null) == sve.SVE_ERR_ARG
+
+
+def test_missing_library_fails_loudly(monkeypatch, tmp_path):
+    """No CPU fallback: without libsve.so the binding raises instead of
+    computing anything."""
+    monkeypatch.setattr(sve, "_LIB", None)
+    monkeypatch.setattr(sve, "lib_path", lambda: str(tmp_path / "libsve.so"))
+    with pytest.raises(RuntimeError, match="libsve.so not found"):
+        sve.load()
