@@ -83,6 +83,7 @@ class _RiemannOut(ctypes.Structure):
         ("Z", ctypes.c_double * 6), ("Pi", ctypes.c_double * 6), ("Om", ctypes.c_double * 6),
         ("Am", ctypes.c_double * 4), ("Ap", ctypes.c_double * 4),
         ("iters", ctypes.c_int), ("status", ctypes.c_int),
+        ("halvings", ctypes.c_int), ("raised", ctypes.c_int), ("retries", ctypes.c_int),
     ]
 
 
@@ -168,10 +169,11 @@ class Oracle:
         L.orc_run.argtypes = [ctypes.POINTER(_Params), ctypes.c_int, dp, dp, dp, dp, dp, dp, dp, dp,
                               ctypes.POINTER(ctypes.c_int)]
         L.orc_run.restype = ctypes.c_int
-        for name in ("orc_block_ghost", "orc_block_speeds", "orc_block_advance"):
-            getattr(L, name).argtypes = [ctypes.POINTER(_Params), ctypes.c_int, ctypes.c_int, dp, dp, dp, dp] + (
-                [ctypes.c_int] if name == "orc_block_ghost" else [dp] if name == "orc_block_speeds" else
-                [ctypes.c_double])
+        blk = [ctypes.POINTER(_Params), ctypes.c_int, ctypes.c_int, dp, dp, dp, dp]
+        L.orc_block_ghost.argtypes = blk + [ctypes.c_int]
+        L.orc_block_solve.argtypes = blk + [dp, dp]
+        L.orc_block_update.argtypes = blk + [dp, ctypes.c_double]
+        for name in ("orc_block_ghost", "orc_block_solve", "orc_block_update"):
             getattr(L, name).restype = ctypes.c_int
         L.orc_block_dt.argtypes = [ctypes.POINTER(_Params), ctypes.c_double, ctypes.c_double, dp]
         L.orc_block_dt.restype = ctypes.c_int
@@ -187,7 +189,8 @@ class Oracle:
         cp = p.to_c()
         st = self.lib.orc_riemann(ctypes.byref(cp), lc, rc, ctypes.byref(out))
         res = {
-            "status": st, "iters": out.iters, "a": out.a, "b": out.b, "K": out.K,
+            "status": st, "iters": out.iters, "halvings": out.halvings, "raised": out.raised,
+            "retries": out.retries, "a": out.a, "b": out.b, "K": out.K,
             "lam": np.array(out.lam[:]),
             "tau": np.array(out.tau[:]), "u": np.array(out.u[:]), "v": np.array(out.v[:]),
             "Z": np.array(out.Z[:]), "Pi": np.array(out.Pi[:]), "Om": np.array(out.Om[:]),
@@ -268,6 +271,8 @@ class Block:
         self.orc, self.p, self.cp = orc, p, p.to_c()
         self.nxl, self.nyl = nxl, nyl
         self.f = {k: np.zeros((nyl + 2, nxl + 2)) for k in ("h", "hu", "hv", "z")}
+        self.work = np.zeros(4 * nxl * nyl)  # net fluctuations of the last solve
+        self.solved = False
 
     def set_interior(self, h, hu, hv, z):
         for k, a in zip(("h", "hu", "hv", "z"), (h, hu, hv, z)):
@@ -285,10 +290,14 @@ class Block:
             raise OracleError(st, "block_ghost")
 
     def speeds(self):
+        """Solve every interface of the block (ghosts filled), keep the net
+        fluctuations for ``advance`` and return the extreme speeds."""
         S = (ctypes.c_double * 2)()
-        st = self.orc.lib.orc_block_speeds(ctypes.byref(self.cp), self.nxl, self.nyl, *self._ptrs(), S)
+        wp = self.work.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+        st = self.orc.lib.orc_block_solve(ctypes.byref(self.cp), self.nxl, self.nyl, *self._ptrs(), wp, S)
         if st:
-            raise OracleError(st, "block_speeds")
+            raise OracleError(st, "block_solve")
+        self.solved = True
         return S[0], S[1]
 
     def dt(self, Sx: float, Sy: float) -> float:
@@ -299,9 +308,15 @@ class Block:
         return d.value
 
     def advance(self, dt: float):
-        st = self.orc.lib.orc_block_advance(ctypes.byref(self.cp), self.nxl, self.nyl, *self._ptrs(), float(dt))
+        """Step dt from the fluctuations of the preceding ``speeds`` call."""
+        if not self.solved:
+            raise RuntimeError("Block.advance needs the solve of Block.speeds on the same state")
+        wp = self.work.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+        st = self.orc.lib.orc_block_update(ctypes.byref(self.cp), self.nxl, self.nyl, *self._ptrs(), wp,
+                                           float(dt))
+        self.solved = False
         if st:
-            raise OracleError(st, "block_advance")
+            raise OracleError(st, "block_update")
 
 
 _DEFAULT: Oracle | None = None

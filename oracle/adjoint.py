@@ -172,31 +172,44 @@ def riemann(p, L, R, tol=1e-9, maxit=30):
     Hmax = torch.maximum(L["H"], R["H"])
     need = b * b + 2.0 * g * p["gamma_z"] * torch.abs(R["Z"] - L["Z"]) * Hmax * Hmax
     a = torch.where(a * a < need, torch.sqrt(need), a)
-    K = (a * a - b * b) / (2.0 * g)
-    D = (R["tau"] - L["tau"]) + (R["Pi"] - L["Pi"]) / (a * a)
-    c = dict(a=a, b=b, K=K, D=D, du=R["un"] - L["un"], dZ=R["Z"] - L["Z"])
-    p0 = L["tau"] + R["tau"] + c["du"] / a
-    # Newton to convergence without gradients (reading R2)
-    with torch.no_grad():
-        cd = {k: v.detach() for k, v in c.items()}
-        Ld = {k: v.detach() for k, v in L.items()}
-        Rd = {k: v.detach() for k, v in R.items()}
-        pp = p0.detach().clone()
-        done = torch.zeros_like(pp, dtype=torch.bool)
-        for _ in range(maxit):
-            e = _eval(pp, cd, Ld, Rd)
-            step = -e["F"] / _dF(pp, cd, Ld, Rd)
-            step = torch.where(done, torch.zeros_like(step), step)
-            for _h in range(61):
-                t = _eval(pp + step, cd, Ld, Rd)
-                ok = (t["tau1"] > 0) & (t["tau2"] > 0) & (t["tau3"] > 0) & (t["tau4"] > 0)
-                if bool(ok.all()):
+    same = (L["H"] == R["H"]) & (L["Hn"] == R["Hn"]) & (L["Ht"] == R["Ht"]) & (L["Z"] == R["Z"])
+    Ld = {k: v.detach() for k, v in L.items()}
+    Rd = {k: v.detach() for k, v in R.items()}
+    # Newton to convergence without gradients (reading R2); where the
+    # celerities admit no root with positive tau_k, a is doubled and the
+    # iteration restarted, at most three times (reading R12)
+    for attempt in range(4):
+        K = (a * a - b * b) / (2.0 * g)
+        D = (R["tau"] - L["tau"]) + (R["Pi"] - L["Pi"]) / (a * a)
+        c = dict(a=a, b=b, K=K, D=D, du=R["un"] - L["un"], dZ=R["Z"] - L["Z"])
+        p0 = L["tau"] + R["tau"] + c["du"] / a
+        with torch.no_grad():
+            cd = {k: v.detach() for k, v in c.items()}
+            pp = p0.detach().clone()
+            done = torch.zeros_like(pp, dtype=torch.bool)
+            for _ in range(maxit):
+                e = _eval(pp, cd, Ld, Rd)
+                step = -e["F"] / _dF(pp, cd, Ld, Rd)
+                step = torch.where(done, torch.zeros_like(step), step)
+                halved = torch.zeros_like(done)
+                for _h in range(61):
+                    t = _eval(pp + step, cd, Ld, Rd)
+                    ok = (t["tau1"] > 0) & (t["tau2"] > 0) & (t["tau3"] > 0) & (t["tau4"] > 0)
+                    if bool(ok.all()):
+                        break
+                    step = torch.where(ok, step, 0.5 * step)
+                    halved = halved | ~ok
+                pp = pp + step
+                # only a full Newton step measures the distance to the root
+                done = done | (~halved & (step.abs() <= tol * pp))
+                if bool(done.all()):
                     break
-                step = torch.where(ok, step, 0.5 * step)
-            pp = pp + step
-            done = done | (step.abs() <= tol * pp)
-            if bool(done.all()):
+            t = _eval(pp, cd, Ld, Rd)
+            good = same | (done & (t["tau1"] > 0) & (t["tau2"] > 0) & (t["tau3"] > 0) & (t["tau4"] > 0))
+            if bool(good.all()) or attempt == 3:
                 break
+        a = torch.where(good, a, 2.0 * a)
+    with torch.no_grad():
         Fp = _dF(pp, cd, Ld, Rd)
     # one Newton update with F' held constant: value ~ the root, derivative
     # of the implicit function theorem

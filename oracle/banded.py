@@ -5,13 +5,14 @@ one ghost layer) per band, stepped on a pool of threads.
 Test infrastructure, like the rest of ``oracle/``: only the tests and the
 benchmark's CPU legs use it.  It adds no arithmetic of its own: each band
 runs the oracle's own block functions (``orc_block_ghost``,
-``orc_block_speeds``, ``orc_block_dt``, ``orc_block_advance``), which do the
+``orc_block_solve``, ``orc_block_dt``, ``orc_block_update``), which do the
 arithmetic of the whole-grid stepper, and the ctypes calls release the GIL,
 so the bands run in parallel.  Per step: (1) every band's halo rows are
 copied from its neighbours' interiors (periodic sides wrap), (2) each band
-fills its ghosts on physical sides and returns its extreme wave speeds,
-(3) the global CFL step is taken from the maximum over the bands (an
-order-free reduction), (4) each band advances.  The result equals the
+fills its ghosts on physical sides, solves its interfaces and returns its
+extreme wave speeds, (3) the global CFL step is taken from the maximum over
+the bands (an order-free reduction), (4) each band advances with the
+fluctuations of its solve.  The result equals the
 single-threaded run bit for bit (tested).
 """
 from __future__ import annotations

@@ -119,6 +119,11 @@ typedef struct {
   double tau[6], u[6], v[6], Z[6], Pi[6], Om[6];
   double Am[4], Ap[4]; /* fluctuations of (H, H u_n, H u_t, Z) */
   int iters, status;
+  /* which safeguards this solve used: halvings = Newton steps halved (summed
+   * over the accepted updates and the attempts); raised = 1 if the bed-jump
+   * bound of reading R1 set a; retries = how often a was doubled (reading
+   * R12) -- counters for the tests, no effect on the result */
+  int halvings, raised, retries;
 } orc_riemann_out;
 
 /* ---- closures (Sec. 2) ------------------------------------------------- */
@@ -263,8 +268,8 @@ static orc_cell orc_project(const orc_params* P, double H, double Hun, double Hu
  * and a raised where needed so that K = (a^2 - b^2)/(2g) satisfies
  * K tau_min^2 >= gamma_z |Z_R - Z_L| (the sediment waves can carry the bed
  * jump; one of the "stronger bounds" Sec. 3 says well-definedness may need). */
-static void orc_celerities(const orc_params* P, const orc_cell* L, const orc_cell* R, double* a_out,
-                           double* b_out) {
+static int orc_celerities(const orc_params* P, const orc_cell* L, const orc_cell* R, double* a_out,
+                          double* b_out) {
   double a0 = L->ca > R->ca ? L->ca : R->ca;
   double b0 = L->cb > R->cb ? L->cb : R->cb;
   double a = P->kappa_a * (a0 > b0 ? a0 : b0);
@@ -272,9 +277,11 @@ static void orc_celerities(const orc_params* P, const orc_cell* L, const orc_cel
   double b = b0 > bfloor ? b0 : bfloor;
   double Hmax = L->H > R->H ? L->H : R->H;
   double need = b * b + 2.0 * P->g * P->gamma_z * fabs(R->Z - L->Z) * (Hmax * Hmax);
-  if (a * a < need) a = sqrt(need);
+  int raised = a * a < need;
+  if (raised) a = sqrt(need);
   *a_out = a;
   *b_out = b;
+  return raised;
 }
 
 typedef struct {
@@ -327,30 +334,15 @@ static int orc_tau_positive(const orc_eval* e) {
   return e->tau[0] > 0.0 && e->tau[1] > 0.0 && e->tau[2] > 0.0 && e->tau[3] > 0.0;
 }
 
-/* Solve one interface.  L, R projected cells; Lc, Rc their conserved states
- * (H, H un, H ut, Z).  Fills o (states, speeds, fluctuations). */
-static int orc_solve(const orc_params* P, const orc_cell* L, const orc_cell* R, const double Lc[4],
-                     const double Rc[4], orc_riemann_out* o) {
-  memset(o, 0, sizeof(*o));
-  o->status = ORC_OK;
-  double a, b;
-  orc_celerities(P, L, R, &a, &b);
+/* The Riemann problem at the celerities (a, b): the scalar Newton iteration
+ * in p, then the intermediate states and the fluctuations.  ORC_ERR_RIEMANN
+ * if no root with positive tau_k was reached. */
+static int orc_solve_at(const orc_params* P, const orc_cell* L, const orc_cell* R, const double Lc[4],
+                        const double Rc[4], double a, double b, orc_riemann_out* o) {
   double K = (a * a - b * b) / (2.0 * P->g);
   o->a = a; o->b = b; o->K = K;
   o->lam[0] = L->un - a * L->tau;
   o->lam[4] = R->un + a * R->tau;
-
-  /* reading R3: identical states */
-  if (Lc[0] == Rc[0] && Lc[1] == Rc[1] && Lc[2] == Rc[2] && Lc[3] == Rc[3]) {
-    o->lam[1] = L->un - b * L->tau;
-    o->lam[2] = L->un;
-    o->lam[3] = L->un + b * L->tau;
-    for (int k = 0; k < 6; ++k) {
-      o->tau[k] = L->tau; o->u[k] = L->un; o->v[k] = L->ut; o->Z[k] = L->Z; o->Pi[k] = L->Pi; o->Om[k] = L->Om;
-    }
-    return ORC_OK;
-  }
-
   double D = (R->tau - L->tau) + (R->Pi - L->Pi) / (a * a);
   double du = R->un - L->un;
   double dZ = R->Z - L->Z;
@@ -367,22 +359,23 @@ static int orc_solve(const orc_params* P, const orc_cell* L, const orc_cell* R, 
     if (!isfinite(dp)) break;
     double step = dp;
     orc_eval trial;
-    int ok = 0;
+    int ok = 0, halved = 0;
     for (int halve = 0; halve <= 60; ++halve) {
       orc_eval_p(p + step, a, b, K, D, du, dZ, L, R, 1, &trial);
-      if (orc_tau_positive(&trial)) { ok = 1; break; }
+      if (orc_tau_positive(&trial)) { ok = 1; halved = halve; break; }
       step = 0.5 * step;
     }
     if (!ok) break;
+    o->halvings += halved;
     p = p + step;
     e = trial;
-    if (fabs(step) <= P->newton_tol * p) { converged = 1; break; }
+    /* only a full Newton step measures the distance to the root: a step
+     * shortened to keep the tau_k positive is small because the iterate sits
+     * at the edge of the admissible set, not because F is small there */
+    if (!halved && fabs(step) <= P->newton_tol * p) { converged = 1; break; }
   }
-  o->iters = it;
-  if (!converged || !orc_tau_positive(&e)) {
-    o->status = ORC_ERR_RIEMANN;
-    return ORC_ERR_RIEMANN;
-  }
+  o->iters += it;
+  if (!converged || !orc_tau_positive(&e)) return ORC_ERR_RIEMANN;
 
   double a2 = a * a;
   /* states L, W1, W2, W3, W4, R in (tau, u, v, Z, Pi, Omega) */
@@ -426,14 +419,41 @@ static int orc_solve(const orc_params* P, const orc_cell* L, const orc_cell* R, 
   return ORC_OK;
 }
 
-/* Max of |lambda1|, |lambda5| at one interface (reading R5); the celerity a
- * is the one the solver would use there. */
-static double orc_interface_speed(const orc_params* P, const orc_cell* L, const orc_cell* R) {
+/* Solve one interface.  L, R projected cells; Lc, Rc their conserved states
+ * (H, H un, H ut, Z).  Fills o (states, speeds, fluctuations).  Celerities
+ * of reading R1; where they admit no solution with positive tau_k, a is
+ * doubled and the problem solved again, at most ORC_A_RETRIES times
+ * (reading R12). */
+#define ORC_A_RETRIES 3
+static int orc_solve(const orc_params* P, const orc_cell* L, const orc_cell* R, const double Lc[4],
+                     const double Rc[4], orc_riemann_out* o) {
+  memset(o, 0, sizeof(*o));
+  o->status = ORC_OK;
   double a, b;
-  orc_celerities(P, L, R, &a, &b);
-  double l1 = fabs(L->un - a * L->tau);
-  double l5 = fabs(R->un + a * R->tau);
-  return l1 > l5 ? l1 : l5;
+  o->raised = orc_celerities(P, L, R, &a, &b);
+
+  /* reading R3: identical states */
+  if (Lc[0] == Rc[0] && Lc[1] == Rc[1] && Lc[2] == Rc[2] && Lc[3] == Rc[3]) {
+    o->a = a; o->b = b; o->K = (a * a - b * b) / (2.0 * P->g);
+    o->lam[0] = L->un - a * L->tau;
+    o->lam[1] = L->un - b * L->tau;
+    o->lam[2] = L->un;
+    o->lam[3] = L->un + b * L->tau;
+    o->lam[4] = R->un + a * R->tau;
+    for (int k = 0; k < 6; ++k) {
+      o->tau[k] = L->tau; o->u[k] = L->un; o->v[k] = L->ut; o->Z[k] = L->Z; o->Pi[k] = L->Pi; o->Om[k] = L->Om;
+    }
+    return ORC_OK;
+  }
+  for (;;) {
+    if (orc_solve_at(P, L, R, Lc, Rc, a, b, o) == ORC_OK) return ORC_OK;
+    if (o->retries == ORC_A_RETRIES) {
+      o->status = ORC_ERR_RIEMANN;
+      return ORC_ERR_RIEMANN;
+    }
+    a = 2.0 * a;
+    o->retries += 1;
+  }
 }
 
 /* ---- ghost cells (reading R7) ------------------------------------------ */
@@ -575,39 +595,10 @@ static void orc_conserved(const orc_ext* X, int i, int j, int ydir, double c[4])
 static double orc_dx(const orc_params* P) { return P->lx / P->nx; }
 static double orc_dy(const orc_params* P) { return (P->dim == 2) ? P->ly / P->ny : 1.0; }
 
-/* Extreme wave speeds over the interfaces of a padded block (reading R5). */
-static void orc_ext_speeds(const orc_params* P, const orc_ext* X, double* Sx_out, double* Sy_out) {
-  int nx = X->nx, ny = X->ny;
-  double Sx = 0.0, Sy = 0.0;
-  for (int j = 0; j < ny; ++j)
-    for (int i = 0; i <= nx; ++i) {
-      orc_cell L = orc_project_dir(P, X, i - 1, j, 0);
-      orc_cell R = orc_project_dir(P, X, i, j, 0);
-      double s = orc_interface_speed(P, &L, &R);
-      if (s > Sx) Sx = s;
-    }
-  if (P->dim == 2)
-    for (int j = 0; j <= ny; ++j)
-      for (int i = 0; i < nx; ++i) {
-        orc_cell L = orc_project_dir(P, X, i, j - 1, 1);
-        orc_cell R = orc_project_dir(P, X, i, j, 1);
-        double s = orc_interface_speed(P, &L, &R);
-        if (s > Sy) Sy = s;
-      }
-  *Sx_out = Sx;
-  *Sy_out = Sy;
-}
-
 /* CFL time step from the extreme speeds (reading R5). */
 static double orc_dt_of_speeds(const orc_params* P, double Sx, double Sy) {
   if (P->dim == 1) return P->cfl * orc_dx(P) / Sx;
   return P->cfl / (Sx / orc_dx(P) + Sy / orc_dy(P));
-}
-
-static double orc_cfl_dt(const orc_params* P, const orc_ext* X) {
-  double Sx, Sy;
-  orc_ext_speeds(P, X, &Sx, &Sy);
-  return orc_dt_of_speeds(P, Sx, Sy);
 }
 
 /* Validity of a padded state (interior and ghosts, corners excepted). */
@@ -624,14 +615,18 @@ static int orc_ext_check(const orc_params* P, const orc_ext* X) {
   return ORC_OK;
 }
 
-/* The update of Sec. 3 on a padded block whose ghosts are filled: one
- * Riemann solve per interface, Godunov average of the interior cells in
- * fluctuation form, then friction; the interior of X is overwritten. */
-static int orc_ext_advance(const orc_params* P, orc_ext* X, double dt, double* work /* 4 nx ny */) {
+/* The Riemann problems of Sec. 3 on a padded block whose ghosts are
+ * filled: one solve per interface; acc[4 c + comp] receives the cell's net
+ * fluctuation (A+ of its left / lower interface + A- of its right / upper
+ * one, over dx, dy; comp = H, Hu, Hv, Z) and (Sx, Sy) the extreme wave
+ * speeds max(|lambda1|, |lambda5|) of the x and y solves (reading R5, with
+ * the celerity a each solve used). */
+static int orc_ext_solve(const orc_params* P, const orc_ext* X, double* acc /* 4 nx ny */, double* Sx_out,
+                         double* Sy_out) {
   int nx = X->nx, ny = X->ny;
   double dx = orc_dx(P);
   double dy = orc_dy(P);
-  double* acc = work; /* acc[4*c + comp], comp = H, Hu, Hv, Z */
+  double Sx = 0.0, Sy = 0.0;
   memset(acc, 0, sizeof(double) * 4 * (size_t)nx * ny);
   orc_riemann_out o;
   /* x-interfaces i - 1/2, i = 0..nx */
@@ -644,6 +639,9 @@ static int orc_ext_advance(const orc_params* P, orc_ext* X, double dt, double* w
       orc_conserved(X, i, j, 0, Rc);
       int st = orc_solve(P, &L, &R, Lc, Rc, &o);
       if (st) return st;
+      double l1 = fabs(o.lam[0]), l5 = fabs(o.lam[4]);
+      double sp = l1 > l5 ? l1 : l5;
+      if (sp > Sx) Sx = sp;
       /* A- goes to the left cell, A+ to the right cell; (H, Hu, Hv, Z) */
       if (i - 1 >= 0) {
         double* a = acc + 4 * ((size_t)j * nx + (i - 1));
@@ -665,6 +663,9 @@ static int orc_ext_advance(const orc_params* P, orc_ext* X, double dt, double* w
         orc_conserved(X, i, j, 1, Rc);
         int st = orc_solve(P, &L, &R, Lc, Rc, &o);
         if (st) return st;
+        double l1 = fabs(o.lam[0]), l5 = fabs(o.lam[4]);
+        double sp = l1 > l5 ? l1 : l5;
+        if (sp > Sy) Sy = sp;
         /* back to (H, Hu, Hv, Z): comp 1 is Hv (normal), comp 2 is Hu */
         if (j - 1 >= 0) {
           double* a = acc + 4 * ((size_t)(j - 1) * nx + i);
@@ -676,7 +677,16 @@ static int orc_ext_advance(const orc_params* P, orc_ext* X, double dt, double* w
         }
       }
   }
-  /* forward Euler, then friction */
+  *Sx_out = Sx;
+  *Sy_out = Sy;
+  return ORC_OK;
+}
+
+/* The Godunov average of Sec. 3 in fluctuation form (forward Euler with the
+ * net fluctuations acc of orc_ext_solve), then friction; the interior of X
+ * is overwritten. */
+static int orc_ext_update(const orc_params* P, orc_ext* X, double dt, const double* acc) {
+  int nx = X->nx, ny = X->ny;
   for (int j = 0; j < ny; ++j)
     for (int i = 0; i < nx; ++i) {
       size_t c = (size_t)j * nx + i;
@@ -705,10 +715,13 @@ static int orc_step(const orc_params* P, orc_ext* X, double dt_fixed, double* h,
   orc_fill(P, X, h, hu, hv, z);
   int st = orc_ext_check(P, X);
   if (st) return st;
-  double dt = dt_fixed > 0.0 ? dt_fixed : orc_cfl_dt(P, X);
+  double Sx, Sy;
+  st = orc_ext_solve(P, X, work, &Sx, &Sy);
+  if (st) return st;
+  double dt = dt_fixed > 0.0 ? dt_fixed : orc_dt_of_speeds(P, Sx, Sy);
   if (!(dt > 0.0) || !isfinite(dt)) return ORC_ERR_DT;
   *dt_used = dt;
-  st = orc_ext_advance(P, X, dt, work);
+  st = orc_ext_update(P, X, dt, work);
   if (st) return st;
   for (int j = 0; j < ny; ++j)
     for (int i = 0; i < nx; ++i) {
@@ -775,9 +788,14 @@ int orc_cfl(const orc_params* P, const double* h, const double* hu, const double
   orc_ext X;
   if (orc_ext_alloc(&X, P->nx, P->ny)) { orc_ext_free(&X); return ORC_ERR_ARG; }
   orc_fill(P, &X, h, hu, P->dim == 2 ? hv : NULL, z);
-  *dt_out = orc_cfl_dt(P, &X);
+  double* acc = malloc(sizeof(double) * 4 * (size_t)P->nx * P->ny);
+  if (!acc) { orc_ext_free(&X); return ORC_ERR_ARG; }
+  double Sx, Sy;
+  st = orc_ext_solve(P, &X, acc, &Sx, &Sy);
+  if (!st) *dt_out = orc_dt_of_speeds(P, Sx, Sy);
+  free(acc);
   orc_ext_free(&X);
-  return ORC_OK;
+  return st;
 }
 
 /* nsteps steps in place.  dts: NULL for CFL steps, else the fixed step of
@@ -859,15 +877,17 @@ int orc_block_ghost(const orc_params* P, int nxl, int nyl, double* H, double* Hu
   return ORC_OK;
 }
 
-/* Extreme wave speeds (S[0] x, S[1] y) over the block's interfaces. */
-int orc_block_speeds(const orc_params* P, int nxl, int nyl, double* H, double* Hu, double* Hv, double* Z,
-                     double* S) {
-  if (!P || !S || nxl < 1 || nyl < 1) return ORC_ERR_ARG;
+/* One solve per interface of the block (ghosts filled by the caller): the
+ * net fluctuation of each interior cell into work (4 nxl nyl doubles, owned
+ * by the caller, read by orc_block_update) and the extreme wave speeds
+ * (S[0] x, S[1] y) of the block's solves. */
+int orc_block_solve(const orc_params* P, int nxl, int nyl, double* H, double* Hu, double* Hv, double* Z,
+                    double* work, double* S) {
+  if (!P || !S || !work || nxl < 1 || nyl < 1) return ORC_ERR_ARG;
   orc_ext X = orc_block_view(nxl, nyl, H, Hu, Hv, Z);
   int st = orc_ext_check(P, &X);
   if (st) return st;
-  orc_ext_speeds(P, &X, &S[0], &S[1]);
-  return ORC_OK;
+  return orc_ext_solve(P, &X, work, &S[0], &S[1]);
 }
 
 /* CFL step of the whole grid from its extreme speeds. */
@@ -877,15 +897,11 @@ int orc_block_dt(const orc_params* P, double Sx, double Sy, double* dt) {
   return (*dt > 0.0 && isfinite(*dt)) ? ORC_OK : ORC_ERR_DT;
 }
 
-/* One step of size dt on the block's interior (ghosts filled by the caller). */
-int orc_block_advance(const orc_params* P, int nxl, int nyl, double* H, double* Hu, double* Hv, double* Z,
-                      double dt) {
-  if (!P || nxl < 1 || nyl < 1 || !(dt > 0.0)) return ORC_ERR_ARG;
+/* One step of size dt on the block's interior from the net fluctuations
+ * orc_block_solve left in work for the same state. */
+int orc_block_update(const orc_params* P, int nxl, int nyl, double* H, double* Hu, double* Hv, double* Z,
+                     const double* work, double dt) {
+  if (!P || !work || nxl < 1 || nyl < 1 || !(dt > 0.0)) return ORC_ERR_ARG;
   orc_ext X = orc_block_view(nxl, nyl, H, Hu, Hv, Z);
-  double* work = malloc(sizeof(double) * 4 * (size_t)nxl * nyl);
-  if (!work) return ORC_ERR_ARG;
-  int st = orc_ext_check(P, &X);
-  if (!st) st = orc_ext_advance(P, &X, dt, work);
-  free(work);
-  return st;
+  return orc_ext_update(P, &X, dt, work);
 }

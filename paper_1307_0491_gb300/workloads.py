@@ -245,6 +245,32 @@ def thin_dam_break(nx: int = 200, h_thin: float = 1e-3) -> dict:
     return dict(params=params, h=h, hu=np.zeros(nx), hv=None, z=z, nsteps=None)
 
 
+def colliding_streams(nx: int = 200, dim: int = 1, ny: int = 1, h0: float = 0.1, u0: float = 3.0,
+                      A_g: float = 1e-2, m_g: float = 3.0, ymod: float = 0.0) -> dict:
+    """Two supercritical streams (depth h0, speeds +u0 and -u0, Froude
+    u0 / sqrt(g h0)) meeting at the middle of a 10 m walled channel over a
+    flat mobile bed (Grass law): the strong compression where the
+    relaxation solver halves Newton steps and, at the first steps, needs
+    celerities above its default bounds.  In 2D the depth varies across the
+    channel by the relative amplitude ymod (one sine period over ly), walls
+    on all sides."""
+    L = 10.0
+    x = _centers(nx, L)
+    if dim == 1:
+        h = np.full(nx, h0)
+        hu = np.where(x < 0.5 * L, h0 * u0, -h0 * u0)
+        params = base_params(dim=1, nx=nx, ny=1, lx=L, A_g=A_g, m_g=m_g, bc=("wall", "wall", "free", "free"))
+        return dict(params=params, h=h, hu=hu, hv=None, z=np.zeros(nx), nsteps=None)
+    ly = L * ny / nx
+    y = _centers(ny, ly)
+    X, Y = np.meshgrid(x, y)
+    h = h0 * (1.0 + ymod * np.sin(2.0 * np.pi * Y / ly))
+    hu = np.where(X < 0.5 * L, 1.0, -1.0) * h * u0
+    params = base_params(dim=2, nx=nx, ny=ny, lx=L, ly=ly, A_g=A_g, m_g=m_g,
+                         bc=("wall", "wall", "wall", "wall"))
+    return dict(params=params, h=h, hu=hu, hv=np.zeros_like(h), z=np.zeros_like(h), nsteps=None)
+
+
 def random_smooth(nx: int, ny: int, seed: int, dim: int = 2, bc=("periodic", "periodic", "periodic", "periodic"),
                   **kw) -> dict:
     """Smooth random state (h in [0.8, 1.2], |u| < 0.5, z in [0, 0.2]) as a

@@ -130,10 +130,14 @@ def suliciu_fluct(p: dict, L, R):
 # ---------------------------------------------------------------------------
 # 50-digit solve of the relaxation Riemann problem
 
-def mp_riemann(p: dict, L, R, dps: int = 50):
+def mp_riemann(p: dict, L, R, dps: int = 50, start=None, ab=None):
     """Relaxation Riemann problem as four contact conditions in the four
     unknown specific volumes (tau1..tau4), every other quantity written from
     the Riemann invariants of the a- and b-waves (Eqs. relaxh--relaxqs).
+    The multidimensional root search starts from (tauL, tauL, tauR, tauR),
+    or from ``start`` (four specific volumes) where the system has several
+    roots and the one near a given point is wanted.  The celerities are those
+    of reading R1, or ``ab`` = (a, b) where a solve used others.
     Returns dict(lam[5], U[6][4], a, b) in mpmath numbers."""
     import mpmath as mp
 
@@ -143,7 +147,7 @@ def mp_riemann(p: dict, L, R, dps: int = 50):
     q["g"] = g
     L = [mp.mpf(x) for x in L]
     R = [mp.mpf(x) for x in R]
-    a, b = celerities(q, L, R, lib=mp)
+    a, b = celerities(q, L, R, lib=mp) if ab is None else (mp.mpf(ab[0]), mp.mpf(ab[1]))
     K = (a * a - b * b) / (2 * g)
     HL, HR = L[0], R[0]
     tL, tR = 1 / HL, 1 / HR
@@ -176,7 +180,8 @@ def mp_riemann(p: dict, L, R, dps: int = 50):
     if list(L) == list(R):
         sol = [tL, tL, tR, tR]
     else:
-        sol = mp.findroot(eqs, (tL, tL, tR, tR), tol=mp.mpf(10) ** (-(dps - 8)), maxsteps=200)
+        x0 = (tL, tL, tR, tR) if start is None else tuple(mp.mpf(x) for x in start)
+        sol = mp.findroot(eqs, x0, tol=mp.mpf(10) ** (-(dps - 8)), maxsteps=200)
         sol = [sol[i] for i in range(4)]
     t1, t2, t3, t4 = sol
     u1, u2, u3, u4, P2, P3, Z2, Z3, l2, l4, O2, O3 = states(t1, t2, t3, t4)
@@ -193,10 +198,10 @@ def mp_riemann(p: dict, L, R, dps: int = 50):
     return dict(lam=lam, U=U, a=a, b=b, tau=taus)
 
 
-def mp_fluct(p: dict, L, R, dps: int = 50):
+def mp_fluct(p: dict, L, R, dps: int = 50, start=None, ab=None):
     import mpmath as mp
 
-    r = mp_riemann(p, L, R, dps)
+    r = mp_riemann(p, L, R, dps, start, ab)
     Am = [mp.mpf(0)] * 4
     Ap = [mp.mpf(0)] * 4
     for k in range(5):

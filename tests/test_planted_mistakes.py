@@ -49,7 +49,10 @@ MUTANTS = [
     ("tangential_velocity_side", "o->v[3] = R->ut;", "o->v[3] = L->ut;"),
     ("bed_update_sign", "double Zn = X->Z[k] - dt * a[3];", "double Zn = X->Z[k] + dt * a[3];"),
     ("wall_not_mirrored", "out[normal] = -in[normal];", "out[normal] = in[normal];"),
-    ("bed_step_bound_dropped", "if (a * a < need) a = sqrt(need);", "(void)need;"),
+    ("bed_step_bound_dropped", "if (raised) a = sqrt(need);", "(void)need;"),
+    ("newton_stops_on_halved_step", "if (!halved && fabs(step) <= P->newton_tol * p)",
+     "if (fabs(step) <= P->newton_tol * p)"),
+    ("celerity_not_doubled_on_retry", "    a = 2.0 * a;\n", "    a = 1.0 * a;\n"),
 ]
 
 # pins run against each mutant: (callable, args)
@@ -66,6 +69,7 @@ PINS = [
     (pins.test_single_step_50_digit, (2,)),
     (pins.test_mass_conservation, ("walls2d",)),
     (pins.test_cfl_rule, ()),
+    (pins.test_riemann_hard_pairs_reach_a_root, ()),
 ]
 
 
