@@ -7,8 +7,14 @@
 // pay allocation latency or risk an out-of-memory failure mid-run, or in a
 // plug-in that is handed device buffers but no allocator.  Such a caller
 // passes its own device arrays for the state; every other buffer the step
-// needs (padded state, projection, fluctuations, block partials, scalars)
-// is carved out of one file-scope device array below.
+// needs (padded state, projection or net fluctuations, interface
+// fluctuations, block partials, scalars) is carved out of one file-scope
+// device array below.
+//
+// The kernels are those of the regular entry points for the configuration:
+// the two-kernel step (interface_kernel + cell_kernel) in FP64 and in 1D,
+// the fused FP32 stencil (solve_kernel + apply_kernel) for the FP32 state in
+// 2D.
 //
 // The array is a static __device__ object: it exists on every GPU that loads
 // the library, for the life of the process, whether or not this entry point
@@ -17,10 +23,18 @@
 #include <stddef.h>
 #include <string.h>
 
+#include <algorithm>
 #include <mutex>
 
 #include "../../include/sve.h"
 #include "sve_device.cuh"
+#include "sve_fused.cuh"
+
+// Parameter checks, derived constants and status codes are the ones the
+// regular entry points use (defined in sve_api.cu).
+__attribute__((visibility("hidden"))) int sve_internal_validate(const sve_config* c);
+__attribute__((visibility("hidden"))) void sve_internal_make_params(const sve_config* c, sve::DevParams* P);
+__attribute__((visibility("hidden"))) int sve_internal_status_code(int st);
 
 namespace {
 
@@ -33,10 +47,13 @@ constexpr int kDtlogEntries = 1024;  // steps per chunk (the per-step dt log liv
 
 std::mutex g_setup_mutex;
 unsigned char* g_scratch_ptr[kMaxDevices] = {};
+int g_nsm[kMaxDevices] = {};          // SMs of the device
+int g_solve_per_sm[kMaxDevices] = {};  // resident blocks of the fused solve kernel per SM
 
-// Device address of the scratch on the current device, looked up once per
-// device (with that device current).
-int scratch_address(unsigned char** out) {
+// Device address of the scratch on the current device, and the launch facts
+// the fused FP32 step needs, looked up once per device (with that device
+// current).
+int device_setup(int* dev_out) {
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return SVE_ERR_CUDA;
   if (dev < 0 || dev >= kMaxDevices) return SVE_ERR_ARG;
@@ -44,49 +61,103 @@ int scratch_address(unsigned char** out) {
   if (!g_scratch_ptr[dev]) {
     void* p = nullptr;
     if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return SVE_ERR_CUDA;
+    int nsm = 0, bs = 0;
+    if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || nsm < 1)
+      return SVE_ERR_CUDA;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bs, sve::solve_kernel<float>, sve::kFThreads, 0) !=
+            cudaSuccess ||
+        bs < 1)
+      return SVE_ERR_CUDA;
+    g_nsm[dev] = nsm;
+    g_solve_per_sm[dev] = bs;
     g_scratch_ptr[dev] = (unsigned char*)p;
   }
-  *out = g_scratch_ptr[dev];
+  *dev_out = dev;
   return SVE_OK;
 }
 
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
-// Byte layout of the scratch for one configuration (offsets from the base).
-struct Layout {
-  size_t fields[13], fx, fy, mpart, sc, dtlog, total;
+// Launch shape of one call: the two-kernel step (blocks of the interface and
+// cell kernels) or the fused FP32 stencil (solve blocks over the tiles, the
+// apply pass's 2D grid); nmpart = block partials the largest pass writes.
+struct Shape {
+  bool fused;
+  int nb_iface, nb_cell;                 // two-kernel step
+  int ntiles, tiles_x, solve_blocks;     // fused: tiles and resident solve blocks
+  int agx, agy;                          // fused: apply grid
+  size_t nmpart;
 };
 
-Layout layout_for(const sve::DevParams& P, size_t elem, int nb_cell) {
-  Layout L;
+Shape shape_for(const sve::DevParams& P, bool fused, int nsm, int solve_per_sm) {
+  Shape S = {};
+  S.fused = fused;
+  const size_t init_blocks = (size_t)sve::cell_blocks(P, sve::kThreads);
+  if (!fused) {
+    S.nb_iface = (int)sve::iface_blocks(P, sve::kThreadsStep);
+    S.nb_cell = (int)sve::cell_blocks(P, sve::kThreadsStep);
+    S.nmpart = std::max(init_blocks, (size_t)S.nb_cell);
+  } else {
+    S.tiles_x = (P.nx + sve::kFTX - 1) / sve::kFTX;
+    S.ntiles = S.tiles_x * ((P.ny + sve::kFTY - 1) / sve::kFTY);
+    S.solve_blocks = std::min(S.ntiles, nsm * solve_per_sm);
+    S.agx = (P.nx + sve::kAThreads - 1) / sve::kAThreads;
+    S.agy = std::min(P.ny, std::max(1, (nsm * (2048 / sve::kAThreads) + S.agx - 1) / S.agx));
+    S.nmpart = std::max(init_blocks, (size_t)S.agx * (size_t)S.agy);
+  }
+  return S;
+}
+
+// Byte layout of the scratch for one configuration (offsets from the base):
+// 13 padded fields (state + projection: the state upload's init_kernel
+// writes all of them), then the fluctuation planes of the two-kernel step or
+// the 4 planes of net fluctuations of the fused step.
+struct Layout {
+  size_t fields[13], fx, fy, net, mpart, sc, dtlog, total;
+};
+
+Layout layout_for(const sve::DevParams& P, size_t elem, const Shape& S) {
+  Layout L = {};
   size_t off = 0;
   const size_t next = (size_t)(P.nx + 2) * (size_t)(P.ny + 2);
   for (int k = 0; k < 13; ++k) { L.fields[k] = off; off = align256(off + elem * next); }
-  L.fx = off; off = align256(off + 8 * elem * (size_t)P.nfx);
-  L.fy = off; off = align256(off + 8 * elem * (size_t)(P.nfy > 0 ? P.nfy : 1));
-  L.mpart = off; off = align256(off + 2 * sizeof(double) * (size_t)nb_cell);
+  if (!S.fused) {
+    L.fx = off; off = align256(off + 8 * elem * (size_t)P.nfx);
+    L.fy = off; off = align256(off + 8 * elem * (size_t)(P.nfy > 0 ? P.nfy : 1));
+  } else {
+    L.net = off; off = align256(off + 4 * elem * (size_t)P.nx * (size_t)P.ny);
+  }
+  L.mpart = off; off = align256(off + 2 * sizeof(double) * S.nmpart);
   L.sc = off; off = align256(off + sizeof(sve::DevScalars));
   L.dtlog = off; off = align256(off + sizeof(double) * kDtlogEntries);
   L.total = off;
   return L;
 }
 
-int status_code(int st) {
-  if (st & sve::ST_NAN) return SVE_ERR_NAN;
-  if (st & sve::ST_NEG_DEPTH) return SVE_ERR_NEG_DEPTH;
-  if (st & sve::ST_RIEMANN) return SVE_ERR_RIEMANN;
-  if (st & sve::ST_DT) return SVE_ERR_DT;
-  return SVE_OK;
+}  // namespace
+
+namespace {
+
+// The latched device status, read after the stream's work so far (one small
+// copy and a wait).
+int read_status(const sve::DevScalars* sc, cudaStream_t st, double* t_out) {
+  sve::DevScalars host;
+  if (cudaMemcpyAsync(&host, sc, sizeof(host), cudaMemcpyDeviceToHost, st) != cudaSuccess) return SVE_ERR_CUDA;
+  if (cudaStreamSynchronize(st) != cudaSuccess) return SVE_ERR_CUDA;
+  if (t_out) *t_out = host.t;
+  return sve_internal_status_code(host.status);
 }
 
 template <typename T>
-int run(const sve::DevParams& P, unsigned char* base, const Layout& L, int nb_iface, int nb_cell, void* depth,
-        void* hu, void* hv, void* zb, int nsteps, double* t_inout, cudaStream_t st) {
-  sve::DevState<T> S;
+int run(const sve::DevParams& P, unsigned char* base, const Layout& L, const Shape& SH, void* depth, void* hu,
+        void* hv, void* zb, int nsteps, double* t_inout, cudaStream_t st) {
+  sve::DevState<T> S = {};
   T** f[13] = {&S.h, &S.hu, &S.hv, &S.z, &S.tau, &S.u, &S.v, &S.pi, &S.omx, &S.omy, &S.ca, &S.cbx, &S.cby};
   for (int k = 0; k < 13; ++k) *f[k] = (T*)(base + L.fields[k]);
-  S.fx = (T*)(base + L.fx);
-  S.fy = (T*)(base + L.fy);
+  if (!SH.fused) {
+    S.fx = (T*)(base + L.fx);
+    S.fy = (T*)(base + L.fy);
+  }
   double* mpart = (double*)(base + L.mpart);
   sve::DevScalars* sc = (sve::DevScalars*)(base + L.sc);
   double* dtlog = (double*)(base + L.dtlog);
@@ -108,36 +179,54 @@ int run(const sve::DevParams& P, unsigned char* base, const Layout& L, int nb_if
     if (cudaMemcpy2DAsync(dst, pitch, user[k], row, row, P.ny, cudaMemcpyDeviceToDevice, st) != cudaSuccess)
       return SVE_ERR_CUDA;
   }
+  // ghosts, projection (two-kernel step) and the checks of the input state;
+  // a bad input is reported before any step, the caller's arrays untouched
   sve::init_kernel<T><<<(unsigned)sve::cell_blocks(P, sve::kThreads), sve::kThreads, 0, st>>>(P, S, sc, mpart);
+  if (cudaGetLastError() != cudaSuccess) return SVE_ERR_CUDA;
+  int rc = read_status(sc, st, nullptr);
+  if (rc) return rc;
+  sve::StateBuf<T> B = {S.h, S.hu, S.hv, S.z};
+  sve::NetFluct<T> D = {};
+  if (SH.fused) {
+    const size_t ncell = (size_t)P.nx * (size_t)P.ny;
+    D.h = (T*)(base + L.net); D.hu = D.h + ncell; D.hv = D.hu + ncell; D.z = D.hv + ncell;
+  }
   for (int done = 0; done < nsteps;) {
     const int chunk = nsteps - done < kDtlogEntries ? nsteps - done : kDtlogEntries;
     if (cudaMemsetAsync(&sc->call_step, 0, sizeof(int), st) != cudaSuccess) return SVE_ERR_CUDA;
     for (int s = 0; s < chunk; ++s) {
-      sve::interface_kernel<T><<<nb_iface, sve::kThreadsStep, 0, st>>>(P, S, sc, dtlog, dtlog, 0);
-      sve::cell_kernel<T><<<nb_cell, sve::kThreadsStep, 0, st>>>(P, S, sc, mpart, sve::Mirror<T>{});
+      if constexpr (sizeof(T) == 4) {
+        if (SH.fused) {
+          sve::solve_kernel<T><<<SH.solve_blocks, sve::kFThreads, 0, st>>>(P, B, D, sc, dtlog, dtlog, 0, SH.ntiles,
+                                                                            SH.tiles_x);
+          sve::apply_kernel<T><<<dim3(SH.agx, SH.agy), sve::kAThreads, 0, st>>>(P, B, D, sc, mpart,
+                                                                                sve::Mirror<T>{});
+          continue;
+        }
+      }
+      sve::interface_kernel<T><<<SH.nb_iface, sve::kThreadsStep, 0, st>>>(P, S, sc, dtlog, dtlog, 0);
+      sve::cell_kernel<T><<<SH.nb_cell, sve::kThreadsStep, 0, st>>>(P, S, sc, mpart, sve::Mirror<T>{});
     }
     done += chunk;
   }
   if (cudaGetLastError() != cudaSuccess) return SVE_ERR_CUDA;
+  // the steps' latched status first: on an error the caller's arrays keep
+  // their input
+  double t_new = *t_inout;
+  rc = read_status(sc, st, &t_new);
+  if (rc) return rc;
   for (int k = 0; k < 4; ++k) {
     if (!user[k]) continue;
     const char* src = (const char*)*f[k] + elem * (size_t)(P.ex + 1);
     if (cudaMemcpy2DAsync(user[k], row, src, pitch, row, P.ny, cudaMemcpyDeviceToDevice, st) != cudaSuccess)
       return SVE_ERR_CUDA;
   }
-  sve::DevScalars out;
-  if (cudaMemcpyAsync(&out, sc, sizeof(out), cudaMemcpyDeviceToHost, st) != cudaSuccess) return SVE_ERR_CUDA;
   if (cudaStreamSynchronize(st) != cudaSuccess) return SVE_ERR_CUDA;
-  *t_inout = out.t;
-  return status_code(out.status);
+  *t_inout = t_new;
+  return SVE_OK;
 }
 
 }  // namespace
-
-// Parameter checks and the derived constants are the ones sve_create uses
-// (defined in sve_api.cu).
-__attribute__((visibility("hidden"))) int sve_internal_validate(const sve_config* c);
-__attribute__((visibility("hidden"))) void sve_internal_make_params(const sve_config* c, sve::DevParams* P);
 
 extern "C" int sve_step_noalloc(const sve_config* cfg, void* depth, void* hu, void* hv, void* zb, int nsteps,
                                 double* t_inout, void* stream) {
@@ -147,15 +236,16 @@ extern "C" int sve_step_noalloc(const sve_config* cfg, void* depth, void* hu, vo
   if (cfg->dim == 2 && !hv) return SVE_ERR_ARG;
   sve::DevParams P;
   sve_internal_make_params(cfg, &P);
-  const size_t elem = cfg->precision == SVE_FP64 ? 8 : 4;
-  const int nb_iface = (int)sve::iface_blocks(P, sve::kThreadsStep);
-  const int nb_cell = (int)sve::cell_blocks(P, sve::kThreadsStep);
-  const Layout L = layout_for(P, elem, nb_cell);
-  if (L.total > (size_t)SVE_NOALLOC_SCRATCH_BYTES) return SVE_ERR_NOALLOC_SIZE;
-  unsigned char* base = nullptr;
-  rc = scratch_address(&base);
+  int dev = 0;
+  rc = device_setup(&dev);
   if (rc) return rc;
+  const bool fused = cfg->precision == SVE_FP32 && cfg->dim == 2;
+  const Shape SH = shape_for(P, fused, g_nsm[dev], g_solve_per_sm[dev]);
+  const size_t elem = cfg->precision == SVE_FP64 ? 8 : 4;
+  const Layout L = layout_for(P, elem, SH);
+  if (L.total > (size_t)SVE_NOALLOC_SCRATCH_BYTES) return SVE_ERR_NOALLOC_SIZE;
+  unsigned char* base = g_scratch_ptr[dev];
   cudaStream_t st = (cudaStream_t)stream;
-  if (cfg->precision == SVE_FP64) return run<double>(P, base, L, nb_iface, nb_cell, depth, hu, hv, zb, nsteps, t_inout, st);
-  return run<float>(P, base, L, nb_iface, nb_cell, depth, hu, hv, zb, nsteps, t_inout, st);
+  if (cfg->precision == SVE_FP64) return run<double>(P, base, L, SH, depth, hu, hv, zb, nsteps, t_inout, st);
+  return run<float>(P, base, L, SH, depth, hu, hv, zb, nsteps, t_inout, st);
 }

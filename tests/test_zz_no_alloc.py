@@ -73,6 +73,52 @@ def test_noalloc_matches_regular_entry_points_twice(dim):
     ref.close()
 
 
+def test_noalloc_fp32_2d_matches_regular_entry_points_twice():
+    """The FP32 state in 2D: the no-allocation call runs the fused stencil of
+    the regular FP32 handle with the same launch shape, so both give the
+    same state to FP32 rounding, on two calls in a row."""
+    import torch
+
+    w = W.antidune2d(nx=200, ny=96, seed=3)
+    p = w["params"]
+    cfg = sve.config_from_params(p, "fp32")
+    names = ("h", "hu", "hv", "z")
+    dev = {k: torch.tensor(np.asarray(w[k]), dtype=torch.float32, device="cuda").contiguous() for k in names}
+    ref = sve.Solver(p, "fp32")
+    ref.set_state(*(np.asarray(w[k], np.float32) for k in names))
+    t = 0.0
+    for call, n in enumerate((30, 17)):
+        rc, t = sve.sve_step_noalloc(cfg, *(dev[k].data_ptr() for k in names), n, t)
+        assert rc == sve.SVE_OK, sve.sve_strerror(rc)
+        t_ref = ref.step(n)
+        exp = ref.get_state()
+        qscale = max(np.max(np.abs(exp["hu"])), np.max(np.abs(exp["hv"])))
+        for k in names:
+            scale = qscale if k in ("hu", "hv") else max(np.max(np.abs(exp[k])), 1e-12)
+            assert _rel(dev[k].cpu().numpy(), exp[k], scale) <= 1e-6, (call, k)
+        assert abs(t - t_ref) <= 1e-12 * t_ref, (call, t, t_ref)
+    ref.close()
+
+
+def test_noalloc_bad_input_leaves_arrays_untouched():
+    """A non-finite input is reported by the device checks before any step,
+    and the caller's arrays and time keep their values."""
+    import torch
+
+    w = W.dune2d(nx=64, ny=32, seed=2, lx=64.0, ly=32.0)
+    cfg = sve.config_from_params(w["params"], "fp64")
+    dev = {k: torch.tensor(w[k], dtype=torch.float64, device="cuda") for k in ("h", "hu", "hv", "z")}
+    dev["hu"][5, 7] = float("nan")
+    before = {k: v.clone() for k, v in dev.items()}
+    rc, t = sve.sve_step_noalloc(cfg, dev["h"].data_ptr(), dev["hu"].data_ptr(), dev["hv"].data_ptr(),
+                                 dev["z"].data_ptr(), 5, 1.5)
+    assert rc == sve.SVE_ERR_NAN, sve.sve_strerror(rc)
+    assert t == 1.5
+    for k in ("h", "hv", "z"):
+        assert torch.equal(before[k], dev[k]), k
+    assert torch.equal(torch.isnan(before["hu"]), torch.isnan(dev["hu"]))
+
+
 def test_noalloc_rejects_grid_beyond_scratch():
     import torch
 
