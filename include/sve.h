@@ -217,6 +217,25 @@ int sve_profile_read(sve_handle* h, double* ms, long long* launches);
  * Blocks; returns the latched device status. */
 int sve_get_counters(sve_handle* h, long long* steps, unsigned long long* newton_iters);
 
+/* Safeguards of the Riemann solves taken since the last sve_set_state,
+ * summed over all interfaces and steps (Sec. 3: the relaxation solver is
+ * well defined for celerities that satisfy the bounds of Eq. (ab), and
+ * stronger bounds may be needed):
+ *   halvings  Newton steps of the scalar equation in p = tau1 + tau4 that
+ *             were halved because the full step made a specific volume
+ *             tau_k non-positive (each halving counts one; a halved step
+ *             never ends the iteration);
+ *   raised    solves whose celerity a was raised by the bed-jump bound
+ *             a^2 >= b^2 + 2 g gamma_z |dzb| hmax^2;
+ *   retries   doublings of a in solves whose celerities admitted no
+ *             solution with positive tau_k (at most 3 per solve; the
+ *             solve's wave speeds, and so the CFL step, use the final a;
+ *             past the third the step latches SVE_ERR_RIEMANN).
+ * Any pointer may be NULL.  Blocks; returns the latched device status
+ * (SVE_ERR_STATE without a state, SVE_ERR_ARG for a NULL handle). */
+int sve_get_safeguards(sve_handle* h, unsigned long long* halvings, unsigned long long* raised,
+                       unsigned long long* retries);
+
 /* ---- launch shape of the two-kernel step -------------------------------------
  * Threads per block of the step's two kernels (interface kernel, cell
  * kernel): 128 (measured fastest on large grids), 256, or 32 (one warp per
@@ -342,30 +361,42 @@ int sve_adjoint(sve_handle* h, const void* lam_h, const void* lam_hu, const void
  * must not pay allocation latency or fail for lack of memory mid-run, and
  * plug-ins that are handed device buffers but no allocator.
  *
- * sve_step_noalloc advances the caller's state by nsteps CFL steps (the same
- * kernels and arithmetic as sve_create + sve_set_state + sve_step).  The
- * caller passes its state as device arrays (depth, hu, hv, zb: nx*ny values
- * of the configured precision, row-major [ny][nx], hv NULL in 1D), updated
- * in place, and the simulated time in *t_inout (host; read, then
- * overwritten with the time after the steps).  stream: a cudaStream_t or
- * NULL (legacy default stream).  Blocks until the steps are done.
+ * sve_step_noalloc advances the caller's state by nsteps CFL steps with the
+ * kernels and arithmetic of sve_create + sve_set_state + sve_step for the
+ * same configuration: the two-kernel step in FP64 and in 1D, the fused
+ * shared-memory stencil for the FP32 state in 2D (128-thread blocks for the
+ * two-kernel step at every grid size, so the mass sums may be added in
+ * another order than a small grid's regular handle adds them).  The caller
+ * passes its state as device arrays (depth, hu, hv, zb: nx*ny values of the
+ * configured precision, row-major [ny][nx], hv NULL in 1D), updated in
+ * place, and the simulated time in *t_inout (host; read, then overwritten
+ * with the time after the steps).  stream: a cudaStream_t or NULL (legacy
+ * default stream).  The call is host-synchronous: it waits for the input
+ * checks, for the steps and for the copy back, reading the device status
+ * after each.
  *
- * No memory is allocated: every other buffer (padded state, projection,
- * fluctuations, block partials, scalars) lives in one file-scope device
- * array of SVE_NOALLOC_SCRATCH_BYTES that every GPU loading the library
- * holds until the process exits.  A configuration whose buffers do not fit
- * returns SVE_ERR_NOALLOC_SIZE without touching the state; in FP64 a step
- * needs about 232 bytes per cell (13 padded fields + 8 fluctuation planes
- * per interface), so grids up to about 36 000 cells fit (e.g. 180 x 180).
+ * No memory is allocated: every other buffer (padded state and projection,
+ * fluctuations or net fluctuations, block partials, scalars) lives in one
+ * file-scope device array of SVE_NOALLOC_SCRATCH_BYTES that every GPU
+ * loading the library holds until the process exits.  A configuration
+ * whose buffers do not fit returns SVE_ERR_NOALLOC_SIZE without touching
+ * the state: in FP64 a step needs about 232 bytes per cell (13 padded
+ * fields + 8 fluctuation planes per interface), so grids up to about
+ * 36 000 cells fit (e.g. 180 x 180); the 2D FP32 state about 68 bytes per
+ * cell (about 120 000 cells, e.g. 340 x 340).
  *
  * The first call on a device looks up the device address of the array
- * (cudaGetSymbolAddress, with that device current); make that first call
- * before any stream capture.  All calls share the array and it keeps the
- * previous call's contents (each call clears what must start at zero): two
- * calls that overlap on the GPU -- on different streams or devices' threads
- * sharing one device -- race on it and must be serialised by the caller.
- * Errors: SVE_ERR_ARG (bad config or pointers), SVE_ERR_NOALLOC_SIZE, the
- * latched device errors of the steps, SVE_ERR_CUDA. */
+ * (cudaGetSymbolAddress, with that device current) and the fused step's
+ * launch shape; make that first call before any stream capture.  All calls
+ * share the array and it keeps the previous call's contents (each call
+ * clears what must start at zero): two calls that overlap on the GPU -- on
+ * different streams or devices' threads sharing one device -- race on it and
+ * must be serialised by the caller.
+ * Errors: SVE_ERR_ARG (bad config or pointers), SVE_ERR_NOALLOC_SIZE,
+ * SVE_ERR_CUDA, the device errors of the input checks (SVE_ERR_NAN,
+ * SVE_ERR_NEG_DEPTH: returned before any step) and of the steps (the first
+ * latched one).  On any error the caller's arrays and *t_inout keep their
+ * input values. */
 #define SVE_NOALLOC_SCRATCH_BYTES (8u << 20)
 int sve_step_noalloc(const sve_config* cfg, void* depth, void* hu, void* hv, void* zb, int nsteps, double* t_inout,
                      void* stream);

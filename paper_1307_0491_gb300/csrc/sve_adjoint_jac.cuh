@@ -12,7 +12,8 @@
 //                   the implicit function theorem: the cotangent of p*,
 //                   pbar, becomes Fbar = -pbar / F_p on F at fixed p);
 //   jac_pass        forward mode with dual numbers through the same
-//                   templates the step uses (two passes of five directions):
+//                   templates the step uses (two passes of five directions,
+//                   given the root and the doublings of a the solve made):
 //                   the reference the reverse mode is tested against.
 // Branches (max of the celerity bounds, signs of the wave speeds) follow the
 // values, as in the step.
@@ -58,7 +59,7 @@ __device__ __forceinline__ Cell<T> project_grass(const DevParams& P, T H, T Hn, 
 template <int PASS>
 __device__ __forceinline__ void jac_pass(const DevParams& P, const double u[8], double A, double m, double pstar,
                                          double Fp, const double muL[4], const double muR[4], double w,
-                                         double out[10]) {
+                                         double out[10], int retries = 0) {
   using D = Dual<5>;
   D x[10];
 #pragma unroll
@@ -72,6 +73,7 @@ __device__ __forceinline__ void jac_pass(const DevParams& P, const double u[8], 
   const Cell<D> R = project_grass(P, x[4], x[5], x[6], x[7], x[8], x[9]);
   D a, b;
   celerities(P, L, R, a, b);
+  for (int k = 0; k < retries; ++k) a = D(2.0) * a;  // doublings of the step's solve
   NewtonConst<D> c;
   newton_setup(P, L, R, a, b, c);
   NewtonEval<D> e;
@@ -432,14 +434,23 @@ __device__ __forceinline__ bool interface_vjp(const DevParams& P, const double u
   const double need = b * b + 2.0 * g * P.gamma_z * adZ * (Hmax * Hmax);
   const bool step = a * a < need;
   if (step) a = sqrt(need);
+  // the root as the step finds it: the same iterates, and a doubled where
+  // the celerities admit no root with positive tau_k (riemann_retry)
   NewtonConst<double> c;
-  double ip0;
-  double pstar = newton_setup(P, L, R, a, b, c, &ip0);  // as the step: the same iterates
+  double pstar;
   NewtonEval<double> e;
-  newton_eval_ip(pstar, ip0, c, L, R, e);
-  int its = 0;
-  if (!newton_loop(c, L, R, pstar, e, P.newton_maxit, fmax(P.newton_tol, 16.0 * 2.220446049250313e-16), its))
-    return false;
+  int retries = 0;
+  for (;; ++retries) {
+    double ip0;
+    pstar = newton_setup(P, L, R, a, b, c, &ip0);
+    newton_eval_ip(pstar, ip0, c, L, R, e);
+    int its = 0;
+    if (newton_loop(c, L, R, pstar, e, P.newton_maxit, fmax(P.newton_tol, 16.0 * 2.220446049250313e-16), its) &&
+        newton_positive(e))
+      break;
+    if (retries == kARetries) return false;
+    a = 2.0 * a;
+  }
   const double Fp = newton_deriv(c, e);
   newton_eval(pstar, c, L, R, e);  // the states at the root, by a full evaluation
   // fan (as fan_fluctuations, keeping the branches)
@@ -560,10 +571,14 @@ __device__ __forceinline__ bool interface_vjp(const DevParams& P, const double u
   Rb.tau += cb.C0 * a;
   Rb.Z += cb.dZ;
   Lb.Z -= cb.dZ;
+  // a = 2^retries times the celerity of the bounds: back to the latter
+  const double a_scale = (double)(1 << retries);
+  ab *= a_scale;
+  const double inv_a_bound = c.inv_a * a_scale;
   // celerities, along the branches taken
   double a0b = 0.0, b0b = 0.0;
   if (step) {
-    const double needb = ab * 0.5 * c.inv_a;
+    const double needb = ab * 0.5 * inv_a_bound;
     bb += needb * 2.0 * b;
     const double sgn = dZ < 0.0 ? -1.0 : 1.0;
     const double dZb = needb * 2.0 * g * P.gamma_z * (Hmax * Hmax) * sgn;

@@ -444,6 +444,7 @@ __attribute__((visibility("hidden"))) int sve_internal_reserve_dtlog(sve_handle*
 __attribute__((visibility("hidden"))) void sve_internal_make_params(const sve_config* c, DevParams* P) {
   make_params(c, P);
 }
+__attribute__((visibility("hidden"))) int sve_internal_status_code(int st) { return status_to_code(st); }
 
 extern "C" {
 
@@ -842,6 +843,19 @@ int sve_get_counters(sve_handle* h, long long* steps, unsigned long long* newton
   SVE_TRY(cudaStreamSynchronize(h->stream));
   if (steps) *steps = s.steps;
   if (newton_iters) *newton_iters = s.newton_iters;
+  return status_to_code(s.status);
+}
+
+int sve_get_safeguards(sve_handle* h, unsigned long long* halvings, unsigned long long* raised,
+                       unsigned long long* retries) {
+  if (!h) return SVE_ERR_ARG;
+  if (!h->has_state) return SVE_ERR_STATE;
+  DevScalars s;
+  SVE_TRY(cudaMemcpyAsync(&s, h->sc, sizeof(s), cudaMemcpyDeviceToHost, h->stream));
+  SVE_TRY(cudaStreamSynchronize(h->stream));
+  if (halvings) *halvings = s.halvings;
+  if (raised) *raised = s.raised;
+  if (retries) *retries = s.retries;
   return status_to_code(s.status);
 }
 

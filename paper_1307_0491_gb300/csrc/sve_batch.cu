@@ -55,19 +55,19 @@ __global__ void __launch_bounds__(NT, sve::iface_min_blocks<NT>::value)
   __shared__ BatchRun<T> R;
   // block tallies: maximal x / y speed (bit patterns), Newton updates, warps done
   __shared__ unsigned long long s_bits[2];
-  __shared__ unsigned int s_its, s_warps;
+  __shared__ unsigned int s_its, s_warps, s_halv, s_raised, s_retry;
   const int2 t = tiles[blockIdx.x];
-  if (threadIdx.x == 0) { s_bits[0] = 0ull; s_bits[1] = 0ull; s_its = 0u; s_warps = 0u; }
+  if (threadIdx.x == 0) { s_bits[0] = 0ull; s_bits[1] = 0ull; s_its = 0u; s_warps = 0u; s_halv = 0u; s_raised = 0u; s_retry = 0u; }
   load_run(runs, t.x, &R);  // ends with a barrier
   const DevParams& P = R.P;
   const long long item = (long long)t.y * NT + threadIdx.x;
   double sx = 0.0, sy = 0.0;
-  int iters = 0;
+  int iters = 0, branch = 0;
   bool fail = false;
   if (item < P.nfx) {
-    fail = !sve::interface_item(P, R.S, false, item, sx, iters);
+    fail = !sve::interface_item(P, R.S, false, item, sx, iters, branch);
   } else if (item < P.nfx + P.nfy) {
-    fail = !sve::interface_item(P, R.S, true, item - P.nfx, sy, iters);
+    fail = !sve::interface_item(P, R.S, true, item - P.nfx, sy, iters, branch);
   }
   if (fail) atomicOr(&sc[t.x].status, sve::ST_RIEMANN);
   // as in interface_kernel: warp shuffles, shared-memory atomics, no block
@@ -82,15 +82,27 @@ __global__ void __launch_bounds__(NT, sve::iface_min_blocks<NT>::value)
     by = oy > by ? oy : by;
     iters += __shfl_xor_sync(0xffffffffu, iters, o);
   }
+  const unsigned wb = __reduce_or_sync(0xffffffffu, (unsigned)branch);
+  unsigned wr = 0u, wt = 0u, wh = 0u;
+  if (wb) {
+    wr = __reduce_add_sync(0xffffffffu, sve::branch_raised(branch));
+    wt = __reduce_add_sync(0xffffffffu, sve::branch_retries(branch));
+    wh = __reduce_add_sync(0xffffffffu, sve::branch_halvings(branch));
+  }
   if ((threadIdx.x & 31) != 0) return;
   atomicMax(&s_bits[0], (unsigned long long)bx);
   atomicMax(&s_bits[1], (unsigned long long)by);
   atomicAdd(&s_its, (unsigned int)iters);
+  if (wb) { atomicAdd(&s_raised, wr); atomicAdd(&s_retry, wt); atomicAdd(&s_halv, wh); }
   __threadfence_block();
   if (atomicAdd(&s_warps, 1u) != NT / 32 - 1) return;
   __threadfence_block();
   DevScalars& S = sc[t.x];
   atomicAdd(&S.newton_iters, (unsigned long long)atomicAdd(&s_its, 0u));
+  const unsigned br = atomicAdd(&s_raised, 0u), bt = atomicAdd(&s_retry, 0u), bh = atomicAdd(&s_halv, 0u);
+  if (bt) atomicAdd(&S.retries, (unsigned long long)bt);
+  if (br) atomicAdd(&S.raised, (unsigned long long)br);
+  if (bh) atomicAdd(&S.halvings, (unsigned long long)bh);
   atomicMax(&S.smax_bits[0], atomicMax(&s_bits[0], 0ull));
   atomicMax(&S.smax_bits[1], atomicMax(&s_bits[1], 0ull));
   __threadfence();

@@ -72,6 +72,11 @@ struct DevScalars {
   unsigned long long newton_iters;  // Newton updates summed over all solves since the state was set
   unsigned long long smax_bits[2];  // running max of the x / y wave speeds of the step (bit patterns; 0 between steps)
   unsigned int mass_parts;  // per-block (h, z) partials of the last step or upload, summed on read-out (mass_kernel)
+  // safeguards taken since the state was set, summed over all solves:
+  // Newton steps halved to keep every tau_k positive, solves whose celerity
+  // a was raised by the bed-jump bound (gamma_z), and doublings of a where
+  // the bounds admitted no solution with positive tau_k
+  unsigned long long halvings, raised, retries;
 };
 
 // Ghost-padded state and projection (SoA) of precision T.
@@ -420,11 +425,14 @@ __device__ __forceinline__ bool abs_le(double x, double y) {
 __device__ __forceinline__ bool abs_le(float x, float y) { return fabsf(x) <= y; }
 
 // Safeguarded Newton from the evaluated point (p, e): steps that would make
-// a tau_k non-positive are halved (at most 60 times); stops when
-// |step| <= tol p.  iters is incremented per accepted update.
+// a tau_k non-positive are halved (at most 60 times); stops after a full
+// (unhalved) step with |step| <= tol p -- a halved step is short because the
+// iterate is at the edge of the admissible set, not because it is near the
+// root, so it never ends the iteration.  iters is incremented per accepted
+// update, halv by the halvings of the accepted updates.
 template <typename T>
 __device__ __forceinline__ bool newton_loop(const NewtonConst<T>& c, const Cell<T>& L, const Cell<T>& R, T& p,
-                                            NewtonEval<T>& e, int maxit, T tol, int& iters) {
+                                            NewtonEval<T>& e, int maxit, T tol, int& iters, int& halv) {
   for (int it = 0; it < maxit; ++it) {
     T dm;
     T step = tdiv(-e.F, newton_deriv(c, e, dm));
@@ -448,19 +456,27 @@ __device__ __forceinline__ bool newton_loop(const NewtonConst<T>& c, const Cell<
         return true;
       }
     }
-    bool pos = false;
-    for (int h = 0; h <= 60; ++h) {
+    int h = 0;
+    for (; h <= 60; ++h) {
       newton_eval(p + step, c, L, R, tr);
-      if (newton_positive(tr)) { pos = true; break; }
+      if (newton_positive(tr)) break;
       step = T(0.5) * step;
     }
-    if (!pos) return false;
+    if (h > 60) return false;
     p = p + step;
     e = tr;
     ++iters;
-    if (abs_le(step, tol * p)) return true;
+    halv += h;
+    if (h == 0 && abs_le(step, tol * p)) return true;
   }
   return false;
+}
+
+template <typename T>
+__device__ __forceinline__ bool newton_loop(const NewtonConst<T>& c, const Cell<T>& L, const Cell<T>& R, T& p,
+                                            NewtonEval<T>& e, int maxit, T tol, int& iters) {
+  int halv = 0;
+  return newton_loop(c, L, R, p, e, maxit, tol, iters, halv);
 }
 
 template <typename T> __device__ __forceinline__ T eps_of();
@@ -478,18 +494,20 @@ template <> __device__ __forceinline__ float newton_floor<float>() { return 64.0
 // ip0 = 1/p0.
 template <typename T>
 __device__ __forceinline__ bool newton_root(const DevParams& P, const NewtonConst<T>& c, const Cell<T>& L,
-                                            const Cell<T>& R, T p0, T ip0, NewtonEval<T>& e, int& iters) {
+                                            const Cell<T>& R, T p0, T ip0, NewtonEval<T>& e, int& iters,
+                                            int& halv) {
   const T tol = tmax(par<T>(P.newton_tol, P.f.newton_tol), newton_floor<T>());
   T p = p0;
   newton_eval_ip(p, ip0, c, L, R, e);
-  return newton_loop(c, L, R, p, e, P.newton_maxit, tol, iters);
+  return newton_loop(c, L, R, p, e, P.newton_maxit, tol, iters, halv);
 }
 
 // Celerities of one interface: the bounds of Eq. (ab) over both states,
 // a scaled by kappa_a, b floored at beta_min a0, and a raised so that
 // K tau_min^2 >= gamma_z |dZ| (the sediment waves can carry the bed jump).
+// Returns whether that last bound raised a.
 template <typename T>
-__device__ __forceinline__ void celerities(const DevParams& P, const Cell<T>& L, const Cell<T>& R, T& a, T& b) {
+__device__ __forceinline__ bool celerities(const DevParams& P, const Cell<T>& L, const Cell<T>& R, T& a, T& b) {
   const T g = par<T>(P.g, P.f.g);
   const T a0 = nnmax(L.ca, R.ca);
   const T b0 = nnmax(L.cb, R.cb);
@@ -497,7 +515,9 @@ __device__ __forceinline__ void celerities(const DevParams& P, const Cell<T>& L,
   b = nnmax(b0, par<T>(P.beta_min, P.f.beta_min) * a0);
   const T Hmax = nnmax(L.H, R.H);
   const T need = b * b + par<T>(P.two_g_gamma, P.f.two_g_gamma) * (absbits(R.Z - L.Z) * (Hmax * Hmax));
-  if (a * a < need) a = tsqrt(need);
+  const bool raised = a * a < need;
+  if (raised) a = tsqrt(need);
+  return raised;
 }
 
 // Constants of the Newton iteration; returns its start p0, the root of the
@@ -629,23 +649,49 @@ __device__ __forceinline__ void fan_fluctuations(const DevParams& P, const Cell<
   Ap[3] = (n2 ? T(0) : lam2 * zj2) + (n4 ? T(0) : lam4 * zj4);
 }
 
-// iters receives the number of Newton updates (0 for identical states).
+// The safeguards one solve took, packed into an int ("branch"): bit 0 = the
+// bed-jump bound raised a, bits 1-2 = doublings of a, bits 3.. = halved
+// Newton steps.
+__device__ __forceinline__ unsigned branch_raised(int br) { return (unsigned)(br & 1); }
+__device__ __forceinline__ unsigned branch_retries(int br) { return (unsigned)((br >> 1) & 3); }
+__device__ __forceinline__ unsigned branch_halvings(int br) { return (unsigned)(br >> 3); }
+
+// Doublings of a allowed where the celerities admit no root with positive
+// tau_k (the paper's remark after Eq. (ab): stronger bounds may be needed).
+constexpr int kARetries = 3;
+
+// iters receives the number of Newton updates (0 for identical states);
+// branch the safeguards taken (branch_raised, _retries, _halvings); smax the
+// extreme wave speed max(|lambda1|, |lambda5|) with the celerity a used.
 template <typename T>
 __device__ bool riemann_solve(const DevParams& P, const Cell<T>& L, const Cell<T>& R, T Am[4], T Ap[4], T& smax,
-                              int& iters) {
+                              int& iters, int& branch) {
   iters = 0;
   T a, b;
-  celerities(P, L, R, a, b);
+  const bool raised = celerities(P, L, R, a, b);
+  branch = raised ? 1 : 0;
   smax = nnmax(absbits(L.un - a * L.tau), absbits(R.un + a * R.tau));
 #pragma unroll
   for (int c = 0; c < 4; ++c) { Am[c] = T(0); Ap[c] = T(0); }
   if (same_bits(L.H, R.H) && same_bits(L.Hn, R.Hn) && same_bits(L.Ht, R.Ht) && same_bits(L.Z, R.Z)) return true;
   NewtonConst<T> c;
-  T ip0;
-  const T p0 = newton_setup(P, L, R, a, b, c, &ip0);
   NewtonEval<T> e;
-  const bool ok = newton_root(P, c, L, R, p0, ip0, e, iters);
-  if (!ok || !newton_positive(e)) return false;
+  int halv = 0, retries = 0;
+  bool ok;
+  // where the celerities admit no root with positive tau_k, a is doubled and
+  // the iteration restarted (at most kARetries times; one loop, so that the
+  // common single pass costs no extra registers)
+  for (;;) {
+    T ip0;
+    const T p0 = newton_setup(P, L, R, a, b, c, &ip0);
+    ok = newton_root(P, c, L, R, p0, ip0, e, iters, halv) && newton_positive(e);
+    if (ok || retries == kARetries) break;
+    ++retries;
+    a = T(2) * a;
+  }
+  if (retries) smax = nnmax(absbits(L.un - a * L.tau), absbits(R.un + a * R.tau));
+  branch += 2 * retries + 8 * halv;
+  if (!ok) return false;
   fan_fluctuations(P, L, R, c, e, Am, Ap);
   return true;
 }
@@ -821,7 +867,7 @@ __device__ __forceinline__ Cell<T> load_cell(const DevState<T>& S, long long e, 
 // Newton updates; false if the solve failed (fluctuations zero then).
 template <typename T>
 __device__ __forceinline__ bool interface_item(const DevParams& P, const DevState<T>& S, bool ydir, long long k,
-                                               double& smax, int& iters) {
+                                               double& smax, int& iters, int& branch) {
   T Am[4], Ap[4], s;
   bool ok;
   if (!ydir) {
@@ -830,7 +876,7 @@ __device__ __forceinline__ bool interface_item(const DevParams& P, const DevStat
     const long long eR = ext_index(P, i, row);
     const Cell<T> L = load_cell(S, eR - 1, false);
     const Cell<T> R = load_cell(S, eR, false);
-    ok = riemann_solve(P, L, R, Am, Ap, s, iters);
+    ok = riemann_solve(P, L, R, Am, Ap, s, iters, branch);
 #pragma unroll
     for (int c = 0; c < 4; ++c) { S.fx[c * P.nfx + k] = Am[c]; S.fx[(4 + c) * P.nfx + k] = Ap[c]; }
   } else {
@@ -839,7 +885,7 @@ __device__ __forceinline__ bool interface_item(const DevParams& P, const DevStat
     const long long eR = ext_index(P, i, row);
     const Cell<T> L = load_cell(S, eR - P.ex, true);
     const Cell<T> R = load_cell(S, eR, true);
-    ok = riemann_solve(P, L, R, Am, Ap, s, iters);
+    ok = riemann_solve(P, L, R, Am, Ap, s, iters, branch);
 #pragma unroll
     for (int c = 0; c < 4; ++c) { S.fy[c * P.nfy + k] = Am[c]; S.fy[(4 + c) * P.nfy + k] = Ap[c]; }
   }
@@ -883,16 +929,16 @@ __global__ void __launch_bounds__(NT, iface_min_blocks<NT>::value) interface_ker
   // block tallies: the block's maximal speed (bit pattern) and Newton
   // updates, and how many of its warps have added theirs
   __shared__ unsigned long long s_bits;
-  __shared__ unsigned int s_its, s_warps;
-  if (threadIdx.x == 0) { s_bits = 0ull; s_its = 0u; s_warps = 0u; }
+  __shared__ unsigned int s_its, s_warps, s_halv, s_raised, s_retry;
+  if (threadIdx.x == 0) { s_bits = 0ull; s_its = 0u; s_warps = 0u; s_halv = 0u; s_raised = 0u; s_retry = 0u; }
   __syncthreads();
   const unsigned nbx = (unsigned)((P.nfx + NT - 1) / NT);
   const bool ydir = blockIdx.x >= nbx;
   const long long k = (long long)(ydir ? blockIdx.x - nbx : blockIdx.x) * NT + threadIdx.x;
   double smax = 0.0;
-  int iters = 0;
+  int iters = 0, branch = 0;
   if (k < (ydir ? P.nfy : P.nfx)) {
-    if (!interface_item(P, S, ydir, k, smax, iters)) atomicOr(&sc->status, ST_RIEMANN);
+    if (!interface_item(P, S, ydir, k, smax, iters, branch)) atomicOr(&sc->status, ST_RIEMANN);
   }
   // Max of the (non-negative) speeds and sum of the Newton updates, on
   // integers (off the FP64 pipe): over the warp by shuffles, over the block
@@ -909,15 +955,27 @@ __global__ void __launch_bounds__(NT, iface_min_blocks<NT>::value) interface_ker
     bits = ob > bits ? ob : bits;
     iters += __shfl_xor_sync(0xffffffffu, iters, o);
   }
+  const unsigned wb = __reduce_or_sync(0xffffffffu, (unsigned)branch);
+  unsigned wr = 0u, wt = 0u, wh = 0u;
+  if (wb) {  // a safeguard was taken in this warp (rare): count them
+    wr = __reduce_add_sync(0xffffffffu, branch_raised(branch));
+    wt = __reduce_add_sync(0xffffffffu, branch_retries(branch));
+    wh = __reduce_add_sync(0xffffffffu, branch_halvings(branch));
+  }
   if ((threadIdx.x & 31) != 0) return;
   atomicMax(&s_bits, (unsigned long long)bits);
   atomicAdd(&s_its, (unsigned int)iters);
+  if (wb) { atomicAdd(&s_raised, wr); atomicAdd(&s_retry, wt); atomicAdd(&s_halv, wh); }
   __threadfence_block();
   if (atomicAdd(&s_warps, 1u) != NT / 32 - 1) return;
   // last warp of the block
   __threadfence_block();
   const unsigned long long bb = atomicMax(&s_bits, 0ull);
   atomicAdd(&sc->newton_iters, (unsigned long long)atomicAdd(&s_its, 0u));
+  const unsigned br = atomicAdd(&s_raised, 0u), bt = atomicAdd(&s_retry, 0u), bh = atomicAdd(&s_halv, 0u);
+  if (br) atomicAdd(&sc->raised, (unsigned long long)br);
+  if (bt) atomicAdd(&sc->retries, (unsigned long long)bt);
+  if (bh) atomicAdd(&sc->halvings, (unsigned long long)bh);
   atomicMax(&sc->smax_bits[ydir ? 1 : 0], bb);
   __threadfence();
   if (atomicAdd(&sc->done_iface, 1u) != gridDim.x - 1) return;

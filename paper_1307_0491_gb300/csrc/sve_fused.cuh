@@ -151,12 +151,13 @@ __global__ void __launch_bounds__(kFThreads, 3) solve_kernel(DevParams P, StateB
   // neighbouring banks: [c] = A- (c < 4) and A+ (c >= 4) of (H, Hn, Ht, Z)
   __shared__ T fx[8][kFTY][kFTX + 1];
   __shared__ T fy[8][kFTY + 1][kFTX];
-  __shared__ unsigned int s_sx, s_sy, s_its, s_warps;
-  if (threadIdx.x == 0) { s_sx = 0u; s_sy = 0u; s_its = 0u; s_warps = 0u; }
+  __shared__ unsigned int s_sx, s_sy, s_its, s_warps, s_halv, s_raised, s_retry;
+  if (threadIdx.x == 0) { s_sx = 0u; s_sy = 0u; s_its = 0u; s_warps = 0u; s_halv = 0u; s_raised = 0u; s_retry = 0u; }
   __syncthreads();
   const T idx = par<T>(P.inv_dx, (float)P.inv_dx), idy = par<T>(P.inv_dy, (float)P.inv_dy);
   const int tx = threadIdx.x % kFTX, ty = threadIdx.x / kFTX;  // cell of this thread (ty < TY)
   int fail = 0, iters = 0;
+  unsigned int nraised = 0u, nretry = 0u, nhalv = 0u;
   unsigned int mx = 0u, my = 0u;  // speed maxima (bit patterns of non-negative floats)
   for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
     const int i0 = (t % tiles_x) * kFTX, j0 = (t / tiles_x) * kFTY;
@@ -168,9 +169,12 @@ __global__ void __launch_bounds__(kFThreads, 3) solve_kernel(DevParams P, StateB
       const Cell<T> L = frame_cell(!ydir ? cells[lj][li - 1] : cells[lj - 1][li], ydir);
       const Cell<T> R = frame_cell(cells[lj][li], ydir);
       T Am[4], Ap[4], smax;
-      int its = 0;
-      if (!riemann_solve(P, L, R, Am, Ap, smax, its)) fail = 1;
+      int its = 0, branch = 0;
+      if (!riemann_solve(P, L, R, Am, Ap, smax, its, branch)) fail = 1;
       iters += its;
+      nraised += branch_raised(branch);
+      nretry += branch_retries(branch);
+      nhalv += branch_halvings(branch);
       const unsigned int sb = __float_as_uint(smax);
       if (!ydir) {
         mx = max(mx, sb);
@@ -201,16 +205,24 @@ __global__ void __launch_bounds__(kFThreads, 3) solve_kernel(DevParams P, StateB
   mx = __reduce_max_sync(0xffffffffu, mx);
   my = __reduce_max_sync(0xffffffffu, my);
   iters = __reduce_add_sync(0xffffffffu, iters);
+  nraised = __reduce_add_sync(0xffffffffu, nraised);
+  nhalv = __reduce_add_sync(0xffffffffu, nhalv);
+  nretry = __reduce_add_sync(0xffffffffu, nretry);
   if ((threadIdx.x & 31) != 0) return;
   atomicMax(&s_sx, mx);
   atomicMax(&s_sy, my);
   atomicAdd(&s_its, (unsigned int)iters);
+  if (nraised | nretry | nhalv) { atomicAdd(&s_raised, nraised); atomicAdd(&s_retry, nretry); atomicAdd(&s_halv, nhalv); }
   __threadfence_block();
   if (atomicAdd(&s_warps, 1u) != kFThreads / 32 - 1) return;
   __threadfence_block();
   const double bx = (double)__uint_as_float(atomicMax(&s_sx, 0u));
   const double by = (double)__uint_as_float(atomicMax(&s_sy, 0u));
   atomicAdd(&sc->newton_iters, (unsigned long long)atomicAdd(&s_its, 0u));
+  const unsigned br = atomicAdd(&s_raised, 0u), bt = atomicAdd(&s_retry, 0u), bh = atomicAdd(&s_halv, 0u);
+  if (bt) atomicAdd(&sc->retries, (unsigned long long)bt);
+  if (br) atomicAdd(&sc->raised, (unsigned long long)br);
+  if (bh) atomicAdd(&sc->halvings, (unsigned long long)bh);
   atomicMax(&sc->smax_bits[0], (unsigned long long)__double_as_longlong(bx));
   atomicMax(&sc->smax_bits[1], (unsigned long long)__double_as_longlong(by));
   __threadfence();

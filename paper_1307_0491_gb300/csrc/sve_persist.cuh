@@ -94,15 +94,18 @@ __global__ void __launch_bounds__(kPersistThreads, 1) persistent_kernel(DevParam
     const int par = st & 1;
     // A: interfaces
     long long bx = 0, by = 0;
-    int iters = 0;
+    int iters = 0, nraised = 0, nretry = 0, nhalv = 0;
     int bad = 0;
     for (long long idx = t0; idx < nf; idx += stride) {
       const bool ydir = idx >= P.nfx;
       const long long k = ydir ? idx - P.nfx : idx;
       double smax = 0.0;
-      int it = 0;
-      if (!interface_item(P, S, ydir, k, smax, it)) bad = ST_RIEMANN;
+      int it = 0, branch = 0;
+      if (!interface_item(P, S, ydir, k, smax, it, branch)) bad = ST_RIEMANN;
       iters += it;
+      nraised += (int)branch_raised(branch);
+      nretry += (int)branch_retries(branch);
+      nhalv += (int)branch_halvings(branch);
       const long long b = __double_as_longlong(smax);  // speeds are >= 0: integer order = IEEE order
       if (ydir) by = b > by ? b : by;
       else bx = b > bx ? b : bx;
@@ -115,9 +118,15 @@ __global__ void __launch_bounds__(kPersistThreads, 1) persistent_kernel(DevParam
       iters += __shfl_xor_sync(0xffffffffu, iters, o);
       bad |= __shfl_xor_sync(0xffffffffu, bad, o);
     }
+    nraised = (int)__reduce_add_sync(0xffffffffu, (unsigned)nraised);
+    nhalv = (int)__reduce_add_sync(0xffffffffu, (unsigned)nhalv);
+    nretry = (int)__reduce_add_sync(0xffffffffu, (unsigned)nretry);
     if (threadIdx.x == 0) {
       if (bad) atomicOr(&sc->status, bad);
       atomicAdd(&sc->newton_iters, (unsigned long long)iters);
+      if (nraised) atomicAdd(&sc->raised, (unsigned long long)nraised);
+      if (nhalv) atomicAdd(&sc->halvings, (unsigned long long)nhalv);
+      if (nretry) atomicAdd(&sc->retries, (unsigned long long)nretry);
       atomicMax(&ps->smax[par][0], (unsigned long long)bx);
       atomicMax(&ps->smax[par][1], (unsigned long long)by);
     }

@@ -37,7 +37,8 @@ EXPORTS = ("sve_config_default", "sve_create", "sve_set_stream", "sve_set_state"
            "sve_batch_step_async", "sve_batch_get_state", "sve_batch_get_diag", "sve_batch_get_counters",
            "sve_batch_autotune", "sve_batch_set_schedule", "sve_batch_last_launch_count", "sve_batch_destroy",
            "sve_record_forward", "sve_adjoint", "sve_set_block_size", "sve_get_block_size", "sve_advance",
-           "sve_get_checkpoint_every", "sve_set_persistent", "sve_get_persistent", "sve_check_sync_timeout")
+           "sve_get_checkpoint_every", "sve_set_persistent", "sve_get_persistent", "sve_check_sync_timeout",
+           "sve_get_safeguards")
 
 
 class sve_config(ctypes.Structure):
@@ -94,6 +95,8 @@ def load() -> ctypes.CDLL:
         "sve_profile": ([vp, ip], ip),
         "sve_profile_read": ([vp, dp, ctypes.POINTER(ctypes.c_longlong)], ip),
         "sve_get_counters": ([vp, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_ulonglong)], ip),
+        "sve_get_safeguards": ([vp, ctypes.POINTER(ctypes.c_ulonglong), ctypes.POINTER(ctypes.c_ulonglong),
+                                ctypes.POINTER(ctypes.c_ulonglong)], ip),
         "sve_step_noalloc": ([cfgp, vp, vp, vp, vp, ip, dp, vp], ip),
         "sve_batch_create": ([cfgp, ip, ctypes.POINTER(vp)], ip),
         "sve_batch_set_stream": ([vp, vp], ip),
@@ -222,6 +225,14 @@ def sve_get_counters(h) -> tuple[int, int, int]:
     its = ctypes.c_ulonglong(0)
     rc = load().sve_get_counters(h, ctypes.byref(steps), ctypes.byref(its))
     return rc, steps.value, its.value
+
+
+def sve_get_safeguards(h) -> tuple[int, int, int, int]:
+    halv = ctypes.c_ulonglong(0)
+    raised = ctypes.c_ulonglong(0)
+    retries = ctypes.c_ulonglong(0)
+    rc = load().sve_get_safeguards(h, ctypes.byref(halv), ctypes.byref(raised), ctypes.byref(retries))
+    return rc, halv.value, raised.value, retries.value
 
 
 def sve_step_noalloc(cfg: sve_config, depth: int, hu: int, hv: int | None, zb: int, nsteps: int, t: float,
@@ -478,6 +489,11 @@ class Solver:
         rc, steps, its = sve_get_counters(self.h)
         _check(rc, "sve_get_counters")
         return dict(steps=steps, newton_iters=its)
+
+    def safeguards(self) -> dict:
+        rc, halv, raised, retries = sve_get_safeguards(self.h)
+        _check(rc, "sve_get_safeguards")
+        return dict(halvings=halv, raised=raised, retries=retries)
 
     def checkpoint_every(self) -> int:
         """The recording's checkpoint interval (nsteps: every step kept)."""

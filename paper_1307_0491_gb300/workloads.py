@@ -245,6 +245,28 @@ def thin_dam_break(nx: int = 200, h_thin: float = 1e-3) -> dict:
     return dict(params=params, h=h, hu=np.zeros(nx), hv=None, z=z, nsteps=None)
 
 
+def bed_step(nx: int = 100, dim: int = 1, ny: int = 1, step: float = 0.4, q: float = 0.5,
+             A_g: float = 1e-3) -> dict:
+    """Flow of discharge q over a bed step of height `step` at mid-channel
+    (10 m long, free surface at 1.2 m): a step of about a third of the depth,
+    where the bed-jump bound of the celerities sets a (the stronger bound of
+    Sec. 3, reading R1).  Inflow q on the west side, free elsewhere.  In 2D
+    the step line is oblique (x = 5 m + 0.5 (y - ly/2)), so x- and
+    y-interfaces both cross it."""
+    L = 10.0
+    x = _centers(nx, L)
+    if dim == 1:
+        z = np.where(x > 0.5 * L, step, 0.0)
+        params = base_params(dim=1, nx=nx, ny=1, lx=L, A_g=A_g, q_in=q, bc=("inflow_q", "free", "free", "free"))
+        return dict(params=params, h=1.2 - z, hu=np.full(nx, q), hv=None, z=z, nsteps=None)
+    ly = L * ny / nx
+    y = _centers(ny, ly)
+    X, Y = np.meshgrid(x, y)
+    z = np.where(X > 0.5 * L + 0.5 * (Y - 0.5 * ly), step, 0.0)
+    params = base_params(dim=2, nx=nx, ny=ny, lx=L, ly=ly, A_g=A_g, q_in=q, bc=("inflow_q", "free", "free", "free"))
+    return dict(params=params, h=1.2 - z, hu=np.full_like(z, q), hv=np.zeros_like(z), z=z, nsteps=None)
+
+
 def colliding_streams(nx: int = 200, dim: int = 1, ny: int = 1, h0: float = 0.1, u0: float = 3.0,
                       A_g: float = 1e-2, m_g: float = 3.0, ymod: float = 0.0) -> dict:
     """Two supercritical streams (depth h0, speeds +u0 and -u0, Froude

@@ -1,13 +1,13 @@
-// Test probe: the Newton-Raphson inverse cube root of sve_device.cuh against
+// Test driver: the Newton-Raphson inverse cube root of sve_device.cuh against
 // CUDA's IEEE result, on inputs read from stdin.
-// Usage: gpu_arith_probe < inputs (one double per line) > outputs
+// Usage: gpu_arith_driver < inputs (one double per line) > outputs
 // Output per input: x, rcbrt64(x), 1/cbrt(x)
 #include <cstdio>
 #include <vector>
 
 #include "../paper_1307_0491_gb300/csrc/sve_device.cuh"
 
-__global__ void probe(const double* x, double* out, int n) {
+__global__ void rcbrt_values(const double* x, double* out, int n) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   const double v = x[i];
@@ -25,7 +25,7 @@ int main() {
   if (cudaMalloc(&dx, sizeof(double) * n) != cudaSuccess) return 2;
   if (cudaMalloc(&dout, sizeof(double) * 2 * n) != cudaSuccess) return 2;
   cudaMemcpy(dx, x.data(), sizeof(double) * n, cudaMemcpyHostToDevice);
-  probe<<<(n + 255) / 256, 256>>>(dx, dout, n);
+  rcbrt_values<<<(n + 255) / 256, 256>>>(dx, dout, n);
   std::vector<double> out(2 * (size_t)n);
   if (cudaMemcpy(out.data(), dout, sizeof(double) * 2 * n, cudaMemcpyDeviceToHost) != cudaSuccess) return 3;
   for (int i = 0; i < n; ++i)

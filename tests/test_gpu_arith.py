@@ -27,9 +27,9 @@ def test_inverse_cube_root_within_2_ulp():
     x = np.concatenate([10.0 ** rng.uniform(-6, 6, 20000), rng.uniform(0.5, 2.0, 5000),
                         [1.0, 2.0, 0.1, 1e-36, 1e-40, 1e40, 3.0e38, 1.5e-38, 7.0]])
     with tempfile.TemporaryDirectory() as tmp:
-        exe = os.path.join(tmp, "probe")
+        exe = os.path.join(tmp, "arith_driver")
         subprocess.run([nvcc, "-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-std=c++17", "-o", exe,
-                        os.path.join(HERE, "gpu_arith_probe.cu")], check=True)
+                        os.path.join(HERE, "gpu_arith_driver.cu")], check=True)
         r = subprocess.run([exe], input="\n".join(repr(float(v)) for v in x), capture_output=True, text=True,
                            check=True)
     out = np.array([[float(t) for t in line.split()] for line in r.stdout.splitlines()])
