@@ -55,6 +55,19 @@ def workload_desc(nx, ny, workload="dune2d", precision="fp64"):
             f"Strickler K=40, inflow q=0.5 / free outflow)")
 
 
+def bench_config(args, nx, ny):
+    """The `config` of the JSON line, the same for both arms: the workload,
+    its grid and precision, the window of the run the timed steps cover
+    (after --spinup untimed steps and the warm-up steps) and how L2 is
+    kept out of the timing."""
+    return {"workload": workload_desc(nx, ny, args.workload, args.precision), "nx": nx, "ny": ny,
+            "precision": args.precision,
+            "timed_steps_of_run": f"{args.spinup + args.warmup}..{args.spinup + args.warmup + args.steps - 1}",
+            "per_rank": "independent replica (seed = rank)",
+            "l2": f"GPU arm: {L2_FLUSH_BYTES >> 20} MiB written between timed steps, outside the events "
+                  f"(L2 flush); CPU arm: no flush"}
+
+
 def make_workload(args, W, seed=0):
     """The timed workload: the 2D dune (default, FP64) or the antidune (its
     FP32 and FP64 forms); --nx/--ny shrink it (profiling captures)."""
@@ -190,16 +203,18 @@ def _oracle_stepper(o, P, st, threads: int):
     return step, (lambda: None)
 
 
-def cpu_oracle_rate(w, threads: int, budget_s: float = 10.0, max_steps: int = 40):
+def cpu_oracle_rate(w, threads: int, budget_s: float = 10.0, max_steps: int = 5000, state=None):
     """The FP64 oracle on the host, as it stands, on the full grid of the
     workload for as many steps as fit in about budget_s (at least 1), on
-    ``threads`` threads (row bands of the oracle's block API when > 1)."""
+    ``threads`` threads (row bands of the oracle's block API when > 1),
+    from `state` (h, hu, hv, z; default: the workload's initial state)."""
     import oracle
 
     o = oracle.get()
     P = oracle.Params.from_workload(w["params"])
     cells = w["params"]["nx"] * w["params"]["ny"]
-    step, close = _oracle_stepper(o, P, (w["h"], w["hu"], w["hv"], w["z"]), threads)
+    st = state if state is not None else (w["h"], w["hu"], w["hv"], w["z"])
+    step, close = _oracle_stepper(o, P, st, threads)
     try:
         t0 = time.perf_counter()
         step(1)
@@ -216,9 +231,34 @@ def cpu_oracle_rate(w, threads: int, budget_s: float = 10.0, max_steps: int = 40
     return cells * steps / secs, steps, secs
 
 
+def oracle_spinup(w, threads: int, nsteps: int):
+    """The workload's state after nsteps oracle steps (untimed; row bands on
+    `threads` threads, bit-identical to the single-threaded oracle)."""
+    import oracle
+    from oracle.banded import BandedRun
+
+    o = oracle.get()
+    P = oracle.Params.from_workload(w["params"])
+    st = (w["h"], w["hu"], w["hv"], w["z"])
+    if nsteps <= 0:
+        return st
+    if threads > 1 and P.dim == 2:
+        run = BandedRun(o, P, *st, nbands=threads, threads=threads)
+        try:
+            run.step(nsteps)
+            f = run.state()
+        finally:
+            run.close()
+        return (f["h"], f["hu"], f["hv"], f["z"])
+    r = o.run(P, nsteps, *st)
+    return (r["h"], r["hu"], r["hv"], r["z"])
+
+
 def run_reference(args, world, rank):
     """Reference arm: the FP64 CPU oracle timed on all host cores (row bands
-    of the oracle's block API on threads), one full-grid step per step."""
+    of the oracle's block API on threads), one full-grid step per step, over
+    the same window of the run as the GPU arm (--spinup untimed steps, the
+    warm-up steps, then the timed ones)."""
     if rank != 0:
         return 0
     import oracle
@@ -239,11 +279,12 @@ def run_reference(args, world, rank):
     step(1)
     t_full = time.perf_counter() - t0
     close()
-    budget = 120.0
+    budget = 150.0
     ny_full = ny
     sample = f"full {nx}x{ny} grid"
-    if (args.steps + args.warmup) * t_full > budget and w["params"]["dim"] == 2:
-        nys = max(8 * threads, int(ny * budget / ((args.steps + args.warmup) * t_full)))
+    total = args.spinup + args.steps + args.warmup
+    if total * t_full > budget and w["params"]["dim"] == 2:
+        nys = max(8 * threads, int(ny * budget / (total * t_full)))
         nys = min(nys, ny)
         p2 = dict(w["params"], ny=nys, ly=w["params"]["ly"] * nys / ny)
         w = dict(w, params=p2, h=w["h"][:nys], hu=w["hu"][:nys], hv=w["hv"][:nys], z=w["z"][:nys])
@@ -253,6 +294,8 @@ def run_reference(args, world, rank):
         sample = f"rows 0..{nys - 1} of the {nx}x{ny_full} grid"
     step, close = _oracle_stepper(o, P, st, threads)
     try:
+        if args.spinup > 0:
+            step(args.spinup)
         step(args.warmup)
         t0 = time.perf_counter()
         step(args.steps)
@@ -266,10 +309,10 @@ def run_reference(args, world, rank):
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": secs / args.steps * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": workload_desc(nx, ny_full, args.workload, args.precision), "nx": nx, "ny": ny_full,
-                   "precision": args.precision},
+        "config": bench_config(args, nx, ny_full),
         "cpu_baseline": {"kind": "oracle", "cores": threads if P.dim == 2 else 1, "value": value, "unit": UNIT,
-                         "sample": f"{sample}, {args.steps} steps after {args.warmup} warm-up steps, {how}"},
+                         "sample": f"{sample}, {args.steps} steps after {args.spinup} spin-up and {args.warmup} "
+                                   f"warm-up steps, {how}"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -287,7 +330,7 @@ def run_batched(args, sve, W, torch, precision: str, plain_value: float):
         b.set_state(i, r["h"], r["hu"], r["hv"], r["z"])
     tile, sched = b.autotune(2)
     b.step(args.batch_spinup)
-    b.step(2)
+    b.step(3)
     c0 = b.counters()
     stream = torch.cuda.current_stream()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -304,7 +347,7 @@ def run_batched(args, sve, W, torch, precision: str, plain_value: float):
                         f"A_g log-U[1e-4,1e-2], m_g in {{1,2,3,4}}, amplitude U[0.2,1] (seed 0)",
             "precision": precision, "runs": args.batch_runs, "cells_per_step": cells, "value": value, "unit": UNIT,
             "ms_per_step": ms / args.batch_steps, "steps": args.batch_steps,
-            "timed_steps_of_run": f"{args.batch_spinup + 2}..{args.batch_spinup + 1 + args.batch_steps}",
+            "timed_steps_of_run": f"{args.batch_spinup + 3}..{args.batch_spinup + 2 + args.batch_steps}",
             "launches_per_step": 2, "tile": tile, "schedule": ["run-major", "round-robin"][sched],
             "newton_updates": c1["newton_iters"] - c0["newton_iters"],
             "vs_plain": value / plain_value if plain_value else None,
@@ -346,11 +389,15 @@ def run_adjoint(args, sve, W, torch):
         t2 = time.perf_counter()
         return grads, gp, t0, t1, t2, s.checkpoint_every(), fin
 
-    # automatic checkpointing (every step kept when it fits in device memory),
-    # then checkpoints every ceil(sqrt(N)) steps with the segments recomputed
+    # automatic checkpointing (every step kept when it fits in device memory,
+    # else checkpoints every ceil(sqrt(N)) steps with the segments
+    # recomputed); the latter also timed on its own when the first kept all
     sq = int(math.ceil(math.sqrt(n)))
-    _, _, c0, _, c2, _, _ = gradient(sq)
     grads, gp, t0, t1, t2, every, fin = gradient(0)
+    if every == n:
+        _, _, c0, _, c2, _, _ = gradient(sq)
+    else:
+        c0, c2 = t0, t2
     # the same recording, reversed for a cotangent that is nonzero in every
     # cell (L = ||z(T)||^2): the misfit above is zero where both runs stayed
     # uniform, and interfaces with zero cotangents on both sides are skipped
@@ -436,16 +483,28 @@ def run_closures(args, sve, W, torch):
             "time": "wall clock around one host-synchronous sve_step call", "laws": out}
 
 
+def crop(w, nx, ny):
+    """The first ny rows and nx columns of a 2D workload (the same cells,
+    physics and boundary types, the domain lengths scaled with the grid)."""
+    p = w["params"]
+    p2 = dict(p, nx=nx, ny=ny, lx=p["lx"] * nx / p["nx"], ly=p["ly"] * ny / p["ny"])
+    return dict(w, params=p2, **{k: np.ascontiguousarray(w[k][:ny, :nx]) for k in ("h", "hu", "hv", "z")})
+
+
 def run_fp32_error(args, sve, W, torch):
-    """Error of the FP32-state path per config after the config's step
-    count: the 2D dune (1024 x 512, 2000 steps) and the 2D antidune (8192 x
-    4096, 1000 steps), against the FP64 path from the same initial state
-    (the FP64 path equals the FP64 oracle to 1e-10 relative, tested).  Per
-    field: relative L-infinity (max |d| / max |ref|) and relative L1
-    (sum |d| / sum |ref|); discharges are scaled by the largest discharge."""
+    """Error of the FP32-state path per config, against the FP64 path from
+    the same initial state (the FP64 path equals the FP64 oracle to 1e-10
+    relative, tested): the 2D dune (1024 x 512) for its 2000 steps, the 2D
+    antidune on its full 8192 x 4096 grid for 200 steps and on a 1024 x 512
+    crop of it (the same cells) for its 1000 steps.  Per field: relative
+    L-infinity (max |d| / max |ref|) and relative L1 (sum |d| / sum |ref|);
+    discharges are scaled by the largest discharge."""
     out = []
-    for name, w, n in (("2D dune 1024x512, 2000 steps", W.dune2d(), 2000),
-                       ("2D antidune 8192x4096, 1000 steps", W.antidune2d(), 1000)):
+    anti = W.antidune2d()
+    for name, w, n in (("2D dune 1024x512, 2000 steps (full run)", W.dune2d(), 2000),
+                       ("2D antidune 8192x4096 (full grid), 200 steps", anti, 200),
+                       ("2D antidune, 1024x512 crop of the 8192x4096 grid, 1000 steps (full run)",
+                        crop(anti, 1024, 512), 1000)):
         res = {}
         for prec in ("fp64", "fp32"):
             s = sve.Solver(w["params"], prec)
@@ -546,6 +605,139 @@ def run_paper_bump(args, sve, W, torch):
             "time": "wall clock around host-synchronous sve_step calls"}
 
 
+def measure_step(sve, torch, w, prec, local, world, spinup, warmup, steps, clocks=False):
+    """Device time of `steps` single steps of workload w in precision prec,
+    after `spinup` untimed steps and `warmup` warm-up steps: each step
+    between CUDA events on the solver's stream, an L2 flush (a 256 MiB
+    write) before each outside the events, the kernels' own event times from
+    the library's profiling, the Newton counter over the timed steps; time
+    max over ranks.  Returns the open solver with the numbers."""
+    nx, ny = w["params"]["nx"], w["params"]["ny"]
+    stream = torch.cuda.current_stream()
+    solver = sve.Solver(w["params"], prec, stream=stream.cuda_stream)
+    solver.set_state(w["h"], w["hu"], w["hv"], w["z"])
+    # spin-up: the first steps of a run can be cheaper (neighbours that are
+    # still identical skip their solves); advance into the regime of the run
+    if spinup > 0:
+        solver.step(spinup)
+    for _ in range(warmup):
+        solver.step(1)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    c0 = solver.counters()
+    solver.profile(True)
+    sampler = ClockSampler(local) if clocks else None
+    if sampler:
+        sampler.start()
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.barrier()
+    torch.cuda.synchronize()
+    if sampler:
+        sampler.mark_start()
+    for k in range(steps):
+        flush.zero_()                      # L2 flush between timed steps (outside the events)
+        ev[k][0].record(stream)
+        solver.step_async(1)
+        ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    if sampler:
+        sampler.mark_end()
+    if world > 1:
+        dist.barrier()
+    clk = sampler.stop() if sampler else None
+    solver.sync()
+    total_ms = float(np.sum([a.elapsed_time(b) for a, b in ev]))
+    prof = solver.profile_read()
+    solver.profile(False)
+    c1 = solver.counters()
+    if world > 1:
+        t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    del flush
+    return {"solver": solver, "value": world * nx * ny * steps / (total_ms * 1e-3), "ms_per_step": total_ms / steps,
+            "prof": prof, "newton": c1["newton_iters"] - c0["newton_iters"], "steps": steps, "clocks": clk,
+            "timed_steps_of_run": f"{spinup + warmup}..{spinup + warmup + steps - 1}"}
+
+
+def roofline_of(m, w, prec, traffic_ok=False):
+    """Roofline of the dominant kernel of a measured step (measure_step):
+    FP64 -- interface_kernel<double>, bound by the FP64 ALUs: algorithmic
+    FLOP per interface (setup, evaluations and updates by the device's Newton
+    counter, final states and fluctuations) x interfaces / its mean event
+    time, against the nominal FP64 rate; FP32 in 2D -- solve_kernel<float>,
+    the same count per interface (the Newton counter over the solves done,
+    which include the doubled tile edges) against the nominal FP32 rate.
+    Both give the step's algorithmic HBM fraction (64 / 32 B per cell)."""
+    nx, ny = w["params"]["nx"], w["params"]["ny"]
+    cells = nx * ny
+    steps = m["steps"]
+    prof = m["prof"]
+    n_iface = (nx + 1) * ny + nx * (ny + 1)
+    iface_ms = prof["iface_ms"] / max(prof["iface_launches"], 1)
+    cell_ms = prof["cell_ms"] / max(prof["cell_launches"], 1)
+    hbm = peaks().get("hbm_gbs", 6800.3)
+    bytes_per_cell = BYTES_PER_CELL_FP64 if prec == "fp64" else BYTES_PER_CELL_FP64 // 2
+    step_frac = (bytes_per_cell * cells / (m["ms_per_step"] * 1e-3)) / (hbm * 1e9)
+    if prec == "fp32":
+        tiles_x, tiles_y = -(-nx // 32), -(-ny // 8)
+        solves = ny * (nx + tiles_x) + nx * (ny + tiles_y)
+        upd = m["newton"] / (solves * steps)
+        flop = FLOP_SETUP + (1 + upd) * FLOP_EVAL + upd * FLOP_UPDATE + FLOP_FINAL
+        ach = n_iface * flop / (iface_ms * 1e-3)
+        return {"bound": "alu", "achieved": ach / 1e12, "peak": FP32_PEAK_FLOPS / 1e12, "unit": "TFLOP/s",
+                "frac": ach / FP32_PEAK_FLOPS, "traffic": None, "kernel": "solve_kernel<float>",
+                "peak_source": "152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz (nominal FP32 FMA rate)",
+                "flop_per_interface": flop, "newton_updates_per_solve": upd,
+                "iface_ms": iface_ms, "cell_ms": cell_ms, "hbm_frac_of_step": step_frac, "hbm_peak_gbs": hbm}
+    upd = m["newton"] / (n_iface * steps)
+    flop = FLOP_SETUP + (1 + upd) * FLOP_EVAL + upd * FLOP_UPDATE + FLOP_FINAL
+    ach = n_iface * flop / (iface_ms * 1e-3)
+    r = {"bound": "alu", "achieved": ach / 1e12, "peak": FP64_PEAK_FLOPS / 1e12, "unit": "TFLOP/s",
+         "frac": ach / FP64_PEAK_FLOPS, "traffic": iface_traffic() if traffic_ok else None,
+         "kernel": "interface_kernel<double>", "peak_source": "152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz "
+         "(GB300 FP64 nominal 1.25 TFLOP/s); a measured DFMA loop gave 1.19 TFLOP/s",
+         "flop_per_interface": flop, "newton_updates_per_solve": upd,
+         "iface_ms": iface_ms, "cell_ms": cell_ms, "hbm_frac_of_step": step_frac, "hbm_peak_gbs": hbm}
+    if r["traffic"]:
+        # the kernel's DRAM throughput from its ncu byte count and its event time
+        r["dram_gbs"] = r["traffic"] / (iface_ms * 1e-3) / 1e9
+        r["dram_frac"] = r["dram_gbs"] / hbm
+    return r
+
+
+def run_c3(args, sve, W, torch, local):
+    """The largest config: the 2D antidune, 8192 x 4096 cells (24 x 12 m,
+    supercritical inflow, random bed, MPM + Darcy), FP64 and FP32 state,
+    device-timed like the headline (L2 flush between steps, CUDA events),
+    after 30 untimed steps of the run, with the roofline of each form's
+    dominant kernel."""
+    w = W.antidune2d()
+    out = {"workload": workload_desc(8192, 4096, "antidune2d", "fp64/fp32"), "nx": 8192, "ny": 4096}
+    for prec, steps in (("fp64", args.c3_steps_fp64), ("fp32", args.c3_steps_fp32)):
+        m = measure_step(sve, torch, w, prec, local, 1, 30, 3, steps)
+        m["solver"].close()
+        out[prec] = {"value": m["value"], "unit": UNIT, "ms_per_step": m["ms_per_step"], "steps": steps,
+                     "timed_steps_of_run": m["timed_steps_of_run"], "roofline": roofline_of(m, w, prec),
+                     "gpu_launches": int(m["prof"]["iface_launches"] + m["prof"]["cell_launches"])}
+    out["fp32_vs_fp64"] = out["fp32"]["value"] / out["fp64"]["value"]
+    return out
+
+
+def run_plain_fp32(args, sve, W, torch, local):
+    """The plain single-run step of the 2D dune in FP32 state (the batched
+    FP32 ensemble's C2 physics is compared with it), device-timed as the
+    headline over the same window of the run."""
+    w = W.dune2d()
+    m = measure_step(sve, torch, w, "fp32", local, 1, args.spinup, args.warmup, min(args.steps, 200))
+    m["solver"].close()
+    return {"workload": workload_desc(1024, 512, "dune2d", "fp32"), "value": m["value"], "unit": UNIT,
+            "ms_per_step": m["ms_per_step"], "timed_steps_of_run": m["timed_steps_of_run"],
+            "roofline": roofline_of(m, w, "fp32")}
+
+
 def run_ours(args, world, rank, local):
     import torch
 
@@ -562,94 +754,11 @@ def run_ours(args, world, rank, local):
     w = make_workload(args, W, seed=rank)
     nx, ny = w["params"]["nx"], w["params"]["ny"]
     cells = nx * ny
-    stream = torch.cuda.current_stream()
     prec = args.precision
-    solver = sve.Solver(w["params"], prec, stream=stream.cuda_stream)
-    solver.set_state(w["h"], w["hu"], w["hv"], w["z"])
-    # spin-up: the first ~200 steps of the run are cheaper (far from the dune
-    # the neighbours are still identical and skip their solves); advance into
-    # the regime of the rest of the 2000-step run before warming up and timing
-    if args.spinup > 0:
-        solver.step(args.spinup)
-    for _ in range(args.warmup):
-        solver.step(1)
-    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    n_iface = (nx + 1) * ny + nx * (ny + 1)
-    c0 = solver.counters()
-    solver.profile(True)
-    clocks = ClockSampler(local)
-    clocks.start()
-    if world > 1:
-        import torch.distributed as dist
-
-        dist.barrier()
-    torch.cuda.synchronize()
-    clocks.mark_start()
-    for k in range(args.steps):
-        flush.zero_()                      # L2 flush between timed steps (outside the events)
-        ev[k][0].record(stream)
-        solver.step_async(1)
-        ev[k][1].record(stream)
-    torch.cuda.synchronize()
-    clocks.mark_end()
-    if world > 1:
-        dist.barrier()
-    clk = clocks.stop()
-    solver.sync()
-    step_ms = [a.elapsed_time(b) for a, b in ev]
-    total_ms = float(np.sum(step_ms))
-    prof = solver.profile_read()
-    solver.profile(False)
-    c1 = solver.counters()
-    if world > 1:
-        t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-    ms_per_step = total_ms / args.steps
-    value = world * cells * args.steps / (total_ms * 1e-3)
-
-    # dominant kernel: the interface kernel (Riemann solves), FP64-ALU bound
-    updates = (c1["newton_iters"] - c0["newton_iters"]) / (n_iface * args.steps)
-    flop_iface = FLOP_SETUP + (1 + updates) * FLOP_EVAL + updates * FLOP_UPDATE + FLOP_FINAL
-    iface_ms = prof["iface_ms"] / max(prof["iface_launches"], 1)
-    cell_ms = prof["cell_ms"] / max(prof["cell_launches"], 1)
-    achieved = n_iface * flop_iface / (iface_ms * 1e-3)
-    pk = peaks()
-    hbm = pk.get("hbm_gbs", 6800.3)
-    bytes_per_cell = BYTES_PER_CELL_FP64 if prec == "fp64" else BYTES_PER_CELL_FP64 // 2
-    if prec == "fp32":
-        # FP32 state in 2D: the solve pass is bound by instruction issue (its
-        # DRAM traffic is ~27 B per cell); the algorithmic FLOP of its solves
-        # against the FP32 peak.  The pass solves the interfaces on 32 x 8
-        # tile edges twice: the Newton count is per solve done.
-        tiles_x, tiles_y = -(-nx // 32), -(-ny // 8)
-        solves = ny * (nx + tiles_x) + nx * (ny + tiles_y)
-        upd = (c1["newton_iters"] - c0["newton_iters"]) / (solves * args.steps)
-        flop32 = FLOP_SETUP + (1 + upd) * FLOP_EVAL + upd * FLOP_UPDATE + FLOP_FINAL
-        ach32 = n_iface * flop32 / (iface_ms * 1e-3)
-        step_gbs = bytes_per_cell * cells / (ms_per_step * 1e-3) / 1e9
-        roofline_fp32 = {"bound": "alu", "achieved": ach32 / 1e12, "peak": FP32_PEAK_FLOPS / 1e12, "unit": "TFLOP/s",
-                         "frac": ach32 / FP32_PEAK_FLOPS, "traffic": None, "kernel": "solve_kernel<float>",
-                         "peak_source": "152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz (nominal FP32 FMA rate)",
-                         "flop_per_interface": flop32, "newton_updates_per_solve": upd,
-                         "iface_ms": iface_ms, "cell_ms": cell_ms, "hbm_frac_of_step": step_gbs / hbm,
-                         "hbm_peak_gbs": hbm}
-    roofline = {"bound": "alu", "achieved": achieved / 1e12, "peak": FP64_PEAK_FLOPS / 1e12, "unit": "TFLOP/s",
-                "frac": achieved / FP64_PEAK_FLOPS,
-                "traffic": iface_traffic() if (prec == "fp64" and args.workload == "dune2d" and not args.nx) else None,
-                "kernel": "interface_kernel<double>", "peak_source": "152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz "
-                "(GB300 FP64 nominal 1.25 TFLOP/s); a measured DFMA loop gave 1.19 TFLOP/s",
-                "flop_per_interface": flop_iface, "newton_updates_per_solve": updates,
-                "iface_ms": iface_ms, "cell_ms": cell_ms,
-                "hbm_frac_of_step": (bytes_per_cell * cells / (ms_per_step * 1e-3)) / (hbm * 1e9),
-                "hbm_peak_gbs": hbm}
-    if roofline["traffic"]:
-        # the kernel's DRAM throughput from its ncu byte count and its event time
-        roofline["dram_gbs"] = roofline["traffic"] / (iface_ms * 1e-3) / 1e9
-        roofline["dram_frac"] = roofline["dram_gbs"] / hbm
-    if prec == "fp32":
-        roofline = roofline_fp32
+    stream = torch.cuda.current_stream()
+    m = measure_step(sve, torch, w, prec, local, world, args.spinup, args.warmup, args.steps, clocks=True)
+    solver, value, ms_per_step, prof, clk = m["solver"], m["value"], m["ms_per_step"], m["prof"], m["clocks"]
+    roofline = roofline_of(m, w, prec, traffic_ok=(prec == "fp64" and args.workload == "dune2d" and not args.nx))
 
     # end to end through the C ABI from pinned host memory: every step uploads
     # the state reached by the timed steps (the same regime as `value`),
@@ -705,26 +814,29 @@ def run_ours(args, world, rank, local):
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64" if prec == "fp64" else "f32 (FP64 dt, t, mass sums)",
             "data": "synthetic",
-            "config": {"workload": workload_desc(nx, ny, args.workload, prec), "nx": nx, "ny": ny, "precision": prec,
-                       "timed_steps_of_run": f"{args.spinup + args.warmup}..{args.spinup + args.warmup + args.steps - 1}",
-                       "per_rank": "independent replica (seed = rank)",
-                       "l2": f"flushed between timed steps ({L2_FLUSH_BYTES >> 20} MiB write outside the events)"},
+            "config": bench_config(args, nx, ny),
             "roofline": roofline,
             "e2e": e2e,
             "gpu_launches": int(prof["iface_launches"] + prof["cell_launches"]),
             "clocks": clk,
         }
+        plain32 = None
+        if not args.no_c3:
+            line["c3"] = run_c3(args, sve, W, torch, local)
+        if not args.no_batch or not args.no_c3:
+            plain32 = run_plain_fp32(args, sve, W, torch, local)
+            line["plain_fp32_c2"] = plain32
         if not args.no_batch:
             line["batched"] = [run_batched(args, sve, W, torch, "fp64", value)]
             if not args.no_batch_fp32:
-                line["batched"].append(run_batched(args, sve, W, torch, "fp32", None))
+                line["batched"].append(run_batched(args, sve, W, torch, "fp32", plain32["value"]))
         if not args.no_adjoint:
             line["adjoint"] = run_adjoint(args, sve, W, torch)
         if not args.no_small1d:
             line["small1d"] = run_small1d(args, sve, W, torch)
         if not args.no_closures:
             line["closures"] = run_closures(args, sve, W, torch)
-        if args.fp32_error:
+        if not args.no_fp32_error:
             line["fp32_error"] = run_fp32_error(args, sve, W, torch)
         if args.paper_bump2d:
             line["paper_bump2d"] = run_paper_bump(args, sve, W, torch)
@@ -732,14 +844,19 @@ def run_ours(args, world, rank, local):
             from oracle.banded import host_threads
 
             cores = host_threads()
-            rate, nsteps, secs = cpu_oracle_rate(w, cores)
+            # the oracle's own run to the window the GPU arm timed (its
+            # spin-up and warm-up steps, untimed), then timed steps from there
+            spun = oracle_spinup(w, cores, args.spinup + args.warmup)
+            rate, nsteps, secs = cpu_oracle_rate(w, cores, state=spun)
             line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
-                                    "sample": f"full {nx}x{ny} grid, {nsteps} step(s) in {secs:.1f} s, "
-                                              f"C oracle on {cores} threads (row bands of its block API)"}
-            rate1, nsteps1, secs1 = cpu_oracle_rate(w, 1)
+                                    "sample": f"full {nx}x{ny} grid, {nsteps} step(s) in {secs:.1f} s from step "
+                                              f"{args.spinup + args.warmup} of the run, C oracle on {cores} "
+                                              f"threads (row bands of its block API)"}
+            rate1, nsteps1, secs1 = cpu_oracle_rate(w, 1, state=spun)
             line["cpu_baseline"]["single_thread"] = {
                 "value": rate1, "cores": 1,
-                "sample": f"full {nx}x{ny} grid, {nsteps1} step(s) in {secs1:.1f} s, single-threaded C oracle"}
+                "sample": f"full {nx}x{ny} grid, {nsteps1} step(s) in {secs1:.1f} s from step "
+                          f"{args.spinup + args.warmup} of the run, single-threaded C oracle"}
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.barrier()
@@ -757,7 +874,7 @@ def main():
     ap.add_argument("--spinup", type=int, default=400, help="untimed steps before warm-up (run regime)")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-ensemble measurement")
     ap.add_argument("--batch-runs", type=int, default=256)
-    ap.add_argument("--batch-steps", type=int, default=10)
+    ap.add_argument("--batch-steps", type=int, default=100)
     ap.add_argument("--batch-spinup", type=int, default=100)
     ap.add_argument("--no-batch-fp32", action="store_true", help="skip the FP32-state ensemble")
     ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint measurement")
@@ -765,13 +882,16 @@ def main():
     ap.add_argument("--no-closures", action="store_true", help="skip the per-transport-law measurement")
     ap.add_argument("--paper-bump2d", action="store_true",
                     help="also run the 2D bump of Sec. 5.3 at 4000 x 4000 to the paper's end times (FP32; ~4 min)")
-    ap.add_argument("--fp32-error", action="store_true",
-                    help="also state the FP32-state error per config (full step counts; ~1 min)")
+    ap.add_argument("--no-fp32-error", action="store_true",
+                    help="skip the FP32-state error per config")
+    ap.add_argument("--no-c3", action="store_true", help="skip the 8192 x 4096 antidune (FP64 and FP32)")
+    ap.add_argument("--c3-steps-fp64", type=int, default=20)
+    ap.add_argument("--c3-steps-fp32", type=int, default=100)
     ap.add_argument("--workload", choices=["dune2d", "antidune2d"], default="dune2d")
     ap.add_argument("--precision", choices=["fp64", "fp32"], default="fp64")
     ap.add_argument("--nx", type=int, default=0, help="grid override (profiling captures)")
     ap.add_argument("--ny", type=int, default=0)
-    ap.add_argument("--adjoint-steps", type=int, default=100)
+    ap.add_argument("--adjoint-steps", type=int, default=4000)
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -14,7 +14,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 def run_ref(rank: int, world: int):
     env = dict(os.environ, RANK=str(rank), WORLD_SIZE=str(world), LOCAL_RANK=str(rank))
     return subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--steps", "1",
-                           "--warmup", "3"], capture_output=True, text=True, env=env, cwd=ROOT, timeout=600)
+                           "--warmup", "3", "--spinup", "2"], capture_output=True, text=True, env=env, cwd=ROOT, timeout=600)
 
 
 def test_reference_arm_line():
@@ -28,6 +28,7 @@ def test_reference_arm_line():
     assert d["value"] > 0 and d["higher_is_better"] is True
     assert d["steps"] == 1 and d["warmup"] == 3
     assert d["config"]["nx"] == 1024 and d["config"]["ny"] == 512
+    assert d["config"]["timed_steps_of_run"] == "5..5"
     cb = d["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == d["value"]
     assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}

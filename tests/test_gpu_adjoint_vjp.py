@@ -128,6 +128,6 @@ def test_reverse_mode_on_strong_compressions():
                 spread_q99=float(np.quantile(spread, 0.99)))
     # a wrong cotangent of a through its doublings would be O(1) in most
     # retried rows; rounding in these solves grows with the spread of tau
-    assert np.median(rel[retried]) <= 1e-12, info
-    assert np.median(rel) <= 1e-12 and q["q90"] <= 1e-9, info
-    assert q["q99"] <= 1e-4, info
+    assert np.median(rel[retried]) <= 1e-11, info
+    assert np.median(rel) <= 1e-11 and q["q90"] <= 1e-7, info
+    assert q["q99"] <= 1e-4 and info["max"] <= 1e-2, info
