@@ -13,6 +13,7 @@
 #include "../../include/sve.h"
 #include "sve_device.cuh"
 #include "sve_fused.cuh"
+#include "sve_march.cuh"
 #include "sve_persist.cuh"
 #include "sve_handle.h"
 
@@ -147,18 +148,19 @@ void launch_step(sve_handle* h, cudaStream_t st, int fixed, cudaEvent_t* ev, con
   if (ev) cudaEventRecord(ev[2], st);
 }
 
-// FP32 state in 2D: the solve pass (fluctuations on chip, net fluctuation
-// per cell out, time step from the solves) and the in-place apply pass.
+// FP32 state in 2D: the solve pass (column strips marching over rows,
+// fluctuations in registers, net fluctuation per cell out, time step from
+// the solves) and the in-place apply pass.
 void launch_fused_step(sve_handle* h, cudaStream_t st, int fixed, cudaEvent_t* ev, const void* const* mirror) {
   sve::StateBuf<float> B;
   B.h = (float*)h->fields[0]; B.hu = (float*)h->fields[1]; B.hv = (float*)h->fields[2]; B.z = (float*)h->fields[3];
   const size_t ncell = (size_t)h->P.nx * (size_t)h->P.ny;
   sve::NetFluct<float> D;  // in the fluctuation planes of the two-kernel form (8 (nx+1) ny >= 4 nx ny floats)
   D.h = (float*)h->fx; D.hu = D.h + ncell; D.hv = D.hu + ncell; D.z = D.hv + ncell;
-  const int ntiles = h->fgx * h->fgy;
+  const sve::MarchShape& M = h->march;
   if (ev) cudaEventRecord(ev[0], st);
-  sve::solve_kernel<float><<<h->fgrid_solve, sve::kFThreads, 0, st>>>(h->P, B, D, h->sc, h->fixed, h->dtlog, fixed,
-                                                                      ntiles, h->fgx);
+  sve::march_kernel<float><<<M.blocks, sve::kMThreads, 0, st>>>(h->P, B, D, h->sc, h->fixed, h->dtlog, fixed,
+                                                                M.strips, M.rows, M.tasks);
   if (ev) cudaEventRecord(ev[1], st);
   sve::Mirror<float> out{};
   if (mirror) out = {(float*)mirror[0], (float*)mirror[1], (float*)mirror[2], (float*)mirror[3]};
@@ -504,14 +506,8 @@ int sve_create(const sve_config* cfg, sve_handle** out) {
   ok = ok && cudaMalloc(&h->fx, 8 * h->elem * (size_t)h->P.nfx) == cudaSuccess;
   ok = ok && cudaMalloc(&h->fy, 8 * h->elem * (size_t)(h->P.nfy > 0 ? h->P.nfy : 1)) == cudaSuccess;
   h->fused = cfg->precision == SVE_FP32 && cfg->dim == 2;
-  h->fgx = (h->P.nx + sve::kFTX - 1) / sve::kFTX;
-  h->fgy = (h->P.ny + sve::kFTY - 1) / sve::kFTY;
-  const size_t nbf = (size_t)h->fgx * (size_t)h->fgy;
   if (h->fused) {
-    int bs = 0;
-    ok = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bs, sve::solve_kernel<float>, sve::kFThreads, 0) ==
-         cudaSuccess;
-    h->fgrid_solve = (int)std::min<size_t>(nbf, (size_t)std::max(1, h->nsm * bs));
+    h->march = sve::march_shape(h->P, h->nsm);
     h->agx = (h->P.nx + sve::kAThreads - 1) / sve::kAThreads;
     h->agy = std::min(h->P.ny, std::max(1, (h->nsm * (2048 / sve::kAThreads) + h->agx - 1) / h->agx));
   }

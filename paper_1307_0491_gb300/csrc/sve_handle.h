@@ -7,6 +7,7 @@
 #include "../../include/sve.h"
 #include "sve_device.cuh"
 #include "sve_persist.cuh"
+#include "sve_march.cuh"
 
 struct sve_adjoint_rec;  // recorded forward run (sve_adjoint.cu)
 
@@ -32,10 +33,10 @@ struct sve_handle {
   double* fixed = nullptr;
   int fixed_cap = 0;
   cudaGraphExec_t graph[2] = {nullptr, nullptr};  // [fixed]
-  // FP32 state in 2D: the fused stencil (solve pass over 32 x 8 tiles, apply pass)
+  // FP32 state in 2D: the fused stencil (solve pass of strips marching over
+  // rows, apply pass)
   bool fused = false;
-  int fgx = 0, fgy = 0;    // tiles in x and y
-  int fgrid_solve = 0;     // resident blocks of the solve pass (grid stride over the tiles)
+  sve::MarchShape march = {};  // launch shape of the solve pass (sve_march.cuh)
   int agx = 0, agy = 0;    // apply pass grid (grid stride over columns and rows)
   int nt = 256;   // threads per block of the two-kernel step (32 or 256)
   int nsm = 152;  // SMs of the device

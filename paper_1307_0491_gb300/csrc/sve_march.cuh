@@ -1,0 +1,225 @@
+// sve_march.cuh -- the solve pass of the FP32-state 2D step as register
+// stencils marching along column strips.
+//
+// One warp owns a strip of 30 interior columns plus one halo column on each
+// side (lane l <-> column x0 - 1 + l) and walks a run of rows j0..j1-1.  Per
+// row it projects its cell of the next row (Pi = g h^2 / 2, Omega = q_b: the
+// lambda -> 0 projection of Sec. 3), solves the y-interface between the
+// current and the next row at its column and the x-interface on its left
+// (the left neighbour's projected cell comes by warp shuffles), takes the
+// right interface's A- from its right neighbour by a shuffle, and writes the
+// cell's net fluctuation dF = (A+ left + A- right) / dx + (A+ below + A- above)
+// / dy -- the below term carried in registers from the previous row.  No
+// shared memory and no block barrier: every warp is independent, the state
+// is read once per strip (the two halo columns are read by both neighbouring
+// strips, 1/15 more reads), and each interface is solved once except the
+// strip edges' x-interfaces (1/30 more) and one row of y-interfaces per run
+// of rows.  The extreme wave speeds come from the solves and the last block
+// turns them into the time step, as in the other solve passes.
+#pragma once
+#include "sve_fused.cuh"
+
+namespace sve {
+
+constexpr int kMCols = 30;    // interior columns per strip (32 lanes: 30 + two halo columns)
+constexpr int kMWarps = 4;    // warps per block
+constexpr int kMThreads = 32 * kMWarps;
+
+// Runs of rows per strip: as many rows per warp as keep about 16 warps per SM
+// busy (at least 8 rows, so that the one extra row of y-solves per run stays
+// small; at most 64).
+struct MarchShape {
+  int strips, rows, chunks;
+  long long tasks;
+  unsigned blocks;
+};
+
+inline MarchShape march_shape(const DevParams& P, int nsm) {
+  MarchShape M;
+  M.strips = (P.nx + kMCols - 1) / kMCols;
+  const long long want = 16LL * nsm;  // warps in flight
+  long long rows = ((long long)M.strips * P.ny + want - 1) / want;
+  rows = rows < 8 ? 8 : (rows > 64 ? 64 : rows);
+  M.rows = (int)rows;
+  M.chunks = (P.ny + M.rows - 1) / M.rows;
+  M.tasks = (long long)M.strips * M.chunks;
+  M.blocks = (unsigned)((M.tasks + kMWarps - 1) / kMWarps);
+  return M;
+}
+
+// Running maximum of non-negative wave speeds held as bit patterns (integer
+// order = IEEE order for them): 32-bit in FP32, 64-bit in FP64; the warp
+// maximum as the double value's bit pattern.
+template <typename T> struct SpeedMax;
+template <> struct SpeedMax<float> {
+  unsigned v = 0u;
+  __device__ __forceinline__ void add(float s) { v = max(v, __float_as_uint(s)); }
+  __device__ __forceinline__ unsigned long long warp_bits() const {
+    return (unsigned long long)__double_as_longlong((double)__uint_as_float(__reduce_max_sync(0xffffffffu, v)));
+  }
+};
+template <> struct SpeedMax<double> {
+  unsigned long long v = 0ull;
+  __device__ __forceinline__ void add(double s) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(s);
+    v = b > v ? b : v;
+  }
+  __device__ __forceinline__ unsigned long long warp_bits() const {
+    unsigned long long b = v;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const unsigned long long ob = __shfl_xor_sync(0xffffffffu, b, o);
+      b = ob > b ? ob : b;
+    }
+    return b;
+  }
+};
+
+// Projected cell of column c, row j of the padded state (c in [-1, nx], j in
+// [-1, ny]); a unit state outside (never solved with).
+template <typename T>
+__device__ __forceinline__ void march_project(const DevParams& P, const StateBuf<T>& B, int c, int j, bool in,
+                                              SCell<T>& s) {
+  if (in) {
+    const long long e = ext_index(P, c, j);
+    project_into(P, B.h[e], B.hu[e], B.hv[e], B.z[e], s);
+  } else {
+    project_into(P, T(1), T(0), T(0), T(0), s);
+  }
+}
+
+// The x-frame cell of the lane below (lane - 1) by shuffles.
+template <typename T>
+__device__ __forceinline__ Cell<T> left_cell(const SCell<T>& s) {
+  Cell<T> c;
+  const unsigned m = 0xffffffffu;
+  c.H = __shfl_up_sync(m, s.H, 1);
+  c.Hn = __shfl_up_sync(m, s.Hu, 1);
+  c.Ht = __shfl_up_sync(m, s.Hv, 1);
+  c.Z = __shfl_up_sync(m, s.Z, 1);
+  c.tau = __shfl_up_sync(m, s.tau, 1);
+  c.un = __shfl_up_sync(m, s.u, 1);
+  c.ut = __shfl_up_sync(m, s.v, 1);
+  c.Pi = __shfl_up_sync(m, s.Pi, 1);
+  c.Om = __shfl_up_sync(m, s.omx, 1);
+  c.ca = __shfl_up_sync(m, s.ca, 1);
+  c.cb = __shfl_up_sync(m, s.cbx, 1);
+  return c;
+}
+
+// Five blocks per SM (<= 102 registers a thread, no spills): 20 warps per SM
+// measured 5 % faster than the unconstrained 123 registers (16 warps) and
+// than six blocks (<= 85 registers) on the 8192 x 4096 antidune.
+template <typename T>
+__global__ void __launch_bounds__(kMThreads, 5) march_kernel(DevParams P, StateBuf<T> B, NetFluct<T> D,
+                                                          DevScalars* sc, const double* fixed_dts, double* dtlog,
+                                                          int fixed, int strips, int rows, long long ntasks) {
+  __shared__ unsigned long long s_sx, s_sy;
+  __shared__ unsigned int s_its, s_warps, s_halv, s_raised, s_retry;
+  if (threadIdx.x == 0) { s_sx = 0ull; s_sy = 0ull; s_its = 0u; s_warps = 0u; s_halv = 0u; s_raised = 0u; s_retry = 0u; }
+  __syncthreads();
+  const int lane = threadIdx.x & 31;
+  const long long task = (long long)blockIdx.x * kMWarps + (threadIdx.x >> 5);
+  int fail = 0, iters = 0;
+  unsigned int nraised = 0u, nretry = 0u, nhalv = 0u;
+  SpeedMax<T> mx, my;  // extreme wave speeds of the x- and y-solves
+  if (task < ntasks) {
+    const int strip = (int)(task % strips), chunk = (int)(task / strips);
+    const int c = strip * kMCols - 1 + lane;          // this lane's column
+    const bool col_in = c <= P.nx;                    // inside the padded grid
+    const bool interior = lane >= 1 && lane <= kMCols && c < P.nx;  // a cell this strip updates
+    const bool xface = lane >= 1 && col_in;           // the x-interface c - 1/2 exists
+    const int j0 = chunk * rows, j1 = min(j0 + rows, P.ny);
+    const T idx = par<T>(P.inv_dx, (float)P.inv_dx), idy = par<T>(P.inv_dy, (float)P.inv_dy);
+    SCell<T> cur, nxt;
+    T apb[4] = {T(0), T(0), T(0), T(0)};  // A+ of the y-interface below (j - 1/2), y frame
+    march_project(P, B, c, j0 - 1, col_in, cur);
+    // j = j0 - 1 only solves the y-interface j0 - 1/2 (its A+ enters row j0)
+    for (int j = j0 - 1; j < j1; ++j) {
+      march_project(P, B, c, j + 1, col_in, nxt);
+      const bool row = j >= j0;  // row j is updated by this task (warp-uniform)
+      // the y-interface j + 1/2 at this column
+      T amu[4] = {T(0), T(0), T(0), T(0)}, apu[4] = {T(0), T(0), T(0), T(0)};
+      if (interior) {
+        T s = T(0);
+        int its = 0, br = 0;
+        if (!riemann_solve(P, frame_cell(cur, true), frame_cell(nxt, true), amu, apu, s, its, br)) fail = 1;
+        my.add(s);
+        iters += its;
+        nraised += branch_raised(br);
+        nretry += branch_retries(br);
+        nhalv += branch_halvings(br);
+      }
+      if (row) {
+        // the x-interface c - 1/2 of row j; its A- goes to the lane below
+        const Cell<T> L = left_cell(cur);
+        T amx[4] = {T(0), T(0), T(0), T(0)}, apx[4] = {T(0), T(0), T(0), T(0)};
+        if (xface) {
+          T s = T(0);
+          int its = 0, br = 0;
+          if (!riemann_solve(P, L, frame_cell(cur, false), amx, apx, s, its, br)) fail = 1;
+          mx.add(s);
+          iters += its;
+          nraised += branch_raised(br);
+          nretry += branch_retries(br);
+          nhalv += branch_halvings(br);
+        }
+        T amr[4];  // A- of the x-interface c + 1/2 (the right neighbour's)
+#pragma unroll
+        for (int k = 0; k < 4; ++k) amr[k] = __shfl_down_sync(0xffffffffu, amx[k], 1);
+        if (interior) {
+          // the y fluctuations are in the y frame: (H, Hv, Hu, Z)
+          const long long o = (long long)j * P.nx + c;
+          D.h[o] = (apx[0] + amr[0]) * idx + (apb[0] + amu[0]) * idy;
+          D.hu[o] = (apx[1] + amr[1]) * idx + (apb[2] + amu[2]) * idy;
+          D.hv[o] = (apx[2] + amr[2]) * idx + (apb[1] + amu[1]) * idy;
+          D.z[o] = (apx[3] + amr[3]) * idx + (apb[3] + amu[3]) * idy;
+        }
+      }
+#pragma unroll
+      for (int k = 0; k < 4; ++k) apb[k] = apu[k];
+      cur = nxt;
+    }
+  }
+  if (fail) atomicOr(&sc->status, ST_RIEMANN);
+  // tallies: warp reductions, shared-memory atomics, the block's last warp
+  // folds them into the step's running maxima, the last block takes dt
+  const unsigned long long wx = mx.warp_bits(), wy = my.warp_bits();
+  iters = __reduce_add_sync(0xffffffffu, iters);
+  nraised = __reduce_add_sync(0xffffffffu, nraised);
+  nhalv = __reduce_add_sync(0xffffffffu, nhalv);
+  nretry = __reduce_add_sync(0xffffffffu, nretry);
+  if (lane != 0) return;
+  atomicMax(&s_sx, wx);
+  atomicMax(&s_sy, wy);
+  atomicAdd(&s_its, (unsigned int)iters);
+  if (nraised | nretry | nhalv) { atomicAdd(&s_raised, nraised); atomicAdd(&s_retry, nretry); atomicAdd(&s_halv, nhalv); }
+  __threadfence_block();
+  if (atomicAdd(&s_warps, 1u) != kMWarps - 1) return;
+  __threadfence_block();
+  const unsigned long long bx = atomicMax(&s_sx, 0ull), by = atomicMax(&s_sy, 0ull);
+  atomicAdd(&sc->newton_iters, (unsigned long long)atomicAdd(&s_its, 0u));
+  const unsigned br = atomicAdd(&s_raised, 0u), bt = atomicAdd(&s_retry, 0u), bh = atomicAdd(&s_halv, 0u);
+  if (br) atomicAdd(&sc->raised, (unsigned long long)br);
+  if (bt) atomicAdd(&sc->retries, (unsigned long long)bt);
+  if (bh) atomicAdd(&sc->halvings, (unsigned long long)bh);
+  atomicMax(&sc->smax_bits[0], bx);
+  atomicMax(&sc->smax_bits[1], by);
+  __threadfence();
+  if (atomicAdd(&sc->done_iface, 1u) != gridDim.x - 1) return;
+  __threadfence();
+  const double sx = __longlong_as_double((long long)atomicExch(&sc->smax_bits[0], 0ull));
+  const double sy = __longlong_as_double((long long)atomicExch(&sc->smax_bits[1], 0ull));
+  const int cs = sc->call_step;
+  double dt;
+  if (fixed) dt = fixed_dts[cs];
+  else dt = P.cfl / (sx / P.dx + sy / P.dy);
+  if (!(dt > 0.0) || !isfinite(dt)) { atomicOr(&sc->status, ST_DT); dt = 0.0; }
+  sc->dt = dt;
+  sc->Sx = sx;
+  sc->Sy = sy;
+  dtlog[cs] = dt;
+  sc->done_iface = 0u;
+}
+
+}  // namespace sve

@@ -13,7 +13,7 @@
 //
 // The kernels are those of the regular entry points for the configuration:
 // the two-kernel step (interface_kernel + cell_kernel) in FP64 and in 1D,
-// the fused FP32 stencil (solve_kernel + apply_kernel) for the FP32 state in
+// the fused FP32 stencil (march_kernel + apply_kernel) for the FP32 state in
 // 2D.
 //
 // The array is a static __device__ object: it exists on every GPU that loads
@@ -29,6 +29,7 @@
 #include "../../include/sve.h"
 #include "sve_device.cuh"
 #include "sve_fused.cuh"
+#include "sve_march.cuh"
 
 // Parameter checks, derived constants and status codes are the ones the
 // regular entry points use (defined in sve_api.cu).
@@ -48,7 +49,6 @@ constexpr int kDtlogEntries = 1024;  // steps per chunk (the per-step dt log liv
 std::mutex g_setup_mutex;
 unsigned char* g_scratch_ptr[kMaxDevices] = {};
 int g_nsm[kMaxDevices] = {};          // SMs of the device
-int g_solve_per_sm[kMaxDevices] = {};  // resident blocks of the fused solve kernel per SM
 
 // Device address of the scratch on the current device, and the launch facts
 // the fused FP32 step needs, looked up once per device (with that device
@@ -61,15 +61,10 @@ int device_setup(int* dev_out) {
   if (!g_scratch_ptr[dev]) {
     void* p = nullptr;
     if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return SVE_ERR_CUDA;
-    int nsm = 0, bs = 0;
+    int nsm = 0;
     if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || nsm < 1)
       return SVE_ERR_CUDA;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bs, sve::solve_kernel<float>, sve::kFThreads, 0) !=
-            cudaSuccess ||
-        bs < 1)
-      return SVE_ERR_CUDA;
     g_nsm[dev] = nsm;
-    g_solve_per_sm[dev] = bs;
     g_scratch_ptr[dev] = (unsigned char*)p;
   }
   *dev_out = dev;
@@ -79,17 +74,17 @@ int device_setup(int* dev_out) {
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 // Launch shape of one call: the two-kernel step (blocks of the interface and
-// cell kernels) or the fused FP32 stencil (solve blocks over the tiles, the
+// cell kernels) or the fused FP32 stencil (the strips of the solve pass, the
 // apply pass's 2D grid); nmpart = block partials the largest pass writes.
 struct Shape {
   bool fused;
   int nb_iface, nb_cell;                 // two-kernel step
-  int ntiles, tiles_x, solve_blocks;     // fused: tiles and resident solve blocks
+  sve::MarchShape march;                 // fused: solve pass
   int agx, agy;                          // fused: apply grid
   size_t nmpart;
 };
 
-Shape shape_for(const sve::DevParams& P, bool fused, int nsm, int solve_per_sm) {
+Shape shape_for(const sve::DevParams& P, bool fused, int nsm) {
   Shape S = {};
   S.fused = fused;
   const size_t init_blocks = (size_t)sve::cell_blocks(P, sve::kThreads);
@@ -98,9 +93,7 @@ Shape shape_for(const sve::DevParams& P, bool fused, int nsm, int solve_per_sm) 
     S.nb_cell = (int)sve::cell_blocks(P, sve::kThreadsStep);
     S.nmpart = std::max(init_blocks, (size_t)S.nb_cell);
   } else {
-    S.tiles_x = (P.nx + sve::kFTX - 1) / sve::kFTX;
-    S.ntiles = S.tiles_x * ((P.ny + sve::kFTY - 1) / sve::kFTY);
-    S.solve_blocks = std::min(S.ntiles, nsm * solve_per_sm);
+    S.march = sve::march_shape(P, nsm);
     S.agx = (P.nx + sve::kAThreads - 1) / sve::kAThreads;
     S.agy = std::min(P.ny, std::max(1, (nsm * (2048 / sve::kAThreads) + S.agx - 1) / S.agx));
     S.nmpart = std::max(init_blocks, (size_t)S.agx * (size_t)S.agy);
@@ -197,8 +190,8 @@ int run(const sve::DevParams& P, unsigned char* base, const Layout& L, const Sha
     for (int s = 0; s < chunk; ++s) {
       if constexpr (sizeof(T) == 4) {
         if (SH.fused) {
-          sve::solve_kernel<T><<<SH.solve_blocks, sve::kFThreads, 0, st>>>(P, B, D, sc, dtlog, dtlog, 0, SH.ntiles,
-                                                                            SH.tiles_x);
+          sve::march_kernel<T><<<SH.march.blocks, sve::kMThreads, 0, st>>>(P, B, D, sc, dtlog, dtlog, 0, SH.march.strips,
+                                                                          SH.march.rows, SH.march.tasks);
           sve::apply_kernel<T><<<dim3(SH.agx, SH.agy), sve::kAThreads, 0, st>>>(P, B, D, sc, mpart,
                                                                                 sve::Mirror<T>{});
           continue;
@@ -240,7 +233,7 @@ extern "C" int sve_step_noalloc(const sve_config* cfg, void* depth, void* hu, vo
   rc = device_setup(&dev);
   if (rc) return rc;
   const bool fused = cfg->precision == SVE_FP32 && cfg->dim == 2;
-  const Shape SH = shape_for(P, fused, g_nsm[dev], g_solve_per_sm[dev]);
+  const Shape SH = shape_for(P, fused, g_nsm[dev]);
   const size_t elem = cfg->precision == SVE_FP64 ? 8 : 4;
   const Layout L = layout_for(P, elem, SH);
   if (L.total > (size_t)SVE_NOALLOC_SCRATCH_BYTES) return SVE_ERR_NOALLOC_SIZE;
