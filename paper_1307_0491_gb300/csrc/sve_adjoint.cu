@@ -52,6 +52,10 @@ struct sve_adjoint_rec {
   size_t seg_cap = 0;
   double* segc = nullptr;           // their convected (pre-friction) interior states, 4 planes each
   size_t segc_cap = 0;
+  double* roots = nullptr;          // their interfaces' Newton roots p* (x then y interfaces, one plane a step)
+  size_t roots_cap = 0;
+  unsigned char* rtry = nullptr;    // and the doublings of a of those solves
+  size_t rtry_cap = 0;
   double* lam = nullptr;            // 2 x 4 interior planes (current, next)
   double* mu = nullptr;             // 4 interior planes
   double* gpart = nullptr;          // per-block parameter partials
@@ -178,8 +182,9 @@ __global__ void __launch_bounds__(kAdjThreads) adj_friction_kernel(DevParams P, 
 template <bool GRASS>
 __global__ void __launch_bounds__(kAdjThreads) adj_interface_kernel(DevParams P, DevState<double> S,
                                                                     const double* mu, double dt, double A,
-                                                                    double m, double* gpart, double* gacc,
-                                                                    unsigned int* done) {
+                                                                    double m, const double* roots,
+                                                                    const unsigned char* rtry, double* gpart,
+                                                                    double* gacc, unsigned int* done) {
   __shared__ double sh[kAdjThreads / 32];
   const long long ncell = (long long)P.nx * P.ny;
   const long long nall = P.nfx + P.nfy;
@@ -230,7 +235,9 @@ __global__ void __launch_bounds__(kAdjThreads) adj_interface_kernel(DevParams P,
       double ub[8] = {0, 0, 0, 0, 0, 0, 0, 0}, Ab = 0.0, mb = 0.0, Kb = 0.0;
       // (the forward run solved this interface at this state; a failure
       // here leaves its contribution at zero, as the value pass did before)
-      sve::interface_vjp<GRASS>(P, u, A, m, Amb, Apb, ub, Ab, mb, Kb);
+      // the forward solve's root (kept by the recording or the segment's
+      // recompute) spares the value pass its Newton iteration
+      sve::interface_vjp<GRASS>(P, u, A, m, Amb, Apb, ub, Ab, mb, Kb, roots[idx], (int)rtry[idx]);
 #pragma unroll
       for (int q = 0; q < 8; ++q) out[q] = ub[q];
       // Grass: the A_g and m_g gradients; Shields laws: the friction
@@ -358,11 +365,12 @@ int load_state(sve_handle* h, const double* src) {
   return SVE_OK;
 }
 
-int grow(double** p, size_t* cap, size_t n) {
+template <typename E>
+int grow(E** p, size_t* cap, size_t n) {
   if (*cap >= n) return SVE_OK;
   if (*p) cudaFree(*p);
   *p = nullptr;
-  if (cudaMalloc(p, sizeof(double) * n) != cudaSuccess) return SVE_ERR_OOM;
+  if (cudaMalloc(p, sizeof(E) * n) != cudaSuccess) return SVE_ERR_OOM;
   *cap = n;
   return SVE_OK;
 }
@@ -372,6 +380,8 @@ void free_rec(sve_adjoint_rec* r) {
   for (double* c : r->checkpoints) cudaFree(c);
   if (r->seg) cudaFree(r->seg);
   if (r->segc) cudaFree(r->segc);
+  if (r->roots) cudaFree(r->roots);
+  if (r->rtry) cudaFree(r->rtry);
   if (r->lam) cudaFree(r->lam);
   if (r->mu) cudaFree(r->mu);
   if (r->gpart) cudaFree(r->gpart);
@@ -383,8 +393,10 @@ void free_rec(sve_adjoint_rec* r) {
 // One forward step with the handle's kernels: of size dt (fixed-dt mode),
 // or with cfl set of the CFL size, logged in the handle's time-step log at
 // the call's step counter.  With conv, the step's convected (pre-friction)
-// interior state is kept there.
-int forward_step(sve_handle* h, double dt, double* conv = nullptr, bool cfl = false) {
+// interior state is kept there; with roots, each interface's Newton root
+// and the doublings of a of its solve (roots, rtry).
+int forward_step(sve_handle* h, double dt, double* conv = nullptr, bool cfl = false, double* roots = nullptr,
+                 unsigned char* rtry = nullptr) {
   if (!cfl) {
     ADJ_TRY(cudaMemcpyAsync(h->fixed, &dt, sizeof(double), cudaMemcpyHostToDevice, h->stream));
     ADJ_TRY(cudaMemsetAsync(&h->sc->call_step, 0, sizeof(int), h->stream));
@@ -392,8 +404,12 @@ int forward_step(sve_handle* h, double dt, double* conv = nullptr, bool cfl = fa
   DevState<double> S = state_of<double>(h);
   const unsigned nbi = (unsigned)sve::iface_blocks(h->P, sve::kThreadsStep);
   const unsigned nbc = (unsigned)sve::cell_blocks(h->P, sve::kThreadsStep);
-  sve::interface_kernel<double><<<nbi, sve::kThreadsStep, 0, h->stream>>>(h->P, S, h->sc, h->fixed, h->dtlog,
-                                                                          cfl ? 0 : 1);
+  if (roots)
+    sve::interface_kernel<double, sve::kThreadsStep, true><<<nbi, sve::kThreadsStep, 0, h->stream>>>(
+        h->P, S, h->sc, h->fixed, h->dtlog, cfl ? 0 : 1, roots, rtry);
+  else
+    sve::interface_kernel<double><<<nbi, sve::kThreadsStep, 0, h->stream>>>(h->P, S, h->sc, h->fixed, h->dtlog,
+                                                                            cfl ? 0 : 1);
   if (conv) {
     const long long ncell = (long long)h->P.nx * h->P.ny;
     convect_save_kernel<<<(unsigned)((ncell + kAdjThreads - 1) / kAdjThreads), kAdjThreads, 0, h->stream>>>(
@@ -437,7 +453,9 @@ int sve_record_forward(sve_handle* h, int nsteps, int checkpoint_every) {
   if (checkpoint_every <= 0) {
     size_t free_b = 0, total_b = 0;
     ADJ_TRY(cudaMemGetInfo(&free_b, &total_b));
-    const double need = (double)sizeof(double) * ((double)n + 4.0 * (double)ncell) * (double)nsteps;
+    const double nf = (double)(h->P.nfx + h->P.nfy);
+    const double need =
+        ((double)sizeof(double) * ((double)n + 4.0 * (double)ncell + nf) + nf) * (double)nsteps;
     r->stored = need <= 0.5 * (double)free_b;
   }
   if (r->stored) {
@@ -448,11 +466,16 @@ int sve_record_forward(sve_handle* h, int nsteps, int checkpoint_every) {
     if (!rc) rc = save_state(h, c);
     if (!rc) rc = grow(&r->seg, &r->seg_cap, n * (size_t)nsteps);
     if (!rc) rc = grow(&r->segc, &r->segc_cap, 4 * (size_t)ncell * (size_t)nsteps);
+    const size_t nf = (size_t)(h->P.nfx + h->P.nfy);
+    if (!rc) rc = grow(&r->roots, &r->roots_cap, nf * (size_t)nsteps);
+    if (!rc) rc = grow(&r->rtry, &r->rtry_cap, nf * (size_t)nsteps);
     if (!rc) rc = sve_internal_reserve_dtlog(h, nsteps);
     if (!rc && cudaMemsetAsync(&h->sc->call_step, 0, sizeof(int), h->stream) != cudaSuccess) rc = SVE_ERR_CUDA;
     for (int s = 0; s < nsteps && !rc; ++s) {
       rc = save_state(h, r->seg + (size_t)s * n);
-      if (!rc) rc = forward_step(h, 0.0, r->segc + (size_t)s * 4 * (size_t)ncell, true);
+      if (!rc)
+        rc = forward_step(h, 0.0, r->segc + (size_t)s * 4 * (size_t)ncell, true, r->roots + (size_t)s * nf,
+                          r->rtry + (size_t)s * nf);
     }
     if (!rc) rc = status_of(h);
     if (!rc && cudaMemcpy(r->dts.data(), h->dtlog, sizeof(double) * (size_t)nsteps, cudaMemcpyDeviceToHost) !=
@@ -505,6 +528,11 @@ int sve_adjoint(sve_handle* h, const void* lam_h, const void* lam_hu, const void
   if (rc) return rc;
   rc = grow(&r->segc, &r->segc_cap, 4 * (size_t)ncell * (size_t)r->every);
   if (rc) return rc;
+  const size_t nf = (size_t)(P.nfx + P.nfy);
+  rc = grow(&r->roots, &r->roots_cap, nf * (size_t)r->every);
+  if (rc) return rc;
+  rc = grow(&r->rtry, &r->rtry_cap, nf * (size_t)r->every);
+  if (rc) return rc;
   double* lam = r->lam;             // lambda^{n+1}
   double* lam_next = r->lam + 4 * ncell;
   ADJ_TRY(cudaMemsetAsync(r->gacc, 0, sizeof(double) * 4, h->stream));
@@ -531,7 +559,9 @@ int sve_adjoint(sve_handle* h, const void* lam_h, const void* lam_hu, const void
       sve::init_kernel<double><<<nbc, sve::kThreads, 0, h->stream>>>(P, S, h->sc, h->mpart);
       for (int s = 0; s < len; ++s) {
         rc = save_state(h, r->seg + (size_t)s * nst);
-        if (!rc) rc = forward_step(h, r->dts[n0 + s], r->segc + (size_t)s * 4 * (size_t)ncell);
+        if (!rc)
+          rc = forward_step(h, r->dts[n0 + s], r->segc + (size_t)s * 4 * (size_t)ncell, false,
+                            r->roots + (size_t)s * nf, r->rtry + (size_t)s * nf);
         if (rc) return rc;
       }
     }
@@ -543,12 +573,14 @@ int sve_adjoint(sve_handle* h, const void* lam_h, const void* lam_hu, const void
       if (rc) return rc;
       adj_friction_kernel<<<nb_c, kAdjThreads, 0, h->stream>>>(P, r->segc + (size_t)s * 4 * (size_t)ncell, lam,
                                                               r->mu, dt, r->gpart, r->gacc, r->done);
+      const double* roots = r->roots + (size_t)s * nf;
+      const unsigned char* rtry = r->rtry + (size_t)s * nf;
       if (P.bedload == 0)
         adj_interface_kernel<true><<<nb_if, kAdjThreads, 0, h->stream>>>(P, S, r->mu, dt, h->cfg.A_g, h->cfg.m_g,
-                                                                         r->gpart, r->gacc, r->done);
+                                                                         roots, rtry, r->gpart, r->gacc, r->done);
       else
         adj_interface_kernel<false><<<nb_if, kAdjThreads, 0, h->stream>>>(P, S, r->mu, dt, h->cfg.A_g, h->cfg.m_g,
-                                                                          r->gpart, r->gacc, r->done);
+                                                                          roots, rtry, r->gpart, r->gacc, r->done);
       adj_gather_kernel<<<nb_c, kAdjThreads, 0, h->stream>>>(P, S, r->mu, lam_next);
       if (cudaGetLastError() != cudaSuccess) return SVE_ERR_CUDA;
       double* t = lam;

@@ -405,13 +405,16 @@ __device__ __forceinline__ void newton_eval_bar(const NewtonConst<double>& c, co
 // Product of the transposed Jacobian of one interface's fluctuations with
 // the cotangents Amb (of A-) and Apb (of A+), added to ub[0..7] (left then
 // right state, frame order), Ab, mb (A_g, m_g).  u, A, m: as jac_pass.  The
-// value pass solves for the root as the step does; false if it fails.
+// value pass solves for the root as the step does (false if it fails), or,
+// given the root p_root > 0 and the doublings of a (retries_in) that the
+// forward solve of this interface at this state kept, evaluates the states
+// and F' there once instead of iterating.
 // GRASS: the Grass law (else a Shields-parameter law), compiled separately
 // to keep each form's registers.
 template <bool GRASS = true>
 __device__ __forceinline__ bool interface_vjp(const DevParams& P, const double u[8], double A, double m,
                                               const double Amb[4], const double Apb[4], double ub[8], double& Ab,
-                                              double& mb, double& Kb) {
+                                              double& mb, double& Kb, double p_root = 0.0, int retries_in = 0) {
   // ---- value pass
   ProjRec rL, rR;
   constexpr bool grass = GRASS;
@@ -440,19 +443,30 @@ __device__ __forceinline__ bool interface_vjp(const DevParams& P, const double u
   double pstar;
   NewtonEval<double> e;
   int retries = 0;
-  for (;; ++retries) {
-    double ip0;
-    pstar = newton_setup(P, L, R, a, b, c, &ip0);
-    newton_eval_ip(pstar, ip0, c, L, R, e);
-    int its = 0;
-    if (newton_loop(c, L, R, pstar, e, P.newton_maxit, fmax(P.newton_tol, 16.0 * 2.220446049250313e-16), its) &&
-        newton_positive(e))
-      break;
-    if (retries == kARetries) return false;
-    a = 2.0 * a;
+  double Fp;
+  if (p_root > 0.0) {
+    // the forward solve's root: the states and F' there, one evaluation
+    retries = retries_in;
+    for (int k = 0; k < retries; ++k) a = 2.0 * a;
+    newton_setup(P, L, R, a, b, c);
+    pstar = p_root;
+    newton_eval(pstar, c, L, R, e);
+    Fp = newton_deriv(c, e);
+  } else {
+    for (;; ++retries) {
+      double ip0;
+      pstar = newton_setup(P, L, R, a, b, c, &ip0);
+      newton_eval_ip(pstar, ip0, c, L, R, e);
+      int its = 0;
+      if (newton_loop(c, L, R, pstar, e, P.newton_maxit, fmax(P.newton_tol, 16.0 * 2.220446049250313e-16), its) &&
+          newton_positive(e))
+        break;
+      if (retries == kARetries) return false;
+      a = 2.0 * a;
+    }
+    Fp = newton_deriv(c, e);
+    newton_eval(pstar, c, L, R, e);  // the states at the root, by a full evaluation
   }
-  const double Fp = newton_deriv(c, e);
-  newton_eval(pstar, c, L, R, e);  // the states at the root, by a full evaluation
   // fan (as fan_fluctuations, keeping the branches)
   const double lam1 = L.un - a * L.tau, lam5 = R.un + a * R.tau;
   const double us = e.u1 + b * (e.tau2 - e.tau1);

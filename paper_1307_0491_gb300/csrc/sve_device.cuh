@@ -495,9 +495,9 @@ template <> __device__ __forceinline__ float newton_floor<float>() { return 64.0
 template <typename T>
 __device__ __forceinline__ bool newton_root(const DevParams& P, const NewtonConst<T>& c, const Cell<T>& L,
                                             const Cell<T>& R, T p0, T ip0, NewtonEval<T>& e, int& iters,
-                                            int& halv) {
+                                            int& halv, T& p) {
   const T tol = tmax(par<T>(P.newton_tol, P.f.newton_tol), newton_floor<T>());
-  T p = p0;
+  p = p0;
   newton_eval_ip(p, ip0, c, L, R, e);
   return newton_loop(c, L, R, p, e, P.newton_maxit, tol, iters, halv);
 }
@@ -662,10 +662,11 @@ constexpr int kARetries = 3;
 
 // iters receives the number of Newton updates (0 for identical states);
 // branch the safeguards taken (branch_raised, _retries, _halvings); smax the
-// extreme wave speed max(|lambda1|, |lambda5|) with the celerity a used.
+// extreme wave speed max(|lambda1|, |lambda5|) with the celerity a used;
+// pstar (if given) the root p = tau1 + tau4 reached (0 for identical states).
 template <typename T>
 __device__ bool riemann_solve(const DevParams& P, const Cell<T>& L, const Cell<T>& R, T Am[4], T Ap[4], T& smax,
-                              int& iters, int& branch) {
+                              int& iters, int& branch, T* pstar = nullptr) {
   iters = 0;
   T a, b;
   const bool raised = celerities(P, L, R, a, b);
@@ -673,18 +674,20 @@ __device__ bool riemann_solve(const DevParams& P, const Cell<T>& L, const Cell<T
   smax = nnmax(absbits(L.un - a * L.tau), absbits(R.un + a * R.tau));
 #pragma unroll
   for (int c = 0; c < 4; ++c) { Am[c] = T(0); Ap[c] = T(0); }
+  if (pstar) *pstar = T(0);
   if (same_bits(L.H, R.H) && same_bits(L.Hn, R.Hn) && same_bits(L.Ht, R.Ht) && same_bits(L.Z, R.Z)) return true;
   NewtonConst<T> c;
   NewtonEval<T> e;
   int halv = 0, retries = 0;
   bool ok;
+  T p;
   // where the celerities admit no root with positive tau_k, a is doubled and
   // the iteration restarted (at most kARetries times; one loop, so that the
   // common single pass costs no extra registers)
   for (;;) {
     T ip0;
     const T p0 = newton_setup(P, L, R, a, b, c, &ip0);
-    ok = newton_root(P, c, L, R, p0, ip0, e, iters, halv) && newton_positive(e);
+    ok = newton_root(P, c, L, R, p0, ip0, e, iters, halv, p) && newton_positive(e);
     if (ok || retries == kARetries) break;
     ++retries;
     a = T(2) * a;
@@ -692,6 +695,7 @@ __device__ bool riemann_solve(const DevParams& P, const Cell<T>& L, const Cell<T
   if (retries) smax = nnmax(absbits(L.un - a * L.tau), absbits(R.un + a * R.tau));
   branch += 2 * retries + 8 * halv;
   if (!ok) return false;
+  if (pstar) *pstar = p;
   fan_fluctuations(P, L, R, c, e, Am, Ap);
   return true;
 }
@@ -867,7 +871,7 @@ __device__ __forceinline__ Cell<T> load_cell(const DevState<T>& S, long long e, 
 // Newton updates; false if the solve failed (fluctuations zero then).
 template <typename T>
 __device__ __forceinline__ bool interface_item(const DevParams& P, const DevState<T>& S, bool ydir, long long k,
-                                               double& smax, int& iters, int& branch) {
+                                               double& smax, int& iters, int& branch, T* pstar = nullptr) {
   T Am[4], Ap[4], s;
   bool ok;
   if (!ydir) {
@@ -876,7 +880,7 @@ __device__ __forceinline__ bool interface_item(const DevParams& P, const DevStat
     const long long eR = ext_index(P, i, row);
     const Cell<T> L = load_cell(S, eR - 1, false);
     const Cell<T> R = load_cell(S, eR, false);
-    ok = riemann_solve(P, L, R, Am, Ap, s, iters, branch);
+    ok = riemann_solve(P, L, R, Am, Ap, s, iters, branch, pstar);
 #pragma unroll
     for (int c = 0; c < 4; ++c) { S.fx[c * P.nfx + k] = Am[c]; S.fx[(4 + c) * P.nfx + k] = Ap[c]; }
   } else {
@@ -885,7 +889,7 @@ __device__ __forceinline__ bool interface_item(const DevParams& P, const DevStat
     const long long eR = ext_index(P, i, row);
     const Cell<T> L = load_cell(S, eR - P.ex, true);
     const Cell<T> R = load_cell(S, eR, true);
-    ok = riemann_solve(P, L, R, Am, Ap, s, iters, branch);
+    ok = riemann_solve(P, L, R, Am, Ap, s, iters, branch, pstar);
 #pragma unroll
     for (int c = 0; c < 4; ++c) { S.fy[c * P.nfy + k] = Am[c]; S.fy[(4 + c) * P.nfy + k] = Ap[c]; }
   }
@@ -923,9 +927,13 @@ __device__ __forceinline__ void block_maxbits_sum(double& v, int& n) {
 // nby) the y-interfaces (i, j - 1/2), i in [0, nx), j in [0, ny] (nbx, nby =
 // the interface counts over NT, rounded up).  The last block to finish turns
 // the step's maximal speeds into its time step.
-template <typename T, int NT = kThreadsStep>
+// ROOTS: also keep each interface's Newton root p* and the doublings of a
+// its solve made (roots[k], retries[k], k = x-interfaces then y-interfaces;
+// p* = 0 for identical neighbours), for the adjoint's value pass.
+template <typename T, int NT = kThreadsStep, bool ROOTS = false>
 __global__ void __launch_bounds__(NT, iface_min_blocks<NT>::value) interface_kernel(DevParams P, DevState<T> S, DevScalars* sc,
-                                                       const double* fixed_dts, double* dtlog, int fixed) {
+                                                       const double* fixed_dts, double* dtlog, int fixed,
+                                                       T* roots = nullptr, unsigned char* retries = nullptr) {
   // block tallies: the block's maximal speed (bit pattern) and Newton
   // updates, and how many of its warps have added theirs
   __shared__ unsigned long long s_bits;
@@ -938,7 +946,15 @@ __global__ void __launch_bounds__(NT, iface_min_blocks<NT>::value) interface_ker
   double smax = 0.0;
   int iters = 0, branch = 0;
   if (k < (ydir ? P.nfy : P.nfx)) {
-    if (!interface_item(P, S, ydir, k, smax, iters, branch)) atomicOr(&sc->status, ST_RIEMANN);
+    if constexpr (ROOTS) {
+      T p = T(0);
+      if (!interface_item(P, S, ydir, k, smax, iters, branch, &p)) atomicOr(&sc->status, ST_RIEMANN);
+      const long long g = ydir ? P.nfx + k : k;
+      roots[g] = p;
+      retries[g] = (unsigned char)branch_retries(branch);
+    } else {
+      if (!interface_item(P, S, ydir, k, smax, iters, branch)) atomicOr(&sc->status, ST_RIEMANN);
+    }
   }
   // Max of the (non-negative) speeds and sum of the Newton updates, on
   // integers (off the FP64 pipe): over the warp by shuffles, over the block

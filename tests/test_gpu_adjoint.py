@@ -292,3 +292,45 @@ def test_shields_adjoint_vs_central_differences():
           loss(forward_fixed(w, p, dts, z0=w["z"] - e * d), target)) / (2 * e)
     ad = float(np.sum(grads["z"] * d))
     assert abs(ad - fd) <= 1e-6 * abs(fd), (ad, fd)
+
+
+@pytest.mark.parametrize("every", [6, 0])
+def test_adjoint_through_halvings_and_doublings(every):
+    """Colliding supercritical streams (1D, 20 steps from the meeting): the
+    forward solves halve Newton steps and double the celerity a; the value
+    pass starts from the roots (and doublings) the recording or the
+    segment's recompute kept.  GPU adjoint against the oracle-side adjoint
+    (which solves and retries on its own), with checkpoints every 6 steps
+    and with every step kept."""
+    pytest.importorskip("torch")
+    import oracle
+    from oracle import adjoint as OA
+
+    w = W.colliding_streams(60, m_g=3.1)
+    p = w["params"]
+    rng = np.random.default_rng(3)
+    # depths and discharges perturbed by 0.1 % and m_g off 3: no ties of the
+    # celerity bounds between neighbours (at m_g = 3 the bound g h^2 dQ/du of
+    # a uniform discharge does not depend on h; the map has kinks at ties,
+    # where the adjoint and autograd take different one-sided derivatives)
+    w["h"] = w["h"] * (1.0 + 1e-3 * rng.uniform(-1.0, 1.0, w["h"].shape))
+    w["hu"] = w["hu"] * (1.0 + 1e-3 * rng.uniform(-1.0, 1.0, w["hu"].shape))
+    target = w["z"] + 0.001 * rng.standard_normal(w["z"].shape)
+    n = 20
+    s = sve.Solver(p, "fp64")
+    s.set_state(w["h"], w["hu"], w["hv"], w["z"])
+    s.record_forward(n, every)
+    sg = s.safeguards()
+    fin = s.get_state()
+    grads, gp = s.adjoint(lam_z=2.0 * (fin["z"] - target))
+    s.close()
+    assert sg["halvings"] > 0 and sg["retries"] > 0, sg
+    ref = oracle.get().run(oracle.Params.from_workload(p), n, w["h"], w["hu"], w["hv"], w["z"])
+    og = OA.gradients(p, w, ref["dts"], 2.0 * (np.asarray(ref["z"]) - target))
+    scale = max(np.max(np.abs(og["z"])), np.max(np.abs(og["h"])))
+    errs = {f: float(np.max(np.abs(grads[f] - og[f])) / scale) for f in ("z", "h")}
+    pscale = max(abs(b) for b in og["params"][:2])
+    perr = [abs(a - b) / pscale for a, b in zip(gp[:2], og["params"][:2])]
+    print("adjoint vs oracle adjoint (colliding streams):", errs, perr)
+    assert max(errs.values()) <= 1e-9, errs
+    assert max(perr) <= 1e-9, (gp, og["params"])

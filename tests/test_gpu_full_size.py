@@ -10,7 +10,9 @@ its block API on threads, bit-identical to the single-threaded oracle):
 * the 256-run ensemble for its full 1000 steps, the smallest, the median and
   the largest run element by element;
 * the adjoint config (2048 x 1024, periodic): the gradient against central
-  differences of the GPU forward run (a property that holds at any size).
+  differences of the GPU forward run (a property that holds at any size);
+* the 2D bump of Sec. 5.3 on a 1000 x 1000 grid (the large-grid launch
+  shape) for 200 steps, element by element, both A_g of the paper.
 """
 from __future__ import annotations
 
@@ -197,3 +199,25 @@ def test_adjoint_config_full_grid_vs_central_differences():
     fd = (loss(p, w["z"] + e * d) - loss(p, w["z"] - e * d)) / (2 * e)
     ad = float(np.sum(grads["z"] * d))
     assert abs(ad - fd) <= 1e-5 * abs(fd) + 1e-9, (ad, fd)
+
+
+@pytest.mark.parametrize("A_g", [1.0, 0.1])
+def test_paper_bump2d_1000x1000(A_g):
+    """The 2D bump of Sec. 5.3 (1000 x 1000 m, q0 = 10, h = 10 - z_b, 2D
+    Grass m_g = 3, inflow upstream, free elsewhere) on a 1000 x 1000 grid --
+    128-thread blocks, CUDA graphs: the large-grid launch of the paper's
+    4000 x 4000 run -- for 200 steps, element by element at 1e-10 against
+    the banded oracle, with every time step."""
+    w = W.paper_bump2d(nx=1000, ny=1000, A_g=A_g)
+    s = sve.Solver(w["params"], "fp64")
+    assert s.block_size == 128
+    s.set_state(w["h"], w["hu"], w["hv"], w["z"])
+    t = s.step(200)
+    got = s.get_state()
+    dts = s.dts(200)
+    s.close()
+    ref = oracle_banded(w, 200)
+    errs = rel_errs(got, ref)
+    assert max(errs.values()) <= TOL64, errs
+    assert abs(t - ref["t"]) <= TOL64 * ref["t"]
+    assert np.max(np.abs(dts - ref["dts"])) <= TOL64 * np.max(ref["dts"])
