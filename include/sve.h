@@ -60,7 +60,8 @@ enum { SVE_FP64 = 0, SVE_FP32 = 1 };                       /* state precision */
 /* bedload law: Grass, or a Shields-parameter law of Sec. 2 */
 enum { SVE_GRASS = 0, SVE_MPM = 1, SVE_FLVB = 2, SVE_NIELSEN = 3, SVE_RIBBERINK = 4, SVE_CAMENEN = 5 };
 enum { SVE_FRIC_NONE = 0, SVE_FRIC_DARCY = 1, SVE_FRIC_STRICKLER = 2 };
-enum { SVE_BC_PERIODIC = 0, SVE_BC_FREE = 1, SVE_BC_INFLOW_Q = 2, SVE_BC_INFLOW_QH = 3, SVE_BC_WALL = 4 };
+enum { SVE_BC_PERIODIC = 0, SVE_BC_FREE = 1, SVE_BC_INFLOW_Q = 2, SVE_BC_INFLOW_QH = 3, SVE_BC_WALL = 4,
+       SVE_BC_EXTERNAL = 5 /* ghost ring set by the caller: a side of a block of a decomposed grid */ };
 enum { SVE_HOST = 0, SVE_DEVICE = 1 };
 enum { SVE_W = 0, SVE_E = 1, SVE_S = 2, SVE_N = 3 };
 
@@ -88,7 +89,10 @@ enum { SVE_W = 0, SVE_E = 1, SVE_S = 2, SVE_N = 3 };
  * friction      SVE_FRIC_NONE / _DARCY (f_dw) / _STRICKLER (K_st = 1/n).
  * bc[4]         W, E, S, N ghost rules: PERIODIC (both sides of an axis),
  *               FREE (copy), INFLOW_Q (inward normal discharge q_in, h and
- *               zb copied), INFLOW_QH (h = h_in as well), WALL (mirror).
+ *               zb copied), INFLOW_QH (h = h_in as well), WALL (mirror),
+ *               EXTERNAL (the ghost ring of that side is set by the caller,
+ *               sve_block_set_ghosts; not for batches, the adjoint or
+ *               sve_step_noalloc).
  * q_in, h_in    inflow data.
  * kappa_a, beta_min, gamma_z  relaxation celerities of one interface:
  *               a = max(kappa_a max(a0, b0), sqrt(b^2 + 2 g gamma_z |dzb| hmax^2)),
@@ -353,6 +357,47 @@ int sve_record_forward(sve_handle* h, int nsteps, int checkpoint_every);
 int sve_get_checkpoint_every(sve_handle* h);
 int sve_adjoint(sve_handle* h, const void* lam_h, const void* lam_hu, const void* lam_hv, const void* lam_z,
                 int where, void* g_h0, void* g_hu0, void* g_hv0, void* g_z0, double* g_params);
+
+/* ---- one block of a decomposed grid ----------------------------------------
+ * The domain decomposition of Sec. 4: the grid is cut into blocks, each with
+ * one ghost layer filled from the neighbouring blocks before every step, and
+ * the time step is the CFL step of the extreme wave speeds over all blocks.
+ * A handle for a block is created with the block's cell counts and lengths
+ * (the whole grid's dx, dy) and SVE_BC_EXTERNAL on every side that borders
+ * another block (the other sides keep their boundary rules).  A step of a
+ * decomposed run, after sve_set_state on every block:
+ *   1. each block's edge cells to its neighbours: sve_block_get_edge on the
+ *      block, sve_block_set_ghosts on the neighbour (the opposite side);
+ *   2. sve_block_speeds on every block; the caller takes the maximum of Sx
+ *      and of Sy over all blocks (an all-reduce across processes);
+ *   3. sve_block_advance on every block with those maxima.
+ * The kernels are those of a whole-grid step, so with the same launch shape
+ * of the two-kernel step (sve_set_block_size) the decomposed run equals the
+ * whole-grid run cell for cell.  The block's own boundary rules refill its
+ * other ghosts at every update; external ghosts keep what was set last.
+ *
+ * sve_block_get_edge copies the interior cells along side (SVE_W: column 0,
+ * SVE_E: column nx - 1, SVE_S: row 0, SVE_N: row ny - 1) into edge: four
+ * consecutive planes (h, hu, hv, zb) of n values of the state type, n = ny
+ * for W/E and nx for S/N (hv zeros in 1D), in memory `where`.  Blocks.
+ * sve_block_set_ghosts sets the ghost ring of an EXTERNAL side from the same
+ * layout (the neighbour's edge), projecting it as the step projects its
+ * ghosts; a non-finite value or a depth <= 0 is latched (SVE_ERR_NAN,
+ * SVE_ERR_NEG_DEPTH at the next blocking call).  SVE_ERR_ARG for a side that
+ * is not EXTERNAL.  Returns once a host buffer may be reused.
+ * sve_block_speeds solves every interface of the block (Sec. 3) and returns
+ * its extreme wave speeds max(|lambda1|, |lambda5|) over the x- and the
+ * y-interfaces (*sy = 0 in 1D; sy may be NULL); the fluctuations wait for
+ * the update.  Blocks; returns the latched device status.
+ * sve_block_advance updates the block's cells (Godunov average, friction,
+ * checks, boundary-rule ghosts) with the CFL step of the given maxima,
+ * dt = cfl dx / sx (1D) or cfl / (sx / dx + sy / dy) (2D): the one every
+ * block computes alike.  SVE_ERR_DT if that step is not positive and finite.
+ * Blocks; returns the latched device status. */
+int sve_block_get_edge(sve_handle* h, int side, void* edge, int where);
+int sve_block_set_ghosts(sve_handle* h, int side, const void* ghosts, int where);
+int sve_block_speeds(sve_handle* h, double* sx, double* sy);
+int sve_block_advance(sve_handle* h, double sx, double sy);
 
 /* ---- stepping without device allocation ----------------------------------
  * The paper has no counterpart of this entry point: it serves callers that

@@ -57,7 +57,7 @@ int validate(const sve_config* c) {
   if (c->friction == SVE_FRIC_DARCY && !(c->f_dw >= 0)) return SVE_ERR_ARG;
   const int nsides = c->dim == 2 ? 4 : 2;
   for (int s = 0; s < nsides; ++s)
-    if (c->bc[s] < SVE_BC_PERIODIC || c->bc[s] > SVE_BC_WALL) return SVE_ERR_ARG;
+    if (c->bc[s] < SVE_BC_PERIODIC || c->bc[s] > SVE_BC_EXTERNAL) return SVE_ERR_ARG;
   if ((c->bc[0] == SVE_BC_PERIODIC) != (c->bc[1] == SVE_BC_PERIODIC)) return SVE_ERR_ARG;
   if (c->dim == 2 && (c->bc[2] == SVE_BC_PERIODIC) != (c->bc[3] == SVE_BC_PERIODIC)) return SVE_ERR_ARG;
   if (!(c->kappa_a > 1.0) || !(c->beta_min > 0.0) || !(c->gamma_z >= 0.0)) return SVE_ERR_ARG;
@@ -447,6 +447,14 @@ __attribute__((visibility("hidden"))) void sve_internal_make_params(const sve_co
   make_params(c, P);
 }
 __attribute__((visibility("hidden"))) int sve_internal_status_code(int st) { return status_to_code(st); }
+// Whether a side of the configuration takes its ghost ring from outside (a
+// block of a decomposed grid): only the handle's block calls can fill it.
+__attribute__((visibility("hidden"))) bool sve_internal_has_external(const sve_config* c) {
+  const int nsides = c->dim == 2 ? 4 : 2;
+  for (int s = 0; s < nsides; ++s)
+    if (c->bc[s] == SVE_BC_EXTERNAL) return true;
+  return false;
+}
 
 extern "C" {
 
@@ -733,6 +741,7 @@ void sve_destroy(sve_handle* h) {
   if (h->mpart) cudaFree(h->mpart);
   if (h->sc) cudaFree(h->sc);
   if (h->ps) cudaFree(h->ps);
+  if (h->halo) cudaFree(h->halo);
   if (h->dtlog) cudaFree(h->dtlog);
   if (h->fixed) cudaFree(h->fixed);
   if (h->capture) cudaStreamDestroy(h->capture);

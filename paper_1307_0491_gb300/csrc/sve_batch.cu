@@ -184,6 +184,7 @@ constexpr int kSchedules = 2;  // 0: run after run (largest first), 1: round rob
 }  // namespace
 
 __attribute__((visibility("hidden"))) int sve_internal_validate(const sve_config* c);
+__attribute__((visibility("hidden"))) bool sve_internal_has_external(const sve_config* c);
 __attribute__((visibility("hidden"))) void sve_internal_make_params(const sve_config* c, DevParams* P);
 
 struct sve_batch {
@@ -383,7 +384,8 @@ int sve_batch_create(const sve_config* cfgs, int nruns, sve_batch** out) {
   if (!cfgs || nruns < 1 || !out) return SVE_ERR_ARG;
   *out = nullptr;
   for (int r = 0; r < nruns; ++r) {
-    const int rc = sve_internal_validate(&cfgs[r]);
+    int rc = sve_internal_validate(&cfgs[r]);
+    if (!rc && sve_internal_has_external(&cfgs[r])) rc = SVE_ERR_ARG;  // no block calls on a batch
     if (rc) return rc;
     if (cfgs[r].precision != cfgs[0].precision) return SVE_ERR_ARG;
   }

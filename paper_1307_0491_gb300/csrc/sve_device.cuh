@@ -25,7 +25,12 @@
 namespace sve {
 
 enum : int { ST_RIEMANN = 1, ST_NEG_DEPTH = 2, ST_NAN = 4, ST_DT = 8 };
-enum : int { GHOST_PERIODIC = 0, GHOST_FREE = 1, GHOST_INFLOW_Q = 2, GHOST_INFLOW_QH = 3, GHOST_WALL = 4 };
+enum : int { GHOST_PERIODIC = 0, GHOST_FREE = 1, GHOST_INFLOW_Q = 2, GHOST_INFLOW_QH = 3, GHOST_WALL = 4,
+             GHOST_EXTERNAL = 5 };  // external: the ghost ring is set from outside (a neighbouring block)
+// How the solve pass ends a step: the CFL step of its speeds, a given step,
+// or only the block's extreme speeds (a block of a decomposed grid: the step
+// comes from the maximum over all blocks).
+enum : int { DT_CFL = 0, DT_FIXED = 1, DT_SPEEDS_ONLY = 2 };
 
 // Physical and numerical constants, precomputed on the host.
 struct DevParams {
@@ -117,6 +122,12 @@ __device__ __forceinline__ double texp(double x) { return exp(x); }
 __device__ __forceinline__ float texp(float x) { return expf(x); }
 __device__ __forceinline__ float tpow(float x, float y) { return powf(x, y); }
 __device__ __forceinline__ bool tfinite(double x) { return isfinite(x); }
+// a b + c with one rounding, written out where a sum has two products: the
+// compiler's own contraction may fuse either product, and not alike in
+// every kernel that inlines the expression -- the projection of a cell runs
+// in several kernels (upload, update, ghosts) that must agree bit for bit.
+__device__ __forceinline__ double tfma(double a, double b, double c) { return fma(a, b, c); }
+__device__ __forceinline__ float tfma(float a, float b, float c) { return fmaf(a, b, c); }
 __device__ __forceinline__ bool tfinite(float x) { return isfinite(x); }
 // Whether a quotient is cheap enough to take several where one would do (FP32:
 // div.approx); in FP64 (and its dual numbers) divides are folded into one.
@@ -196,7 +207,7 @@ __device__ __forceinline__ bool shields_rate(const DevParams& P, T ts, T& q, T& 
     const T sts = tsqrt(ts);
     const T e = texp(T(-4.5) * r);
     q = T(12) * ts * sts * e;
-    dq = T(12) * e * (T(1.5) * sts + T(4.5) * tcr * tdiv(T(1), sts));
+    dq = T(12) * e * tfma(T(1.5), sts, T(4.5) * tcr * tdiv(T(1), sts));
     return true;
   }
   const T x = ts - tcr;
@@ -221,7 +232,7 @@ __device__ __forceinline__ bool shields_rate(const DevParams& P, T ts, T& q, T& 
 // tau* = alpha |U|^2 (q* above).
 template <typename T>
 __device__ __forceinline__ void closure(const DevParams& P, T H, T un, T ut, T& Q, T& dQ) {
-  const T speed2 = un * un + ut * ut;
+  const T speed2 = tfma(un, un, ut * ut);
   if (P.bedload == 0) {
     const T A = par<T>(P.A_g, P.f.A_g);
     if (speed2 == T(0)) {
@@ -229,21 +240,22 @@ __device__ __forceinline__ void closure(const DevParams& P, T H, T un, T ut, T& 
       dQ = (P.m_int == 1) ? A : T(0);
       return;
     }
-    T pm1, second;
+    // |U|^(m-1) and the second term (m-1) un^2 |U|^(m-3) of dQ/dun
+    T pm1, d;
     switch (P.m_int) {
-      case 1: pm1 = T(1); second = T(0); break;
-      case 2: { T sp = tsqrt(speed2); pm1 = sp; second = tdiv(un * un, sp); } break;
-      case 3: pm1 = speed2; second = T(2) * (un * un); break;
-      case 4: { T sp = tsqrt(speed2); pm1 = speed2 * sp; second = T(3) * (un * un) * sp; } break;
+      case 1: pm1 = T(1); d = T(1); break;
+      case 2: { T sp = tsqrt(speed2); pm1 = sp; d = pm1 + tdiv(un * un, sp); } break;
+      case 3: pm1 = speed2; d = tfma(T(2), un * un, pm1); break;
+      case 4: { T sp = tsqrt(speed2); pm1 = speed2 * sp; d = tfma(T(3) * (un * un), sp, pm1); } break;
       default: {
         T sp = tsqrt(speed2);
         T m = par<T>(P.m_g, P.f.m_g);
         pm1 = tpow(sp, m - T(1));
-        second = (m - T(1)) * (un * un) * tpow(sp, m - T(3));
+        d = tfma((m - T(1)) * (un * un), tpow(sp, m - T(3)), pm1);
       }
     }
     Q = A * un * pm1;
-    dQ = A * (pm1 + second);
+    dQ = A * d;
     return;
   }
   T alpha = par<T>(P.mpm_alpha, P.f.mpm_alpha);
@@ -259,7 +271,7 @@ __device__ __forceinline__ void closure(const DevParams& P, T H, T un, T ut, T& 
   const T C = par<T>(P.qs_scale, P.f.qs_scale);
   Q = C * q * (un * isp);
   // d/dun [q*(alpha |U|^2) un/|U|] = q*' 2 alpha un^2/|U| + q* ut^2/|U|^3
-  dQ = C * (T(2) * dq * alpha * (un * un) * isp + q * (ut * ut) * (isp * isp * isp));
+  dQ = C * tfma(T(2) * dq * alpha * (un * un), isp, q * (ut * ut) * (isp * isp * isp));
 }
 
 // Both normal directions of a 2D cell at once: (Qx, dQx/du) along x and
@@ -268,7 +280,7 @@ __device__ __forceinline__ void closure(const DevParams& P, T H, T un, T ut, T& 
 // calls up to rounding order.
 template <typename T>
 __device__ __forceinline__ void closure2(const DevParams& P, T H, T u, T v, T& Qx, T& dQx, T& Qy, T& dQy) {
-  const T speed2 = u * u + v * v;
+  const T speed2 = tfma(u, u, v * v);
   if (P.bedload == 0) {
     const T A = par<T>(P.A_g, P.f.A_g);
     if (speed2 == T(0)) {
@@ -291,9 +303,9 @@ __device__ __forceinline__ void closure2(const DevParams& P, T H, T u, T v, T& Q
       }
     }
     Qx = A * u * pm1;
-    dQx = A * (pm1 + (u * u) * f);
+    dQx = A * tfma(u * u, f, pm1);
     Qy = A * v * pm1;
-    dQy = A * (pm1 + (v * v) * f);
+    dQy = A * tfma(v * v, f, pm1);
     return;
   }
   T alpha = par<T>(P.mpm_alpha, P.f.mpm_alpha);
@@ -310,8 +322,8 @@ __device__ __forceinline__ void closure2(const DevParams& P, T H, T u, T v, T& Q
   const T cq = C * q, c2 = C * (T(2) * dq * alpha) * isp;
   Qx = cq * (u * isp);
   Qy = cq * (v * isp);
-  dQx = c2 * (u * u) + cq * (v * v) * isp3;
-  dQy = c2 * (v * v) + cq * (u * u) * isp3;
+  dQx = tfma(c2, u * u, cq * (v * v) * isp3);
+  dQy = tfma(c2, v * v, cq * (u * u) * isp3);
 }
 
 // Projected cell in the frame of one interface: n = normal, t = tangential.
@@ -735,34 +747,35 @@ __device__ __forceinline__ void store_cell(const DevParams& P, const DevState<T>
   S.pi[e] = T(0.5) * gHH;
   S.omx[e] = Qx; S.omy[e] = Qy;
   S.ca[e] = H * tsqrt(gH);
-  S.cbx[e] = tsqrt(s[1] * s[1] + gHH * dQx);
-  S.cby[e] = P.dim == 2 ? tsqrt(s[2] * s[2] + gHH * dQy) : T(0);
+  S.cbx[e] = tsqrt(tfma(s[1], s[1], gHH * dQx));
+  S.cby[e] = P.dim == 2 ? tsqrt(tfma(s[2], s[2], gHH * dQy)) : T(0);
 }
 
 __device__ __forceinline__ long long ext_index(const DevParams& P, int i, int j) {
   return (long long)(j + 1) * P.ex + (i + 1);
 }
 
-// Write the ghosts that the interior cell (i, j) with new state s feeds.
+// Write the ghosts that the interior cell (i, j) with new state s feeds
+// (external sides are left to the caller).
 template <typename T>
 __device__ __forceinline__ void write_ghosts(const DevParams& P, const DevState<T>& S, int i, int j, const T s[4]) {
   T gs[4];
   const bool perx = P.bc[0] == GHOST_PERIODIC;
-  if ((!perx && i == 0) || (perx && i == P.nx - 1)) {
+  if (((!perx && i == 0) || (perx && i == P.nx - 1)) && P.bc[0] != GHOST_EXTERNAL) {
     ghost_state(P, 0, s, gs);
     store_cell(P, S, ext_index(P, -1, j), gs, tdiv(T(1), gs[0]));
   }
-  if ((!perx && i == P.nx - 1) || (perx && i == 0)) {
+  if (((!perx && i == P.nx - 1) || (perx && i == 0)) && P.bc[1] != GHOST_EXTERNAL) {
     ghost_state(P, 1, s, gs);
     store_cell(P, S, ext_index(P, P.nx, j), gs, tdiv(T(1), gs[0]));
   }
   if (P.dim == 2) {
     const bool pery = P.bc[2] == GHOST_PERIODIC;
-    if ((!pery && j == 0) || (pery && j == P.ny - 1)) {
+    if (((!pery && j == 0) || (pery && j == P.ny - 1)) && P.bc[2] != GHOST_EXTERNAL) {
       ghost_state(P, 2, s, gs);
       store_cell(P, S, ext_index(P, i, -1), gs, tdiv(T(1), gs[0]));
     }
-    if ((!pery && j == P.ny - 1) || (pery && j == 0)) {
+    if (((!pery && j == P.ny - 1) || (pery && j == 0)) && P.bc[3] != GHOST_EXTERNAL) {
       ghost_state(P, 3, s, gs);
       store_cell(P, S, ext_index(P, i, P.ny), gs, tdiv(T(1), gs[0]));
     }
@@ -1001,10 +1014,11 @@ __global__ void __launch_bounds__(NT, iface_min_blocks<NT>::value) interface_ker
   const double sy = __longlong_as_double((long long)atomicExch(&sc->smax_bits[1], 0ull));
   double dt;
   const int cs = sc->call_step;
-  if (fixed) dt = fixed_dts[cs];
+  if (fixed == DT_FIXED) dt = fixed_dts[cs];
+  else if (fixed == DT_SPEEDS_ONLY) dt = 0.0;  // set by the caller from all blocks' speeds
   else if (P.dim == 1) dt = P.cfl * P.dx / sx;
   else dt = P.cfl / (sx / P.dx + sy / P.dy);
-  if (!(dt > 0.0) || !isfinite(dt)) { atomicOr(&sc->status, ST_DT); dt = 0.0; }
+  if (fixed != DT_SPEEDS_ONLY && (!(dt > 0.0) || !isfinite(dt))) { atomicOr(&sc->status, ST_DT); dt = 0.0; }
   sc->dt = dt;
   sc->Sx = sx;
   sc->Sy = sy;

@@ -49,8 +49,8 @@ __device__ __forceinline__ void project_into(const DevParams& P, T H, T Hu, T Hv
   c.omx = Qx;
   c.omy = Qy;
   c.ca = H * tsqrt(g * H);
-  c.cbx = tsqrt(Hu * Hu + g * H * H * dQx);
-  c.cby = P.dim == 2 ? tsqrt(Hv * Hv + g * H * H * dQy) : T(0);
+  c.cbx = tsqrt(tfma(Hu, Hu, g * H * H * dQx));
+  c.cby = P.dim == 2 ? tsqrt(tfma(Hv, Hv, g * H * H * dQy)) : T(0);
 }
 
 template <typename T>
@@ -72,12 +72,12 @@ __device__ __forceinline__ void write_ghost_state(const DevParams& P, const Stat
     B.h[e] = gs[0]; B.hu[e] = gs[1]; B.hv[e] = gs[2]; B.z[e] = gs[3];
   };
   const bool perx = P.bc[0] == GHOST_PERIODIC;
-  if ((!perx && i == 0) || (perx && i == P.nx - 1)) { ghost_state(P, 0, s, gs); put(-1, j); }
-  if ((!perx && i == P.nx - 1) || (perx && i == 0)) { ghost_state(P, 1, s, gs); put(P.nx, j); }
+  if (((!perx && i == 0) || (perx && i == P.nx - 1)) && P.bc[0] != GHOST_EXTERNAL) { ghost_state(P, 0, s, gs); put(-1, j); }
+  if (((!perx && i == P.nx - 1) || (perx && i == 0)) && P.bc[1] != GHOST_EXTERNAL) { ghost_state(P, 1, s, gs); put(P.nx, j); }
   if (P.dim == 2) {
     const bool pery = P.bc[2] == GHOST_PERIODIC;
-    if ((!pery && j == 0) || (pery && j == P.ny - 1)) { ghost_state(P, 2, s, gs); put(i, -1); }
-    if ((!pery && j == P.ny - 1) || (pery && j == 0)) { ghost_state(P, 3, s, gs); put(i, P.ny); }
+    if (((!pery && j == 0) || (pery && j == P.ny - 1)) && P.bc[2] != GHOST_EXTERNAL) { ghost_state(P, 2, s, gs); put(i, -1); }
+    if (((!pery && j == P.ny - 1) || (pery && j == 0)) && P.bc[3] != GHOST_EXTERNAL) { ghost_state(P, 3, s, gs); put(i, P.ny); }
   }
 }
 

@@ -212,9 +212,10 @@ __global__ void __launch_bounds__(kMThreads, 5) march_kernel(DevParams P, StateB
   const double sy = __longlong_as_double((long long)atomicExch(&sc->smax_bits[1], 0ull));
   const int cs = sc->call_step;
   double dt;
-  if (fixed) dt = fixed_dts[cs];
+  if (fixed == DT_FIXED) dt = fixed_dts[cs];
+  else if (fixed == DT_SPEEDS_ONLY) dt = 0.0;  // set by the caller from all blocks' speeds
   else dt = P.cfl / (sx / P.dx + sy / P.dy);
-  if (!(dt > 0.0) || !isfinite(dt)) { atomicOr(&sc->status, ST_DT); dt = 0.0; }
+  if (fixed != DT_SPEEDS_ONLY && (!(dt > 0.0) || !isfinite(dt))) { atomicOr(&sc->status, ST_DT); dt = 0.0; }
   sc->dt = dt;
   sc->Sx = sx;
   sc->Sy = sy;

@@ -36,6 +36,7 @@
 __attribute__((visibility("hidden"))) int sve_internal_validate(const sve_config* c);
 __attribute__((visibility("hidden"))) void sve_internal_make_params(const sve_config* c, sve::DevParams* P);
 __attribute__((visibility("hidden"))) int sve_internal_status_code(int st);
+__attribute__((visibility("hidden"))) bool sve_internal_has_external(const sve_config* c);
 
 namespace {
 
@@ -226,7 +227,7 @@ extern "C" int sve_step_noalloc(const sve_config* cfg, void* depth, void* hu, vo
   if (!cfg || !depth || !hu || !zb || !t_inout || nsteps < 0) return SVE_ERR_ARG;
   int rc = sve_internal_validate(cfg);
   if (rc) return rc;
-  if (cfg->dim == 2 && !hv) return SVE_ERR_ARG;
+  if ((cfg->dim == 2 && !hv) || sve_internal_has_external(cfg)) return SVE_ERR_ARG;
   sve::DevParams P;
   sve_internal_make_params(cfg, &P);
   int dev = 0;

@@ -26,7 +26,8 @@ SVE_NOALLOC_SCRATCH_BYTES = 8 << 20
 SVE_FP64, SVE_FP32 = 0, 1
 SVE_GRASS, SVE_MPM, SVE_FLVB, SVE_NIELSEN, SVE_RIBBERINK, SVE_CAMENEN = 0, 1, 2, 3, 4, 5
 SVE_FRIC_NONE, SVE_FRIC_DARCY, SVE_FRIC_STRICKLER = 0, 1, 2
-SVE_BC_PERIODIC, SVE_BC_FREE, SVE_BC_INFLOW_Q, SVE_BC_INFLOW_QH, SVE_BC_WALL = 0, 1, 2, 3, 4
+SVE_BC_PERIODIC, SVE_BC_FREE, SVE_BC_INFLOW_Q, SVE_BC_INFLOW_QH, SVE_BC_WALL, SVE_BC_EXTERNAL = 0, 1, 2, 3, 4, 5
+SVE_W, SVE_E, SVE_S, SVE_N = 0, 1, 2, 3
 SVE_HOST, SVE_DEVICE = 0, 1
 
 #: every symbol include/sve.h declares
@@ -38,7 +39,8 @@ EXPORTS = ("sve_config_default", "sve_create", "sve_set_stream", "sve_set_state"
            "sve_batch_autotune", "sve_batch_set_schedule", "sve_batch_last_launch_count", "sve_batch_destroy",
            "sve_record_forward", "sve_adjoint", "sve_set_block_size", "sve_get_block_size", "sve_advance",
            "sve_get_checkpoint_every", "sve_set_persistent", "sve_get_persistent", "sve_check_sync_timeout",
-           "sve_get_safeguards")
+           "sve_get_safeguards", "sve_block_get_edge", "sve_block_set_ghosts", "sve_block_speeds",
+           "sve_block_advance")
 
 
 class sve_config(ctypes.Structure):
@@ -117,6 +119,10 @@ def load() -> ctypes.CDLL:
         "sve_check_sync_timeout": ([vp, ctypes.c_longlong], ip),
         "sve_adjoint": ([vp, vp, vp, vp, vp, ip, vp, vp, vp, vp, dp], ip),
         "sve_set_block_size": ([vp, ip], ip),
+        "sve_block_get_edge": ([vp, ip, vp, ip], ip),
+        "sve_block_set_ghosts": ([vp, ip, vp, ip], ip),
+        "sve_block_speeds": ([vp, dp, dp], ip),
+        "sve_block_advance": ([vp, ctypes.c_double, ctypes.c_double], ip),
         "sve_get_block_size": ([vp], ip),
     }
     for name, (args, res) in sig.items():
@@ -235,6 +241,24 @@ def sve_get_safeguards(h) -> tuple[int, int, int, int]:
     return rc, halv.value, raised.value, retries.value
 
 
+def sve_block_get_edge(h, side: int, edge: int, where: int) -> int:
+    return load().sve_block_get_edge(h, int(side), edge, int(where))
+
+
+def sve_block_set_ghosts(h, side: int, ghosts: int, where: int) -> int:
+    return load().sve_block_set_ghosts(h, int(side), ghosts, int(where))
+
+
+def sve_block_speeds(h) -> tuple[int, float, float]:
+    sx, sy = ctypes.c_double(0.0), ctypes.c_double(0.0)
+    rc = load().sve_block_speeds(h, ctypes.byref(sx), ctypes.byref(sy))
+    return rc, sx.value, sy.value
+
+
+def sve_block_advance(h, sx: float, sy: float) -> int:
+    return load().sve_block_advance(h, float(sx), float(sy))
+
+
 def sve_step_noalloc(cfg: sve_config, depth: int, hu: int, hv: int | None, zb: int, nsteps: int, t: float,
                      stream: int | None = None) -> tuple[int, float]:
     """Steps on caller-owned device arrays without any device allocation
@@ -333,7 +357,7 @@ _BEDLOAD = {"grass": SVE_GRASS, "mpm": SVE_MPM, "flvb": SVE_FLVB, "nielsen": SVE
             "ribberink": SVE_RIBBERINK, "camenen": SVE_CAMENEN}
 _FRICTION = {"none": SVE_FRIC_NONE, "darcy": SVE_FRIC_DARCY, "strickler": SVE_FRIC_STRICKLER}
 _BC = {"periodic": SVE_BC_PERIODIC, "free": SVE_BC_FREE, "inflow_q": SVE_BC_INFLOW_Q,
-       "inflow_qh": SVE_BC_INFLOW_QH, "wall": SVE_BC_WALL}
+       "inflow_qh": SVE_BC_INFLOW_QH, "wall": SVE_BC_WALL, "external": SVE_BC_EXTERNAL}
 
 
 def config_from_params(p: dict, precision: str = "fp64") -> sve_config:
@@ -489,6 +513,27 @@ class Solver:
         rc, steps, its = sve_get_counters(self.h)
         _check(rc, "sve_get_counters")
         return dict(steps=steps, newton_iters=its)
+
+    # -- one block of a decomposed grid (sides marked "external") ----------
+    def edge(self, side: int) -> np.ndarray:
+        """The interior cells along a side: (4, n) array (h, hu, hv, z)."""
+        n = self.ny if side in (SVE_W, SVE_E) else self.nx
+        out = np.empty((4, n), dtype=self.dtype)
+        _check(sve_block_get_edge(self.h, side, out.ctypes.data, SVE_HOST), "sve_block_get_edge")
+        return out
+
+    def set_ghosts(self, side: int, ghosts) -> None:
+        """The ghost ring of an external side from a (4, n) array."""
+        g = np.ascontiguousarray(np.asarray(ghosts, dtype=self.dtype))
+        _check(sve_block_set_ghosts(self.h, side, g.ctypes.data, SVE_HOST), "sve_block_set_ghosts")
+
+    def block_speeds(self) -> tuple[float, float]:
+        rc, sx, sy = sve_block_speeds(self.h)
+        _check(rc, "sve_block_speeds")
+        return sx, sy
+
+    def block_advance(self, sx: float, sy: float) -> None:
+        _check(sve_block_advance(self.h, sx, sy), "sve_block_advance")
 
     def safeguards(self) -> dict:
         rc, halv, raised, retries = sve_get_safeguards(self.h)

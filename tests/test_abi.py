@@ -110,6 +110,11 @@ def test_null_handle_checks_of_later_calls(lib):
     assert lib.sve_get_checkpoint_every(null) == sve.SVE_ERR_ARG
     rc, _, _, _ = sve.sve_get_safeguards(null)
     assert rc == sve.SVE_ERR_ARG
+    assert lib.sve_block_get_edge(null, 0, None, sve.SVE_HOST) == sve.SVE_ERR_ARG
+    assert lib.sve_block_set_ghosts(null, 0, None, sve.SVE_HOST) == sve.SVE_ERR_ARG
+    rc, _, _ = sve.sve_block_speeds(null)
+    assert rc == sve.SVE_ERR_ARG
+    assert lib.sve_block_advance(null, 1.0, 1.0) == sve.SVE_ERR_ARG
 
 
 def test_missing_library_fails_loudly(monkeypatch, tmp_path):
