@@ -328,7 +328,9 @@ def run_batched(args, sve, W, torch, precision: str, plain_value: float):
     b = sve.Batch([r["params"] for r in runs], precision, stream=torch.cuda.current_stream().cuda_stream)
     for i, r in enumerate(runs):
         b.set_state(i, r["h"], r["hu"], r["hv"], r["z"])
-    tile, sched = b.autotune(2)
+    tile, sched = b.autotune(10)
+    trials = b.trials()
+    rows = b.rows
     b.step(args.batch_spinup)
     b.step(3)
     c0 = b.counters()
@@ -349,6 +351,9 @@ def run_batched(args, sve, W, torch, precision: str, plain_value: float):
             "ms_per_step": ms / args.batch_steps, "steps": args.batch_steps,
             "timed_steps_of_run": f"{args.batch_spinup + 3}..{args.batch_spinup + 2 + args.batch_steps}",
             "launches_per_step": 2, "tile": tile, "schedule": ["run-major", "round-robin"][sched],
+            "rows_per_strip_run": rows or None,
+            "solve_pass": "marching strips (fused FP32 step)" if rows else "interface tiles (two-kernel step)",
+            "autotune": {"trial_steps": 10, "candidates": trials},
             "newton_updates": c1["newton_iters"] - c0["newton_iters"],
             "vs_plain": value / plain_value if plain_value else None,
             "l2": "working set larger than L2 (no flush)"}

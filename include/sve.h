@@ -289,6 +289,9 @@ int sve_get_block_size(sve_handle* h);
  * time step, time and mass sums, stepped together: every step is one launch
  * over all runs' interfaces and one over all their cells, cut into tiles of
  * one run each (a tile table in a schedule order), captured in CUDA graphs.
+ * With the FP32 state and every run 2D, the interface launch is the fused
+ * FP32 step's solve pass (column strips marching over runs of rows, four
+ * strip-runs of one run per block) and the cell launch its update pass.
  * Each run advances as a single handle with the same configuration would:
  * the same per-interface and per-cell code, compiled into other kernels, so
  * results agree to round-off (FMA contraction may differ).  Run r's state
@@ -313,9 +316,19 @@ int sve_batch_get_diag(sve_batch* b, int run, double* mass_h, double* mass_z, do
 int sve_batch_get_counters(sve_batch* b, long long* steps, unsigned long long* newton_iters);
 /* Time trial_steps steps of every candidate tile size (128, 256 work items)
  * and schedule (0: run after run, largest first; 1: round robin over the
- * runs), keep the fastest; the runs' states are restored afterwards.
+ * runs) -- for the fused FP32 2D form also the rows of a strip-run (8, 16,
+ * 32, 64) -- and keep the fastest; the runs' states are restored afterwards.
  * Reports the choice in *tile, *schedule (nullable). */
 int sve_batch_autotune(sve_batch* b, int trial_steps, int* tile, int* schedule);
+/* The last autotune's candidates: copies min(n, count) entries (tile,
+ * schedule, rows -- 0 outside the fused form -- and the mean time of a trial
+ * step [ms]) into the nullable arrays and returns the count. */
+int sve_batch_autotune_trials(sve_batch* b, int n, int* tile, int* schedule, int* rows, double* ms_per_step);
+/* Rows of a strip-run of the fused FP32 2D form (8, 16, 32 or 64; SVE_ERR_ARG
+ * otherwise or for another form); sve_batch_get_rows returns the current
+ * value (0 outside the fused form). */
+int sve_batch_set_rows(sve_batch* b, int rows);
+int sve_batch_get_rows(sve_batch* b);
 /* Select a tile size and schedule directly. */
 int sve_batch_set_schedule(sve_batch* b, int tile, int schedule);
 long long sve_batch_last_launch_count(sve_batch* b);

@@ -23,6 +23,8 @@
 
 #include "../../include/sve.h"
 #include "sve_device.cuh"
+#include "sve_fused.cuh"
+#include "sve_march.cuh"
 
 using sve::DevParams;
 using sve::DevScalars;
@@ -38,6 +40,7 @@ struct BatchRun {
   int ntile_if;   // interface tiles of this run (at the current tile size)
   int part_cell;  // first cell partial
   int ntile_cell;
+  int strips, rows, mtasks;  // FP32 2D (fused): strips, rows a run, strip-runs of this run
 };
 
 // Copy the run record of the block's tile into shared memory.
@@ -165,6 +168,98 @@ __global__ void __launch_bounds__(NT) batch_cell_kernel(const BatchRun<T>* runs,
   S.done_cell = 0u;
 }
 
+// FP32 2D runs: the solve pass as column strips marching over rows
+// (march_task of sve_march.cuh), four strip-runs of one run per block; the
+// run's last block turns its speed maxima into its time step.  Four blocks
+// per SM: the run record in shared memory costs registers that five blocks
+// (<= 102) would spill.
+template <typename T>
+__global__ void __launch_bounds__(sve::kMThreads, 4) batch_march_kernel(const BatchRun<T>* runs, const int2* tiles,
+                                                                        DevScalars* sc) {
+  __shared__ BatchRun<T> R;
+  __shared__ unsigned long long s_sx, s_sy;
+  __shared__ unsigned int s_cnt[5];
+  const int2 t = tiles[blockIdx.x];
+  if (threadIdx.x == 0) { s_sx = 0ull; s_sy = 0ull; for (int k = 0; k < 5; ++k) s_cnt[k] = 0u; }
+  load_run(runs, t.x, &R);  // ends with a barrier
+  const DevParams& P = R.P;
+  const int task = t.y * sve::kMWarps + (int)(threadIdx.x >> 5);
+  sve::MarchTally<T> tl;
+  if (task < R.mtasks) {
+    const sve::StateBuf<T> B = {R.S.h, R.S.hu, R.S.hv, R.S.z};
+    const long long ncell = (long long)P.nx * P.ny;
+    const sve::NetFluct<T> D = {R.S.fx, R.S.fx + ncell, R.S.fx + 2 * ncell, R.S.fx + 3 * ncell};
+    sve::march_task(P, B, D, task % R.strips, task / R.strips, R.rows, tl);
+  }
+  DevScalars& S = sc[t.x];
+  if (!sve::march_fold(tl, &S, &s_sx, &s_sy, s_cnt)) return;
+  __threadfence();
+  if (atomicAdd(&S.done_iface, 1u) != (unsigned)R.ntile_if - 1) return;
+  __threadfence();
+  const double mx = __longlong_as_double((long long)atomicExch(&S.smax_bits[0], 0ull));
+  const double my = __longlong_as_double((long long)atomicExch(&S.smax_bits[1], 0ull));
+  double dt = P.cfl / (mx / P.dx + my / P.dy);
+  if (!(dt > 0.0) || !isfinite(dt)) { atomicOr(&S.status, sve::ST_DT); dt = 0.0; }
+  S.dt = dt;
+  S.Sx = mx;
+  S.Sy = my;
+  S.done_iface = 0u;
+}
+
+// FP32 2D runs: the update from the net fluctuations (apply_cell of
+// sve_fused.cuh), one cell a thread over tiles of NT cells of one run.
+template <typename T, int NT>
+__global__ void __launch_bounds__(NT) batch_apply_kernel(const BatchRun<T>* runs, const int2* tiles, DevScalars* sc,
+                                                         double* mpart) {
+  __shared__ BatchRun<T> R;
+  __shared__ double s_m[2][NT];
+  __shared__ unsigned int s_warps;
+  const int2 t = tiles[blockIdx.x];
+  if (threadIdx.x == 0) s_warps = 0u;
+  load_run(runs, t.x, &R);  // ends with a barrier
+  const DevParams& P = R.P;
+  const long long k = (long long)t.y * NT + threadIdx.x;
+  double mh = 0.0, mz = 0.0;
+  if (k < (long long)P.nx * P.ny) {
+    const int j = (int)(k / P.nx), i = (int)(k - (long long)j * P.nx);
+    const sve::StateBuf<T> B = {R.S.h, R.S.hu, R.S.hv, R.S.z};
+    const long long ncell = (long long)P.nx * P.ny;
+    const sve::NetFluct<T> D = {R.S.fx, R.S.fx + ncell, R.S.fx + 2 * ncell, R.S.fx + 3 * ncell};
+    T h1, z1;
+    const int st = sve::apply_cell(P, B, D, T(sc[t.x].dt), i, j, sve::Mirror<T>{}, h1, z1);
+    if (st) atomicOr(&sc[t.x].status, st);
+    mh = (double)h1;
+    mz = (double)z1;
+  }
+  s_m[0][threadIdx.x] = mh;
+  s_m[1][threadIdx.x] = mz;
+  __syncwarp();
+  unsigned int w = 0u;
+  if ((threadIdx.x & 31) == 0) {
+    __threadfence_block();
+    w = atomicAdd(&s_warps, 1u);
+  }
+  w = __shfl_sync(0xffffffffu, w, 0);
+  if (w != NT / 32 - 1) return;
+  __threadfence_block();
+  const int lane = threadIdx.x & 31;
+  double a = 0.0, b = 0.0;
+#pragma unroll
+  for (int q = 0; q < NT / 32; ++q) { a += s_m[0][lane + 32 * q]; b += s_m[1][lane + 32 * q]; }
+  a = sve::warp_sum(a);
+  b = sve::warp_sum(b);
+  if (lane != 0) return;
+  mpart[2 * (R.part_cell + t.y)] = a;
+  mpart[2 * (R.part_cell + t.y) + 1] = b;
+  __threadfence();
+  DevScalars& S = sc[t.x];
+  if (atomicAdd(&S.done_cell, 1u) != (unsigned)R.ntile_cell - 1) return;
+  S.mass_parts = (unsigned)R.ntile_cell;
+  S.t += S.dt;
+  S.steps += 1;
+  S.done_cell = 0u;
+}
+
 // Mass sums of one run from its per-tile (or, after an upload, per-block)
 // partials, in a fixed order (one block; launched when they are read).
 __global__ void __launch_bounds__(sve::kThreads) batch_mass_kernel(const double* part, DevScalars* S, double cell) {
@@ -180,6 +275,7 @@ __global__ void __launch_bounds__(sve::kThreads) batch_mass_kernel(const double*
 constexpr int kBatchGraphSteps = 8;
 constexpr int kTileSizes[2] = {128, 256};
 constexpr int kSchedules = 2;  // 0: run after run (largest first), 1: round robin over runs
+constexpr int kMarchRows[4] = {8, 16, 32, 64};  // rows a strip-run of the FP32 2D batch (autotuner's choices)
 
 }  // namespace
 
@@ -210,6 +306,10 @@ struct sve_batch {
   // (d_mpart), 2 the scalars themselves (already reduced)
   std::vector<int> mass_src;
   int tile = 128, schedule = 0;
+  bool fused = false;                // FP32 state, every run 2D: the marching solve pass + apply pass
+  int rows = 32;                     // rows a strip-run of the fused solve pass
+  struct Trial { int tile, schedule, rows; float ms_per_step; };
+  std::vector<Trial> trials;         // the last autotune's candidates and their times
   cudaStream_t stream = nullptr;
   cudaStream_t capture = nullptr;
   cudaGraphExec_t graph = nullptr;
@@ -258,7 +358,11 @@ int build_tables(sve_batch* b, int tile, int schedule) {
   for (int r = 0; r < n; ++r) {
     runs[r].P = b->P[r];
     runs[r].S = run_state<T>(b, r);
-    runs[r].ntile_if = (int)tiles_of(b->P[r].nfx + b->P[r].nfy, tile);
+    runs[r].strips = (b->P[r].nx + sve::kMCols - 1) / sve::kMCols;
+    runs[r].rows = b->rows;
+    runs[r].mtasks = runs[r].strips * ((b->P[r].ny + b->rows - 1) / b->rows);
+    runs[r].ntile_if = b->fused ? (int)tiles_of(runs[r].mtasks, sve::kMWarps)
+                                : (int)tiles_of(b->P[r].nfx + b->P[r].nfy, tile);
     runs[r].ntile_cell = (int)tiles_of((long long)b->P[r].nx * b->P[r].ny, tile);
     runs[r].part_if = pif;
     runs[r].part_cell = pcell;
@@ -313,6 +417,16 @@ int build_tables_any(sve_batch* b, int tile, int schedule) {
 template <typename T>
 void launch_batch_step(sve_batch* b, cudaStream_t st) {
   const BatchRun<T>* runs = (const BatchRun<T>*)b->d_runs;
+  if (b->fused) {
+    if constexpr (sizeof(T) == 4) {
+      batch_march_kernel<T><<<b->nt_if, sve::kMThreads, 0, st>>>(runs, b->d_tiles_if, b->d_sc);
+      if (b->tile == 128)
+        batch_apply_kernel<T, 128><<<b->nt_cell, 128, 0, st>>>(runs, b->d_tiles_cell, b->d_sc, b->d_mpart);
+      else
+        batch_apply_kernel<T, 256><<<b->nt_cell, 256, 0, st>>>(runs, b->d_tiles_cell, b->d_sc, b->d_mpart);
+    }
+    return;
+  }
   if (b->tile == 128) {
     batch_interface_kernel<T, 128><<<b->nt_if, 128, 0, st>>>(runs, b->d_tiles_if, b->d_sc);
     batch_cell_kernel<T, 128><<<b->nt_cell, 128, 0, st>>>(runs, b->d_tiles_cell, b->d_sc, b->d_mpart);
@@ -406,6 +520,8 @@ int sve_batch_create(const sve_config* cfgs, int nruns, sve_batch** out) {
     part_cell += tiles_of((long long)b->P[r].nx * b->P[r].ny, kTileSizes[0]);
   }
   b->arena_bytes = bytes;
+  b->fused = b->precision == SVE_FP32;
+  for (int r = 0; r < nruns; ++r) b->fused = b->fused && cfgs[r].dim == 2;
   bool ok = cudaMalloc(&b->arena, bytes) == cudaSuccess;
   const size_t rec = b->precision == SVE_FP64 ? sizeof(BatchRun<double>) : sizeof(BatchRun<float>);
   ok = ok && cudaMalloc(&b->d_runs, rec * nruns) == cudaSuccess;
@@ -565,33 +681,66 @@ int sve_batch_autotune(sve_batch* b, int trial_steps, int* tile, int* schedule) 
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
   float best = 1e30f;
-  int best_tile = b->tile, best_sched = b->schedule;
-  for (int ti = 0; ti < 2 && !rc; ++ti)
-    for (int sc = 0; sc < kSchedules && !rc; ++sc) {
-      rc = build_tables_any(b, kTileSizes[ti], sc);
-      if (rc) break;
-      launch_batch_step_any(b, b->stream);  // warm-up
-      cudaEventRecord(e0, b->stream);
-      for (int s = 0; s < trial_steps; ++s) launch_batch_step_any(b, b->stream);
-      cudaEventRecord(e1, b->stream);
-      if (cudaEventSynchronize(e1) != cudaSuccess) { rc = SVE_ERR_CUDA; break; }
-      float ms = 0.f;
-      cudaEventElapsedTime(&ms, e0, e1);
-      if (ms < best) { best = ms; best_tile = kTileSizes[ti]; best_sched = sc; }
-      // back to the saved state for the next candidate
-      if (cudaMemcpyAsync(b->arena, save, b->arena_bytes, cudaMemcpyDeviceToDevice, b->stream) != cudaSuccess ||
-          cudaMemcpyAsync(b->d_sc, sc0.data(), sizeof(DevScalars) * b->nruns, cudaMemcpyHostToDevice,
-                          b->stream) != cudaSuccess ||
-          cudaStreamSynchronize(b->stream) != cudaSuccess)
-        rc = SVE_ERR_CUDA;
-    }
+  int best_tile = b->tile, best_sched = b->schedule, best_rows = b->rows;
+  b->trials.clear();
+  // candidates: the tile size of the per-item launches (the cell or apply
+  // pass, and the interface pass of the two-kernel form), the tile order,
+  // and for the fused FP32 2D form the rows of a strip-run (the solve
+  // pass's tile: 30 columns x rows)
+  const int nrows = b->fused ? 4 : 1;
+  for (int ri = 0; ri < nrows && !rc; ++ri)
+    for (int ti = 0; ti < 2 && !rc; ++ti)
+      for (int sc = 0; sc < kSchedules && !rc; ++sc) {
+        if (b->fused) b->rows = kMarchRows[ri];
+        rc = build_tables_any(b, kTileSizes[ti], sc);
+        if (rc) break;
+        launch_batch_step_any(b, b->stream);  // warm-up
+        cudaEventRecord(e0, b->stream);
+        for (int s = 0; s < trial_steps; ++s) launch_batch_step_any(b, b->stream);
+        cudaEventRecord(e1, b->stream);
+        if (cudaEventSynchronize(e1) != cudaSuccess) { rc = SVE_ERR_CUDA; break; }
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        b->trials.push_back({kTileSizes[ti], sc, b->fused ? b->rows : 0, ms / (float)trial_steps});
+        if (ms < best) { best = ms; best_tile = kTileSizes[ti]; best_sched = sc; best_rows = b->rows; }
+        // back to the saved state for the next candidate
+        if (cudaMemcpyAsync(b->arena, save, b->arena_bytes, cudaMemcpyDeviceToDevice, b->stream) != cudaSuccess ||
+            cudaMemcpyAsync(b->d_sc, sc0.data(), sizeof(DevScalars) * b->nruns, cudaMemcpyHostToDevice,
+                            b->stream) != cudaSuccess ||
+            cudaStreamSynchronize(b->stream) != cudaSuccess)
+          rc = SVE_ERR_CUDA;
+      }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   cudaFree(save);
+  b->rows = best_rows;
   if (!rc) rc = build_tables_any(b, best_tile, best_sched);
   if (tile) *tile = best_tile;
   if (schedule) *schedule = best_sched;
   return rc;
+}
+
+int sve_batch_autotune_trials(sve_batch* b, int n, int* tile, int* schedule, int* rows, double* ms_per_step) {
+  if (!b || n < 0) return SVE_ERR_ARG;
+  const int m = std::min(n, (int)b->trials.size());
+  for (int k = 0; k < m; ++k) {
+    if (tile) tile[k] = b->trials[k].tile;
+    if (schedule) schedule[k] = b->trials[k].schedule;
+    if (rows) rows[k] = b->trials[k].rows;
+    if (ms_per_step) ms_per_step[k] = b->trials[k].ms_per_step;
+  }
+  return (int)b->trials.size();
+}
+
+int sve_batch_set_rows(sve_batch* b, int rows) {
+  if (!b || !b->fused || (rows != 8 && rows != 16 && rows != 32 && rows != 64)) return SVE_ERR_ARG;
+  b->rows = rows;
+  return build_tables_any(b, b->tile, b->schedule);
+}
+
+int sve_batch_get_rows(sve_batch* b) {
+  if (!b) return SVE_ERR_ARG;
+  return b->fused ? b->rows : 0;
 }
 
 int sve_batch_set_schedule(sve_batch* b, int tile, int schedule) {

@@ -1070,7 +1070,7 @@ __device__ __forceinline__ int cell_item(const DevParams& P, const DevState<T>& 
   // semi-implicit friction: q <- q / (1 + dt C(h) |q|),
   // C = f / (8 h^2) (Darcy) or g / (K^2 h^(7/3)) (Strickler)
   if (P.friction != 0) {
-    const T qn = tsqrt(s[1] * s[1] + s[2] * s[2]);
+    const T qn = tsqrt(tfma(s[1], s[1], s[2] * s[2]));
     T C = par<T>(P.fric_c, P.f.fric_c) * (tau * tau);
     if (P.friction == 2) C = C * rcbrt64(s[0]);
     const T rden = tdiv(T(1), T(1) + T(dt) * C * qn);

@@ -112,6 +112,34 @@ template <> struct MassSum<float> { using type = FSum; };
 
 constexpr int kAThreads = 256;
 
+// The update of one interior cell (i, j) from its net fluctuation: U <- U -
+// dt dF, semi-implicit friction, checks, the ghosts it feeds, the optional
+// mirror; returns status bits, (mh, mz) = the new (h, z).
+template <typename T>
+__device__ __forceinline__ int apply_cell(const DevParams& P, const StateBuf<T>& B, const NetFluct<T>& D, T dt,
+                                          int i, int j, const Mirror<T>& out, T& mh, T& mz) {
+  const long long e = ext_index(P, i, j), k = (long long)j * P.nx + i;
+  T s[4] = {B.h[e] - dt * D.h[k], B.hu[e] - dt * D.hu[k], B.hv[e] - dt * D.hv[k], B.z[e] - dt * D.z[k]};
+  if (P.friction != 0) {
+    const T tau = tdiv(T(1), s[0]);
+    const T qn = tsqrt(tfma(s[1], s[1], s[2] * s[2]));
+    T C = par<T>(P.fric_c, P.f.fric_c) * (tau * tau);
+    if (P.friction == 2) C = C * rcbrt64(s[0]);
+    const T den = T(1) + dt * C * qn;
+    s[1] = tdiv(s[1], den);
+    s[2] = tdiv(s[2], den);
+  }
+  int st = 0;
+  if (!(finite_bits(s[0]) && finite_bits(s[1]) && finite_bits(s[2]) && finite_bits(s[3]))) st = ST_NAN;
+  else if (!positive(s[0])) st = ST_NEG_DEPTH;
+  B.h[e] = s[0]; B.hu[e] = s[1]; B.hv[e] = s[2]; B.z[e] = s[3];
+  if (out.h) { out.h[k] = s[0]; out.hu[k] = s[1]; out.hv[k] = s[2]; out.z[k] = s[3]; }
+  write_ghost_state(P, B, i, j, s);
+  mh = s[0];
+  mz = s[3];
+  return st;
+}
+
 template <typename T>
 __global__ void __launch_bounds__(kAThreads) apply_kernel(DevParams P, StateBuf<T> B, NetFluct<T> D,
                                                           DevScalars* sc, double* mpart, Mirror<T> out) {
@@ -125,24 +153,10 @@ __global__ void __launch_bounds__(kAThreads) apply_kernel(DevParams P, StateBuf<
   // rows by a grid stride in y, columns by a grid stride in x
   for (int j = blockIdx.y; j < P.ny; j += gridDim.y) {
     for (int i = blockIdx.x * kAThreads + threadIdx.x; i < P.nx; i += gridDim.x * kAThreads) {
-      const long long e = ext_index(P, i, j), k = (long long)j * P.nx + i;
-      T s[4] = {B.h[e] - dt * D.h[k], B.hu[e] - dt * D.hu[k], B.hv[e] - dt * D.hv[k], B.z[e] - dt * D.z[k]};
-      if (P.friction != 0) {
-        const T tau = tdiv(T(1), s[0]);
-        const T qn = tsqrt(s[1] * s[1] + s[2] * s[2]);
-        T C = par<T>(P.fric_c, P.f.fric_c) * (tau * tau);
-        if (P.friction == 2) C = C * rcbrt64(s[0]);
-        const T den = T(1) + dt * C * qn;
-        s[1] = tdiv(s[1], den);
-        s[2] = tdiv(s[2], den);
-      }
-      if (!(finite_bits(s[0]) && finite_bits(s[1]) && finite_bits(s[2]) && finite_bits(s[3]))) st |= ST_NAN;
-      else if (!positive(s[0])) st |= ST_NEG_DEPTH;
-      B.h[e] = s[0]; B.hu[e] = s[1]; B.hv[e] = s[2]; B.z[e] = s[3];
-      if (out.h) { out.h[k] = s[0]; out.hu[k] = s[1]; out.hv[k] = s[2]; out.z[k] = s[3]; }
-      write_ghost_state(P, B, i, j, s);
-      sh_h.add(s[0]);
-      sh_z.add(s[3]);
+      T mh, mz;
+      st |= apply_cell(P, B, D, dt, i, j, out, mh, mz);
+      sh_h.add(mh);
+      sh_z.add(mz);
     }
   }
   if (st) atomicOr(&sc->status, st);

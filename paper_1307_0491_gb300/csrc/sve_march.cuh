@@ -107,6 +107,111 @@ __device__ __forceinline__ Cell<T> left_cell(const SCell<T>& s) {
   return c;
 }
 
+// Tallies of one thread's solves: failures, Newton updates, safeguards,
+// extreme speeds of the x- and y-solves.
+template <typename T>
+struct MarchTally {
+  int fail = 0, iters = 0;
+  unsigned int nraised = 0u, nretry = 0u, nhalv = 0u;
+  SpeedMax<T> mx, my;
+};
+
+// One task: the strip `strip` (columns strip * 30 .. + 29 with a halo column
+// each side) over the run of rows `chunk` (rows chunk * rows ..), by the
+// calling warp (every lane must call it).
+template <typename T>
+__device__ __forceinline__ void march_task(const DevParams& P, const StateBuf<T>& B, const NetFluct<T>& D,
+                                           int strip, int chunk, int rows, MarchTally<T>& t) {
+  const int lane = threadIdx.x & 31;
+  const int c = strip * kMCols - 1 + lane;          // this lane's column
+  const bool col_in = c <= P.nx;                    // inside the padded grid
+  const bool interior = lane >= 1 && lane <= kMCols && c < P.nx;  // a cell this strip updates
+  const bool xface = lane >= 1 && col_in;           // the x-interface c - 1/2 exists
+  const int j0 = chunk * rows, j1 = min(j0 + rows, P.ny);
+  const T idx = par<T>(P.inv_dx, (float)P.inv_dx), idy = par<T>(P.inv_dy, (float)P.inv_dy);
+  SCell<T> cur, nxt;
+  T apb[4] = {T(0), T(0), T(0), T(0)};  // A+ of the y-interface below (j - 1/2), y frame
+  march_project(P, B, c, j0 - 1, col_in, cur);
+  // j = j0 - 1 only solves the y-interface j0 - 1/2 (its A+ enters row j0)
+  for (int j = j0 - 1; j < j1; ++j) {
+    march_project(P, B, c, j + 1, col_in, nxt);
+    const bool row = j >= j0;  // row j is updated by this task (warp-uniform)
+    // the y-interface j + 1/2 at this column
+    T amu[4] = {T(0), T(0), T(0), T(0)}, apu[4] = {T(0), T(0), T(0), T(0)};
+    if (interior) {
+      T s = T(0);
+      int its = 0, br = 0;
+      if (!riemann_solve(P, frame_cell(cur, true), frame_cell(nxt, true), amu, apu, s, its, br)) t.fail = 1;
+      t.my.add(s);
+      t.iters += its;
+      t.nraised += branch_raised(br);
+      t.nretry += branch_retries(br);
+      t.nhalv += branch_halvings(br);
+    }
+    if (row) {
+      // the x-interface c - 1/2 of row j; its A- goes to the lane below
+      const Cell<T> L = left_cell(cur);
+      T amx[4] = {T(0), T(0), T(0), T(0)}, apx[4] = {T(0), T(0), T(0), T(0)};
+      if (xface) {
+        T s = T(0);
+        int its = 0, br = 0;
+        if (!riemann_solve(P, L, frame_cell(cur, false), amx, apx, s, its, br)) t.fail = 1;
+        t.mx.add(s);
+        t.iters += its;
+        t.nraised += branch_raised(br);
+        t.nretry += branch_retries(br);
+        t.nhalv += branch_halvings(br);
+      }
+      T amr[4];  // A- of the x-interface c + 1/2 (the right neighbour's)
+#pragma unroll
+      for (int k = 0; k < 4; ++k) amr[k] = __shfl_down_sync(0xffffffffu, amx[k], 1);
+      if (interior) {
+        // the y fluctuations are in the y frame: (H, Hv, Hu, Z)
+        const long long o = (long long)j * P.nx + c;
+        D.h[o] = (apx[0] + amr[0]) * idx + (apb[0] + amu[0]) * idy;
+        D.hu[o] = (apx[1] + amr[1]) * idx + (apb[2] + amu[2]) * idy;
+        D.hv[o] = (apx[2] + amr[2]) * idx + (apb[1] + amu[1]) * idy;
+        D.z[o] = (apx[3] + amr[3]) * idx + (apb[3] + amu[3]) * idy;
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < 4; ++k) apb[k] = apu[k];
+    cur = nxt;
+  }
+}
+
+// The block's tallies (every thread calls it): over the warp by reductions,
+// over the block by shared-memory atomics, the block's last warp folds them
+// into the run's scalars and returns true for that warp's lane 0 (false
+// elsewhere).
+template <typename T>
+__device__ __forceinline__ bool march_fold(const MarchTally<T>& t, DevScalars* sc, unsigned long long* s_sx,
+                                           unsigned long long* s_sy, unsigned int* s_cnt) {
+  if (t.fail) atomicOr(&sc->status, ST_RIEMANN);
+  const unsigned long long wx = t.mx.warp_bits(), wy = t.my.warp_bits();
+  const unsigned iters = __reduce_add_sync(0xffffffffu, (unsigned)t.iters);
+  const unsigned nraised = __reduce_add_sync(0xffffffffu, t.nraised);
+  const unsigned nhalv = __reduce_add_sync(0xffffffffu, t.nhalv);
+  const unsigned nretry = __reduce_add_sync(0xffffffffu, t.nretry);
+  if ((threadIdx.x & 31) != 0) return false;
+  // s_cnt: Newton updates, raised, doublings, halvings, warps done
+  atomicMax(s_sx, wx);
+  atomicMax(s_sy, wy);
+  atomicAdd(&s_cnt[0], iters);
+  if (nraised | nretry | nhalv) { atomicAdd(&s_cnt[1], nraised); atomicAdd(&s_cnt[2], nretry); atomicAdd(&s_cnt[3], nhalv); }
+  __threadfence_block();
+  if (atomicAdd(&s_cnt[4], 1u) != blockDim.x / 32 - 1) return false;
+  __threadfence_block();
+  atomicAdd(&sc->newton_iters, (unsigned long long)atomicAdd(&s_cnt[0], 0u));
+  const unsigned br = atomicAdd(&s_cnt[1], 0u), bt = atomicAdd(&s_cnt[2], 0u), bh = atomicAdd(&s_cnt[3], 0u);
+  if (br) atomicAdd(&sc->raised, (unsigned long long)br);
+  if (bt) atomicAdd(&sc->retries, (unsigned long long)bt);
+  if (bh) atomicAdd(&sc->halvings, (unsigned long long)bh);
+  atomicMax(&sc->smax_bits[0], atomicMax(s_sx, 0ull));
+  atomicMax(&sc->smax_bits[1], atomicMax(s_sy, 0ull));
+  return true;
+}
+
 // Five blocks per SM (<= 102 registers a thread, no spills): 20 warps per SM
 // measured 5 % faster than the unconstrained 123 registers (16 warps) and
 // than six blocks (<= 85 registers) on the 8192 x 4096 antidune.
@@ -115,96 +220,13 @@ __global__ void __launch_bounds__(kMThreads, 5) march_kernel(DevParams P, StateB
                                                           DevScalars* sc, const double* fixed_dts, double* dtlog,
                                                           int fixed, int strips, int rows, long long ntasks) {
   __shared__ unsigned long long s_sx, s_sy;
-  __shared__ unsigned int s_its, s_warps, s_halv, s_raised, s_retry;
-  if (threadIdx.x == 0) { s_sx = 0ull; s_sy = 0ull; s_its = 0u; s_warps = 0u; s_halv = 0u; s_raised = 0u; s_retry = 0u; }
+  __shared__ unsigned int s_cnt[5];
+  if (threadIdx.x == 0) { s_sx = 0ull; s_sy = 0ull; for (int k = 0; k < 5; ++k) s_cnt[k] = 0u; }
   __syncthreads();
-  const int lane = threadIdx.x & 31;
   const long long task = (long long)blockIdx.x * kMWarps + (threadIdx.x >> 5);
-  int fail = 0, iters = 0;
-  unsigned int nraised = 0u, nretry = 0u, nhalv = 0u;
-  SpeedMax<T> mx, my;  // extreme wave speeds of the x- and y-solves
-  if (task < ntasks) {
-    const int strip = (int)(task % strips), chunk = (int)(task / strips);
-    const int c = strip * kMCols - 1 + lane;          // this lane's column
-    const bool col_in = c <= P.nx;                    // inside the padded grid
-    const bool interior = lane >= 1 && lane <= kMCols && c < P.nx;  // a cell this strip updates
-    const bool xface = lane >= 1 && col_in;           // the x-interface c - 1/2 exists
-    const int j0 = chunk * rows, j1 = min(j0 + rows, P.ny);
-    const T idx = par<T>(P.inv_dx, (float)P.inv_dx), idy = par<T>(P.inv_dy, (float)P.inv_dy);
-    SCell<T> cur, nxt;
-    T apb[4] = {T(0), T(0), T(0), T(0)};  // A+ of the y-interface below (j - 1/2), y frame
-    march_project(P, B, c, j0 - 1, col_in, cur);
-    // j = j0 - 1 only solves the y-interface j0 - 1/2 (its A+ enters row j0)
-    for (int j = j0 - 1; j < j1; ++j) {
-      march_project(P, B, c, j + 1, col_in, nxt);
-      const bool row = j >= j0;  // row j is updated by this task (warp-uniform)
-      // the y-interface j + 1/2 at this column
-      T amu[4] = {T(0), T(0), T(0), T(0)}, apu[4] = {T(0), T(0), T(0), T(0)};
-      if (interior) {
-        T s = T(0);
-        int its = 0, br = 0;
-        if (!riemann_solve(P, frame_cell(cur, true), frame_cell(nxt, true), amu, apu, s, its, br)) fail = 1;
-        my.add(s);
-        iters += its;
-        nraised += branch_raised(br);
-        nretry += branch_retries(br);
-        nhalv += branch_halvings(br);
-      }
-      if (row) {
-        // the x-interface c - 1/2 of row j; its A- goes to the lane below
-        const Cell<T> L = left_cell(cur);
-        T amx[4] = {T(0), T(0), T(0), T(0)}, apx[4] = {T(0), T(0), T(0), T(0)};
-        if (xface) {
-          T s = T(0);
-          int its = 0, br = 0;
-          if (!riemann_solve(P, L, frame_cell(cur, false), amx, apx, s, its, br)) fail = 1;
-          mx.add(s);
-          iters += its;
-          nraised += branch_raised(br);
-          nretry += branch_retries(br);
-          nhalv += branch_halvings(br);
-        }
-        T amr[4];  // A- of the x-interface c + 1/2 (the right neighbour's)
-#pragma unroll
-        for (int k = 0; k < 4; ++k) amr[k] = __shfl_down_sync(0xffffffffu, amx[k], 1);
-        if (interior) {
-          // the y fluctuations are in the y frame: (H, Hv, Hu, Z)
-          const long long o = (long long)j * P.nx + c;
-          D.h[o] = (apx[0] + amr[0]) * idx + (apb[0] + amu[0]) * idy;
-          D.hu[o] = (apx[1] + amr[1]) * idx + (apb[2] + amu[2]) * idy;
-          D.hv[o] = (apx[2] + amr[2]) * idx + (apb[1] + amu[1]) * idy;
-          D.z[o] = (apx[3] + amr[3]) * idx + (apb[3] + amu[3]) * idy;
-        }
-      }
-#pragma unroll
-      for (int k = 0; k < 4; ++k) apb[k] = apu[k];
-      cur = nxt;
-    }
-  }
-  if (fail) atomicOr(&sc->status, ST_RIEMANN);
-  // tallies: warp reductions, shared-memory atomics, the block's last warp
-  // folds them into the step's running maxima, the last block takes dt
-  const unsigned long long wx = mx.warp_bits(), wy = my.warp_bits();
-  iters = __reduce_add_sync(0xffffffffu, iters);
-  nraised = __reduce_add_sync(0xffffffffu, nraised);
-  nhalv = __reduce_add_sync(0xffffffffu, nhalv);
-  nretry = __reduce_add_sync(0xffffffffu, nretry);
-  if (lane != 0) return;
-  atomicMax(&s_sx, wx);
-  atomicMax(&s_sy, wy);
-  atomicAdd(&s_its, (unsigned int)iters);
-  if (nraised | nretry | nhalv) { atomicAdd(&s_raised, nraised); atomicAdd(&s_retry, nretry); atomicAdd(&s_halv, nhalv); }
-  __threadfence_block();
-  if (atomicAdd(&s_warps, 1u) != kMWarps - 1) return;
-  __threadfence_block();
-  const unsigned long long bx = atomicMax(&s_sx, 0ull), by = atomicMax(&s_sy, 0ull);
-  atomicAdd(&sc->newton_iters, (unsigned long long)atomicAdd(&s_its, 0u));
-  const unsigned br = atomicAdd(&s_raised, 0u), bt = atomicAdd(&s_retry, 0u), bh = atomicAdd(&s_halv, 0u);
-  if (br) atomicAdd(&sc->raised, (unsigned long long)br);
-  if (bt) atomicAdd(&sc->retries, (unsigned long long)bt);
-  if (bh) atomicAdd(&sc->halvings, (unsigned long long)bh);
-  atomicMax(&sc->smax_bits[0], bx);
-  atomicMax(&sc->smax_bits[1], by);
+  MarchTally<T> t;
+  if (task < ntasks) march_task(P, B, D, (int)(task % strips), (int)(task / strips), rows, t);
+  if (!march_fold(t, sc, &s_sx, &s_sy, s_cnt)) return;
   __threadfence();
   if (atomicAdd(&sc->done_iface, 1u) != gridDim.x - 1) return;
   __threadfence();

@@ -40,7 +40,7 @@ EXPORTS = ("sve_config_default", "sve_create", "sve_set_stream", "sve_set_state"
            "sve_record_forward", "sve_adjoint", "sve_set_block_size", "sve_get_block_size", "sve_advance",
            "sve_get_checkpoint_every", "sve_set_persistent", "sve_get_persistent", "sve_check_sync_timeout",
            "sve_get_safeguards", "sve_block_get_edge", "sve_block_set_ghosts", "sve_block_speeds",
-           "sve_block_advance")
+           "sve_block_advance", "sve_batch_autotune_trials", "sve_batch_set_rows", "sve_batch_get_rows")
 
 
 class sve_config(ctypes.Structure):
@@ -110,6 +110,9 @@ def load() -> ctypes.CDLL:
         "sve_batch_get_counters": ([vp, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_ulonglong)], ip),
         "sve_batch_autotune": ([vp, ip, ctypes.POINTER(ip), ctypes.POINTER(ip)], ip),
         "sve_batch_set_schedule": ([vp, ip, ip], ip),
+        "sve_batch_autotune_trials": ([vp, ip, ctypes.POINTER(ip), ctypes.POINTER(ip), ctypes.POINTER(ip), dp], ip),
+        "sve_batch_set_rows": ([vp, ip], ip),
+        "sve_batch_get_rows": ([vp], ip),
         "sve_batch_last_launch_count": ([vp], ctypes.c_longlong),
         "sve_batch_destroy": ([vp], None),
         "sve_record_forward": ([vp, ip, ip], ip),
@@ -639,3 +642,20 @@ class Batch:
 
     def set_schedule(self, tile: int, schedule: int) -> None:
         _check(sve_batch_set_schedule(self.h, tile, schedule), "sve_batch_set_schedule")
+
+    def trials(self) -> list[dict]:
+        """The last autotune's candidates and their mean trial-step times."""
+        L = load()
+        n = L.sve_batch_autotune_trials(self.h, 0, None, None, None, None)
+        _check(min(n, 0), "sve_batch_autotune_trials")
+        t, s, r = (ctypes.c_int * max(n, 1))(), (ctypes.c_int * max(n, 1))(), (ctypes.c_int * max(n, 1))()
+        ms = (ctypes.c_double * max(n, 1))()
+        L.sve_batch_autotune_trials(self.h, n, t, s, r, ms)
+        return [dict(tile=t[k], schedule=s[k], rows=r[k], ms_per_step=ms[k]) for k in range(n)]
+
+    def set_rows(self, rows: int) -> None:
+        _check(load().sve_batch_set_rows(self.h, int(rows)), "sve_batch_set_rows")
+
+    @property
+    def rows(self) -> int:
+        return load().sve_batch_get_rows(self.h)

@@ -115,6 +115,9 @@ def test_null_handle_checks_of_later_calls(lib):
     rc, _, _ = sve.sve_block_speeds(null)
     assert rc == sve.SVE_ERR_ARG
     assert lib.sve_block_advance(null, 1.0, 1.0) == sve.SVE_ERR_ARG
+    assert lib.sve_batch_autotune_trials(null, 0, None, None, None, None) == sve.SVE_ERR_ARG
+    assert lib.sve_batch_set_rows(null, 32) == sve.SVE_ERR_ARG
+    assert lib.sve_batch_get_rows(null) == sve.SVE_ERR_ARG
 
 
 def test_missing_library_fails_loudly(monkeypatch, tmp_path):

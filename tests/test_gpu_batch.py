@@ -107,11 +107,48 @@ def test_autotune_keeps_state():
 
 
 def test_batch_fp32_runs():
+    """FP32 state, 2D runs: the batch runs the fused step's kernels (the
+    marching solve pass, the apply pass) with the per-interface and per-cell
+    code of a single FP32 handle, compiled into other kernels: every run
+    equals its single run to FP32 rounding (the compiler may contract a sum
+    of two products differently), for each rows-per-strip-run choice and
+    tile size."""
     runs = small_ensemble()[:3]
-    got = batch(runs, 60, precision="fp32")
-    for r, g in zip(runs, got):
-        ref = single(r, 60, "fp32")
-        close(g, ref, tol=1e-4)
+    refs = [single(r, 60, "fp32") for r in runs]
+    for rows, tile in ((32, 256), (8, 128), (64, 256)):
+        b = sve.Batch([r["params"] for r in runs], "fp32")
+        for i, r in enumerate(runs):
+            b.set_state(i, r["h"], r["hu"], r["hv"], r["z"])
+        b.set_schedule(tile, 1)
+        b.set_rows(rows)
+        assert b.rows == rows
+        b.step(60)
+        for i, ref in enumerate(refs):
+            g = b.get_state(i)
+            close(g, ref, tol=1e-5)
+            assert abs(b.diag(i)["t"] - ref["t"]) <= 1e-6 * ref["t"], (rows, tile, i)
+        b.close()
+
+
+def test_autotune_trials_fp32():
+    """The autotuner's candidate table of the fused FP32 batch: tile size x
+    schedule x rows of a strip-run (16 candidates), each timed; the choice is
+    the fastest and the runs' states are restored."""
+    runs = small_ensemble()[:4]
+    b = sve.Batch([r["params"] for r in runs], "fp32")
+    for i, r in enumerate(runs):
+        b.set_state(i, r["h"], r["hu"], r["hv"], r["z"])
+    tile, sched = b.autotune(3)
+    trials = b.trials()
+    assert len(trials) == 16
+    assert {t["rows"] for t in trials} == {8, 16, 32, 64}
+    best = min(trials, key=lambda t: t["ms_per_step"])
+    assert (best["tile"], best["schedule"], best["rows"]) == (tile, sched, b.rows)
+    b.step(20)
+    g = b.get_state(0)
+    b.close()
+    ref = single(runs[0], 20, "fp32")
+    close(g, ref, tol=1e-5)
 
 
 def test_batch_error_latched():
