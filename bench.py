@@ -671,13 +671,13 @@ def measure_step(sve, torch, w, prec, local, world, spinup, warmup, steps, clock
 def march_shape(nx, ny, nsm=None):
     """Strips and runs of rows of the FP32 solve pass for a grid (the launch
     shape the library picks: 30 columns a strip, rows a run so that ~16 warps
-    per SM are busy, 8 to 64)."""
+    per SM are busy, 8 to 32)."""
     if nsm is None:
         import torch
 
         nsm = torch.cuda.get_device_properties(0).multi_processor_count
     strips = -(-nx // 30)
-    rows = min(64, max(8, -(-(strips * ny) // (16 * nsm))))
+    rows = min(32, max(8, -(-(strips * ny) // (16 * nsm))))
     return strips, -(-ny // rows)
 
 
