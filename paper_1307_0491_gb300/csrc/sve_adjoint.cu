@@ -56,6 +56,8 @@ struct sve_adjoint_rec {
   size_t roots_cap = 0;
   unsigned char* rtry = nullptr;    // and the doublings of a of those solves
   size_t rtry_cap = 0;
+  double* cells = nullptr;          // per-cell projection record of the state being reversed (adj_cells_kernel)
+  size_t cells_cap = 0;
   double* lam = nullptr;            // 2 x 4 interior planes (current, next)
   double* mu = nullptr;             // 4 interior planes
   double* gpart = nullptr;          // per-block parameter partials
@@ -175,15 +177,108 @@ __global__ void __launch_bounds__(kAdjThreads) adj_friction_kernel(DevParams P, 
   finish_partials<kAdjThreads>(gpart, 1, gacc + 2, done);
 }
 
+// Planes of the per-cell projection record (padded cells, plane k at
+// cells + k * next): what the interface adjoint reads instead of projecting
+// both its cells itself (each cell then projected once per step, not once
+// per interface side).  Grass / Shields-parameter law:
+enum AdjCellPlane {
+  kCTau, kCPi, kCCa,
+  kCSp,                // |U|            / s2 = |U|^2
+  kCIsp,               // 1/|U| (0 where |U| = 0; Shields: 0 where no transport)
+  kCLsp,               // log |U|        / alpha
+  kCPm1,               // |U|^(m-1)      / q*
+  kCPm3,               // |U|^(m-3)      / dq*/dtau*
+  kCDdq,               // -              / d2q*/dtau*2
+  kCU, kCV,            // velocities
+  kCOmx, kCCbx, kCIcbx, kCDQx,  // x frame: Omega, cb, 1/cb, dQ/du
+  kCOmy, kCCby, kCIcby, kCDQy,  // y frame
+  kCPlanes
+};
+
+// The projection record of every padded cell with a positive depth, in the
+// x frame and (2D) the y frame, by the adjoint's own projection
+// (project_grass_rec / project_shields_rec).
+template <bool GRASS>
+__global__ void __launch_bounds__(kAdjThreads) adj_cells_kernel(DevParams P, DevState<double> S, double A,
+                                                                double m, double* cells, long long next) {
+  const long long e = (long long)blockIdx.x * kAdjThreads + threadIdx.x;
+  if (e >= next) return;
+  const double H = S.h[e], Hu = S.hu[e], Hv = P.dim == 2 ? S.hv[e] : 0.0, Z = S.z[e];
+  if (!(H > 0.0)) return;  // corners of the padding: never an interface's cell
+  auto put = [&](int k, double v) { cells[(long long)k * next + e] = v; };
+  sve::ProjRec r;
+  const Cell<double> cx = GRASS ? sve::project_grass_rec(P, H, Hu, Hv, Z, A, m, r)
+                                : sve::project_shields_rec(P, H, Hu, Hv, Z, r);
+  put(kCTau, cx.tau); put(kCPi, cx.Pi); put(kCCa, cx.ca);
+  put(kCSp, GRASS ? r.sp : r.s2);
+  put(kCIsp, r.isp);
+  put(kCLsp, GRASS ? r.lsp : r.alpha);
+  put(kCPm1, GRASS ? r.pm1 : r.q);
+  put(kCPm3, GRASS ? r.pm3 : r.dq);
+  put(kCDdq, GRASS ? 0.0 : r.ddq);
+  put(kCU, cx.un); put(kCV, cx.ut);
+  put(kCOmx, cx.Om); put(kCCbx, cx.cb); put(kCIcbx, r.icb); put(kCDQx, r.dQ);
+  if (P.dim == 2) {
+    const Cell<double> cy = GRASS ? sve::project_grass_rec(P, H, Hv, Hu, Z, A, m, r)
+                                  : sve::project_shields_rec(P, H, Hv, Hu, Z, r);
+    put(kCOmy, cy.Om); put(kCCby, cy.cb); put(kCIcby, r.icb); put(kCDQy, r.dQ);
+  }
+}
+
+// The projected cell at padded index e in the frame of an x (ydir false) or
+// y interface, and its record, from the planes of adj_cells_kernel.
+template <bool GRASS>
+__device__ __forceinline__ Cell<double> adj_load_cell(const DevState<double>& S, const double* cells,
+                                                      long long next, long long e, bool ydir, sve::ProjRec& r) {
+  auto get = [&](int k) { return cells[(long long)k * next + e]; };
+  Cell<double> c;
+  c.H = S.h[e];
+  c.Hn = ydir ? S.hv[e] : S.hu[e];
+  c.Ht = ydir ? S.hu[e] : S.hv[e];
+  c.Z = S.z[e];
+  c.tau = get(kCTau);
+  const double u = get(kCU), v = get(kCV);
+  c.un = ydir ? v : u;
+  c.ut = ydir ? u : v;
+  c.Pi = get(kCPi);
+  c.ca = get(kCCa);
+  c.Om = get(ydir ? kCOmy : kCOmx);
+  c.cb = get(ydir ? kCCby : kCCbx);
+  r.H = c.H; r.Hn = c.Hn; r.Ht = c.Ht; r.tau = c.tau; r.un = c.un; r.ut = c.ut; r.ca = c.ca; r.cb = c.cb;
+  r.icb = get(ydir ? kCIcby : kCIcbx);
+  r.dQ = get(ydir ? kCDQy : kCDQx);
+  r.isp = get(kCIsp);
+  if (GRASS) {
+    r.sp = get(kCSp);
+    r.lsp = get(kCLsp);
+    r.pm1 = get(kCPm1);
+    r.pm3 = get(kCPm3);
+    r.still = r.sp == 0.0;
+  } else {
+    r.s2 = get(kCSp);
+    r.alpha = get(kCLsp);
+    r.q = get(kCPm1);
+    r.dq = get(kCPm3);
+    r.ddq = get(kCDdq);
+    r.active = r.isp > 0.0;
+    r.still = r.s2 == 0.0;
+    r.sp = 0.0;
+    r.lsp = 0.0;
+  }
+  return c;
+}
+
 // Per interface: the Jacobian-transpose product of its fluctuations with mu of
 // its two cells (a ghost side has mu = 0), stored in the fluctuation planes
 // (8 values: left state then right state, interface frame); A_g and m_g
-// gradients accumulated.
+// gradients accumulated.  The cells' projections and records come from the
+// planes of adj_cells_kernel.
 template <bool GRASS>
 __global__ void __launch_bounds__(kAdjThreads) adj_interface_kernel(DevParams P, DevState<double> S,
                                                                     const double* mu, double dt, double A,
                                                                     double m, const double* roots,
-                                                                    const unsigned char* rtry, double* gpart,
+                                                                    const unsigned char* rtry, const double* cells,
+                                                                    long long next, double* gpart,
                                                                     double* gacc, unsigned int* done) {
   __shared__ double sh[kAdjThreads / 32];
   const long long ncell = (long long)P.nx * P.ny;
@@ -223,9 +318,9 @@ __global__ void __launch_bounds__(kAdjThreads) adj_interface_kernel(DevParams P,
 #pragma unroll
     for (int c = 0; c < 4; ++c) any = any || muL[c] != 0.0 || muR[c] != 0.0;
     if (any) {
-      const double* hn = ydir ? S.hv : S.hu;
-      const double* ht = ydir ? S.hu : S.hv;
-      const double u[8] = {S.h[eL], hn[eL], ht[eL], S.z[eL], S.h[eR], hn[eR], ht[eR], S.z[eR]};
+      sve::ProjRec rL, rR;
+      const Cell<double> L = adj_load_cell<GRASS>(S, cells, next, eL, ydir, rL);
+      const Cell<double> R = adj_load_cell<GRASS>(S, cells, next, eR, ydir, rR);
       // reverse mode: the transposed Jacobian of the fluctuations applied
       // to -dt/dx (mu of the left cell, mu of the right cell)
       const double w = -dt * (ydir ? P.inv_dy : P.inv_dx);
@@ -237,7 +332,7 @@ __global__ void __launch_bounds__(kAdjThreads) adj_interface_kernel(DevParams P,
       // here leaves its contribution at zero, as the value pass did before)
       // the forward solve's root (kept by the recording or the segment's
       // recompute) spares the value pass its Newton iteration
-      sve::interface_vjp<GRASS>(P, u, A, m, Amb, Apb, ub, Ab, mb, Kb, roots[idx], (int)rtry[idx]);
+      sve::interface_vjp_cells<GRASS>(P, L, R, rL, rR, A, m, Amb, Apb, ub, Ab, mb, Kb, roots[idx], (int)rtry[idx]);
 #pragma unroll
       for (int q = 0; q < 8; ++q) out[q] = ub[q];
       // Grass: the A_g and m_g gradients; Shields laws: the friction
@@ -382,6 +477,7 @@ void free_rec(sve_adjoint_rec* r) {
   if (r->segc) cudaFree(r->segc);
   if (r->roots) cudaFree(r->roots);
   if (r->rtry) cudaFree(r->rtry);
+  if (r->cells) cudaFree(r->cells);
   if (r->lam) cudaFree(r->lam);
   if (r->mu) cudaFree(r->mu);
   if (r->gpart) cudaFree(r->gpart);
@@ -535,6 +631,9 @@ int sve_adjoint(sve_handle* h, const void* lam_h, const void* lam_hu, const void
   if (rc) return rc;
   rc = grow(&r->rtry, &r->rtry_cap, nf * (size_t)r->every);
   if (rc) return rc;
+  rc = grow(&r->cells, &r->cells_cap, (size_t)kCPlanes * (size_t)h->next);
+  if (rc) return rc;
+  const unsigned nb_pad = (unsigned)((h->next + kAdjThreads - 1) / kAdjThreads);
   double* lam = r->lam;             // lambda^{n+1}
   double* lam_next = r->lam + 4 * ncell;
   ADJ_TRY(cudaMemsetAsync(r->gacc, 0, sizeof(double) * 4, h->stream));
@@ -577,12 +676,19 @@ int sve_adjoint(sve_handle* h, const void* lam_h, const void* lam_hu, const void
                                                               r->mu, dt, r->gpart, r->gacc, r->done);
       const double* roots = r->roots + (size_t)s * nf;
       const unsigned char* rtry = r->rtry + (size_t)s * nf;
-      if (P.bedload == 0)
+      if (P.bedload == 0) {
+        adj_cells_kernel<true><<<nb_pad, kAdjThreads, 0, h->stream>>>(P, S, h->cfg.A_g, h->cfg.m_g, r->cells,
+                                                                      h->next);
         adj_interface_kernel<true><<<nb_if, kAdjThreads, 0, h->stream>>>(P, S, r->mu, dt, h->cfg.A_g, h->cfg.m_g,
-                                                                         roots, rtry, r->gpart, r->gacc, r->done);
-      else
+                                                                         roots, rtry, r->cells, h->next, r->gpart,
+                                                                         r->gacc, r->done);
+      } else {
+        adj_cells_kernel<false><<<nb_pad, kAdjThreads, 0, h->stream>>>(P, S, h->cfg.A_g, h->cfg.m_g, r->cells,
+                                                                       h->next);
         adj_interface_kernel<false><<<nb_if, kAdjThreads, 0, h->stream>>>(P, S, r->mu, dt, h->cfg.A_g, h->cfg.m_g,
-                                                                          roots, rtry, r->gpart, r->gacc, r->done);
+                                                                          roots, rtry, r->cells, h->next, r->gpart,
+                                                                          r->gacc, r->done);
+      }
       adj_gather_kernel<<<nb_c, kAdjThreads, 0, h->stream>>>(P, S, r->mu, lam_next);
       if (cudaGetLastError() != cudaSuccess) return SVE_ERR_CUDA;
       double* t = lam;

@@ -100,8 +100,10 @@ __device__ __forceinline__ void jac_pass(const DevParams& P, const double u[8], 
 struct ProjRec {
   double H, Hn, Ht, tau, un, ut, sp, pm1, pm3, dQ, ca, cb;
   bool still;  // |U| = 0
+  // 1/cb (0 where cb = 0), 1/|U| (0 where |U| = 0), log |U| (Grass)
+  double icb, isp, lsp;
   // Shields-parameter laws: tau* = alpha |U|^2, q*, its first two derivatives
-  double s2, isp, alpha, q, dq, ddq;
+  double s2, alpha, q, dq, ddq;
   bool active;  // |U| > 0 and above the threshold
 };
 
@@ -174,6 +176,9 @@ __device__ __forceinline__ Cell<double> project_shields_rec(const DevParams& P, 
   c.cb = sqrt(Hn * Hn + P.g * H * H * dQ);
   r.still = r.s2 == 0.0;
   r.sp = 0.0;
+  r.lsp = 0.0;
+  r.icb = c.cb > 0.0 ? 1.0 / c.cb : 0.0;
+  if (!r.active) r.isp = 0.0;
   r.H = H; r.Hn = Hn; r.Ht = Ht; r.tau = c.tau; r.un = c.un; r.ut = c.ut; r.dQ = dQ; r.ca = c.ca; r.cb = c.cb;
   return c;
 }
@@ -214,6 +219,19 @@ __device__ __forceinline__ Cell<double> project_grass_rec(const DevParams& P, do
   c.ca = H * sqrt(P.g * H);
   c.cb = sqrt(Hn * Hn + P.g * H * H * dQ);
   r.H = H; r.Hn = Hn; r.Ht = Ht; r.tau = c.tau; r.un = c.un; r.ut = c.ut; r.dQ = dQ; r.ca = c.ca; r.cb = c.cb;
+  // the backward sweep's 1/cb, 1/|U| and log |U| (one divide for both
+  // reciprocals where both are needed)
+  r.icb = r.isp = r.lsp = 0.0;
+  if (c.cb > 0.0 && !r.still) {
+    const double q = 1.0 / (c.cb * r.sp);
+    r.icb = q * r.sp;
+    r.isp = q * c.cb;
+  } else if (c.cb > 0.0) {
+    r.icb = 1.0 / c.cb;
+  } else if (!r.still) {
+    r.isp = 1.0 / r.sp;
+  }
+  if (!r.still) r.lsp = log(r.sp);
   return c;
 }
 
@@ -222,17 +240,7 @@ __device__ __forceinline__ Cell<double> project_grass_rec(const DevParams& P, do
 __device__ __forceinline__ void project_grass_bar(const DevParams& P, const ProjRec& r, double A, double m,
                                                   CellBar cb, double ub[4], double& Ab, double& mb) {
   double Hb = cb.H, Hnb = cb.Hn, Htb = cb.Ht, taub = cb.tau, unb = cb.un, utb = cb.ut;
-  // 1/cb and 1/|U| from one divide where both are needed
-  double icb = 0.0, isp = 0.0;
-  if (r.cb > 0.0 && !r.still) {
-    const double q = 1.0 / (r.cb * r.sp);
-    icb = q * r.sp;
-    isp = q * r.cb;
-  } else if (r.cb > 0.0) {
-    icb = 1.0 / r.cb;
-  } else if (!r.still) {
-    isp = 1.0 / r.sp;
-  }
+  const double icb = r.icb, isp = r.isp;
   // cb = sqrt(Hn^2 + g H^2 dQ)
   double dQb = 0.0;
   if (r.cb > 0.0) {
@@ -259,7 +267,7 @@ __device__ __forceinline__ void project_grass_bar(const DevParams& P, const Proj
     mb += secondb * un2 * r.pm3;
     unb += secondb * (m - 1.0) * 2.0 * r.un * r.pm3;
     const double pm3b = secondb * (m - 1.0) * un2;
-    const double lsp = log(r.sp);
+    const double lsp = r.lsp;
     double spb = (pm1b * (m - 1.0) * r.pm1 + pm3b * (m - 3.0) * r.pm3) * isp;
     mb += pm1b * r.pm1 * lsp + pm3b * r.pm3 * lsp;
     const double s2b = spb * 0.5 * isp;
@@ -287,7 +295,7 @@ __device__ __forceinline__ void project_shields_bar(const DevParams& P, const Pr
   double Hb = cb.H, Hnb = cb.Hn, Htb = cb.Ht, taub = cb.tau, unb = cb.un, utb = cb.ut;
   double dQb = 0.0;
   if (r.cb > 0.0) {
-    const double Xb = cb.cb * 0.5 / r.cb;
+    const double Xb = cb.cb * 0.5 * r.icb;
     Hnb += Xb * 2.0 * r.Hn;
     Hb += Xb * 2.0 * P.g * r.H * r.dQ;
     dQb = Xb * P.g * r.H * r.H;
@@ -404,24 +412,22 @@ __device__ __forceinline__ void newton_eval_bar(const NewtonConst<double>& c, co
 
 // Product of the transposed Jacobian of one interface's fluctuations with
 // the cotangents Amb (of A-) and Apb (of A+), added to ub[0..7] (left then
-// right state, frame order), Ab, mb (A_g, m_g).  u, A, m: as jac_pass.  The
-// value pass solves for the root as the step does (false if it fails), or,
-// given the root p_root > 0 and the doublings of a (retries_in) that the
-// forward solve of this interface at this state kept, evaluates the states
-// and F' there once instead of iterating.
-// GRASS: the Grass law (else a Shields-parameter law), compiled separately
-// to keep each form's registers.
+// right state, frame order), Ab, mb (A_g, m_g), from the projected cells L, R
+// and their records rL, rR (project_grass_rec / project_shields_rec, or the
+// same values computed once per cell).  The value pass solves for the root
+// as the step does (false if it fails), or, given the root p_root > 0 and the
+// doublings of a (retries_in) that the forward solve of this interface at
+// this state kept, evaluates the states and F' there once instead of
+// iterating.  GRASS: the Grass law (else a Shields-parameter law), compiled
+// separately to keep each form's registers.
 template <bool GRASS = true>
-__device__ __forceinline__ bool interface_vjp(const DevParams& P, const double u[8], double A, double m,
-                                              const double Amb[4], const double Apb[4], double ub[8], double& Ab,
-                                              double& mb, double& Kb, double p_root = 0.0, int retries_in = 0) {
+__device__ __forceinline__ bool interface_vjp_cells(const DevParams& P, const Cell<double>& L,
+                                                    const Cell<double>& R, const ProjRec& rL, const ProjRec& rR,
+                                                    double A, double m, const double Amb[4], const double Apb[4],
+                                                    double ub[8], double& Ab, double& mb, double& Kb,
+                                                    double p_root = 0.0, int retries_in = 0) {
   // ---- value pass
-  ProjRec rL, rR;
   constexpr bool grass = GRASS;
-  const Cell<double> L = grass ? project_grass_rec(P, u[0], u[1], u[2], u[3], A, m, rL)
-                               : project_shields_rec(P, u[0], u[1], u[2], u[3], rL);
-  const Cell<double> R = grass ? project_grass_rec(P, u[4], u[5], u[6], u[7], A, m, rR)
-                               : project_shields_rec(P, u[4], u[5], u[6], u[7], rR);
   const double g = P.g;
   // celerities (as celerities(), keeping the branches)
   const bool a0L = L.ca >= R.ca, b0L = L.cb >= R.cb;
@@ -554,14 +560,23 @@ __device__ __forceinline__ bool interface_vjp(const DevParams& P, const double u
   Rb.un += FqRb * R.Hn;
   Rb.Pi += FqRb;
   Rb.ut += FvRb * R.Hn;
-  // the evaluation at p*: direct part, then the root through F (implicit
-  // function theorem: Fbar = -pbar / F_p, at fixed p)
-  double pb = 0.0;
-  newton_eval_bar(c, e, pstar, L, R, eb, pb, cb, Lb, Rb);
-  EvalBar fb = {};
-  fb.F = -pb * iFp;
+  // the evaluation at p*, directly and through the root (implicit function
+  // theorem: Fbar = -pbar / F_p at fixed p), in one backward sweep: the
+  // direct cotangent of p, pbar, is the cotangents of the evaluated states
+  // against their derivatives in p (those of newton_deriv), so Fbar is known
+  // before the sweep, and the sweep is linear in its cotangents
+  {
+    const double dm = -c.dN * e.ip * c.inv_K - e.m * e.ip;
+    const double dt1 = 0.5 + 0.5 * dm, dt4 = 0.5 - 0.5 * dm, dt2 = 0.5 * c.dsig;  // dtau3 = dtau2
+    const double dZs = 2.0 * c.K * (e.tau2 * dt2 - e.tau1 * dt1);
+    // u1 = uL + a (tau1 - tauL), u4 = uR - a (tau4 - tauR), lam2 = u1 - b tau1,
+    // lam4 = u4 + b tau4
+    const double pbd = (eb.tau1 + c.a * eb.u1 + c.amb * eb.lam2) * dt1 + (eb.tau2 + eb.tau3) * dt2 +
+                       (eb.tau4 - c.a * eb.u4 - c.amb * eb.lam4) * dt4 + eb.Zs * dZs;
+    eb.F = -pbd * iFp;
+  }
   double pb_unused = 0.0;
-  newton_eval_bar(c, e, pstar, L, R, fb, pb_unused, cb, Lb, Rb);
+  newton_eval_bar(c, e, pstar, L, R, eb, pb_unused, cb, Lb, Rb);
   // Newton constants: a, b, K = (a^2 - b^2)/(2g), inv_b = 1/b,
   // inv_K = 2g/(a^2 - b^2), D = dtau + dPi/a^2, C0 = du + a (tauL + tauR), dZ
   ab += cb.a;
@@ -620,6 +635,20 @@ __device__ __forceinline__ bool interface_vjp(const DevParams& P, const double u
     project_shields_bar(P, rR, Rb, ub + 4, Kb);
   }
   return true;
+}
+
+// The same product from the two cells' conserved states u[0..7] (left then
+// right, frame order), each projected here with its record.
+template <bool GRASS = true>
+__device__ __forceinline__ bool interface_vjp(const DevParams& P, const double u[8], double A, double m,
+                                              const double Amb[4], const double Apb[4], double ub[8], double& Ab,
+                                              double& mb, double& Kb, double p_root = 0.0, int retries_in = 0) {
+  ProjRec rL, rR;
+  const Cell<double> L = GRASS ? project_grass_rec(P, u[0], u[1], u[2], u[3], A, m, rL)
+                               : project_shields_rec(P, u[0], u[1], u[2], u[3], rL);
+  const Cell<double> R = GRASS ? project_grass_rec(P, u[4], u[5], u[6], u[7], A, m, rR)
+                               : project_shields_rec(P, u[4], u[5], u[6], u[7], rR);
+  return interface_vjp_cells<GRASS>(P, L, R, rL, rR, A, m, Amb, Apb, ub, Ab, mb, Kb, p_root, retries_in);
 }
 
 }  // namespace sve
