@@ -6,19 +6,24 @@
 // reverse sweep propagates lambda^n = (dU^{n+1}/dU^n)^T lambda^{n+1}:
 //   adj_friction_kernel  mu = (dFric/dU~)^T lambda^{n+1} per cell (closed form),
 //                        and the friction coefficient's gradient;
+//   adj_cells_kernel     the projection of every cell (ghosts included) with
+//                        the record its backward sweep needs, once per step;
 //   adj_interface_kernel per interface, the product of the transposed
 //                        Jacobian of (A-, A+) -- with respect to both cells'
 //                        conserved states, A_g and m_g -- with mu of both
-//                        cells, in reverse mode (interface_vjp of
+//                        cells, in reverse mode (interface_vjp_cells of
 //                        sve_adjoint_jac.cuh: one value pass through the
-//                        step's own templates, one hand-written backward
-//                        sweep; the Newton root enters through the implicit
-//                        function theorem at the converged p); tested
-//                        against forward-mode dual numbers through the same
-//                        templates;
+//                        step's own templates at the kept Newton root, one
+//                        hand-written backward sweep; the root enters through
+//                        the implicit function theorem), up to the transport
+//                        law: the cotangents of the cells' Omega and dQ are
+//                        passed on; tested against forward-mode dual numbers
+//                        through the same templates;
 //   adj_gather_kernel    lambda^n = mu + the contributions of the cell's four
-//                        interfaces, ghost cells routed back to the cells they
-//                        copy (the transposed ghost rule).
+//                        interfaces, the law's part of the cell's projection
+//                        once per frame for the sum of its two interfaces, ghost
+//                        cells routed back to the cells they copy (the
+//                        transposed ghost rule); the law parameters' gradients.
 // Forward states are recomputed per segment from checkpoints taken every C
 // steps (C ~ sqrt(N)): memory of ~2 sqrt(N) states, one extra forward pass.
 // Supported: FP64 state, Grass bedload (A_g, m_g), any friction law (its
@@ -58,6 +63,8 @@ struct sve_adjoint_rec {
   size_t rtry_cap = 0;
   double* cells = nullptr;          // per-cell projection record of the state being reversed (adj_cells_kernel)
   size_t cells_cap = 0;
+  double* q = nullptr;              // per interface, the cotangents of both cells' (Omega, dQ) (4 planes)
+  size_t q_cap = 0;
   double* lam = nullptr;            // 2 x 4 interior planes (current, next)
   double* mu = nullptr;             // 4 interior planes
   double* gpart = nullptr;          // per-block parameter partials
@@ -197,7 +204,8 @@ enum AdjCellPlane {
 
 // The projection record of every padded cell with a positive depth, in the
 // x frame and (2D) the y frame, by the adjoint's own projection
-// (project_grass_rec / project_shields_rec).
+// (project_grass_rec / project_shields_rec in the x frame; in the y frame
+// only Omega, dQ, cb and 1/cb differ).
 template <bool GRASS>
 __global__ void __launch_bounds__(kAdjThreads) adj_cells_kernel(DevParams P, DevState<double> S, double A,
                                                                 double m, double* cells, long long next) {
@@ -219,9 +227,12 @@ __global__ void __launch_bounds__(kAdjThreads) adj_cells_kernel(DevParams P, Dev
   put(kCU, cx.un); put(kCV, cx.ut);
   put(kCOmx, cx.Om); put(kCCbx, cx.cb); put(kCIcbx, r.icb); put(kCDQx, r.dQ);
   if (P.dim == 2) {
-    const Cell<double> cy = GRASS ? sve::project_grass_rec(P, H, Hv, Hu, Z, A, m, r)
-                                  : sve::project_shields_rec(P, H, Hv, Hu, Z, r);
-    put(kCOmy, cy.Om); put(kCCby, cy.cb); put(kCIcby, r.icb); put(kCDQy, r.dQ);
+    // y frame: normal velocity v, tangential u
+    double Q, dQ;
+    if (GRASS) sve::grass_q(r, cx.ut, A, m, Q, dQ);
+    else sve::shields_q(P, r, cx.ut, cx.un, Q, dQ);
+    const double cb = sqrt(Hv * Hv + P.g * H * H * dQ);
+    put(kCOmy, Q); put(kCCby, cb); put(kCIcby, cb > 0.0 ? 1.0 / cb : 0.0); put(kCDQy, dQ);
   }
 }
 
@@ -269,96 +280,77 @@ __device__ __forceinline__ Cell<double> adj_load_cell(const DevState<double>& S,
 }
 
 // Per interface: the Jacobian-transpose product of its fluctuations with mu of
-// its two cells (a ghost side has mu = 0), stored in the fluctuation planes
-// (8 values: left state then right state, interface frame); A_g and m_g
-// gradients accumulated.  The cells' projections and records come from the
-// planes of adj_cells_kernel.
+// its two cells (a ghost side has mu = 0) up to the transport law: the
+// cotangents of both cells' conserved states in the fluctuation planes (8
+// values: left state then right state, interface frame) and those of both
+// cells' (Omega, dQ) in the planes of q (4 values: left then right), which
+// adj_gather_kernel takes through the law once per cell.  The cells'
+// projections and records come from the planes of adj_cells_kernel.
 template <bool GRASS>
 __global__ void __launch_bounds__(kAdjThreads) adj_interface_kernel(DevParams P, DevState<double> S,
                                                                     const double* mu, double dt, double A,
                                                                     double m, const double* roots,
                                                                     const unsigned char* rtry, const double* cells,
-                                                                    long long next, double* gpart,
-                                                                    double* gacc, unsigned int* done) {
-  __shared__ double sh[kAdjThreads / 32];
+                                                                    long long next, double* q) {
   const long long ncell = (long long)P.nx * P.ny;
   const long long nall = P.nfx + P.nfy;
   const long long idx = (long long)blockIdx.x * kAdjThreads + threadIdx.x;
-  double gA = 0.0, gm = 0.0;
-  if (idx < nall) {
-    const bool ydir = idx >= P.nfx;
-    const long long k = ydir ? idx - P.nfx : idx;
-    int iL, jL, iR, jR;
-    if (!ydir) {
-      jR = (int)(k / (P.nx + 1));
-      iR = (int)(k - (long long)jR * (P.nx + 1));
-      iL = iR - 1;
-      jL = jR;
-    } else {
-      jR = (int)(k / P.nx);
-      iR = (int)(k - (long long)jR * P.nx);
-      iL = iR;
-      jL = jR - 1;
-    }
-    const long long eL = sve::ext_index(P, iL, jL), eR = sve::ext_index(P, iR, jR);
-    const bool inL = iL >= 0 && iL < P.nx && jL >= 0 && jL < P.ny;
-    const bool inR = iR >= 0 && iR < P.nx && jR >= 0 && jR < P.ny;
-    const int cn = ydir ? 2 : 1, ct = ydir ? 1 : 2;  // normal / tangential component in (h, hu, hv, z)
-    double muL[4] = {0, 0, 0, 0}, muR[4] = {0, 0, 0, 0};
-    if (inL) {
-      const long long c = (long long)jL * P.nx + iL;
-      muL[0] = mu[c]; muL[1] = mu[cn * ncell + c]; muL[2] = mu[ct * ncell + c]; muL[3] = mu[3 * ncell + c];
-    }
-    if (inR) {
-      const long long c = (long long)jR * P.nx + iR;
-      muR[0] = mu[c]; muR[1] = mu[cn * ncell + c]; muR[2] = mu[ct * ncell + c]; muR[3] = mu[3 * ncell + c];
-    }
-    double out[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
-    bool any = false;
-#pragma unroll
-    for (int c = 0; c < 4; ++c) any = any || muL[c] != 0.0 || muR[c] != 0.0;
-    if (any) {
-      sve::ProjRec rL, rR;
-      const Cell<double> L = adj_load_cell<GRASS>(S, cells, next, eL, ydir, rL);
-      const Cell<double> R = adj_load_cell<GRASS>(S, cells, next, eR, ydir, rR);
-      // reverse mode: the transposed Jacobian of the fluctuations applied
-      // to -dt/dx (mu of the left cell, mu of the right cell)
-      const double w = -dt * (ydir ? P.inv_dy : P.inv_dx);
-      double Amb[4], Apb[4];
-#pragma unroll
-      for (int q = 0; q < 4; ++q) { Amb[q] = w * muL[q]; Apb[q] = w * muR[q]; }
-      double ub[8] = {0, 0, 0, 0, 0, 0, 0, 0}, Ab = 0.0, mb = 0.0, Kb = 0.0;
-      // (the forward run solved this interface at this state; a failure
-      // here leaves its contribution at zero, as the value pass did before)
-      // the forward solve's root (kept by the recording or the segment's
-      // recompute) spares the value pass its Newton iteration
-      sve::interface_vjp_cells<GRASS>(P, L, R, rL, rR, A, m, Amb, Apb, ub, Ab, mb, Kb, roots[idx], (int)rtry[idx]);
-#pragma unroll
-      for (int q = 0; q < 8; ++q) out[q] = ub[q];
-      // Grass: the A_g and m_g gradients; Shields laws: the friction
-      // coefficient's (through tau*)
-      out[8] = GRASS ? Ab : Kb;
-      out[9] = mb;
-    }
-    double* v = ydir ? S.fy : S.fx;
-    const long long nf = ydir ? P.nfy : P.nfx;
-#pragma unroll
-    for (int q = 0; q < 8; ++q) v[q * nf + k] = out[q];
-    gA = out[8];
-    gm = out[9];
-  }
-  const double bA = block_sum(gA, sh);
-  const double bm = block_sum(gm, sh);
-  if (GRASS) {
-    if (threadIdx.x == 0) {
-      gpart[2 * blockIdx.x] = bA;
-      gpart[2 * blockIdx.x + 1] = bm;
-    }
-    finish_partials<kAdjThreads>(gpart, 2, gacc, done);
+  if (idx >= nall) return;
+  const bool ydir = idx >= P.nfx;
+  const long long k = ydir ? idx - P.nfx : idx;
+  int iL, jL, iR, jR;
+  if (!ydir) {
+    jR = (int)(k / (P.nx + 1));
+    iR = (int)(k - (long long)jR * (P.nx + 1));
+    iL = iR - 1;
+    jL = jR;
   } else {
-    if (threadIdx.x == 0) gpart[blockIdx.x] = bA;  // d/d(friction coefficient) through tau*
-    finish_partials<kAdjThreads>(gpart, 1, gacc + 2, done);
+    jR = (int)(k / P.nx);
+    iR = (int)(k - (long long)jR * P.nx);
+    iL = iR;
+    jL = jR - 1;
   }
+  const long long eL = sve::ext_index(P, iL, jL), eR = sve::ext_index(P, iR, jR);
+  const bool inL = iL >= 0 && iL < P.nx && jL >= 0 && jL < P.ny;
+  const bool inR = iR >= 0 && iR < P.nx && jR >= 0 && jR < P.ny;
+  const int cn = ydir ? 2 : 1, ct = ydir ? 1 : 2;  // normal / tangential component in (h, hu, hv, z)
+  double muL[4] = {0, 0, 0, 0}, muR[4] = {0, 0, 0, 0};
+  if (inL) {
+    const long long c = (long long)jL * P.nx + iL;
+    muL[0] = mu[c]; muL[1] = mu[cn * ncell + c]; muL[2] = mu[ct * ncell + c]; muL[3] = mu[3 * ncell + c];
+  }
+  if (inR) {
+    const long long c = (long long)jR * P.nx + iR;
+    muR[0] = mu[c]; muR[1] = mu[cn * ncell + c]; muR[2] = mu[ct * ncell + c]; muR[3] = mu[3 * ncell + c];
+  }
+  double ub[8] = {0, 0, 0, 0, 0, 0, 0, 0}, qb[4] = {0, 0, 0, 0};
+  bool any = false;
+#pragma unroll
+  for (int c = 0; c < 4; ++c) any = any || muL[c] != 0.0 || muR[c] != 0.0;
+  if (any) {
+    sve::ProjRec rL, rR;
+    const Cell<double> L = adj_load_cell<GRASS>(S, cells, next, eL, ydir, rL);
+    const Cell<double> R = adj_load_cell<GRASS>(S, cells, next, eR, ydir, rR);
+    // reverse mode: the transposed Jacobian of the fluctuations applied
+    // to -dt/dx (mu of the left cell, mu of the right cell)
+    const double w = -dt * (ydir ? P.inv_dy : P.inv_dx);
+    double Amb[4], Apb[4];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) { Amb[c] = w * muL[c]; Apb[c] = w * muR[c]; }
+    double Ab = 0.0, mb = 0.0, Kb = 0.0;  // (the laws' part is adj_gather_kernel's)
+    // (the forward run solved this interface at this state; a failure here
+    // leaves its contribution at zero, as the value pass did before) the
+    // forward solve's root (kept by the recording or the segment's
+    // recompute) spares the value pass its Newton iteration
+    sve::interface_vjp_cells<GRASS>(P, L, R, rL, rR, A, m, Amb, Apb, ub, Ab, mb, Kb, roots[idx], (int)rtry[idx],
+                                    qb);
+  }
+  double* v = ydir ? S.fy : S.fx;
+  const long long nf = ydir ? P.nfy : P.nfx;
+#pragma unroll
+  for (int c = 0; c < 8; ++c) v[c * nf + k] = ub[c];
+#pragma unroll
+  for (int c = 0; c < 4; ++c) q[c * nall + idx] = qb[c];
 }
 
 // Transposed ghost rule of side s in the side's frame (h, normal, tangential,
@@ -373,61 +365,125 @@ __device__ __forceinline__ void ghost_transpose(int type, double g[4]) {
   }
 }
 
+// The law's part of a cell's (or ghost's) projection backward in one frame:
+// the cotangents (Qb, dQb) of its Omega and dQ, summed over the interfaces of
+// that frame, taken to its conserved state (H, Hn, Ht) in the frame order.
+template <bool GRASS>
+__device__ __forceinline__ void law_bar(const DevParams& P, const DevState<double>& S, const double* cells,
+                                        long long next, long long e, bool ydir, double A, double m, double Qb,
+                                        double dQb, double g[3], double& Ab, double& mb, double& Kb) {
+  if (Qb == 0.0 && dQb == 0.0) return;
+  sve::ProjRec r;
+  adj_load_cell<GRASS>(S, cells, next, e, ydir, r);
+  double unb = 0.0, utb = 0.0, Hb = 0.0, Hnb = 0.0, Htb = 0.0;
+  sve::closure_bar<GRASS>(P, r, A, m, Qb, dQb, unb, utb, Hb, Ab, mb, Kb);
+  sve::vel_fold_bar(r, unb, utb, 0.0, Hb, Hnb, Htb);
+  g[0] += Hb;
+  g[1] += Hnb;
+  g[2] += Htb;
+}
+
+// lambda^n per interior cell: mu, plus the cotangents of the cell's four
+// interfaces (their conserved parts, and the law's part of the cell's
+// projection for the sum over each frame's two interfaces), ghost cells
+// routed back to the cells they copy (the law's part with the ghost's own
+// record, then the transposed ghost rule); the parameters' gradients of the
+// law's part accumulated.
+template <bool GRASS>
 __global__ void __launch_bounds__(kAdjThreads) adj_gather_kernel(DevParams P, DevState<double> S, const double* mu,
-                                                                 double* lam) {
+                                                                 const double* q, const double* cells,
+                                                                 long long next, double A, double m, double* lam,
+                                                                 double* gpart, double* gacc, unsigned int* done) {
+  __shared__ double sh[kAdjThreads / 32];
   const long long ncell = (long long)P.nx * P.ny;
   const long long k = (long long)blockIdx.x * kAdjThreads + threadIdx.x;
-  if (k >= ncell) return;
-  const int j = (int)(k / P.nx), i = (int)(k - (long long)j * P.nx);
-  const long long nfx = P.nfx, nfy = P.nfy;
-  double r[4] = {mu[k], mu[ncell + k], mu[2 * ncell + k], mu[3 * ncell + k]};
-  // x: as the right cell of interface (i - 1/2, j), as the left cell of (i + 1/2, j)
-  const long long kx = (long long)j * (P.nx + 1) + i;
+  double Ab = 0.0, mb = 0.0, Kb = 0.0;
+  if (k < ncell) {
+    const int j = (int)(k / P.nx), i = (int)(k - (long long)j * P.nx);
+    const long long nfx = P.nfx, nfy = P.nfy, nall = nfx + nfy;
+    const long long e = sve::ext_index(P, i, j);
+    double r[4] = {mu[k], mu[ncell + k], mu[2 * ncell + k], mu[3 * ncell + k]};
+    // x: as the right cell of interface (i - 1/2, j), as the left cell of (i + 1/2, j)
+    const long long kx = (long long)j * (P.nx + 1) + i;
 #pragma unroll
-  for (int c = 0; c < 4; ++c) r[c] += S.fx[(4 + c) * nfx + kx] + S.fx[c * nfx + kx + 1];
-  if (P.dim == 2) {
-    // y frame (h, hv, hu, z)
-    const long long ky = (long long)j * P.nx + i;
-    const double* y = S.fy;
-    r[0] += y[4 * nfy + ky] + y[0 * nfy + ky + P.nx];
-    r[2] += y[5 * nfy + ky] + y[1 * nfy + ky + P.nx];
-    r[1] += y[6 * nfy + ky] + y[2 * nfy + ky + P.nx];
-    r[3] += y[7 * nfy + ky] + y[3 * nfy + ky + P.nx];
-  }
-  // ghosts this cell feeds: their adjoint flows back through the ghost rule
-  double g[4];
-  const bool perx = P.bc[0] == sve::GHOST_PERIODIC;
-  if ((!perx && i == 0) || (perx && i == P.nx - 1)) {  // W ghost: left state of (0 - 1/2, j)
-    const long long kk = (long long)j * (P.nx + 1);
-    for (int c = 0; c < 4; ++c) g[c] = S.fx[c * nfx + kk];
-    ghost_transpose(P.bc[0], g);
-    for (int c = 0; c < 4; ++c) r[c] += g[c];
-  }
-  if ((!perx && i == P.nx - 1) || (perx && i == 0)) {  // E ghost: right state of (nx - 1/2, j)
-    const long long kk = (long long)j * (P.nx + 1) + P.nx;
-    for (int c = 0; c < 4; ++c) g[c] = S.fx[(4 + c) * nfx + kk];
-    ghost_transpose(P.bc[1], g);
-    for (int c = 0; c < 4; ++c) r[c] += g[c];
-  }
-  if (P.dim == 2) {
-    const bool pery = P.bc[2] == sve::GHOST_PERIODIC;
-    if ((!pery && j == 0) || (pery && j == P.ny - 1)) {  // S ghost: left state of (i, 0 - 1/2)
-      const long long kk = i;
-      for (int c = 0; c < 4; ++c) g[c] = S.fy[c * nfy + kk];
-      ghost_transpose(P.bc[2], g);
-      r[0] += g[0]; r[2] += g[1]; r[1] += g[2]; r[3] += g[3];
+    for (int c = 0; c < 4; ++c) r[c] += S.fx[(4 + c) * nfx + kx] + S.fx[c * nfx + kx + 1];
+    {
+      double g[3] = {0.0, 0.0, 0.0};
+      law_bar<GRASS>(P, S, cells, next, e, false, A, m, q[2 * nall + kx] + q[kx + 1],
+                     q[3 * nall + kx] + q[nall + kx + 1], g, Ab, mb, Kb);
+      r[0] += g[0]; r[1] += g[1]; r[2] += g[2];
     }
-    if ((!pery && j == P.ny - 1) || (pery && j == 0)) {  // N ghost: right state of (i, ny - 1/2)
-      const long long kk = (long long)P.ny * P.nx + i;
-      for (int c = 0; c < 4; ++c) g[c] = S.fy[(4 + c) * nfy + kk];
-      ghost_transpose(P.bc[3], g);
-      r[0] += g[0]; r[2] += g[1]; r[1] += g[2]; r[3] += g[3];
+    if (P.dim == 2) {
+      // y frame (h, hv, hu, z)
+      const long long ky = (long long)j * P.nx + i;
+      const double* y = S.fy;
+      r[0] += y[4 * nfy + ky] + y[0 * nfy + ky + P.nx];
+      r[2] += y[5 * nfy + ky] + y[1 * nfy + ky + P.nx];
+      r[1] += y[6 * nfy + ky] + y[2 * nfy + ky + P.nx];
+      r[3] += y[7 * nfy + ky] + y[3 * nfy + ky + P.nx];
+      double g[3] = {0.0, 0.0, 0.0};
+      const long long qy = nfx + ky;
+      law_bar<GRASS>(P, S, cells, next, e, true, A, m, q[2 * nall + qy] + q[qy + P.nx],
+                     q[3 * nall + qy] + q[nall + qy + P.nx], g, Ab, mb, Kb);
+      r[0] += g[0]; r[2] += g[1]; r[1] += g[2];
     }
+    // ghosts this cell feeds: their adjoint flows back through the ghost rule
+    double g[4];
+    const bool perx = P.bc[0] == sve::GHOST_PERIODIC;
+    if ((!perx && i == 0) || (perx && i == P.nx - 1)) {  // W ghost: left state of (0 - 1/2, j)
+      const long long kk = (long long)j * (P.nx + 1);
+      for (int c = 0; c < 4; ++c) g[c] = S.fx[c * nfx + kk];
+      law_bar<GRASS>(P, S, cells, next, sve::ext_index(P, -1, j), false, A, m, q[kk], q[nall + kk], g, Ab, mb, Kb);
+      ghost_transpose(P.bc[0], g);
+      for (int c = 0; c < 4; ++c) r[c] += g[c];
+    }
+    if ((!perx && i == P.nx - 1) || (perx && i == 0)) {  // E ghost: right state of (nx - 1/2, j)
+      const long long kk = (long long)j * (P.nx + 1) + P.nx;
+      for (int c = 0; c < 4; ++c) g[c] = S.fx[(4 + c) * nfx + kk];
+      law_bar<GRASS>(P, S, cells, next, sve::ext_index(P, P.nx, j), false, A, m, q[2 * nall + kk],
+                     q[3 * nall + kk], g, Ab, mb, Kb);
+      ghost_transpose(P.bc[1], g);
+      for (int c = 0; c < 4; ++c) r[c] += g[c];
+    }
+    if (P.dim == 2) {
+      const bool pery = P.bc[2] == sve::GHOST_PERIODIC;
+      if ((!pery && j == 0) || (pery && j == P.ny - 1)) {  // S ghost: left state of (i, 0 - 1/2)
+        const long long kk = i;
+        for (int c = 0; c < 4; ++c) g[c] = S.fy[c * nfy + kk];
+        law_bar<GRASS>(P, S, cells, next, sve::ext_index(P, i, -1), true, A, m, q[nfx + kk], q[nall + nfx + kk], g,
+                       Ab, mb, Kb);
+        ghost_transpose(P.bc[2], g);
+        r[0] += g[0]; r[2] += g[1]; r[1] += g[2]; r[3] += g[3];
+      }
+      if ((!pery && j == P.ny - 1) || (pery && j == 0)) {  // N ghost: right state of (i, ny - 1/2)
+        const long long kk = (long long)P.ny * P.nx + i;
+        for (int c = 0; c < 4; ++c) g[c] = S.fy[(4 + c) * nfy + kk];
+        law_bar<GRASS>(P, S, cells, next, sve::ext_index(P, i, P.ny), true, A, m, q[2 * nall + nfx + kk],
+                       q[3 * nall + nfx + kk], g, Ab, mb, Kb);
+        ghost_transpose(P.bc[3], g);
+        r[0] += g[0]; r[2] += g[1]; r[1] += g[2]; r[3] += g[3];
+      }
+    }
+    lam[k] = r[0];
+    lam[ncell + k] = r[1];
+    lam[2 * ncell + k] = r[2];
+    lam[3 * ncell + k] = r[3];
   }
-  lam[k] = r[0];
-  lam[ncell + k] = r[1];
-  lam[2 * ncell + k] = r[2];
-  lam[3 * ncell + k] = r[3];
+  // Grass: the A_g and m_g gradients; Shields laws: the friction
+  // coefficient's (through tau*)
+  if (GRASS) {
+    const double bA = block_sum(Ab, sh);
+    const double bm = block_sum(mb, sh);
+    if (threadIdx.x == 0) {
+      gpart[2 * blockIdx.x] = bA;
+      gpart[2 * blockIdx.x + 1] = bm;
+    }
+    finish_partials<kAdjThreads>(gpart, 2, gacc, done);
+  } else {
+    const double bK = block_sum(Kb, sh);
+    if (threadIdx.x == 0) gpart[blockIdx.x] = bK;
+    finish_partials<kAdjThreads>(gpart, 1, gacc + 2, done);
+  }
 }
 
 #define ADJ_TRY(expr)                               \
@@ -478,6 +534,7 @@ void free_rec(sve_adjoint_rec* r) {
   if (r->roots) cudaFree(r->roots);
   if (r->rtry) cudaFree(r->rtry);
   if (r->cells) cudaFree(r->cells);
+  if (r->q) cudaFree(r->q);
   if (r->lam) cudaFree(r->lam);
   if (r->mu) cudaFree(r->mu);
   if (r->gpart) cudaFree(r->gpart);
@@ -633,6 +690,8 @@ int sve_adjoint(sve_handle* h, const void* lam_h, const void* lam_hu, const void
   if (rc) return rc;
   rc = grow(&r->cells, &r->cells_cap, (size_t)kCPlanes * (size_t)h->next);
   if (rc) return rc;
+  rc = grow(&r->q, &r->q_cap, 4 * nf);
+  if (rc) return rc;
   const unsigned nb_pad = (unsigned)((h->next + kAdjThreads - 1) / kAdjThreads);
   double* lam = r->lam;             // lambda^{n+1}
   double* lam_next = r->lam + 4 * ncell;
@@ -676,20 +735,20 @@ int sve_adjoint(sve_handle* h, const void* lam_h, const void* lam_hu, const void
                                                               r->mu, dt, r->gpart, r->gacc, r->done);
       const double* roots = r->roots + (size_t)s * nf;
       const unsigned char* rtry = r->rtry + (size_t)s * nf;
+      const double A = h->cfg.A_g, m = h->cfg.m_g;
       if (P.bedload == 0) {
-        adj_cells_kernel<true><<<nb_pad, kAdjThreads, 0, h->stream>>>(P, S, h->cfg.A_g, h->cfg.m_g, r->cells,
-                                                                      h->next);
-        adj_interface_kernel<true><<<nb_if, kAdjThreads, 0, h->stream>>>(P, S, r->mu, dt, h->cfg.A_g, h->cfg.m_g,
-                                                                         roots, rtry, r->cells, h->next, r->gpart,
-                                                                         r->gacc, r->done);
+        adj_cells_kernel<true><<<nb_pad, kAdjThreads, 0, h->stream>>>(P, S, A, m, r->cells, h->next);
+        adj_interface_kernel<true><<<nb_if, kAdjThreads, 0, h->stream>>>(P, S, r->mu, dt, A, m, roots, rtry,
+                                                                         r->cells, h->next, r->q);
+        adj_gather_kernel<true><<<nb_c, kAdjThreads, 0, h->stream>>>(P, S, r->mu, r->q, r->cells, h->next, A, m,
+                                                                     lam_next, r->gpart, r->gacc, r->done);
       } else {
-        adj_cells_kernel<false><<<nb_pad, kAdjThreads, 0, h->stream>>>(P, S, h->cfg.A_g, h->cfg.m_g, r->cells,
-                                                                       h->next);
-        adj_interface_kernel<false><<<nb_if, kAdjThreads, 0, h->stream>>>(P, S, r->mu, dt, h->cfg.A_g, h->cfg.m_g,
-                                                                          roots, rtry, r->cells, h->next, r->gpart,
-                                                                          r->gacc, r->done);
+        adj_cells_kernel<false><<<nb_pad, kAdjThreads, 0, h->stream>>>(P, S, A, m, r->cells, h->next);
+        adj_interface_kernel<false><<<nb_if, kAdjThreads, 0, h->stream>>>(P, S, r->mu, dt, A, m, roots, rtry,
+                                                                          r->cells, h->next, r->q);
+        adj_gather_kernel<false><<<nb_c, kAdjThreads, 0, h->stream>>>(P, S, r->mu, r->q, r->cells, h->next, A,
+                                                                      m, lam_next, r->gpart, r->gacc, r->done);
       }
-      adj_gather_kernel<<<nb_c, kAdjThreads, 0, h->stream>>>(P, S, r->mu, lam_next);
       if (cudaGetLastError() != cudaSuccess) return SVE_ERR_CUDA;
       double* t = lam;
       lam = lam_next;

@@ -150,6 +150,19 @@ __device__ __forceinline__ bool shields_rate2(const DevParams& P, double ts, dou
   }
 }
 
+// Omega = Q and dQ/dun of a Shields-parameter law for the normal velocity un
+// and the tangential ut, from the record (as project_shields_rec computes it).
+__device__ __forceinline__ void shields_q(const DevParams& P, const ProjRec& r, double un, double ut, double& Q,
+                                          double& dQ) {
+  Q = 0.0;
+  dQ = 0.0;
+  if (r.active) {
+    const double C = P.qs_scale;
+    Q = C * r.q * (un * r.isp);
+    dQ = C * (2.0 * r.dq * r.alpha * (un * un) * r.isp + r.q * (ut * ut) * (r.isp * r.isp * r.isp));
+  }
+}
+
 // Projection of one side with a Shields-parameter law (as closure() in the
 // interface frame), keeping its record.
 __device__ __forceinline__ Cell<double> project_shields_rec(const DevParams& P, double H, double Hn, double Ht,
@@ -164,13 +177,9 @@ __device__ __forceinline__ Cell<double> project_shields_rec(const DevParams& P, 
   r.alpha = P.mpm_alpha;
   if (P.friction != 1) r.alpha = r.alpha * rcbrt64(H);  // Manning: tau* over h^(1/3)
   r.active = r.s2 > 0.0 && shields_rate2(P, r.alpha * r.s2, r.q, r.dq, r.ddq);
-  double Q = 0.0, dQ = 0.0;
-  if (r.active) {
-    r.isp = 1.0 / sqrt(r.s2);
-    const double C = P.qs_scale;
-    Q = C * r.q * (c.un * r.isp);
-    dQ = C * (2.0 * r.dq * r.alpha * (c.un * c.un) * r.isp + r.q * (c.ut * c.ut) * (r.isp * r.isp * r.isp));
-  }
+  if (r.active) r.isp = 1.0 / sqrt(r.s2);
+  double Q, dQ;
+  shields_q(P, r, c.un, c.ut, Q, dQ);
   c.Om = Q;
   c.ca = H * sqrt(P.g * H);
   c.cb = sqrt(Hn * Hn + P.g * H * H * dQ);
@@ -188,6 +197,18 @@ struct CellBar {
   double H, Hn, Ht, Z, tau, un, ut, Pi, Om, ca, cb;
 };
 
+// Omega = Q and dQ/dun of the Grass law for the normal velocity un, from the
+// powers of |U| in the record (as project_grass_rec computes them).
+__device__ __forceinline__ void grass_q(const ProjRec& r, double un, double A, double m, double& Q, double& dQ) {
+  if (r.still) {
+    Q = 0.0;
+    dQ = (m == 1.0) ? A : 0.0;
+  } else {
+    Q = A * un * r.pm1;
+    dQ = A * (r.pm1 + (m - 1.0) * (un * un) * r.pm3);
+  }
+}
+
 __device__ __forceinline__ Cell<double> project_grass_rec(const DevParams& P, double H, double Hn, double Ht,
                                                           double Z, double A, double m, ProjRec& r) {
   Cell<double> c;
@@ -198,10 +219,7 @@ __device__ __forceinline__ Cell<double> project_grass_rec(const DevParams& P, do
   c.Pi = 0.5 * P.g * H * H;
   const double s2 = c.un * c.un + c.ut * c.ut;
   r.still = s2 == 0.0;
-  double Q, dQ;
   if (r.still) {
-    Q = 0.0;
-    dQ = (m == 1.0) ? A : 0.0;
     r.sp = r.pm1 = r.pm3 = 0.0;
   } else {
     r.sp = sqrt(s2);
@@ -212,9 +230,9 @@ __device__ __forceinline__ Cell<double> project_grass_rec(const DevParams& P, do
     else if (m == 4.0) { r.pm1 = s2 * r.sp; r.pm3 = r.sp; }
     else if (m == 1.0) { r.pm1 = 1.0; r.pm3 = 1.0 / s2; }
     else { r.pm1 = pow(r.sp, m - 1.0); r.pm3 = pow(r.sp, m - 3.0); }
-    Q = A * c.un * r.pm1;
-    dQ = A * (r.pm1 + (m - 1.0) * (c.un * c.un) * r.pm3);
   }
+  double Q, dQ;
+  grass_q(r, c.un, A, m, Q, dQ);
   c.Om = Q;
   c.ca = H * sqrt(P.g * H);
   c.cb = sqrt(Hn * Hn + P.g * H * H * dQ);
@@ -235,64 +253,31 @@ __device__ __forceinline__ Cell<double> project_grass_rec(const DevParams& P, do
   return c;
 }
 
-// Backward sweep of project_grass: cotangents of the cell's fields -> of
-// (H, Hn, Ht, Z) in ub[0..3], A_g, m_g.
-__device__ __forceinline__ void project_grass_bar(const DevParams& P, const ProjRec& r, double A, double m,
-                                                  CellBar cb, double ub[4], double& Ab, double& mb) {
-  double Hb = cb.H, Hnb = cb.Hn, Htb = cb.Ht, taub = cb.tau, unb = cb.un, utb = cb.ut;
-  const double icb = r.icb, isp = r.isp;
-  // cb = sqrt(Hn^2 + g H^2 dQ)
-  double dQb = 0.0;
-  if (r.cb > 0.0) {
-    const double Xb = cb.cb * 0.5 * icb;
-    Hnb += Xb * 2.0 * r.Hn;
-    Hb += Xb * 2.0 * P.g * r.H * r.dQ;
-    dQb = Xb * P.g * r.H * r.H;
-  }
-  // ca = H sqrt(g H)
-  Hb += cb.ca * 1.5 * r.ca * r.tau;
-  // Pi = g H^2 / 2
-  Hb += cb.Pi * P.g * r.H;
-  // Om = Q = A un |U|^(m-1); dQ = A (|U|^(m-1) + (m-1) un^2 |U|^(m-3))
-  if (r.still) {
-    if (m == 1.0) Ab += dQb;
-  } else {
-    const double Qb = cb.Om;
-    const double un2 = r.un * r.un;
-    const double second = (m - 1.0) * un2 * r.pm3;
-    Ab += Qb * r.un * r.pm1 + dQb * (r.pm1 + second);
-    unb += Qb * A * r.pm1;
-    double pm1b = Qb * A * r.un + dQb * A;
-    const double secondb = dQb * A;
-    mb += secondb * un2 * r.pm3;
-    unb += secondb * (m - 1.0) * 2.0 * r.un * r.pm3;
-    const double pm3b = secondb * (m - 1.0) * un2;
-    const double lsp = r.lsp;
-    double spb = (pm1b * (m - 1.0) * r.pm1 + pm3b * (m - 3.0) * r.pm3) * isp;
-    mb += pm1b * r.pm1 * lsp + pm3b * r.pm3 * lsp;
-    const double s2b = spb * 0.5 * isp;
-    unb += s2b * 2.0 * r.un;
-    utb += s2b * 2.0 * r.ut;
-  }
-  // un = Hn tau, ut = Ht tau, tau = 1/H
+// The backward sweep of a projection (project_grass_rec /
+// project_shields_rec) in three parts, so that the transport law's part can
+// run once per cell for the sum over the cell's interfaces:
+//   proj_fold_bar   the fields other than Omega: cb = sqrt(Hn^2 + g H^2 dQ)
+//                   (its cotangent passed on to dQ), ca = H sqrt(g H),
+//                   Pi = g H^2 / 2 and (un, ut, tau) -> (H, Hn, Ht, Z), into
+//                   ub[0..3]; qb += the cotangents of (Omega, dQ);
+//   closure_bar     Omega and dQ of the law in the frame of the record ->
+//                   un, ut (unb, utb), H (Hb: a Shields law's alpha through
+//                   h^(-1/3) for Strickler) and the parameters (Ab, mb: A_g,
+//                   m_g of the Grass law; Kb: the friction coefficient in a
+//                   Shields law's tau*);
+//   vel_fold_bar    un = Hn tau, ut = Ht tau, tau = 1/H.
+__device__ __forceinline__ void vel_fold_bar(const ProjRec& r, double unb, double utb, double taub, double& Hb,
+                                             double& Hnb, double& Htb) {
   Hnb += unb * r.tau;
   taub += unb * r.Hn;
   Htb += utb * r.tau;
   taub += utb * r.Ht;
   Hb -= taub * r.tau * r.tau;
-  ub[0] += Hb;
-  ub[1] += Hnb;
-  ub[2] += Htb;
-  ub[3] += cb.Z;
 }
 
-// Backward sweep of project_shields_rec: cotangents of the cell's fields ->
-// of (H, Hn, Ht, Z) in ub[0..3] and of the friction coefficient (Kb:
-// through alpha = f / (8 g (s-1) d_s) for Darcy, n^2 / ((s-1) d_s) h^(-1/3)
-// with n = 1/K for Strickler).
-__device__ __forceinline__ void project_shields_bar(const DevParams& P, const ProjRec& r, CellBar cb, double ub[4],
-                                                    double& Kb) {
-  double Hb = cb.H, Hnb = cb.Hn, Htb = cb.Ht, taub = cb.tau, unb = cb.un, utb = cb.ut;
+__device__ __forceinline__ void proj_fold_bar(const DevParams& P, const ProjRec& r, const CellBar& cb, double ub[4],
+                                              double qb[2]) {
+  double Hb = cb.H, Hnb = cb.Hn, Htb = cb.Ht;
   double dQb = 0.0;
   if (r.cb > 0.0) {
     const double Xb = cb.cb * 0.5 * r.icb;
@@ -300,29 +285,63 @@ __device__ __forceinline__ void project_shields_bar(const DevParams& P, const Pr
     Hb += Xb * 2.0 * P.g * r.H * r.dQ;
     dQb = Xb * P.g * r.H * r.H;
   }
-  Hb += cb.ca * 1.5 * r.ca * r.tau;  // ca = H sqrt(g H)
-  Hb += cb.Pi * P.g * r.H;           // Pi = g H^2 / 2
-  if (r.active) {
+  Hb += cb.ca * 1.5 * r.ca * r.tau;
+  Hb += cb.Pi * P.g * r.H;
+  vel_fold_bar(r, cb.un, cb.ut, cb.tau, Hb, Hnb, Htb);
+  ub[0] += Hb;
+  ub[1] += Hnb;
+  ub[2] += Htb;
+  ub[3] += cb.Z;
+  qb[0] += cb.Om;
+  qb[1] += dQb;
+}
+
+template <bool GRASS>
+__device__ __forceinline__ void closure_bar(const DevParams& P, const ProjRec& r, double A, double m, double Qb,
+                                            double dQb, double& unb, double& utb, double& Hb, double& Ab,
+                                            double& mb, double& Kb) {
+  if constexpr (GRASS) {
+    // Om = Q = A un |U|^(m-1); dQ = A (|U|^(m-1) + (m-1) un^2 |U|^(m-3))
+    if (r.still) {
+      if (m == 1.0) Ab += dQb;
+      return;
+    }
+    const double un2 = r.un * r.un;
+    const double second = (m - 1.0) * un2 * r.pm3;
+    Ab += Qb * r.un * r.pm1 + dQb * (r.pm1 + second);
+    unb += Qb * A * r.pm1;
+    const double pm1b = Qb * A * r.un + dQb * A;
+    const double secondb = dQb * A;
+    mb += secondb * un2 * r.pm3;
+    unb += secondb * (m - 1.0) * 2.0 * r.un * r.pm3;
+    const double pm3b = secondb * (m - 1.0) * un2;
+    const double spb = (pm1b * (m - 1.0) * r.pm1 + pm3b * (m - 3.0) * r.pm3) * r.isp;
+    mb += (pm1b * r.pm1 + pm3b * r.pm3) * r.lsp;
+    const double s2b = spb * 0.5 * r.isp;
+    unb += s2b * 2.0 * r.un;
+    utb += s2b * 2.0 * r.ut;
+  } else {
+    if (!r.active) return;
+    // Q = C q un isp, dQ = C (2 dq alpha un^2 isp + q ut^2 isp^3),
+    // q = q*(ts), dq = dq*/dts(ts), ts = alpha s2, isp = s2^(-1/2)
     const double C = P.qs_scale, isp = r.isp, isp3 = isp * isp * isp;
     const double un = r.un, ut = r.ut;
-    // Q = C q un isp
-    const double Qb = cb.Om;
     double qb = Qb * C * un * isp;
     unb += Qb * C * r.q * isp;
     double ispb = Qb * C * r.q * un;
-    // dQ = C (2 dq alpha un^2 isp + q ut^2 isp^3)
     const double dqb = dQb * C * 2.0 * r.alpha * un * un * isp;
     double alphab = dQb * C * 2.0 * r.dq * un * un * isp;
     unb += dQb * C * 4.0 * r.dq * r.alpha * un * isp;
     ispb += dQb * C * (2.0 * r.dq * r.alpha * un * un + 3.0 * r.q * ut * ut * isp * isp);
     qb += dQb * C * ut * ut * isp3;
     utb += dQb * C * 2.0 * r.q * ut * isp3;
-    // q(ts), dq(ts), ts = alpha s2; isp = s2^(-1/2)
     const double tsb = qb * r.dq + dqb * r.ddq;
     alphab += tsb * r.s2;
     const double s2b = tsb * r.alpha - 0.5 * ispb * isp3;
     unb += 2.0 * un * s2b;
     utb += 2.0 * ut * s2b;
+    // alpha = f / (8 g (s-1) d_s) for Darcy, n^2 / ((s-1) d_s) h^(-1/3) with
+    // n = 1/K for Strickler
     if (P.friction == 1) {
       Kb += alphab * r.alpha / P.fric_coef;
     } else {
@@ -330,15 +349,21 @@ __device__ __forceinline__ void project_shields_bar(const DevParams& P, const Pr
       Hb -= alphab * r.alpha * r.tau * (1.0 / 3.0);
     }
   }
-  Hnb += unb * r.tau;
-  taub += unb * r.Hn;
-  Htb += utb * r.tau;
-  taub += utb * r.Ht;
-  Hb -= taub * r.tau * r.tau;
+}
+
+// The whole backward sweep of one side's projection: cotangents of its
+// cell's fields -> of (H, Hn, Ht, Z) in ub[0..3] and of the parameters.
+template <bool GRASS>
+__device__ __forceinline__ void project_bar(const DevParams& P, const ProjRec& r, double A, double m,
+                                            const CellBar& cb, double ub[4], double& Ab, double& mb, double& Kb) {
+  double qb[2] = {0.0, 0.0};
+  proj_fold_bar(P, r, cb, ub, qb);
+  double unb = 0.0, utb = 0.0, Hb = 0.0, Hnb = 0.0, Htb = 0.0;
+  closure_bar<GRASS>(P, r, A, m, qb[0], qb[1], unb, utb, Hb, Ab, mb, Kb);
+  vel_fold_bar(r, unb, utb, 0.0, Hb, Hnb, Htb);
   ub[0] += Hb;
   ub[1] += Hnb;
   ub[2] += Htb;
-  ub[3] += cb.Z;
 }
 
 // Cotangents of the Newton constants used by the evaluation and the fan.
@@ -414,7 +439,11 @@ __device__ __forceinline__ void newton_eval_bar(const NewtonConst<double>& c, co
 // the cotangents Amb (of A-) and Apb (of A+), added to ub[0..7] (left then
 // right state, frame order), Ab, mb (A_g, m_g), from the projected cells L, R
 // and their records rL, rR (project_grass_rec / project_shields_rec, or the
-// same values computed once per cell).  The value pass solves for the root
+// same values computed once per cell).  With qb given, the transport law's
+// part of both projections' backward sweeps is left out: qb[0..3] receives
+// the cotangents of (Omega, dQ) of the left then the right cell (closure_bar
+// and vel_fold_bar take them on), and Ab, mb, Kb are not touched.  The value
+// pass solves for the root
 // as the step does (false if it fails), or, given the root p_root > 0 and the
 // doublings of a (retries_in) that the forward solve of this interface at
 // this state kept, evaluates the states and F' there once instead of
@@ -425,9 +454,9 @@ __device__ __forceinline__ bool interface_vjp_cells(const DevParams& P, const Ce
                                                     const Cell<double>& R, const ProjRec& rL, const ProjRec& rR,
                                                     double A, double m, const double Amb[4], const double Apb[4],
                                                     double ub[8], double& Ab, double& mb, double& Kb,
-                                                    double p_root = 0.0, int retries_in = 0) {
+                                                    double p_root = 0.0, int retries_in = 0,
+                                                    double* qb = nullptr) {
   // ---- value pass
-  constexpr bool grass = GRASS;
   const double g = P.g;
   // celerities (as celerities(), keeping the branches)
   const bool a0L = L.ca >= R.ca, b0L = L.cb >= R.cb;
@@ -627,12 +656,13 @@ __device__ __forceinline__ bool interface_vjp_cells(const DevParams& P, const Ce
   if (b0L) Lb.cb += b0b;
   else Rb.cb += b0b;
   // projections
-  if constexpr (grass) {
-    project_grass_bar(P, rL, A, m, Lb, ub, Ab, mb);
-    project_grass_bar(P, rR, A, m, Rb, ub + 4, Ab, mb);
+  if (qb) {
+    // the laws' part of the projections' backward sweeps left to the caller
+    proj_fold_bar(P, rL, Lb, ub, qb);
+    proj_fold_bar(P, rR, Rb, ub + 4, qb + 2);
   } else {
-    project_shields_bar(P, rL, Lb, ub, Kb);
-    project_shields_bar(P, rR, Rb, ub + 4, Kb);
+    project_bar<GRASS>(P, rL, A, m, Lb, ub, Ab, mb, Kb);
+    project_bar<GRASS>(P, rR, A, m, Rb, ub + 4, Ab, mb, Kb);
   }
   return true;
 }
