@@ -389,16 +389,17 @@ def run_adjoint(args, sve, W, torch):
         s.record_forward(n, every)
         fin = s.get_state()
         t1 = time.perf_counter()
+        kept = s.adjoint_kept_steps()
         grads, gp = s.adjoint(lam_z=2.0 * (fin["z"] - z_target))
         torch.cuda.synchronize()
         t2 = time.perf_counter()
-        return grads, gp, t0, t1, t2, s.checkpoint_every(), fin
+        return grads, gp, t0, t1, t2, (s.checkpoint_every(), kept), fin
 
     # automatic checkpointing (every step kept when it fits in device memory,
     # else checkpoints every ceil(sqrt(N)) steps with the segments
     # recomputed); the latter also timed on its own when the first kept all
     sq = int(math.ceil(math.sqrt(n)))
-    grads, gp, t0, t1, t2, every, fin = gradient(0)
+    grads, gp, t0, t1, t2, (every, kept), fin = gradient(0)
     if every == n:
         _, _, c0, _, c2, _, _ = gradient(sq)
     else:
@@ -417,7 +418,10 @@ def run_adjoint(args, sve, W, torch):
     return {"workload": f"adjoint config {p['nx']}x{p['ny']} periodic, dune physics in 2D, Grass A_g=1e-3 m_g=3, "
                         f"Strickler K=40; misfit to a (1.1 A_g, m_g=3.1, K=36, +5 m) run",
             "steps": n, "checkpoint_every": every,
-            "storage": "every step's state kept in device memory" if every == n else "checkpoints, segments recomputed",
+            "storage": "every step's state kept in device memory" if every == n else
+            f"checkpoints every {every} steps; the last {kept} steps' forward data kept in device memory "
+            "(half of the free memory), the earlier segments recomputed",
+            "kept_steps": kept,
             "checkpointed_value": cells * n / (c2 - c0), "checkpointed_every": sq,
             "value": grad_rate, "unit": "cell-updates/s (forward record + reverse sweep)",
             "plain_forward_value": plain, "vs_plain": grad_rate / plain,

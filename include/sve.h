@@ -344,10 +344,14 @@ void sve_batch_destroy(sve_batch* b);
  * sve_record_forward advances the handle's current state by nsteps CFL
  * steps (as sve_step) and records the time steps and a checkpoint of the
  * conserved state every checkpoint_every steps.  With checkpoint_every <= 0
- * the choice is automatic: when every step's padded state and its convected
- * (pre-friction) state fit in half of the free device memory (2 x 32 bytes
- * a cell a step in 2D), all of them are kept and the adjoint recomputes
- * nothing; otherwise a checkpoint every ceil(sqrt(nsteps)) steps.  The
+ * the choice is automatic, within a memory budget (sve_set_adjoint_budget;
+ * by default half of the device memory free when the recording starts):
+ * when every step's forward data -- its padded state, convected
+ * (pre-friction) state and Newton roots, 2 x 32 bytes a cell and 9 bytes an
+ * interface a step in 2D -- fit, all of them are kept and the adjoint
+ * recomputes nothing; otherwise a checkpoint every ceil(sqrt(nsteps)) steps,
+ * and the last segments' forward data are kept as far as the rest of the
+ * budget allows (the adjoint recomputes only the earlier segments).  The
  * handle then holds U^N.
  *
  * sve_adjoint propagates a cotangent of the final state back to the
@@ -365,9 +369,18 @@ void sve_batch_destroy(sve_batch* b);
  *
  * sve_get_checkpoint_every returns the recording's checkpoint interval
  * (nsteps when every step was kept), SVE_ERR_STATE if nothing was recorded,
- * SVE_ERR_ARG for a NULL handle. */
+ * SVE_ERR_ARG for a NULL handle.
+ *
+ * sve_set_adjoint_budget sets the bytes of forward data that the handle's
+ * next automatic recordings may keep in device memory (bytes >= 0; -1: half
+ * of the free device memory, the default); SVE_ERR_ARG for a NULL handle or
+ * bytes < -1.  sve_get_adjoint_kept_steps returns how many of the recorded
+ * steps' forward data the recording kept (nsteps when all, 0 with
+ * checkpoints only), SVE_ERR_STATE if nothing was recorded. */
 int sve_record_forward(sve_handle* h, int nsteps, int checkpoint_every);
 int sve_get_checkpoint_every(sve_handle* h);
+int sve_set_adjoint_budget(sve_handle* h, long long bytes);
+int sve_get_adjoint_kept_steps(sve_handle* h);
 int sve_adjoint(sve_handle* h, const void* lam_h, const void* lam_hu, const void* lam_hv, const void* lam_z,
                 int where, void* g_h0, void* g_hu0, void* g_hv0, void* g_z0, double* g_params);
 

@@ -50,7 +50,16 @@ using sve::NewtonEval;
 struct sve_adjoint_rec {
   int nsteps = 0;
   int every = 0;
+  int ncp = 0;                      // segments of `every` steps (the last one shorter)
   bool stored = false;              // every step's states kept by the recording (no recompute)
+  // segments kept_from .. ncp - 1 (checkpoint mode): their steps' padded and
+  // convected states, roots and doublings kept by the recording, so that the
+  // reverse sweep recomputes only the earlier segments
+  int kept_from = 0;
+  double* kseg = nullptr;
+  double* ksegc = nullptr;
+  double* kroots = nullptr;
+  unsigned char* krtry = nullptr;
   std::vector<double> dts;          // dt of each recorded step
   std::vector<double*> checkpoints;  // padded (h, hu, hv, z) at steps 0, C, 2C, ...
   double* seg = nullptr;            // padded states of one segment (C of them)
@@ -150,19 +159,29 @@ __global__ void __launch_bounds__(kAdjThreads) adj_friction_kernel(DevParams P, 
     const double lh = lam[k], l1 = lam[ncell + k], l2 = lam[2 * ncell + k], lz = lam[3 * ncell + k];
     double mh = lh, m1 = l1, m2 = l2;
     if (P.friction != 0) {
+      // C(h) and den as the step's friction computes them; one divide for
+      // 1/den and 1/|q|
       const double h = s[0], q1 = s[1], q2 = s[2];
-      const double qn = sqrt(q1 * q1 + q2 * q2);
+      const double qn = sqrt(fma(q1, q1, q2 * q2));
       const double tau = 1.0 / h;
-      double C = P.fric_c * tau * tau;
-      if (P.friction == 2) C = C / cbrt(h);
+      double C = P.fric_c * (tau * tau);
+      if (P.friction == 2) C = C * sve::rcbrt64(h);
       const double den = 1.0 + dt * C * qn;
-      const double id = 1.0 / den, id2 = id * id;
+      double id, iqn = 0.0;
+      if (qn > 0.0) {
+        const double r = 1.0 / (den * qn);
+        id = r * qn;
+        iqn = r * den;
+      } else {
+        id = 1.0 / den;
+      }
+      const double id2 = id * id;
       // dC/dh = -2 C / h (Darcy), -7/3 C / h (Strickler)
       const double dCdh = (P.friction == 1 ? -2.0 : -7.0 / 3.0) * C * tau;
       const double lq = l1 * q1 + l2 * q2;  // lambda . q
       mh = lh - lq * dt * qn * dCdh * id2;
       if (qn > 0.0) {
-        const double f = dt * C / qn * id2;
+        const double f = dt * C * iqn * id2;
         m1 = l1 * id - lq * f * q1;
         m2 = l2 * id - lq * f * q2;
       } else {
@@ -529,6 +548,10 @@ int grow(E** p, size_t* cap, size_t n) {
 void free_rec(sve_adjoint_rec* r) {
   if (!r) return;
   for (double* c : r->checkpoints) cudaFree(c);
+  if (r->kseg) cudaFree(r->kseg);
+  if (r->ksegc) cudaFree(r->ksegc);
+  if (r->kroots) cudaFree(r->kroots);
+  if (r->krtry) cudaFree(r->krtry);
   if (r->seg) cudaFree(r->seg);
   if (r->segc) cudaFree(r->segc);
   if (r->roots) cudaFree(r->roots);
@@ -601,20 +624,24 @@ int sve_record_forward(sve_handle* h, int nsteps, int checkpoint_every) {
   ADJ_TRY(cudaMemcpy(&t0, &h->sc->t, sizeof(double), cudaMemcpyDeviceToHost));
   r->t0 = t0;
   r->dts.resize(nsteps);
-  // Automatic checkpointing: when every step's padded state and convected
-  // state fit in half of the free device memory, the recording keeps them
+  // Automatic checkpointing, within the memory budget (sve_set_adjoint_budget;
+  // by default half of the free device memory): when every step's padded
+  // state, convected state and Newton roots fit, the recording keeps them
   // all and the adjoint recomputes nothing; otherwise checkpoints every
-  // ceil(sqrt(N)) steps, each segment recomputed once before its reverse sweep.
+  // ceil(sqrt(N)) steps, each segment recomputed once before its reverse
+  // sweep, except the last segments whose data the rest of the budget holds.
+  const double nfd = (double)(h->P.nfx + h->P.nfy);
+  const double per_step = (double)sizeof(double) * ((double)n + 4.0 * (double)ncell + nfd) + nfd;
+  double budget = 0.0;
   if (checkpoint_every <= 0) {
     size_t free_b = 0, total_b = 0;
     ADJ_TRY(cudaMemGetInfo(&free_b, &total_b));
-    const double nf = (double)(h->P.nfx + h->P.nfy);
-    const double need =
-        ((double)sizeof(double) * ((double)n + 4.0 * (double)ncell + nf) + nf) * (double)nsteps;
-    r->stored = need <= 0.5 * (double)free_b;
+    budget = h->adj_budget >= 0 ? (double)h->adj_budget : 0.5 * (double)free_b;
+    r->stored = per_step * (double)nsteps <= budget;
   }
   if (r->stored) {
     r->every = nsteps;
+    r->ncp = 1;
     double* c = nullptr;
     int rc = cudaMalloc(&c, sizeof(double) * n) == cudaSuccess ? SVE_OK : SVE_ERR_OOM;
     if (!rc) r->checkpoints.push_back(c);
@@ -643,15 +670,69 @@ int sve_record_forward(sve_handle* h, int nsteps, int checkpoint_every) {
   r->every = checkpoint_every > 0 ? checkpoint_every : (int)ceil(sqrt((double)nsteps));
   if (r->every > nsteps) r->every = nsteps;
   const int ncp = (nsteps + r->every - 1) / r->every;
+  r->ncp = ncp;
+  r->kept_from = ncp;
+  auto seg_len = [&](int k) { return (k + 1) * r->every <= nsteps ? r->every : nsteps - k * r->every; };
+  if (checkpoint_every <= 0) {
+    // what the budget holds beyond the checkpoints and one recomputed
+    // segment of the reverse sweep, from the last segment backwards
+    double rest = budget - per_step * (double)r->every - (double)sizeof(double) * (double)n * (double)ncp;
+    int kept = 0;
+    for (int k = ncp - 1; k >= 1; --k) {
+      if (per_step * (double)(kept + seg_len(k)) > rest) break;
+      kept += seg_len(k);
+      r->kept_from = k;
+    }
+    if (kept > 0) {
+      const size_t nf = (size_t)(h->P.nfx + h->P.nfy);
+      size_t c0 = 0, c1 = 0, c2 = 0, c3 = 0;
+      int rc = grow(&r->kseg, &c0, n * (size_t)kept);
+      if (!rc) rc = grow(&r->ksegc, &c1, 4 * (size_t)ncell * (size_t)kept);
+      if (!rc) rc = grow(&r->kroots, &c2, nf * (size_t)kept);
+      if (!rc) rc = grow(&r->krtry, &c3, nf * (size_t)kept);
+      if (rc) {  // not there after all: checkpoints only
+        cudaGetLastError();
+        cudaFree(r->kseg); cudaFree(r->ksegc); cudaFree(r->kroots); cudaFree(r->krtry);
+        r->kseg = r->ksegc = r->kroots = nullptr;
+        r->krtry = nullptr;
+        r->kept_from = ncp;
+      }
+    }
+  }
+  const size_t nf = (size_t)(h->P.nfx + h->P.nfy);
+  const int n0k = r->kept_from * r->every;
   for (int k = 0; k < ncp; ++k) {
-    double* c = nullptr;
-    if (cudaMalloc(&c, sizeof(double) * n) != cudaSuccess) { sve_internal_adjoint_free(h); return SVE_ERR_OOM; }
-    r->checkpoints.push_back(c);
-    int rc = save_state(h, c);
-    const int len = (k + 1) * r->every <= nsteps ? r->every : nsteps - k * r->every;
-    rc = rc ? rc : sve_step(h, len, nullptr);
+    const int len = seg_len(k);
+    if (k < r->kept_from) {
+      double* c = nullptr;
+      if (cudaMalloc(&c, sizeof(double) * n) != cudaSuccess) { sve_internal_adjoint_free(h); return SVE_ERR_OOM; }
+      r->checkpoints.push_back(c);
+      int rc = save_state(h, c);
+      rc = rc ? rc : sve_step(h, len, nullptr);
+      if (rc) { sve_internal_adjoint_free(h); return rc; }
+      if (sve_get_dts(h, r->dts.data() + (size_t)k * r->every, len) != len) { sve_internal_adjoint_free(h); return SVE_ERR_CUDA; }
+      continue;
+    }
+    // a kept segment: as the stored recording, step by step
+    int rc = SVE_OK;
+    if (k == r->kept_from) {
+      rc = sve_internal_reserve_dtlog(h, nsteps - n0k);
+      if (!rc && cudaMemsetAsync(&h->sc->call_step, 0, sizeof(int), h->stream) != cudaSuccess) rc = SVE_ERR_CUDA;
+    }
+    for (int s = 0; s < len && !rc; ++s) {
+      const size_t g = (size_t)(k * r->every + s - n0k);
+      rc = save_state(h, r->kseg + g * n);
+      if (!rc) rc = forward_step(h, 0.0, r->ksegc + g * 4 * (size_t)ncell, true, r->kroots + g * nf, r->krtry + g * nf);
+    }
     if (rc) { sve_internal_adjoint_free(h); return rc; }
-    if (sve_get_dts(h, r->dts.data() + (size_t)k * r->every, len) != len) { sve_internal_adjoint_free(h); return SVE_ERR_CUDA; }
+  }
+  if (r->kept_from < ncp) {
+    int rc = status_of(h);
+    if (!rc && cudaMemcpy(r->dts.data() + n0k, h->dtlog, sizeof(double) * (size_t)(nsteps - n0k),
+                          cudaMemcpyDeviceToHost) != cudaSuccess)
+      rc = SVE_ERR_CUDA;
+    if (rc) { sve_internal_adjoint_free(h); return rc; }
+    h->last_steps = nsteps - n0k;
   }
   return SVE_OK;
 }
@@ -660,6 +741,20 @@ int sve_get_checkpoint_every(sve_handle* h) {
   if (!h) return SVE_ERR_ARG;
   if (!h->adj) return SVE_ERR_STATE;
   return h->adj->every;
+}
+
+int sve_set_adjoint_budget(sve_handle* h, long long bytes) {
+  if (!h || bytes < -1) return SVE_ERR_ARG;
+  h->adj_budget = bytes;
+  return SVE_OK;
+}
+
+int sve_get_adjoint_kept_steps(sve_handle* h) {
+  if (!h) return SVE_ERR_ARG;
+  if (!h->adj) return SVE_ERR_STATE;
+  const sve_adjoint_rec* r = h->adj;
+  if (r->stored) return r->nsteps;
+  return r->kept_from >= r->ncp ? 0 : r->nsteps - r->kept_from * r->every;
 }
 
 int sve_adjoint(sve_handle* h, const void* lam_h, const void* lam_hu, const void* lam_hv, const void* lam_z,
@@ -707,13 +802,24 @@ int sve_adjoint(sve_handle* h, const void* lam_h, const void* lam_hu, const void
   }
   DevState<double> S = state_of<double>(h);
   const unsigned nbc = (unsigned)sve::cell_blocks(P, sve::kThreads);
-  const int ncp = (int)r->checkpoints.size();
+  const int ncp = r->ncp;
   for (int k = ncp - 1; k >= 0; --k) {
     const int n0 = k * r->every;
     const int len = (k + 1) * r->every <= r->nsteps ? r->every : r->nsteps - n0;
-    // recompute the segment's states U^{n0} .. U^{n0 + len - 1} (kept by
-    // the recording when it stored every step)
-    if (!r->stored) {
+    // the segment's states U^{n0} .. U^{n0 + len - 1}: kept by the recording
+    // (every step, or this segment), else recomputed from its checkpoint
+    const double* seg = r->seg;
+    const double* segc = r->segc;
+    const double* kr = r->roots;
+    const unsigned char* kt = r->rtry;
+    if (!r->stored && k >= r->kept_from) {
+      const size_t g0 = (size_t)(n0 - r->kept_from * r->every);
+      seg = r->kseg + g0 * nst;
+      segc = r->ksegc + g0 * 4 * (size_t)ncell;
+      kr = r->kroots + g0 * nf;
+      kt = r->krtry + g0 * nf;
+    }
+    if (!r->stored && k < r->kept_from) {
       rc = load_state(h, r->checkpoints[k]);
       if (rc) return rc;
       sve::init_kernel<double><<<nbc, sve::kThreads, 0, h->stream>>>(P, S, h->sc, h->mpart);
@@ -729,12 +835,12 @@ int sve_adjoint(sve_handle* h, const void* lam_h, const void* lam_hu, const void
     // included) and its convected state are all the adjoint kernels read
     for (int s = len - 1; s >= 0; --s) {
       const double dt = r->dts[n0 + s];
-      rc = load_state(h, r->seg + (size_t)s * nst);
+      rc = load_state(h, seg + (size_t)s * nst);
       if (rc) return rc;
-      adj_friction_kernel<<<nb_c, kAdjThreads, 0, h->stream>>>(P, r->segc + (size_t)s * 4 * (size_t)ncell, lam,
+      adj_friction_kernel<<<nb_c, kAdjThreads, 0, h->stream>>>(P, segc + (size_t)s * 4 * (size_t)ncell, lam,
                                                               r->mu, dt, r->gpart, r->gacc, r->done);
-      const double* roots = r->roots + (size_t)s * nf;
-      const unsigned char* rtry = r->rtry + (size_t)s * nf;
+      const double* roots = kr + (size_t)s * nf;
+      const unsigned char* rtry = kt + (size_t)s * nf;
       const double A = h->cfg.A_g, m = h->cfg.m_g;
       if (P.bedload == 0) {
         adj_cells_kernel<true><<<nb_pad, kAdjThreads, 0, h->stream>>>(P, S, A, m, r->cells, h->next);

@@ -55,6 +55,7 @@ struct sve_handle {
   double prof_ms[2] = {0.0, 0.0};
   long long prof_launches[2] = {0, 0};
   sve_adjoint_rec* adj = nullptr;
+  long long adj_budget = -1;  // bytes of forward data a recording may keep (-1: half the free device memory)
   void* halo = nullptr;    // staging of one side's ghost ring for the block calls (sve_block.cu)
 };
 

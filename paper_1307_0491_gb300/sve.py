@@ -40,7 +40,8 @@ EXPORTS = ("sve_config_default", "sve_create", "sve_set_stream", "sve_set_state"
            "sve_record_forward", "sve_adjoint", "sve_set_block_size", "sve_get_block_size", "sve_advance",
            "sve_get_checkpoint_every", "sve_set_persistent", "sve_get_persistent", "sve_check_sync_timeout",
            "sve_get_safeguards", "sve_block_get_edge", "sve_block_set_ghosts", "sve_block_speeds",
-           "sve_block_advance", "sve_batch_autotune_trials", "sve_batch_set_rows", "sve_batch_get_rows")
+           "sve_block_advance", "sve_batch_autotune_trials", "sve_batch_set_rows", "sve_batch_get_rows",
+           "sve_set_adjoint_budget", "sve_get_adjoint_kept_steps")
 
 
 class sve_config(ctypes.Structure):
@@ -117,6 +118,8 @@ def load() -> ctypes.CDLL:
         "sve_batch_destroy": ([vp], None),
         "sve_record_forward": ([vp, ip, ip], ip),
         "sve_get_checkpoint_every": ([vp], ip),
+        "sve_set_adjoint_budget": ([vp, ctypes.c_longlong], ip),
+        "sve_get_adjoint_kept_steps": ([vp], ip),
         "sve_set_persistent": ([vp, ip], ip),
         "sve_get_persistent": ([vp], ip),
         "sve_check_sync_timeout": ([vp, ctypes.c_longlong], ip),
@@ -548,6 +551,17 @@ class Solver:
         n = load().sve_get_checkpoint_every(self.h)
         _check(min(n, 0), "sve_get_checkpoint_every")
         return n
+
+    def adjoint_kept_steps(self) -> int:
+        """How many recorded steps' forward data the recording kept."""
+        n = load().sve_get_adjoint_kept_steps(self.h)
+        _check(min(n, 0), "sve_get_adjoint_kept_steps")
+        return n
+
+    def set_adjoint_budget(self, nbytes: int) -> None:
+        """Bytes of forward data the next automatic recordings may keep (-1:
+        half of the free device memory)."""
+        _check(load().sve_set_adjoint_budget(self.h, int(nbytes)), "sve_set_adjoint_budget")
 
     def record_forward(self, nsteps: int, checkpoint_every: int = 0) -> None:
         _check(sve_record_forward(self.h, nsteps, checkpoint_every), "sve_record_forward")

@@ -208,6 +208,44 @@ def test_stored_and_checkpointed_recordings_agree():
         assert list(out[every][3]) == list(out[0][3])
 
 
+def test_partly_kept_recording_agrees():
+    """An automatic recording whose memory budget holds the last two
+    checkpoint segments' forward data (23 steps: segments of 5, 5, 5, 5, 3
+    steps, the last 8 kept) recomputes only the first three in the reverse
+    sweep; with a zero budget it keeps nothing.  Final states, gradients and
+    the state stepped on from U^0 afterwards equal those of the recording
+    that keeps every step, bit for bit."""
+    w, target = case()
+    p = w["params"]
+    nx, ny = p["nx"], p["ny"]
+    n, every = 23, 5
+    npad = (nx + 2) * (ny + 2)
+    nf = (nx + 1) * ny + nx * (ny + 1)
+    per_step = 8 * (4 * npad + 4 * nx * ny + nf) + nf
+    ncp = -(-n // every)
+    out = {}
+    for name, budget in (("all", -1), ("two", per_step * (every + 8) + 8 * 4 * npad * ncp + 64), ("none", 0)):
+        s = sve.Solver(p, "fp64")
+        s.set_adjoint_budget(budget)
+        s.set_state(w["h"], w["hu"], w["hv"], w["z"])
+        s.record_forward(n, 0)
+        kept, ce = s.adjoint_kept_steps(), s.checkpoint_every()
+        fin = s.get_state()
+        grads, gp = s.adjoint(lam_z=2.0 * (fin["z"] - target))
+        s.step(4)
+        after = s.get_state()
+        s.close()
+        out[name] = (kept, ce, fin, grads, gp, after)
+    assert out["all"][:2] == (n, n)
+    assert out["two"][:2] == (8, every)
+    assert out["none"][:2] == (0, every)
+    for name in ("two", "none"):
+        for k in ("h", "hu", "hv", "z"):
+            for i in (2, 3, 5):
+                assert np.array_equal(out[name][i][k], out["all"][i][k]), (name, i, k)
+        assert list(out[name][4]) == list(out["all"][4])
+
+
 def shields_case(law, friction, bc):
     """A Shields-parameter law on a supercritical channel with a rippled bed,
     a small random transverse flow and a depth perturbed by 0.1 mm (tau*
