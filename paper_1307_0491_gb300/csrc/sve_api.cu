@@ -164,7 +164,59 @@ void launch_fused_step(sve_handle* h, cudaStream_t st, int fixed, cudaEvent_t* e
   if (ev) cudaEventRecord(ev[1], st);
   sve::Mirror<float> out{};
   if (mirror) out = {(float*)mirror[0], (float*)mirror[1], (float*)mirror[2], (float*)mirror[3]};
-  sve::apply_kernel<float><<<dim3(h->agx, h->agy), sve::kAThreads, 0, st>>>(h->P, B, D, h->sc, h->mpart, out);
+  sve::apply_kernel<float><<<dim3(h->agx, h->agy), sve::kAThreads, 0, st>>>(h->P, B, B, D, h->sc, h->mpart, out);
+  if (ev) cudaEventRecord(ev[2], st);
+}
+
+// The carried update within a call of n steps (FP32 state in 2D): step 0's
+// solve pass on U^0 in the handle's state buffer; step k >= 1's solve pass
+// applies step k - 1's update as it reads U^{k-1} from buffer (k - 1) % 2 and
+// the net fluctuations from half (k - 1) % 2 of the fluctuation planes,
+// storing U^k into the other buffer and its own net fluctuations into the
+// other half; after step n - 1 the apply pass takes U^{n-1} and the last
+// update into the handle's state buffer (ghosts, checks, mass sums).  Every
+// state and time step equals the one-step-at-a-time sequence bit for bit.
+sve::StateBuf<float> fused_buf(const sve_handle* h, int p) {
+  void* const* f = p ? h->alt : h->fields;
+  return {(float*)f[0], (float*)f[1], (float*)f[2], (float*)f[3]};
+}
+sve::NetFluct<float> fused_dF(const sve_handle* h, int p) {
+  const size_t ncell = (size_t)h->P.nx * (size_t)h->P.ny;
+  float* b = (float*)h->fx + (size_t)p * 4 * ncell;  // 8 (nx + 1) ny >= 8 nx ny floats
+  return {b, b + ncell, b + 2 * ncell, b + 3 * ncell};
+}
+
+// The solve pass of step k of a carried call.
+void launch_carried_march(sve_handle* h, cudaStream_t st, int fixed, int k, cudaEvent_t* ev) {
+  const sve::MarchShape& M = h->march;
+  if (ev) cudaEventRecord(ev[0], st);
+  if (k == 0) {
+    sve::march_kernel<float><<<M.blocks, sve::kMThreads, 0, st>>>(h->P, fused_buf(h, 0), fused_dF(h, 0), h->sc,
+                                                                  h->fixed, h->dtlog, fixed, M.strips, M.rows,
+                                                                  M.tasks);
+  } else {
+    const int q = (k - 1) & 1;
+    sve::march_kernel<float><<<M.blocks, sve::kMThreads, 0, st>>>(
+        h->P, fused_buf(h, q), fused_dF(h, 1 - q), h->sc, h->fixed, h->dtlog, fixed, M.strips, M.rows, M.tasks, 1,
+        fused_buf(h, 1 - q), fused_dF(h, q));
+  }
+  if (ev) {
+    cudaEventRecord(ev[1], st);
+    cudaEventRecord(ev[2], st);
+  }
+}
+
+// The apply pass after the last solve pass (step n - 1) of a carried call.
+void launch_carried_apply(sve_handle* h, cudaStream_t st, int n, cudaEvent_t* ev, const void* const* mirror) {
+  const int q = (n - 1) & 1;
+  sve::Mirror<float> out{};
+  if (mirror) out = {(float*)mirror[0], (float*)mirror[1], (float*)mirror[2], (float*)mirror[3]};
+  if (ev) {
+    cudaEventRecord(ev[0], st);
+    cudaEventRecord(ev[1], st);
+  }
+  sve::apply_kernel<float><<<dim3(h->agx, h->agy), sve::kAThreads, 0, st>>>(
+      h->P, fused_buf(h, q), fused_buf(h, 0), fused_dF(h, q), h->sc, h->mpart, out);
   if (ev) cudaEventRecord(ev[2], st);
 }
 
@@ -177,13 +229,16 @@ void launch_step_any(sve_handle* h, cudaStream_t st, int fixed, cudaEvent_t* ev 
   else launch_step<float>(h, st, fixed, ev, mirror);
 }
 
-// Three events for one profiled step (grown on demand).
-cudaEvent_t* next_events(sve_handle* h) {
+// Three events for one profiled step or pass (grown on demand); kind: which
+// intervals count (bit 0: solve pass, bit 1: update pass).
+cudaEvent_t* next_events(sve_handle* h, unsigned char kind = 3) {
   while (h->events.size() < h->events_used + 3) {
     cudaEvent_t e;
     if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
     h->events.push_back(e);
   }
+  if (h->ev_kind.size() < h->events.size() / 3) h->ev_kind.resize(h->events.size() / 3);
+  h->ev_kind[h->events_used / 3] = kind;
   cudaEvent_t* ev = &h->events[h->events_used];
   h->events_used += 3;
   return ev;
@@ -196,10 +251,15 @@ int drain_events(sve_handle* h) {
     if (cudaEventSynchronize(h->events[k + 2]) != cudaSuccess) return SVE_ERR_CUDA;
     if (cudaEventElapsedTime(&a, h->events[k], h->events[k + 1]) != cudaSuccess) return SVE_ERR_CUDA;
     if (cudaEventElapsedTime(&b, h->events[k + 1], h->events[k + 2]) != cudaSuccess) return SVE_ERR_CUDA;
-    h->prof_ms[0] += a;
-    h->prof_ms[1] += b;
-    h->prof_launches[0] += 1;
-    h->prof_launches[1] += 1;
+    const unsigned char kind = h->ev_kind[k / 3];
+    if (kind & 1) {
+      h->prof_ms[0] += a;
+      h->prof_launches[0] += 1;
+    }
+    if (kind & 2) {
+      h->prof_ms[1] += b;
+      h->prof_launches[1] += 1;
+    }
   }
   h->events_used = 0;
   return SVE_OK;
@@ -216,12 +276,18 @@ int ensure_capacity(double** buf, int* cap, int n) {
   return SVE_OK;
 }
 
+// kGraphSteps steps: the two-kernel or fused step, or, for the carried
+// update, kGraphSteps carried solve passes from buffer 0 (steps k = 1, 3,
+// ... of a call: kGraphSteps is even, so every such graph starts there).
 int get_graph(sve_handle* h, int fixed, cudaGraphExec_t* out) {
   cudaGraphExec_t& G = h->graph[fixed ? 1 : 0];
   if (!G) {
     cudaGraph_t g = nullptr;
     SVE_TRY(cudaStreamBeginCapture(h->capture, cudaStreamCaptureModeThreadLocal));
-    for (int s = 0; s < kGraphSteps; ++s) launch_step_any(h, h->capture, fixed);
+    for (int s = 0; s < kGraphSteps; ++s) {
+      if (h->carry) launch_carried_march(h, h->capture, fixed, s + 1, nullptr);
+      else launch_step_any(h, h->capture, fixed);
+    }
     cudaError_t e = cudaStreamEndCapture(h->capture, &g);
     if (e != cudaSuccess) return SVE_ERR_CUDA;
     e = cudaGraphInstantiate(&G, g, 0);
@@ -302,6 +368,32 @@ int enqueue_steps(sve_handle* h, int nsteps, int fixed, const void* const* mirro
     }
     SVE_TRY(cudaGetLastError());
     h->last_launches = launches;
+    h->last_steps = nsteps;
+    return SVE_OK;
+  }
+  if (h->carry) {
+    // the carried update: step 0, steps 1 .. n - 1 (graphs of kGraphSteps
+    // from step 1 on), the apply pass
+    int k = 1;
+    cudaEvent_t* ev = h->profiling ? next_events(h, 1) : nullptr;
+    if (h->profiling && !ev) return SVE_ERR_CUDA;
+    launch_carried_march(h, h->stream, fixed, 0, ev);
+    if (nsteps - 1 >= kGraphSteps && !h->profiling) {
+      cudaGraphExec_t ex;
+      rc = get_graph(h, fixed, &ex);
+      if (rc) return rc;
+      for (; k + kGraphSteps <= nsteps; k += kGraphSteps) SVE_TRY(cudaGraphLaunch(ex, h->stream));
+    }
+    for (; k < nsteps; ++k) {
+      ev = h->profiling ? next_events(h, 1) : nullptr;
+      if (h->profiling && !ev) return SVE_ERR_CUDA;
+      launch_carried_march(h, h->stream, fixed, k, ev);
+    }
+    ev = h->profiling ? next_events(h, 2) : nullptr;
+    if (h->profiling && !ev) return SVE_ERR_CUDA;
+    launch_carried_apply(h, h->stream, nsteps, ev, mirror);
+    SVE_TRY(cudaGetLastError());
+    h->last_launches = (long long)nsteps + 1;
     h->last_steps = nsteps;
     return SVE_OK;
   }
@@ -514,6 +606,12 @@ int sve_create(const sve_config* cfg, sve_handle** out) {
   ok = ok && cudaMalloc(&h->fx, 8 * h->elem * (size_t)h->P.nfx) == cudaSuccess;
   ok = ok && cudaMalloc(&h->fy, 8 * h->elem * (size_t)(h->P.nfy > 0 ? h->P.nfy : 1)) == cudaSuccess;
   h->fused = cfg->precision == SVE_FP32 && cfg->dim == 2;
+  // the carried update needs every ghost from a boundary rule (a block's
+  // external ghosts are set by the caller between single steps)
+  h->carry = h->fused;
+  for (int k = 0; k < 4; ++k) h->carry = h->carry && cfg->bc[k] != SVE_BC_EXTERNAL;
+  if (h->carry)
+    for (int k = 0; k < 4 && ok; ++k) ok = cudaMalloc(&h->alt[k], h->elem * (size_t)h->next) == cudaSuccess;
   if (h->fused) {
     h->march = sve::march_shape(h->P, h->nsm);
     h->agx = (h->P.nx + sve::kAThreads - 1) / sve::kAThreads;
@@ -735,6 +833,8 @@ void sve_destroy(sve_handle* h) {
   cudaStreamSynchronize(h->stream);
   for (auto e : h->events) cudaEventDestroy(e);
   for (auto& f : h->fields)
+    if (f) cudaFree(f);
+  for (auto& f : h->alt)
     if (f) cudaFree(f);
   if (h->fx) cudaFree(h->fx);
   if (h->fy) cudaFree(h->fy);

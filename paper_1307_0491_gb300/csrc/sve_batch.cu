@@ -226,7 +226,7 @@ __global__ void __launch_bounds__(NT) batch_apply_kernel(const BatchRun<T>* runs
     const long long ncell = (long long)P.nx * P.ny;
     const sve::NetFluct<T> D = {R.S.fx, R.S.fx + ncell, R.S.fx + 2 * ncell, R.S.fx + 3 * ncell};
     T h1, z1;
-    const int st = sve::apply_cell(P, B, D, T(sc[t.x].dt), i, j, sve::Mirror<T>{}, h1, z1);
+    const int st = sve::apply_cell(P, B, B, D, T(sc[t.x].dt), i, j, sve::Mirror<T>{}, h1, z1);
     if (st) atomicOr(&sc[t.x].status, st);
     mh = (double)h1;
     mz = (double)z1;

@@ -102,7 +102,7 @@ void launch_update(sve_handle* h) {
       const size_t ncell = (size_t)h->P.nx * (size_t)h->P.ny;
       sve::NetFluct<T> D;
       D.h = (T*)h->fx; D.hu = D.h + ncell; D.hv = D.hu + ncell; D.z = D.hv + ncell;
-      sve::apply_kernel<T><<<dim3(h->agx, h->agy), sve::kAThreads, 0, h->stream>>>(h->P, B, D, h->sc, h->mpart,
+      sve::apply_kernel<T><<<dim3(h->agx, h->agy), sve::kAThreads, 0, h->stream>>>(h->P, B, B, D, h->sc, h->mpart,
                                                                                      sve::Mirror<T>{});
     }
     return;

@@ -14,10 +14,15 @@
 //                  from the solves and the last block turns their running
 //                  maximum into the time step, as interface_kernel does;
 //   apply_kernel   U <- U - dt dF per cell, semi-implicit friction, checks,
-//                  the ghosts, per-block mass partials; in place, bound by
-//                  its 48 B per cell of HBM traffic (a grid stride over rows
-//                  and columns with as many blocks as fit at once, so that
-//                  the per-block partials stay few).
+//                  the ghosts, per-block mass partials; in place (or from a
+//                  second state buffer), bound by its 48 B per cell of HBM
+//                  traffic (a grid stride over rows and columns with as many
+//                  blocks as fit at once, so that the per-block partials
+//                  stay few).
+// Within one call of several steps, the update of step n is instead applied
+// by the solve pass of step n + 1 as it reads the state (march_kernel's
+// carried form, sve_march.cuh), and the apply pass runs once, after the last
+// solve pass.
 #pragma once
 #include "sve_device.cuh"
 
@@ -112,37 +117,60 @@ template <> struct MassSum<float> { using type = FSum; };
 
 constexpr int kAThreads = 256;
 
-// The update of one interior cell (i, j) from its net fluctuation: U <- U -
-// dt dF, semi-implicit friction, checks, the ghosts it feeds, the optional
-// mirror; returns status bits, (mh, mz) = the new (h, z).
+// The new state of one cell from its state u and net fluctuation d: U <-
+// U - dt dF, then the semi-implicit friction (every product written as the
+// FMA it is, so that every kernel that applies an update -- the apply pass,
+// the solve pass applying the previous step's -- gives the same bits).
 template <typename T>
-__device__ __forceinline__ int apply_cell(const DevParams& P, const StateBuf<T>& B, const NetFluct<T>& D, T dt,
-                                          int i, int j, const Mirror<T>& out, T& mh, T& mz) {
-  const long long e = ext_index(P, i, j), k = (long long)j * P.nx + i;
-  T s[4] = {B.h[e] - dt * D.h[k], B.hu[e] - dt * D.hu[k], B.hv[e] - dt * D.hv[k], B.z[e] - dt * D.z[k]};
+__device__ __forceinline__ void apply_state(const DevParams& P, T dt, const T u[4], const T d[4], T s[4]) {
+#pragma unroll
+  for (int c = 0; c < 4; ++c) s[c] = tfma(-dt, d[c], u[c]);
   if (P.friction != 0) {
     const T tau = tdiv(T(1), s[0]);
     const T qn = tsqrt(tfma(s[1], s[1], s[2] * s[2]));
     T C = par<T>(P.fric_c, P.f.fric_c) * (tau * tau);
     if (P.friction == 2) C = C * rcbrt64(s[0]);
-    const T den = T(1) + dt * C * qn;
+    const T den = tfma(dt * C, qn, T(1));
     s[1] = tdiv(s[1], den);
     s[2] = tdiv(s[2], den);
   }
-  int st = 0;
-  if (!(finite_bits(s[0]) && finite_bits(s[1]) && finite_bits(s[2]) && finite_bits(s[3]))) st = ST_NAN;
-  else if (!positive(s[0])) st = ST_NEG_DEPTH;
-  B.h[e] = s[0]; B.hu[e] = s[1]; B.hv[e] = s[2]; B.z[e] = s[3];
+}
+
+// Status bits of a new state: non-finite, or a non-positive depth.
+template <typename T>
+__device__ __forceinline__ int state_check(const T s[4]) {
+  if (!(finite_bits(s[0]) && finite_bits(s[1]) && finite_bits(s[2]) && finite_bits(s[3]))) return ST_NAN;
+  return positive(s[0]) ? 0 : ST_NEG_DEPTH;
+}
+
+// The update of one interior cell (i, j) from its net fluctuation: the state
+// of src plus the update into dst (src == dst: in place), checks, the ghosts
+// it feeds (in dst), the optional mirror; returns status bits, (mh, mz) = the
+// new (h, z).
+template <typename T>
+__device__ __forceinline__ int apply_cell(const DevParams& P, const StateBuf<T>& src, const StateBuf<T>& dst,
+                                          const NetFluct<T>& D, T dt, int i, int j, const Mirror<T>& out, T& mh,
+                                          T& mz) {
+  const long long e = ext_index(P, i, j), k = (long long)j * P.nx + i;
+  const T u[4] = {src.h[e], src.hu[e], src.hv[e], src.z[e]};
+  const T d[4] = {D.h[k], D.hu[k], D.hv[k], D.z[k]};
+  T s[4];
+  apply_state(P, dt, u, d, s);
+  const int st = state_check(s);
+  dst.h[e] = s[0]; dst.hu[e] = s[1]; dst.hv[e] = s[2]; dst.z[e] = s[3];
   if (out.h) { out.h[k] = s[0]; out.hu[k] = s[1]; out.hv[k] = s[2]; out.z[k] = s[3]; }
-  write_ghost_state(P, B, i, j, s);
+  write_ghost_state(P, dst, i, j, s);
   mh = s[0];
   mz = s[3];
   return st;
 }
 
+// src: the state the update applies to; B: where the new state goes (the
+// same buffer: in place).
 template <typename T>
-__global__ void __launch_bounds__(kAThreads) apply_kernel(DevParams P, StateBuf<T> B, NetFluct<T> D,
-                                                          DevScalars* sc, double* mpart, Mirror<T> out) {
+__global__ void __launch_bounds__(kAThreads) apply_kernel(DevParams P, StateBuf<T> src, StateBuf<T> B,
+                                                          NetFluct<T> D, DevScalars* sc, double* mpart,
+                                                          Mirror<T> out) {
   __shared__ double s_m[2][kAThreads];
   __shared__ unsigned int s_warps;
   if (threadIdx.x == 0) s_warps = 0u;
@@ -154,7 +182,7 @@ __global__ void __launch_bounds__(kAThreads) apply_kernel(DevParams P, StateBuf<
   for (int j = blockIdx.y; j < P.ny; j += gridDim.y) {
     for (int i = blockIdx.x * kAThreads + threadIdx.x; i < P.nx; i += gridDim.x * kAThreads) {
       T mh, mz;
-      st |= apply_cell(P, B, D, dt, i, j, out, mh, mz);
+      st |= apply_cell(P, src, B, D, dt, i, j, out, mh, mz);
       sh_h.add(mh);
       sh_z.add(mz);
     }

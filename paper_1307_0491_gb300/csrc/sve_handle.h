@@ -36,6 +36,8 @@ struct sve_handle {
   // FP32 state in 2D: the fused stencil (solve pass of strips marching over
   // rows, apply pass)
   bool fused = false;
+  bool carry = false;          // fused, and no external sides: the carried update within a call
+  void* alt[4] = {};           // second state buffer: the carried update's U^{n+1} (odd steps of a call)
   sve::MarchShape march = {};  // launch shape of the solve pass (sve_march.cuh)
   int agx = 0, agy = 0;    // apply pass grid (grid stride over columns and rows)
   int nt = 256;   // threads per block of the two-kernel step (32 or 256)
@@ -48,9 +50,12 @@ struct sve_handle {
   int pmax = 0;            // most co-resident one-warp blocks allowed
   long long last_launches = 0;
   int last_steps = 0;
-  // kernel timing (sve_profile): 3 events per step, read back lazily
+  // kernel timing (sve_profile): 3 events per step, read back lazily; per
+  // triple, which of its two intervals count (bit 0: the solve pass, bit 1:
+  // the update pass)
   bool profiling = false;
   std::vector<cudaEvent_t> events;
+  std::vector<unsigned char> ev_kind;
   size_t events_used = 0;
   double prof_ms[2] = {0.0, 0.0};
   long long prof_launches[2] = {0, 0};

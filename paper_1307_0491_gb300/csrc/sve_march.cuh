@@ -77,16 +77,51 @@ template <> struct SpeedMax<double> {
   }
 };
 
-// Projected cell of column c, row j of the padded state (c in [-1, nx], j in
-// [-1, ny]); a unit state outside (never solved with).
+// The carried update: within a call of several steps the solve pass of step
+// n + 1 reads U^n and the net fluctuations of step n and applies the update
+// itself (apply_state, bit for bit the apply pass's), so that the state makes
+// one trip through memory per step instead of two.
 template <typename T>
-__device__ __forceinline__ void march_project(const DevParams& P, const StateBuf<T>& B, int c, int j, bool in,
-                                              SCell<T>& s) {
-  if (in) {
-    const long long e = ext_index(P, c, j);
-    project_into(P, B.h[e], B.hu[e], B.hv[e], B.z[e], s);
+struct Carry {
+  StateBuf<T> dst;  // where the owning lanes store U^{n+1} (interior cells; not the ghosts)
+  NetFluct<T> D;    // the net fluctuations of step n
+  T dt;             // the time step of step n
+};
+
+// U^{n+1} of padded cell (c, j) from U^n in B and the carried update:
+// interior cells by apply_state, ghost cells by their side's ghost rule from
+// the cell they copy (as write_ghost_state fills them: the first or last
+// interior cell, the far one across a periodic side), corners (never solved
+// with) a unit state.  No external sides.
+template <typename T>
+__device__ __forceinline__ void carried_state(const DevParams& P, const StateBuf<T>& B, const Carry<T>& K, int c,
+                                              int j, T s[4]) {
+  const bool xin = c >= 0 && c < P.nx, yin = j >= 0 && j < P.ny;
+  int side = -1, i0 = c, j0 = j;
+  if (!xin && !yin) {
+    s[0] = T(1); s[1] = T(0); s[2] = T(0); s[3] = T(0);
+    return;
+  }
+  if (!xin) {
+    const bool per = P.bc[0] == GHOST_PERIODIC;
+    side = c < 0 ? 0 : 1;
+    i0 = (c < 0) != per ? 0 : P.nx - 1;
+  } else if (!yin) {
+    const bool per = P.bc[2] == GHOST_PERIODIC;
+    side = j < 0 ? 2 : 3;
+    j0 = (j < 0) != per ? 0 : P.ny - 1;
+  }
+  const long long e = ext_index(P, i0, j0), k = (long long)j0 * P.nx + i0;
+  const T u[4] = {B.h[e], B.hu[e], B.hv[e], B.z[e]};
+  const T d[4] = {K.D.h[k], K.D.hu[k], K.D.hv[k], K.D.z[k]};
+  if (side < 0) {
+    apply_state(P, K.dt, u, d, s);
   } else {
-    project_into(P, T(1), T(0), T(0), T(0), s);
+    T a[4];
+    apply_state(P, K.dt, u, d, a);
+    // (a runtime side: the rule's component indices make this a small
+    // local-memory array; dispatching on constant sides measured 2 % slower)
+    ghost_state(P, side, a, s);
   }
 }
 
@@ -113,17 +148,22 @@ __device__ __forceinline__ Cell<T> left_cell(const SCell<T>& s) {
 // extreme speeds of the x- and y-solves.
 template <typename T>
 struct MarchTally {
-  int fail = 0, iters = 0;
+  int fail = 0, iters = 0, status = 0;
   unsigned int nraised = 0u, nretry = 0u, nhalv = 0u;
   SpeedMax<T> mx, my;
 };
 
 // One task: the strip `strip` (columns strip * 30 .. + 29 with a halo column
 // each side) over the run of rows `chunk` (rows chunk * rows ..), by the
-// calling warp (every lane must call it).
+// calling warp (every lane must call it).  carry: B holds U^n and the
+// carried update K gives the state the step solves with (the task's own
+// cells stored into K.dst and checked).  One code path for both (a runtime
+// switch and a single projection site), so that the solves of a carried
+// step are the same instructions as those of a plain one, bit for bit.
 template <typename T>
 __device__ __forceinline__ void march_task(const DevParams& P, const StateBuf<T>& B, const NetFluct<T>& D,
-                                           int strip, int chunk, int rows, MarchTally<T>& t) {
+                                           int strip, int chunk, int rows, MarchTally<T>& t, bool carry = false,
+                                           const Carry<T>& K = Carry<T>{}) {
   const int lane = threadIdx.x & 31;
   const int c = strip * kMCols - 1 + lane;          // this lane's column
   const bool col_in = c <= P.nx;                    // inside the padded grid
@@ -133,10 +173,29 @@ __device__ __forceinline__ void march_task(const DevParams& P, const StateBuf<T>
   const T idx = par<T>(P.inv_dx, (float)P.inv_dx), idy = par<T>(P.inv_dy, (float)P.inv_dy);
   SCell<T> cur, nxt;
   T apb[4] = {T(0), T(0), T(0), T(0)};  // A+ of the y-interface below (j - 1/2), y frame
-  march_project(P, B, c, j0 - 1, col_in, cur);
+  // the projected cell of this lane's column at row jj (with the carried
+  // update: the updated state, stored by the lane that owns the cell)
+  auto project_row = [&](int jj, SCell<T>& out) {
+    T a[4] = {T(1), T(0), T(0), T(0)};  // outside the padded grid: a unit state (never solved with)
+    if (col_in) {
+      if (carry) {
+        carried_state(P, B, K, c, jj, a);
+      } else {
+        const long long e = ext_index(P, c, jj);
+        a[0] = B.h[e]; a[1] = B.hu[e]; a[2] = B.hv[e]; a[3] = B.z[e];
+      }
+    }
+    project_into(P, a[0], a[1], a[2], a[3], out);
+    if (carry && interior && jj >= j0 && jj < j1) {
+      const long long e = ext_index(P, c, jj);
+      K.dst.h[e] = a[0]; K.dst.hu[e] = a[1]; K.dst.hv[e] = a[2]; K.dst.z[e] = a[3];
+      t.status |= state_check(a);
+    }
+  };
+  project_row(j0 - 1, cur);
   // j = j0 - 1 only solves the y-interface j0 - 1/2 (its A+ enters row j0)
   for (int j = j0 - 1; j < j1; ++j) {
-    march_project(P, B, c, j + 1, col_in, nxt);
+    project_row(j + 1, nxt);
     const bool row = j >= j0;  // row j is updated by this task (warp-uniform)
     // the y-interface j + 1/2 at this column
     T amu[4] = {T(0), T(0), T(0), T(0)}, apu[4] = {T(0), T(0), T(0), T(0)};
@@ -190,6 +249,7 @@ template <typename T>
 __device__ __forceinline__ bool march_fold(const MarchTally<T>& t, DevScalars* sc, unsigned long long* s_sx,
                                            unsigned long long* s_sy, unsigned int* s_cnt) {
   if (t.fail) atomicOr(&sc->status, ST_RIEMANN);
+  if (t.status) atomicOr(&sc->status, t.status);
   const unsigned long long wx = t.mx.warp_bits(), wy = t.my.warp_bits();
   const unsigned iters = __reduce_add_sync(0xffffffffu, (unsigned)t.iters);
   const unsigned nraised = __reduce_add_sync(0xffffffffu, t.nraised);
@@ -217,23 +277,35 @@ __device__ __forceinline__ bool march_fold(const MarchTally<T>& t, DevScalars* s
 // Five blocks per SM (<= 102 registers a thread, no spills): 20 warps per SM
 // measured 5 % faster than the unconstrained 123 registers (16 warps) and
 // than six blocks (<= 85 registers) on the 8192 x 4096 antidune.
+// carry: the carried form (B holds U^n; carry_dst, carry_D: where U^{n+1}
+// goes and the net fluctuations of step n, whose time the finalizer accounts
+// for before it takes step n + 1's time step).
 template <typename T>
 __global__ void __launch_bounds__(kMThreads, 5) march_kernel(DevParams P, StateBuf<T> B, NetFluct<T> D,
                                                           DevScalars* sc, const double* fixed_dts, double* dtlog,
-                                                          int fixed, int strips, int rows, long long ntasks) {
+                                                          int fixed, int strips, int rows, long long ntasks,
+                                                          int carry = 0, StateBuf<T> carry_dst = StateBuf<T>{},
+                                                          NetFluct<T> carry_D = NetFluct<T>{}) {
   __shared__ unsigned long long s_sx, s_sy;
   __shared__ unsigned int s_cnt[5];
   if (threadIdx.x == 0) { s_sx = 0ull; s_sy = 0ull; for (int k = 0; k < 5; ++k) s_cnt[k] = 0u; }
   __syncthreads();
   const long long task = (long long)blockIdx.x * kMWarps + (threadIdx.x >> 5);
   MarchTally<T> t;
-  if (task < ntasks) march_task(P, B, D, (int)(task % strips), (int)(task / strips), rows, t);
+  const Carry<T> K{carry_dst, carry_D, carry ? T(sc->dt) : T(0)};
+  if (task < ntasks) march_task(P, B, D, (int)(task % strips), (int)(task / strips), rows, t, carry != 0, K);
   if (!march_fold(t, sc, &s_sx, &s_sy, s_cnt)) return;
   __threadfence();
   if (atomicAdd(&sc->done_iface, 1u) != gridDim.x - 1) return;
   __threadfence();
   const double sx = __longlong_as_double((long long)atomicExch(&sc->smax_bits[0], 0ull));
   const double sy = __longlong_as_double((long long)atomicExch(&sc->smax_bits[1], 0ull));
+  if (carry) {
+    // the carried step is complete (its mass sums: from the final apply pass)
+    sc->t += sc->dt;
+    sc->call_step += 1;
+    sc->steps += 1;
+  }
   const int cs = sc->call_step;
   double dt;
   if (fixed == DT_FIXED) dt = fixed_dts[cs];

@@ -193,7 +193,7 @@ int run(const sve::DevParams& P, unsigned char* base, const Layout& L, const Sha
         if (SH.fused) {
           sve::march_kernel<T><<<SH.march.blocks, sve::kMThreads, 0, st>>>(P, B, D, sc, dtlog, dtlog, 0, SH.march.strips,
                                                                           SH.march.rows, SH.march.tasks);
-          sve::apply_kernel<T><<<dim3(SH.agx, SH.agy), sve::kAThreads, 0, st>>>(P, B, D, sc, mpart,
+          sve::apply_kernel<T><<<dim3(SH.agx, SH.agy), sve::kAThreads, 0, st>>>(P, B, B, D, sc, mpart,
                                                                                 sve::Mirror<T>{});
           continue;
         }
