@@ -371,9 +371,9 @@ int enqueue_steps(sve_handle* h, int nsteps, int fixed, const void* const* mirro
     h->last_steps = nsteps;
     return SVE_OK;
   }
-  if (h->carry) {
+  if (h->carry && nsteps > 1) {
     // the carried update: step 0, steps 1 .. n - 1 (graphs of kGraphSteps
-    // from step 1 on), the apply pass
+    // from step 1 on), the apply pass (one step: the plain step below)
     int k = 1;
     cudaEvent_t* ev = h->profiling ? next_events(h, 1) : nullptr;
     if (h->profiling && !ev) return SVE_ERR_CUDA;

@@ -173,9 +173,28 @@ __global__ void __launch_bounds__(NT) batch_cell_kernel(const BatchRun<T>* runs,
 // run's last block turns its speed maxima into its time step.  Four blocks
 // per SM: the run record in shared memory costs registers that five blocks
 // (<= 102) would spill.
+// The two state buffers of a run for the carried update (p = 0: its state;
+// 1: its projection planes tau, u, v, pi, which the FP32 2D form does not
+// use) and the two halves of its fluctuation planes.
+template <typename T>
+__device__ __forceinline__ sve::StateBuf<T> run_buf(const BatchRun<T>& R, int p) {
+  if (p) return {R.S.tau, R.S.u, R.S.v, R.S.pi};
+  return {R.S.h, R.S.hu, R.S.hv, R.S.z};
+}
+template <typename T>
+__device__ __forceinline__ sve::NetFluct<T> run_dF(const BatchRun<T>& R, int p) {
+  const long long ncell = (long long)R.P.nx * R.P.ny;
+  T* b = R.S.fx + (long long)p * 4 * ncell;  // 8 (nx + 1) ny >= 8 nx ny
+  return {b, b + ncell, b + 2 * ncell, b + 3 * ncell};
+}
+
+// carry < 0: a plain solve pass on the runs' states; carry = q >= 0: the
+// carried form of a call's step k >= 1 with q = (k - 1) % 2 (as the single
+// run's: U^{k-1} in buffer q, the update of step k - 1 in half q, U^k to
+// buffer 1 - q, this step's net fluctuations to half 1 - q).
 template <typename T>
 __global__ void __launch_bounds__(sve::kMThreads, 4) batch_march_kernel(const BatchRun<T>* runs, const int2* tiles,
-                                                                        DevScalars* sc) {
+                                                                        DevScalars* sc, int carry) {
   __shared__ BatchRun<T> R;
   __shared__ unsigned long long s_sx, s_sy;
   __shared__ unsigned int s_cnt[5];
@@ -186,10 +205,10 @@ __global__ void __launch_bounds__(sve::kMThreads, 4) batch_march_kernel(const Ba
   const int task = t.y * sve::kMWarps + (int)(threadIdx.x >> 5);
   sve::MarchTally<T> tl;
   if (task < R.mtasks) {
-    const sve::StateBuf<T> B = {R.S.h, R.S.hu, R.S.hv, R.S.z};
-    const long long ncell = (long long)P.nx * P.ny;
-    const sve::NetFluct<T> D = {R.S.fx, R.S.fx + ncell, R.S.fx + 2 * ncell, R.S.fx + 3 * ncell};
-    sve::march_task(P, B, D, task % R.strips, task / R.strips, R.rows, tl);
+    const int q = carry < 0 ? 0 : carry;
+    const sve::Carry<T> K{run_buf(R, 1 - q), run_dF(R, q), carry < 0 ? T(0) : T(sc[t.x].dt)};
+    sve::march_task(P, run_buf(R, q), run_dF(R, carry < 0 ? 0 : 1 - q), task % R.strips, task / R.strips, R.rows,
+                    tl, carry >= 0, K);
   }
   DevScalars& S = sc[t.x];
   if (!sve::march_fold(tl, &S, &s_sx, &s_sy, s_cnt)) return;
@@ -198,6 +217,10 @@ __global__ void __launch_bounds__(sve::kMThreads, 4) batch_march_kernel(const Ba
   __threadfence();
   const double mx = __longlong_as_double((long long)atomicExch(&S.smax_bits[0], 0ull));
   const double my = __longlong_as_double((long long)atomicExch(&S.smax_bits[1], 0ull));
+  if (carry >= 0) {  // the carried step is complete (its mass sums: from the final apply pass)
+    S.t += S.dt;
+    S.steps += 1;
+  }
   double dt = P.cfl / (mx / P.dx + my / P.dy);
   if (!(dt > 0.0) || !isfinite(dt)) { atomicOr(&S.status, sve::ST_DT); dt = 0.0; }
   S.dt = dt;
@@ -208,9 +231,11 @@ __global__ void __launch_bounds__(sve::kMThreads, 4) batch_march_kernel(const Ba
 
 // FP32 2D runs: the update from the net fluctuations (apply_cell of
 // sve_fused.cuh), one cell a thread over tiles of NT cells of one run.
+// q: the buffer and half holding the state and update the pass applies
+// (the new state goes to buffer 0).
 template <typename T, int NT>
 __global__ void __launch_bounds__(NT) batch_apply_kernel(const BatchRun<T>* runs, const int2* tiles, DevScalars* sc,
-                                                         double* mpart) {
+                                                         double* mpart, int q) {
   __shared__ BatchRun<T> R;
   __shared__ double s_m[2][NT];
   __shared__ unsigned int s_warps;
@@ -222,11 +247,9 @@ __global__ void __launch_bounds__(NT) batch_apply_kernel(const BatchRun<T>* runs
   double mh = 0.0, mz = 0.0;
   if (k < (long long)P.nx * P.ny) {
     const int j = (int)(k / P.nx), i = (int)(k - (long long)j * P.nx);
-    const sve::StateBuf<T> B = {R.S.h, R.S.hu, R.S.hv, R.S.z};
-    const long long ncell = (long long)P.nx * P.ny;
-    const sve::NetFluct<T> D = {R.S.fx, R.S.fx + ncell, R.S.fx + 2 * ncell, R.S.fx + 3 * ncell};
     T h1, z1;
-    const int st = sve::apply_cell(P, B, B, D, T(sc[t.x].dt), i, j, sve::Mirror<T>{}, h1, z1);
+    const int st =
+        sve::apply_cell(P, run_buf(R, q), run_buf(R, 0), run_dF(R, q), T(sc[t.x].dt), i, j, sve::Mirror<T>{}, h1, z1);
     if (st) atomicOr(&sc[t.x].status, st);
     mh = (double)h1;
     mz = (double)z1;
@@ -414,17 +437,26 @@ int build_tables_any(sve_batch* b, int tile, int schedule) {
   return b->precision == SVE_FP64 ? build_tables<double>(b, tile, schedule) : build_tables<float>(b, tile, schedule);
 }
 
+// The fused FP32 2D passes: the solve pass (carry as batch_march_kernel's)
+// and the apply pass from buffer q.
+void launch_batch_march(sve_batch* b, cudaStream_t st, int carry) {
+  batch_march_kernel<float><<<b->nt_if, sve::kMThreads, 0, st>>>((const BatchRun<float>*)b->d_runs, b->d_tiles_if,
+                                                                 b->d_sc, carry);
+}
+void launch_batch_apply(sve_batch* b, cudaStream_t st, int q) {
+  const BatchRun<float>* runs = (const BatchRun<float>*)b->d_runs;
+  if (b->tile == 128)
+    batch_apply_kernel<float, 128><<<b->nt_cell, 128, 0, st>>>(runs, b->d_tiles_cell, b->d_sc, b->d_mpart, q);
+  else
+    batch_apply_kernel<float, 256><<<b->nt_cell, 256, 0, st>>>(runs, b->d_tiles_cell, b->d_sc, b->d_mpart, q);
+}
+
 template <typename T>
 void launch_batch_step(sve_batch* b, cudaStream_t st) {
   const BatchRun<T>* runs = (const BatchRun<T>*)b->d_runs;
   if (b->fused) {
-    if constexpr (sizeof(T) == 4) {
-      batch_march_kernel<T><<<b->nt_if, sve::kMThreads, 0, st>>>(runs, b->d_tiles_if, b->d_sc);
-      if (b->tile == 128)
-        batch_apply_kernel<T, 128><<<b->nt_cell, 128, 0, st>>>(runs, b->d_tiles_cell, b->d_sc, b->d_mpart);
-      else
-        batch_apply_kernel<T, 256><<<b->nt_cell, 256, 0, st>>>(runs, b->d_tiles_cell, b->d_sc, b->d_mpart);
-    }
+    launch_batch_march(b, st, -1);
+    launch_batch_apply(b, st, 0);
     return;
   }
   if (b->tile == 128) {
@@ -444,12 +476,38 @@ void launch_batch_step_any(sve_batch* b, cudaStream_t st) {
 int enqueue_batch(sve_batch* b, int nsteps) {
   for (int r = 0; r < b->nruns; ++r)
     if (!b->has_state[r]) return SVE_ERR_STATE;
+  if (b->fused && nsteps > 1) {
+    // the carried update (as a single run's call): step 0, steps 1 .. n - 1
+    // (graphs of kBatchGraphSteps carried solve passes from buffer 0), the
+    // apply pass
+    launch_batch_march(b, b->stream, -1);
+    int k = 1;
+    if (nsteps - 1 >= kBatchGraphSteps) {
+      if (!b->graph) {
+        cudaGraph_t g = nullptr;
+        if (cudaStreamBeginCapture(b->capture, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return SVE_ERR_CUDA;
+        for (int s = 0; s < kBatchGraphSteps; ++s) launch_batch_march(b, b->capture, s & 1);
+        if (cudaStreamEndCapture(b->capture, &g) != cudaSuccess) return SVE_ERR_CUDA;
+        const cudaError_t e = cudaGraphInstantiate(&b->graph, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) { b->graph = nullptr; return SVE_ERR_CUDA; }
+      }
+      for (; k + kBatchGraphSteps <= nsteps; k += kBatchGraphSteps)
+        if (cudaGraphLaunch(b->graph, b->stream) != cudaSuccess) return SVE_ERR_CUDA;
+    }
+    for (; k < nsteps; ++k) launch_batch_march(b, b->stream, (k - 1) & 1);
+    launch_batch_apply(b, b->stream, (nsteps - 1) & 1);
+    if (cudaGetLastError() != cudaSuccess) return SVE_ERR_CUDA;
+    std::fill(b->mass_src.begin(), b->mass_src.end(), 1);
+    b->last_launches = (long long)nsteps + 1;
+    return SVE_OK;
+  }
   int done = 0;
   if (nsteps >= kBatchGraphSteps) {
     if (!b->graph) {
       cudaGraph_t g = nullptr;
       if (cudaStreamBeginCapture(b->capture, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return SVE_ERR_CUDA;
-      for (int s = 0; s < kBatchGraphSteps; ++s) launch_batch_step_any(b, b->capture);
+      for (int s = 0; s < kBatchGraphSteps; ++s) launch_batch_step_any(b, b->capture);  // (not fused FP32 2D)
       if (cudaStreamEndCapture(b->capture, &g) != cudaSuccess) return SVE_ERR_CUDA;
       const cudaError_t e = cudaGraphInstantiate(&b->graph, g, 0);
       cudaGraphDestroy(g);

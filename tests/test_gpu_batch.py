@@ -130,6 +130,36 @@ def test_batch_fp32_runs():
         b.close()
 
 
+@pytest.mark.parametrize("n", [2, 9, 20])
+def test_fp32_batch_carried_call_equals_single_steps(n):
+    """The fused FP32 batch's carried update: one call of n steps (each
+    run's solve pass applying its previous update, the apply pass once;
+    graphs of 8 carried steps) equals n calls of one step, bit for bit --
+    states, simulated times and mass sums of every run."""
+    runs = small_ensemble()[:4]
+
+    def go(one_at_a_time):
+        b = sve.Batch([r["params"] for r in runs], "fp32")
+        for i, r in enumerate(runs):
+            b.set_state(i, r["h"], r["hu"], r["hv"], r["z"])
+        b.set_schedule(128, 1)
+        if one_at_a_time:
+            for _ in range(n):
+                b.step(1)
+        else:
+            b.step(n)
+        out = [dict(b.get_state(i), **b.diag(i)) for i in range(len(runs))]
+        b.close()
+        return out
+
+    a, c = go(False), go(True)
+    for i in range(len(runs)):
+        for k in ("h", "hu", "hv", "z"):
+            assert np.array_equal(a[i][k], c[i][k]), (i, k)
+        assert a[i]["t"] == c[i]["t"]
+        assert a[i]["mass_h"] == c[i]["mass_h"] and a[i]["mass_z"] == c[i]["mass_z"]
+
+
 def test_autotune_trials_fp32():
     """The autotuner's candidate table of the fused FP32 batch: tile size x
     schedule x rows of a strip-run (16 candidates), each timed; the choice is
