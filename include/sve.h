@@ -145,7 +145,12 @@ int sve_set_state(sve_handle* h, const void* depth, const void* hu, const void* 
 
 /* Advance nsteps CFL steps.  *t_out (nullable) receives the simulated time.
  * Blocks until the steps are done and returns the first latched device
- * error, if any. */
+ * error, if any.  With the FP32 state in 2D a call of several steps (this
+ * one, sve_step_dt, sve_step_async, sve_advance) carries each step's update
+ * into the next step's solve pass, which applies it as it reads the state,
+ * and runs the update pass once after the last solve pass: the same states,
+ * time steps and mass sums as one-step calls, bit for bit, with one trip of
+ * the state through device memory per step instead of two. */
 int sve_step(sve_handle* h, int nsteps, double* t_out);
 
 /* Advance nsteps steps of the given sizes dts[0..nsteps-1] (host memory). */
@@ -212,8 +217,10 @@ int sve_sync(sve_handle* h);
 int sve_profile(sve_handle* h, int on);
 
 /* Device time [ms] and launch count accumulated since sve_profile(h, 1):
- * index 0 = interface kernel (Riemann solves), 1 = cell kernel (update).
- * ms and launches point to two elements each.  Blocks. */
+ * index 0 = interface kernel or solve pass (Riemann solves), 1 = cell
+ * kernel or update pass (in an FP32 2D call of several steps the solve
+ * passes, which carry the updates, count under 0 and the call's one update
+ * pass under 1).  ms and launches point to two elements each.  Blocks. */
 int sve_profile_read(sve_handle* h, double* ms, long long* launches);
 
 /* Counters since the last sve_set_state: steps taken and Newton updates
@@ -248,8 +255,8 @@ int sve_get_safeguards(sve_handle* h, unsigned long long* halvings, unsigned lon
  * interfaces in large blocks would occupy a handful of SMs.  threads = 0
  * (the default at sve_create) picks 32 while a 256-thread interface launch
  * would give fewer than two blocks per SM, else 128.  Results do not depend
- * on it beyond the order of the mass sums.  The 2D FP32 step (a fused
- * shared-memory stencil with its own tiling) does not use it.  The step is
+ * on it beyond the order of the mass sums.  The 2D FP32 step (column strips
+ * marching over runs of rows, with its own launch shape) does not use it.  The step is
  * that of Sec. 3 for every shape; the paper has no counterpart of this
  * choice.  SVE_ERR_ARG for other values. */
 int sve_set_block_size(sve_handle* h, int threads);
@@ -291,7 +298,10 @@ int sve_get_block_size(sve_handle* h);
  * one run each (a tile table in a schedule order), captured in CUDA graphs.
  * With the FP32 state and every run 2D, the interface launch is the fused
  * FP32 step's solve pass (column strips marching over runs of rows, four
- * strip-runs of one run per block) and the cell launch its update pass.
+ * strip-runs of one run per block) and the cell launch its update pass;
+ * a call of several steps carries each run's update into its next solve
+ * pass (as a single handle's call does), one launch a step and one update
+ * pass a call.
  * Each run advances as a single handle with the same configuration would:
  * the same per-interface and per-cell code, compiled into other kernels, so
  * results agree to round-off (FMA contraction may differ).  Run r's state
@@ -434,8 +444,8 @@ int sve_block_advance(sve_handle* h, double sx, double sy);
  *
  * sve_step_noalloc advances the caller's state by nsteps CFL steps with the
  * kernels and arithmetic of sve_create + sve_set_state + sve_step for the
- * same configuration: the two-kernel step in FP64 and in 1D, the fused
- * shared-memory stencil for the FP32 state in 2D (128-thread blocks for the
+ * same configuration: the two-kernel step in FP64 and in 1D, the marching
+ * solve pass and the update pass for the FP32 state in 2D (128-thread blocks for the
  * two-kernel step at every grid size, so the mass sums may be added in
  * another order than a small grid's regular handle adds them).  The caller
  * passes its state as device arrays (depth, hu, hv, zb: nx*ny values of the
