@@ -167,9 +167,9 @@ def test_shields_laws_2d(law, fric):
     (31, 7, ("inflow_q", "free", "free", "free"), dict(q_in=0.5)),
 ])
 def test_fp32_state_ragged_tiles_and_boundaries(nx, ny, bc, extra):
-    """The FP32 2D step (32 x 8 tiles) on grids that leave partial tiles at
-    the right and top edges, or are smaller than one tile, under every
-    boundary rule: error against the FP64 oracle after 150 steps within the
+    """The FP32 2D step (30-column strips marching over runs of rows) on
+    grids that leave partial strips and runs at the right and top edges, or
+    are narrower than one strip, under every boundary rule: error against the FP64 oracle after 150 steps within the
     FP32 bounds, masses conserved (to FP32 rounding) on the closed and
     periodic grids."""
     w = W.random_smooth(nx, ny, seed=nx + ny, bc=bc, A_g=0.02, **extra)
