@@ -610,8 +610,11 @@ int sve_create(const sve_config* cfg, sve_handle** out) {
   // external ghosts are set by the caller between single steps)
   h->carry = h->fused;
   for (int k = 0; k < 4; ++k) h->carry = h->carry && cfg->bc[k] != SVE_BC_EXTERNAL;
+  // its second state buffer: the projection planes tau, u, v, pi, which the
+  // FP32 2D step does not read (the state upload fills them; no step reads
+  // what the upload left there)
   if (h->carry)
-    for (int k = 0; k < 4 && ok; ++k) ok = cudaMalloc(&h->alt[k], h->elem * (size_t)h->next) == cudaSuccess;
+    for (int k = 0; k < 4; ++k) h->alt[k] = h->fields[4 + k];
   if (h->fused) {
     h->march = sve::march_shape(h->P, h->nsm);
     h->agx = (h->P.nx + sve::kAThreads - 1) / sve::kAThreads;
@@ -833,8 +836,6 @@ void sve_destroy(sve_handle* h) {
   cudaStreamSynchronize(h->stream);
   for (auto e : h->events) cudaEventDestroy(e);
   for (auto& f : h->fields)
-    if (f) cudaFree(f);
-  for (auto& f : h->alt)
     if (f) cudaFree(f);
   if (h->fx) cudaFree(h->fx);
   if (h->fy) cudaFree(h->fy);

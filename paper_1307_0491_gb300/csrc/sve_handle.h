@@ -37,7 +37,7 @@ struct sve_handle {
   // rows, apply pass)
   bool fused = false;
   bool carry = false;          // fused, and no external sides: the carried update within a call
-  void* alt[4] = {};           // second state buffer: the carried update's U^{n+1} (odd steps of a call)
+  void* alt[4] = {};           // second state buffer of the carried update (= fields[4..7], unused by this form)
   sve::MarchShape march = {};  // launch shape of the solve pass (sve_march.cuh)
   int agx = 0, agy = 0;    // apply pass grid (grid stride over columns and rows)
   int nt = 256;   // threads per block of the two-kernel step (32 or 256)
