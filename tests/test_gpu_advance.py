@@ -95,13 +95,17 @@ def test_advance_in_place_pinned_and_repeated():
         assert np.array_equal(buf[k], ref[k]), k
 
 
-@pytest.mark.parametrize("kind", ["pinned", "pageable"])
-def test_advance_fp32_fused_2d(kind):
+@pytest.mark.parametrize("kind", ["pinned", "pageable", "device"])
+@pytest.mark.parametrize("n", [1, 2, 21])
+def test_advance_fp32_fused_2d(kind, n):
+    """The FP32 2D step through sve_advance: one step, and calls of several
+    steps (the carried update; device outputs written by the call's final
+    update pass itself), equal to sve_step's result bit for bit."""
     w = W.antidune2d(nx=100, ny=44, seed=13)
-    ref, t_ref = reference(w, 21, "fp32")
+    ref, t_ref = reference(w, n, "fp32")
     s = sve.Solver(w["params"], "fp32")
     inp, out = buffers(w, np.float32, kind)
-    t = s.advance(21, inp, out)
+    t = s.advance(n, inp, out)
     s.close()
     for k in KEYS:
         assert np.array_equal(host(out[k]), ref[k]), k
