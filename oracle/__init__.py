@@ -169,6 +169,8 @@ class Oracle:
         L.orc_run.argtypes = [ctypes.POINTER(_Params), ctypes.c_int, dp, dp, dp, dp, dp, dp, dp, dp,
                               ctypes.POINTER(ctypes.c_int)]
         L.orc_run.restype = ctypes.c_int
+        L.orc_split_run.argtypes = L.orc_run.argtypes
+        L.orc_split_run.restype = ctypes.c_int
         blk = [ctypes.POINTER(_Params), ctypes.c_int, ctypes.c_int, dp, dp, dp, dp]
         L.orc_block_ghost.argtypes = blk + [ctypes.c_int]
         L.orc_block_solve.argtypes = blk + [dp, dp]
@@ -232,8 +234,12 @@ class Oracle:
             raise OracleError(st, "cfl")
         return dt.value
 
-    def run(self, p: Params, nsteps: int, h, hu, hv, z, dts=None, t0: float = 0.0, check: bool = True) -> dict:
-        """Advance nsteps steps (CFL steps, or the given fixed steps dts).
+    def run(self, p: Params, nsteps: int, h, hu, hv, z, dts=None, t0: float = 0.0, check: bool = True,
+            split: bool = False) -> dict:
+        """Advance nsteps steps (CFL steps, or the given fixed steps dts);
+        split: the splitting scheme (shallow-water step, then the Exner
+        update of the bed: reading R13 of sve_oracle.c) instead of the coupled
+        step.
 
         Returns dict(h, hu, hv, z, t, dts, diag, status, done) with arrays
         shaped (ny, nx) (1D: (nx,))."""
@@ -250,9 +256,9 @@ class Oracle:
         diag = np.zeros(2 * max(nsteps, 1))
         done = ctypes.c_int(0)
         cp = p.to_c()
-        st = self.lib.orc_run(ctypes.byref(cp), int(nsteps), self._ptr(fixed), self._ptr(h), self._ptr(hu),
-                              self._ptr(hv), self._ptr(z), ctypes.byref(t), self._ptr(dts_out), self._ptr(diag),
-                              ctypes.byref(done))
+        fn = self.lib.orc_split_run if split else self.lib.orc_run
+        st = fn(ctypes.byref(cp), int(nsteps), self._ptr(fixed), self._ptr(h), self._ptr(hu), self._ptr(hv),
+                self._ptr(z), ctypes.byref(t), self._ptr(dts_out), self._ptr(diag), ctypes.byref(done))
         if st and check:
             raise OracleError(st, f"run (after {done.value} steps)")
         shape = (p.ny, p.nx) if p.dim == 2 else (p.nx,)

@@ -81,6 +81,11 @@
  *       n^2 |U|^2 / ((s-1) d_s h^(1/3)) (Manning).  The other laws of the
  *       list in Sec. 2 (Eqs. FLVB, Nielsen, Ribberink, Camenen) replace the
  *       non-dimensional rate q* in the same way.
+ *   R13 The splitting scheme (orc_split_run, the alternative Sec. 1
+ *       contrasts with the coupled method): the step with the transport
+ *       switched off for (h, hu, hv) over the fixed bed, then a first-order
+ *       Exner update of the bed with the bedload flux upwinded by the sign of
+ *       the interfaces' mean normal velocity.
  */
 #include <math.h>
 #include <stddef.h>
@@ -831,6 +836,107 @@ int orc_run(const orc_params* P, int nsteps, const double* dts, double* h, doubl
     }
   }
   if (done) *done = n;
+  free(work);
+  orc_ext_free(&X);
+  return st;
+}
+
+/* ---- the splitting scheme (the approach the paper contrasts with its own) ----
+ *
+ * Sec. 1 describes the usual alternative to the coupled method: a
+ * shallow-water step over the time step, after which the Exner equation
+ * updates the bed.  The paper gives no discretisation of it; this file takes
+ * (reading R13):
+ *   1. the shallow-water step: the step above with the transport switched off
+ *      (the Grass law with A_g = 0, so Omega = 0 and dQ/du = 0: the relaxation
+ *      solver for shallow water over the bed), its CFL time step from those
+ *      waves, friction as in the step; the bed is held at z^n;
+ *   2. the Exner step with the transport law of P and the new flow:
+ *        z_i <- z_i - dt/dx (F_{i+1/2} - F_{i-1/2}) - dt/dy (G_{j+1/2} - G_{j-1/2}),
+ *      the bedload flux at an interface being Q_s of the cell upwind of it
+ *      by the sign of the sum of the two cells' normal velocities (the mean
+ *      of both cells' where the sum is 0, so that a wall, whose ghost
+ *      mirrors the normal velocity, passes no sediment), ghost cells by the
+ *      boundary rules. */
+
+/* Bedload flux through the interface between cells (iL, jL) and (iR, jR) of
+ * X in the x (ydir = 0) or y direction: Q_s of the upwind cell, the mean of
+ * both where the normal velocities cancel (a wall: zero). */
+static double orc_exner_flux(const orc_params* P, const orc_ext* X, int iL, int jL, int iR, int jR, int ydir) {
+  double cL[4], cR[4];
+  orc_conserved(X, iL, jL, ydir, cL);
+  orc_conserved(X, iR, jR, ydir, cR);
+  double unL = cL[1] / cL[0], unR = cR[1] / cR[0];
+  double s = unL + unR, QL = 0.0, QR = 0.0, dQ;
+  if (s >= 0.0) orc_closure(P, cL[0], unL, cL[2] / cL[0], &QL, &dQ);
+  if (s <= 0.0) orc_closure(P, cR[0], unR, cR[2] / cR[0], &QR, &dQ);
+  if (s > 0.0) return QL;
+  if (s < 0.0) return QR;
+  return 0.5 * (QL + QR);
+}
+
+static int orc_split_step(const orc_params* P, orc_ext* X, double dt_fixed, double* h, double* hu, double* hv,
+                          double* z, double* dt_used, double* work, double* zn) {
+  int nx = X->nx, ny = X->ny;
+  size_t n = (size_t)nx * ny;
+  orc_params Psw = *P;
+  Psw.bedload = ORC_GRASS;
+  Psw.A_g = 0.0;
+  Psw.m_g = 3.0;
+  memcpy(zn, z, sizeof(double) * n);
+  int st = orc_step(&Psw, X, dt_fixed, h, hu, hv, z, dt_used, work);
+  if (st) return st;
+  memcpy(z, zn, sizeof(double) * n); /* the bed held fixed through the shallow-water step */
+  orc_fill(P, X, h, hu, hv, z);
+  double dt = *dt_used, dx = orc_dx(P), dy = orc_dy(P);
+  for (int j = 0; j < ny; ++j)
+    for (int i = 0; i < nx; ++i) {
+      double fe = orc_exner_flux(P, X, i, j, i + 1, j, 0);
+      double fw = orc_exner_flux(P, X, i - 1, j, i, j, 0);
+      double d = dt / dx * (fe - fw);
+      if (P->dim == 2) {
+        double gn = orc_exner_flux(P, X, i, j, i, j + 1, 1);
+        double gs = orc_exner_flux(P, X, i, j - 1, i, j, 1);
+        d += dt / dy * (gn - gs);
+      }
+      zn[(size_t)j * nx + i] = z[(size_t)j * nx + i] - d;
+    }
+  for (size_t c = 0; c < n; ++c) {
+    if (!isfinite(zn[c])) return ORC_ERR_NAN;
+    z[c] = zn[c];
+  }
+  return ORC_OK;
+}
+
+/* nsteps steps of the splitting scheme in place (arguments as orc_run). */
+int orc_split_run(const orc_params* P, int nsteps, const double* dts, double* h, double* hu, double* hv, double* z,
+                  double* t, double* dts_out, double* diag, int* done) {
+  int st = orc_check_params(P);
+  if (st) return st;
+  if (nsteps < 0 || !h || !hu || !z || (P->dim == 2 && !hv)) return ORC_ERR_ARG;
+  int nx = P->nx, ny = P->ny;
+  orc_ext X;
+  if (orc_ext_alloc(&X, nx, ny)) { orc_ext_free(&X); return ORC_ERR_ARG; }
+  double* work = malloc(sizeof(double) * 5 * (size_t)nx * ny);
+  if (!work) { orc_ext_free(&X); return ORC_ERR_ARG; }
+  double dx = orc_dx(P), dy = orc_dy(P);
+  int k;
+  st = ORC_OK;
+  for (k = 0; k < nsteps; ++k) {
+    double dt_used = 0.0;
+    st = orc_split_step(P, &X, dts ? dts[k] : 0.0, h, hu, P->dim == 2 ? hv : NULL, z, &dt_used, work,
+                        work + 4 * (size_t)nx * ny);
+    if (st) break;
+    if (t) *t += dt_used;
+    if (dts_out) dts_out[k] = dt_used;
+    if (diag) {
+      double mh = 0.0, mz = 0.0;
+      for (size_t c = 0; c < (size_t)nx * ny; ++c) { mh += h[c]; mz += z[c]; }
+      diag[2 * k] = mh * dx * dy;
+      diag[2 * k + 1] = mz * dx * dy;
+    }
+  }
+  if (done) *done = k;
   free(work);
   orc_ext_free(&X);
   return st;

@@ -16,6 +16,7 @@ import pytest
 
 import oracle
 from tests import test_oracle_pins as pins
+from tests import test_oracle_split as split
 
 SRC = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "oracle", "sve_oracle.c")
 
@@ -53,6 +54,13 @@ MUTANTS = [
     ("newton_stops_on_halved_step", "if (!halved && fabs(step) <= P->newton_tol * p)",
      "if (fabs(step) <= P->newton_tol * p)"),
     ("celerity_not_doubled_on_retry", "    a = 2.0 * a;\n", "    a = 1.0 * a;\n"),
+    # the splitting scheme (reading R13)
+    ("split_exner_downwind", "  if (s > 0.0) return QL;", "  if (s > 0.0) return QR;"),
+    ("split_exner_sign", "zn[(size_t)j * nx + i] = z[(size_t)j * nx + i] - d;",
+     "zn[(size_t)j * nx + i] = z[(size_t)j * nx + i] + d;"),
+    ("split_bed_not_held", "  memcpy(z, zn, sizeof(double) * n); /* the bed held fixed", "  /* the bed held fixed"),
+    ("split_dy_for_dx", "double d = dt / dx * (fe - fw);", "double d = dt / dy * (fe - fw);"),
+    ("split_old_ghosts", "  orc_fill(P, X, h, hu, hv, z);\n  double dt = *dt_used, dx", "  double dt = *dt_used, dx"),
 ]
 
 # pins run against each mutant: (callable, args)
@@ -70,6 +78,10 @@ PINS = [
     (pins.test_mass_conservation, ("walls2d",)),
     (pins.test_cfl_rule, ()),
     (pins.test_riemann_hard_pairs_reach_a_root, ()),
+    (split.test_without_transport_the_bed_is_rigid_and_the_flow_that_of_the_coupled_step, ()),
+    (split.test_exner_conserves_the_sediment, (1, ("wall", "wall", "wall", "wall"))),
+    (split.test_one_step_by_hand, ()),
+    (split.test_uniform_flow_moves_no_bed, ()),
 ]
 
 
