@@ -57,6 +57,7 @@ enum {
 };
 
 enum { SVE_FP64 = 0, SVE_FP32 = 1 };                       /* state precision */
+enum { SVE_SCHEME_COUPLED = 0, SVE_SCHEME_SPLIT = 1 };      /* step scheme (sve_set_scheme) */
 /* bedload law: Grass, or a Shields-parameter law of Sec. 2 */
 enum { SVE_GRASS = 0, SVE_MPM = 1, SVE_FLVB = 2, SVE_NIELSEN = 3, SVE_RIBBERINK = 4, SVE_CAMENEN = 5 };
 enum { SVE_FRIC_NONE = 0, SVE_FRIC_DARCY = 1, SVE_FRIC_STRICKLER = 2 };
@@ -260,6 +261,27 @@ int sve_get_safeguards(sve_handle* h, unsigned long long* halvings, unsigned lon
  * that of Sec. 3 for every shape; the paper has no counterpart of this
  * choice.  SVE_ERR_ARG for other values. */
 int sve_set_block_size(sve_handle* h, int threads);
+
+/* ---- the splitting scheme (comparison) ------------------------------------
+ * Sec. 1 of the paper contrasts its coupled method with the usual
+ * splitting approach -- a shallow-water step over the time step, then the
+ * Exner equation updates the bed -- which it says can create spurious
+ * oscillations.  sve_set_scheme(h, SVE_SCHEME_SPLIT) makes the handle's
+ * steps that scheme (the paper gives no discretisation of it; this library
+ * takes): (1) the coupled step with the transport switched off (Grass law
+ * with A_g = 0: the relaxation solver for shallow water over the bed; its
+ * CFL time step; friction as configured), the bed held at z^n; (2) the bed
+ * updated by a first-order finite-volume Exner step with the configured
+ * transport law evaluated on the new flow, the flux through each interface
+ * taken from the cell upwind of it by the sign of the sum of the two cells'
+ * normal velocities (their mean where that sum is 0: a wall passes no
+ * sediment).  SVE_SCHEME_COUPLED (the default) restores the paper's step.
+ * FP64 handles without external sides only (SVE_ERR_ARG otherwise); the
+ * current state, if any, is re-projected for the new scheme (blocks).  Not
+ * for the adjoint (sve_record_forward returns SVE_ERR_ARG while it is on).
+ * sve_get_scheme returns the scheme, SVE_ERR_ARG for a NULL handle. */
+int sve_set_scheme(sve_handle* h, int scheme);
+int sve_get_scheme(sve_handle* h);
 
 /* ---- persistent step of small grids (opt-in) -------------------------------
  * With on = 1 the steps of one call run as cooperative launches of one-warp

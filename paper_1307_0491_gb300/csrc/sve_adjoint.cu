@@ -613,7 +613,7 @@ extern "C" {
 int sve_record_forward(sve_handle* h, int nsteps, int checkpoint_every) {
   if (!h || nsteps < 1) return SVE_ERR_ARG;
   if (!h->has_state) return SVE_ERR_STATE;
-  if (h->cfg.precision != SVE_FP64 || sve_internal_has_external(&h->cfg)) return SVE_ERR_ARG;
+  if (h->cfg.precision != SVE_FP64 || sve_internal_has_external(&h->cfg) || h->scheme) return SVE_ERR_ARG;
   sve_internal_adjoint_free(h);
   sve_adjoint_rec* r = new sve_adjoint_rec();
   h->adj = r;

@@ -8,6 +8,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <type_traits>
 #include <vector>
 
 #include "../../include/sve.h"
@@ -124,27 +125,45 @@ void make_params(const sve_config* c, DevParams* P) {
   P->f.two_g_gamma = (float)P->two_g_gamma;
 }
 
+// The parameters of the step's kernels: the configuration's, or for the
+// splitting scheme its shallow-water step's (transport switched off).
+const DevParams& step_params(const sve_handle* h) { return h->scheme ? h->P_sw : h->P; }
+
 template <typename T>
 void launch_step(sve_handle* h, cudaStream_t st, int fixed, cudaEvent_t* ev, const void* const* mirror) {
   DevState<T> S = state_of<T>(h);
   sve::Mirror<T> out{};
   if (mirror) out = {(T*)mirror[0], (T*)mirror[1], (T*)mirror[2], (T*)mirror[3]};
   const int nt = h->nt;
+  const DevParams& PS = step_params(h);
   const unsigned nbi = (unsigned)sve::iface_blocks(h->P, nt), nbc = (unsigned)sve::cell_blocks(h->P, nt);
+  const bool split = std::is_same<T, double>::value && h->scheme;
+  if (split) cudaMemcpyAsync(h->zsave, h->fields[3], sizeof(double) * (size_t)h->next, cudaMemcpyDeviceToDevice, st);
   if (ev) cudaEventRecord(ev[0], st);
   if (nt == sve::kThreadsNarrow)
-    sve::interface_kernel<T, sve::kThreadsNarrow><<<nbi, nt, 0, st>>>(h->P, S, h->sc, h->fixed, h->dtlog, fixed);
+    sve::interface_kernel<T, sve::kThreadsNarrow><<<nbi, nt, 0, st>>>(PS, S, h->sc, h->fixed, h->dtlog, fixed);
   else if (nt == sve::kThreadsStep)
-    sve::interface_kernel<T, sve::kThreadsStep><<<nbi, nt, 0, st>>>(h->P, S, h->sc, h->fixed, h->dtlog, fixed);
+    sve::interface_kernel<T, sve::kThreadsStep><<<nbi, nt, 0, st>>>(PS, S, h->sc, h->fixed, h->dtlog, fixed);
   else
-    sve::interface_kernel<T, sve::kThreads><<<nbi, nt, 0, st>>>(h->P, S, h->sc, h->fixed, h->dtlog, fixed);
+    sve::interface_kernel<T, sve::kThreads><<<nbi, nt, 0, st>>>(PS, S, h->sc, h->fixed, h->dtlog, fixed);
   if (ev) cudaEventRecord(ev[1], st);
   if (nt == sve::kThreadsNarrow)
-    sve::cell_kernel<T, sve::kThreadsNarrow><<<nbc, nt, 0, st>>>(h->P, S, h->sc, h->mpart, out);
+    sve::cell_kernel<T, sve::kThreadsNarrow><<<nbc, nt, 0, st>>>(PS, S, h->sc, h->mpart, out);
   else if (nt == sve::kThreadsStep)
-    sve::cell_kernel<T, sve::kThreadsStep><<<nbc, nt, 0, st>>>(h->P, S, h->sc, h->mpart, out);
+    sve::cell_kernel<T, sve::kThreadsStep><<<nbc, nt, 0, st>>>(PS, S, h->sc, h->mpart, out);
   else
-    sve::cell_kernel<T, sve::kThreads><<<nbc, nt, 0, st>>>(h->P, S, h->sc, h->mpart, out);
+    sve::cell_kernel<T, sve::kThreads><<<nbc, nt, 0, st>>>(PS, S, h->sc, h->mpart, out);
+  if constexpr (std::is_same<T, double>::value) {
+    if (split) {
+      // the Exner update of the held bed with the configured transport law
+      if (nt == sve::kThreadsNarrow)
+        sve::exner_kernel<sve::kThreadsNarrow><<<nbc, nt, 0, st>>>(h->P, S, h->zsave, h->sc, h->mpart);
+      else if (nt == sve::kThreadsStep)
+        sve::exner_kernel<sve::kThreadsStep><<<nbc, nt, 0, st>>>(h->P, S, h->zsave, h->sc, h->mpart);
+      else
+        sve::exner_kernel<sve::kThreads><<<nbc, nt, 0, st>>>(h->P, S, h->zsave, h->sc, h->mpart);
+    }
+  }
   if (ev) cudaEventRecord(ev[2], st);
 }
 
@@ -308,7 +327,9 @@ void drop_graphs(sve_handle* h) {
 // Whether steps run as persistent cooperative launches (opt-in: measured no
 // faster than the two kernels from CUDA graphs, whose launches overlap the
 // steps' FP64 latency chains).
-bool use_persistent(const sve_handle* h) { return h->persist_ok && !h->profiling && h->persist_mode == 1; }
+bool use_persistent(const sve_handle* h) {
+  return h->persist_ok && !h->profiling && h->persist_mode == 1 && !h->scheme;
+}
 
 constexpr int kPersistChunk = 4096;  // steps per persistent launch
 
@@ -482,7 +503,7 @@ __global__ void __launch_bounds__(sve::kThreads) init_rows_kernel(DevParams P, D
 // Host upload of the interior state in bands of rows on the upload stream,
 // each band projected on the handle's stream as soon as it has arrived.
 int upload_in_bands(sve_handle* h, const void* const src[4], int nbands) {
-  const DevParams& P = h->P;
+  const DevParams& P = step_params(h);
   const size_t row = h->elem * (size_t)P.nx, pitch = h->elem * (size_t)P.ex;
   SVE_TRY(cudaMemsetAsync(h->sc, 0, sizeof(DevScalars), h->stream));
   SVE_TRY(cudaEventRecord(h->up_ev[0], h->stream));  // the state may still be in use
@@ -590,6 +611,13 @@ int sve_create(const sve_config* cfg, sve_handle** out) {
   make_params(cfg, &h->P);
   if (cudaGetDevice(&h->device) != cudaSuccess) { delete h; return SVE_ERR_CUDA; }
   h->elem = cfg->precision == SVE_FP64 ? 8 : 4;
+  h->P_sw = h->P;  // the splitting scheme's shallow-water step: no transport
+  h->P_sw.bedload = 0;
+  h->P_sw.A_g = 0.0;
+  h->P_sw.f.A_g = 0.0f;
+  h->P_sw.m_g = 3.0;
+  h->P_sw.f.m_g = 3.0f;
+  h->P_sw.m_int = 3;
   h->next = (long long)(h->P.nx + 2) * (h->P.ny + 2);
   // block size of the two-kernel step: 128 threads, or one warp per block
   // while the grid is too small to give every SM two 256-thread blocks
@@ -690,7 +718,7 @@ int sve_advance(sve_handle* h, int nsteps, const void* depth_in, const void* hu_
   // whose run time covers the host-link time of its stores.  The FP32 fused
   // step's apply pass is memory-bound, and host stores from it make it
   // link-bound (slower than a copy after it).
-  bool direct = where == SVE_DEVICE || !h->fused;
+  bool direct = (where == SVE_DEVICE || !h->fused) && !h->scheme;  // (the split step's bed changes after the cell update)
   for (int f = 0; f < 4; ++f) {
     if (!out[f]) continue;
     mirror[f] = direct_ptr(out[f], where);
@@ -719,7 +747,7 @@ namespace {
 int enqueue_set_state(sve_handle* h, const void* depth, const void* hu, const void* hv, const void* zb, int where) {
   if (!h || !depth || !hu || !zb || (h->cfg.dim == 2 && !hv)) return SVE_ERR_ARG;
   if (where != SVE_HOST && where != SVE_DEVICE) return SVE_ERR_ARG;
-  const DevParams& P = h->P;
+  const DevParams& P = step_params(h);
   const size_t row = h->elem * (size_t)P.nx;
   const size_t pitch = h->elem * (size_t)P.ex;
   const cudaMemcpyKind kind = where == SVE_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
@@ -839,6 +867,7 @@ void sve_destroy(sve_handle* h) {
     if (f) cudaFree(f);
   if (h->fx) cudaFree(h->fx);
   if (h->fy) cudaFree(h->fy);
+  if (h->zsave) cudaFree(h->zsave);
   if (h->mpart) cudaFree(h->mpart);
   if (h->sc) cudaFree(h->sc);
   if (h->ps) cudaFree(h->ps);
@@ -894,6 +923,25 @@ int sve_get_persistent(sve_handle* h) {
   if (!h) return SVE_ERR_ARG;
   return use_persistent(h) ? 1 : 0;
 }
+
+int sve_set_scheme(sve_handle* h, int scheme) {
+  if (!h || (scheme != SVE_SCHEME_COUPLED && scheme != SVE_SCHEME_SPLIT)) return SVE_ERR_ARG;
+  if (scheme == SVE_SCHEME_SPLIT && (h->cfg.precision != SVE_FP64 || sve_internal_has_external(&h->cfg)))
+    return SVE_ERR_ARG;
+  if (scheme == h->scheme) return SVE_OK;
+  if (scheme == SVE_SCHEME_SPLIT && !h->zsave &&
+      cudaMalloc(&h->zsave, sizeof(double) * (size_t)h->next) != cudaSuccess)
+    return SVE_ERR_OOM;
+  drop_graphs(h);  // they hold the other step
+  h->scheme = scheme;
+  if (!h->has_state) return SVE_OK;
+  // the current state projected for the new step's parameters
+  sve::init_kernel<double><<<(unsigned)sve::cell_blocks(h->P, sve::kThreads), sve::kThreads, 0, h->stream>>>(
+      step_params(h), state_of<double>(h), h->sc, h->mpart);
+  return wait_status(h);
+}
+
+int sve_get_scheme(sve_handle* h) { return h ? h->scheme : SVE_ERR_ARG; }
 
 int sve_check_sync_timeout(sve_handle* h, long long polls) {
   if (!h || polls < 1) return SVE_ERR_ARG;

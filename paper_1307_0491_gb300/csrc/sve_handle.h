@@ -8,6 +8,7 @@
 #include "sve_device.cuh"
 #include "sve_persist.cuh"
 #include "sve_march.cuh"
+#include "sve_split.cuh"
 
 struct sve_adjoint_rec;  // recorded forward run (sve_adjoint.cu)
 
@@ -59,6 +60,11 @@ struct sve_handle {
   size_t events_used = 0;
   double prof_ms[2] = {0.0, 0.0};
   long long prof_launches[2] = {0, 0};
+  // the splitting scheme (sve_split.cuh; FP64): 1 when on; the step's
+  // parameters with the transport switched off; the held bed (padded)
+  int scheme = 0;
+  sve::DevParams P_sw;
+  double* zsave = nullptr;
   sve_adjoint_rec* adj = nullptr;
   long long adj_budget = -1;  // bytes of forward data a recording may keep (-1: half the free device memory)
   void* halo = nullptr;    // staging of one side's ghost ring for the block calls (sve_block.cu)

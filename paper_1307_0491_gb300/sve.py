@@ -24,6 +24,7 @@ SVE_ERR_NOALLOC_SIZE = -9
 SVE_ERR_SYNC = -10
 SVE_NOALLOC_SCRATCH_BYTES = 8 << 20
 SVE_FP64, SVE_FP32 = 0, 1
+SVE_SCHEME_COUPLED, SVE_SCHEME_SPLIT = 0, 1
 SVE_GRASS, SVE_MPM, SVE_FLVB, SVE_NIELSEN, SVE_RIBBERINK, SVE_CAMENEN = 0, 1, 2, 3, 4, 5
 SVE_FRIC_NONE, SVE_FRIC_DARCY, SVE_FRIC_STRICKLER = 0, 1, 2
 SVE_BC_PERIODIC, SVE_BC_FREE, SVE_BC_INFLOW_Q, SVE_BC_INFLOW_QH, SVE_BC_WALL, SVE_BC_EXTERNAL = 0, 1, 2, 3, 4, 5
@@ -41,7 +42,7 @@ EXPORTS = ("sve_config_default", "sve_create", "sve_set_stream", "sve_set_state"
            "sve_get_checkpoint_every", "sve_set_persistent", "sve_get_persistent", "sve_check_sync_timeout",
            "sve_get_safeguards", "sve_block_get_edge", "sve_block_set_ghosts", "sve_block_speeds",
            "sve_block_advance", "sve_batch_autotune_trials", "sve_batch_set_rows", "sve_batch_get_rows",
-           "sve_set_adjoint_budget", "sve_get_adjoint_kept_steps")
+           "sve_set_adjoint_budget", "sve_get_adjoint_kept_steps", "sve_set_scheme", "sve_get_scheme")
 
 
 class sve_config(ctypes.Structure):
@@ -119,6 +120,8 @@ def load() -> ctypes.CDLL:
         "sve_record_forward": ([vp, ip, ip], ip),
         "sve_get_checkpoint_every": ([vp], ip),
         "sve_set_adjoint_budget": ([vp, ctypes.c_longlong], ip),
+        "sve_set_scheme": ([vp, ip], ip),
+        "sve_get_scheme": ([vp], ip),
         "sve_get_adjoint_kept_steps": ([vp], ip),
         "sve_set_persistent": ([vp, ip], ip),
         "sve_get_persistent": ([vp], ip),
@@ -551,6 +554,17 @@ class Solver:
         n = load().sve_get_checkpoint_every(self.h)
         _check(min(n, 0), "sve_get_checkpoint_every")
         return n
+
+    def set_scheme(self, scheme: str) -> None:
+        """"coupled" (the paper's step, the default) or "split" (the
+        splitting scheme it is contrasted with: a shallow-water step, then
+        an upwind Exner update of the bed) -- sve_set_scheme."""
+        code = {"coupled": SVE_SCHEME_COUPLED, "split": SVE_SCHEME_SPLIT}[scheme]
+        _check(load().sve_set_scheme(self.h, code), "sve_set_scheme")
+
+    @property
+    def scheme(self) -> str:
+        return "split" if load().sve_get_scheme(self.h) == SVE_SCHEME_SPLIT else "coupled"
 
     def adjoint_kept_steps(self) -> int:
         """How many recorded steps' forward data the recording kept."""
