@@ -434,6 +434,41 @@ def run_adjoint(args, sve, W, torch):
             "time": "wall clock around the C-ABI calls (host-synchronous)"}
 
 
+def run_splitting(args, sve, W, torch):
+    """The splitting scheme Sec. 2 contrasts with the coupled method (a
+    shallow-water step, then an upwind Exner update of the bed;
+    sve_set_scheme) against the coupled step, on the paper's 1D dune (1000 m,
+    h = 10 - z_b, q0 = 10, Grass A_g = 1, m_g = 3) at J = 2000 for 2000 CFL
+    steps: steps per second of each (wall clock around one host-synchronous
+    sve_step call) and the bed it leaves -- total variation, local extrema,
+    crest and trough."""
+    w = W.paper_dune1d(nx=2000, A_g=1.0)
+    n = 2000
+
+    def bed(z):
+        dz = np.diff(np.asarray(z, dtype=np.float64))
+        return {"total_variation": float(np.sum(np.abs(dz))),
+                "local_extrema": int(np.sum(np.sign(dz[1:]) * np.sign(dz[:-1]) < 0)),
+                "z_max": float(np.max(z)), "z_min": float(np.min(z))}
+
+    out = {"workload": "1D dune (Sec. 5.1 setting: 1000 m, h = 10 - z_b, q0 = 10, Grass A_g = 1, m_g = 3), "
+                       "2000 cells, 2000 CFL steps", "steps": n, "initial_bed": bed(w["z"])}
+    for scheme in ("coupled", "split"):
+        s = sve.Solver(w["params"], "fp64")
+        s.set_scheme(scheme)
+        s.set_state(w["h"], w["hu"], w["hv"], w["z"])
+        s.step(16)  # graphs captured
+        s.set_state(w["h"], w["hu"], w["hv"], w["z"])
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        t = s.step(n)
+        dt = time.perf_counter() - t0
+        out[scheme] = {"steps_per_s": n / dt, "t_end": t, "bed": bed(s.get_state()["z"])}
+        s.close()
+    out["time"] = "wall clock around one host-synchronous sve_step call of all steps"
+    return out
+
+
 def run_small1d(args, sve, W, torch):
     """Small 1D grids, where a step is a few microseconds of work and its FP64
     work has to be spread over many SMs: the 1D dune (1000 cells, periodic,
@@ -903,6 +938,7 @@ def run_ours(args, world, rank, local):
             line["adjoint"] = run_adjoint(args, sve, W, torch)
         if not args.no_small1d:
             line["small1d"] = run_small1d(args, sve, W, torch)
+            line["splitting"] = run_splitting(args, sve, W, torch)
         if not args.no_closures:
             line["closures"] = run_closures(args, sve, W, torch)
         if not args.no_fp32_error:

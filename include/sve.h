@@ -263,7 +263,7 @@ int sve_get_safeguards(sve_handle* h, unsigned long long* halvings, unsigned lon
 int sve_set_block_size(sve_handle* h, int threads);
 
 /* ---- the splitting scheme (comparison) ------------------------------------
- * Sec. 1 of the paper contrasts its coupled method with the usual
+ * The end of Sec. 2 of the paper contrasts its coupled method with the usual
  * splitting approach -- a shallow-water step over the time step, then the
  * Exner equation updates the bed -- which it says can create spurious
  * oscillations.  sve_set_scheme(h, SVE_SCHEME_SPLIT) makes the handle's

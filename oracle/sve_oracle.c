@@ -81,7 +81,7 @@
  *       n^2 |U|^2 / ((s-1) d_s h^(1/3)) (Manning).  The other laws of the
  *       list in Sec. 2 (Eqs. FLVB, Nielsen, Ribberink, Camenen) replace the
  *       non-dimensional rate q* in the same way.
- *   R13 The splitting scheme (orc_split_run, the alternative Sec. 1
+ *   R13 The splitting scheme (orc_split_run, the alternative Sec. 2
  *       contrasts with the coupled method): the step with the transport
  *       switched off for (h, hu, hv) over the fixed bed, then a first-order
  *       Exner update of the bed with the bedload flux upwinded by the sign of
@@ -843,7 +843,7 @@ int orc_run(const orc_params* P, int nsteps, const double* dts, double* h, doubl
 
 /* ---- the splitting scheme (the approach the paper contrasts with its own) ----
  *
- * Sec. 1 describes the usual alternative to the coupled method: a
+ * The end of Sec. 2 describes the usual alternative to the coupled method: a
  * shallow-water step over the time step, after which the Exner equation
  * updates the bed.  The paper gives no discretisation of it; this file takes
  * (reading R13):

@@ -1,5 +1,5 @@
 // sve_split.cuh -- the splitting scheme (FP64): the approach the paper's
-// Sec. 1 contrasts with its coupled method -- a shallow-water step over the
+// Sec. 2 contrasts with its coupled method -- a shallow-water step over the
 // time step, after which the Exner equation updates the bed.
 //
 // The paper gives no discretisation of it; the library takes:

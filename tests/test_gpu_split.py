@@ -1,5 +1,5 @@
 """The splitting scheme on the GPU (sve_set_scheme(SVE_SCHEME_SPLIT); the
-alternative Sec. 1 of the paper contrasts with its coupled method): against
+alternative Sec. 2 of the paper contrasts with its coupled method): against
 the oracle's splitting scheme (reading R13 of oracle/sve_oracle.c) element
 by element at 1e-10 after the config's step count, in 1D and 2D, under every
 boundary rule and for the Grass and a Shields-parameter law; steps in CUDA

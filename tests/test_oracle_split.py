@@ -1,5 +1,5 @@
 """Pins of the oracle's splitting scheme (orc_split_run; reading R13 of
-oracle/sve_oracle.c): the alternative the paper's Sec. 1 contrasts with its
+oracle/sve_oracle.c): the alternative the paper's Sec. 2 contrasts with its
 coupled method -- a shallow-water step, then the Exner equation updates the
 bed.  Each test checks it against what the paper or the mathematics fix:
 A_g = 0 leaves the bed rigid (Sec. 2) and the flow that of the coupled step;
