@@ -194,6 +194,20 @@ int sve_get_diag(sve_handle* h, double* mass_h, double* mass_z, double* t, doubl
  * error code. */
 int sve_get_dts(sve_handle* h, double* dts, int n);
 
+/* Per-step history (off by default).  sve_set_history(h, capacity) keeps,
+ * after every later step, one record of six doubles in a device ring of
+ * `capacity` records: t after the step, its dt, mass_h and mass_z of the new
+ * state (as sve_get_diag sums them) and the step's extreme wave speeds Sx,
+ * Sy (0 in 1D).  capacity 0 switches it off; every call empties the ring,
+ * and so does sve_set_state.  Each step then launches one more small kernel,
+ * and FP32 2D calls of several steps run their steps one at a time (each
+ * step's mass sums are needed).  SVE_ERR_ARG for capacity < 0, SVE_ERR_OOM.
+ * sve_get_history copies the last min(n, steps recorded, capacity) records,
+ * oldest first, into records (host, 6 doubles each) and returns how many
+ * (blocks); SVE_ERR_STATE while the history is off. */
+int sve_set_history(sve_handle* h, int capacity);
+int sve_get_history(sve_handle* h, double* records, int n);
+
 /* Release everything the handle owns.  NULL is accepted. */
 void sve_destroy(sve_handle* h);
 

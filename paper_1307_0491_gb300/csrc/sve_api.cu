@@ -241,11 +241,32 @@ void launch_carried_apply(sve_handle* h, cudaStream_t st, int n, cudaEvent_t* ev
 
 // mirror: null, or four row-major destinations (device-accessible) that the
 // step's cell update also writes the new interior state to.
+// One record of the per-step history ring after a step: (t, dt, mass_h,
+// mass_z, Sx, Sy) -- the masses from the step's per-block partials, summed
+// as mass_kernel sums them.
+__global__ void __launch_bounds__(sve::kThreads) history_kernel(DevParams P, DevScalars* sc, const double* mpart,
+                                                                double* hist, int cap) {
+  __shared__ double sh[2 * (sve::kThreads / 32)];
+  double a, b;
+  sve::reduce_partials<sve::kThreads>(mpart, sc->mass_parts, a, b, sh);
+  if (threadIdx.x != 0) return;
+  const double cell = P.dx * (P.dim == 2 ? P.dy : 1.0);
+  double* r = hist + 6 * (size_t)(sc->hist_count % (unsigned long long)cap);
+  r[0] = sc->t;
+  r[1] = sc->dt;
+  r[2] = a * cell;
+  r[3] = b * cell;
+  r[4] = sc->Sx;
+  r[5] = P.dim == 2 ? sc->Sy : 0.0;
+  sc->hist_count += 1;
+}
+
 void launch_step_any(sve_handle* h, cudaStream_t st, int fixed, cudaEvent_t* ev = nullptr,
                      const void* const* mirror = nullptr) {
   if (h->cfg.precision == SVE_FP64) launch_step<double>(h, st, fixed, ev, mirror);
   else if (h->fused) launch_fused_step(h, st, fixed, ev, mirror);
   else launch_step<float>(h, st, fixed, ev, mirror);
+  if (h->hist_cap > 0) history_kernel<<<1, sve::kThreads, 0, st>>>(h->P, h->sc, h->mpart, h->hist, h->hist_cap);
 }
 
 // Three events for one profiled step or pass (grown on demand); kind: which
@@ -295,6 +316,11 @@ int ensure_capacity(double** buf, int* cap, int n) {
   return SVE_OK;
 }
 
+// Whether calls of several steps carry the FP32 2D update into the next
+// solve pass (not while per-step records are kept: those need each step's
+// mass sums).
+bool carrying(const sve_handle* h) { return h->carry && h->hist_cap == 0; }
+
 // kGraphSteps steps: the two-kernel or fused step, or, for the carried
 // update, kGraphSteps carried solve passes from buffer 0 (steps k = 1, 3,
 // ... of a call: kGraphSteps is even, so every such graph starts there).
@@ -304,7 +330,7 @@ int get_graph(sve_handle* h, int fixed, cudaGraphExec_t* out) {
     cudaGraph_t g = nullptr;
     SVE_TRY(cudaStreamBeginCapture(h->capture, cudaStreamCaptureModeThreadLocal));
     for (int s = 0; s < kGraphSteps; ++s) {
-      if (h->carry) launch_carried_march(h, h->capture, fixed, s + 1, nullptr);
+      if (carrying(h)) launch_carried_march(h, h->capture, fixed, s + 1, nullptr);
       else launch_step_any(h, h->capture, fixed);
     }
     cudaError_t e = cudaStreamEndCapture(h->capture, &g);
@@ -328,7 +354,7 @@ void drop_graphs(sve_handle* h) {
 // faster than the two kernels from CUDA graphs, whose launches overlap the
 // steps' FP64 latency chains).
 bool use_persistent(const sve_handle* h) {
-  return h->persist_ok && !h->profiling && h->persist_mode == 1 && !h->scheme;
+  return h->persist_ok && !h->profiling && h->persist_mode == 1 && !h->scheme && h->hist_cap == 0;
 }
 
 constexpr int kPersistChunk = 4096;  // steps per persistent launch
@@ -392,7 +418,7 @@ int enqueue_steps(sve_handle* h, int nsteps, int fixed, const void* const* mirro
     h->last_steps = nsteps;
     return SVE_OK;
   }
-  if (h->carry && nsteps > 1) {
+  if (carrying(h) && nsteps > 1) {
     // the carried update: step 0, steps 1 .. n - 1 (graphs of kGraphSteps
     // from step 1 on), the apply pass (one step: the plain step below)
     int k = 1;
@@ -868,6 +894,7 @@ void sve_destroy(sve_handle* h) {
   if (h->fx) cudaFree(h->fx);
   if (h->fy) cudaFree(h->fy);
   if (h->zsave) cudaFree(h->zsave);
+  if (h->hist) cudaFree(h->hist);
   if (h->mpart) cudaFree(h->mpart);
   if (h->sc) cudaFree(h->sc);
   if (h->ps) cudaFree(h->ps);
@@ -942,6 +969,42 @@ int sve_set_scheme(sve_handle* h, int scheme) {
 }
 
 int sve_get_scheme(sve_handle* h) { return h ? h->scheme : SVE_ERR_ARG; }
+
+int sve_set_history(sve_handle* h, int capacity) {
+  if (!h || capacity < 0) return SVE_ERR_ARG;
+  if (capacity != h->hist_cap) {
+    SVE_TRY(cudaStreamSynchronize(h->stream));
+    if (h->hist) cudaFree(h->hist);
+    h->hist = nullptr;
+    h->hist_cap = 0;
+    if (capacity > 0 && cudaMalloc(&h->hist, sizeof(double) * 6 * (size_t)capacity) != cudaSuccess) return SVE_ERR_OOM;
+    h->hist_cap = capacity;
+    drop_graphs(h);  // they hold the step without (or with) its record
+  }
+  SVE_TRY(cudaMemsetAsync(&h->sc->hist_count, 0, sizeof(unsigned long long), h->stream));
+  return SVE_OK;
+}
+
+int sve_get_history(sve_handle* h, double* records, int n) {
+  if (!h || n < 0 || (n > 0 && !records)) return SVE_ERR_ARG;
+  if (h->hist_cap == 0) return SVE_ERR_STATE;
+  unsigned long long count = 0;
+  SVE_TRY(cudaMemcpyAsync(&count, &h->sc->hist_count, sizeof(count), cudaMemcpyDeviceToHost, h->stream));
+  SVE_TRY(cudaStreamSynchronize(h->stream));
+  const unsigned long long avail = count < (unsigned long long)h->hist_cap ? count : (unsigned long long)h->hist_cap;
+  const int m = (int)(avail < (unsigned long long)n ? avail : (unsigned long long)n);
+  // the last m records, oldest first: at most two pieces of the ring
+  const size_t start = (size_t)((count - (unsigned long long)m) % (unsigned long long)h->hist_cap);
+  const size_t first = std::min((size_t)m, (size_t)h->hist_cap - start);
+  if (first > 0)
+    SVE_TRY(cudaMemcpyAsync(records, h->hist + 6 * start, sizeof(double) * 6 * first, cudaMemcpyDeviceToHost,
+                            h->stream));
+  if ((size_t)m > first)
+    SVE_TRY(cudaMemcpyAsync(records + 6 * first, h->hist, sizeof(double) * 6 * ((size_t)m - first),
+                            cudaMemcpyDeviceToHost, h->stream));
+  SVE_TRY(cudaStreamSynchronize(h->stream));
+  return m;
+}
 
 int sve_check_sync_timeout(sve_handle* h, long long polls) {
   if (!h || polls < 1) return SVE_ERR_ARG;

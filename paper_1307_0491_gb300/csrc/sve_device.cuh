@@ -82,6 +82,7 @@ struct DevScalars {
   // a was raised by the bed-jump bound (gamma_z), and doublings of a where
   // the bounds admitted no solution with positive tau_k
   unsigned long long halvings, raised, retries;
+  unsigned long long hist_count;  // records written to the per-step history ring (sve_set_history)
 };
 
 // Ghost-padded state and projection (SoA) of precision T.

@@ -60,6 +60,9 @@ struct sve_handle {
   size_t events_used = 0;
   double prof_ms[2] = {0.0, 0.0};
   long long prof_launches[2] = {0, 0};
+  // per-step history ring (sve_set_history): capacity records of 6 doubles
+  double* hist = nullptr;
+  int hist_cap = 0;
   // the splitting scheme (sve_split.cuh; FP64): 1 when on; the step's
   // parameters with the transport switched off; the held bed (padded)
   int scheme = 0;

@@ -42,7 +42,8 @@ EXPORTS = ("sve_config_default", "sve_create", "sve_set_stream", "sve_set_state"
            "sve_get_checkpoint_every", "sve_set_persistent", "sve_get_persistent", "sve_check_sync_timeout",
            "sve_get_safeguards", "sve_block_get_edge", "sve_block_set_ghosts", "sve_block_speeds",
            "sve_block_advance", "sve_batch_autotune_trials", "sve_batch_set_rows", "sve_batch_get_rows",
-           "sve_set_adjoint_budget", "sve_get_adjoint_kept_steps", "sve_set_scheme", "sve_get_scheme")
+           "sve_set_adjoint_budget", "sve_get_adjoint_kept_steps", "sve_set_scheme", "sve_get_scheme",
+           "sve_set_history", "sve_get_history")
 
 
 class sve_config(ctypes.Structure):
@@ -121,6 +122,8 @@ def load() -> ctypes.CDLL:
         "sve_get_checkpoint_every": ([vp], ip),
         "sve_set_adjoint_budget": ([vp, ctypes.c_longlong], ip),
         "sve_set_scheme": ([vp, ip], ip),
+        "sve_set_history": ([vp, ip], ip),
+        "sve_get_history": ([vp, dp, ip], ip),
         "sve_get_scheme": ([vp], ip),
         "sve_get_adjoint_kept_steps": ([vp], ip),
         "sve_set_persistent": ([vp, ip], ip),
@@ -554,6 +557,19 @@ class Solver:
         n = load().sve_get_checkpoint_every(self.h)
         _check(min(n, 0), "sve_get_checkpoint_every")
         return n
+
+    def set_history(self, capacity: int) -> None:
+        """Keep a record (t, dt, mass_h, mass_z, Sx, Sy) after every later
+        step in a device ring of `capacity` records (0: off) -- sve_set_history."""
+        _check(load().sve_set_history(self.h, int(capacity)), "sve_set_history")
+
+    def history(self, n: int) -> np.ndarray:
+        """The last records, oldest first: an (m, 6) array (t, dt, mass_h,
+        mass_z, Sx, Sy), m <= n."""
+        out = np.zeros((max(n, 1), 6))
+        m = load().sve_get_history(self.h, out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), int(n))
+        _check(min(m, 0), "sve_get_history")
+        return out[:m]
 
     def set_scheme(self, scheme: str) -> None:
         """"coupled" (the paper's step, the default) or "split" (the

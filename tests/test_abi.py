@@ -112,6 +112,8 @@ def test_null_handle_checks_of_later_calls(lib):
     assert lib.sve_get_adjoint_kept_steps(null) == sve.SVE_ERR_ARG
     assert lib.sve_set_scheme(null, sve.SVE_SCHEME_SPLIT) == sve.SVE_ERR_ARG
     assert lib.sve_get_scheme(null) == sve.SVE_ERR_ARG
+    assert lib.sve_set_history(null, 4) == sve.SVE_ERR_ARG
+    assert lib.sve_get_history(null, None, 0) == sve.SVE_ERR_ARG
     rc, _, _, _ = sve.sve_get_safeguards(null)
     assert rc == sve.SVE_ERR_ARG
     assert lib.sve_block_get_edge(null, 0, None, sve.SVE_HOST) == sve.SVE_ERR_ARG
