@@ -505,8 +505,7 @@ __device__ __forceinline__ bool interface_vjp_cells(const DevParams& P, const Ce
   // fan (as fan_fluctuations, keeping the branches)
   const double lam1 = L.un - a * L.tau, lam5 = R.un + a * R.tau;
   const double us = e.u1 + b * (e.tau2 - e.tau1);
-  const int mi = (int)negative(lam1) + (int)negative(e.lam2) + (int)negative(us) + (int)negative(e.lam4) +
-                 (int)negative(lam5);
+  const int mi = fan_state(negative(lam1), negative(e.lam2), negative(us), negative(e.lam4), negative(lam5));
   const double a2 = a * a;
   const bool left = mi <= 2;
   const double tk = mi == 1 ? e.tau1 : (mi == 2 ? e.tau2 : (mi == 3 ? e.tau3 : e.tau4));

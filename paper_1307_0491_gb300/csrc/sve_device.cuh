@@ -443,6 +443,18 @@ __device__ __forceinline__ bool abs_le(float x, float y) { return fabsf(x) <= y;
 // iterate is at the edge of the admissible set, not because it is near the
 // root, so it never ends the iteration.  iters is incremented per accepted
 // update, halv by the halvings of the accepted updates.
+//
+// The update that meets the stopping rule takes the states at p + step as
+// first-order updates of those at p (m by dm/dp, 1/p by -1/p^2; tau2, tau3
+// exact), an O(tol^2) difference from a full evaluation -- no divide.  In
+// FP32, where instruction issue bounds the solve, the lanes of a warp on
+// either side of the rule evaluate the states at p + step in one code path
+// (only m and 1/p differ); in FP64, where the FP64 pipe bounds it, the
+// separate paths measured faster (C2 interface kernel 0.383 ms against
+// 0.391 ms), the converged lanes' path first.
+template <typename T> struct shared_update { static constexpr bool value = false; };
+template <> struct shared_update<float> { static constexpr bool value = true; };
+
 template <typename T>
 __device__ __forceinline__ bool newton_loop(const NewtonConst<T>& c, const Cell<T>& L, const Cell<T>& R, T& p,
                                             NewtonEval<T>& e, int maxit, T tol, int& iters, int& halv) {
@@ -452,24 +464,48 @@ __device__ __forceinline__ bool newton_loop(const NewtonConst<T>& c, const Cell<
     if (!finite_bits(step)) return false;
     NewtonEval<T> tr;
     const T pn = p + step;
-    if (abs_le(step, tol * pn)) {
-      // The update that meets the stopping rule: |step| <= tol p leaves the
-      // states at p + step first-order updates of those at p (m by dm/dp,
-      // 1/p by -1/p^2; tau2, tau3 exact), an O(tol^2) difference from a full
-      // evaluation -- no divide.
+    const bool conv = abs_le(step, tol * pn);
+    int h = 0;
+    if constexpr (shared_update<T>::value) {
       T sigma;
       newton_sigma(pn, c, tr, sigma);
-      tr.m = e.m + dm * step;
-      tr.ip = e.ip - (e.ip * e.ip) * step;
+      if (conv) {
+        tr.m = e.m + dm * step;
+        tr.ip = e.ip - (e.ip * e.ip) * step;
+      } else {
+        const T N = c.dZ + c.KD * sigma;
+        tr.ip = tdiv(T(1), pn);
+        tr.m = -N * tr.ip * c.inv_K;
+      }
       newton_states(pn, c, L, R, tr);
       if (newton_positive(tr)) {
         p = pn;
         e = tr;
         ++iters;
-        return true;
+        if (conv) return true;
+        continue;
+      }
+      // not admissible: a step that met the rule is evaluated in full next,
+      // any other one is halved
+      if (!conv) {
+        h = 1;
+        step = T(0.5) * step;
+      }
+    } else {
+      if (conv) {
+        T sigma;
+        newton_sigma(pn, c, tr, sigma);
+        tr.m = e.m + dm * step;
+        tr.ip = e.ip - (e.ip * e.ip) * step;
+        newton_states(pn, c, L, R, tr);
+        if (newton_positive(tr)) {
+          p = pn;
+          e = tr;
+          ++iters;
+          return true;
+        }
       }
     }
-    int h = 0;
     for (; h <= 60; ++h) {
       newton_eval(p + step, c, L, R, tr);
       if (newton_positive(tr)) break;
@@ -484,7 +520,6 @@ __device__ __forceinline__ bool newton_loop(const NewtonConst<T>& c, const Cell<
   }
   return false;
 }
-
 template <typename T>
 __device__ __forceinline__ bool newton_loop(const NewtonConst<T>& c, const Cell<T>& L, const Cell<T>& R, T& p,
                                             NewtonEval<T>& e, int maxit, T tol, int& iters) {
@@ -586,6 +621,13 @@ __device__ __forceinline__ T newton_setup(const DevParams& P, const Cell<T>& L, 
   return p0;
 }
 
+// State m of the fan (0 = L, 1..4 = W1..W4, 5 = R: the state after the
+// last wave of negative speed) from the signs of lam1, lam2, u*, lam4, lam5,
+// by the rule fan_fluctuations selects with.
+__device__ __forceinline__ int fan_state(bool n1, bool n2, bool n3, bool n4, bool n5) {
+  return !n1 ? 0 : (n5 ? 5 : (n4 ? 4 : (n3 ? 3 : (n2 ? 2 : 1))));
+}
+
 // Fluctuations A- = sum_{lam_k < 0} lam_k [U]_k and A+ = sum_{lam_k >= 0}
 // lam_k [U]_k over the five waves of the fan evaluated at e, U = (H, H un,
 // H ut, Z), written with the jump relations every wave of the fan satisfies
@@ -603,30 +645,34 @@ __device__ __forceinline__ void fan_fluctuations(const DevParams& P, const Cell<
   const T lam5 = c.lam5;
   const T us = e.u1 + b * (e.tau2 - e.tau1);
   const T lam2 = e.lam2, lam4 = e.lam4;
-  const int m = (int)negative(lam1) + (int)negative(lam2) + (int)negative(us) + (int)negative(lam4) +
-                (int)negative(lam5);
+  // The fan's speeds are ordered (lam1 < lam2 < u* < lam4 < lam5 for
+  // positive tau_k and a > b), so state m follows from the signs of the
+  // speeds directly: m = 0 (L) if lam1 >= 0, else 5 (R) if lam5 < 0, else
+  // the highest k in 4, 3, 2 whose wave (lam4, u*, lam2) is negative, else 1
+  // (fan_state; the same rule wherever rounding breaks the order).
+  const bool n1 = negative(lam1), n2 = negative(lam2), n3 = negative(us), n4 = negative(lam4),
+             n5 = negative(lam5);
   const T a2 = a * a;
   // flux (H un, H un^2 + Pi, H un ut) of L, R and of the state m
   const T FhL = L.Hn, FqL = L.Hn * L.un + L.Pi, FvL = L.Hn * L.ut;
   const T FhR = R.Hn, FqR = R.Hn * R.un + R.Pi, FvR = R.Hn * R.ut;
   T Fh, Fq, Fv;
   T tkv = T(1), ukv = T(0), vkv = T(0), Pkv = T(0);  // state m (m = 1..4)
-  if (m == 0) {
+  const bool inner = n1 && !n5;
+  if (!n1) {
     Fh = FhL; Fq = FqL; Fv = FvL;
-  } else if (m == 5) {
+  } else if (n5) {
     Fh = FhR; Fq = FqR; Fv = FvR;
   } else {
     // W1, W2 carry the left tangential velocity and Pi_L + a^2 (tau_L - tau);
     // W3, W4 the right ones
-    const bool left = m <= 2;
-    const T tk = m == 1 ? e.tau1 : (m == 2 ? e.tau2 : (m == 3 ? e.tau3 : e.tau4));
-    const T uk = m == 1 ? e.u1 : (m == 4 ? e.u4 : us);
-    const T vk = left ? L.ut : R.ut;
-    const T Pk = left ? L.Pi + a2 * (L.tau - tk) : R.Pi + a2 * (R.tau - tk);
+    const bool right = n3 || n4;  // m = 3 or 4
+    const T tk = n4 ? e.tau4 : (n3 ? e.tau3 : (n2 ? e.tau2 : e.tau1));
+    const T uk = n4 ? e.u4 : ((n2 || n3) ? us : e.u1);
     tkv = tk;
     ukv = uk;
-    vkv = vk;
-    Pkv = Pk;
+    vkv = right ? R.ut : L.ut;
+    Pkv = (right ? R.Pi : L.Pi) + a2 * ((right ? R.tau : L.tau) - tk);
   }
   // b-waves: bed jumps and the non-conservative source g Hbar [Z]; one
   // divide for 1/tau_k, 1/(tau1 + tau2) and 1/(tau3 + tau4)
@@ -646,12 +692,11 @@ __device__ __forceinline__ void fan_fluctuations(const DevParams& P, const Cell<
     S4 = (g2 * zj4) * (rt * d12);
     Hk = r * d1234;
   }
-  if (m != 0 && m != 5) {
+  if (inner) {
     Fh = Hk * ukv;
     Fq = Fh * ukv + Pkv;
     Fv = Fh * vkv;
   }
-  const bool n2 = negative(lam2), n4 = negative(lam4);
   Am[0] = Fh - FhL;
   Ap[0] = FhR - Fh;
   Am[1] = (Fq - FqL) + ((n2 ? S2 : T(0)) + (n4 ? S4 : T(0)));
