@@ -502,6 +502,7 @@ __device__ __forceinline__ bool interface_vjp_cells(const DevParams& P, const Ce
     Fp = newton_deriv(c, e);
     newton_eval(pstar, c, L, R, e);  // the states at the root, by a full evaluation
   }
+  newton_fill(c, L, e);
   // fan (as fan_fluctuations, keeping the branches)
   const double lam1 = L.un - a * L.tau, lam5 = R.un + a * R.tau;
   const double us = e.u1 + b * (e.tau2 - e.tau1);
@@ -511,7 +512,7 @@ __device__ __forceinline__ bool interface_vjp_cells(const DevParams& P, const Ce
   const double tk = mi == 1 ? e.tau1 : (mi == 2 ? e.tau2 : (mi == 3 ? e.tau3 : e.tau4));
   const double uk = mi == 1 ? e.u1 : (mi == 4 ? e.u4 : us);
   const double vk = left ? L.ut : R.ut;
-  const double zj2 = e.Zs - L.Z, zj4 = R.Z - e.Zs;
+  const double zj2 = e.zl, zj4 = -e.zr;  // Z* - ZL, ZR - Z*
   const double d12 = e.tau1 + e.tau2, d34 = e.tau3 + e.tau4;
   // one divide for 1/F_p, 1/tau_k, 1/(tau1 + tau2) and 1/(tau3 + tau4)
   const double t1234 = tk * (d12 * d34);

@@ -351,36 +351,47 @@ struct NewtonConst {
   T a, b, K, inv_a, inv_b, inv_K, D, C0, dZ, dsig, dN;
   // combinations the evaluation uses as they are (loop invariants of the
   // Newton iteration): sigma = s0 + dsig p, tau2,3 = sigma/2 -+ hD,
-  // N = dZ + KD sigma, u1 = lam1 + a tau1, u4 = lam5 - a tau4,
-  // F = dOm + lam2 zl - lam4 zr, F' uses amb = a - b
+  // m = -(N / K) / p with N / K = dZK + KDK sigma (N = dZ + KD sigma),
+  // lam2 = lam1 + amb tau1, lam4 = lam5 - amb tau4 (amb = a - b),
+  // F = dOm + lam2 zl - lam4 zr; F' uses dNK = dN / K and hamb = amb / 2
   T s0, hD, KD, lam1, lam5, dOm, amb;
+  T dZK, KDK, dNK, hamb;
 };
 
 // The intermediate states as functions of p (every invariant relation of the
 // a- and b-waves and the contact holds for any p) and the residual F(p) of
 // the one remaining condition, continuity of Omega across the contact.
+// (u1, u4, Zs: set by newton_fill, for the states at the root only.)
 template <typename T>
 struct NewtonEval {
   T tau1, tau2, tau3, tau4, u1, u4, lam2, lam4, Zs, F;
   T m, ip, zl, zr;  // kept for F'(p)
 };
 
-// The states at p given m = tau1 - tau4 and 1/p (e.tau2, e.tau3 set).
-// (u1 = uL + a (tau1 - tauL) = lam1 + a tau1, u4 = lam5 - a tau4.)
+// The states at p given m = tau1 - tau4 and 1/p (e.tau2, e.tau3 set): what
+// F needs -- the b-wave speeds lam2 = u1 - b tau1 = lam1 + (a - b) tau1 and
+// lam4 = lam5 - (a - b) tau4, the bed jumps zl = Z* - ZL = K (tau2^2 -
+// tau1^2) and zr = Z* - ZR = zl - (ZR - ZL).
 template <typename T>
 __device__ __forceinline__ void newton_states(T p, const NewtonConst<T>& c, const Cell<T>& L, const Cell<T>& R,
                                               NewtonEval<T>& e) {
   const T hp = T(0.5) * p;
   e.tau1 = hp + T(0.5) * e.m;
   e.tau4 = hp - T(0.5) * e.m;
+  e.lam2 = c.lam1 + c.amb * e.tau1;
+  e.lam4 = c.lam5 - c.amb * e.tau4;
+  e.zl = c.K * (e.tau2 * e.tau2 - e.tau1 * e.tau1);
+  e.zr = e.zl - c.dZ;
+  e.F = c.dOm + e.lam2 * e.zl - e.lam4 * e.zr;
+}
+
+// The rest of the states at an evaluated point: the velocities u1 = uL + a
+// (tau1 - tauL) = lam1 + a tau1 and u4 = lam5 - a tau4, and Z* = ZL + zl.
+template <typename T>
+__device__ __forceinline__ void newton_fill(const NewtonConst<T>& c, const Cell<T>& L, NewtonEval<T>& e) {
   e.u1 = c.lam1 + c.a * e.tau1;
   e.u4 = c.lam5 - c.a * e.tau4;
-  e.lam2 = e.u1 - c.b * e.tau1;
-  e.lam4 = e.u4 + c.b * e.tau4;
-  e.Zs = L.Z + c.K * (e.tau2 * e.tau2 - e.tau1 * e.tau1);
-  e.zl = e.Zs - L.Z;
-  e.zr = e.Zs - R.Z;
-  e.F = c.dOm + e.lam2 * e.zl - e.lam4 * e.zr;
+  e.Zs = L.Z + e.zl;
 }
 
 template <typename T>
@@ -396,9 +407,8 @@ __device__ __forceinline__ void newton_eval_ip(T p, T ip, const NewtonConst<T>& 
                                                const Cell<T>& R, NewtonEval<T>& e) {
   T sigma;
   newton_sigma(p, c, e, sigma);
-  const T N = c.dZ + c.KD * sigma;
   e.ip = ip;
-  e.m = -N * e.ip * c.inv_K;                        // from Z* continuity
+  e.m = -(c.dZK + c.KDK * sigma) * ip;              // from Z* continuity: -N / (K p)
   newton_states(p, c, L, R, e);
 }
 
@@ -411,13 +421,12 @@ __device__ __forceinline__ void newton_eval(T p, const NewtonConst<T>& c, const 
 // Analytic F'(p) at an evaluated point.
 template <typename T>
 __device__ __forceinline__ T newton_deriv(const NewtonConst<T>& c, const NewtonEval<T>& e, T& dm) {
-  dm = -c.dN * e.ip * c.inv_K - e.m * e.ip;
-  const T dtau1 = T(0.5) + T(0.5) * dm;
-  const T dtau4 = T(0.5) - T(0.5) * dm;
-  const T dtau2 = T(0.5) * c.dsig;
-  const T dZs = T(2) * c.K * (e.tau2 * dtau2 - e.tau1 * dtau1);
-  // (a - b) (dtau1 zl + dtau4 zr) + (lam2 - lam4) dZs
-  return c.amb * (dtau1 * e.zl + dtau4 * e.zr) + (e.lam2 - e.lam4) * dZs;
+  dm = -(c.dNK + e.m) * e.ip;                       // (-dN/K - m) / p
+  // dtau1,4/dp = (1 +- dm)/2, dtau2,3/dp = dsig/2:
+  // dZ*/dp = 2K (tau2 dsig/2 - tau1 (1 + dm)/2)
+  const T dZs = c.K * (c.dsig * e.tau2 - e.tau1 * (T(1) + dm));
+  // (a - b) (dtau1 zl + dtau4 zr) + (lam2 - lam4) dZs, with zl - zr = dZ
+  return c.hamb * ((e.zl + e.zr) + dm * c.dZ) + (e.lam2 - e.lam4) * dZs;
 }
 
 template <typename T>
@@ -473,9 +482,8 @@ __device__ __forceinline__ bool newton_loop(const NewtonConst<T>& c, const Cell<
         tr.m = e.m + dm * step;
         tr.ip = e.ip - (e.ip * e.ip) * step;
       } else {
-        const T N = c.dZ + c.KD * sigma;
         tr.ip = tdiv(T(1), pn);
-        tr.m = -N * tr.ip * c.inv_K;
+        tr.m = -(c.dZK + c.KDK * sigma) * tr.ip;
       }
       newton_states(pn, c, L, R, tr);
       if (newton_positive(tr)) {
@@ -609,6 +617,10 @@ __device__ __forceinline__ T newton_setup(const DevParams& P, const Cell<T>& L, 
   c.dsig = -c.amb * c.inv_b;
   c.KD = c.K * c.D;
   c.dN = c.KD * c.dsig;
+  c.dZK = c.dZ * c.inv_K;
+  c.KDK = c.KD * c.inv_K;
+  c.dNK = c.dN * c.inv_K;
+  c.hamb = T(0.5) * c.amb;
   c.s0 = c.C0 * c.inv_b;
   c.hD = T(0.5) * c.D;
   c.lam1 = L.un - a * L.tau;
@@ -643,7 +655,8 @@ __device__ __forceinline__ void fan_fluctuations(const DevParams& P, const Cell<
   const T a = c.a, b = c.b;
   const T lam1 = c.lam1;
   const T lam5 = c.lam5;
-  const T us = e.u1 + b * (e.tau2 - e.tau1);
+  const T u1 = c.lam1 + a * e.tau1, u4 = c.lam5 - a * e.tau4;
+  const T us = u1 + b * (e.tau2 - e.tau1);
   const T lam2 = e.lam2, lam4 = e.lam4;
   // The fan's speeds are ordered (lam1 < lam2 < u* < lam4 < lam5 for
   // positive tau_k and a > b), so state m follows from the signs of the
@@ -668,7 +681,7 @@ __device__ __forceinline__ void fan_fluctuations(const DevParams& P, const Cell<
     // W3, W4 the right ones
     const bool right = n3 || n4;  // m = 3 or 4
     const T tk = n4 ? e.tau4 : (n3 ? e.tau3 : (n2 ? e.tau2 : e.tau1));
-    const T uk = n4 ? e.u4 : ((n2 || n3) ? us : e.u1);
+    const T uk = n4 ? u4 : ((n2 || n3) ? us : u1);
     tkv = tk;
     ukv = uk;
     vkv = right ? R.ut : L.ut;

@@ -55,6 +55,7 @@ __global__ void vjp_pairs(DevParams P, const double* in, double* out, int n) {
   // diagnostics: the fan state and the celerity branch
   NewtonEval<double> ee;
   newton_eval(p, c, L, R, ee);
+  newton_fill(c, L, ee);  // u1, u4, Z* at the root
   const double lam1 = L.un - a * L.tau, lam5 = R.un + a * R.tau, us = ee.u1 + b * (ee.tau2 - ee.tau1);
   o[21] = (double)((lam1 < 0) + (ee.lam2 < 0) + (us < 0) + (ee.lam4 < 0) + (lam5 < 0));
   o[22] = raised ? 1.0 : 0.0;
