@@ -351,27 +351,29 @@ struct NewtonConst {
   T a, b, K, inv_a, inv_b, inv_K, D, C0, dZ, dsig, dN;
   // combinations the evaluation uses as they are (loop invariants of the
   // Newton iteration): sigma = s0 + dsig p, tau2,3 = sigma/2 -+ hD,
-  // m = -(N / K) / p with N / K = dZK + KDK sigma (N = dZ + KD sigma),
+  // m = -(N / K) / p with N / K = dZK + D sigma (N = dZ + KD sigma),
   // lam2 = lam1 + amb tau1, lam4 = lam5 - amb tau4 (amb = a - b),
-  // F = dOm + lam2 zl - lam4 zr; F' uses dNK = dN / K and hamb = amb / 2
+  // F = (lam2 - lam4) zl + (dOm + lam4 dZ); F' uses dNK = dN / K = D dsig;
+  // the fan uses a2 = a^2
   T s0, hD, KD, lam1, lam5, dOm, amb;
-  T dZK, KDK, dNK, hamb;
+  T dZK, dNK, a2;
 };
 
 // The intermediate states as functions of p (every invariant relation of the
 // a- and b-waves and the contact holds for any p) and the residual F(p) of
 // the one remaining condition, continuity of Omega across the contact.
-// (u1, u4, Zs: set by newton_fill, for the states at the root only.)
+// (u1, u4, Zs, zr: set by newton_fill, for the states at the root only.)
 template <typename T>
 struct NewtonEval {
   T tau1, tau2, tau3, tau4, u1, u4, lam2, lam4, Zs, F;
-  T m, ip, zl, zr;  // kept for F'(p)
+  T m, ip, zl, zr, dl;  // kept for F'(p); dl = lam2 - lam4
 };
 
 // The states at p given m = tau1 - tau4 and 1/p (e.tau2, e.tau3 set): what
 // F needs -- the b-wave speeds lam2 = u1 - b tau1 = lam1 + (a - b) tau1 and
-// lam4 = lam5 - (a - b) tau4, the bed jumps zl = Z* - ZL = K (tau2^2 -
-// tau1^2) and zr = Z* - ZR = zl - (ZR - ZL).
+// lam4 = lam5 - (a - b) tau4, the bed jump zl = Z* - ZL = K (tau2^2 -
+// tau1^2); with zr = Z* - ZR = zl - (ZR - ZL), F = dOm + lam2 zl - lam4 zr =
+// (lam2 - lam4) zl + (dOm + lam4 dZ).
 template <typename T>
 __device__ __forceinline__ void newton_states(T p, const NewtonConst<T>& c, const Cell<T>& L, const Cell<T>& R,
                                               NewtonEval<T>& e) {
@@ -381,17 +383,19 @@ __device__ __forceinline__ void newton_states(T p, const NewtonConst<T>& c, cons
   e.lam2 = c.lam1 + c.amb * e.tau1;
   e.lam4 = c.lam5 - c.amb * e.tau4;
   e.zl = c.K * (e.tau2 * e.tau2 - e.tau1 * e.tau1);
-  e.zr = e.zl - c.dZ;
-  e.F = c.dOm + e.lam2 * e.zl - e.lam4 * e.zr;
+  e.dl = e.lam2 - e.lam4;
+  e.F = e.dl * e.zl + (c.dOm + e.lam4 * c.dZ);
 }
 
 // The rest of the states at an evaluated point: the velocities u1 = uL + a
-// (tau1 - tauL) = lam1 + a tau1 and u4 = lam5 - a tau4, and Z* = ZL + zl.
+// (tau1 - tauL) = lam1 + a tau1 and u4 = lam5 - a tau4, Z* = ZL + zl and
+// zr = Z* - ZR = zl - dZ.
 template <typename T>
 __device__ __forceinline__ void newton_fill(const NewtonConst<T>& c, const Cell<T>& L, NewtonEval<T>& e) {
   e.u1 = c.lam1 + c.a * e.tau1;
   e.u4 = c.lam5 - c.a * e.tau4;
   e.Zs = L.Z + e.zl;
+  e.zr = e.zl - c.dZ;
 }
 
 template <typename T>
@@ -408,7 +412,7 @@ __device__ __forceinline__ void newton_eval_ip(T p, T ip, const NewtonConst<T>& 
   T sigma;
   newton_sigma(p, c, e, sigma);
   e.ip = ip;
-  e.m = -(c.dZK + c.KDK * sigma) * ip;              // from Z* continuity: -N / (K p)
+  e.m = -(c.dZK + c.D * sigma) * ip;                // from Z* continuity: -N / (K p)
   newton_states(p, c, L, R, e);
 }
 
@@ -425,8 +429,9 @@ __device__ __forceinline__ T newton_deriv(const NewtonConst<T>& c, const NewtonE
   // dtau1,4/dp = (1 +- dm)/2, dtau2,3/dp = dsig/2:
   // dZ*/dp = 2K (tau2 dsig/2 - tau1 (1 + dm)/2)
   const T dZs = c.K * (c.dsig * e.tau2 - e.tau1 * (T(1) + dm));
-  // (a - b) (dtau1 zl + dtau4 zr) + (lam2 - lam4) dZs, with zl - zr = dZ
-  return c.hamb * ((e.zl + e.zr) + dm * c.dZ) + (e.lam2 - e.lam4) * dZs;
+  // (a - b) (dtau1 zl + dtau4 zr) + (lam2 - lam4) dZs, where dtau1 zl +
+  // dtau4 zr = zl + (dm - 1) dZ / 2 (zr = zl - dZ)
+  return c.amb * (e.zl + (T(0.5) * dm - T(0.5)) * c.dZ) + e.dl * dZs;
 }
 
 template <typename T>
@@ -483,7 +488,7 @@ __device__ __forceinline__ bool newton_loop(const NewtonConst<T>& c, const Cell<
         tr.ip = e.ip - (e.ip * e.ip) * step;
       } else {
         tr.ip = tdiv(T(1), pn);
-        tr.m = -(c.dZK + c.KDK * sigma) * tr.ip;
+        tr.m = -(c.dZK + c.D * sigma) * tr.ip;
       }
       newton_states(pn, c, L, R, tr);
       if (newton_positive(tr)) {
@@ -583,7 +588,8 @@ __device__ __forceinline__ T newton_setup(const DevParams& P, const Cell<T>& L, 
                                           NewtonConst<T>& c, T* ip0 = nullptr) {
   const T g = par<T>(P.g, P.f.g);
   const T ab = a * b;
-  const T a2mb2 = a * a - b * b;
+  c.a2 = a * a;
+  const T a2mb2 = c.a2 - b * b;
   const T du = R.un - L.un;
   c.C0 = du + a * (L.tau + R.tau);  // a p0
   T rab;
@@ -618,9 +624,7 @@ __device__ __forceinline__ T newton_setup(const DevParams& P, const Cell<T>& L, 
   c.KD = c.K * c.D;
   c.dN = c.KD * c.dsig;
   c.dZK = c.dZ * c.inv_K;
-  c.KDK = c.KD * c.inv_K;
-  c.dNK = c.dN * c.inv_K;
-  c.hamb = T(0.5) * c.amb;
+  c.dNK = c.D * c.dsig;  // dN / K (K inv_K = 1)
   c.s0 = c.C0 * c.inv_b;
   c.hD = T(0.5) * c.D;
   c.lam1 = L.un - a * L.tau;
@@ -665,7 +669,7 @@ __device__ __forceinline__ void fan_fluctuations(const DevParams& P, const Cell<
   // (fan_state; the same rule wherever rounding breaks the order).
   const bool n1 = negative(lam1), n2 = negative(lam2), n3 = negative(us), n4 = negative(lam4),
              n5 = negative(lam5);
-  const T a2 = a * a;
+  const T a2 = c.a2;
   // flux (H un, H un^2 + Pi, H un ut) of L, R and of the state m
   const T FhL = L.Hn, FqL = L.Hn * L.un + L.Pi, FvL = L.Hn * L.ut;
   const T FhR = R.Hn, FqR = R.Hn * R.un + R.Pi, FvR = R.Hn * R.ut;
@@ -689,7 +693,7 @@ __device__ __forceinline__ void fan_fluctuations(const DevParams& P, const Cell<
   }
   // b-waves: bed jumps and the non-conservative source g Hbar [Z]; one
   // divide for 1/tau_k, 1/(tau1 + tau2) and 1/(tau3 + tau4)
-  const T zj2 = e.zl, zj4 = -e.zr;  // Z* - ZL, ZR - Z*
+  const T zj2 = e.zl, zj4 = c.dZ - e.zl;  // Z* - ZL, ZR - Z*
   const T d12 = e.tau1 + e.tau2, d34 = e.tau3 + e.tau4;
   const T g2 = par<T>(P.two_g, P.f.two_g);
   T S2, S4, Hk;
@@ -700,9 +704,9 @@ __device__ __forceinline__ void fan_fluctuations(const DevParams& P, const Cell<
   } else {
     const T d1234 = d12 * d34;
     const T r = tdiv(T(1), tkv * d1234);
-    const T rt = r * tkv;
-    S2 = (g2 * zj2) * (rt * d34);
-    S4 = (g2 * zj4) * (rt * d12);
+    const T grt = g2 * (r * tkv);
+    S2 = zj2 * (grt * d34);
+    S4 = zj4 * (grt * d12);
     Hk = r * d1234;
   }
   if (inner) {
