@@ -44,7 +44,7 @@ L2_FLUSH_BYTES = 256 << 20
 # DRAM bytes (read + write) of one interface-kernel launch on this workload,
 # from the ncu capture summarised in profiles/interface_kernel_dune2d_fp64_1024x512.md,
 # valid only for the kernel source it was taken with (sha256 prefix)
-IFACE_TRAFFIC = {"sha256": "862f0a641e094088", "bytes": 94_050_048}
+IFACE_TRAFFIC = {"sha256": "b0de5f66329ab712", "bytes": 94_304_256}
 
 
 def workload_desc(nx, ny, workload="dune2d", precision="fp64"):
