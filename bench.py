@@ -744,14 +744,14 @@ def measure_call(sve, torch, w, prec, spinup, warmup, steps):
 
 def march_shape(nx, ny, nsm=None):
     """Strips and runs of rows of the FP32 solve pass for a grid (the launch
-    shape the library picks: 30 columns a strip, rows a run so that ~16 warps
-    per SM are busy, 8 to 32)."""
+    shape the library picks: 30 columns a strip, rows a run so that every SM
+    has its 20 resident warps, 4 to 32)."""
     if nsm is None:
         import torch
 
         nsm = torch.cuda.get_device_properties(0).multi_processor_count
     strips = -(-nx // 30)
-    rows = min(32, max(8, -(-(strips * ny) // (16 * nsm))))
+    rows = min(32, max(4, -(-(strips * ny) // (20 * nsm))))
     return strips, -(-ny // rows)
 
 

@@ -25,11 +25,12 @@ constexpr int kMCols = 30;    // interior columns per strip (32 lanes: 30 + two 
 constexpr int kMWarps = 4;    // warps per block
 constexpr int kMThreads = 32 * kMWarps;
 
-// Runs of rows per strip: as many rows per warp as keep about 16 warps per SM
-// busy, at least 8 rows (so that the one extra row of y-solves per run stays
-// small) and at most 32 (on the 8192 x 4096 antidune runs of 32 rows measured
-// 2.3 % faster than 64 and 1.6 % faster than 16; warps drawing their runs
-// from a ticket counter instead of one run per warp made no difference).
+// Runs of rows per strip: as many rows per warp as give every SM its 20
+// resident warps (five 4-warp blocks), at least 4 rows (the one extra row of
+// y-solves per run costs 1/rows) and at most 32 (on the 8192 x 4096
+// antidune runs of 32 rows measured 2.3 % faster than 64 and 1.6 % faster
+// than 16; warps drawing their runs from a ticket counter instead of one run
+// per warp made no difference).
 struct MarchShape {
   int strips, rows, chunks;
   long long tasks;
@@ -39,9 +40,9 @@ struct MarchShape {
 inline MarchShape march_shape(const DevParams& P, int nsm) {
   MarchShape M;
   M.strips = (P.nx + kMCols - 1) / kMCols;
-  const long long want = 16LL * nsm;  // warps in flight
+  const long long want = 20LL * nsm;  // warps in flight
   long long rows = ((long long)M.strips * P.ny + want - 1) / want;
-  rows = rows < 8 ? 8 : (rows > 32 ? 32 : rows);
+  rows = rows < 4 ? 4 : (rows > 32 ? 32 : rows);
   M.rows = (int)rows;
   M.chunks = (P.ny + M.rows - 1) / M.rows;
   M.tasks = (long long)M.strips * M.chunks;
